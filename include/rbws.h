@@ -1,0 +1,162 @@
+/*
+ * rbws.h -- C ABI of librbws, a GB300 (sm_103a) implementation of the online
+ * hot path of the reduced basis warm-start (RBWS) iterative method
+ * (Hou, Chen & Xia, arXiv 2311.13862).
+ *
+ * The library solves, for a batch of parameters mu, the parametrised system of
+ * Eq. (1), A(mu) u = f, where A(mu) = sum_q mu_q A_q is the 7-point finite
+ * difference discretisation of -div(kappa grad u) on the unit cube with zero
+ * Dirichlet data (the diffusion model of Sec. 4), kappa piecewise constant on
+ * Q block subdomains (kappa = mu_q on subdomain q).  The interior grid has
+ * nx*ny*nz nodes, h = 1/(n+1) per axis, the face coefficient between two nodes
+ * is the arithmetic mean of their kappa (a boundary face takes the interior
+ * node's kappa), and the 1/h^2 scaling is part of A.
+ *
+ * Conventions for every call:
+ *  - Vectors on the grid are planar: instance b, node (i,j,k) is element
+ *    b*n_dof + (k*ny + j)*nx + i (x fastest), n_dof = nx*ny*nz.
+ *  - Parameter arrays are host arrays, row-major [B][Q], float64, copied by
+ *    the call.
+ *  - "device" pointers are CUDA device pointers on the problem's device
+ *    (e.g. a torch tensor's data_ptr()); the caller owns them.  The library
+ *    owns the problem, its reduced basis and surrogate network, and its own
+ *    workspace (allocated lazily, kept until rbws_problem_destroy).
+ *  - Calls are synchronous: they return after their GPU work is complete.
+ *  - Negative status = error, nothing usable was produced; positive = result
+ *    usable with a warning.  rbws_last_error() gives a message (thread-local).
+ *    No C++ exception crosses this interface.
+ *  - A problem handle must not be used by two threads at once.
+ */
+#ifndef RBWS_H
+#define RBWS_H
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RBWS_API __attribute__((visibility("default")))
+#else
+#define RBWS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbws_problem_s* rbws_problem; /* opaque, library-owned */
+
+typedef enum {
+  RBWS_OK = 0,
+  RBWS_WARN_NOT_CONVERGED = 1, /* some instances hit max_iters or broke down */
+  RBWS_ERR_INVALID_ARG = -1,
+  RBWS_ERR_OOM = -2,
+  RBWS_ERR_CUDA = -3,
+  RBWS_ERR_NO_BASIS = -4,      /* a reduced basis / surrogate is required first */
+  RBWS_ERR_NOT_SPD = -5,       /* a reduced matrix failed its Cholesky factorisation */
+  RBWS_ERR_DEVICE_TIMEOUT = -6,
+  RBWS_ERR_STATE = -7,
+  RBWS_ERR_UNSUPPORTED = -8
+} rbws_status;
+
+/* Initial value of the online solve (Algorithm 4, line 2). */
+typedef enum {
+  RBWS_WARM_ZERO = 0,               /* u0 = 0 (the zero-start baseline)           */
+  RBWS_WARM_GALERKIN = 1,           /* u0 = W A_N(mu)^{-1} W^T f (Sec. 2.3)       */
+  RBWS_WARM_LEARNED = 2,            /* u0 = W c_net(mu), surrogate network          */
+  RBWS_WARM_LEARNED_CORRECTED = 3   /* c_net plus one reduced CG step on A_N c = f_N */
+} rbws_warm_mode;
+
+/* Preconditioner P of Algorithm 1. */
+typedef enum {
+  RBWS_PREC_NONE = 0,   /* plain CG                                           */
+  RBWS_PREC_JACOBI = 1, /* P(r) = D^{-1} r, D = diag(A(mu))                      */
+  RBWS_PREC_MSRB = 2    /* Algorithm 3: one Jacobi sweep + RB correction (W)     */
+} rbws_precond;
+
+typedef enum {
+  RBWS_FP64 = 0,    /* all CG arithmetic in FP64                                */
+  RBWS_FP32_IR = 1  /* FP32 inner PCG inside FP64 iterative refinement          */
+} rbws_precision;
+
+typedef struct { int32_t nx, ny, nz; } rbws_grid;   /* interior nodes per axis */
+typedef struct { int32_t bx, by, bz; } rbws_blocks; /* block rule, Q = bx*by*bz */
+
+typedef struct {
+  int32_t max_iters;    /* L_max of Algorithm 1 (counted over all restarts)     */
+  int32_t precond;      /* rbws_precond                                          */
+  int32_t precision;    /* rbws_precision                                        */
+  int32_t max_restarts; /* true-residual restarts of Algorithm 4 (default 3)     */
+  double inner_tol;     /* FP32_IR: relative reduction per inner solve (1e-5)   */
+  int32_t max_outer;    /* FP32_IR: maximum refinement steps (10)                */
+  int32_t check_every;  /* iterations between host convergence polls (0 = auto)  */
+  void* stream;         /* cudaStream_t for all work, NULL = legacy default      */
+} rbws_options;
+
+/* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64). */
+RBWS_API void rbws_options_default(rbws_options* opt);
+
+/* Creates a problem on CUDA device `device` (Eq. 1).  The subdomain of each
+ * node follows the block rule: along an axis with n nodes and b blocks, node
+ * i (1..n) lies in block min(floor(b*i/(n+1)), b-1); id = (kz*by+ky)*bx+kx.
+ * Exactly one of `blocks` / `subdomain_map` must be non-NULL; explicit maps
+ * ([nz][ny][nx] uint8, values < Q) currently return RBWS_ERR_UNSUPPORTED.
+ * Q must equal bx*by*bz and be <= 64.  f_host: host [n_dof] right-hand side,
+ * or NULL for f = 1 at every interior node (copied).  Each axis needs
+ * 2 <= n <= 1024. */
+RBWS_API rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
+                                const uint8_t* subdomain_map, int32_t Q, const double* f_host,
+                                int device, rbws_problem* out);
+RBWS_API void rbws_problem_destroy(rbws_problem p);
+
+/* Problem sizes: n_dof, Q and the current reduced basis dimension N (0 if
+ * none).  Any pointer may be NULL. */
+RBWS_API rbws_status rbws_problem_info(rbws_problem p, int64_t* n_dof, int32_t* Q, int32_t* N);
+
+/* y[b] = A(mu[b]) x[b] for B instances (the stencil of Eq. 1 applied
+ * matrix-free).  x, y: device [B][n_dof], float64 (RBWS_FP64) or float32
+ * (RBWS_FP32_IR selects the FP32 kernel).  stream: cudaStream_t or NULL. */
+RBWS_API rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, const void* x,
+                                void* y, int32_t precision, void* stream);
+
+/* Offline greedy (Algorithm 5's loop with the Galerkin RB of Sec. 2.3 and a
+ * residual indicator): first parameter = mu_train[0]; snapshot solves by
+ * Jacobi-PCG to snapshot_tol; Gram-Schmidt applied twice; the next parameter
+ * maximises eta(mu) = ||f - A(mu) W c(mu)|| / ||f|| over the training points
+ * not yet selected (ties: smallest index).  Stops at n_max, when max eta <
+ * greedy_tol, or when a snapshot adds no new direction (||w|| < 1e-10 ||u||).
+ * Replaces any previous basis.  selected_out [n_max], eta_hist_out [n_max]
+ * (eta_hist[k] = max eta once the basis has k+1 vectors) may be NULL. */
+RBWS_API rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
+                                int32_t n_max, double greedy_tol, double snapshot_tol,
+                                int32_t* selected_out, double* eta_hist_out, int32_t* n_out);
+
+/* Installs a reduced basis computed elsewhere: W host [N][n_dof] (orthonormal
+ * columns stored one after another), ANq host [Q][N][N] = W^T A_q W,
+ * fN host [N] = W^T f.  Copied. */
+RBWS_API rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const double* ANq,
+                           const double* fN);
+/* Copies the basis out: W host [N][n_dof], ANq host [Q][N][N], fN host [N];
+ * any pointer may be NULL. */
+RBWS_API rbws_status rbws_get_basis(rbws_problem p, double* W, double* ANq, double* fN);
+
+/* Reduced Galerkin solve only: c[b] = A_N(mu[b])^{-1} f_N, host out [B][N]. */
+RBWS_API rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, double* c_out);
+
+/* Online batched solve: Algorithm 4 with the chosen initial value and
+ * preconditioner for B parameters.  Stopping test ||r||_2/||f||_2 < tol on
+ * the recursive residual, then a true-residual check with restarts.
+ * u_out: device [B][n_dof] float64.  iters_out (host [B]) = applications of
+ * A to a search direction (inner iterations for FP32_IR), 0 if the initial
+ * value already meets tol.  relres_out (host [B], may be NULL) = final true
+ * relative residual.  status_out (host [B], may be NULL): 0 converged,
+ * 1 max_iters, 2 breakdown.  opt may be NULL (defaults).  Returns RBWS_OK,
+ * RBWS_WARN_NOT_CONVERGED, or an error. */
+RBWS_API rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double tol,
+                             int32_t warm, const rbws_options* opt, void* u_out,
+                             int32_t* iters_out, double* relres_out, int32_t* status_out);
+
+/* Thread-local message for the last error (never NULL). */
+RBWS_API const char* rbws_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

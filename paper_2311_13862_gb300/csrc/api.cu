@@ -1,0 +1,888 @@
+// api.cu -- the C ABI of librbws and the host-side orchestration: problem
+// set-up, the batched PCG driver (CUDA-graph captured iterations with device
+// convergence masks), FP32-inner / FP64-outer refinement, the Galerkin warm
+// start and the offline greedy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace rbws;
+
+namespace rbws {
+
+static thread_local std::string g_last_error = "";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return RBWS_ERR_CUDA;
+}
+
+}  // namespace rbws
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return (rbws_status)cuda_fail(e_, #call); \
+  } while (0)
+
+#define CKI(call)                                       \
+  do {                                                  \
+    int r_ = (call);                                    \
+    if (r_ != 0) return (rbws_status)r_;                \
+  } while (0)
+
+namespace {
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+AxisClasses make_axis(int n, int b) {
+  AxisClasses a;
+  a.n = n;
+  a.b = b;
+  a.cls.resize(n);
+  auto blk = [&](int i) {  // i: 1..n
+    int k = (int)(((int64_t)b * i) / (n + 1));
+    return k < b - 1 ? k : b - 1;
+  };
+  std::map<std::tuple<int, int, int>, int> ids;
+  for (int i = 1; i <= n; i++) {
+    const int own = blk(i), lo = i > 1 ? blk(i - 1) : -1, hi = i < n ? blk(i + 1) : -1;
+    auto key = std::make_tuple(own, lo, hi);
+    auto it = ids.find(key);
+    int id;
+    if (it == ids.end()) {
+      id = (int)ids.size();
+      ids[key] = id;
+      a.key.push_back((int8_t)own);
+      a.key.push_back((int8_t)lo);
+      a.key.push_back((int8_t)hi);
+    } else {
+      id = it->second;
+    }
+    a.cls[i - 1] = (uint8_t)id;
+  }
+  return a;
+}
+
+}  // namespace
+
+struct rbws_problem_s {
+  int device = 0;
+  int nx = 0, ny = 0, nz = 0, bx = 1, by = 1, bz = 1, Q = 1;
+  int64_t n = 0;
+  double sx = 0, sy = 0, sz = 0;
+  AxisClasses ax, ay, az;
+  uint8_t* d_cls = nullptr;  // cx | cy | cz
+  int8_t* d_keys = nullptr;  // kx | ky | kz
+  Geo geo{};
+  double* d_f = nullptr;     // nullptr: f == 1
+  double* d_ones = nullptr;  // ones vector (for W^T f when f == 1)
+  double fnorm = 0.0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  int* h_active = nullptr;   // pinned
+  // reduced basis
+  int N = 0;
+  double* d_W = nullptr;    // [N][n]
+  double* d_ANq = nullptr;  // [Q][N][N]
+  double* d_fN = nullptr;   // [N]
+  std::vector<double> h_ANq, h_fN;  // packed [Q][N][N], [N]
+  std::map<std::string, DevBuf> bufs;
+
+  void* buf(const std::string& name, size_t bytes, int* err) {
+    DevBuf& d = bufs[name];
+    if (d.bytes < bytes) {
+      if (d.ptr) cudaFree(d.ptr);
+      d.ptr = nullptr;
+      d.bytes = 0;
+      cudaError_t e = cudaMalloc(&d.ptr, bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("out of device memory allocating " + name + " (" + std::to_string(bytes) + " B)");
+        *err = RBWS_ERR_OOM;
+        return nullptr;
+      }
+      d.bytes = bytes;
+    }
+    return d.ptr;
+  }
+};
+
+namespace {
+
+Tile choose_tile(int nx) {
+  Tile t;
+  t.tx = nx >= 64 ? 64 : (nx > 16 ? 32 : 16);
+  t.ty = 256 / t.tx;
+  return t;
+}
+
+// z-chunking: enough CTAs for several waves, chunks of at least 8 planes.
+int choose_zc(int nz, int64_t ctas_per_chunk) {
+  int nzc = 1;
+  while (ctas_per_chunk * nzc < 8 * 1216 && (nz / (nzc * 2)) >= 8) nzc *= 2;
+  return (nz + nzc - 1) / nzc;
+}
+
+struct StreamGuard {
+  rbws_problem p;
+  bool ok = true;
+  StreamGuard(rbws_problem p_, void* user) : p(p_) {
+    cudaSetDevice(p->device);
+    cudaStream_t us = (cudaStream_t)user;
+    cudaEventRecord(p->ev, us);
+    cudaStreamWaitEvent(p->stream, p->ev, 0);
+  }
+};
+
+// Coefficient tables for B parameters already on the device.
+rbws_status coef_tables(rbws_problem p, const double* d_mu, int B, double** c64, float** c32) {
+  int err = 0;
+  const size_t ncls = (size_t)p->geo.ncls();
+  *c64 = (double*)p->buf("coef64", sizeof(double) * ncls * kCoefStride * B, &err);
+  if (err) return (rbws_status)err;
+  if (c32) {
+    *c32 = (float*)p->buf("coef32", sizeof(float) * ncls * kCoefStride * B, &err);
+    if (err) return (rbws_status)err;
+  }
+  const int8_t* kx = p->d_keys;
+  const int8_t* ky = kx + p->ax.key.size();
+  const int8_t* kz = ky + p->ay.key.size();
+  launch_coef_tables(p->geo, kx, ky, kz, p->bx, p->by, p->sx, p->sy, p->sz, p->Q, d_mu, B, *c64,
+                     c32 ? *c32 : nullptr, p->stream);
+  CK(cudaGetLastError());
+  return RBWS_OK;
+}
+
+rbws_status upload_mu(rbws_problem p, const double* mu, int B, double** d_mu, const char* name) {
+  int err = 0;
+  *d_mu = (double*)p->buf(name, sizeof(double) * (size_t)B * p->Q, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(*d_mu, mu, sizeof(double) * (size_t)B * p->Q, cudaMemcpyHostToDevice,
+                     p->stream));
+  return RBWS_OK;
+}
+
+// Sets the inner states of finished instances to CONVERGED before an inner solve.
+__global__ void k_mask_done(InstState* st, const int* done, int B, int* active) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (done[b] && st[b].status == ST_ACTIVE) {
+    st[b].status = ST_CONVERGED;
+    atomicSub(active, 1);
+  }
+}
+
+// The batched PCG driver.  On entry a.u holds the initial values.  Runs
+// Algorithm 1 with the true-residual restarts of Algorithm 4.
+// `done` (device [B] or nullptr) marks instances that must not run; with
+// check_true = false the true-residual check is skipped (inner solves of
+// FP32_IR, whose outer loop checks the FP64 residual itself).
+template <typename T>
+rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int check_every,
+                    const int* done, bool check_true) {
+  cudaStream_t s = p->stream;
+  CK(cudaMemsetAsync(a.active, 0, sizeof(int), s));
+  launch_cg_init<T>(a, t, 0, 0, s);
+  launch_cg_finalize<T>(a, 0, 0, max_restarts, s);
+  if (done) k_mask_done<<<(a.B + 127) / 128, 128, 0, s>>>(a.st, done, a.B, a.active);
+  CK(cudaGetLastError());
+  int M = check_every > 0 ? check_every : 8;
+  if (M % 2) M++;
+  // Capture M iterations (parities 0,1,0,1,...) once; relaunch until done.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < M; k++) {
+    launch_cg_a<T>(a, t, k & 1, s);
+    launch_cg_b<T>(a, t, k & 1, s);
+  }
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
+  }
+  rbws_status rc = RBWS_OK;
+  for (;;) {
+    cudaMemcpyAsync(p->h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+      rc = (rbws_status)cuda_fail(ce, "solve loop");
+      break;
+    }
+    if (*p->h_active > 0) {
+      if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+        rc = (rbws_status)cuda_fail(ce, "cudaGraphLaunch");
+        break;
+      }
+      continue;
+    }
+    if (!check_true) break;
+    // all stopped: check the true residual f - A u, restart the failures
+    launch_cg_init<T>(a, t, 0, 0, s);
+    launch_cg_finalize<T>(a, 0, 1, max_restarts, s);
+    cudaMemcpyAsync(p->h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+      rc = (rbws_status)cuda_fail(ce, "true residual");
+      break;
+    }
+    if (*p->h_active == 0) break;
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  return rc;
+}
+
+template <typename T>
+rbws_status make_cg_args(rbws_problem p, int B, Tile t, const T* coef, T* u, CGArgs<T>* out,
+                         const std::string& tag) {
+  int err = 0;
+  CGArgs<T> a{};
+  a.g = p->geo;
+  a.B = B;
+  a.tiles_x = (p->nx + t.tx - 1) / t.tx;
+  a.tiles_y = (p->ny + t.ty - 1) / t.ty;
+  a.zc = choose_zc(p->nz, (int64_t)a.tiles_x * a.tiles_y * B);
+  a.nzc = (p->nz + a.zc - 1) / a.zc;
+  a.P = a.tiles_x * a.tiles_y * a.nzc;
+  a.coef = coef;
+  a.u = u;
+  const size_t vb = sizeof(T) * (size_t)B * p->n;
+  a.r = (T*)p->buf(tag + "r", vb, &err);
+  if (!err) a.s = (T*)p->buf(tag + "s", vb, &err);
+  if (!err) a.p0 = (T*)p->buf(tag + "p0", vb, &err);
+  if (!err) a.p1 = (T*)p->buf(tag + "p1", vb, &err);
+  if (!err) a.q = (T*)p->buf(tag + "q", vb, &err);
+  if (!err) a.rho_rr = (double2*)p->buf(tag + "rho_rr", sizeof(double2) * 2 * (size_t)B * a.P, &err);
+  if (!err) a.gam = (double*)p->buf(tag + "gam", sizeof(double) * (size_t)B * a.P, &err);
+  if (!err) a.st = (InstState*)p->buf(tag + "st", sizeof(InstState) * (size_t)B, &err);
+  if (!err) a.active = (int*)p->buf(tag + "active", sizeof(int) * 4, &err);
+  if (!err) a.fnorm = (const double*)p->buf(tag + "fnorm", sizeof(double) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  *out = a;
+  return RBWS_OK;
+}
+
+__global__ void k_fill(double* x, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+// u[b] += scale[b] * d[b] for instances not yet done (FP32_IR update).
+__global__ void k_ir_update(int64_t n, int B, const float* __restrict__ d,
+                            const double* __restrict__ scale, const int* __restrict__ done,
+                            double* __restrict__ u) {
+  const int b = blockIdx.y;
+  if (done[b]) return;
+  const double sc = scale[b];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[(int64_t)b * n + i] = fma(sc, (double)d[(int64_t)b * n + i], u[(int64_t)b * n + i]);
+}
+
+void fill(double* x, int64_t n, double v, cudaStream_t s) {
+  k_fill<<<152 * 4, 256, 0, s>>>(x, n, v);
+}
+
+// Per-instance FP64 true residual norms ||f - A u|| / ||f||  (B values, device).
+rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const double* u,
+                           double* r_out, double* rel_dev) {
+  Tile t = choose_tile(p->nx);
+  const int tiles = ((p->nx + t.tx - 1) / t.tx) * ((p->ny + t.ty - 1) / t.ty);
+  const int zc = choose_zc(p->nz, (int64_t)tiles * B);
+  const int P = tiles * ((p->nz + zc - 1) / zc);
+  int err = 0;
+  double* part = (double*)p->buf("res_part", sizeof(double) * (size_t)B * P, &err);
+  if (err) return (rbws_status)err;
+  launch_residual64(p->geo, t, zc, coef64, B, p->d_f, u, r_out, part, P, p->stream);
+  launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->stream);
+  CK(cudaGetLastError());
+  return RBWS_OK;
+}
+
+// Galerkin warm start u[b] = W A_N(mu_b)^{-1} fN.
+rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u) {
+  if (p->N <= 0) {
+    set_error("no reduced basis: run rbws_offline_greedy or rbws_set_basis first");
+    return RBWS_ERR_NO_BASIS;
+  }
+  int err = 0;
+  double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
+  int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, p->stream);
+  launch_lift(p->n, p->N, p->d_W, C, B, u, p->stream);
+  CK(cudaGetLastError());
+  std::vector<int> h(B);
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  for (int b = 0; b < B; b++)
+    if (h[b] != 0) {
+      set_error("reduced matrix A_N(mu) is not positive definite for instance " + std::to_string(b));
+      return RBWS_ERR_NOT_SPD;
+    }
+  return RBWS_OK;
+}
+
+rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, const rbws_options& o,
+                       double* u, std::vector<InstState>& st) {
+  double* coef64 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &coef64, nullptr));
+  Tile t = choose_tile(p->nx);
+  CGArgs<double> a{};
+  CKI(make_cg_args<double>(p, B, t, coef64, u, &a, "d_"));
+  a.f = p->d_f;
+  a.tol = tol;
+  a.max_iters = o.max_iters;
+  a.precond = o.precond;
+  fill((double*)a.fnorm, B, p->fnorm, p->stream);
+  CKI(run_pcg<double>(p, a, t, o.max_restarts, o.check_every, nullptr, true));
+  st.resize(B);
+  CK(cudaMemcpyAsync(st.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return RBWS_OK;
+}
+
+// FP32 inner Jacobi-PCG inside FP64 iterative refinement:
+//   r = f - A u (FP64);  stop if ||r||/||f|| < tol;  solve A d = r/||r|| in FP32
+//   to a relative reduction inner_tol;  u += ||r|| d (FP64).
+rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
+                          const rbws_options& o, double* u, std::vector<InstState>& st) {
+  double* coef64 = nullptr;
+  float* coef32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &coef64, &coef32));
+  Tile t = choose_tile(p->nx);
+  CGArgs<float> a{};
+  int err = 0;
+  float* d = (float*)p->buf("ir_d", sizeof(float) * (size_t)B * p->n, &err);
+  double* r64 = err ? nullptr : (double*)p->buf("ir_r64", sizeof(double) * (size_t)B * p->n, &err);
+  double* rel = err ? nullptr : (double*)p->buf("ir_rel", sizeof(double) * (size_t)B, &err);
+  double* rnorm = err ? nullptr : (double*)p->buf("ir_rnorm", sizeof(double) * (size_t)B, &err);
+  int* done = err ? nullptr : (int*)p->buf("ir_done", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  CKI(make_cg_args<float>(p, B, t, coef32, d, &a, "f_"));
+  a.f = nullptr;
+  a.rhs64 = r64;
+  a.tol = o.inner_tol;
+  a.precond = o.precond;
+  std::vector<double> h_rel(B);
+  std::vector<int> h_done(B, 0);
+  std::vector<InstState> inner(B);
+  st.assign(B, InstState{ST_ACTIVE, 0, 0, 0, 0.0, 0.0});
+  for (int outer = 0;; outer++) {
+    CKI(residual_norms(p, coef64, B, u, r64, rel));
+    CK(cudaMemcpyAsync(h_rel.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    int left = 0;
+    for (int b = 0; b < B; b++) {
+      if (outer == 0) st[b].relres0 = h_rel[b];
+      st[b].relres = h_rel[b];
+      if (!h_done[b]) {
+        if (h_rel[b] < tol) {
+          h_done[b] = 1;
+          st[b].status = ST_CONVERGED;
+        } else if (!(h_rel[b] == h_rel[b])) {
+          h_done[b] = 1;
+          st[b].status = ST_BREAKDOWN;
+        } else if (outer >= o.max_outer || st[b].iters >= o.max_iters) {
+          h_done[b] = 1;
+          st[b].status = ST_MAX_ITERS;
+        }
+      }
+      left += !h_done[b];
+    }
+    if (!left) break;
+    // inner system: A d = r / ||r||; the relative test uses ||r_in|| / 1
+    std::vector<double> hn(B);
+    for (int b = 0; b < B; b++) hn[b] = h_rel[b] * p->fnorm;
+    CK(cudaMemcpyAsync(rnorm, hn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(done, h_done.data(), sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+    a.max_iters = o.max_iters;
+    // The inner right-hand side is r/||r|| (norm 1 up to FP32 rounding), so
+    // the inner relative test divides by a vector of ones.
+    double* ones = (double*)p->buf("ir_ones", sizeof(double) * (size_t)B, &err);
+    if (err) return (rbws_status)err;
+    fill(ones, B, 1.0, p->stream);
+    CGArgs<float> ai = a;
+    ai.fnorm = ones;
+    ai.rhs_scale = rnorm;
+    CKI(run_pcg<float>(p, ai, t, 0, o.check_every, done, false));
+    CK(cudaMemcpyAsync(inner.data(), ai.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost,
+                       p->stream));
+    {
+      const int threads = 256;
+      dim3 grid((unsigned)std::min<int64_t>((p->n + threads - 1) / threads, 152 * 4), B);
+      k_ir_update<<<grid, threads, 0, p->stream>>>(p->n, B, d, rnorm, done, u);
+      CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(p->stream));
+    for (int b = 0; b < B; b++)
+      if (!h_done[b]) st[b].iters += inner[b].iters;
+  }
+  return RBWS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* rbws_last_error(void) { return g_last_error.c_str(); }
+
+void rbws_options_default(rbws_options* o) {
+  if (!o) return;
+  o->max_iters = 20000;
+  o->precond = RBWS_PREC_JACOBI;
+  o->precision = RBWS_FP64;
+  o->max_restarts = 3;
+  o->inner_tol = 1e-5;
+  o->max_outer = 10;
+  o->check_every = 0;
+  o->stream = nullptr;
+}
+
+rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
+                                const uint8_t* subdomain_map, int32_t Q, const double* f_host,
+                                int device, rbws_problem* out) {
+  if (!out || !grid) {
+    set_error("rbws_problem_create: null argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if ((blocks == nullptr) == (subdomain_map == nullptr)) {
+    set_error("rbws_problem_create: give exactly one of blocks / subdomain_map");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (subdomain_map) {
+    set_error("rbws_problem_create: explicit subdomain maps are not supported by the CUDA path");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  const int dims[3] = {grid->nx, grid->ny, grid->nz};
+  for (int d : dims)
+    if (d < 2 || d > kMaxAxis) {
+      set_error("rbws_problem_create: each axis needs 2..1024 interior nodes");
+      return RBWS_ERR_INVALID_ARG;
+    }
+  if (blocks->bx < 1 || blocks->by < 1 || blocks->bz < 1 || blocks->bx > 16 || blocks->by > 16 ||
+      blocks->bz > 16 || Q != blocks->bx * blocks->by * blocks->bz || Q > kMaxQ) {
+    set_error("rbws_problem_create: need 1 <= b <= 16 per axis and Q = bx*by*bz <= 64");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (blocks->bx > grid->nx || blocks->by > grid->ny || blocks->bz > grid->nz) {
+    set_error("rbws_problem_create: more blocks than nodes along an axis");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    set_error("rbws_problem_create: CUDA device " + std::to_string(device) + " not available");
+    return RBWS_ERR_CUDA;
+  }
+  rbws_problem p = new rbws_problem_s();
+  p->device = device;
+  p->nx = grid->nx;
+  p->ny = grid->ny;
+  p->nz = grid->nz;
+  p->bx = blocks->bx;
+  p->by = blocks->by;
+  p->bz = blocks->bz;
+  p->Q = Q;
+  p->n = (int64_t)p->nx * p->ny * p->nz;
+  p->sx = (double)(p->nx + 1) * (p->nx + 1);
+  p->sy = (double)(p->ny + 1) * (p->ny + 1);
+  p->sz = (double)(p->nz + 1) * (p->nz + 1);
+  p->ax = make_axis(p->nx, p->bx);
+  p->ay = make_axis(p->ny, p->by);
+  p->az = make_axis(p->nz, p->bz);
+  auto fail = [&](cudaError_t e, const char* w) {
+    cuda_fail(e, w);
+    rbws_problem_destroy(p);
+    return RBWS_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return fail(e, "cudaSetDevice");
+  if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e, "cudaEventCreate");
+  if ((e = cudaMallocHost(&p->h_active, sizeof(int))) != cudaSuccess) return fail(e, "cudaMallocHost");
+  std::vector<uint8_t> cls;
+  cls.insert(cls.end(), p->ax.cls.begin(), p->ax.cls.end());
+  cls.insert(cls.end(), p->ay.cls.begin(), p->ay.cls.end());
+  cls.insert(cls.end(), p->az.cls.begin(), p->az.cls.end());
+  std::vector<int8_t> keys;
+  keys.insert(keys.end(), p->ax.key.begin(), p->ax.key.end());
+  keys.insert(keys.end(), p->ay.key.begin(), p->ay.key.end());
+  keys.insert(keys.end(), p->az.key.begin(), p->az.key.end());
+  if ((e = cudaMalloc(&p->d_cls, cls.size())) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->d_keys, keys.size())) != cudaSuccess) return fail(e, "cudaMalloc");
+  cudaMemcpy(p->d_cls, cls.data(), cls.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_keys, keys.data(), keys.size(), cudaMemcpyHostToDevice);
+  Geo& g = p->geo;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  g.ncx = p->ax.ncls();
+  g.ncy = p->ay.ncls();
+  g.ncz = p->az.ncls();
+  g.n = p->n;
+  g.cx = p->d_cls;
+  g.cy = p->d_cls + p->nx;
+  g.cz = p->d_cls + p->nx + p->ny;
+  if (f_host) {
+    if ((e = cudaMalloc(&p->d_f, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc f");
+    cudaMemcpy(p->d_f, f_host, sizeof(double) * p->n, cudaMemcpyHostToDevice);
+    double s = 0.0;
+    for (int64_t i = 0; i < p->n; i++) s += f_host[i] * f_host[i];
+    p->fnorm = std::sqrt(s);
+  } else {
+    p->fnorm = std::sqrt((double)p->n);
+  }
+  if ((e = cudaMalloc(&p->d_ones, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc");
+  fill(p->d_ones, p->n, 1.0, p->stream);
+  if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(e, "set-up");
+  if (!(p->fnorm > 0.0)) {
+    set_error("rbws_problem_create: f must be nonzero");
+    rbws_problem_destroy(p);
+    return RBWS_ERR_INVALID_ARG;
+  }
+  *out = p;
+  return RBWS_OK;
+}
+
+void rbws_problem_destroy(rbws_problem p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (auto& kv : p->bufs)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  cudaFree(p->d_cls);
+  cudaFree(p->d_keys);
+  cudaFree(p->d_f);
+  cudaFree(p->d_ones);
+  cudaFree(p->d_W);
+  cudaFree(p->d_ANq);
+  cudaFree(p->d_fN);
+  if (p->h_active) cudaFreeHost(p->h_active);
+  if (p->ev) cudaEventDestroy(p->ev);
+  if (p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+rbws_status rbws_problem_info(rbws_problem p, int64_t* n_dof, int32_t* Q, int32_t* N) {
+  if (!p) {
+    set_error("rbws_problem_info: null problem");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (n_dof) *n_dof = p->n;
+  if (Q) *Q = p->Q;
+  if (N) *N = p->N;
+  return RBWS_OK;
+}
+
+rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, const void* x, void* y,
+                                int32_t precision, void* stream) {
+  if (!p || !mu || !x || !y || B < 1 || B > 65535 ||
+      (precision != RBWS_FP64 && precision != RBWS_FP32_IR)) {
+    set_error("rbws_apply_operator: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, stream);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_apply"));
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &c64, precision == RBWS_FP32_IR ? &c32 : nullptr));
+  Tile t = choose_tile(p->nx);
+  if (precision == RBWS_FP64)
+    launch_apply<double>(p->geo, t, c64, B, (const double*)x, p->n, (double*)y, p->stream);
+  else
+    launch_apply<float>(p->geo, t, c32, B, (const float*)x, p->n, (float*)y, p->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->stream));
+  return RBWS_OK;
+}
+
+rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const double* ANq,
+                           const double* fN) {
+  if (!p || N < 1 || N > 256 || !W || !ANq || !fN) {
+    set_error("rbws_set_basis: invalid argument (1 <= N <= 256)");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  cudaSetDevice(p->device);
+  cudaStreamSynchronize(p->stream);
+  cudaFree(p->d_W);
+  cudaFree(p->d_ANq);
+  cudaFree(p->d_fN);
+  p->d_W = p->d_ANq = p->d_fN = nullptr;
+  p->N = 0;
+  CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)N * p->n));
+  CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)p->Q * N * N));
+  CK(cudaMalloc(&p->d_fN, sizeof(double) * (size_t)N));
+  CK(cudaMemcpy(p->d_W, W, sizeof(double) * (size_t)N * p->n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->d_ANq, ANq, sizeof(double) * (size_t)p->Q * N * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->d_fN, fN, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice));
+  p->h_ANq.assign(ANq, ANq + (size_t)p->Q * N * N);
+  p->h_fN.assign(fN, fN + N);
+  p->N = N;
+  return RBWS_OK;
+}
+
+rbws_status rbws_get_basis(rbws_problem p, double* W, double* ANq, double* fN) {
+  if (!p) {
+    set_error("rbws_get_basis: null problem");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->N <= 0) {
+    set_error("rbws_get_basis: no basis");
+    return RBWS_ERR_NO_BASIS;
+  }
+  cudaSetDevice(p->device);
+  CK(cudaStreamSynchronize(p->stream));
+  if (W) CK(cudaMemcpy(W, p->d_W, sizeof(double) * (size_t)p->N * p->n, cudaMemcpyDeviceToHost));
+  if (ANq) std::memcpy(ANq, p->h_ANq.data(), sizeof(double) * p->h_ANq.size());
+  if (fN) std::memcpy(fN, p->h_fN.data(), sizeof(double) * p->h_fN.size());
+  return RBWS_OK;
+}
+
+rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, double* c_out) {
+  if (!p || !mu || !c_out || B < 1) {
+    set_error("rbws_reduced_solve: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->N <= 0) {
+    set_error("rbws_reduced_solve: no basis");
+    return RBWS_ERR_NO_BASIS;
+  }
+  StreamGuard sg(p, nullptr);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_rs"));
+  int err = 0;
+  double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
+  int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, p->stream);
+  CK(cudaGetLastError());
+  std::vector<int> h(B);
+  CK(cudaMemcpyAsync(c_out, C, sizeof(double) * (size_t)B * p->N, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  for (int b = 0; b < B; b++)
+    if (h[b]) {
+      set_error("rbws_reduced_solve: A_N(mu) not positive definite");
+      return RBWS_ERR_NOT_SPD;
+    }
+  return RBWS_OK;
+}
+
+rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
+                                int32_t n_max, double greedy_tol, double snapshot_tol,
+                                int32_t* selected_out, double* eta_hist_out, int32_t* n_out) {
+  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 256 || !(snapshot_tol > 0.0)) {
+    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 256, snapshot_tol > 0)");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  cudaStream_t s = p->stream;
+  const int64_t n = p->n;
+  const int Q = p->Q;
+  int err = 0;
+  // Drop any previous basis; the new one is built in place.
+  cudaStreamSynchronize(s);
+  cudaFree(p->d_W);
+  cudaFree(p->d_ANq);
+  cudaFree(p->d_fN);
+  p->d_W = p->d_ANq = p->d_fN = nullptr;
+  p->N = 0;
+  CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)n_max * n));
+  CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)Q * n_max * n_max));
+  CK(cudaMalloc(&p->d_fN, sizeof(double) * (size_t)n_max));
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu_train, n_train, &d_mu, "mu_train"));
+  double* usnap = (double*)p->buf("g_usnap", sizeof(double) * n, &err);
+  double* w = err ? nullptr : (double*)p->buf("g_w", sizeof(double) * n, &err);
+  double* V = err ? nullptr : (double*)p->buf("g_V", sizeof(double) * (size_t)Q * n, &err);
+  double* dots = err ? nullptr : (double*)p->buf("g_dots", sizeof(double) * (size_t)(Q + 2) * (n_max + 1), &err);
+  const int scratch_len = 256 * (n_max + 2);
+  double* scratch = err ? nullptr : (double*)p->buf("g_scratch", sizeof(double) * scratch_len, &err);
+  double* eye = err ? nullptr : (double*)p->buf("g_eye", sizeof(double) * (size_t)Q * Q, &err);
+  if (err) return (rbws_status)err;
+  {
+    std::vector<double> I((size_t)Q * Q, 0.0);
+    for (int q = 0; q < Q; q++) I[(size_t)q * Q + q] = 1.0;
+    CK(cudaMemcpyAsync(eye, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  const double* fvec = p->d_f ? p->d_f : p->d_ones;
+  std::vector<double> ANq((size_t)Q * n_max * n_max, 0.0), fN(n_max, 0.0);
+  std::vector<char> taken(n_train, 0);
+  std::vector<double> eta(n_train);
+  std::vector<double> hist(n_max, NAN);
+  std::vector<int32_t> sel(n_max, -1);
+  rbws_options o;
+  rbws_options_default(&o);
+  o.max_iters = 1000000;
+  o.precond = RBWS_PREC_JACOBI;
+  int N = 0, next = 0;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_train, ((int64_t)1 << 28) / n));
+  while (N < n_max) {
+    // snapshot u(mu_next) by Jacobi-PCG from zero
+    std::vector<InstState> st;
+    CK(cudaMemsetAsync(usnap, 0, sizeof(double) * n, s));
+    CKI(solve_fp64(p, d_mu + (int64_t)next * Q, 1, snapshot_tol, o, usnap, st));
+    if (st[0].status != ST_CONVERGED) {
+      set_error("rbws_offline_greedy: snapshot solve did not converge");
+      return RBWS_ERR_STATE;
+    }
+    // w = (I - W W^T)^2 u
+    CK(cudaMemcpyAsync(w, usnap, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    for (int pass = 0; pass < 2 && N > 0; pass++) {
+      launch_multi_dot(n, N, p->d_W, n, w, dots, scratch, scratch_len, s);
+      launch_sub_combination(n, N, p->d_W, dots, w, s);
+    }
+    launch_multi_dot(n, 1, w, n, w, dots, scratch, scratch_len, s);
+    launch_multi_dot(n, 1, usnap, n, usnap, dots + 1, scratch, scratch_len, s);
+    double nn[2];
+    CK(cudaMemcpyAsync(nn, dots, sizeof(nn), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double wn = std::sqrt(nn[0]), un = std::sqrt(nn[1]);
+    if (!(wn >= 1e-10 * un)) break;  // no new direction
+    double* wN = p->d_W + (int64_t)N * n;
+    CK(cudaMemcpyAsync(wN, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(dots, &wn, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_inv(n, dots, wN, s);
+    // V[q] = A_q w_N, then the new row/column of A_N^q and the new entry of f_N
+    double* c64 = nullptr;
+    CKI(coef_tables(p, eye, Q, &c64, nullptr));
+    launch_apply<double>(p->geo, choose_tile(p->nx), c64, Q, wN, 0, V, s);
+    for (int q = 0; q < Q; q++)
+      launch_multi_dot(n, N + 1, p->d_W, n, V + (int64_t)q * n, dots + (int64_t)q * (N + 1), scratch,
+                       scratch_len, s);
+    launch_multi_dot(n, 1, wN, n, fvec, dots + (int64_t)Q * (N + 1), scratch, scratch_len, s);
+    CK(cudaGetLastError());
+    std::vector<double> hd((size_t)Q * (N + 1) + 1);
+    CK(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < Q; q++)
+      for (int j = 0; j <= N; j++) {
+        const double a = hd[(size_t)q * (N + 1) + j];  // w_j^T A_q w_N
+        ANq[((size_t)q * n_max + j) * n_max + N] = a;
+        ANq[((size_t)q * n_max + N) * n_max + j] = a;
+      }
+    fN[N] = hd[(size_t)Q * (N + 1)];
+    sel[N] = next;
+    taken[next] = 1;
+    N++;
+    // publish the packed reduced operators for the reduced solves
+    p->h_ANq.assign((size_t)Q * N * N, 0.0);
+    for (int q = 0; q < Q; q++)
+      for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+          p->h_ANq[((size_t)q * N + i) * N + j] = ANq[((size_t)q * n_max + i) * n_max + j];
+    p->h_fN.assign(fN.begin(), fN.begin() + N);
+    CK(cudaMemcpyAsync(p->d_ANq, p->h_ANq.data(), sizeof(double) * p->h_ANq.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->d_fN, p->h_fN.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    p->N = N;
+    // residual indicator over the training set
+    for (int64_t b0 = 0; b0 < n_train; b0 += chunk) {
+      const int Bc = (int)std::min<int64_t>(chunk, n_train - b0);
+      double* U = (double*)p->buf("g_U", sizeof(double) * (size_t)Bc * n, &err);
+      double* etad = err ? nullptr : (double*)p->buf("g_eta", sizeof(double) * (size_t)Bc, &err);
+      if (err) return (rbws_status)err;
+      CKI(galerkin_start(p, d_mu + b0 * Q, Bc, U));
+      double* cc = nullptr;
+      CKI(coef_tables(p, d_mu + b0 * Q, Bc, &cc, nullptr));
+      CKI(residual_norms(p, cc, Bc, U, nullptr, etad));
+      CK(cudaMemcpyAsync(eta.data() + b0, etad, sizeof(double) * Bc, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    double best = -1.0;
+    next = -1;
+    for (int t = 0; t < n_train; t++)
+      if (!taken[t] && eta[t] > best) {
+        best = eta[t];
+        next = t;
+      }
+    hist[N - 1] = next >= 0 ? best : NAN;
+    if (next < 0 || best < greedy_tol) break;
+  }
+  if (N == 0) {
+    set_error("rbws_offline_greedy: no basis vector was added");
+    return RBWS_ERR_STATE;
+  }
+  if (selected_out) std::copy(sel.begin(), sel.begin() + n_max, selected_out);
+  if (eta_hist_out) std::copy(hist.begin(), hist.end(), eta_hist_out);
+  if (n_out) *n_out = N;
+  // compact A_N^q to [Q][N][N] on the device (already done above)
+  return RBWS_OK;
+}
+
+rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double tol, int32_t warm,
+                             const rbws_options* opt, void* u_out, int32_t* iters_out,
+                             double* relres_out, int32_t* status_out) {
+  rbws_options o;
+  rbws_options_default(&o);
+  if (opt) o = *opt;
+  if (!p || !mu || !u_out || !iters_out || B < 1 || B > 65535 || !(tol > 0.0) ||
+      o.max_iters < 0 || o.max_restarts < 0) {
+    set_error("rbws_solve_batch: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI) {
+    set_error("rbws_solve_batch: this preconditioner is not available yet");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  if (warm != RBWS_WARM_ZERO && warm != RBWS_WARM_GALERKIN) {
+    set_error("rbws_solve_batch: this warm-start mode is not available yet");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  if (o.precision != RBWS_FP64 && o.precision != RBWS_FP32_IR) {
+    set_error("rbws_solve_batch: unknown precision");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, o.stream);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_solve"));
+  double* u = (double*)u_out;
+  if (warm == RBWS_WARM_ZERO) {
+    CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->stream));
+  } else {
+    CKI(galerkin_start(p, d_mu, B, u));
+  }
+  std::vector<InstState> st;
+  if (o.precision == RBWS_FP64) {
+    CKI(solve_fp64(p, d_mu, B, tol, o, u, st));
+  } else {
+    CKI(solve_fp32_ir(p, d_mu, B, tol, o, u, st));
+  }
+  int warn = 0;
+  for (int b = 0; b < B; b++) {
+    iters_out[b] = st[b].iters;
+    if (relres_out) relres_out[b] = st[b].relres;
+    const int s = st[b].status == ST_CONVERGED ? 0 : (st[b].status == ST_BREAKDOWN ? 2 : 1);
+    if (status_out) status_out[b] = s;
+    warn |= s != 0;
+  }
+  return warn ? RBWS_WARN_NOT_CONVERGED : RBWS_OK;
+}
+
+}  // extern "C"

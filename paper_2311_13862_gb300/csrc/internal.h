@@ -1,0 +1,155 @@
+// internal.h -- shared declarations of librbws (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rbws.h"
+
+namespace rbws {
+
+// ---------------------------------------------------------------------------
+// Geometry and coefficient classes.
+//
+// With block-constant kappa, the seven coefficients of a node's stencil row
+// depend only on which block the node and each of its neighbours lie in (or
+// whether a neighbour is on the boundary).  Along one axis a node's "class"
+// is the triple (own block, lower neighbour's block or -1, upper neighbour's
+// block or -1); a node's full class is (z class, y class, x class).  There
+// are at most 3b+2 classes per axis, so each instance's coefficients fit in a
+// small table [ncz][ncy][ncx] of 8 values:
+//   -kW, -kE, -kS, -kN, -kD, -kU  (negated face coefficients, 1/h^2 included),
+//   D = kW+kE+kS+kN+kD+kU,  Dinv = 1/D.
+// The stencil is then y = D x_c + sum_f (-k_f) x_f: 1 multiply + 6 FMAs.
+// ---------------------------------------------------------------------------
+constexpr int kCoefStride = 8;  // values per class entry
+constexpr int kMaxQ = 64;
+constexpr int kMaxAxis = 1024;
+constexpr int kMaxClassPerAxis = 3 * 16 + 2;
+
+struct AxisClasses {
+  int n = 0, b = 0;
+  std::vector<uint8_t> cls;   // [n] class id of each node
+  std::vector<int8_t> key;    // [ncls][3] (own, lo, hi) blocks, -1 = boundary
+  int ncls() const { return (int)key.size() / 3; }
+};
+
+// Device-side view of the grid shared by the kernels.
+struct Geo {
+  int nx, ny, nz;
+  int ncx, ncy, ncz;          // classes per axis
+  int64_t n;                  // nx*ny*nz
+  const uint8_t* cx;          // [nx] class ids (device)
+  const uint8_t* cy;          // [ny]
+  const uint8_t* cz;          // [nz]
+  __host__ __device__ int ncls() const { return ncx * ncy * ncz; }
+};
+
+// Per-instance solver state kept on the device.
+enum : int { ST_ACTIVE = -1, ST_CONVERGED = 0, ST_MAX_ITERS = 1, ST_BREAKDOWN = 2, ST_IDLE = 3 };
+
+struct InstState {
+  int status;    // ST_*
+  int iters;     // applications of A to a search direction
+  int restarts;  // true-residual restarts used
+  int pad;
+  double relres; // last relative residual (true residual after finalisation)
+  double relres0;
+};
+
+// Arguments of the CG phase kernels (one struct so launches stay short).
+template <typename T>
+struct CGArgs {
+  Geo g;
+  int B;                // instances in the launch
+  int tiles_x, tiles_y; // tiles per plane
+  int zc;               // planes per z-chunk
+  int nzc;              // z-chunks
+  int P;                // CTAs (partials) per instance = tiles_x*tiles_y*nzc
+  const T* coef;        // [B][ncls][8]
+  const T* f;           // right-hand side [n] (shared) or nullptr -> 1 (init kernel only)
+  const double* rhs64;  // FP32_IR init: FP64 residual [B][n] to be scaled, else nullptr
+  const double* rhs_scale; // FP32_IR init: per-instance norm of rhs64 (the inner rhs is rhs64/norm)
+  T* u;                 // [B][n]
+  T* r;
+  T* s;
+  T* p0;                // ping-pong search directions
+  T* p1;
+  T* q;                 // A p
+  double2* rho_rr;      // [2][B][P] partials (rho = r.s, rr = r.r)
+  double* gam;          // [B][P] partials of p.Ap
+  InstState* st;        // [B]
+  const double* fnorm;  // [B] norm of the right-hand side of each instance
+  double tol;
+  int max_iters;
+  int* active;          // number of active instances
+  int precond;          // RBWS_PREC_NONE / JACOBI
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (stencil.cu)
+// ---------------------------------------------------------------------------
+struct Tile {
+  int tx, ty;  // threads per CTA in x and y (one node per thread per plane)
+};
+
+// Builds per-instance coefficient tables: coef64 [B][ncls][8] (and coef32 if
+// non-null) from mu [B][Q] on the device.
+void launch_coef_tables(const Geo& g, const int8_t* keys_x, const int8_t* keys_y,
+                        const int8_t* keys_z, int bx, int by, double sx, double sy, double sz,
+                        int Q, const double* mu, int B, double* coef64, float* coef32,
+                        cudaStream_t s);
+
+// y[b] = A(mu_b) x[b]; x_stride = 0 broadcasts one x to every instance.
+template <typename T>
+void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_t x_stride, T* y,
+                  cudaStream_t s);
+
+// r = f - A u (FP64) per instance; rr partials [B][P] and the residual
+// written to r (if non-null); also used for the outer residual of FP32_IR.
+void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
+                       const double* u, double* r, double* rr_part, int P, cudaStream_t s);
+
+template <typename T>
+void launch_cg_init(const CGArgs<T>& a, Tile t, int parity, int only_status, cudaStream_t s);
+template <typename T>
+void launch_cg_a(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s);
+template <typename T>
+void launch_cg_b(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s);
+// Per-instance finalisation after an init pass: mode 0 = start (record
+// relres0, set ACTIVE/CONVERGED, count active); mode 1 = true-residual check
+// (record relres, restart CONVERGED instances that fail tol).
+template <typename T>
+void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restarts,
+                        cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Reduced basis kernels (rb.cu)
+// ---------------------------------------------------------------------------
+// c[b] = (sum_q mu[b][q] ANq[q])^{-1} fN; info[b] = 0 or -1 (not SPD).
+void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu,
+                          int B, double* c, int* info, cudaStream_t s);
+// u[b] = sum_j c[b][j] W[j]  (W: [N][n]).
+void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,
+                 cudaStream_t s);
+// out[k] = X[k] . y for k < K (X rows of length n, row stride ldx), two-stage deterministic.
+void launch_multi_dot(int64_t n, int K, const double* X, int64_t ldx, const double* y,
+                      double* out, double* scratch, int scratch_len, cudaStream_t s);
+// w -= sum_j coef[j] W[j]   (coef device [K])
+void launch_sub_combination(int64_t n, int K, const double* W, const double* coef, double* w,
+                            cudaStream_t s);
+// w *= 1/alpha (alpha device scalar)
+void launch_scale_inv(int64_t n, const double* alpha, double* w, cudaStream_t s);
+// per-instance eta[b] = sqrt(sum partials)/fnorm
+void launch_norms_from_partials(const double* part, int B, int P, double fnorm, double* out,
+                                cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);  // sets message, returns RBWS_ERR_CUDA
+
+}  // namespace rbws

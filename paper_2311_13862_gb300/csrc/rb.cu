@@ -1,0 +1,198 @@
+// rb.cu -- reduced basis kernels: batched reduced Galerkin solve (Sec. 2.3),
+// lift u0 = W c (Algorithm 4, line 2), and the dense helpers of the offline
+// greedy (projections W^T y, Gram-Schmidt updates).  All FP64.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rbws {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum_down(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+
+// One CTA per parameter: A = sum_q mu_q ANq[q] in shared memory, right-looking
+// Cholesky, then the two triangular solves for c = A^{-1} fN.
+__global__ void k_reduced_solve(int N, int Q, const double* __restrict__ ANq,
+                                const double* __restrict__ fN, const double* __restrict__ mu,
+                                double* __restrict__ c, int* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = reinterpret_cast<double*>(smem_raw);  // N*N
+  double* x = A + N * N;                             // N
+  __shared__ int bad;
+  const int b = blockIdx.x;
+  const double* m = mu + (int64_t)b * Q;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < Q; q++) s = fma(m[q], ANq[(int64_t)q * N * N + e], s);
+    A[e] = s;
+  }
+  for (int e = threadIdx.x; e < N; e += blockDim.x) x[e] = fN[e];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < N; j++) {
+    if (threadIdx.x == 0) {
+      const double d = A[j * N + j];
+      if (!(d > 0.0)) bad = 1;
+      A[j * N + j] = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    const double ljj = A[j * N + j];
+    for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) A[i * N + j] /= ljj;
+    __syncthreads();
+    const int m2 = N - j - 1;
+    for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) {
+      const int i = j + 1 + e / m2, k = j + 1 + e % m2;
+      if (k <= i) A[i * N + k] = fma(-A[i * N + j], A[k * N + j], A[i * N + k]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < N; i++) {  // L y = f
+      double s = x[i];
+      for (int k = 0; k < i; k++) s = fma(-A[i * N + k], x[k], s);
+      x[i] = s / A[i * N + i];
+    }
+    for (int i = N - 1; i >= 0; i--) {  // L^T c = y
+      double s = x[i];
+      for (int k = i + 1; k < N; k++) s = fma(-A[k * N + i], x[k], s);
+      x[i] = s / A[i * N + i];
+    }
+    info[b] = bad ? -1 : 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N; e += blockDim.x) c[(int64_t)b * N + e] = x[e];
+}
+
+// u[b][i] = sum_j c[b][j] W[j][i]; each thread one node for kLiftB instances.
+constexpr int kLiftB = 8;
+__global__ void k_lift(int64_t n, int N, const double* __restrict__ W, const double* __restrict__ c,
+                       int B, double* __restrict__ u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* cs = reinterpret_cast<double*>(smem_raw);  // [kLiftB][N]
+  const int b0 = blockIdx.y * kLiftB;
+  const int nb = min(kLiftB, B - b0);
+  for (int e = threadIdx.x; e < nb * N; e += blockDim.x) cs[e] = c[(int64_t)b0 * N + e];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc[kLiftB];
+#pragma unroll
+    for (int k = 0; k < kLiftB; k++) acc[k] = 0.0;
+    for (int j = 0; j < N; j++) {
+      const double w = W[(int64_t)j * n + i];
+#pragma unroll
+      for (int k = 0; k < kLiftB; k++) acc[k] = fma(cs[k * N + j], w, acc[k]);
+    }
+    for (int k = 0; k < nb; k++) u[(int64_t)(b0 + k) * n + i] = acc[k];
+  }
+}
+
+// Stage 1 of out[k] = X[k].y: partial sums over fixed chunks.
+__global__ void k_dot_stage1(int64_t n, const double* __restrict__ X, int64_t ldx,
+                             const double* __restrict__ y, double* __restrict__ part, int chunks) {
+  __shared__ double red[32];
+  const int k = blockIdx.y;
+  const double* xk = X + (int64_t)k * ldx;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)chunks * blockDim.x)
+    s = fma(xk[i], y[i], s);
+  s = warp_sum_down(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    v = warp_sum_down(v);
+    if (lane == 0) part[(int64_t)k * chunks + blockIdx.x] = v;
+  }
+}
+
+__global__ void k_dot_stage2(const double* __restrict__ part, int chunks, int K,
+                             double* __restrict__ out) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int c = lane; c < chunks; c += 32) s += part[(int64_t)k * chunks + c];
+  s = warp_sum_down(s);
+  if (lane == 0) out[k] = s;
+}
+
+__global__ void k_sub_combination(int64_t n, int K, const double* __restrict__ W,
+                                  const double* __restrict__ coef, double* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = w[i];
+    for (int j = 0; j < K; j++) v = fma(-coef[j], W[(int64_t)j * n + i], v);
+    w[i] = v;
+  }
+}
+
+__global__ void k_scale_inv(int64_t n, const double* __restrict__ alpha, double* __restrict__ w) {
+  const double s = 1.0 / alpha[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] *= s;
+}
+
+__global__ void k_norms_from_partials(const double* __restrict__ part, int B, int P, double fnorm,
+                                      double* __restrict__ out) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int c = lane; c < P; c += 32) s += part[(int64_t)b * P + c];
+  s = warp_sum_down(s);
+  if (lane == 0) out[b] = sqrt(s) / fnorm;
+}
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+}  // namespace
+
+void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu, int B,
+                          double* c, int* info, cudaStream_t s) {
+  const size_t smem = sizeof(double) * ((size_t)N * N + N);
+  k_reduced_solve<<<B, 128, smem, s>>>(N, Q, ANq, fN, mu, c, info);
+}
+
+void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,
+                 cudaStream_t s) {
+  const int threads = 256;
+  dim3 grid(grid_for(n, threads, 152 * 4), (B + kLiftB - 1) / kLiftB);
+  k_lift<<<grid, threads, sizeof(double) * kLiftB * N, s>>>(n, N, W, c, B, u);
+}
+
+void launch_multi_dot(int64_t n, int K, const double* X, int64_t ldx, const double* y, double* out,
+                      double* scratch, int scratch_len, cudaStream_t s) {
+  int chunks = 256;
+  while ((int64_t)chunks * K > scratch_len && chunks > 1) chunks /= 2;
+  k_dot_stage1<<<dim3(chunks, K), 256, 0, s>>>(n, X, ldx, y, scratch, chunks);
+  k_dot_stage2<<<(K + 3) / 4, 128, 0, s>>>(scratch, chunks, K, out);
+}
+
+void launch_sub_combination(int64_t n, int K, const double* W, const double* coef, double* w,
+                            cudaStream_t s) {
+  k_sub_combination<<<grid_for(n, 256), 256, 0, s>>>(n, K, W, coef, w);
+}
+
+void launch_scale_inv(int64_t n, const double* alpha, double* w, cudaStream_t s) {
+  k_scale_inv<<<grid_for(n, 256), 256, 0, s>>>(n, alpha, w);
+}
+
+void launch_norms_from_partials(const double* part, int B, int P, double fnorm, double* out,
+                                cudaStream_t s) {
+  k_norms_from_partials<<<(B + 3) / 4, 128, 0, s>>>(part, B, P, fnorm, out);
+}
+
+}  // namespace rbws

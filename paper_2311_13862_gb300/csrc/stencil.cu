@@ -1,0 +1,596 @@
+// stencil.cu -- matrix-free affine 7-point operator and the fused Jacobi-PCG
+// phase kernels (Algorithm 1) for sm_103a.
+//
+// Layout: planar [B][nz][ny][nx], x fastest.  Every stencil kernel marches a
+// CTA tile of TX x TY columns through a chunk of z planes.  Plane z (with a
+// one-node halo in x and y) is staged in a 3-slot shared-memory ring; the
+// z-1 / z+1 values of a thread's own column stay in registers, so each plane
+// is read from memory once per tile.  One __syncthreads per plane.
+//
+// Coefficients come from a per-instance class table (see internal.h): a
+// thread caches its column's 8-value row and reloads it only when the z class
+// changes, so the FP64 stencil costs 1 DMUL + 6 DFMA per node.  GB300 runs
+// FP64 at ~1/60 of its FP32 rate, so the FP64 kernels are written to minimise
+// FP64 instructions, not bytes.
+//
+// Reductions are deterministic: each CTA reduces its threads in a fixed tree
+// and writes one partial; consumers sum an instance's partials in index order
+// with a fixed shuffle tree, so every CTA of an instance (and every rerun)
+// sees bit-identical scalars.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rbws {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum_down(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;  // valid in lane 0
+}
+
+// Deterministic block sum of two values; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  a = warp_sum_down(a);
+  b = warp_sum_down(b);
+  __syncthreads();  // red may still be in use by an earlier reduction
+  if (lane == 0) {
+    red[warp] = a;
+    red[32 + warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double x = lane < nw ? red[lane] : 0.0;
+    double y = lane < nw ? red[32 + lane] : 0.0;
+    a = warp_sum_down(x);
+    b = warp_sum_down(y);
+  }
+}
+
+// Sum of an instance's partials in a fixed order (called by a full warp);
+// result valid in lane 0.
+__device__ __forceinline__ double sum_partials(const double* part, int P, int lane) {
+  double s = 0.0;
+  for (int c = lane; c < P; c += 32) s += part[c];
+  return warp_sum_down(s);
+}
+__device__ __forceinline__ double2 sum_partials2(const double2* part, int P, int lane) {
+  double x = 0.0, y = 0.0;
+  for (int c = lane; c < P; c += 32) {
+    double2 v = part[c];
+    x += v.x;
+    y += v.y;
+  }
+  return make_double2(warp_sum_down(x), warp_sum_down(y));
+}
+
+// Column geometry of the calling thread inside its CTA tile.
+struct Column {
+  int i, j;
+  bool own;
+  int64_t col;  // j*nx + i
+  int xy;       // class index (cy*ncx + cx) of the column
+};
+
+__device__ __forceinline__ Column make_column(const Geo& g, int x0, int y0) {
+  Column c;
+  c.i = x0 + (int)threadIdx.x;
+  c.j = y0 + (int)threadIdx.y;
+  c.own = c.i < g.nx && c.j < g.ny;
+  c.col = (int64_t)c.j * g.nx + c.i;
+  c.xy = c.own ? (int)g.cy[c.j] * g.ncx + (int)g.cx[c.i] : 0;
+  return c;
+}
+
+// The z-marching stencil skeleton.  load(idx) returns the staged field at an
+// in-domain node (idx = z*nx*ny + j*nx + i); consume(idx, x_c, y, dinv) gets
+// y = (A x)(node) for each owned node of planes [z0, z1).
+template <typename T, class Load, class Consume>
+__device__ __forceinline__ void zmarch(const Geo& g, const T* __restrict__ coef_b, int x0, int y0,
+                                       int z0, int z1, T* sm, Load load, Consume consume) {
+  const int TX = blockDim.x, TY = blockDim.y;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const Column cl = make_column(g, x0, y0);
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int PW = TX + 2, PS = PW * (TY + 2);
+  const int nh = 2 * TX + 2 * TY;
+  int hi, hj;
+  if (tid < TX) {
+    hi = tid; hj = -1;
+  } else if (tid < 2 * TX) {
+    hi = tid - TX; hj = TY;
+  } else if (tid < 2 * TX + TY) {
+    hi = -1; hj = tid - 2 * TX;
+  } else {
+    hi = TX; hj = tid - 2 * TX - TY;
+  }
+  const int gi = x0 + hi, gj = y0 + hj;
+  const bool has_halo = tid < nh;
+  const bool hin = has_halo && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+  const int64_t hcol = (int64_t)gj * g.nx + gi;
+  const int hslot = (hj + 1) * PW + hi + 1;
+  const int oslot = ((int)threadIdx.y + 1) * PW + (int)threadIdx.x + 1;
+
+  auto stage = [&](int z, T* Pl) -> T {
+    T v = T(0);
+    const bool zin = z >= 0 && z < g.nz;
+    if (zin && cl.own) v = load((int64_t)z * plane + cl.col);
+    Pl[oslot] = v;
+    if (has_halo) {
+      T hv = T(0);
+      if (zin && hin) hv = load((int64_t)z * plane + hcol);
+      Pl[hslot] = hv;
+    }
+    return v;
+  };
+
+  int zcls_cur = -1;
+  T c[kCoefStride];
+#pragma unroll
+  for (int k = 0; k < kCoefStride; k++) c[k] = T(0);
+  T xm = (z0 > 0 && cl.own) ? load((int64_t)(z0 - 1) * plane + cl.col) : T(0);
+  T xc = stage(z0, sm + (z0 % 3) * PS);
+  for (int z = z0; z < z1; ++z) {
+    T xp = stage(z + 1, sm + ((z + 1) % 3) * PS);
+    __syncthreads();
+    const T* Pl = sm + (z % 3) * PS;
+    const int zcl = g.cz[z];
+    if (zcl != zcls_cur) {
+      zcls_cur = zcl;
+      const T* row = coef_b + ((int64_t)zcl * g.ncy * g.ncx + cl.xy) * kCoefStride;
+#pragma unroll
+      for (int k = 0; k < kCoefStride; k++) c[k] = row[k];
+    }
+    if (cl.own) {
+      T y = c[6] * xc;
+      y = fma(c[0], Pl[oslot - 1], y);
+      y = fma(c[1], Pl[oslot + 1], y);
+      y = fma(c[2], Pl[oslot - PW], y);
+      y = fma(c[3], Pl[oslot + PW], y);
+      y = fma(c[4], xm, y);
+      y = fma(c[5], xp, y);
+      consume((int64_t)z * plane + cl.col, xc, y, c[7]);
+    }
+    xm = xc;
+    xc = xp;
+  }
+}
+
+struct TilePos {
+  int x0, y0, z0, z1, part;
+};
+
+__device__ __forceinline__ TilePos tile_pos(const Geo& g, int tiles_x, int zc) {
+  TilePos t;
+  const int tile = blockIdx.x;
+  t.x0 = (tile % tiles_x) * blockDim.x;
+  t.y0 = (tile / tiles_x) * blockDim.y;
+  t.z0 = blockIdx.y * zc;
+  t.z1 = min(g.nz, t.z0 + zc);
+  t.part = blockIdx.y * gridDim.x + blockIdx.x;
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Coefficient tables
+// ---------------------------------------------------------------------------
+__global__ void k_coef_tables(Geo g, const int8_t* __restrict__ kx, const int8_t* __restrict__ ky,
+                              const int8_t* __restrict__ kz, int bx, int by, double sx, double sy,
+                              double sz, int Q, const double* __restrict__ mu, int B,
+                              double* __restrict__ coef64, float* __restrict__ coef32) {
+  const int ncls = g.ncls();
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ncls * B) return;
+  const int b = (int)(t / ncls), e = (int)(t % ncls);
+  const int cxi = e % g.ncx, cyi = (e / g.ncx) % g.ncy, czi = e / (g.ncx * g.ncy);
+  const int ox = kx[3 * cxi], lx = kx[3 * cxi + 1], hx = kx[3 * cxi + 2];
+  const int oy = ky[3 * cyi], ly = ky[3 * cyi + 1], hy = ky[3 * cyi + 2];
+  const int oz = kz[3 * czi], lz = kz[3 * czi + 1], hz = kz[3 * czi + 2];
+  const double* m = mu + (int64_t)b * Q;
+  auto kap = [&](int ax, int ay, int az) { return m[(az * by + ay) * bx + ax]; };
+  const double kc = kap(ox, oy, oz);
+  // face coefficient: arithmetic mean of the two kappas; boundary face: own kappa
+  auto face = [&](int nb_ok, double knb, double s) { return nb_ok ? 0.5 * (kc + knb) * s : kc * s; };
+  const double kW = face(lx >= 0, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx);
+  const double kE = face(hx >= 0, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx);
+  const double kS = face(ly >= 0, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy);
+  const double kN = face(hy >= 0, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy);
+  const double kD = face(lz >= 0, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz);
+  const double kU = face(hz >= 0, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz);
+  const double D = kW + kE + kS + kN + kD + kU;
+  const double v[kCoefStride] = {-kW, -kE, -kS, -kN, -kD, -kU, D, 1.0 / D};
+  double* o64 = coef64 + ((int64_t)b * ncls + e) * kCoefStride;
+  for (int k = 0; k < kCoefStride; k++) o64[k] = v[k];
+  if (coef32) {
+    float* o32 = coef32 + ((int64_t)b * ncls + e) * kCoefStride;
+    for (int k = 0; k < kCoefStride; k++) o32[k] = (float)v[k];
+    o32[7] = 1.0f / (float)D;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y = A(mu) x
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_apply(Geo g, int tiles_x, int zc, const T* __restrict__ coef, const T* __restrict__ x,
+                        int64_t x_stride, T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.z;
+  const TilePos tp = tile_pos(g, tiles_x, zc);
+  const T* xb = x + (int64_t)b * x_stride;
+  T* yb = y + (int64_t)b * g.n;
+  const T* cb = coef + (int64_t)b * g.ncls() * kCoefStride;
+  zmarch<T>(
+      g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return xb[idx]; },
+      [&](int64_t idx, T, T v, T) { yb[idx] = v; });
+}
+
+// r = f - A u in FP64 with partial sums of r.r per CTA.
+__global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restrict__ coef,
+                             const double* __restrict__ f, const double* __restrict__ u,
+                             double* __restrict__ r, double* __restrict__ rr_part, int P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  const int b = blockIdx.z;
+  const TilePos tp = tile_pos(g, tiles_x, zc);
+  const double* ub = u + (int64_t)b * g.n;
+  double* rb = r ? r + (int64_t)b * g.n : nullptr;
+  const double* cb = coef + (int64_t)b * g.ncls() * kCoefStride;
+  double acc = 0.0;
+  zmarch<double>(
+      g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return ub[idx]; },
+      [&](int64_t idx, double, double v, double) {
+        const double rv = (f ? f[idx] : 1.0) - v;
+        if (rb) rb[idx] = rv;
+        acc = fma(rv, rv, acc);
+      });
+  double dummy = 0.0;
+  block_sum2(acc, dummy, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) rr_part[(int64_t)b * P + tp.part] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// PCG phase kernels.  Per iteration k (parity = k % 2):
+//   A: beta = rho_k / rho_{k-1};  p_new = s + beta p_old (staged, halo too);
+//      q = A p_new;  gamma partials = p_new . q.       Stops converged ones.
+//   B: alpha = rho_k / gamma;  u += alpha p;  r -= alpha q;  s = D^{-1} r;
+//      partials of rho_{k+1} = r.s and r.r.
+// Search directions ping-pong: A(parity) reads pbuf[parity], writes
+// pbuf[parity^1]; rho/rr partials ping-pong the same way.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_cg_init(CGArgs<T> a, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.z;
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const int64_t off = (int64_t)b * a.g.n;
+  const T* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
+  T* pold = (parity ? a.p1 : a.p0) + off;
+  T* ub = a.u + off;
+  T* rb = a.r + off;
+  T* sb = a.s + off;
+  const bool jac = a.precond == RBWS_PREC_JACOBI;
+  T rho = T(0), rr = T(0);
+  if (a.rhs64 == nullptr) {
+    zmarch<T>(
+        a.g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return ub[idx]; },
+        [&](int64_t idx, T, T v, T dinv) {
+          const T rv = (a.f ? a.f[idx] : T(1)) - v;
+          const T sv = jac ? dinv * rv : rv;
+          rb[idx] = rv;
+          if (jac) sb[idx] = sv;
+          pold[idx] = T(0);
+          rho = fma(rv, sv, rho);
+          rr = fma(rv, rv, rr);
+        });
+  } else {
+    // FP32_IR inner system: right-hand side = FP64 outer residual / ||residual||
+    const Column cl = make_column(a.g, tp.x0, tp.y0);
+    const double scale = 1.0 / a.rhs_scale[b];
+    const double* hb = a.rhs64 + off;
+    const int64_t plane = (int64_t)a.g.nx * a.g.ny;
+    if (cl.own) {
+      int zcls_cur = -1;
+      T dinv = T(1);
+      for (int z = tp.z0; z < tp.z1; ++z) {
+        const int zcl = a.g.cz[z];
+        if (zcl != zcls_cur) {
+          zcls_cur = zcl;
+          dinv = cb[((int64_t)zcl * a.g.ncy * a.g.ncx + cl.xy) * kCoefStride + 7];
+        }
+        const int64_t idx = (int64_t)z * plane + cl.col;
+        const T rv = (T)(hb[idx] * scale);
+        const T sv = jac ? dinv * rv : rv;
+        ub[idx] = T(0);
+        rb[idx] = rv;
+        if (jac) sb[idx] = sv;
+        pold[idx] = T(0);
+        rho = fma(rv, sv, rho);
+        rr = fma(rv, rv, rr);
+      }
+    }
+  }
+  double drho = (double)rho, drr = (double)rr;
+  block_sum2(drho, drr, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    a.rho_rr[((int64_t)parity * a.B + b) * a.P + tp.part] = make_double2(drho, drr);
+    // rho_{k-1} := 1 (p_old = 0, so beta only has to be finite)
+    a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + tp.part] =
+        make_double2(tp.part == 0 ? 1.0 : 0.0, 0.0);
+  }
+}
+
+template <typename T>
+__global__ void k_cg_finalize(CGArgs<T> a, int parity, int mode, int max_restarts) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= a.B) return;
+  const double2 v = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, lane);
+  if (lane != 0) return;
+  InstState& s = a.st[b];
+  const double rel = sqrt(v.y) / a.fnorm[b];
+  if (mode == 0) {
+    s.relres0 = rel;
+    s.relres = rel;
+    s.iters = 0;
+    s.restarts = 0;
+    if (rel < a.tol) {
+      s.status = ST_CONVERGED;
+    } else if (!(rel == rel) || a.max_iters <= 0) {
+      s.status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
+    } else {
+      s.status = ST_ACTIVE;
+      atomicAdd(a.active, 1);
+    }
+  } else {
+    s.relres = rel;
+    if (s.status == ST_CONVERGED && !(rel < a.tol)) {
+      if (s.restarts < max_restarts && s.iters < a.max_iters && rel == rel) {
+        s.restarts += 1;
+        s.status = ST_ACTIVE;
+        atomicAdd(a.active, 1);
+      } else {
+        s.status = ST_MAX_ITERS;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_cg_a(CGArgs<T> a, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  __shared__ double s_beta;
+  __shared__ int s_run;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const bool leader = tp.part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double2 cur = make_double2(0.0, 0.0);
+    double prev = 0.0;
+    if (status == ST_ACTIVE) {
+      cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      const double2 pv = sum_partials2(a.rho_rr + ((int64_t)(parity ^ 1) * a.B + b) * a.P, a.P, tid);
+      prev = pv.x;
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double rel = sqrt(cur.y) / a.fnorm[b];
+        if (rel < a.tol) {
+          if (leader) {
+            st->status = ST_CONVERGED;
+            st->relres = rel;
+            atomicSub(a.active, 1);
+          }
+        } else if (st->iters >= a.max_iters || !(rel == rel)) {
+          if (leader) {
+            st->status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
+            st->relres = rel;
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_beta = cur.x / prev;
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const T beta = (T)s_beta;
+  const int64_t off = (int64_t)b * a.g.n;
+  const T* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
+  const T* sb = (a.precond == RBWS_PREC_JACOBI ? a.s : a.r) + off;
+  const T* pold = (parity ? a.p1 : a.p0) + off;
+  T* pnew = (parity ? a.p0 : a.p1) + off;
+  T* qb = a.q + off;
+  T gam = T(0);
+  zmarch<T>(
+      a.g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm,
+      [&](int64_t idx) { return fma(beta, pold[idx], sb[idx]); },
+      [&](int64_t idx, T pc, T v, T) {
+        pnew[idx] = pc;
+        qb[idx] = v;
+        gam = fma(pc, v, gam);
+      });
+  double dg = (double)gam, dummy = 0.0;
+  block_sum2(dg, dummy, red);
+  if (tid == 0) a.gam[(int64_t)b * a.P + tp.part] = dg;
+}
+
+template <typename T>
+__global__ void k_cg_b(CGArgs<T> a, int parity) {
+  __shared__ double red[64];
+  __shared__ double s_alpha;
+  __shared__ int s_run;
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const bool leader = tp.part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double rho = 0.0, gam = 0.0, rr = 0.0;
+    if (status == ST_ACTIVE) {
+      const double2 cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      rho = cur.x;
+      rr = cur.y;
+      gam = sum_partials(a.gam + (int64_t)b * a.P, a.P, tid);
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double alpha = rho / gam;
+        if (!(gam > 0.0) || !(alpha == alpha) || alpha == INFINITY) {
+          if (leader) {
+            st->status = ST_BREAKDOWN;
+            st->relres = sqrt(rr) / a.fnorm[b];
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_alpha = alpha;
+          if (leader) st->iters += 1;
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const T alpha = (T)s_alpha;
+  const int64_t off = (int64_t)b * a.g.n;
+  const T* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
+  const T* pn = (parity ? a.p0 : a.p1) + off;
+  const T* qb = a.q + off;
+  T* ub = a.u + off;
+  T* rb = a.r + off;
+  T* sb = a.s + off;
+  const bool jac = a.precond == RBWS_PREC_JACOBI;
+  const Column cl = make_column(a.g, tp.x0, tp.y0);
+  const int64_t plane = (int64_t)a.g.nx * a.g.ny;
+  T rho = T(0), rr = T(0);
+  if (cl.own) {
+    int zcls_cur = -1;
+    T dinv = T(1);
+    for (int z = tp.z0; z < tp.z1; ++z) {
+      const int zcl = a.g.cz[z];
+      if (zcl != zcls_cur) {
+        zcls_cur = zcl;
+        dinv = cb[((int64_t)zcl * a.g.ncy * a.g.ncx + cl.xy) * kCoefStride + 7];
+      }
+      const int64_t idx = (int64_t)z * plane + cl.col;
+      const T pv = pn[idx];
+      const T qv = qb[idx];
+      ub[idx] = fma(alpha, pv, ub[idx]);
+      const T rv = fma(-alpha, qv, rb[idx]);
+      rb[idx] = rv;
+      T sv = rv;
+      if (jac) {
+        sv = dinv * rv;
+        sb[idx] = sv;
+      }
+      rho = fma(rv, sv, rho);
+      rr = fma(rv, rv, rr);
+    }
+  }
+  double drho = (double)rho, drr = (double)rr;
+  block_sum2(drho, drr, red);
+  if (tid == 0)
+    a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + tp.part] = make_double2(drho, drr);
+}
+
+inline size_t plane_smem(Tile t, size_t elem) { return 3 * (size_t)(t.tx + 2) * (t.ty + 2) * elem; }
+
+template <typename T>
+dim3 cg_grid(const CGArgs<T>& a) {
+  return dim3(a.tiles_x * a.tiles_y, a.nzc, a.B);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void launch_coef_tables(const Geo& g, const int8_t* kx, const int8_t* ky, const int8_t* kz, int bx,
+                        int by, double sx, double sy, double sz, int Q, const double* mu, int B,
+                        double* coef64, float* coef32, cudaStream_t s) {
+  const int64_t total = (int64_t)g.ncls() * B;
+  const int threads = 128;
+  const int blocks = (int)((total + threads - 1) / threads);
+  k_coef_tables<<<blocks, threads, 0, s>>>(g, kx, ky, kz, bx, by, sx, sy, sz, Q, mu, B, coef64, coef32);
+}
+
+template <typename T>
+void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_t x_stride, T* y,
+                  cudaStream_t s) {
+  const int tiles_x = (g.nx + t.tx - 1) / t.tx, tiles_y = (g.ny + t.ty - 1) / t.ty;
+  // z-chunks: enough CTAs to fill the GPU a few times over
+  int nzc = 1;
+  const int64_t per_chunk = (int64_t)tiles_x * tiles_y * B;
+  while (per_chunk * nzc < 4 * 152 && nzc * 2 <= g.nz / 4) nzc *= 2;
+  const int zc = (g.nz + nzc - 1) / nzc;
+  nzc = (g.nz + zc - 1) / zc;
+  dim3 grid(tiles_x * tiles_y, nzc, B), block(t.tx, t.ty);
+  k_apply<T><<<grid, block, plane_smem(t, sizeof(T)), s>>>(g, tiles_x, zc, coef, x, x_stride, y);
+}
+
+void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
+                       const double* u, double* r, double* rr_part, int P, cudaStream_t s) {
+  const int tiles_x = (g.nx + t.tx - 1) / t.tx, tiles_y = (g.ny + t.ty - 1) / t.ty;
+  const int nzc = (g.nz + zc - 1) / zc;
+  (void)P;
+  dim3 grid(tiles_x * tiles_y, nzc, B), block(t.tx, t.ty);
+  k_residual64<<<grid, block, plane_smem(t, sizeof(double)), s>>>(g, tiles_x, zc, coef, f, u, r,
+                                                                  rr_part, tiles_x * tiles_y * nzc);
+}
+
+template <typename T>
+void launch_cg_init(const CGArgs<T>& a, Tile t, int parity, int only_status, cudaStream_t s) {
+  (void)only_status;
+  k_cg_init<T><<<cg_grid(a), dim3(t.tx, t.ty), plane_smem(t, sizeof(T)), s>>>(a, parity);
+}
+template <typename T>
+void launch_cg_a(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s) {
+  k_cg_a<T><<<cg_grid(a), dim3(t.tx, t.ty), plane_smem(t, sizeof(T)), s>>>(a, parity);
+}
+template <typename T>
+void launch_cg_b(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s) {
+  k_cg_b<T><<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, parity);
+}
+template <typename T>
+void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restarts, cudaStream_t s) {
+  const int warps = 4;
+  k_cg_finalize<T><<<(a.B + warps - 1) / warps, 32 * warps, 0, s>>>(a, parity, mode, max_restarts);
+}
+
+template void launch_apply<double>(const Geo&, Tile, const double*, int, const double*, int64_t,
+                                   double*, cudaStream_t);
+template void launch_apply<float>(const Geo&, Tile, const float*, int, const float*, int64_t, float*,
+                                  cudaStream_t);
+#define RBWS_INST(T)                                                                       \
+  template void launch_cg_init<T>(const CGArgs<T>&, Tile, int, int, cudaStream_t);        \
+  template void launch_cg_a<T>(const CGArgs<T>&, Tile, int, cudaStream_t);                \
+  template void launch_cg_b<T>(const CGArgs<T>&, Tile, int, cudaStream_t);                \
+  template void launch_cg_finalize<T>(const CGArgs<T>&, int, int, int, cudaStream_t);
+RBWS_INST(double)
+RBWS_INST(float)
+#undef RBWS_INST
+
+}  // namespace rbws

@@ -1,0 +1,205 @@
+"""Thin Python binding of librbws (include/rbws.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: host arrays are passed as numpy float64 arrays,
+device arrays as torch CUDA tensors (their data_ptr()).  The shared library
+must have been built (paper_2311_13862_gb300.build.build()); if it is missing
+or a call fails, an exception is raised -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librbws.so")
+
+RBWS_OK = 0
+RBWS_WARN_NOT_CONVERGED = 1
+STATUS_NAMES = {0: "OK", 1: "WARN_NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
+                -4: "ERR_NO_BASIS", -5: "ERR_NOT_SPD", -6: "ERR_DEVICE_TIMEOUT", -7: "ERR_STATE",
+                -8: "ERR_UNSUPPORTED"}
+WARM_ZERO, WARM_GALERKIN, WARM_LEARNED, WARM_LEARNED_CORRECTED = 0, 1, 2, 3
+PREC_NONE, PREC_JACOBI, PREC_MSRB = 0, 1, 2
+FP64, FP32_IR = 0, 1
+
+
+class RbwsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib().rbws_last_error().decode()
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), msg))
+
+
+class rbws_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+class rbws_blocks(C.Structure):
+    _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32)]
+
+
+class rbws_options(C.Structure):
+    _fields_ = [("max_iters", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32),
+                ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
+                ("check_every", C.c_int32), ("stream", C.c_void_p)]
+
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librbws.so is not built: run paper_2311_13862_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.rbws_last_error.restype = C.c_char_p
+        L.rbws_options_default.argtypes = [C.POINTER(rbws_options)]
+        L.rbws_problem_create.argtypes = [C.POINTER(rbws_grid), C.POINTER(rbws_blocks), P, i32, P, C.c_int,
+                                          C.POINTER(P)]
+        L.rbws_problem_destroy.argtypes = [P]
+        L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
+        L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
+        L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
+        L.rbws_set_basis.argtypes = [P, i32, P, P, P]
+        L.rbws_get_basis.argtypes = [P, P, P, P]
+        L.rbws_reduced_solve.argtypes = [P, P, i32, P]
+        L.rbws_solve_batch.argtypes = [P, P, i32, d, i32, C.POINTER(rbws_options), P, P, P, P]
+        for name in ("rbws_problem_create", "rbws_problem_info", "rbws_apply_operator",
+                     "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
+                     "rbws_solve_batch"):
+            getattr(L, name).restype = C.c_int
+        _L = L
+    return _L
+
+
+def _check(rc, where):
+    if rc < 0:
+        raise RbwsError(rc, where)
+    return rc
+
+
+def _host(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dp(t):
+    """Device pointer of a CUDA tensor (contiguous required)."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def rbws_options_default(**kw) -> rbws_options:
+    o = rbws_options()
+    _lib().rbws_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def rbws_problem_create(grid, blocks, Q=None, f=None, device=0):
+    g = rbws_grid(*grid)
+    b = rbws_blocks(*blocks)
+    Q = blocks[0] * blocks[1] * blocks[2] if Q is None else Q
+    fh = None if f is None else _host(f)
+    h = C.c_void_p()
+    _check(_lib().rbws_problem_create(C.byref(g), C.byref(b), None, Q, _hp(fh), device, C.byref(h)),
+           "rbws_problem_create")
+    return h
+
+
+def rbws_problem_destroy(h):
+    _lib().rbws_problem_destroy(h)
+
+
+def rbws_problem_info(h):
+    n, Q, N = C.c_int64(), C.c_int32(), C.c_int32()
+    _check(_lib().rbws_problem_info(h, C.byref(n), C.byref(Q), C.byref(N)), "rbws_problem_info")
+    return n.value, Q.value, N.value
+
+
+def rbws_apply_operator(h, mu, x, y, precision=FP64, stream=None):
+    mu = _host(np.atleast_2d(mu))
+    _check(_lib().rbws_apply_operator(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), precision, stream),
+           "rbws_apply_operator")
+
+
+def rbws_offline_greedy(h, mu_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12):
+    mu = _host(np.atleast_2d(mu_train))
+    sel = np.full(n_max, -1, dtype=np.int32)
+    eta = np.full(n_max, np.nan)
+    n_out = C.c_int32(0)
+    _check(_lib().rbws_offline_greedy(h, _hp(mu), mu.shape[0], n_max, greedy_tol, snapshot_tol, _hp(sel),
+                                      _hp(eta), C.byref(n_out)), "rbws_offline_greedy")
+    N = n_out.value
+    return N, sel[:N], eta[:N]
+
+
+def rbws_set_basis(h, W, ANq, fN):
+    W, ANq, fN = _host(W), _host(ANq), _host(fN)
+    _check(_lib().rbws_set_basis(h, W.shape[0], _hp(W), _hp(ANq), _hp(fN)), "rbws_set_basis")
+
+
+def rbws_get_basis(h):
+    n, Q, N = rbws_problem_info(h)
+    W = np.empty((N, n))
+    ANq = np.empty((Q, N, N))
+    fN = np.empty(N)
+    _check(_lib().rbws_get_basis(h, _hp(W), _hp(ANq), _hp(fN)), "rbws_get_basis")
+    return W, ANq, fN
+
+
+def rbws_reduced_solve(h, mu):
+    mu = _host(np.atleast_2d(mu))
+    _, _, N = rbws_problem_info(h)
+    c = np.empty((mu.shape[0], N))
+    _check(_lib().rbws_reduced_solve(h, _hp(mu), mu.shape[0], _hp(c)), "rbws_reduced_solve")
+    return c
+
+
+def rbws_solve_batch(h, mu, tol, warm, u_out, options: rbws_options | None = None):
+    """Returns (status, iters, relres, inst_status); u_out is a CUDA float64 tensor [B][n]."""
+    mu = _host(np.atleast_2d(mu))
+    B = mu.shape[0]
+    it = np.zeros(B, dtype=np.int32)
+    rel = np.zeros(B)
+    st = np.zeros(B, dtype=np.int32)
+    rc = _check(_lib().rbws_solve_batch(h, _hp(mu), B, tol, warm, None if options is None else C.byref(options),
+                                        _dp(u_out), _hp(it), _hp(rel), _hp(st)), "rbws_solve_batch")
+    return rc, it, rel, st
+
+
+class Problem:
+    """Owning wrapper around an rbws_problem handle."""
+
+    def __init__(self, grid, blocks, f=None, device=0):
+        self.grid, self.blocks = tuple(grid), tuple(blocks)
+        self.Q = blocks[0] * blocks[1] * blocks[2]
+        self.n = grid[0] * grid[1] * grid[2]
+        self.h = rbws_problem_create(grid, blocks, self.Q, f, device)
+
+    def close(self):
+        if self.h:
+            rbws_problem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
