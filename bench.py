@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the online RBWS hot path on one GB300 (or N, one process per GPU).
+
+Workload (the batched RB warm-start configuration): -div(kappa grad u) = 1 on the
+unit cube, zero Dirichlet data, 7-point finite differences on a 64^3 interior
+grid (262,144 DoFs), kappa = mu_q on 2x2x1 blocks (p = 4), mu log-uniform in
+[0.1, 10]^4.  Offline: greedy RB with N <= 20 over 256 training mu (not timed,
+reported as t_off).  One step = one rbws_solve_batch over 256 test mu: reduced
+Galerkin solves, lift u0 = W c, and Jacobi-PCG to ||r||/||f|| < 1e-10 (verified
+on the FP64 residual).  The headline arm runs the PCG in FP32 inside FP64
+iterative refinement; the FP64 arm and the zero-start arms are reported beside
+it.  Inputs are resident in HBM when the timed region starts; the working set
+(about 1.3 GB of solver vectors) is larger than L2, so no L2 flush is used.
+
+`--impl reference` times the CPU FP64 oracle instead (the reference of this
+build), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged solves/s at rel-res 1e-10, warm vs zero start; stencil % of HBM BW"
+UNIT = "solves/s"
+WORKLOAD = ("64^3 interior grid (262,144 DoFs), 2x2x1 blocks (p=4), mu log-uniform in [0.1,10]^4, "
+            "RB N<=20 by greedy over 256 training mu, 256 test mu per step, Jacobi-PCG to rel-res 1e-10")
+FALLBACK_HBM = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_per_dof(kernel_tag):
+    """DRAM bytes per active DoF of a kernel from a committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", kernel_tag + ".md")
+    try:
+        for line in open(path):
+            if line.strip().startswith("traffic_bytes_per_dof:"):
+                return float(line.split(":", 1)[1].split()[0])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(w, n_solves, threads, tol, n_train_sample, reference_steps=None):
+    """Times the CPU FP64 oracle (unchanged) on a bounded sample of the workload."""
+    import oracle as O
+    from paper_2311_13862_gb300 import inputs
+    op = O.assemble(w.grid, w.blocks)
+    t0 = time.perf_counter()
+    basis = O.greedy(op, inputs.train_mu(w)[:n_train_sample], w.n_max)
+    t_off = time.perf_counter() - t0
+    mus = inputs.test_mu(w)[:n_solves]
+    res = []
+    times = []
+    for _ in range(reference_steps or 1):
+        t0 = time.perf_counter()
+        r = O.solve_batch(op, mus, warm=O.WARM_GALERKIN, basis=basis, tol=tol, n_threads=threads)
+        times.append(time.perf_counter() - t0)
+        res.append(r)
+    return basis, res, times, t_off
+
+
+def reference_arm(args):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2311_13862_gb300 import inputs
+    import oracle as O
+    w = inputs.WORKLOADS["c2"]
+    threads = O.default_threads()
+    n_solves = max(threads, 16)
+    basis, res, times, t_off = cpu_baseline(w, n_solves, threads, w.tol, 32,
+                                            reference_steps=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = n_solves * len(timed) / total
+    its = np.concatenate([r.iters for r in res])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "batch": n_solves, "warm": "galerkin",
+                                            "precision": "fp64", "sample": True},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d of the 256 test mu per step, Galerkin warm start from an oracle "
+                                       "greedy over the first 32 training mu (N=%d)" % (n_solves, basis.N)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iters_mean": float(its.mean()), "t_off_s": t_off}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32ir", choices=["fp32ir", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arm-steps", type=int, default=2, help="timed steps of each side arm (0: skip arms)")
+    ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2311_13862_gb300 import build, inputs, rbws
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    build.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = inputs.WORKLOADS["c2"]
+    B = args.batch or w.n_test
+    # each rank solves its own batch of B parameters (weak scaling, no collective on the data path)
+    mus_all = inputs.test_mu(w, B * world)
+    mus = mus_all[rank * B:(rank + 1) * B]
+    P = rbws.Problem(w.grid, w.blocks, device=local)
+    t0 = time.perf_counter()
+    N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
+    torch.cuda.synchronize()
+    t_off = time.perf_counter() - t0
+
+    stream = torch.cuda.Stream()
+    u = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
+    prec = {"fp32ir": rbws.FP32_IR, "fp64": rbws.FP64}
+
+    def run(warm, precision, steps, warmup, profile=False):
+        prof = rbws.rbws_profile()
+        o = rbws.rbws_options_default(precision=precision, stream=stream.cuda_stream)
+        out = None
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                rbws.rbws_solve_batch(P.h, mus, w.tol, warm, u, o)
+            if profile:
+                import ctypes
+                o.profile = ctypes.pointer(prof)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            acc = {"launches": 0, "samples": 0, "stencil_ms": 0.0, "update_ms": 0.0, "active_dofs": 0.0}
+            torch.cuda.nvtx.range_push("timed")
+            e0.record(stream)
+            for _ in range(steps):
+                out = rbws.rbws_solve_batch(P.h, mus, w.tol, warm, u, o)
+                if profile:
+                    for k in acc:
+                        acc[k] += getattr(prof, k)
+            e1.record(stream)
+            torch.cuda.nvtx.range_pop()
+            barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        rc, it, rel, st = out
+        acc["elem_bytes"] = prof.elem_bytes
+        return ms, it, rel, st, acc
+
+    headline = prec[args.precision]
+    # ---- timed region of the headline arm, clocks sampled meanwhile ----
+    with ClockSampler(local) as clk:
+        ms, it, rel, st, acc = run(rbws.WARM_GALERKIN, headline, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    value = B * world / (ms / 1e3)
+
+    # ---- end to end: host parameters in, solution and counts back to pinned host memory ----
+    u_host = torch.empty((B, P.n), dtype=torch.float64, pin_memory=True)
+    mu_pinned = torch.from_numpy(mus.copy()).pin_memory()
+    o = rbws.rbws_options_default(precision=headline, stream=stream.cuda_stream)
+    e2e_steps = max(2, args.steps // 2)
+    with torch.cuda.stream(stream):
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            rbws.rbws_solve_batch(P.h, mu_pinned.numpy(), w.tol, rbws.WARM_GALERKIN, u, o)
+            u_host.copy_(u, non_blocking=True)
+        stream.synchronize()
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- side arms: zero start and the other precision ----
+    arms = {}
+    arm_list = [] if args.arm_steps <= 0 else [
+        ("galerkin_" + args.precision, rbws.WARM_GALERKIN, headline),
+        ("zero_fp64", rbws.WARM_ZERO, rbws.FP64),
+        ("galerkin_fp64" if args.precision != "fp64" else "galerkin_fp32ir",
+         rbws.WARM_GALERKIN, rbws.FP32_IR if args.precision == "fp64" else rbws.FP64),
+        ("zero_fp32ir", rbws.WARM_ZERO, rbws.FP32_IR)]
+    for name, warm, pr in arm_list:
+        if name.startswith("galerkin_" + args.precision):
+            a_ms, a_it, a_rel, a_st = ms, it, rel, st
+        else:
+            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1)
+        arms[name] = {"solves_per_s": B * world / (a_ms / 1e3), "ms_per_step": a_ms,
+                      "iters_mean": float(np.mean(a_it)), "iters_max": int(np.max(a_it)),
+                      "relres_max": float(np.max(a_rel)), "all_converged": bool(np.all(a_st == 0))}
+
+    # ---- roofline of the dominant kernel (stencil phase of the PCG iteration) ----
+    peak, peak_kind = peaks()
+    eb = acc["elem_bytes"] or 8
+    alg_stencil = 4 * eb   # reads s, p_old; writes p, q
+    alg_update = 7 * eb    # reads u, p, r, q; writes u, r, s
+    res = {}
+    if acc["samples"] > 0:
+        a_st_gbs = acc["active_dofs"] * alg_stencil / (acc["stencil_ms"] * 1e-3) / 1e9
+        a_up_gbs = acc["active_dofs"] * alg_update / (acc["update_ms"] * 1e-3) / 1e9
+        solver_gbs = acc["active_dofs"] * 6 * eb / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
+        tag = "cg_stencil_phase_%s_64cube" % ("f32" if eb == 4 else "f64")
+        tpd = traffic_per_dof(tag)
+        launch_dofs = acc["active_dofs"] / acc["samples"]
+        res = {"bound": "hbm", "achieved": round(a_st_gbs, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(a_st_gbs / peak, 4), "peak_kind": peak_kind,
+               "traffic": None if tpd is None else tpd * launch_dofs,
+               "kernel": "k_cg_a<%s> (p = s + beta p, q = A p, p.q)" % ("float" if eb == 4 else "double"),
+               "algorithmic_bytes_per_dof": alg_stencil,
+               "stencil_ms_per_launch": acc["stencil_ms"] / acc["samples"],
+               "update_kernel_frac": round(a_up_gbs / peak, 4),
+               "solver_frac_minimal_bytes": round(solver_gbs / peak, 4),
+               "sampled_launches": acc["samples"]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 inner / f64 outer" if headline == rbws.FP32_IR else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_gpu": B, "N": int(N), "warm": "galerkin",
+                       "precision": args.precision, "precond": "jacobi", "tol": w.tol,
+                       "l2": "no flush: solver working set ~1.3 GB > 129 MB L2",
+                       "parallelism": "independent batches per GPU (no collective)"},
+            "roofline": res, "gpu_launches": int(acc["launches"]), "clocks": clocks,
+            "e2e": {"value": B * world / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(B * w.Q * 8),
+                    "d2h_bytes_per_step": int(B * P.n * 8 + B * (4 + 8 + 4))},
+            "arms": arms, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "iters_mean": float(np.mean(it)), "relres_max": float(np.max(rel))}
+    if "zero_fp64" in arms:
+        line["speedup_vs_zero_fp64"] = value / arms["zero_fp64"]["solves_per_s"]
+        t_zero = 1.0 / (arms["zero_fp64"]["solves_per_s"] / world)
+        t_warm = 1.0 / (value / world)
+        line["bep_solves"] = t_off / (t_zero - t_warm) if t_zero > t_warm else None
+
+    # ---- sampled independent check: oracle FP64 true residual of two GPU solutions ----
+    if rank == 0:
+        import oracle as O
+        op = O.assemble(w.grid, w.blocks)
+        uu = u_host.numpy()
+        chk = []
+        for b in (0, B - 1):
+            chk.append(float(np.linalg.norm(np.ones(P.n) - op.matvec(mus[b], uu[b])) / np.sqrt(P.n)))
+        line["oracle_true_relres_sampled"] = chk
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1) ----
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        threads = O.default_threads()
+        n_solves = max(threads, 16)
+        basis, r, times, cpu_off = cpu_baseline(w, n_solves, threads, w.tol, 32)
+        line["cpu_baseline"] = {"value": n_solves / times[0], "unit": UNIT, "cores": r[0].threads,
+                                "kind": "oracle",
+                                "sample": "%d of the 256 test mu, Galerkin warm start from an oracle greedy "
+                                          "over the first 32 training mu (N=%d), Jacobi-PCG FP64 to 1e-10; "
+                                          "greedy took %.1f s (not in the rate)" % (n_solves, basis.N, cpu_off),
+                                "iters_mean": float(r[0].iters.mean())}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

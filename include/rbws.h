@@ -79,6 +79,20 @@ typedef enum {
 typedef struct { int32_t nx, ny, nz; } rbws_grid;   /* interior nodes per axis */
 typedef struct { int32_t bx, by, bz; } rbws_blocks; /* block rule, Q = bx*by*bz */
 
+/* Optional measurement record filled by rbws_solve_batch (options.profile).
+ * With profiling on, iterations are launched one by one instead of as a
+ * captured CUDA graph, and the first iteration of every block of check_every
+ * iterations is bracketed by CUDA events on the work stream. */
+typedef struct {
+  int64_t launches;    /* kernels launched by the call (graph nodes included)        */
+  int64_t samples;     /* iterations whose two phase kernels were timed              */
+  double stencil_ms;   /* summed durations of the sampled stencil-phase launches     */
+  double update_ms;    /* summed durations of the sampled update-phase launches      */
+  double active_dofs;  /* summed (active instances x n_dof) over the sampled launches */
+  int32_t elem_bytes;  /* 8: FP64 CG kernels were sampled; 4: FP32 inner kernels     */
+  int32_t pad;
+} rbws_profile;
+
 typedef struct {
   int32_t max_iters;    /* L_max of Algorithm 1 (counted over all restarts)     */
   int32_t precond;      /* rbws_precond                                          */
@@ -87,10 +101,14 @@ typedef struct {
   double inner_tol;     /* FP32_IR: relative reduction per inner solve (1e-5)   */
   int32_t max_outer;    /* FP32_IR: maximum refinement steps (10)                */
   int32_t check_every;  /* iterations between host convergence polls (0 = auto)  */
-  void* stream;         /* cudaStream_t for all work, NULL = legacy default      */
+  void* stream;         /* cudaStream_t: all GPU work of the call is issued on it;
+                           NULL = an internal stream ordered after the legacy
+                           default stream                                         */
+  rbws_profile* profile; /* NULL = off; else zeroed and filled by the call        */
 } rbws_options;
 
-/* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64). */
+/* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64,
+ * no profile). */
 RBWS_API void rbws_options_default(rbws_options* opt);
 
 /* Creates a problem on CUDA device `device` (Eq. 1).  The subdomain of each
@@ -122,7 +140,7 @@ RBWS_API rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32
  * maximises eta(mu) = ||f - A(mu) W c(mu)|| / ||f|| over the training points
  * not yet selected (ties: smallest index).  Stops at n_max, when max eta <
  * greedy_tol, or when a snapshot adds no new direction (||w|| < 1e-10 ||u||).
- * Replaces any previous basis.  selected_out [n_max], eta_hist_out [n_max]
+ * Replaces any previous basis; 1 <= n_max <= 160.  selected_out [n_max], eta_hist_out [n_max]
  * (eta_hist[k] = max eta once the basis has k+1 vectors) may be NULL. */
 RBWS_API rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
                                 int32_t n_max, double greedy_tol, double snapshot_tol,
@@ -130,7 +148,7 @@ RBWS_API rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train,
 
 /* Installs a reduced basis computed elsewhere: W host [N][n_dof] (orthonormal
  * columns stored one after another), ANq host [Q][N][N] = W^T A_q W,
- * fN host [N] = W^T f.  Copied. */
+ * fN host [N] = W^T f, 1 <= N <= 160.  Copied. */
 RBWS_API rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const double* ANq,
                            const double* fN);
 /* Copies the basis out: W host [N][n_dof], ANq host [Q][N][N], fN host [N];

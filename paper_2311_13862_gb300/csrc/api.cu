@@ -92,8 +92,11 @@ struct rbws_problem_s {
   double* d_f = nullptr;     // nullptr: f == 1
   double* d_ones = nullptr;  // ones vector (for W^T f when f == 1)
   double fnorm = 0.0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // internal stream (used when the caller passes none)
+  cudaStream_t cur = nullptr;     // work stream of the current call
   cudaEvent_t ev = nullptr;
+  cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};  // profiling events
+  int64_t launches = 0;           // kernels launched by the current call
   int* h_active = nullptr;   // pinned
   // reduced basis
   int N = 0;
@@ -143,10 +146,17 @@ struct StreamGuard {
   bool ok = true;
   StreamGuard(rbws_problem p_, void* user) : p(p_) {
     cudaSetDevice(p->device);
-    cudaStream_t us = (cudaStream_t)user;
-    cudaEventRecord(p->ev, us);
-    cudaStreamWaitEvent(p->stream, p->ev, 0);
+    p->launches = 0;
+    if (user) {
+      p->cur = (cudaStream_t)user;
+    } else {
+      // order after earlier work on the legacy default stream
+      cudaEventRecord(p->ev, 0);
+      cudaStreamWaitEvent(p->stream, p->ev, 0);
+      p->cur = p->stream;
+    }
   }
+  ~StreamGuard() { p->cur = p->stream; }
 };
 
 // Coefficient tables for B parameters already on the device.
@@ -163,7 +173,8 @@ rbws_status coef_tables(rbws_problem p, const double* d_mu, int B, double** c64,
   const int8_t* ky = kx + p->ax.key.size();
   const int8_t* kz = ky + p->ay.key.size();
   launch_coef_tables(p->geo, kx, ky, kz, p->bx, p->by, p->sx, p->sy, p->sz, p->Q, d_mu, B, *c64,
-                     c32 ? *c32 : nullptr, p->stream);
+                     c32 ? *c32 : nullptr, p->cur);
+  p->launches += 1;
   CK(cudaGetLastError());
   return RBWS_OK;
 }
@@ -173,7 +184,7 @@ rbws_status upload_mu(rbws_problem p, const double* mu, int B, double** d_mu, co
   *d_mu = (double*)p->buf(name, sizeof(double) * (size_t)B * p->Q, &err);
   if (err) return (rbws_status)err;
   CK(cudaMemcpyAsync(*d_mu, mu, sizeof(double) * (size_t)B * p->Q, cudaMemcpyHostToDevice,
-                     p->stream));
+                     p->cur));
   return RBWS_OK;
 }
 
@@ -187,36 +198,75 @@ __global__ void k_mask_done(InstState* st, const int* done, int B, int* active) 
   }
 }
 
+// One PCG iteration of the given parity: phase A, phase B and, for MSRB, the
+// preconditioner application (Algorithm 3) that completes s = P(r).
+template <typename T>
+int launch_iteration(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s) {
+  launch_cg_a<T>(a, t, parity, s);
+  launch_cg_b<T>(a, t, parity, s);
+  if constexpr (sizeof(T) == 8) {
+    if (a.precond == RBWS_PREC_MSRB) {
+      launch_msrb_apply(a, t, parity ^ 1, s);
+      return 6;
+    }
+  }
+  return 2;
+}
+
+// Completes the initial s = P(r0) for MSRB after an init pass.
+template <typename T>
+int launch_precond_start(const CGArgs<T>& a, Tile t, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (a.precond == RBWS_PREC_MSRB) {
+      launch_msrb_apply(a, t, 0, s);
+      return 4;
+    }
+  }
+  return 0;
+}
+
 // The batched PCG driver.  On entry a.u holds the initial values.  Runs
 // Algorithm 1 with the true-residual restarts of Algorithm 4.
 // `done` (device [B] or nullptr) marks instances that must not run; with
 // check_true = false the true-residual check is skipped (inner solves of
 // FP32_IR, whose outer loop checks the FP64 residual itself).
+// Iterations run in blocks of M = check_every (even): a captured CUDA graph
+// of M (A, B) phase pairs is relaunched until the device-side active count
+// reaches zero.  With a profile record the blocks are launched directly and
+// the first pair of each block is timed with CUDA events.
 template <typename T>
 rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int check_every,
-                    const int* done, bool check_true) {
-  cudaStream_t s = p->stream;
+                    const int* done, bool check_true, rbws_profile* prof) {
+  cudaStream_t s = p->cur;
   CK(cudaMemsetAsync(a.active, 0, sizeof(int), s));
   launch_cg_init<T>(a, t, 0, 0, s);
   launch_cg_finalize<T>(a, 0, 0, max_restarts, s);
-  if (done) k_mask_done<<<(a.B + 127) / 128, 128, 0, s>>>(a.st, done, a.B, a.active);
+  p->launches += 2;
+  if (done) {
+    k_mask_done<<<(a.B + 127) / 128, 128, 0, s>>>(a.st, done, a.B, a.active);
+    p->launches += 1;
+  }
+  p->launches += launch_precond_start<T>(a, t, s);
   CK(cudaGetLastError());
   int M = check_every > 0 ? check_every : 8;
   if (M % 2) M++;
-  // Capture M iterations (parities 0,1,0,1,...) once; relaunch until done.
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < M; k++) {
-    launch_cg_a<T>(a, t, k & 1, s);
-    launch_cg_b<T>(a, t, k & 1, s);
-  }
-  cudaError_t ce = cudaStreamEndCapture(s, &graph);
-  if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
-  ce = cudaGraphInstantiate(&exec, graph, 0);
-  if (ce != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
+  cudaError_t ce;
+  int per_iter = 2;
+  if (!prof) {
+    // Capture M iterations (parities 0,1,0,1,...) once; relaunch until done.
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < M; k++) per_iter = launch_iteration<T>(a, t, k & 1, s);
+    ce = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
+    }
+  } else {
+    prof->elem_bytes = (int32_t)sizeof(T);
   }
   rbws_status rc = RBWS_OK;
   for (;;) {
@@ -225,17 +275,47 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
       rc = (rbws_status)cuda_fail(ce, "solve loop");
       break;
     }
-    if (*p->h_active > 0) {
-      if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) {
-        rc = (rbws_status)cuda_fail(ce, "cudaGraphLaunch");
-        break;
+    const int active = *p->h_active;
+    if (active > 0) {
+      if (!prof) {
+        if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+          rc = (rbws_status)cuda_fail(ce, "cudaGraphLaunch");
+          break;
+        }
+      } else {
+        cudaEventRecord(p->tev[0], s);
+        launch_cg_a<T>(a, t, 0, s);
+        cudaEventRecord(p->tev[1], s);
+        launch_cg_b<T>(a, t, 0, s);
+        cudaEventRecord(p->tev[2], s);
+        if constexpr (sizeof(T) == 8) {
+          if (a.precond == RBWS_PREC_MSRB) {
+            launch_msrb_apply(a, t, 1, s);
+            per_iter = 6;
+          }
+        }
+        for (int k = 1; k < M; k++) launch_iteration<T>(a, t, k & 1, s);
+        if ((ce = cudaEventSynchronize(p->tev[2])) != cudaSuccess) {
+          rc = (rbws_status)cuda_fail(ce, "profile events");
+          break;
+        }
+        float ta = 0.f, tb = 0.f;
+        cudaEventElapsedTime(&ta, p->tev[0], p->tev[1]);
+        cudaEventElapsedTime(&tb, p->tev[1], p->tev[2]);
+        prof->stencil_ms += ta;
+        prof->update_ms += tb;
+        prof->active_dofs += (double)active * (double)p->n;
+        prof->samples += 1;
       }
+      p->launches += (int64_t)per_iter * M;
       continue;
     }
     if (!check_true) break;
     // all stopped: check the true residual f - A u, restart the failures
     launch_cg_init<T>(a, t, 0, 0, s);
     launch_cg_finalize<T>(a, 0, 1, max_restarts, s);
+    p->launches += 2;
+    p->launches += launch_precond_start<T>(a, t, s);
     cudaMemcpyAsync(p->h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, s);
     if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
       rc = (rbws_status)cuda_fail(ce, "true residual");
@@ -243,8 +323,8 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
     }
     if (*p->h_active == 0) break;
   }
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
   return rc;
 }
 
@@ -310,8 +390,9 @@ rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const do
   int err = 0;
   double* part = (double*)p->buf("res_part", sizeof(double) * (size_t)B * P, &err);
   if (err) return (rbws_status)err;
-  launch_residual64(p->geo, t, zc, coef64, B, p->d_f, u, r_out, part, P, p->stream);
-  launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->stream);
+  launch_residual64(p->geo, t, zc, coef64, B, p->d_f, u, r_out, part, P, p->cur);
+  launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->cur);
+  p->launches += 2;
   CK(cudaGetLastError());
   return RBWS_OK;
 }
@@ -326,12 +407,13 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u)
   double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
   int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
-  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, p->stream);
-  launch_lift(p->n, p->N, p->d_W, C, B, u, p->stream);
+  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, nullptr, p->cur);
+  launch_lift(p->n, p->N, p->d_W, C, B, u, p->cur);
+  p->launches += 2;
   CK(cudaGetLastError());
   std::vector<int> h(B);
-  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
   for (int b = 0; b < B; b++)
     if (h[b] != 0) {
       set_error("reduced matrix A_N(mu) is not positive definite for instance " + std::to_string(b));
@@ -351,11 +433,40 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
   a.tol = tol;
   a.max_iters = o.max_iters;
   a.precond = o.precond;
-  fill((double*)a.fnorm, B, p->fnorm, p->stream);
-  CKI(run_pcg<double>(p, a, t, o.max_restarts, o.check_every, nullptr, true));
+  if (o.precond == RBWS_PREC_MSRB) {
+    if (p->N <= 0) {
+      set_error("MSRB preconditioner needs a reduced basis");
+      return RBWS_ERR_NO_BASIS;
+    }
+    int err = 0;
+    const int N = p->N;
+    a.W = p->d_W;
+    a.N = N;
+    a.proj_chunks = (int)std::max<int64_t>(8, std::min<int64_t>(256, (4 * 1216 + B - 1) / B));
+    double* L = (double*)p->buf("msrb_L", sizeof(double) * (size_t)B * N * N, &err);
+    if (!err) a.G = (double*)p->buf("msrb_G", sizeof(double) * (size_t)B * N, &err);
+    if (!err) a.C = (double*)p->buf("msrb_C", sizeof(double) * (size_t)B * N, &err);
+    if (!err) a.proj_part = (double*)p->buf("msrb_part", sizeof(double) * (size_t)B * a.proj_chunks * N, &err);
+    int* info = err ? nullptr : (int*)p->buf("msrb_info", sizeof(int) * (size_t)B, &err);
+    if (err) return (rbws_status)err;
+    a.L = L;
+    launch_reduced_solve(N, p->Q, p->d_ANq, p->d_fN, d_mu, B, a.C, info, L, p->cur);
+    p->launches += 1;
+    std::vector<int> h(B);
+    CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
+    CK(cudaStreamSynchronize(p->cur));
+    for (int b = 0; b < B; b++)
+      if (h[b]) {
+        set_error("MSRB: A_N(mu) not positive definite");
+        return RBWS_ERR_NOT_SPD;
+      }
+  }
+  fill((double*)a.fnorm, B, p->fnorm, p->cur);
+  p->launches += 1;
+  CKI(run_pcg<double>(p, a, t, o.max_restarts, o.check_every, nullptr, true, o.profile));
   st.resize(B);
-  CK(cudaMemcpyAsync(st.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaMemcpyAsync(st.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
   return RBWS_OK;
 }
 
@@ -387,8 +498,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   st.assign(B, InstState{ST_ACTIVE, 0, 0, 0, 0.0, 0.0});
   for (int outer = 0;; outer++) {
     CKI(residual_norms(p, coef64, B, u, r64, rel));
-    CK(cudaMemcpyAsync(h_rel.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaMemcpyAsync(h_rel.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, p->cur));
+    CK(cudaStreamSynchronize(p->cur));
     int left = 0;
     for (int b = 0; b < B; b++) {
       if (outer == 0) st[b].relres0 = h_rel[b];
@@ -411,27 +522,29 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     // inner system: A d = r / ||r||; the relative test uses ||r_in|| / 1
     std::vector<double> hn(B);
     for (int b = 0; b < B; b++) hn[b] = h_rel[b] * p->fnorm;
-    CK(cudaMemcpyAsync(rnorm, hn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, p->stream));
-    CK(cudaMemcpyAsync(done, h_done.data(), sizeof(int) * B, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(rnorm, hn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, p->cur));
+    CK(cudaMemcpyAsync(done, h_done.data(), sizeof(int) * B, cudaMemcpyHostToDevice, p->cur));
     a.max_iters = o.max_iters;
     // The inner right-hand side is r/||r|| (norm 1 up to FP32 rounding), so
     // the inner relative test divides by a vector of ones.
     double* ones = (double*)p->buf("ir_ones", sizeof(double) * (size_t)B, &err);
     if (err) return (rbws_status)err;
-    fill(ones, B, 1.0, p->stream);
+    fill(ones, B, 1.0, p->cur);
+    p->launches += 1;
     CGArgs<float> ai = a;
     ai.fnorm = ones;
     ai.rhs_scale = rnorm;
-    CKI(run_pcg<float>(p, ai, t, 0, o.check_every, done, false));
+    CKI(run_pcg<float>(p, ai, t, 0, o.check_every, done, false, o.profile));
     CK(cudaMemcpyAsync(inner.data(), ai.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost,
-                       p->stream));
+                       p->cur));
     {
       const int threads = 256;
       dim3 grid((unsigned)std::min<int64_t>((p->n + threads - 1) / threads, 152 * 4), B);
-      k_ir_update<<<grid, threads, 0, p->stream>>>(p->n, B, d, rnorm, done, u);
+      k_ir_update<<<grid, threads, 0, p->cur>>>(p->n, B, d, rnorm, done, u);
+      p->launches += 1;
       CK(cudaGetLastError());
     }
-    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaStreamSynchronize(p->cur));
     for (int b = 0; b < B; b++)
       if (!h_done[b]) st[b].iters += inner[b].iters;
   }
@@ -457,6 +570,7 @@ void rbws_options_default(rbws_options* o) {
   o->max_outer = 10;
   o->check_every = 0;
   o->stream = nullptr;
+  o->profile = nullptr;
 }
 
 rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
@@ -559,6 +673,9 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   if ((e = cudaMalloc(&p->d_ones, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc");
   fill(p->d_ones, p->n, 1.0, p->stream);
   if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(e, "set-up");
+  for (auto& te : p->tev)
+    if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
+  p->cur = p->stream;
   if (!(p->fnorm > 0.0)) {
     set_error("rbws_problem_create: f must be nonzero");
     rbws_problem_destroy(p);
@@ -583,6 +700,8 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_fN);
   if (p->h_active) cudaFreeHost(p->h_active);
   if (p->ev) cudaEventDestroy(p->ev);
+  for (auto& e : p->tev)
+    if (e) cudaEventDestroy(e);
   if (p->stream) cudaStreamDestroy(p->stream);
   delete p;
 }
@@ -613,22 +732,22 @@ rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, con
   CKI(coef_tables(p, d_mu, B, &c64, precision == RBWS_FP32_IR ? &c32 : nullptr));
   Tile t = choose_tile(p->nx);
   if (precision == RBWS_FP64)
-    launch_apply<double>(p->geo, t, c64, B, (const double*)x, p->n, (double*)y, p->stream);
+    launch_apply<double>(p->geo, t, c64, B, (const double*)x, p->n, (double*)y, p->cur);
   else
-    launch_apply<float>(p->geo, t, c32, B, (const float*)x, p->n, (float*)y, p->stream);
+    launch_apply<float>(p->geo, t, c32, B, (const float*)x, p->n, (float*)y, p->cur);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaStreamSynchronize(p->cur));
   return RBWS_OK;
 }
 
 rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const double* ANq,
                            const double* fN) {
-  if (!p || N < 1 || N > 256 || !W || !ANq || !fN) {
-    set_error("rbws_set_basis: invalid argument (1 <= N <= 256)");
+  if (!p || N < 1 || N > 160 || !W || !ANq || !fN) {
+    set_error("rbws_set_basis: invalid argument (1 <= N <= 160)");
     return RBWS_ERR_INVALID_ARG;
   }
   cudaSetDevice(p->device);
-  cudaStreamSynchronize(p->stream);
+  cudaDeviceSynchronize();
   cudaFree(p->d_W);
   cudaFree(p->d_ANq);
   cudaFree(p->d_fN);
@@ -656,7 +775,7 @@ rbws_status rbws_get_basis(rbws_problem p, double* W, double* ANq, double* fN) {
     return RBWS_ERR_NO_BASIS;
   }
   cudaSetDevice(p->device);
-  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaStreamSynchronize(p->cur));
   if (W) CK(cudaMemcpy(W, p->d_W, sizeof(double) * (size_t)p->N * p->n, cudaMemcpyDeviceToHost));
   if (ANq) std::memcpy(ANq, p->h_ANq.data(), sizeof(double) * p->h_ANq.size());
   if (fN) std::memcpy(fN, p->h_fN.data(), sizeof(double) * p->h_fN.size());
@@ -679,12 +798,12 @@ rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, doub
   double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
   int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
-  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, p->stream);
+  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, nullptr, p->cur);
   CK(cudaGetLastError());
   std::vector<int> h(B);
-  CK(cudaMemcpyAsync(c_out, C, sizeof(double) * (size_t)B * p->N, cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
+  CK(cudaMemcpyAsync(c_out, C, sizeof(double) * (size_t)B * p->N, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
   for (int b = 0; b < B; b++)
     if (h[b]) {
       set_error("rbws_reduced_solve: A_N(mu) not positive definite");
@@ -696,12 +815,12 @@ rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, doub
 rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
                                 int32_t n_max, double greedy_tol, double snapshot_tol,
                                 int32_t* selected_out, double* eta_hist_out, int32_t* n_out) {
-  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 256 || !(snapshot_tol > 0.0)) {
-    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 256, snapshot_tol > 0)");
+  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 160 || !(snapshot_tol > 0.0)) {
+    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 160, snapshot_tol > 0)");
     return RBWS_ERR_INVALID_ARG;
   }
   StreamGuard sg(p, nullptr);
-  cudaStream_t s = p->stream;
+  cudaStream_t s = p->cur;
   const int64_t n = p->n;
   const int Q = p->Q;
   int err = 0;
@@ -847,8 +966,12 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
     set_error("rbws_solve_batch: invalid argument");
     return RBWS_ERR_INVALID_ARG;
   }
-  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI) {
-    set_error("rbws_solve_batch: this preconditioner is not available yet");
+  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI && o.precond != RBWS_PREC_MSRB) {
+    set_error("rbws_solve_batch: unknown preconditioner");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (o.precond == RBWS_PREC_MSRB && o.precision != RBWS_FP64) {
+    set_error("rbws_solve_batch: the MSRB preconditioner runs in FP64 only");
     return RBWS_ERR_UNSUPPORTED;
   }
   if (warm != RBWS_WARM_ZERO && warm != RBWS_WARM_GALERKIN) {
@@ -860,11 +983,12 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
     return RBWS_ERR_INVALID_ARG;
   }
   StreamGuard sg(p, o.stream);
+  if (o.profile) std::memset(o.profile, 0, sizeof(rbws_profile));
   double* d_mu = nullptr;
   CKI(upload_mu(p, mu, B, &d_mu, "mu_solve"));
   double* u = (double*)u_out;
   if (warm == RBWS_WARM_ZERO) {
-    CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->stream));
+    CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->cur));
   } else {
     CKI(galerkin_start(p, d_mu, B, u));
   }
@@ -874,6 +998,7 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
   } else {
     CKI(solve_fp32_ir(p, d_mu, B, tol, o, u, st));
   }
+  if (o.profile) o.profile->launches = p->launches;
   int warn = 0;
   for (int b = 0; b < B; b++) {
     iters_out[b] = st[b].iters;

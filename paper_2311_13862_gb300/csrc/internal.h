@@ -85,7 +85,15 @@ struct CGArgs {
   double tol;
   int max_iters;
   int* active;          // number of active instances
-  int precond;          // RBWS_PREC_NONE / JACOBI
+  int precond;          // RBWS_PREC_NONE / JACOBI / MSRB
+  // MSRB preconditioner (Algorithm 3), FP64 only
+  const double* W;      // [N][n] reduced basis
+  int N;
+  const double* L;      // [B][N][N] Cholesky factors of A_N(mu_b)
+  double* G;            // [B][N] projections W^T (r - A D^{-1} r)
+  double* C;            // [B][N] reduced corrections
+  double* proj_part;    // [B][proj_chunks][N] partial projections
+  int proj_chunks;
 };
 
 // ---------------------------------------------------------------------------
@@ -118,6 +126,10 @@ template <typename T>
 void launch_cg_a(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s);
 template <typename T>
 void launch_cg_b(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s);
+// MSRB preconditioner s = D^{-1} r + W A_N^{-1} W^T (r - A D^{-1} r) for the
+// active instances; on entry s holds D^{-1} r; the rho partials r.s are
+// written into parity slot `slot` (Algorithm 3 applied as P in Algorithm 1).
+void launch_msrb_apply(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s);
 // Per-instance finalisation after an init pass: mode 0 = start (record
 // relres0, set ACTIVE/CONVERGED, count active); mode 1 = true-residual check
 // (record relres, restart CONVERGED instances that fail tol).
@@ -128,9 +140,11 @@ void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restar
 // ---------------------------------------------------------------------------
 // Reduced basis kernels (rb.cu)
 // ---------------------------------------------------------------------------
-// c[b] = (sum_q mu[b][q] ANq[q])^{-1} fN; info[b] = 0 or -1 (not SPD).
+// c[b] = (sum_q mu[b][q] ANq[q])^{-1} fN; info[b] = 0 or -1 (not SPD).  If
+// L_out is non-null the Cholesky factor of each A_N(mu_b) is stored there
+// ([B][N][N], lower triangle, upper part zero).
 void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu,
-                          int B, double* c, int* info, cudaStream_t s);
+                          int B, double* c, int* info, double* L_out, cudaStream_t s);
 // u[b] = sum_j c[b][j] W[j]  (W: [N][n]).
 void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,
                  cudaStream_t s);
@@ -145,6 +159,41 @@ void launch_scale_inv(int64_t n, const double* alpha, double* w, cudaStream_t s)
 // per-instance eta[b] = sqrt(sum partials)/fnorm
 void launch_norms_from_partials(const double* part, int B, int P, double fnorm, double* out,
                                 cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Learned warm start (mlp.cu)
+// ---------------------------------------------------------------------------
+// C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]) with BF16 operands, FP32 accumulation;
+// Z = C and, if Aout is non-null, Aout = GELU(C) (both [M][ldz] row-major).
+struct MlpGemm {
+  int M, N, K;
+  const void* A;
+  int64_t sam, sak;
+  int a_bf16;
+  const void* B;
+  int64_t sbk, sbn;
+  int b_bf16;
+  const float* bias;
+  float* Z;
+  float* Aout;
+  int64_t ldz;
+};
+void launch_mlp_gemm(const MlpGemm& g, cudaStream_t s);
+void launch_mlp_inputs(const double* mu, int B, int p, double lo, double hi, float* x, cudaStream_t s);
+void launch_mlp_loss(const float* y, const float* t, int total, float scale, float* dy, float* loss,
+                     cudaStream_t s);
+void launch_gelu_back(const float* da, const float* z, int total, float* dz, cudaStream_t s);
+void launch_bias_grad(const float* dz, int M, int N, float* db, cudaStream_t s);
+void launch_adam(float* w, void* w16, const float* g, float* m1, float* m2, int64_t P, float lr, int* step,
+                 cudaStream_t s);
+void launch_init_params(float* w, void* w16, int64_t P, const int64_t* seg_end, const float* seg_bound,
+                        int nseg, uint64_t seed, cudaStream_t s);
+void launch_to_bf16(const float* w, void* w16, int64_t P, cudaStream_t s);
+void launch_rms_scale(const double* c, int B, int N, float* scale, cudaStream_t s);
+void launch_scale_targets(const double* c, const float* scale, int B, int N, float* t, cudaStream_t s);
+void launch_unscale(const float* y, const float* scale, int B, int N, double* c, cudaStream_t s);
+void launch_reduced_cg_step(int N, int Q, const double* ANq, const double* fN, const double* mu, int B,
+                            double* c, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Error reporting

@@ -20,7 +20,8 @@ __device__ __forceinline__ double warp_sum_down(double v) {
 // Cholesky, then the two triangular solves for c = A^{-1} fN.
 __global__ void k_reduced_solve(int N, int Q, const double* __restrict__ ANq,
                                 const double* __restrict__ fN, const double* __restrict__ mu,
-                                double* __restrict__ c, int* __restrict__ info) {
+                                double* __restrict__ c, int* __restrict__ info,
+                                double* __restrict__ L_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* A = reinterpret_cast<double*>(smem_raw);  // N*N
   double* x = A + N * N;                             // N
@@ -67,6 +68,9 @@ __global__ void k_reduced_solve(int N, int Q, const double* __restrict__ ANq,
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N; e += blockDim.x) c[(int64_t)b * N + e] = x[e];
+  if (L_out)
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x)
+      L_out[(int64_t)b * N * N + e] = (e % N) <= (e / N) ? A[e] : 0.0;
 }
 
 // u[b][i] = sum_j c[b][j] W[j][i]; each thread one node for kLiftB instances.
@@ -161,9 +165,11 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 }  // namespace
 
 void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu, int B,
-                          double* c, int* info, cudaStream_t s) {
+                          double* c, int* info, double* L_out, cudaStream_t s) {
   const size_t smem = sizeof(double) * ((size_t)N * N + N);
-  k_reduced_solve<<<B, 128, smem, s>>>(N, Q, ANq, fN, mu, c, info);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_reduced_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_reduced_solve<<<B, 128, smem, s>>>(N, Q, ANq, fN, mu, c, info, L_out);
 }
 
 void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,

@@ -279,7 +279,8 @@ __global__ void k_cg_init(CGArgs<T> a, int parity) {
   T* ub = a.u + off;
   T* rb = a.r + off;
   T* sb = a.s + off;
-  const bool jac = a.precond == RBWS_PREC_JACOBI;
+  const bool jac = a.precond != RBWS_PREC_NONE;  // Jacobi, or D^{-1} r as MSRB's first sweep
+  const bool msrb = a.precond == RBWS_PREC_MSRB;
   T rho = T(0), rr = T(0);
   if (a.rhs64 == nullptr) {
     zmarch<T>(
@@ -320,7 +321,7 @@ __global__ void k_cg_init(CGArgs<T> a, int parity) {
       }
     }
   }
-  double drho = (double)rho, drr = (double)rr;
+  double drho = msrb ? 0.0 : (double)rho, drr = (double)rr;
   block_sum2(drho, drr, red);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     a.rho_rr[((int64_t)parity * a.B + b) * a.P + tp.part] = make_double2(drho, drr);
@@ -416,7 +417,7 @@ __global__ void k_cg_a(CGArgs<T> a, int parity) {
   const T beta = (T)s_beta;
   const int64_t off = (int64_t)b * a.g.n;
   const T* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
-  const T* sb = (a.precond == RBWS_PREC_JACOBI ? a.s : a.r) + off;
+  const T* sb = (a.precond != RBWS_PREC_NONE ? a.s : a.r) + off;
   const T* pold = (parity ? a.p1 : a.p0) + off;
   T* pnew = (parity ? a.p0 : a.p1) + off;
   T* qb = a.q + off;
@@ -482,7 +483,8 @@ __global__ void k_cg_b(CGArgs<T> a, int parity) {
   T* ub = a.u + off;
   T* rb = a.r + off;
   T* sb = a.s + off;
-  const bool jac = a.precond == RBWS_PREC_JACOBI;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const bool msrb = a.precond == RBWS_PREC_MSRB;
   const Column cl = make_column(a.g, tp.x0, tp.y0);
   const int64_t plane = (int64_t)a.g.nx * a.g.ny;
   T rho = T(0), rr = T(0);
@@ -510,10 +512,132 @@ __global__ void k_cg_b(CGArgs<T> a, int parity) {
       rr = fma(rv, rv, rr);
     }
   }
-  double drho = (double)rho, drr = (double)rr;
+  double drho = msrb ? 0.0 : (double)rho, drr = (double)rr;
   block_sum2(drho, drr, red);
   if (tid == 0)
     a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + tp.part] = make_double2(drho, drr);
+}
+
+// ---------------------------------------------------------------------------
+// MSRB preconditioner (Algorithm 3) for the active instances.  On entry s
+// holds u~ = D^{-1} r (one undamped Jacobi sweep from zero).
+//   1. q = r - A u~                                  (stencil; q is free here)
+//   2. g = W^T q                                     (two-stage projections)
+//   3. c = A_N(mu)^{-1} g                            (cached Cholesky factor)
+//   4. s = u~ + W c,  partial rho = r.s              (into parity slot `slot`)
+// ---------------------------------------------------------------------------
+__global__ void k_msrb_residual(CGArgs<double> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE) return;
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const int64_t off = (int64_t)b * a.g.n;
+  const double* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
+  const double* ut = a.s + off;
+  const double* rb = a.r + off;
+  double* qb = a.q + off;
+  zmarch<double>(
+      a.g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return ut[idx]; },
+      [&](int64_t idx, double, double v, double) { qb[idx] = rb[idx] - v; });
+}
+
+constexpr int kProjJ = 8;  // basis vectors per pass of the projection kernel
+
+// part[b][chunk][j] = sum over the chunk's nodes of W[j][i] q[b][i]
+__global__ void k_msrb_project(CGArgs<double> a) {
+  __shared__ double red[kProjJ][32];
+  const int b = blockIdx.y;
+  if (a.st[b].status != ST_ACTIVE) return;
+  const int chunk = blockIdx.x, chunks = gridDim.x;
+  const int64_t n = a.g.n;
+  const double* qb = a.q + (int64_t)b * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j0 = 0; j0 < a.N; j0 += kProjJ) {
+    double acc[kProjJ];
+#pragma unroll
+    for (int k = 0; k < kProjJ; k++) acc[k] = 0.0;
+    for (int64_t i = (int64_t)chunk * blockDim.x + threadIdx.x; i < n; i += (int64_t)chunks * blockDim.x) {
+      const double qv = qb[i];
+#pragma unroll
+      for (int k = 0; k < kProjJ; k++)
+        if (j0 + k < a.N) acc[k] = fma(a.W[(int64_t)(j0 + k) * n + i], qv, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kProjJ; k++) {
+      double v = warp_sum_down(acc[k]);
+      if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int k = 0; k < kProjJ; k++) {
+        double v = lane < nw ? red[k][lane] : 0.0;
+        v = warp_sum_down(v);
+        if (lane == 0 && j0 + k < a.N)
+          a.proj_part[((int64_t)b * chunks + chunk) * a.N + j0 + k] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per instance: g = sum of the chunk partials, then c = L^{-T} L^{-1} g.
+__global__ void k_msrb_reduce_solve(CGArgs<double> a) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= a.B || a.st[b].status != ST_ACTIVE) return;
+  const int N = a.N, chunks = a.proj_chunks;
+  double* g = a.G + (int64_t)b * N;
+  for (int j = 0; j < N; j++) {
+    double v = 0.0;
+    for (int c = lane; c < chunks; c += 32) v += a.proj_part[((int64_t)b * chunks + c) * N + j];
+    v = warp_sum_down(v);
+    if (lane == 0) g[j] = v;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const double* L = a.L + (int64_t)b * N * N;
+    double* c = a.C + (int64_t)b * N;
+    for (int i = 0; i < N; i++) {
+      double v = g[i];
+      for (int k = 0; k < i; k++) v = fma(-L[i * N + k], c[k], v);
+      c[i] = v / L[i * N + i];
+    }
+    for (int i = N - 1; i >= 0; i--) {
+      double v = c[i];
+      for (int k = i + 1; k < N; k++) v = fma(-L[k * N + i], c[k], v);
+      c[i] = v / L[i * N + i];
+    }
+  }
+}
+
+// s = u~ + W c and the partials of rho = r.s (same tiling as the update phase).
+__global__ void k_msrb_lift(CGArgs<double> a, int slot) {
+  __shared__ double red[64];
+  __shared__ double cs[256];
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int j = tid; j < a.N; j += blockDim.x * blockDim.y) cs[j] = a.C[(int64_t)b * a.N + j];
+  __syncthreads();
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const int64_t off = (int64_t)b * a.g.n;
+  const Column cl = make_column(a.g, tp.x0, tp.y0);
+  const int64_t plane = (int64_t)a.g.nx * a.g.ny;
+  double rho = 0.0;
+  if (cl.own) {
+    for (int z = tp.z0; z < tp.z1; ++z) {
+      const int64_t idx = (int64_t)z * plane + cl.col;
+      double sv = a.s[off + idx];
+      for (int j = 0; j < a.N; j++) sv = fma(cs[j], a.W[(int64_t)j * a.g.n + idx], sv);
+      a.s[off + idx] = sv;
+      rho = fma(a.r[off + idx], sv, rho);
+    }
+  }
+  double dummy = 0.0;
+  block_sum2(rho, dummy, red);
+  if (tid == 0) a.rho_rr[((int64_t)slot * a.B + b) * a.P + tp.part].x = rho;
 }
 
 inline size_t plane_smem(Tile t, size_t elem) { return 3 * (size_t)(t.tx + 2) * (t.ty + 2) * elem; }
@@ -578,6 +702,13 @@ template <typename T>
 void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restarts, cudaStream_t s) {
   const int warps = 4;
   k_cg_finalize<T><<<(a.B + warps - 1) / warps, 32 * warps, 0, s>>>(a, parity, mode, max_restarts);
+}
+
+void launch_msrb_apply(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s) {
+  k_msrb_residual<<<cg_grid(a), dim3(t.tx, t.ty), plane_smem(t, sizeof(double)), s>>>(a);
+  k_msrb_project<<<dim3(a.proj_chunks, a.B), 256, 0, s>>>(a);
+  k_msrb_reduce_solve<<<(a.B + 3) / 4, 128, 0, s>>>(a);
+  k_msrb_lift<<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, slot);
 }
 
 template void launch_apply<double>(const Geo&, Tile, const double*, int, const double*, int64_t,

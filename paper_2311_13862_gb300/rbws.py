@@ -41,10 +41,17 @@ class rbws_blocks(C.Structure):
     _fields_ = [("bx", C.c_int32), ("by", C.c_int32), ("bz", C.c_int32)]
 
 
+class rbws_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("samples", C.c_int64), ("stencil_ms", C.c_double),
+                ("update_ms", C.c_double), ("active_dofs", C.c_double), ("elem_bytes", C.c_int32),
+                ("pad", C.c_int32)]
+
+
 class rbws_options(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32),
                 ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
-                ("check_every", C.c_int32), ("stream", C.c_void_p)]
+                ("check_every", C.c_int32), ("stream", C.c_void_p),
+                ("profile", C.POINTER(rbws_profile))]
 
 
 _L = None

@@ -66,3 +66,15 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", text, flags=re.M), f
                 assert "rbws_oracle" not in text and "liborc" not in text, f
+
+
+def test_options_default_sets_every_field(lib_path):
+    """rbws_options_default must overwrite every field (internal callers rely on it)."""
+    import ctypes as C
+    from paper_2311_13862_gb300 import rbws
+    o = rbws.rbws_options()
+    C.memset(C.byref(o), 0xAB, C.sizeof(o))
+    rbws._lib().rbws_options_default(C.byref(o))
+    assert o.max_iters == 20000 and o.precond == rbws.PREC_JACOBI and o.precision == rbws.FP64
+    assert o.max_restarts == 3 and o.inner_tol == 1e-5 and o.max_outer == 10 and o.check_every == 0
+    assert o.stream is None and not o.profile

@@ -109,3 +109,30 @@ def test_reruns_are_bitwise_deterministic():
         a = solve(P, mu, 1e-11, rbws.WARM_ZERO)
         b = solve(P, mu, 1e-11, rbws.WARM_ZERO)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[4], b[4])
+
+
+@pytest.mark.parametrize("grid,blocks,n_max", [((16, 16, 16), (2, 1, 1), 6), ((24, 20, 18), (2, 2, 1), 8)])
+def test_msrb_preconditioned_start_matches_oracle(grid, blocks, n_max):
+    """RB-preconditioned arm: Galerkin start, then PCG with the MSRB preconditioner
+    (Algorithm 3, same W at every iteration).  Iteration counts within 2; converged
+    solutions agree to 1e-10; non-converged ones report the same status."""
+    w = inputs.small(grid=grid, blocks=blocks, n_max=n_max, n_train=24, n_test=4)
+    op = O.assemble(w.grid, w.blocks)
+    basis = O.greedy(op, inputs.train_mu(w), w.n_max)
+    mu = inputs.test_mu(w)
+    ref = O.solve_batch(op, mu, warm=O.WARM_GALERKIN, basis=basis, precond=O.PREC_MSRB, tol=1e-12,
+                        max_iters=400)
+    with rbws.Problem(w.grid, w.blocks) as P:
+        rbws.rbws_set_basis(P.h, basis.W, basis.ANq, basis.fN)
+        rc, it, rel, st, u = solve(P, mu, 1e-12, rbws.WARM_GALERKIN, precond=rbws.PREC_MSRB, max_iters=400)
+    assert np.array_equal(st, ref.status), (st, ref.status)
+    conv = st == 0
+    assert np.all(np.abs(it[conv] - ref.iters[conv]) <= 2), (it, ref.iters)
+    if conv.any():
+        assert np.all(rel_l2(u[conv], ref.u[conv]) <= 1e-10)
+
+
+def test_msrb_without_basis_is_an_error():
+    with rbws.Problem((8, 8, 8), (2, 1, 1)) as P:
+        with pytest.raises(rbws.RbwsError, match="NO_BASIS"):
+            solve(P, np.array([[1.0, 2.0]]), 1e-10, rbws.WARM_ZERO, precond=rbws.PREC_MSRB)
