@@ -134,6 +134,28 @@ RBWS_API rbws_status rbws_problem_info(rbws_problem p, int64_t* n_dof, int32_t* 
 RBWS_API rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, const void* x,
                                 void* y, int32_t precision, void* stream);
 
+/* rbws_apply_operator for callers that cannot allocate device memory after
+ * start-up: services that run inside a fixed device-memory budget shared with
+ * another framework's caching allocator, or latency-sensitive code that
+ * cannot accept the implicit device synchronisation cudaMalloc / cudaFree may
+ * perform.  The paper has no counterpart; this is a deployment variant.
+ * Same arguments and result as rbws_apply_operator, but the call allocates
+ * nothing: its scratch (the device copy of mu and the per-instance
+ * coefficient tables) lives in one static 4 MiB device array that every GPU
+ * loading the library holds until the process exits.  A call needs
+ * 8*B*Q + 64*B*C bytes (+ 32*B*C for float32), each part rounded up to 256,
+ * where C is the number of coefficient classes of the grid (at most
+ * (3*bx+2)*(3*by+2)*(3*bz+2)); larger requests return RBWS_ERR_INVALID_ARG
+ * with the sizes in the message.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; every call overwrites what it reads, so nothing needs to
+ * start at zero.  Calls whose GPU work overlaps (from two threads, two
+ * problems on one device, or two streams) race on the array.  Synchronous. */
+RBWS_API rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu, int32_t B,
+                                                const void* x, void* y, int32_t precision,
+                                                void* stream);
+
 /* Offline greedy (Algorithm 5's loop with the Galerkin RB of Sec. 2.3 and a
  * residual indicator): first parameter = mu_train[0]; snapshot solves by
  * Jacobi-PCG to snapshot_tol; Gram-Schmidt applied twice; the next parameter

@@ -740,6 +740,21 @@ rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, con
   return RBWS_OK;
 }
 
+rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu, int32_t B, const void* x,
+                                       void* y, int32_t precision, void* stream) {
+  if (!p || !mu || !x || !y || B < 1 || B > 65535 ||
+      (precision != RBWS_FP64 && precision != RBWS_FP32_IR)) {
+    set_error("rbws_apply_operator_static: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, stream);
+  const int8_t* kx = p->d_keys;
+  const int8_t* ky = kx + p->ax.key.size();
+  const int8_t* kz = ky + p->ay.key.size();
+  return (rbws_status)apply_operator_static(p->device, p->geo, kx, ky, kz, p->bx, p->by, p->sx, p->sy, p->sz,
+                                            p->Q, mu, B, x, y, precision, p->cur, choose_tile(p->nx));
+}
+
 rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const double* ANq,
                            const double* fN) {
   if (!p || N < 1 || N > 160 || !W || !ANq || !fN) {

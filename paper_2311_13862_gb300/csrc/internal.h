@@ -196,6 +196,15 @@ void launch_reduced_cg_step(int N, int Q, const double* ANq, const double* fN, c
                             double* c, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Operator apply with static scratch (static_scratch.cu)
+// ---------------------------------------------------------------------------
+size_t static_scratch_need(int Q, int ncls, int B, bool fp32);
+size_t static_scratch_capacity();
+int apply_operator_static(int device, const Geo& g, const int8_t* kx, const int8_t* ky, const int8_t* kz,
+                          int bx, int by, double sx, double sy, double sz, int Q, const double* mu_host,
+                          int B, const void* x, void* y, int precision, cudaStream_t s, Tile t);
+
+// ---------------------------------------------------------------------------
 // Error reporting
 // ---------------------------------------------------------------------------
 void set_error(const std::string& msg);

@@ -71,12 +71,13 @@ def _lib():
         L.rbws_problem_destroy.argtypes = [P]
         L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
+        L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
         L.rbws_set_basis.argtypes = [P, i32, P, P, P]
         L.rbws_get_basis.argtypes = [P, P, P, P]
         L.rbws_reduced_solve.argtypes = [P, P, i32, P]
         L.rbws_solve_batch.argtypes = [P, P, i32, d, i32, C.POINTER(rbws_options), P, P, P, P]
-        for name in ("rbws_problem_create", "rbws_problem_info", "rbws_apply_operator",
+        for name in ("rbws_problem_create", "rbws_problem_info", "rbws_apply_operator", "rbws_apply_operator_static",
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
                      "rbws_solve_batch"):
             getattr(L, name).restype = C.c_int
@@ -138,6 +139,13 @@ def rbws_apply_operator(h, mu, x, y, precision=FP64, stream=None):
     mu = _host(np.atleast_2d(mu))
     _check(_lib().rbws_apply_operator(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), precision, stream),
            "rbws_apply_operator")
+
+
+def rbws_apply_operator_static(h, mu, x, y, precision=FP64, stream=None):
+    """rbws_apply_operator without device allocation (scratch in a static device array)."""
+    mu = _host(np.atleast_2d(mu))
+    _check(_lib().rbws_apply_operator_static(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), precision, stream),
+           "rbws_apply_operator_static")
 
 
 def rbws_offline_greedy(h, mu_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12):
