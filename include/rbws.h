@@ -73,7 +73,12 @@ typedef enum {
 
 typedef enum {
   RBWS_FP64 = 0,    /* all CG arithmetic in FP64                                */
-  RBWS_FP32_IR = 1  /* FP32 inner PCG inside FP64 iterative refinement          */
+  RBWS_FP32_IR = 1  /* PCG in FP32 inside FP64 iterative refinement: the FP32
+                       correction is folded into the FP64 solution and the
+                       FP64 residual f - A u replaces the FP32 one every
+                       inner_tol reduction (reliable updates); the search
+                       direction is kept; convergence is judged on the FP64
+                       residual                                                 */
 } rbws_precision;
 
 typedef struct { int32_t nx, ny, nz; } rbws_grid;   /* interior nodes per axis */
@@ -98,8 +103,10 @@ typedef struct {
   int32_t precond;      /* rbws_precond                                          */
   int32_t precision;    /* rbws_precision                                        */
   int32_t max_restarts; /* true-residual restarts of Algorithm 4 (default 3)     */
-  double inner_tol;     /* FP32_IR: relative reduction per inner solve (1e-5)   */
-  int32_t max_outer;    /* FP32_IR: maximum refinement steps (10)                */
+  double inner_tol;     /* FP32_IR: an FP64 refinement step (reliable update) is
+                           taken each time an instance's FP32 residual has
+                           fallen by this factor since its last one (1e-2)      */
+  int32_t max_outer;    /* reserved (10)                                         */
   int32_t check_every;  /* iterations between host convergence polls (0 = auto)  */
   void* stream;         /* cudaStream_t: all GPU work of the call is issued on it;
                            NULL = an internal stream ordered after the legacy

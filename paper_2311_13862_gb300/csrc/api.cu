@@ -134,6 +134,35 @@ Tile choose_tile(int nx) {
   return t;
 }
 
+// Tile of the 4-node-per-thread FP32 kernels: widest row segment (4*tx nodes,
+// tx in {32,16,8,4}) dividing nx (else the widest that fits), up to 256
+// threads.  tx = 0 when nx % 4 != 0 (the one-node kernels are used then).
+Tile choose_tile_v4(int nx, int ny) {
+  Tile t{0, 0};
+  if (nx % 4) return t;
+  for (int tx : {32, 16, 8, 4})
+    if (4 * tx <= nx && nx % (4 * tx) == 0) {
+      t.tx = tx;
+      break;
+    }
+  if (!t.tx)  // no exact fit: widest segment that fits, last tile ragged
+    for (int tx : {32, 16, 8, 4})
+      if (4 * tx <= nx) {
+        t.tx = tx;
+        break;
+      }
+  if (!t.tx) return t;
+  t.ty = std::min(256 / t.tx, ny);
+  return t;
+}
+
+// z-chunking of the v4 kernels: a few waves of 4 resident CTAs per SM.
+int choose_zc_v4(int nz, int64_t ctas_per_chunk) {
+  int nzc = 1;
+  while (ctas_per_chunk * nzc < 4 * 608 && (nz / (nzc * 2)) >= 8) nzc *= 2;
+  return (nz + nzc - 1) / nzc;
+}
+
 // z-chunking: enough CTAs for several waves, chunks of at least 8 planes.
 int choose_zc(int nz, int64_t ctas_per_chunk) {
   int nzc = 1;
@@ -330,14 +359,15 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
 
 template <typename T>
 rbws_status make_cg_args(rbws_problem p, int B, Tile t, const T* coef, T* u, CGArgs<T>* out,
-                         const std::string& tag) {
+                         const std::string& tag, int vec = 1) {
   int err = 0;
   CGArgs<T> a{};
   a.g = p->geo;
   a.B = B;
-  a.tiles_x = (p->nx + t.tx - 1) / t.tx;
+  a.tiles_x = (p->nx + vec * t.tx - 1) / (vec * t.tx);
   a.tiles_y = (p->ny + t.ty - 1) / t.ty;
-  a.zc = choose_zc(p->nz, (int64_t)a.tiles_x * a.tiles_y * B);
+  a.zc = vec == 4 ? choose_zc_v4(p->nz, (int64_t)a.tiles_x * a.tiles_y * B)
+                  : choose_zc(p->nz, (int64_t)a.tiles_x * a.tiles_y * B);
   a.nzc = (p->nz + a.zc - 1) / a.zc;
   a.P = a.tiles_x * a.tiles_y * a.nzc;
   a.coef = coef;
@@ -364,25 +394,13 @@ __global__ void k_fill(double* x, int64_t n, double v) {
     x[i] = v;
 }
 
-// u[b] += scale[b] * d[b] for instances not yet done (FP32_IR update).
-__global__ void k_ir_update(int64_t n, int B, const float* __restrict__ d,
-                            const double* __restrict__ scale, const int* __restrict__ done,
-                            double* __restrict__ u) {
-  const int b = blockIdx.y;
-  if (done[b]) return;
-  const double sc = scale[b];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    u[(int64_t)b * n + i] = fma(sc, (double)d[(int64_t)b * n + i], u[(int64_t)b * n + i]);
-}
-
 void fill(double* x, int64_t n, double v, cudaStream_t s) {
   k_fill<<<152 * 4, 256, 0, s>>>(x, n, v);
 }
 
 // Per-instance FP64 true residual norms ||f - A u|| / ||f||  (B values, device).
 rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const double* u,
-                           double* r_out, double* rel_dev) {
+                           double* r_out, double* rel_dev, const int* mask = nullptr) {
   Tile t = choose_tile(p->nx);
   const int tiles = ((p->nx + t.tx - 1) / t.tx) * ((p->ny + t.ty - 1) / t.ty);
   const int zc = choose_zc(p->nz, (int64_t)tiles * B);
@@ -390,7 +408,7 @@ rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const do
   int err = 0;
   double* part = (double*)p->buf("res_part", sizeof(double) * (size_t)B * P, &err);
   if (err) return (rbws_status)err;
-  launch_residual64(p->geo, t, zc, coef64, B, p->d_f, u, r_out, part, P, p->cur);
+  launch_residual64(p->geo, t, zc, coef64, B, p->d_f, u, r_out, part, P, mask, p->cur);
   launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->cur);
   p->launches += 2;
   CK(cudaGetLastError());
@@ -470,84 +488,162 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
   return RBWS_OK;
 }
 
-// FP32 inner Jacobi-PCG inside FP64 iterative refinement:
-//   r = f - A u (FP64);  stop if ||r||/||f|| < tol;  solve A d = r/||r|| in FP32
-//   to a relative reduction inner_tol;  u += ||r|| d (FP64).
+// FP32 Jacobi-PCG inside FP64 iterative refinement, with reliable updates:
+// the FP32 iteration accumulates its correction d; whenever an instance's
+// FP32 residual has dropped by the factor inner_tol since its last update (or
+// meets tol), the correction is folded into the FP64 solution u, the FP64
+// residual f - A u is formed, and the FP32 residual is reset from it.  The
+// search direction is kept across updates (restarted only when an FP64 check
+// after apparent convergence fails), so the Krylov space is not thrown away
+// at every refinement step.  Convergence is decided on the FP64 residual.
 rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
                           const rbws_options& o, double* u, std::vector<InstState>& st) {
   double* coef64 = nullptr;
   float* coef32 = nullptr;
   CKI(coef_tables(p, d_mu, B, &coef64, &coef32));
-  Tile t = choose_tile(p->nx);
-  CGArgs<float> a{};
+  const Tile t4 = choose_tile_v4(p->nx, p->ny);
+  const bool v4 = t4.tx > 0;
+  const Tile t = v4 ? t4 : choose_tile(p->nx);
+  auto phase_a = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
+    if (v4) launch_cg_a_v4(aa, t, par, ss);
+    else launch_cg_a<float>(aa, t, par, ss);
+  };
+  auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
+    if (v4) launch_cg_b_v4(aa, t, par, ss);
+    else launch_cg_b<float>(aa, t, par, ss);
+  };
+  auto reset = [&](const CGArgs<float>& aa, int start, cudaStream_t ss) {
+    if (v4) launch_ru_reset_v4(aa, t, start, ss);
+    else launch_ru_reset(aa, t, start, ss);
+  };
+  cudaStream_t s = p->cur;
   int err = 0;
   float* d = (float*)p->buf("ir_d", sizeof(float) * (size_t)B * p->n, &err);
   double* r64 = err ? nullptr : (double*)p->buf("ir_r64", sizeof(double) * (size_t)B * p->n, &err);
   double* rel = err ? nullptr : (double*)p->buf("ir_rel", sizeof(double) * (size_t)B, &err);
-  double* rnorm = err ? nullptr : (double*)p->buf("ir_rnorm", sizeof(double) * (size_t)B, &err);
-  int* done = err ? nullptr : (int*)p->buf("ir_done", sizeof(int) * (size_t)B, &err);
+  double* rr_ref = err ? nullptr : (double*)p->buf("ir_rr_ref", sizeof(double) * (size_t)B, &err);
+  int* upd = err ? nullptr : (int*)p->buf("ir_upd", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
-  CKI(make_cg_args<float>(p, B, t, coef32, d, &a, "f_"));
+  CGArgs<float> a{};
+  CKI(make_cg_args<float>(p, B, t, coef32, d, &a, "f_", v4 ? 4 : 1));
   a.f = nullptr;
-  a.rhs64 = r64;
-  a.tol = o.inner_tol;
+  a.tol = tol;
+  a.max_iters = o.max_iters;
   a.precond = o.precond;
-  std::vector<double> h_rel(B);
-  std::vector<int> h_done(B, 0);
-  std::vector<InstState> inner(B);
-  st.assign(B, InstState{ST_ACTIVE, 0, 0, 0, 0.0, 0.0});
-  for (int outer = 0;; outer++) {
-    CKI(residual_norms(p, coef64, B, u, r64, rel));
-    CK(cudaMemcpyAsync(h_rel.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, p->cur));
-    CK(cudaStreamSynchronize(p->cur));
-    int left = 0;
-    for (int b = 0; b < B; b++) {
-      if (outer == 0) st[b].relres0 = h_rel[b];
-      st[b].relres = h_rel[b];
-      if (!h_done[b]) {
-        if (h_rel[b] < tol) {
-          h_done[b] = 1;
-          st[b].status = ST_CONVERGED;
-        } else if (!(h_rel[b] == h_rel[b])) {
-          h_done[b] = 1;
-          st[b].status = ST_BREAKDOWN;
-        } else if (outer >= o.max_outer || st[b].iters >= o.max_iters) {
-          h_done[b] = 1;
-          st[b].status = ST_MAX_ITERS;
-        }
-      }
-      left += !h_done[b];
+  a.ru = 1;
+  const double delta = (o.inner_tol > 0.0 && o.inner_tol < 1.0) ? o.inner_tol : 1e-2;
+  a.ru_delta2 = delta * delta;
+  a.rr_ref = rr_ref;
+  a.pending = a.active + 1;
+  a.upd = upd;
+  a.u64 = u;
+  a.r64 = r64;
+  a.rel64 = rel;
+  fill((double*)a.fnorm, B, p->fnorm, s);
+  CK(cudaMemsetAsync(d, 0, sizeof(float) * (size_t)B * p->n, s));
+  // start: every instance takes an update from u (restarting its direction)
+  std::vector<int> two(B, 2);
+  CK(cudaMemcpyAsync(upd, two.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(a.active, 0, 2 * sizeof(int), s));
+  CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
+  reset(a, 1, s);
+  p->launches += 2;
+  CK(cudaGetLastError());
+  int M = o.check_every > 0 ? o.check_every : 8;
+  if (M % 2) M++;
+  rbws_profile* prof = o.profile;
+  if (prof) prof->elem_bytes = 4;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ce;
+  if (!prof) {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < M; k++) {
+      phase_a(a, k & 1, s);
+      phase_b(a, k & 1, s);
     }
-    if (!left) break;
-    // inner system: A d = r / ||r||; the relative test uses ||r_in|| / 1
-    std::vector<double> hn(B);
-    for (int b = 0; b < B; b++) hn[b] = h_rel[b] * p->fnorm;
-    CK(cudaMemcpyAsync(rnorm, hn.data(), sizeof(double) * B, cudaMemcpyHostToDevice, p->cur));
-    CK(cudaMemcpyAsync(done, h_done.data(), sizeof(int) * B, cudaMemcpyHostToDevice, p->cur));
-    a.max_iters = o.max_iters;
-    // The inner right-hand side is r/||r|| (norm 1 up to FP32 rounding), so
-    // the inner relative test divides by a vector of ones.
-    double* ones = (double*)p->buf("ir_ones", sizeof(double) * (size_t)B, &err);
-    if (err) return (rbws_status)err;
-    fill(ones, B, 1.0, p->cur);
-    p->launches += 1;
-    CGArgs<float> ai = a;
-    ai.fnorm = ones;
-    ai.rhs_scale = rnorm;
-    CKI(run_pcg<float>(p, ai, t, 0, o.check_every, done, false, o.profile));
-    CK(cudaMemcpyAsync(inner.data(), ai.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost,
-                       p->cur));
-    {
-      const int threads = 256;
-      dim3 grid((unsigned)std::min<int64_t>((p->n + threads - 1) / threads, 152 * 4), B);
-      k_ir_update<<<grid, threads, 0, p->cur>>>(p->n, B, d, rnorm, done, u);
-      p->launches += 1;
-      CK(cudaGetLastError());
+    cudaMemsetAsync(a.pending, 0, sizeof(int), s);
+    launch_ru_decide(a, s);
+    ce = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
     }
-    CK(cudaStreamSynchronize(p->cur));
-    for (int b = 0; b < B; b++)
-      if (!h_done[b]) st[b].iters += inner[b].iters;
   }
+  rbws_status rc = RBWS_OK;
+  int counts[2];
+  for (;;) {
+    cudaMemcpyAsync(counts, a.active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+      rc = (rbws_status)cuda_fail(ce, "solve loop");
+      break;
+    }
+    const int active = counts[0], pending = counts[1];
+    if (pending > 0) {
+      // FP64 reliable update of the flagged instances
+      launch_ru_fold(a, s);
+      if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
+      reset(a, 0, s);
+      CK(cudaMemsetAsync(a.pending, 0, sizeof(int), s));
+      p->launches += 4;
+      continue;
+    }
+    if (active == 0) break;
+    if (!prof) {
+      if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) {
+        rc = (rbws_status)cuda_fail(ce, "cudaGraphLaunch");
+        break;
+      }
+    } else {
+      cudaEventRecord(p->tev[0], s);
+      phase_a(a, 0, s);
+      cudaEventRecord(p->tev[1], s);
+      phase_b(a, 0, s);
+      cudaEventRecord(p->tev[2], s);
+      for (int k = 1; k < M; k++) {
+        phase_a(a, k & 1, s);
+        phase_b(a, k & 1, s);
+      }
+      cudaMemsetAsync(a.pending, 0, sizeof(int), s);
+      launch_ru_decide(a, s);
+      if ((ce = cudaEventSynchronize(p->tev[2])) != cudaSuccess) {
+        rc = (rbws_status)cuda_fail(ce, "profile events");
+        break;
+      }
+      float ta = 0.f, tb = 0.f;
+      cudaEventElapsedTime(&ta, p->tev[0], p->tev[1]);
+      cudaEventElapsedTime(&tb, p->tev[1], p->tev[2]);
+      prof->stencil_ms += ta;
+      prof->update_ms += tb;
+      prof->active_dofs += (double)active * (double)p->n;
+      prof->samples += 1;
+    }
+    p->launches += 2 * M + 1;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != RBWS_OK) return rc;
+  // instances stopped by max_iters or breakdown still hold a correction in d
+  std::vector<InstState> h(B);
+  CK(cudaMemcpyAsync(h.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int> fin(B);
+  int nfin = 0;
+  for (int b = 0; b < B; b++) nfin += (fin[b] = (h[b].status == ST_MAX_ITERS || h[b].status == ST_BREAKDOWN));
+  if (nfin) {
+    CK(cudaMemcpyAsync(upd, fin.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+    launch_ru_fold(a, s);
+    CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
+    std::vector<double> hr(B);
+    CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; b++)
+      if (fin[b]) h[b].relres = hr[b];
+    p->launches += 3;
+  }
+  st = h;
   return RBWS_OK;
 }
 
@@ -566,7 +662,7 @@ void rbws_options_default(rbws_options* o) {
   o->precond = RBWS_PREC_JACOBI;
   o->precision = RBWS_FP64;
   o->max_restarts = 3;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-2;
   o->max_outer = 10;
   o->check_every = 0;
   o->stream = nullptr;

@@ -48,7 +48,15 @@ struct Geo {
 };
 
 // Per-instance solver state kept on the device.
-enum : int { ST_ACTIVE = -1, ST_CONVERGED = 0, ST_MAX_ITERS = 1, ST_BREAKDOWN = 2, ST_IDLE = 3 };
+enum : int {
+  ST_ACTIVE = -1,
+  ST_CONVERGED = 0,
+  ST_MAX_ITERS = 1,
+  ST_BREAKDOWN = 2,
+  ST_IDLE = 3,
+  ST_PAUSED = 4,  // FP32 recursive residual met tol: awaiting the FP64 check
+  ST_UPDATE = 5   // FP32 residual dropped by the update factor: awaiting an FP64 update
+};
 
 struct InstState {
   int status;    // ST_*
@@ -94,6 +102,15 @@ struct CGArgs {
   double* C;            // [B][N] reduced corrections
   double* proj_part;    // [B][proj_chunks][N] partial projections
   int proj_chunks;
+  // FP32 iterations with FP64 reliable updates (T = float)
+  int ru;               // 1: converged instances pause for an FP64 check
+  double ru_delta2;     // update when ||r||^2 < ru_delta2 * ||r at last update||^2
+  double* rr_ref;       // [B] FP64 ||r||^2 at the last update
+  int* pending;         // instances flagged for an update
+  int* upd;             // [B] 0 none, 1 update keeping p, 2 update restarting p
+  double* u64;          // [B][n] FP64 solution
+  double* r64;          // [B][n] FP64 residual f - A u64
+  double* rel64;        // [B] ||r64|| / ||f||
 };
 
 // ---------------------------------------------------------------------------
@@ -116,9 +133,19 @@ void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_
                   cudaStream_t s);
 
 // r = f - A u (FP64) per instance; rr partials [B][P] and the residual
-// written to r (if non-null); also used for the outer residual of FP32_IR.
+// written to r (if non-null); instances with mask[b] == 0 are skipped.
 void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
-                       const double* u, double* r, double* rr_part, int P, cudaStream_t s);
+                       const double* u, double* r, double* rr_part, int P, const int* mask,
+                       cudaStream_t s);
+// FP32 phase kernels with 4 nodes per thread (stencil_v4.cu; nx % 4 == 0).
+// Tile: t.tx threads x 4 nodes in x, t.ty rows.
+void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
+void launch_cg_b_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
+void launch_ru_reset_v4(const CGArgs<float>& a, Tile t, int start, cudaStream_t s);
+// Reliable-update kernels of the FP32 path (see stencil.cu).
+void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s);
+void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s);
+void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s);
 
 template <typename T>
 void launch_cg_init(const CGArgs<T>& a, Tile t, int parity, int only_status, cudaStream_t s);

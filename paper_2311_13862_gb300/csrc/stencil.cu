@@ -19,6 +19,8 @@
 // sees bit-identical scalars.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace rbws {
@@ -235,11 +237,13 @@ __global__ void k_apply(Geo g, int tiles_x, int zc, const T* __restrict__ coef, 
 // r = f - A u in FP64 with partial sums of r.r per CTA.
 __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restrict__ coef,
                              const double* __restrict__ f, const double* __restrict__ u,
-                             double* __restrict__ r, double* __restrict__ rr_part, int P) {
+                             double* __restrict__ r, double* __restrict__ rr_part, int P,
+                             const int* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   double* sm = reinterpret_cast<double*>(smem_raw);
   const int b = blockIdx.z;
+  if (mask && !mask[b]) return;
   const TilePos tp = tile_pos(g, tiles_x, zc);
   const double* ub = u + (int64_t)b * g.n;
   double* rb = r ? r + (int64_t)b * g.n : nullptr;
@@ -394,7 +398,7 @@ __global__ void k_cg_a(CGArgs<T> a, int parity) {
         const double rel = sqrt(cur.y) / a.fnorm[b];
         if (rel < a.tol) {
           if (leader) {
-            st->status = ST_CONVERGED;
+            st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
             st->relres = rel;
             atomicSub(a.active, 1);
           }
@@ -640,6 +644,117 @@ __global__ void k_msrb_lift(CGArgs<double> a, int slot) {
   if (tid == 0) a.rho_rr[((int64_t)slot * a.B + b) * a.P + tp.part].x = rho;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 PCG with FP64 reliable updates.  At the end of every block of
+// iterations (parity 0 again), k_ru_decide flags the instances that need an
+// FP64 update: ACTIVE ones whose FP32 residual fell below sqrt(ru_delta2)
+// times the residual at their last update (the search direction is kept),
+// and PAUSED ones (FP32 residual met tol; the direction restarts if the FP64
+// check fails).  An update folds the FP32 correction d into u64, forms the
+// FP64 residual, and resets the FP32 residual from it.
+// ---------------------------------------------------------------------------
+__global__ void k_ru_decide(CGArgs<float> a) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= a.B) return;
+  InstState& s = a.st[b];
+  const int status = s.status;
+  double rr = 0.0;
+  if (status == ST_ACTIVE) rr = sum_partials2(a.rho_rr + (int64_t)b * a.P, a.P, lane).y;  // slot 0
+  if (lane != 0) return;
+  int u = 0;
+  if (status == ST_ACTIVE && rr < a.ru_delta2 * a.rr_ref[b]) {
+    u = 1;
+    s.status = ST_UPDATE;
+    atomicSub(a.active, 1);
+  } else if (status == ST_PAUSED) {
+    u = 2;
+  }
+  a.upd[b] = u;
+  if (u) atomicAdd(a.pending, 1);
+}
+
+// u64 += d; d = 0 for flagged instances.
+__global__ void k_ru_fold(CGArgs<float> a) {
+  const int b = blockIdx.y;
+  if (!a.upd[b]) return;
+  const int64_t off = (int64_t)b * a.g.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.g.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a.u64[off + i] += (double)a.u[off + i];
+    a.u[off + i] = 0.f;
+  }
+}
+
+// After the FP64 residual of the flagged instances: new status from rel64,
+// r = (float) r64, s = D^{-1} r, partials of rho and ||r||^2 into slot 0.  With
+// upd == 2 (or at the start) the search direction restarts: p_old = 0 and a
+// dummy rho in slot 1.
+__global__ void k_ru_reset(CGArgs<float> a, int start) {
+  __shared__ double red[64];
+  const int b = blockIdx.z;
+  const int mode = a.upd[b];
+  if (!mode) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const bool leader = tp.part == 0;
+  InstState* st = a.st + b;
+  const double rel = a.rel64[b];
+  const int iters = start ? 0 : st->iters;
+  int ns;
+  if (rel < a.tol) ns = ST_CONVERGED;
+  else if (!(rel == rel)) ns = ST_BREAKDOWN;
+  else if (iters >= a.max_iters) ns = ST_MAX_ITERS;
+  else ns = ST_ACTIVE;
+  __syncthreads();  // every thread has read the old state before the leader writes
+  if (leader && tid == 0) {
+    if (start) {
+      st->iters = 0;
+      st->restarts = 0;
+      st->relres0 = rel;
+    }
+    st->status = ns;
+    st->relres = rel;
+    a.rr_ref[b] = (rel * a.fnorm[b]) * (rel * a.fnorm[b]);
+    if (ns == ST_ACTIVE) atomicAdd(a.active, 1);
+    if (ns == ST_ACTIVE && mode == 2 && !start) st->restarts += 1;
+  }
+  if (ns != ST_ACTIVE) return;
+  const bool restart = start || mode == 2;
+  const int64_t off = (int64_t)b * a.g.n;
+  const float* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const Column cl = make_column(a.g, tp.x0, tp.y0);
+  const int64_t plane = (int64_t)a.g.nx * a.g.ny;
+  float rho = 0.f, rr = 0.f;
+  if (cl.own) {
+    int zcls_cur = -1;
+    float dinv = 1.f;
+    for (int z = tp.z0; z < tp.z1; ++z) {
+      const int zcl = a.g.cz[z];
+      if (zcl != zcls_cur) {
+        zcls_cur = zcl;
+        dinv = cb[((int64_t)zcl * a.g.ncy * a.g.ncx + cl.xy) * kCoefStride + 7];
+      }
+      const int64_t idx = off + (int64_t)z * plane + cl.col;
+      const float rv = (float)a.r64[idx];
+      const float sv = jac ? dinv * rv : rv;
+      a.r[idx] = rv;
+      if (jac) a.s[idx] = sv;
+      if (restart) a.p0[idx] = 0.f;
+      rho = fmaf(rv, sv, rho);
+      rr = fmaf(rv, rv, rr);
+    }
+  }
+  double drho = (double)rho, drr = (double)rr;
+  block_sum2(drho, drr, red);
+  if (tid == 0) {
+    a.rho_rr[(int64_t)b * a.P + tp.part] = make_double2(drho, drr);
+    if (restart)
+      a.rho_rr[((int64_t)a.B + b) * a.P + tp.part] = make_double2(tp.part == 0 ? 1.0 : 0.0, 0.0);
+  }
+}
+
 inline size_t plane_smem(Tile t, size_t elem) { return 3 * (size_t)(t.tx + 2) * (t.ty + 2) * elem; }
 
 template <typename T>
@@ -676,13 +791,14 @@ void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_
 }
 
 void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
-                       const double* u, double* r, double* rr_part, int P, cudaStream_t s) {
+                       const double* u, double* r, double* rr_part, int P, const int* mask,
+                       cudaStream_t s) {
   const int tiles_x = (g.nx + t.tx - 1) / t.tx, tiles_y = (g.ny + t.ty - 1) / t.ty;
   const int nzc = (g.nz + zc - 1) / zc;
   (void)P;
   dim3 grid(tiles_x * tiles_y, nzc, B), block(t.tx, t.ty);
   k_residual64<<<grid, block, plane_smem(t, sizeof(double)), s>>>(g, tiles_x, zc, coef, f, u, r,
-                                                                  rr_part, tiles_x * tiles_y * nzc);
+                                                                  rr_part, tiles_x * tiles_y * nzc, mask);
 }
 
 template <typename T>
@@ -702,6 +818,18 @@ template <typename T>
 void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restarts, cudaStream_t s) {
   const int warps = 4;
   k_cg_finalize<T><<<(a.B + warps - 1) / warps, 32 * warps, 0, s>>>(a, parity, mode, max_restarts);
+}
+
+void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s) {
+  k_ru_decide<<<(a.B + 3) / 4, 128, 0, s>>>(a);
+}
+void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((a.g.n + threads - 1) / threads, 152 * 4);
+  k_ru_fold<<<dim3((unsigned)blocks, a.B), threads, 0, s>>>(a);
+}
+void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s) {
+  k_ru_reset<<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, start);
 }
 
 void launch_msrb_apply(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s) {

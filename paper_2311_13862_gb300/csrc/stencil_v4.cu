@@ -1,0 +1,468 @@
+// stencil_v4.cu -- FP32 PCG phase kernels with 4 nodes per thread.
+//
+// The FP32 inner iterations are HBM-bound, and the one-node-per-thread
+// kernels of stencil.cu leave too few bytes in flight on GB300 (a load is
+// issued right before each plane's barrier and waited on at once).  Here a
+// thread owns 4 consecutive x nodes (16-byte loads and stores; requires
+// nx % 4 == 0), and the stencil phase prefetches the next plane's loads into
+// registers before the barrier of the current plane, so a plane's memory
+// latency overlaps the previous plane's arithmetic.
+//
+// Tiles: TXT threads x 4 nodes in x (TXT in {4, 8, 16, 32}), TY rows, 256
+// threads or fewer; each CTA marches a chunk of zc planes.  The partial-sum
+// decomposition (one partial per CTA) is shared by all kernels of a solve
+// that use these tiles: k_cg_a_v4, k_cg_b_v4, k_ru_reset_v4.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rbws {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum_down(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  a = warp_sum_down(a);
+  b = warp_sum_down(b);
+  __syncthreads();
+  if (lane == 0) {
+    red[warp] = a;
+    red[32 + warp] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double x = lane < nw ? red[lane] : 0.0;
+    double y = lane < nw ? red[32 + lane] : 0.0;
+    a = warp_sum_down(x);
+    b = warp_sum_down(y);
+  }
+}
+
+__device__ __forceinline__ double2 sum_partials2(const double2* part, int P, int lane) {
+  double x = 0.0, y = 0.0;
+  for (int c = lane; c < P; c += 32) {
+    double2 v = part[c];
+    x += v.x;
+    y += v.y;
+  }
+  return make_double2(warp_sum_down(x), warp_sum_down(y));
+}
+__device__ __forceinline__ double sum_partials(const double* part, int P, int lane) {
+  double s = 0.0;
+  for (int c = lane; c < P; c += 32) s += part[c];
+  return warp_sum_down(s);
+}
+
+struct Pos4 {
+  int x0, y0, z0, z1, part;  // tile origin (nodes), z range, partial index
+  int i, j;                  // first node of this thread
+  bool own;
+};
+
+__device__ __forceinline__ Pos4 pos4(const Geo& g, int tiles_x, int zc) {
+  Pos4 p;
+  const int tile = blockIdx.x;
+  p.x0 = (tile % tiles_x) * (blockDim.x * 4);
+  p.y0 = (tile / tiles_x) * blockDim.y;
+  p.z0 = blockIdx.y * zc;
+  p.z1 = min(g.nz, p.z0 + zc);
+  p.part = blockIdx.y * gridDim.x + blockIdx.x;
+  p.i = p.x0 + 4 * (int)threadIdx.x;
+  p.j = p.y0 + (int)threadIdx.y;
+  p.own = p.i < g.nx && p.j < g.ny;  // nx % 4 == 0: all 4 nodes in range together
+  return p;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float f4(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// Coefficient rows of the thread's 4 nodes for z class zcl.
+__device__ __forceinline__ void load_coef4(const Geo& g, const float* cb, int zcl, int i, int j, float c[4][8]) {
+  const int yc = (int)g.cy[j];
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+    const float4 a = ld4(row), b = ld4(row + 4);
+    c[e][0] = a.x; c[e][1] = a.y; c[e][2] = a.z; c[e][3] = a.w;
+    c[e][4] = b.x; c[e][5] = b.y; c[e][6] = b.z; c[e][7] = b.w;
+  }
+}
+
+// Shared-memory plane: rows -1..TY, row pitch PW floats; node x (tile-local,
+// -1..TXN) lives at column 4 + x, so the 4-node groups are 16-byte aligned.
+struct Plane {
+  int PW, PS;
+  __device__ __forceinline__ int at(int x, int y) const { return (y + 1) * PW + 4 + x; }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Phase A: beta = rho_k / rho_{k-1}; p = s + beta p_old (halo recomputed);
+// q = A p; partial p.q.  Same scalars and stopping logic as k_cg_a.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cg_a_v4(CGArgs<float> a, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  __shared__ double s_beta;
+  __shared__ int s_run;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const bool leader = ps.part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double2 cur = make_double2(0.0, 0.0);
+    double prev = 0.0;
+    if (status == ST_ACTIVE) {
+      cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      prev = sum_partials2(a.rho_rr + ((int64_t)(parity ^ 1) * a.B + b) * a.P, a.P, tid).x;
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double rel = sqrt(cur.y) / a.fnorm[b];
+        if (rel < a.tol) {
+          if (leader) {
+            st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
+            st->relres = rel;
+            atomicSub(a.active, 1);
+          }
+        } else if (st->iters >= a.max_iters || !(rel == rel)) {
+          if (leader) {
+            st->status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
+            st->relres = rel;
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_beta = cur.x / prev;
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const float beta = (float)s_beta;
+  const Geo& g = a.g;
+  const int64_t off = (int64_t)b * g.n;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const float* sb = (a.precond != RBWS_PREC_NONE ? a.s : a.r) + off;
+  const float* pold = (parity ? a.p1 : a.p0) + off;
+  float* pnew = (parity ? a.p0 : a.p1) + off;
+  float* qb = a.q + off;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  Plane pl{TXN + 8, 0};
+  pl.PS = pl.PW * (TY + 2);
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
+  // Halo assignment: y-halo rows by 4-node groups (2*blockDim.x threads),
+  // then x-halo columns by single nodes (2*TY threads).
+  const int nyh = 2 * blockDim.x;
+  int hx = 0, hy = 0, hkind = 0;  // 0 none, 1 y-row group (4 nodes), 2 x-column node
+  if (tid < nyh) {
+    hkind = 1;
+    hx = 4 * (tid % blockDim.x);
+    hy = tid < (int)blockDim.x ? -1 : TY;
+  } else if (tid < nyh + 2 * TY) {
+    hkind = 2;
+    const int t = tid - nyh;
+    hx = t < TY ? -1 : TXN;
+    hy = t < TY ? t : t - TY;
+  }
+  const int gi = ps.x0 + hx, gj = ps.y0 + hy;
+  const bool hin = hkind != 0 && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+  const int64_t hcol = (int64_t)gj * g.nx + gi;
+  const int hslot = pl.at(hx, hy), oslot = pl.at(lx, ly);
+
+  // register prefetch of (s, p_old) for the own group and the halo element(s)
+  float4 s_own, p_own, s_h, p_h;
+  auto fetch = [&](int z) {
+    const bool zin = z >= 0 && z < g.nz;
+    s_own = p_own = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_h = p_h = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zin && ps.own) {
+      s_own = ld4(sb + z * plane + col);
+      p_own = ld4(pold + z * plane + col);
+    }
+    if (zin && hin) {
+      if (hkind == 1) {
+        s_h = ld4(sb + z * plane + hcol);
+        p_h = ld4(pold + z * plane + hcol);
+      } else {
+        s_h.x = sb[z * plane + hcol];
+        p_h.x = pold[z * plane + hcol];
+      }
+    }
+  };
+  // p_new of the fetched plane into a smem slot; returns the own group
+  auto commit = [&](float* P) -> float4 {
+    const float4 v = fma4(beta, p_own, s_own);
+    st4(P + oslot, v);
+    if (hkind == 1) st4(P + hslot, fma4(beta, p_h, s_h));
+    else if (hkind == 2) P[hslot] = fmaf(beta, p_h.x, s_h.x);
+    return v;
+  };
+
+  float c[4][8];
+  int zcls_cur = -1;
+  const int z0 = ps.z0, z1 = ps.z1;
+  float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (z0 > 0 && ps.own) xm = fma4(beta, ld4(pold + (z0 - 1) * plane + col), ld4(sb + (z0 - 1) * plane + col));
+  fetch(z0);
+  float4 xc = commit(sm + (z0 % 3) * pl.PS);
+  fetch(z0 + 1);
+  float gam = 0.f;
+  for (int z = z0; z < z1; ++z) {
+    const float4 xp = commit(sm + ((z + 1) % 3) * pl.PS);  // plane z+1 (zeros past nz)
+    fetch(z + 2);                                          // in flight during plane z
+    __syncthreads();
+    const float* P = sm + (z % 3) * pl.PS;
+    const int zcl = g.cz[z];
+    if (zcl != zcls_cur && ps.own) {
+      zcls_cur = zcl;
+      load_coef4(g, cb, zcl, ps.i, ps.j, c);
+    }
+    if (ps.own) {
+      const float left = P[oslot - 1], right = P[oslot + 4];
+      const float4 sth = ld4(P + oslot - pl.PW), nth = ld4(P + oslot + pl.PW);
+      float y[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const float xce = f4(xc, e);
+        const float xw = e == 0 ? left : f4(xc, e - 1);
+        const float xe = e == 3 ? right : f4(xc, e + 1);
+        float v = c[e][6] * xce;
+        v = fmaf(c[e][0], xw, v);
+        v = fmaf(c[e][1], xe, v);
+        v = fmaf(c[e][2], f4(sth, e), v);
+        v = fmaf(c[e][3], f4(nth, e), v);
+        v = fmaf(c[e][4], f4(xm, e), v);
+        v = fmaf(c[e][5], f4(xp, e), v);
+        y[e] = v;
+        gam = fmaf(xce, v, gam);
+      }
+      st4(pnew + z * plane + col, xc);
+      st4(qb + z * plane + col, make_float4(y[0], y[1], y[2], y[3]));
+    }
+    xm = xc;
+    xc = xp;
+  }
+  double dg = (double)gam, dummy = 0.0;
+  block_sum2(dg, dummy, red);
+  if (tid == 0) a.gam[(int64_t)b * a.P + ps.part] = dg;
+}
+
+// ---------------------------------------------------------------------------
+// Phase B: alpha = rho / gamma; u += alpha p; r -= alpha q; s = D^{-1} r;
+// partials of rho = r.s and r.r.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cg_b_v4(CGArgs<float> a, int parity) {
+  __shared__ double red[64];
+  __shared__ double s_alpha;
+  __shared__ int s_run;
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const bool leader = ps.part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double rho = 0.0, gam = 0.0, rr = 0.0;
+    if (status == ST_ACTIVE) {
+      const double2 cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      rho = cur.x;
+      rr = cur.y;
+      gam = sum_partials(a.gam + (int64_t)b * a.P, a.P, tid);
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double alpha = rho / gam;
+        if (!(gam > 0.0) || !(alpha == alpha) || alpha == INFINITY) {
+          if (leader) {
+            st->status = ST_BREAKDOWN;
+            st->relres = sqrt(rr) / a.fnorm[b];
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_alpha = alpha;
+          if (leader) st->iters += 1;
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const float alpha = (float)s_alpha;
+  const Geo& g = a.g;
+  const int64_t off = (int64_t)b * g.n;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const float* pn = (parity ? a.p0 : a.p1) + off;
+  const float* qb = a.q + off;
+  float* ub = a.u + off;
+  float* rb = a.r + off;
+  float* sb = a.s + off;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  float rho = 0.f, rr = 0.f;
+  if (ps.own) {
+    int zcls_cur = -1;
+    float dinv[4] = {1.f, 1.f, 1.f, 1.f};
+    const int yc = (int)g.cy[ps.j];
+    // two planes per step: all eight loads are issued before any use
+    for (int z = ps.z0; z < ps.z1; z += 2) {
+      const bool two = z + 1 < ps.z1;
+      const int64_t i0 = z * plane + col, i1 = i0 + plane;
+      const float4 p0v = ld4(pn + i0), q0v = ld4(qb + i0), u0v = ld4(ub + i0), r0v = ld4(rb + i0);
+      float4 p1v = p0v, q1v = q0v, u1v = u0v, r1v = r0v;
+      if (two) {
+        p1v = ld4(pn + i1);
+        q1v = ld4(qb + i1);
+        u1v = ld4(ub + i1);
+        r1v = ld4(rb + i1);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (h == 1 && !two) break;
+        const int zz = z + h;
+        const int zcl = g.cz[zz];
+        if (zcl != zcls_cur) {
+          zcls_cur = zcl;
+#pragma unroll
+          for (int e = 0; e < 4; e++)
+            dinv[e] = cb[(((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[ps.i + e]) * kCoefStride + 7];
+        }
+        const float4 pv = h ? p1v : p0v, qv = h ? q1v : q0v, uv = h ? u1v : u0v, rv0 = h ? r1v : r0v;
+        const float4 uo = fma4(alpha, pv, uv);
+        const float4 ro = fma4(-alpha, qv, rv0);
+        float4 so = ro;
+        if (jac) so = make_float4(dinv[0] * ro.x, dinv[1] * ro.y, dinv[2] * ro.z, dinv[3] * ro.w);
+        const int64_t ii = h ? i1 : i0;
+        st4(ub + ii, uo);
+        st4(rb + ii, ro);
+        if (jac) st4(sb + ii, so);
+        rho = fmaf(ro.x, so.x, rho);
+        rho = fmaf(ro.y, so.y, rho);
+        rho = fmaf(ro.z, so.z, rho);
+        rho = fmaf(ro.w, so.w, rho);
+        rr = fmaf(ro.x, ro.x, rr);
+        rr = fmaf(ro.y, ro.y, rr);
+        rr = fmaf(ro.z, ro.z, rr);
+        rr = fmaf(ro.w, ro.w, rr);
+      }
+    }
+  }
+  double drho = (double)rho, drr = (double)rr;
+  block_sum2(drho, drr, red);
+  if (tid == 0) a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + ps.part] = make_double2(drho, drr);
+}
+
+// Reliable-update reset with the v4 tiles (see k_ru_reset in stencil.cu).
+__global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start) {
+  __shared__ double red[64];
+  const int b = blockIdx.z;
+  const int mode = a.upd[b];
+  if (!mode) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const bool leader = ps.part == 0;
+  InstState* st = a.st + b;
+  const double rel = a.rel64[b];
+  const int iters = start ? 0 : st->iters;
+  int ns;
+  if (rel < a.tol) ns = ST_CONVERGED;
+  else if (!(rel == rel)) ns = ST_BREAKDOWN;
+  else if (iters >= a.max_iters) ns = ST_MAX_ITERS;
+  else ns = ST_ACTIVE;
+  __syncthreads();
+  if (leader && tid == 0) {
+    if (start) {
+      st->iters = 0;
+      st->restarts = 0;
+      st->relres0 = rel;
+    }
+    st->status = ns;
+    st->relres = rel;
+    a.rr_ref[b] = (rel * a.fnorm[b]) * (rel * a.fnorm[b]);
+    if (ns == ST_ACTIVE) atomicAdd(a.active, 1);
+    if (ns == ST_ACTIVE && mode == 2 && !start) st->restarts += 1;
+  }
+  if (ns != ST_ACTIVE) return;
+  const bool restart = start || mode == 2;
+  const Geo& g = a.g;
+  const int64_t off = (int64_t)b * g.n;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  float rho = 0.f, rr = 0.f;
+  if (ps.own) {
+    int zcls_cur = -1;
+    float dinv[4] = {1.f, 1.f, 1.f, 1.f};
+    const int yc = (int)g.cy[ps.j];
+    for (int z = ps.z0; z < ps.z1; ++z) {
+      const int zcl = g.cz[z];
+      if (zcl != zcls_cur) {
+        zcls_cur = zcl;
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+          dinv[e] = cb[(((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[ps.i + e]) * kCoefStride + 7];
+      }
+      const int64_t idx = off + z * plane + col;
+      const double2 ra = *reinterpret_cast<const double2*>(a.r64 + idx);
+      const double2 rb2 = *reinterpret_cast<const double2*>(a.r64 + idx + 2);
+      const float4 rv = make_float4((float)ra.x, (float)ra.y, (float)rb2.x, (float)rb2.y);
+      float4 sv = rv;
+      if (jac) sv = make_float4(dinv[0] * rv.x, dinv[1] * rv.y, dinv[2] * rv.z, dinv[3] * rv.w);
+      st4(a.r + idx, rv);
+      if (jac) st4(a.s + idx, sv);
+      if (restart) st4(a.p0 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
+      rho = fmaf(rv.x, sv.x, fmaf(rv.y, sv.y, fmaf(rv.z, sv.z, fmaf(rv.w, sv.w, rho))));
+      rr = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, rr))));
+    }
+  }
+  double drho = (double)rho, drr = (double)rr;
+  block_sum2(drho, drr, red);
+  if (tid == 0) {
+    a.rho_rr[(int64_t)b * a.P + ps.part] = make_double2(drho, drr);
+    if (restart)
+      a.rho_rr[((int64_t)a.B + b) * a.P + ps.part] = make_double2(ps.part == 0 ? 1.0 : 0.0, 0.0);
+  }
+}
+
+size_t v4_plane_smem(Tile t) { return sizeof(float) * 3 * (size_t)(4 * t.tx + 8) * (t.ty + 2); }
+
+void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
+  k_cg_a_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), v4_plane_smem(t), s>>>(a, parity);
+}
+void launch_cg_b_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
+  k_cg_b_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), 0, s>>>(a, parity);
+}
+void launch_ru_reset_v4(const CGArgs<float>& a, Tile t, int start, cudaStream_t s) {
+  k_ru_reset_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), 0, s>>>(a, start);
+}
+
+}  // namespace rbws

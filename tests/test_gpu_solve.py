@@ -86,8 +86,11 @@ def test_warm_mode_without_basis_is_an_error():
             solve(P, np.array([[1.0, 2.0]]), 1e-10, rbws.WARM_GALERKIN)
 
 
-def test_fp32_refinement_reaches_fp64_residual():
-    grid, blocks = (40, 36, 32), (2, 2, 2)
+@pytest.mark.parametrize("grid,blocks", [((40, 36, 32), (2, 2, 2)),   # 4-node kernels, ragged tiles
+                                         ((33, 17, 20), (2, 2, 2)),   # nx % 4 != 0: 1-node kernels
+                                         ((64, 48, 40), (2, 2, 1)),   # 4-node kernels, full tiles
+                                         ((16, 16, 16), (2, 1, 1))])
+def test_fp32_refinement_reaches_fp64_residual(grid, blocks):
     op = O.assemble(grid, blocks)
     mu = inputs.log_uniform(61, 4, op.Q, 0.01, 100.0)
     ref = O.solve_batch(op, mu, warm=O.WARM_ZERO, tol=1e-13)
