@@ -187,6 +187,46 @@ RBWS_API rbws_status rbws_get_basis(rbws_problem p, double* W, double* ANq, doub
 /* Reduced Galerkin solve only: c[b] = A_N(mu[b])^{-1} f_N, host out [B][N]. */
 RBWS_API rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, double* c_out);
 
+/* ---- learned warm start (a production pattern on top of the paper) -------
+ * A fully connected network x(mu) -> p -> H -> H -> H -> N with GELU (erf
+ * form) after the hidden layers predicts the reduced coefficients c(mu) of
+ * the current basis (N = basis dimension, p = Q); the warm start is u0 = W c
+ * (Algorithm 4, line 2, with the network in place of the RB solver).  Inputs
+ * x_q = 2 (log mu_q - log mu_lo) / (log mu_hi - log mu_lo) - 1; outputs are
+ * scaled by per-coefficient RMS factors of the training targets.  Weights are
+ * BF16 tensor-core operands with FP32 accumulation and FP32 master copies.
+ * Parameter layout (float): W1[H][p] b1[H] W2[H][H] b2[H] W3[H][H] b3[H]
+ * W4[N][H] b4[N], W_l row-major [out][in]. */
+
+/* Trains the network on the GPU: targets host [n][N] (NULL = the reduced
+ * Galerkin coefficients of the n parameters, computed on the device), loss =
+ * mean squared error of the scaled coefficients, Adam (beta 0.9/0.999, eps
+ * 1e-8) with learning rate lr, minibatches of `batch` in the given order
+ * (the remainder n % batch is unused), `epochs` passes.  Parameters start
+ * from U(-1/sqrt(fan_in), 1/sqrt(fan_in)) drawn by splitmix64(seed + index).
+ * final_loss_out: mean minibatch loss of the last epoch (NaN if epochs = 0).
+ * Needs a basis; replaces any previous network. */
+RBWS_API rbws_status rbws_train_surrogate(rbws_problem p, const double* mu, int32_t n,
+                                          const double* targets, int32_t hidden, int32_t epochs,
+                                          int32_t batch, double lr, double mu_lo, double mu_hi,
+                                          uint64_t seed, double* final_loss_out);
+/* Installs network parameters (host float, layout above) and coefficient
+ * scales (host [N] or NULL = ones) for the current basis dimension N. */
+RBWS_API rbws_status rbws_surrogate_set_params(rbws_problem p, int32_t hidden, const float* params,
+                                               const float* coef_scale, double mu_lo, double mu_hi);
+/* Copies the network out (any pointer may be NULL). */
+RBWS_API rbws_status rbws_surrogate_get_params(rbws_problem p, int32_t* hidden, float* params,
+                                               float* coef_scale);
+/* Predicted coefficients c[b] (host [B][N]) for B parameters; corrected != 0
+ * adds one reduced CG step on A_N(mu) c = f_N from the prediction. */
+RBWS_API rbws_status rbws_surrogate_forward(rbws_problem p, const double* mu, int32_t B,
+                                            int32_t corrected, double* c_out);
+/* Loss and gradient of the current network on given inputs x (host [B][p],
+ * already normalised) and scaled targets t (host [B][N]); grad_out host [P]
+ * (layout above) may be NULL.  For gradient checks. */
+RBWS_API rbws_status rbws_surrogate_loss_grad(rbws_problem p, const float* x, const float* t,
+                                              int32_t B, double* loss_out, float* grad_out);
+
 /* Online batched solve: Algorithm 4 with the chosen initial value and
  * preconditioner for B parameters.  Stopping test ||r||_2/||f||_2 < tol on
  * the recursive residual, then a true-residual check with restarts.

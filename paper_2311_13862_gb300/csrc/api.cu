@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 using namespace rbws;
@@ -104,6 +106,13 @@ struct rbws_problem_s {
   double* d_ANq = nullptr;  // [Q][N][N]
   double* d_fN = nullptr;   // [N]
   std::vector<double> h_ANq, h_fN;  // packed [Q][N][N], [N]
+  // surrogate network mu -> c (learned warm start)
+  int net_H = 0, net_N = 0;
+  int64_t net_P = 0;
+  float* d_w32 = nullptr;     // FP32 master parameters [P]
+  void* d_w16 = nullptr;      // BF16 copy [P]
+  float* d_cscale = nullptr;  // [N] coefficient scales
+  double net_lo = 0.0, net_hi = 0.0;
   std::map<std::string, DevBuf> bufs;
 
   void* buf(const std::string& name, size_t bytes, int* err) {
@@ -647,6 +656,184 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   return RBWS_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Surrogate network p -> H -> H -> H -> N (GELU), parameters laid out as
+// W1[H][p] b1[H] W2[H][H] b2[H] W3[H][H] b3[H] W4[N][H] b4[N].
+// ---------------------------------------------------------------------------
+struct NetLayout {
+  int p, H, N;
+  int64_t W[4], b[4], P;
+  int in[4], out[4];
+};
+
+NetLayout net_layout(int p, int H, int N) {
+  NetLayout L;
+  L.p = p;
+  L.H = H;
+  L.N = N;
+  const int in[4] = {p, H, H, H}, out[4] = {H, H, H, N};
+  int64_t o = 0;
+  for (int l = 0; l < 4; l++) {
+    L.in[l] = in[l];
+    L.out[l] = out[l];
+    L.W[l] = o;
+    o += (int64_t)in[l] * out[l];
+    L.b[l] = o;
+    o += out[l];
+  }
+  L.P = o;
+  return L;
+}
+
+// Activations of one batch (device buffers owned by the problem).
+struct NetBufs {
+  float *x, *Z[3], *A[3], *Y, *dY, *dA, *dZ, *loss;
+};
+
+rbws_status net_bufs(rbws_problem p, const NetLayout& L, int B, NetBufs* nb) {
+  int err = 0;
+  const size_t bh = sizeof(float) * (size_t)B * L.H;
+  nb->x = (float*)p->buf("net_x", sizeof(float) * (size_t)B * L.p, &err);
+  for (int l = 0; l < 3 && !err; l++) {
+    nb->Z[l] = (float*)p->buf("net_Z" + std::to_string(l), bh, &err);
+    if (!err) nb->A[l] = (float*)p->buf("net_A" + std::to_string(l), bh, &err);
+  }
+  if (!err) nb->Y = (float*)p->buf("net_Y", sizeof(float) * (size_t)B * L.N, &err);
+  if (!err) nb->dY = (float*)p->buf("net_dY", sizeof(float) * (size_t)B * L.N, &err);
+  if (!err) nb->dA = (float*)p->buf("net_dA", bh, &err);
+  if (!err) nb->dZ = (float*)p->buf("net_dZ", bh, &err);
+  if (!err) nb->loss = (float*)p->buf("net_loss1", sizeof(float) * 4, &err);
+  return (rbws_status)err;
+}
+
+// Forward pass on inputs x [B][p] (float); output nb.Y [B][N].
+void net_forward(rbws_problem p, const NetLayout& L, int B, const float* x, const NetBufs& nb, cudaStream_t s) {
+  const char* w16 = static_cast<const char*>(p->d_w16);
+  const void* in = x;
+  int in_dim = L.p;
+  for (int l = 0; l < 4; l++) {
+    MlpGemm g{};
+    g.M = B;
+    g.N = L.out[l];
+    g.K = L.in[l];
+    g.A = in;
+    g.sam = in_dim;
+    g.sak = 1;
+    g.a_bf16 = 0;
+    g.B = w16 + 2 * L.W[l];
+    g.sbk = 1;
+    g.sbn = L.in[l];
+    g.b_bf16 = 1;
+    g.bias = p->d_w32 + L.b[l];
+    g.Z = l < 3 ? nb.Z[l] : nb.Y;
+    g.Aout = l < 3 ? nb.A[l] : nullptr;
+    g.ldz = L.out[l];
+    launch_mlp_gemm(g, s);
+    in = nb.A[l < 3 ? l : 2];
+    in_dim = L.H;
+  }
+  p->launches += 4;
+}
+
+// Backward pass from dY (nb.dY) into grad [P] (float).
+void net_backward(rbws_problem p, const NetLayout& L, int B, const float* x, const NetBufs& nb, float* grad,
+                  cudaStream_t s) {
+  const char* w16 = static_cast<const char*>(p->d_w16);
+  const float* dout = nb.dY;  // gradient w.r.t. the output of layer l
+  for (int l = 3; l >= 0; l--) {
+    const int no = L.out[l], ni = L.in[l];
+    const float* ain = l == 0 ? x : nb.A[l - 1];
+    // dW_l = dout^T a_in  ([no][ni], k over the batch)
+    MlpGemm gw{};
+    gw.M = no;
+    gw.N = ni;
+    gw.K = B;
+    gw.A = dout;
+    gw.sam = 1;
+    gw.sak = no;
+    gw.B = ain;
+    gw.sbk = ni;
+    gw.sbn = 1;
+    gw.Z = grad + L.W[l];
+    gw.ldz = ni;
+    launch_mlp_gemm(gw, s);
+    launch_bias_grad(dout, B, no, grad + L.b[l], s);
+    p->launches += 2;
+    if (l == 0) break;
+    // d a_in = dout W_l  ([B][ni]), then through GELU of layer l-1
+    MlpGemm gd{};
+    gd.M = B;
+    gd.N = ni;
+    gd.K = no;
+    gd.A = dout;
+    gd.sam = no;
+    gd.sak = 1;
+    gd.B = w16 + 2 * L.W[l];
+    gd.sbk = ni;
+    gd.sbn = 1;
+    gd.b_bf16 = 1;
+    gd.Z = nb.dA;
+    gd.ldz = ni;
+    launch_mlp_gemm(gd, s);
+    launch_gelu_back(nb.dA, nb.Z[l - 1], B * ni, nb.dZ, s);
+    p->launches += 2;
+    // every read of the previous dout (dW, db, dA) is ordered before this
+    // overwrite of dZ on the stream, so one buffer serves all layers
+    dout = nb.dZ;
+  }
+}
+
+// c[b] = W^T-coefficients predicted by the network for mu[b] (device mu).
+rbws_status net_predict(rbws_problem p, const double* d_mu, int B, double* c, bool corrected) {
+  if (!p->d_w32 || p->net_N != p->N || p->N <= 0) {
+    set_error("learned warm start needs a reduced basis and a surrogate trained for it");
+    return RBWS_ERR_NO_BASIS;
+  }
+  const NetLayout L = net_layout(p->Q, p->net_H, p->net_N);
+  NetBufs nb{};
+  CKI(net_bufs(p, L, B, &nb));
+  launch_mlp_inputs(d_mu, B, p->Q, p->net_lo, p->net_hi, nb.x, p->cur);
+  net_forward(p, L, B, nb.x, nb, p->cur);
+  launch_unscale(nb.Y, p->d_cscale, B, L.N, c, p->cur);
+  p->launches += 2;
+  if (corrected) {
+    launch_reduced_cg_step(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, c, p->cur);
+    p->launches += 1;
+  }
+  CK(cudaGetLastError());
+  return RBWS_OK;
+}
+
+rbws_status learned_start(rbws_problem p, const double* d_mu, int B, double* u, bool corrected) {
+  int err = 0;
+  double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * (p->N > 0 ? p->N : 1), &err);
+  if (err) return (rbws_status)err;
+  CKI(net_predict(p, d_mu, B, C, corrected));
+  launch_lift(p->n, p->N, p->d_W, C, B, u, p->cur);
+  p->launches += 1;
+  CK(cudaGetLastError());
+  return RBWS_OK;
+}
+
+rbws_status net_alloc(rbws_problem p, int H, int N) {
+  const NetLayout L = net_layout(p->Q, H, N);
+  cudaFree(p->d_w32);
+  cudaFree(p->d_w16);
+  cudaFree(p->d_cscale);
+  p->d_w32 = nullptr;
+  p->d_w16 = nullptr;
+  p->d_cscale = nullptr;
+  p->net_H = p->net_N = 0;
+  CK(cudaMalloc(&p->d_w32, sizeof(float) * L.P));
+  CK(cudaMalloc(&p->d_w16, 2 * L.P));
+  CK(cudaMalloc(&p->d_cscale, sizeof(float) * N));
+  p->net_H = H;
+  p->net_N = N;
+  p->net_P = L.P;
+  return RBWS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -794,6 +981,9 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_W);
   cudaFree(p->d_ANq);
   cudaFree(p->d_fN);
+  cudaFree(p->d_w32);
+  cudaFree(p->d_w16);
+  cudaFree(p->d_cscale);
   if (p->h_active) cudaFreeHost(p->h_active);
   if (p->ev) cudaEventDestroy(p->ev);
   for (auto& e : p->tev)
@@ -1066,6 +1256,209 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   return RBWS_OK;
 }
 
+rbws_status rbws_surrogate_set_params(rbws_problem p, int32_t hidden, const float* params,
+                                      const float* coef_scale, double mu_lo, double mu_hi) {
+  if (!p || !params || hidden < 1 || hidden > 4096 || !(mu_lo > 0.0) || !(mu_hi > mu_lo)) {
+    set_error("rbws_surrogate_set_params: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->N <= 0) {
+    set_error("rbws_surrogate_set_params: the network predicts reduced coefficients; set a basis first");
+    return RBWS_ERR_NO_BASIS;
+  }
+  StreamGuard sg(p, nullptr);
+  cudaDeviceSynchronize();
+  CKI(net_alloc(p, hidden, p->N));
+  CK(cudaMemcpy(p->d_w32, params, sizeof(float) * p->net_P, cudaMemcpyHostToDevice));
+  std::vector<float> one(p->N, 1.0f);
+  CK(cudaMemcpy(p->d_cscale, coef_scale ? coef_scale : one.data(), sizeof(float) * p->N,
+                cudaMemcpyHostToDevice));
+  launch_to_bf16(p->d_w32, p->d_w16, p->net_P, p->cur);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->cur));
+  p->net_lo = mu_lo;
+  p->net_hi = mu_hi;
+  return RBWS_OK;
+}
+
+rbws_status rbws_surrogate_get_params(rbws_problem p, int32_t* hidden, float* params, float* coef_scale) {
+  if (!p) {
+    set_error("rbws_surrogate_get_params: null problem");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (!p->d_w32) {
+    set_error("rbws_surrogate_get_params: no surrogate");
+    return RBWS_ERR_NO_BASIS;
+  }
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  if (hidden) *hidden = p->net_H;
+  if (params) CK(cudaMemcpy(params, p->d_w32, sizeof(float) * p->net_P, cudaMemcpyDeviceToHost));
+  if (coef_scale) CK(cudaMemcpy(coef_scale, p->d_cscale, sizeof(float) * p->net_N, cudaMemcpyDeviceToHost));
+  return RBWS_OK;
+}
+
+rbws_status rbws_surrogate_forward(rbws_problem p, const double* mu, int32_t B, int32_t corrected,
+                                   double* c_out) {
+  if (!p || !mu || !c_out || B < 1) {
+    set_error("rbws_surrogate_forward: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_net"));
+  int err = 0;
+  double* C = (double*)p->buf("net_C", sizeof(double) * (size_t)B * (p->N > 0 ? p->N : 1), &err);
+  if (err) return (rbws_status)err;
+  CKI(net_predict(p, d_mu, B, C, corrected != 0));
+  CK(cudaMemcpyAsync(c_out, C, sizeof(double) * (size_t)B * p->N, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+rbws_status rbws_surrogate_loss_grad(rbws_problem p, const float* x, const float* t, int32_t B,
+                                     double* loss_out, float* grad_out) {
+  if (!p || !x || !t || B < 1) {
+    set_error("rbws_surrogate_loss_grad: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (!p->d_w32) {
+    set_error("rbws_surrogate_loss_grad: no surrogate");
+    return RBWS_ERR_NO_BASIS;
+  }
+  StreamGuard sg(p, nullptr);
+  const NetLayout L = net_layout(p->Q, p->net_H, p->net_N);
+  NetBufs nb{};
+  CKI(net_bufs(p, L, B, &nb));
+  int err = 0;
+  float* tt = (float*)p->buf("net_t", sizeof(float) * (size_t)B * L.N, &err);
+  float* g = err ? nullptr : (float*)p->buf("net_grad", sizeof(float) * L.P, &err);
+  if (err) return (rbws_status)err;
+  cudaStream_t s = p->cur;
+  CK(cudaMemcpyAsync(nb.x, x, sizeof(float) * (size_t)B * L.p, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(tt, t, sizeof(float) * (size_t)B * L.N, cudaMemcpyHostToDevice, s));
+  net_forward(p, L, B, nb.x, nb, s);
+  launch_mlp_loss(nb.Y, tt, B * L.N, 1.0f / (float)(B * L.N), nb.dY, nb.loss, s);
+  net_backward(p, L, B, nb.x, nb, g, s);
+  CK(cudaGetLastError());
+  float lh = 0.f;
+  CK(cudaMemcpyAsync(&lh, nb.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (grad_out) CK(cudaMemcpyAsync(grad_out, g, sizeof(float) * L.P, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (loss_out) *loss_out = lh;
+  return RBWS_OK;
+}
+
+rbws_status rbws_train_surrogate(rbws_problem p, const double* mu, int32_t n, const double* targets,
+                                 int32_t hidden, int32_t epochs, int32_t batch, double lr, double mu_lo,
+                                 double mu_hi, uint64_t seed, double* final_loss_out) {
+  if (!p || !mu || n < 1 || hidden < 1 || hidden > 4096 || epochs < 0 || batch < 1 || batch > n ||
+      !(lr > 0.0) || !(mu_lo > 0.0) || !(mu_hi > mu_lo)) {
+    set_error("rbws_train_surrogate: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->N <= 0) {
+    set_error("rbws_train_surrogate: the targets are reduced coefficients; build or set a basis first");
+    return RBWS_ERR_NO_BASIS;
+  }
+  StreamGuard sg(p, nullptr);
+  cudaStream_t s = p->cur;
+  cudaStreamSynchronize(s);
+  CKI(net_alloc(p, hidden, p->N));
+  p->net_lo = mu_lo;
+  p->net_hi = mu_hi;
+  const NetLayout L = net_layout(p->Q, hidden, p->N);
+  const int N = p->N;
+  int err = 0;
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, n, &d_mu, "mu_train_net"));
+  double* C = (double*)p->buf("net_Cdata", sizeof(double) * (size_t)n * N, &err);
+  float* X = err ? nullptr : (float*)p->buf("net_Xdata", sizeof(float) * (size_t)n * L.p, &err);
+  float* T = err ? nullptr : (float*)p->buf("net_Tdata", sizeof(float) * (size_t)n * N, &err);
+  float* g = err ? nullptr : (float*)p->buf("net_grad", sizeof(float) * L.P, &err);
+  float* m1 = err ? nullptr : (float*)p->buf("net_m1", sizeof(float) * L.P, &err);
+  float* m2 = err ? nullptr : (float*)p->buf("net_m2", sizeof(float) * L.P, &err);
+  int* step = err ? nullptr : (int*)p->buf("net_step", sizeof(int), &err);
+  int64_t* seg_end = err ? nullptr : (int64_t*)p->buf("net_seg_end", sizeof(int64_t) * 8, &err);
+  float* seg_bound = err ? nullptr : (float*)p->buf("net_seg_bound", sizeof(float) * 8, &err);
+  int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)n, &err);
+  if (err) return (rbws_status)err;
+  // targets: reduced Galerkin coefficients of the method itself, or the caller's
+  if (targets) {
+    CK(cudaMemcpyAsync(C, targets, sizeof(double) * (size_t)n * N, cudaMemcpyHostToDevice, s));
+  } else {
+    launch_reduced_solve(N, p->Q, p->d_ANq, p->d_fN, d_mu, n, C, info, nullptr, s);
+    p->launches += 1;
+  }
+  launch_rms_scale(C, n, N, p->d_cscale, s);
+  launch_scale_targets(C, p->d_cscale, n, N, T, s);
+  launch_mlp_inputs(d_mu, n, L.p, mu_lo, mu_hi, X, s);
+  // initial parameters: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) per layer (weights and biases)
+  {
+    int64_t ends[8];
+    float bounds[8];
+    for (int l = 0; l < 4; l++) {
+      ends[2 * l] = L.b[l];
+      ends[2 * l + 1] = l < 3 ? L.W[l + 1] : L.P;
+      bounds[2 * l] = bounds[2 * l + 1] = (float)(1.0 / std::sqrt((double)L.in[l]));
+    }
+    CK(cudaMemcpyAsync(seg_end, ends, sizeof(ends), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(seg_bound, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    launch_init_params(p->d_w32, p->d_w16, L.P, seg_end, seg_bound, 8, seed, s);
+  }
+  CK(cudaMemsetAsync(m1, 0, sizeof(float) * L.P, s));
+  CK(cudaMemsetAsync(m2, 0, sizeof(float) * L.P, s));
+  CK(cudaMemsetAsync(step, 0, sizeof(int), s));
+  p->launches += 4;
+  CK(cudaGetLastError());
+  const int steps = n / batch;  // minibatches in a fixed order; the remainder is not used
+  NetBufs nb{};
+  CKI(net_bufs(p, L, batch, &nb));
+  float* losses = (float*)p->buf("net_losses", sizeof(float) * (size_t)steps, &err);
+  if (err) return (rbws_status)err;
+  double final_loss = NAN;
+  if (epochs > 0) {
+    // one epoch as a CUDA graph: forward, loss, backward, Adam for each minibatch
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t before = p->launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < steps; k++) {
+      const float* xb = X + (int64_t)k * batch * L.p;
+      const float* tb = T + (int64_t)k * batch * N;
+      net_forward(p, L, batch, xb, nb, s);
+      launch_mlp_loss(nb.Y, tb, batch * N, 1.0f / (float)(batch * N), nb.dY, losses + k, s);
+      net_backward(p, L, batch, xb, nb, g, s);
+      launch_adam(p->d_w32, p->d_w16, g, m1, m2, L.P, (float)lr, step, s);
+    }
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "capture of a training epoch");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    const int64_t per_epoch = p->launches - before + 3 * steps;  // + loss, adam (2) per step
+    p->launches = before;
+    for (int e = 0; e < epochs && ce == cudaSuccess; e++) {
+      ce = cudaGraphLaunch(exec, s);
+      p->launches += per_epoch;
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "training");
+    std::vector<float> hl(steps);
+    CK(cudaMemcpy(hl.data(), losses, sizeof(float) * steps, cudaMemcpyDeviceToHost));
+    double acc = 0.0;
+    for (float v : hl) acc += v;
+    final_loss = acc / steps;
+  }
+  if (final_loss_out) *final_loss_out = final_loss;
+  return RBWS_OK;
+}
+
 rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double tol, int32_t warm,
                              const rbws_options* opt, void* u_out, int32_t* iters_out,
                              double* relres_out, int32_t* status_out) {
@@ -1085,9 +1478,9 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
     set_error("rbws_solve_batch: the MSRB preconditioner runs in FP64 only");
     return RBWS_ERR_UNSUPPORTED;
   }
-  if (warm != RBWS_WARM_ZERO && warm != RBWS_WARM_GALERKIN) {
-    set_error("rbws_solve_batch: this warm-start mode is not available yet");
-    return RBWS_ERR_UNSUPPORTED;
+  if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_LEARNED_CORRECTED) {
+    set_error("rbws_solve_batch: unknown warm-start mode");
+    return RBWS_ERR_INVALID_ARG;
   }
   if (o.precision != RBWS_FP64 && o.precision != RBWS_FP32_IR) {
     set_error("rbws_solve_batch: unknown precision");
@@ -1100,8 +1493,10 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
   double* u = (double*)u_out;
   if (warm == RBWS_WARM_ZERO) {
     CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->cur));
-  } else {
+  } else if (warm == RBWS_WARM_GALERKIN) {
     CKI(galerkin_start(p, d_mu, B, u));
+  } else {
+    CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED));
   }
   std::vector<InstState> st;
   if (o.precision == RBWS_FP64) {

@@ -91,15 +91,17 @@ __device__ __forceinline__ float f4(const float4& v, int e) {
   return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
-// Coefficient rows of the thread's 4 nodes for z class zcl.
-__device__ __forceinline__ void load_coef4(const Geo& g, const float* cb, int zcl, int i, int j, float c[4][8]) {
+// Stencil coefficients (-kW, -kE, -kS, -kN, -kD, -kU, D) of the thread's 4
+// nodes for z class zcl (1/D is not needed by the stencil phase).
+__device__ __forceinline__ void load_coef4(const Geo& g, const float* cb, int zcl, int i, int j, float c[4][7]) {
   const int yc = (int)g.cy[j];
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
-    const float4 a = ld4(row), b = ld4(row + 4);
+    const float4 a = ld4(row);
+    const float2 b = *reinterpret_cast<const float2*>(row + 4);
     c[e][0] = a.x; c[e][1] = a.y; c[e][2] = a.z; c[e][3] = a.w;
-    c[e][4] = b.x; c[e][5] = b.y; c[e][6] = b.z; c[e][7] = b.w;
+    c[e][4] = b.x; c[e][5] = b.y; c[e][6] = row[6];
   }
 }
 
@@ -116,7 +118,7 @@ struct Plane {
 // Phase A: beta = rho_k / rho_{k-1}; p = s + beta p_old (halo recomputed);
 // q = A p; partial p.q.  Same scalars and stopping logic as k_cg_a.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cg_a_v4(CGArgs<float> a, int parity) {
+__global__ void __launch_bounds__(256, 3) k_cg_a_v4(CGArgs<float> a, int parity) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   __shared__ double s_beta;
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(256) k_cg_a_v4(CGArgs<float> a, int parity) {
     return v;
   };
 
-  float c[4][8];
+  float c[4][7];
   int zcls_cur = -1;
   const int z0 = ps.z0, z1 = ps.z1;
   float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(256) k_cg_a_v4(CGArgs<float> a, int parity) {
 // Phase B: alpha = rho / gamma; u += alpha p; r -= alpha q; s = D^{-1} r;
 // partials of rho = r.s and r.r.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cg_b_v4(CGArgs<float> a, int parity) {
+__global__ void __launch_bounds__(256, 4) k_cg_b_v4(CGArgs<float> a, int parity) {
   __shared__ double red[64];
   __shared__ double s_alpha;
   __shared__ int s_run;

@@ -77,9 +77,15 @@ def _lib():
         L.rbws_get_basis.argtypes = [P, P, P, P]
         L.rbws_reduced_solve.argtypes = [P, P, i32, P]
         L.rbws_solve_batch.argtypes = [P, P, i32, d, i32, C.POINTER(rbws_options), P, P, P, P]
+        L.rbws_train_surrogate.argtypes = [P, P, i32, P, i32, i32, i32, d, d, d, C.c_uint64, C.POINTER(d)]
+        L.rbws_surrogate_set_params.argtypes = [P, i32, P, P, d, d]
+        L.rbws_surrogate_get_params.argtypes = [P, C.POINTER(i32), P, P]
+        L.rbws_surrogate_forward.argtypes = [P, P, i32, i32, P]
+        L.rbws_surrogate_loss_grad.argtypes = [P, P, P, i32, C.POINTER(d), P]
         for name in ("rbws_problem_create", "rbws_problem_info", "rbws_apply_operator", "rbws_apply_operator_static",
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
-                     "rbws_solve_batch"):
+                     "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
+                     "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -191,6 +197,58 @@ def rbws_solve_batch(h, mu, tol, warm, u_out, options: rbws_options | None = Non
     rc = _check(_lib().rbws_solve_batch(h, _hp(mu), B, tol, warm, None if options is None else C.byref(options),
                                         _dp(u_out), _hp(it), _hp(rel), _hp(st)), "rbws_solve_batch")
     return rc, it, rel, st
+
+
+def mlp_param_count(p, H, N):
+    return H * p + H + 2 * (H * H + H) + N * H + N
+
+
+def rbws_train_surrogate(h, mu, hidden=256, epochs=2000, batch=256, lr=1e-3, mu_lo=0.1, mu_hi=10.0,
+                         seed=0, targets=None):
+    mu = _host(np.atleast_2d(mu))
+    t = None if targets is None else _host(targets)
+    loss = C.c_double(0)
+    _check(_lib().rbws_train_surrogate(h, _hp(mu), mu.shape[0], _hp(t), hidden, epochs, batch, lr, mu_lo,
+                                       mu_hi, seed, C.byref(loss)), "rbws_train_surrogate")
+    return loss.value
+
+
+def rbws_surrogate_set_params(h, hidden, params, coef_scale=None, mu_lo=0.1, mu_hi=10.0):
+    params = _host(params, np.float32)
+    cs = None if coef_scale is None else _host(coef_scale, np.float32)
+    _check(_lib().rbws_surrogate_set_params(h, hidden, _hp(params), _hp(cs), mu_lo, mu_hi),
+           "rbws_surrogate_set_params")
+
+
+def rbws_surrogate_get_params(h):
+    n, Q, N = rbws_problem_info(h)
+    H = C.c_int32(0)
+    _check(_lib().rbws_surrogate_get_params(h, C.byref(H), None, None), "rbws_surrogate_get_params")
+    params = np.empty(mlp_param_count(Q, H.value, N), dtype=np.float32)
+    cs = np.empty(N, dtype=np.float32)
+    _check(_lib().rbws_surrogate_get_params(h, None, _hp(params), _hp(cs)), "rbws_surrogate_get_params")
+    return H.value, params, cs
+
+
+def rbws_surrogate_forward(h, mu, corrected=False):
+    mu = _host(np.atleast_2d(mu))
+    _, _, N = rbws_problem_info(h)
+    c = np.empty((mu.shape[0], N))
+    _check(_lib().rbws_surrogate_forward(h, _hp(mu), mu.shape[0], int(bool(corrected)), _hp(c)),
+           "rbws_surrogate_forward")
+    return c
+
+
+def rbws_surrogate_loss_grad(h, x, t):
+    x = _host(np.atleast_2d(x), np.float32)
+    t = _host(np.atleast_2d(t), np.float32)
+    n, Q, N = rbws_problem_info(h)
+    H, params, _ = rbws_surrogate_get_params(h)
+    g = np.empty(params.size, dtype=np.float32)
+    loss = C.c_double(0)
+    _check(_lib().rbws_surrogate_loss_grad(h, _hp(x), _hp(t), x.shape[0], C.byref(loss), _hp(g)),
+           "rbws_surrogate_loss_grad")
+    return loss.value, g
 
 
 class Problem:
