@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arm-steps", type=int, default=2, help="timed steps of each side arm (0: skip arms)")
     ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
+    ap.add_argument("--mlp-epochs", type=int, default=2000,
+                    help="epochs of the learned warm start's training (0: skip the learned arms)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -277,6 +279,19 @@ def main():
         ("galerkin_fp64" if args.precision != "fp64" else "galerkin_fp32ir",
          rbws.WARM_GALERKIN, rbws.FP32_IR if args.precision == "fp64" else rbws.FP64),
         ("zero_fp32ir", rbws.WARM_ZERO, rbws.FP32_IR)]
+    learned = None
+    if args.arm_steps > 0 and args.mlp_epochs > 0:
+        # learned warm start (same 64^3 problem): p -> 256 -> 256 -> 256 -> N network trained on
+        # the GPU on the reduced Galerkin coefficients of 4096 seeded parameters
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = rbws.rbws_train_surrogate(P.h, inputs.surrogate_mu(inputs.WORKLOADS["c4"], 4096), hidden=256,
+                                         epochs=args.mlp_epochs, batch=256, lr=1e-3, mu_lo=w.mu_lo,
+                                         mu_hi=w.mu_hi, seed=3004)
+        learned = {"train_s": time.perf_counter() - t0, "final_loss": loss, "samples": 4096,
+                   "epochs": args.mlp_epochs, "hidden": 256}
+        arm_list += [("learned_" + args.precision, rbws.WARM_LEARNED, headline),
+                     ("learned_corrected_" + args.precision, rbws.WARM_LEARNED_CORRECTED, headline)]
     for name, warm, pr in arm_list:
         if name.startswith("galerkin_" + args.precision):
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
@@ -322,7 +337,7 @@ def main():
             "e2e": {"value": B * world / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(B * w.Q * 8),
                     "d2h_bytes_per_step": int(B * P.n * 8 + B * (4 + 8 + 4))},
-            "arms": arms, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "arms": arms, "learned_training": learned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
             "iters_mean": float(np.mean(it)), "relres_max": float(np.max(rel))}
     if "zero_fp64" in arms:
         line["speedup_vs_zero_fp64"] = value / arms["zero_fp64"]["solves_per_s"]
