@@ -240,6 +240,32 @@ RBWS_API rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t 
                              int32_t warm, const rbws_options* opt, void* u_out,
                              int32_t* iters_out, double* relres_out, int32_t* status_out);
 
+/* Autotuner of the FP32 PCG phase kernels for batches of B instances on this
+ * problem's grid (needs nx % 4 == 0): times each candidate tile (4*tx x ty
+ * nodes, tx in {32,16,8,4}, 64..256 threads) and z-chunk (8..64 planes) on the
+ * GPU with CUDA events and keeps the fastest for later FP32_IR solves with B
+ * instances.  cache_path (may be NULL): a text file of "grid/B/fp32 tx ty zc
+ * ms" lines; a matching line is used without timing, a new choice is
+ * appended.  Outputs (may be NULL): the chosen tile, chunk and the mean time
+ * in ms of one stencil-phase plus update-phase pair. */
+RBWS_API rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int32_t* tx_out,
+                                   int32_t* ty_out, int32_t* zc_out, double* ms_out);
+
+/* Solves n_req single-parameter requests that may live on different grids
+ * (problems) in one call: the requests of each problem form one batch, and
+ * the batches of different problems run concurrently, each on its problem's
+ * own stream.  mu[r]: host [Q of probs[r]]; u_out[r]: device [n_dof of
+ * probs[r]] float64.  iters_out (host [n_req]); relres_out, status_out and
+ * latency_ms_out (host [n_req]) may be NULL.  latency_ms_out[r] = time from
+ * the start of the earliest batch to the moment request r reached its final
+ * status, from the GPU's global timer.  opt->stream and opt->profile must be
+ * NULL.  A problem must not be used by another call meanwhile. */
+RBWS_API rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs,
+                                         const double* const* mu, void* const* u_out, double tol,
+                                         int32_t warm, const rbws_options* opt, int32_t* iters_out,
+                                         double* relres_out, int32_t* status_out,
+                                         double* latency_ms_out);
+
 /* Thread-local message for the last error (never NULL). */
 RBWS_API const char* rbws_last_error(void);
 

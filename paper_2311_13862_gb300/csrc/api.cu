@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -114,6 +115,11 @@ struct rbws_problem_s {
   float* d_cscale = nullptr;  // [N] coefficient scales
   double net_lo = 0.0, net_hi = 0.0;
   std::map<std::string, DevBuf> bufs;
+  struct Tuned {
+    int tx, ty, zc;
+    double ms;
+  };
+  std::map<int, Tuned> tuned32;  // batch size -> tuned FP32 tile
 
   void* buf(const std::string& name, size_t bytes, int* err) {
     DevBuf& d = bufs[name];
@@ -368,15 +374,16 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
 
 template <typename T>
 rbws_status make_cg_args(rbws_problem p, int B, Tile t, const T* coef, T* u, CGArgs<T>* out,
-                         const std::string& tag, int vec = 1) {
+                         const std::string& tag, int vec = 1, int zc_force = 0) {
   int err = 0;
   CGArgs<T> a{};
   a.g = p->geo;
   a.B = B;
   a.tiles_x = (p->nx + vec * t.tx - 1) / (vec * t.tx);
   a.tiles_y = (p->ny + t.ty - 1) / t.ty;
-  a.zc = vec == 4 ? choose_zc_v4(p->nz, (int64_t)a.tiles_x * a.tiles_y * B)
-                  : choose_zc(p->nz, (int64_t)a.tiles_x * a.tiles_y * B);
+  a.zc = zc_force > 0 ? std::min(zc_force, p->nz)
+         : vec == 4 ? choose_zc_v4(p->nz, (int64_t)a.tiles_x * a.tiles_y * B)
+                    : choose_zc(p->nz, (int64_t)a.tiles_x * a.tiles_y * B);
   a.nzc = (p->nz + a.zc - 1) / a.zc;
   a.P = a.tiles_x * a.tiles_y * a.nzc;
   a.coef = coef;
@@ -406,6 +413,14 @@ __global__ void k_fill(double* x, int64_t n, double v) {
 void fill(double* x, int64_t n, double v, cudaStream_t s) {
   k_fill<<<152 * 4, 256, 0, s>>>(x, n, v);
 }
+
+__global__ void k_fill_f(float* x, int64_t n, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+void fill_f(float* x, int64_t n, float v, cudaStream_t s) { k_fill_f<<<152 * 4, 256, 0, s>>>(x, n, v); }
 
 // Per-instance FP64 true residual norms ||f - A u|| / ||f||  (B values, device).
 rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const double* u,
@@ -510,7 +525,13 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   double* coef64 = nullptr;
   float* coef32 = nullptr;
   CKI(coef_tables(p, d_mu, B, &coef64, &coef32));
-  const Tile t4 = choose_tile_v4(p->nx, p->ny);
+  Tile t4 = choose_tile_v4(p->nx, p->ny);
+  int zc_force = 0;
+  auto tu = p->tuned32.find(B);
+  if (t4.tx > 0 && tu != p->tuned32.end()) {
+    t4 = Tile{tu->second.tx, tu->second.ty};
+    zc_force = tu->second.zc;
+  }
   const bool v4 = t4.tx > 0;
   const Tile t = v4 ? t4 : choose_tile(p->nx);
   auto phase_a = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
@@ -534,7 +555,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   int* upd = err ? nullptr : (int*)p->buf("ir_upd", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
   CGArgs<float> a{};
-  CKI(make_cg_args<float>(p, B, t, coef32, d, &a, "f_", v4 ? 4 : 1));
+  CKI(make_cg_args<float>(p, B, t, coef32, d, &a, "f_", v4 ? 4 : 1, zc_force));
   a.f = nullptr;
   a.tol = tol;
   a.max_iters = o.max_iters;
@@ -833,6 +854,56 @@ rbws_status net_alloc(rbws_problem p, int H, int N) {
   p->net_P = L.P;
   return RBWS_OK;
 }
+
+
+rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
+  if (!(tol > 0.0) || o.max_iters < 0 || o.max_restarts < 0) {
+    set_error("solve: invalid tolerance or limits");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI && o.precond != RBWS_PREC_MSRB) {
+    set_error("solve: unknown preconditioner");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (o.precond == RBWS_PREC_MSRB && o.precision != RBWS_FP64) {
+    set_error("solve: the MSRB preconditioner runs in FP64 only");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_LEARNED_CORRECTED) {
+    set_error("solve: unknown warm-start mode");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (o.precision != RBWS_FP64 && o.precision != RBWS_FP32_IR) {
+    set_error("solve: unknown precision");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  return RBWS_OK;
+}
+
+// Warm start + PCG for B parameters (host mu) on the problem's current work
+// stream; u: device [B][n].
+rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol, int warm,
+                             const rbws_options& o, double* u, std::vector<InstState>& st) {
+  if (o.profile) std::memset(o.profile, 0, sizeof(rbws_profile));
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_solve"));
+  if (warm == RBWS_WARM_ZERO) {
+    CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->cur));
+  } else if (warm == RBWS_WARM_GALERKIN) {
+    CKI(galerkin_start(p, d_mu, B, u));
+  } else {
+    CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED));
+  }
+  if (o.precision == RBWS_FP64) {
+    CKI(solve_fp64(p, d_mu, B, tol, o, u, st));
+  } else {
+    CKI(solve_fp32_ir(p, d_mu, B, tol, o, u, st));
+  }
+  return RBWS_OK;
+}
+
+__global__ void k_stamp(unsigned long long* t) { *t = global_ns(); }
+void launch_stamp(unsigned long long* t, cudaStream_t s) { k_stamp<<<1, 1, 0, s>>>(t); }
 
 }  // namespace
 
@@ -1465,45 +1536,14 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
   rbws_options o;
   rbws_options_default(&o);
   if (opt) o = *opt;
-  if (!p || !mu || !u_out || !iters_out || B < 1 || B > 65535 || !(tol > 0.0) ||
-      o.max_iters < 0 || o.max_restarts < 0) {
+  if (!p || !mu || !u_out || !iters_out || B < 1 || B > 65535) {
     set_error("rbws_solve_batch: invalid argument");
     return RBWS_ERR_INVALID_ARG;
   }
-  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI && o.precond != RBWS_PREC_MSRB) {
-    set_error("rbws_solve_batch: unknown preconditioner");
-    return RBWS_ERR_INVALID_ARG;
-  }
-  if (o.precond == RBWS_PREC_MSRB && o.precision != RBWS_FP64) {
-    set_error("rbws_solve_batch: the MSRB preconditioner runs in FP64 only");
-    return RBWS_ERR_UNSUPPORTED;
-  }
-  if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_LEARNED_CORRECTED) {
-    set_error("rbws_solve_batch: unknown warm-start mode");
-    return RBWS_ERR_INVALID_ARG;
-  }
-  if (o.precision != RBWS_FP64 && o.precision != RBWS_FP32_IR) {
-    set_error("rbws_solve_batch: unknown precision");
-    return RBWS_ERR_INVALID_ARG;
-  }
+  CKI(check_solve_options(o, tol, warm));
   StreamGuard sg(p, o.stream);
-  if (o.profile) std::memset(o.profile, 0, sizeof(rbws_profile));
-  double* d_mu = nullptr;
-  CKI(upload_mu(p, mu, B, &d_mu, "mu_solve"));
-  double* u = (double*)u_out;
-  if (warm == RBWS_WARM_ZERO) {
-    CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->cur));
-  } else if (warm == RBWS_WARM_GALERKIN) {
-    CKI(galerkin_start(p, d_mu, B, u));
-  } else {
-    CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED));
-  }
   std::vector<InstState> st;
-  if (o.precision == RBWS_FP64) {
-    CKI(solve_fp64(p, d_mu, B, tol, o, u, st));
-  } else {
-    CKI(solve_fp32_ir(p, d_mu, B, tol, o, u, st));
-  }
+  CKI(solve_batch_impl(p, mu, B, tol, warm, o, (double*)u_out, st));
   if (o.profile) o.profile->launches = p->launches;
   int warn = 0;
   for (int b = 0; b < B; b++) {
@@ -1513,6 +1553,225 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
     if (status_out) status_out[b] = s;
     warn |= s != 0;
   }
+  return warn ? RBWS_WARN_NOT_CONVERGED : RBWS_OK;
+}
+
+rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int32_t* tx_out,
+                          int32_t* ty_out, int32_t* zc_out, double* ms_out) {
+  if (!p || B < 1 || B > 65535) {
+    set_error("rbws_autotune: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->nx % 4) {
+    set_error("rbws_autotune: the tuned FP32 kernels need nx % 4 == 0");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  char key[128];
+  std::snprintf(key, sizeof(key), "%dx%dx%d/B%d/fp32", p->nx, p->ny, p->nz, B);
+  // cache: one line per entry, "key tx ty zc ms"
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char k[128];
+      int tx, ty, zc;
+      double ms;
+      while (std::fscanf(f, "%127s %d %d %d %lf", k, &tx, &ty, &zc, &ms) == 5)
+        if (!std::strcmp(k, key)) p->tuned32[B] = {tx, ty, zc, ms};
+      std::fclose(f);
+      auto it = p->tuned32.find(B);
+      if (it != p->tuned32.end()) {
+        if (tx_out) *tx_out = it->second.tx;
+        if (ty_out) *ty_out = it->second.ty;
+        if (zc_out) *zc_out = it->second.zc;
+        if (ms_out) *ms_out = it->second.ms;
+        return RBWS_OK;
+      }
+    }
+  }
+  StreamGuard sg(p, nullptr);
+  cudaStream_t s = p->cur;
+  // synthetic instances: mu = 1 (coefficients do not change the timing)
+  std::vector<double> ones((size_t)B * p->Q, 1.0);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, ones.data(), B, &d_mu, "mu_tune"));
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &c64, &c32));
+  int err = 0;
+  float* d = (float*)p->buf("ir_d", sizeof(float) * (size_t)B * p->n, &err);
+  if (err) return (rbws_status)err;
+  rbws_problem_s::Tuned best{0, 0, 0, 1e30};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int tx : {32, 16, 8, 4}) {
+    if (4 * tx > p->nx) continue;
+    for (int ty : {4, 8, 16, 32, 64}) {
+      if (tx * ty < 64 || tx * ty > 256 || ty > std::max(4, p->ny)) continue;
+      for (int zc : {8, 16, 32, 64}) {
+        if (zc > p->nz && zc != 8) continue;
+        CGArgs<float> a{};
+        int rc = make_cg_args<float>(p, B, Tile{tx, ty}, c32, d, &a, "f_", 4, zc);
+        if (rc) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return (rbws_status)rc;
+        }
+        a.tol = 1e-300;
+        a.max_iters = 1 << 30;
+        a.precond = RBWS_PREC_JACOBI;
+        a.ru = 1;
+        fill((double*)a.fnorm, B, 1.0, s);
+        const size_t vb = sizeof(float) * (size_t)B * p->n;
+        cudaMemsetAsync(a.u, 0, vb, s);
+        fill_f(a.r, (int64_t)B * p->n, 1.f, s);
+        fill_f(a.s, (int64_t)B * p->n, 1.f, s);
+        fill_f(a.p0, (int64_t)B * p->n, 1.f, s);
+        float ta = 0.f, tb = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+          launch_tune_prep(a, s);
+          cudaEventRecord(e0, s);
+          launch_cg_a_v4(a, Tile{tx, ty}, 0, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float t1 = 0.f;
+          cudaEventElapsedTime(&t1, e0, e1);
+          launch_tune_prep(a, s);
+          cudaEventRecord(e0, s);
+          launch_cg_b_v4(a, Tile{tx, ty}, 0, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float t2 = 0.f;
+          cudaEventElapsedTime(&t2, e0, e1);
+          if (rep > 0) {  // the first repetition warms caches and code
+            ta += t1;
+            tb += t2;
+          }
+        }
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return (rbws_status)cuda_fail(ce, "rbws_autotune");
+        }
+        const double ms = 0.5 * (ta + tb);
+        if (ms < best.ms) best = {tx, ty, std::min(zc, p->nz), ms};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!best.tx) {
+    set_error("rbws_autotune: no candidate tile fits this grid");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  p->tuned32[B] = best;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s %d %d %d %.6f\n", key, best.tx, best.ty, best.zc, best.ms);
+      std::fclose(f);
+    }
+  }
+  if (tx_out) *tx_out = best.tx;
+  if (ty_out) *ty_out = best.ty;
+  if (zc_out) *zc_out = best.zc;
+  if (ms_out) *ms_out = best.ms;
+  return RBWS_OK;
+}
+
+rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const double* const* mu,
+                                void* const* u_out, double tol, int32_t warm, const rbws_options* opt,
+                                int32_t* iters_out, double* relres_out, int32_t* status_out,
+                                double* latency_ms_out) {
+  rbws_options o;
+  rbws_options_default(&o);
+  if (opt) o = *opt;
+  if (n_req < 1 || !probs || !mu || !u_out || !iters_out) {
+    set_error("rbws_solve_requests: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  for (int r = 0; r < n_req; r++)
+    if (!probs[r] || !mu[r] || !u_out[r]) {
+      set_error("rbws_solve_requests: null problem, parameter or output for request " + std::to_string(r));
+      return RBWS_ERR_INVALID_ARG;
+    }
+  CKI(check_solve_options(o, tol, warm));
+  if (o.stream || o.profile) {
+    set_error("rbws_solve_requests: runs each grid on its problem's own stream; stream and profile must be NULL");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  // group the requests by problem (one batched solve per grid)
+  std::vector<rbws_problem> groups;
+  std::vector<std::vector<int>> members;
+  for (int r = 0; r < n_req; r++) {
+    size_t g = 0;
+    while (g < groups.size() && groups[g] != probs[r]) g++;
+    if (g == groups.size()) {
+      groups.push_back(probs[r]);
+      members.emplace_back();
+    }
+    members[g].push_back(r);
+  }
+  const size_t G = groups.size();
+  std::vector<int> rc(G, RBWS_OK);
+  std::vector<std::string> msg(G);
+  std::vector<std::vector<InstState>> st(G);
+  std::vector<unsigned long long> t0(G, 0);
+  auto run_group = [&](size_t g) {
+    rbws_problem p = groups[g];
+    const std::vector<int>& mem = members[g];
+    const int B = (int)mem.size();
+    StreamGuard sg(p, nullptr);
+    int err = 0;
+    double* u = (double*)p->buf("req_u", sizeof(double) * (size_t)B * p->n, &err);
+    unsigned long long* d_t0 = err ? nullptr : (unsigned long long*)p->buf("req_t0", 8, &err);
+    if (err) {
+      rc[g] = err;
+      msg[g] = rbws_last_error();
+      return;
+    }
+    std::vector<double> hmu((size_t)B * p->Q);
+    for (int k = 0; k < B; k++) std::memcpy(&hmu[(size_t)k * p->Q], mu[mem[k]], sizeof(double) * p->Q);
+    launch_stamp(d_t0, p->cur);
+    rbws_options og = o;
+    int r = solve_batch_impl(p, hmu.data(), B, tol, warm, og, u, st[g]);
+    if (r == RBWS_OK) {
+      for (int k = 0; k < B && r == RBWS_OK; k++) {
+        cudaError_t e = cudaMemcpyAsync(u_out[mem[k]], u + (size_t)k * p->n, sizeof(double) * p->n,
+                                        cudaMemcpyDeviceToDevice, p->cur);
+        if (e != cudaSuccess) r = cuda_fail(e, "rbws_solve_requests: copy out");
+      }
+      cudaError_t e = cudaMemcpyAsync(&t0[g], d_t0, 8, cudaMemcpyDeviceToHost, p->cur);
+      if (r == RBWS_OK && e != cudaSuccess) r = cuda_fail(e, "rbws_solve_requests: stamp");
+      e = cudaStreamSynchronize(p->cur);
+      if (r == RBWS_OK && e != cudaSuccess) r = cuda_fail(e, "rbws_solve_requests");
+    }
+    rc[g] = r;
+    if (r != RBWS_OK) msg[g] = rbws_last_error();
+  };
+  // every grid's batch runs on its own stream, driven by its own host thread
+  std::vector<std::thread> th;
+  for (size_t g = 1; g < G; g++) th.emplace_back(run_group, g);
+  run_group(0);
+  for (auto& t : th) t.join();
+  for (size_t g = 0; g < G; g++)
+    if (rc[g] != RBWS_OK) {
+      set_error(msg[g]);
+      return (rbws_status)rc[g];
+    }
+  unsigned long long start = t0[0];
+  for (size_t g = 1; g < G; g++) start = std::min(start, t0[g]);
+  int warn = 0;
+  for (size_t g = 0; g < G; g++)
+    for (size_t k = 0; k < members[g].size(); k++) {
+      const int r = members[g][k];
+      const InstState& s = st[g][k];
+      iters_out[r] = s.iters;
+      if (relres_out) relres_out[r] = s.relres;
+      const int code = s.status == ST_CONVERGED ? 0 : (s.status == ST_BREAKDOWN ? 2 : 1);
+      if (status_out) status_out[r] = code;
+      if (latency_ms_out) latency_ms_out[r] = s.t_done > start ? (double)(s.t_done - start) * 1e-6 : 0.0;
+      warn |= code != 0;
+    }
   return warn ? RBWS_WARN_NOT_CONVERGED : RBWS_OK;
 }
 

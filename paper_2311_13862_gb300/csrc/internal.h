@@ -65,7 +65,16 @@ struct InstState {
   int pad;
   double relres; // last relative residual (true residual after finalisation)
   double relres0;
+  unsigned long long t_done;  // %globaltimer (ns) when the status last became final
 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#endif
 
 // Arguments of the CG phase kernels (one struct so launches stay short).
 template <typename T>
@@ -142,6 +151,9 @@ void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, 
 void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
 void launch_cg_b_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
 void launch_ru_reset_v4(const CGArgs<float>& a, Tile t, int start, cudaStream_t s);
+// Autotuning: puts every instance in a runnable state with benign scalars
+// (status ACTIVE, rho = 1, ||r||^2 huge, gamma = 1) so one phase kernel can be timed.
+void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s);
 // Reliable-update kernels of the FP32 path (see stencil.cu).
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s);
 void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s);

@@ -349,6 +349,7 @@ __global__ void k_cg_finalize(CGArgs<T> a, int parity, int mode, int max_restart
     s.relres = rel;
     s.iters = 0;
     s.restarts = 0;
+    s.t_done = global_ns();
     if (rel < a.tol) {
       s.status = ST_CONVERGED;
     } else if (!(rel == rel) || a.max_iters <= 0) {
@@ -400,12 +401,14 @@ __global__ void k_cg_a(CGArgs<T> a, int parity) {
           if (leader) {
             st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
             st->relres = rel;
+            st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else if (st->iters >= a.max_iters || !(rel == rel)) {
           if (leader) {
             st->status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
             st->relres = rel;
+            st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else {
@@ -466,6 +469,7 @@ __global__ void k_cg_b(CGArgs<T> a, int parity) {
           if (leader) {
             st->status = ST_BREAKDOWN;
             st->relres = sqrt(rr) / a.fnorm[b];
+            st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else {
@@ -715,6 +719,7 @@ __global__ void k_ru_reset(CGArgs<float> a, int start) {
     }
     st->status = ns;
     st->relres = rel;
+    if (ns != ST_ACTIVE) st->t_done = global_ns();
     a.rr_ref[b] = (rel * a.fnorm[b]) * (rel * a.fnorm[b]);
     if (ns == ST_ACTIVE) atomicAdd(a.active, 1);
     if (ns == ST_ACTIVE && mode == 2 && !start) st->restarts += 1;

@@ -14,6 +14,8 @@
 // that use these tiles: k_cg_a_v4, k_cg_b_v4, k_ru_reset_v4.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace rbws {
@@ -145,12 +147,14 @@ __global__ void __launch_bounds__(256, 3) k_cg_a_v4(CGArgs<float> a, int parity)
           if (leader) {
             st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
             st->relres = rel;
+            st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else if (st->iters >= a.max_iters || !(rel == rel)) {
           if (leader) {
             st->status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
             st->relres = rel;
+            st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else {
@@ -304,6 +308,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_b_v4(CGArgs<float> a, int parity)
           if (leader) {
             st->status = ST_BREAKDOWN;
             st->relres = sqrt(rr) / a.fnorm[b];
+            st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else {
@@ -408,6 +413,7 @@ __global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start)
     }
     st->status = ns;
     st->relres = rel;
+    if (ns != ST_ACTIVE) st->t_done = global_ns();
     a.rr_ref[b] = (rel * a.fnorm[b]) * (rel * a.fnorm[b]);
     if (ns == ST_ACTIVE) atomicAdd(a.active, 1);
     if (ns == ST_ACTIVE && mode == 2 && !start) st->restarts += 1;
@@ -453,6 +459,25 @@ __global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start)
     if (restart)
       a.rho_rr[((int64_t)a.B + b) * a.P + ps.part] = make_double2(ps.part == 0 ? 1.0 : 0.0, 0.0);
   }
+}
+
+__global__ void k_tune_prep(CGArgs<float> a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nP = (int64_t)a.B * a.P;
+  if (i < a.B) {
+    a.st[i].status = ST_ACTIVE;
+    a.st[i].iters = 0;
+  }
+  if (i < nP) {
+    a.rho_rr[i] = make_double2(1.0, 1e300);
+    a.rho_rr[nP + i] = make_double2(1.0, 1e300);
+    a.gam[i] = 1.0;
+  }
+}
+
+void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s) {
+  const int64_t n = std::max<int64_t>(a.B, (int64_t)a.B * a.P);
+  k_tune_prep<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
 }
 
 size_t v4_plane_smem(Tile t) { return sizeof(float) * 3 * (size_t)(4 * t.tx + 8) * (t.ty + 2); }

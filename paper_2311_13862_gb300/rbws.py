@@ -82,10 +82,14 @@ def _lib():
         L.rbws_surrogate_get_params.argtypes = [P, C.POINTER(i32), P, P]
         L.rbws_surrogate_forward.argtypes = [P, P, i32, i32, P]
         L.rbws_surrogate_loss_grad.argtypes = [P, P, P, i32, C.POINTER(d), P]
+        L.rbws_solve_requests.argtypes = [i32, P, P, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
+        L.rbws_autotune.argtypes = [P, i32, C.c_char_p, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                    C.POINTER(d)]
         for name in ("rbws_problem_create", "rbws_problem_info", "rbws_apply_operator", "rbws_apply_operator_static",
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
-                     "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad"):
+                     "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
+                     "rbws_solve_requests", "rbws_autotune"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -249,6 +253,31 @@ def rbws_surrogate_loss_grad(h, x, t):
     _check(_lib().rbws_surrogate_loss_grad(h, _hp(x), _hp(t), x.shape[0], C.byref(loss), _hp(g)),
            "rbws_surrogate_loss_grad")
     return loss.value, g
+
+
+def rbws_solve_requests(handles, mus, u_outs, tol, warm, options: rbws_options | None = None):
+    """One request per (handle, mu, u_out); returns (status, iters, relres, inst_status, latency_ms)."""
+    n = len(handles)
+    H = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    mus = [_host(np.ravel(m)) for m in mus]
+    M = (C.c_void_p * n)(*[m.ctypes.data for m in mus])
+    U = (C.c_void_p * n)(*[_dp(u).value for u in u_outs])
+    it = np.zeros(n, dtype=np.int32)
+    rel = np.zeros(n)
+    st = np.zeros(n, dtype=np.int32)
+    lat = np.zeros(n)
+    rc = _check(_lib().rbws_solve_requests(n, H, M, U, tol, warm, None if options is None else C.byref(options),
+                                           _hp(it), _hp(rel), _hp(st), _hp(lat)), "rbws_solve_requests")
+    return rc, it, rel, st, lat
+
+
+def rbws_autotune(h, B, cache_path=None):
+    """Returns (tx, ty, zc, ms) of the fastest FP32 tile for batches of B."""
+    tx, ty, zc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+    path = None if cache_path is None else str(cache_path).encode()
+    _check(_lib().rbws_autotune(h, B, path, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(ms)),
+           "rbws_autotune")
+    return tx.value, ty.value, zc.value, ms.value
 
 
 class Problem:
