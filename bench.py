@@ -159,6 +159,73 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_requests(args):
+    """96 requests (32 each on 96^3, 128^3, 256^3 grids, 3x3x3 blocks, mu in [0.1,10]^27) per step,
+    interleaved in a fixed order, in one rbws_solve_requests call: learned start with one reduced
+    correction, FP32 PCG inside FP64 refinement to 1e-10; per-request latency p50/p99."""
+    import torch
+    from paper_2311_13862_gb300 import build, inputs, rbws
+    build.build()
+    torch.cuda.set_device(0)
+    names = ["c5-96", "c5-128", "c5-256"]
+    probs, offline = [], {}
+    for nm in names:
+        w = inputs.WORKLOADS[nm]
+        P = rbws.Problem(w.grid, w.blocks)
+        t0 = time.perf_counter()
+        N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w, args.c5_train), w.n_max, 0.0, 1e-12)
+        t1 = time.perf_counter()
+        loss = rbws.rbws_train_surrogate(P.h, inputs.surrogate_mu(w, 2048), hidden=256, epochs=args.mlp_epochs // 2,
+                                         batch=256, lr=1e-3, mu_lo=w.mu_lo, mu_hi=w.mu_hi, seed=3005)
+        t2 = time.perf_counter()
+        tile = rbws.rbws_autotune(P.h, 32)
+        offline[nm] = {"N": N, "greedy_s": t1 - t0, "train_s": t2 - t1, "train_loss": loss,
+                       "eta_last": float(eta[-1]), "tile": tile[:3], "tile_pair_ms": tile[3]}
+        probs.append((w, P))
+    order = [k % 3 for k in range(96)]  # 96^3, 128^3, 256^3, 96^3, ...
+    mus = [None] * 96
+    count = [0, 0, 0]
+    for r, k in enumerate(order):
+        mus[r] = inputs.test_mu(probs[k][0])[count[k]]
+        count[k] += 1
+    handles = [probs[k][1].h for k in order]
+    outs = [torch.empty(probs[k][1].n, dtype=torch.float64, device="cuda") for k in order]
+    opt = rbws.rbws_options_default(precision=rbws.FP32_IR)
+    for _ in range(args.warmup):
+        rbws.rbws_solve_requests(handles, mus, outs, 1e-10, rbws.WARM_LEARNED_CORRECTED, opt)
+    torch.cuda.synchronize()
+    lats, its, times = [], [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            rc, it, rel, st, lat = rbws.rbws_solve_requests(handles, mus, outs, 1e-10,
+                                                            rbws.WARM_LEARNED_CORRECTED, opt)
+            times.append(time.perf_counter() - t0)
+            assert np.all(st == 0), st
+            lats.append(lat)
+            its.append(it)
+    lat = np.concatenate(lats)
+    it = np.concatenate(its)
+    ms = 1e3 * float(np.mean(times))
+    per_grid = {}
+    for k, nm in enumerate(names):
+        sel_k = np.array([order[r] == k for r in range(96)] * args.steps)
+        per_grid[nm] = {"iters_mean": float(it[sel_k].mean()), "latency_ms_p50": float(np.percentile(lat[sel_k], 50))}
+    line = {"metric": METRIC, "value": 96 / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": "96 requests per step: 32 each on 96^3, 128^3, 256^3 interior grids, 3x3x3 "
+                                   "blocks (p=27), mu log-uniform in [0.1,10]^27, RB N<=60 per grid, learned "
+                                   "start + one reduced correction, FP32 PCG in FP64 refinement to 1e-10",
+                       "timing": "host wall clock around each rbws_solve_requests call (synchronous)"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "per_grid": per_grid, "offline": offline, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    for w, P in probs:
+        P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,11 +238,16 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
     ap.add_argument("--mlp-epochs", type=int, default=2000,
                     help="epochs of the learned warm start's training (0: skip the learned arms)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
+                    help="c2: the 64^3 batched workload (default line); c5: 96 requests on 96^3/128^3/256^3")
+    ap.add_argument("--c5-train", type=int, default=256, help="greedy training parameters per grid (c5)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "c5":
+        return bench_requests(args)
 
     import torch
     import torch.distributed as dist
@@ -311,13 +383,14 @@ def main():
         a_st_gbs = acc["active_dofs"] * alg_stencil / (acc["stencil_ms"] * 1e-3) / 1e9
         a_up_gbs = acc["active_dofs"] * alg_update / (acc["update_ms"] * 1e-3) / 1e9
         solver_gbs = acc["active_dofs"] * 6 * eb / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
-        tag = "cg_stencil_phase_%s_64cube" % ("f32" if eb == 4 else "f64")
+        tag = "cg_stencil_phase_%s_64cube" % ("f32_v4" if eb == 4 else "f64")
         tpd = traffic_per_dof(tag)
         launch_dofs = acc["active_dofs"] / acc["samples"]
         res = {"bound": "hbm", "achieved": round(a_st_gbs, 1), "peak": peak, "unit": "GB/s",
                "frac": round(a_st_gbs / peak, 4), "peak_kind": peak_kind,
                "traffic": None if tpd is None else tpd * launch_dofs,
-               "kernel": "k_cg_a<%s> (p = s + beta p, q = A p, p.q)" % ("float" if eb == 4 else "double"),
+               "kernel": ("k_cg_a_v4 (FP32, 4 nodes/thread: p = s + beta p, q = A p, p.q)" if eb == 4
+                          else "k_cg_a<double> (p = s + beta p, q = A p, p.q)"),
                "algorithmic_bytes_per_dof": alg_stencil,
                "stencil_ms_per_launch": acc["stencil_ms"] / acc["samples"],
                "update_kernel_frac": round(a_up_gbs / peak, 4),

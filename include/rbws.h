@@ -165,7 +165,9 @@ RBWS_API rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu
 
 /* Offline greedy (Algorithm 5's loop with the Galerkin RB of Sec. 2.3 and a
  * residual indicator): first parameter = mu_train[0]; snapshot solves by
- * Jacobi-PCG to snapshot_tol; Gram-Schmidt applied twice; the next parameter
+ * Jacobi-PCG to snapshot_tol (a snapshot that stalls above snapshot_tol at
+ * the rounding floor of the FP64 residual is used if its true relative
+ * residual is below 1e-9); Gram-Schmidt applied twice; the next parameter
  * maximises eta(mu) = ||f - A(mu) W c(mu)|| / ||f|| over the training points
  * not yet selected (ties: smallest index).  Stops at n_max, when max eta <
  * greedy_tol, or when a snapshot adds no new direction (||w|| < 1e-10 ||u||).
@@ -242,12 +244,14 @@ RBWS_API rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t 
 
 /* Autotuner of the FP32 PCG phase kernels for batches of B instances on this
  * problem's grid (needs nx % 4 == 0): times each candidate tile (4*tx x ty
- * nodes, tx in {32,16,8,4}, 64..256 threads) and z-chunk (8..64 planes) on the
- * GPU with CUDA events and keeps the fastest for later FP32_IR solves with B
- * instances.  cache_path (may be NULL): a text file of "grid/B/fp32 tx ty zc
- * ms" lines; a matching line is used without timing, a new choice is
- * appended.  Outputs (may be NULL): the chosen tile, chunk and the mean time
- * in ms of one stencil-phase plus update-phase pair. */
+ * nodes, tx in {32,16,8,4}, 64..256 threads), z-chunk (8..64 planes) and
+ * iteration schedule (32 bytes per DoF: s formed on the fly, A p recomputed;
+ * or 44 bytes per DoF: s and A p stored) on the GPU with CUDA events, and
+ * keeps the fastest for later FP32_IR solves with B instances.  cache_path
+ * (may be NULL): a text file of "grid/B/fp32 tx ty zc ms schedule" lines; a
+ * matching line is used without timing, a new choice is appended.  Outputs
+ * (may be NULL): the chosen tile, chunk and the mean time in ms of one
+ * stencil-phase plus update-phase pair. */
 RBWS_API rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int32_t* tx_out,
                                    int32_t* ty_out, int32_t* zc_out, double* ms_out);
 

@@ -118,6 +118,7 @@ struct rbws_problem_s {
   struct Tuned {
     int tx, ty, zc;
     double ms;
+    int sched;  // 1: 32-byte schedule, 0: 44-byte schedule
   };
   std::map<int, Tuned> tuned32;  // batch size -> tuned FP32 tile
 
@@ -526,20 +527,27 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   float* coef32 = nullptr;
   CKI(coef_tables(p, d_mu, B, &coef64, &coef32));
   Tile t4 = choose_tile_v4(p->nx, p->ny);
-  int zc_force = 0;
+  // The 44-byte schedule is the default: its update phase is a pure stream
+  // (97% of HBM on the 64^3 workload) while both 32-byte phases are stencil
+  // kernels (about 45%); the autotuner picks the 32-byte one where it wins.
+  int zc_force = 0, sched32 = 0;
   auto tu = p->tuned32.find(B);
   if (t4.tx > 0 && tu != p->tuned32.end()) {
     t4 = Tile{tu->second.tx, tu->second.ty};
     zc_force = tu->second.zc;
+    sched32 = tu->second.sched;
   }
   const bool v4 = t4.tx > 0;
+  if (!v4) sched32 = 0;
   const Tile t = v4 ? t4 : choose_tile(p->nx);
   auto phase_a = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
-    if (v4) launch_cg_a_v4(aa, t, par, ss);
+    if (sched32) launch_cg_a32_v4(aa, t, par, ss);
+    else if (v4) launch_cg_a_v4(aa, t, par, ss);
     else launch_cg_a<float>(aa, t, par, ss);
   };
   auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
-    if (v4) launch_cg_b_v4(aa, t, par, ss);
+    if (sched32) launch_cg_b32_v4(aa, t, par, ss);
+    else if (v4) launch_cg_b_v4(aa, t, par, ss);
     else launch_cg_b<float>(aa, t, par, ss);
   };
   auto reset = [&](const CGArgs<float>& aa, int start, cudaStream_t ss) {
@@ -569,6 +577,11 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.u64 = u;
   a.r64 = r64;
   a.rel64 = rel;
+  if (sched32) {
+    a.alpha = (double*)p->buf("ir_alpha", sizeof(double) * 2 * (size_t)B, &err);
+    if (err) return (rbws_status)err;
+    CK(cudaMemsetAsync(a.alpha, 0, sizeof(double) * 2 * (size_t)B, s));
+  }
   fill((double*)a.fnorm, B, p->fnorm, s);
   CK(cudaMemsetAsync(d, 0, sizeof(float) * (size_t)B * p->n, s));
   // start: every instance takes an update from u (restarting its direction)
@@ -661,7 +674,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   CK(cudaStreamSynchronize(s));
   std::vector<int> fin(B);
   int nfin = 0;
-  for (int b = 0; b < B; b++) nfin += (fin[b] = (h[b].status == ST_MAX_ITERS || h[b].status == ST_BREAKDOWN));
+  // mode 2: the fold adds the update still pending at the parity recorded when the instance stopped
+  for (int b = 0; b < B; b++) nfin += (fin[b] = (h[b].status == ST_MAX_ITERS || h[b].status == ST_BREAKDOWN) ? 2 : 0) != 0;
   if (nfin) {
     CK(cudaMemcpyAsync(upd, fin.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
     launch_ru_fold(a, s);
@@ -1239,8 +1253,12 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
     std::vector<InstState> st;
     CK(cudaMemsetAsync(usnap, 0, sizeof(double) * n, s));
     CKI(solve_fp64(p, d_mu + (int64_t)next * Q, 1, snapshot_tol, o, usnap, st));
-    if (st[0].status != ST_CONVERGED) {
-      set_error("rbws_offline_greedy: snapshot solve did not converge");
+    // A snapshot whose true residual stalls above snapshot_tol at the rounding
+    // floor of the FP64 residual (large, high-contrast grids) is still used if
+    // that residual is below 1e-9.
+    if (st[0].status != ST_CONVERGED && !(st[0].status == ST_MAX_ITERS && st[0].relres < 1e-9)) {
+      set_error("rbws_offline_greedy: snapshot solve did not converge (relative residual " +
+                std::to_string(st[0].relres) + ")");
       return RBWS_ERR_STATE;
     }
     // w = (I - W W^T)^2 u
@@ -1572,10 +1590,10 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
       char k[128];
-      int tx, ty, zc;
+      int tx, ty, zc, sched;
       double ms;
-      while (std::fscanf(f, "%127s %d %d %d %lf", k, &tx, &ty, &zc, &ms) == 5)
-        if (!std::strcmp(k, key)) p->tuned32[B] = {tx, ty, zc, ms};
+      while (std::fscanf(f, "%127s %d %d %d %lf %d", k, &tx, &ty, &zc, &ms, &sched) == 6)
+        if (!std::strcmp(k, key)) p->tuned32[B] = {tx, ty, zc, ms, sched};
       std::fclose(f);
       auto it = p->tuned32.find(B);
       if (it != p->tuned32.end()) {
@@ -1599,7 +1617,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
   int err = 0;
   float* d = (float*)p->buf("ir_d", sizeof(float) * (size_t)B * p->n, &err);
   if (err) return (rbws_status)err;
-  rbws_problem_s::Tuned best{0, 0, 0, 1e30};
+  rbws_problem_s::Tuned best{0, 0, 0, 1e30, 0};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1626,35 +1644,46 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
         fill_f(a.r, (int64_t)B * p->n, 1.f, s);
         fill_f(a.s, (int64_t)B * p->n, 1.f, s);
         fill_f(a.p0, (int64_t)B * p->n, 1.f, s);
-        float ta = 0.f, tb = 0.f;
-        for (int rep = 0; rep < 3; rep++) {
-          launch_tune_prep(a, s);
-          cudaEventRecord(e0, s);
-          launch_cg_a_v4(a, Tile{tx, ty}, 0, s);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          float t1 = 0.f;
-          cudaEventElapsedTime(&t1, e0, e1);
-          launch_tune_prep(a, s);
-          cudaEventRecord(e0, s);
-          launch_cg_b_v4(a, Tile{tx, ty}, 0, s);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          float t2 = 0.f;
-          cudaEventElapsedTime(&t2, e0, e1);
-          if (rep > 0) {  // the first repetition warms caches and code
-            ta += t1;
-            tb += t2;
-          }
-        }
-        cudaError_t ce = cudaGetLastError();
-        if (ce != cudaSuccess) {
+        double* alpha = (double*)p->buf("ir_alpha", sizeof(double) * 2 * (size_t)B, &err);
+        if (err) {
           cudaEventDestroy(e0);
           cudaEventDestroy(e1);
-          return (rbws_status)cuda_fail(ce, "rbws_autotune");
+          return (rbws_status)err;
         }
-        const double ms = 0.5 * (ta + tb);
-        if (ms < best.ms) best = {tx, ty, std::min(zc, p->nz), ms};
+        a.alpha = alpha;
+        for (int sched = 0; sched < 2; sched++) {
+          float ta = 0.f, tb = 0.f;
+          for (int rep = 0; rep < 3; rep++) {
+            launch_tune_prep(a, s);
+            cudaEventRecord(e0, s);
+            if (sched) launch_cg_a32_v4(a, Tile{tx, ty}, 0, s);
+            else launch_cg_a_v4(a, Tile{tx, ty}, 0, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float t1 = 0.f;
+            cudaEventElapsedTime(&t1, e0, e1);
+            launch_tune_prep(a, s);
+            cudaEventRecord(e0, s);
+            if (sched) launch_cg_b32_v4(a, Tile{tx, ty}, 0, s);
+            else launch_cg_b_v4(a, Tile{tx, ty}, 0, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float t2 = 0.f;
+            cudaEventElapsedTime(&t2, e0, e1);
+            if (rep > 0) {  // the first repetition warms caches and code
+              ta += t1;
+              tb += t2;
+            }
+          }
+          cudaError_t ce = cudaGetLastError();
+          if (ce != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return (rbws_status)cuda_fail(ce, "rbws_autotune");
+          }
+          const double ms = 0.5 * (ta + tb);
+          if (ms < best.ms) best = {tx, ty, std::min(zc, p->nz), ms, sched};
+        }
       }
     }
   }
@@ -1667,7 +1696,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
   p->tuned32[B] = best;
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
-      std::fprintf(f, "%s %d %d %d %.6f\n", key, best.tx, best.ty, best.zc, best.ms);
+      std::fprintf(f, "%s %d %d %d %.6f %d\n", key, best.tx, best.ty, best.zc, best.ms, best.sched);
       std::fclose(f);
     }
   }

@@ -120,6 +120,9 @@ struct CGArgs {
   double* u64;          // [B][n] FP64 solution
   double* r64;          // [B][n] FP64 residual f - A u64
   double* rel64;        // [B] ||r64|| / ||f||
+  // 32-byte FP32 schedule (k_cg_a32_v4 / k_cg_b32_v4): s is never stored and
+  // the u update of iteration k is applied by phase A of iteration k+1.
+  double* alpha;        // [2][B] alpha_k by parity; 0 = no pending update
 };
 
 // ---------------------------------------------------------------------------
@@ -151,6 +154,10 @@ void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, 
 void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
 void launch_cg_b_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
 void launch_ru_reset_v4(const CGArgs<float>& a, Tile t, int start, cudaStream_t s);
+// 32-byte schedule: phase A reads r, p_old, u and writes p, u; phase B reads
+// r, p (halo) and writes r (A p recomputed); 32 B per DoF and iteration.
+void launch_cg_a32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
+void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
 // Autotuning: puts every instance in a runnable state with benign scalars
 // (status ACTIVE, rho = 1, ||r||^2 huge, gamma = 1) so one phase kernel can be timed.
 void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s);

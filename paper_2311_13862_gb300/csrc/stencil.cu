@@ -678,14 +678,22 @@ __global__ void k_ru_decide(CGArgs<float> a) {
   if (u) atomicAdd(a.pending, 1);
 }
 
-// u64 += d; d = 0 for flagged instances.
+// u64 += d; d = 0 for flagged instances.  With the 32-byte schedule the
+// update alpha p of the last iteration is still pending: it is added here
+// (parity 0 for updates at a block boundary, the recorded parity otherwise).
 __global__ void k_ru_fold(CGArgs<float> a) {
   const int b = blockIdx.y;
-  if (!a.upd[b]) return;
+  const int mode = a.upd[b];
+  if (!mode) return;
+  const int par = mode == 1 ? 0 : a.st[b].pad;
+  const double al = a.alpha ? a.alpha[(int64_t)par * a.B + b] : 0.0;
+  const float* pp = (par ? a.p1 : a.p0) + (int64_t)b * a.g.n;
   const int64_t off = (int64_t)b * a.g.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.g.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    a.u64[off + i] += (double)a.u[off + i];
+    double v = a.u64[off + i] + (double)a.u[off + i];
+    if (al != 0.0) v = fma(al, (double)pp[i], v);
+    a.u64[off + i] = v;
     a.u[off + i] = 0.f;
   }
 }
@@ -720,6 +728,7 @@ __global__ void k_ru_reset(CGArgs<float> a, int start) {
     st->status = ns;
     st->relres = rel;
     if (ns != ST_ACTIVE) st->t_done = global_ns();
+    if (a.alpha) a.alpha[b] = 0.0;  // the fold applied any pending update
     a.rr_ref[b] = (rel * a.fnorm[b]) * (rel * a.fnorm[b]);
     if (ns == ST_ACTIVE) atomicAdd(a.active, 1);
     if (ns == ST_ACTIVE && mode == 2 && !start) st->restarts += 1;

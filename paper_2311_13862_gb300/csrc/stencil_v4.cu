@@ -114,6 +114,64 @@ struct Plane {
   __device__ __forceinline__ int at(int x, int y) const { return (y + 1) * PW + 4 + x; }
 };
 
+// Halo duty of a thread in the v4 tiles: y-halo rows by 4-node groups
+// (2*blockDim.x threads), then x-halo columns by single nodes (2*TY threads).
+struct Halo4 {
+  int kind;      // 0 none, 1 y-row group (4 nodes), 2 x-column node
+  int hx, hy;    // tile-local position
+  bool in;       // inside the domain
+  int64_t col;   // gj*nx + gi
+  int slot;      // shared-memory offset
+};
+
+__device__ __forceinline__ Halo4 halo4(const Geo& g, const Pos4& ps, const Plane& pl, int tid) {
+  Halo4 h{0, 0, 0, false, 0, 0};
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  const int nyh = 2 * blockDim.x;
+  if (tid < nyh) {
+    h.kind = 1;
+    h.hx = 4 * (tid % blockDim.x);
+    h.hy = tid < (int)blockDim.x ? -1 : TY;
+  } else if (tid < nyh + 2 * TY) {
+    h.kind = 2;
+    const int t = tid - nyh;
+    h.hx = t < TY ? -1 : TXN;
+    h.hy = t < TY ? t : t - TY;
+  }
+  const int gi = ps.x0 + h.hx, gj = ps.y0 + h.hy;
+  h.in = h.kind != 0 && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+  h.col = (int64_t)gj * g.nx + gi;
+  h.slot = pl.at(h.hx, h.hy);
+  return h;
+}
+
+// y = A x for the thread's 4 nodes from the staged plane P (x, y neighbours)
+// and the column registers xm (z-1), xc (z), xp (z+1).
+__device__ __forceinline__ void stencil4(const float* P, const Plane& pl, int oslot, const float c[4][7],
+                                         float4 xm, float4 xc, float4 xp, float y[4]) {
+  const float left = P[oslot - 1], right = P[oslot + 4];
+  const float4 sth = ld4(P + oslot - pl.PW), nth = ld4(P + oslot + pl.PW);
+#pragma unroll
+  for (int e = 0; e < 4; e++) {
+    const float xce = f4(xc, e);
+    const float xw = e == 0 ? left : f4(xc, e - 1);
+    const float xe = e == 3 ? right : f4(xc, e + 1);
+    float v = c[e][6] * xce;
+    v = fmaf(c[e][0], xw, v);
+    v = fmaf(c[e][1], xe, v);
+    v = fmaf(c[e][2], f4(sth, e), v);
+    v = fmaf(c[e][3], f4(nth, e), v);
+    v = fmaf(c[e][4], f4(xm, e), v);
+    v = fmaf(c[e][5], f4(xp, e), v);
+    y[e] = v;
+  }
+}
+
+// 1/D of node (i, j) in z class zcl (from the coefficient table).
+__device__ __forceinline__ float dinv_at(const Geo& g, const float* cb, int zcl, int i, int j) {
+  return cb[(((int64_t)zcl * g.ncy + g.cy[j]) * g.ncx + g.cx[i]) * kCoefStride + 7];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -414,6 +472,7 @@ __global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start)
     st->status = ns;
     st->relres = rel;
     if (ns != ST_ACTIVE) st->t_done = global_ns();
+    if (a.alpha) a.alpha[b] = 0.0;  // the fold applied any pending update
     a.rr_ref[b] = (rel * a.fnorm[b]) * (rel * a.fnorm[b]);
     if (ns == ST_ACTIVE) atomicAdd(a.active, 1);
     if (ns == ST_ACTIVE && mode == 2 && !start) st->restarts += 1;
@@ -467,6 +526,7 @@ __global__ void k_tune_prep(CGArgs<float> a) {
   if (i < a.B) {
     a.st[i].status = ST_ACTIVE;
     a.st[i].iters = 0;
+    if (a.alpha) a.alpha[i] = a.alpha[a.B + i] = 0.0;
   }
   if (i < nP) {
     a.rho_rr[i] = make_double2(1.0, 1e300);
@@ -481,6 +541,301 @@ void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s) {
 }
 
 size_t v4_plane_smem(Tile t) { return sizeof(float) * 3 * (size_t)(4 * t.tx + 8) * (t.ty + 2); }
+
+// ---------------------------------------------------------------------------
+// 32-byte schedule.  Phase A of iteration k (parity = k % 2):
+//   u += alpha_{k-1} p_{k-1}            (the update phase B deferred)
+//   p_k = D^{-1} r_k + beta_k p_{k-1}   (D^{-1} r formed on the fly, halo too)
+//   partial gamma_k = p_k . A p_k       (A p_k not stored)
+// reads r, p_old (+halo), u; writes p, u: 20 B per DoF.
+// Phase B: alpha_k = rho_k / gamma_k; r -= alpha_k A p_k (A p_k recomputed from
+// the staged p_k); partials rho_{k+1} = r.D^{-1}r, ||r||^2; reads r, p (+halo),
+// writes r: 12 B per DoF.  alpha_k goes to a.alpha[parity ^ 1][b]; an instance
+// that stops in phase A keeps its pending update, and records its parity in
+// InstState::pad for the reliable-update fold.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 3) k_cg_a32_v4(CGArgs<float> a, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  __shared__ double s_beta, s_alpha;
+  __shared__ int s_run;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const bool leader = ps.part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double2 cur = make_double2(0.0, 0.0);
+    double prev = 0.0;
+    if (status == ST_ACTIVE) {
+      cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      prev = sum_partials2(a.rho_rr + ((int64_t)(parity ^ 1) * a.B + b) * a.P, a.P, tid).x;
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double rel = sqrt(cur.y) / a.fnorm[b];
+        if (rel < a.tol || st->iters >= a.max_iters || !(rel == rel)) {
+          if (leader) {
+            st->status = rel < a.tol ? (a.ru ? ST_PAUSED : ST_CONVERGED)
+                                     : ((rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN);
+            st->relres = rel;
+            st->pad = parity;  // the update alpha[parity] * p_old is still pending
+            st->t_done = global_ns();
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_beta = cur.x / prev;
+          s_alpha = a.alpha[(int64_t)parity * a.B + b];
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const float beta = (float)s_beta, alpha = (float)s_alpha;
+  const Geo& g = a.g;
+  const int64_t off = (int64_t)b * g.n;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const float* rb = a.r + off;
+  const float* pold = (parity ? a.p1 : a.p0) + off;
+  float* pnew = (parity ? a.p0 : a.p1) + off;
+  float* ub = a.u + off;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  Plane pl{TXN + 8, 0};
+  pl.PS = pl.PW * (TY + 2);
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  const int oslot = pl.at(4 * (int)threadIdx.x, (int)threadIdx.y);
+  const Halo4 h = halo4(g, ps, pl, tid);
+  const int hi = ps.x0 + h.hx, hj = ps.y0 + h.hy;
+
+  float c[4][7];
+  int zcls_cur = -1;
+  auto coefs = [&](int z) {
+    const int zcl = g.cz[z];
+    if (zcl != zcls_cur && ps.own) {
+      zcls_cur = zcl;
+      load_coef4(g, cb, zcl, ps.i, ps.j, c);
+    }
+  };
+  float4 r_own, p_own, r_h, p_h;
+  auto fetch = [&](int z) {
+    const bool zin = z >= 0 && z < g.nz;
+    r_own = p_own = r_h = p_h = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zin && ps.own) {
+      r_own = ld4(rb + z * plane + col);
+      p_own = ld4(pold + z * plane + col);
+    }
+    if (zin && h.in) {
+      if (h.kind == 1) {
+        r_h = ld4(rb + z * plane + h.col);
+        p_h = ld4(pold + z * plane + h.col);
+      } else {
+        r_h.x = rb[z * plane + h.col];
+        p_h.x = pold[z * plane + h.col];
+      }
+    }
+  };
+  // p of plane z into a smem slot (needs the own 1/D of plane z); returns the own group
+  auto commit = [&](float* P, int z) -> float4 {
+    float4 sv = r_own;
+    if (jac && z < g.nz && ps.own) {
+      // own nodes: 1/D of plane z (the cached rows may belong to another z class)
+      const int zcl = g.cz[z];
+      sv = make_float4(r_own.x * dinv_at(g, cb, zcl, ps.i, ps.j), r_own.y * dinv_at(g, cb, zcl, ps.i + 1, ps.j),
+                       r_own.z * dinv_at(g, cb, zcl, ps.i + 2, ps.j), r_own.w * dinv_at(g, cb, zcl, ps.i + 3, ps.j));
+    }
+    const float4 v = fma4(beta, p_own, sv);
+    st4(P + oslot, v);
+    if (h.kind != 0) {
+      float4 sh = r_h;
+      if (jac && h.in && z < g.nz) {
+        const int zcl = g.cz[z];
+        if (h.kind == 1)
+          sh = make_float4(r_h.x * dinv_at(g, cb, zcl, hi, hj), r_h.y * dinv_at(g, cb, zcl, hi + 1, hj),
+                           r_h.z * dinv_at(g, cb, zcl, hi + 2, hj), r_h.w * dinv_at(g, cb, zcl, hi + 3, hj));
+        else
+          sh.x = r_h.x * dinv_at(g, cb, zcl, hi, hj);
+      }
+      if (h.kind == 1) st4(P + h.slot, fma4(beta, p_h, sh));
+      else P[h.slot] = fmaf(beta, p_h.x, sh.x);
+    }
+    return v;
+  };
+
+  const int z0 = ps.z0, z1 = ps.z1;
+  float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (z0 > 0 && ps.own) {
+    fetch(z0 - 1);
+    float4 sv = r_own;
+    if (jac) {
+      const int zcl = g.cz[z0 - 1];
+      sv = make_float4(r_own.x * dinv_at(g, cb, zcl, ps.i, ps.j), r_own.y * dinv_at(g, cb, zcl, ps.i + 1, ps.j),
+                       r_own.z * dinv_at(g, cb, zcl, ps.i + 2, ps.j), r_own.w * dinv_at(g, cb, zcl, ps.i + 3, ps.j));
+    }
+    xm = fma4(beta, p_own, sv);
+  }
+  fetch(z0);
+  float4 xc = commit(sm + (z0 % 3) * pl.PS, z0);
+  fetch(z0 + 1);
+  float gam = 0.f;
+  for (int z = z0; z < z1; ++z) {
+    // own u and p_old of plane z for the deferred update (in flight over the barrier)
+    float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f), po4 = u4;
+    if (ps.own) {
+      u4 = ld4(ub + z * plane + col);
+      po4 = ld4(pold + z * plane + col);
+    }
+    const float4 xp = commit(sm + ((z + 1) % 3) * pl.PS, z + 1);
+    fetch(z + 2);
+    __syncthreads();
+    coefs(z);
+    if (ps.own) {
+      float y[4];
+      stencil4(sm + (z % 3) * pl.PS, pl, oslot, c, xm, xc, xp, y);
+      gam = fmaf(xc.x, y[0], fmaf(xc.y, y[1], fmaf(xc.z, y[2], fmaf(xc.w, y[3], gam))));
+      st4(pnew + z * plane + col, xc);
+      st4(ub + z * plane + col, fma4(alpha, po4, u4));
+    }
+    xm = xc;
+    xc = xp;
+  }
+  double dg = (double)gam, dummy = 0.0;
+  block_sum2(dg, dummy, red);
+  if (tid == 0) a.gam[(int64_t)b * a.P + ps.part] = dg;
+}
+
+__global__ void __launch_bounds__(256, 3) k_cg_b32_v4(CGArgs<float> a, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  __shared__ double s_alpha;
+  __shared__ int s_run;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const bool leader = ps.part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double rho = 0.0, gam = 0.0, rr = 0.0;
+    if (status == ST_ACTIVE) {
+      const double2 cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      rho = cur.x;
+      rr = cur.y;
+      gam = sum_partials(a.gam + (int64_t)b * a.P, a.P, tid);
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double alpha = rho / gam;
+        if (!(gam > 0.0) || !(alpha == alpha) || alpha == INFINITY) {
+          if (leader) {
+            st->status = ST_BREAKDOWN;
+            st->relres = sqrt(rr) / a.fnorm[b];
+            st->pad = parity ^ 1;  // no valid alpha_k: nothing pending
+            a.alpha[(int64_t)(parity ^ 1) * a.B + b] = 0.0;
+            st->t_done = global_ns();
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_alpha = alpha;
+          if (leader) {
+            st->iters += 1;
+            a.alpha[(int64_t)(parity ^ 1) * a.B + b] = alpha;
+          }
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const float alpha = (float)s_alpha;
+  const Geo& g = a.g;
+  const int64_t off = (int64_t)b * g.n;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const float* pb = (parity ? a.p0 : a.p1) + off;
+  float* rb = a.r + off;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  Plane pl{TXN + 8, 0};
+  pl.PS = pl.PW * (TY + 2);
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  const int oslot = pl.at(4 * (int)threadIdx.x, (int)threadIdx.y);
+  const Halo4 h = halo4(g, ps, pl, tid);
+
+  float c[4][7];
+  float dinv[4] = {1.f, 1.f, 1.f, 1.f};
+  int zcls_cur = -1;
+  float4 p_own, p_h;
+  auto fetch = [&](int z) {
+    const bool zin = z >= 0 && z < g.nz;
+    p_own = p_h = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zin && ps.own) p_own = ld4(pb + z * plane + col);
+    if (zin && h.in) {
+      if (h.kind == 1) p_h = ld4(pb + z * plane + h.col);
+      else p_h.x = pb[z * plane + h.col];
+    }
+  };
+  auto commit = [&](float* P) -> float4 {
+    st4(P + oslot, p_own);
+    if (h.kind == 1) st4(P + h.slot, p_h);
+    else if (h.kind == 2) P[h.slot] = p_h.x;
+    return p_own;
+  };
+  const int z0 = ps.z0, z1 = ps.z1;
+  float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (z0 > 0 && ps.own) xm = ld4(pb + (z0 - 1) * plane + col);
+  fetch(z0);
+  float4 xc = commit(sm + (z0 % 3) * pl.PS);
+  fetch(z0 + 1);
+  float rho = 0.f, rr = 0.f;
+  for (int z = z0; z < z1; ++z) {
+    float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ps.own) r4 = ld4(rb + z * plane + col);  // in flight over the barrier
+    const float4 xp = commit(sm + ((z + 1) % 3) * pl.PS);
+    fetch(z + 2);
+    __syncthreads();
+    const int zcl = g.cz[z];
+    if (zcl != zcls_cur && ps.own) {
+      zcls_cur = zcl;
+      load_coef4(g, cb, zcl, ps.i, ps.j, c);
+#pragma unroll
+      for (int e = 0; e < 4; e++) dinv[e] = dinv_at(g, cb, zcl, ps.i + e, ps.j);
+    }
+    if (ps.own) {
+      float y[4];
+      stencil4(sm + (z % 3) * pl.PS, pl, oslot, c, xm, xc, xp, y);
+      const float4 rn = make_float4(fmaf(-alpha, y[0], r4.x), fmaf(-alpha, y[1], r4.y),
+                                    fmaf(-alpha, y[2], r4.z), fmaf(-alpha, y[3], r4.w));
+      st4(rb + z * plane + col, rn);
+      const float4 sv = jac ? make_float4(dinv[0] * rn.x, dinv[1] * rn.y, dinv[2] * rn.z, dinv[3] * rn.w) : rn;
+      rho = fmaf(rn.x, sv.x, fmaf(rn.y, sv.y, fmaf(rn.z, sv.z, fmaf(rn.w, sv.w, rho))));
+      rr = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, rr))));
+    }
+    xm = xc;
+    xc = xp;
+  }
+  double drho = (double)rho, drr = (double)rr;
+  block_sum2(drho, drr, red);
+  if (tid == 0) a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + ps.part] = make_double2(drho, drr);
+}
+
+void launch_cg_a32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
+  k_cg_a32_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), v4_plane_smem(t), s>>>(a, parity);
+}
+void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
+  k_cg_b32_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), v4_plane_smem(t), s>>>(a, parity);
+}
 
 void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
   k_cg_a_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), v4_plane_smem(t), s>>>(a, parity);
