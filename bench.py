@@ -383,14 +383,14 @@ def main():
         a_st_gbs = acc["active_dofs"] * alg_stencil / (acc["stencil_ms"] * 1e-3) / 1e9
         a_up_gbs = acc["active_dofs"] * alg_update / (acc["update_ms"] * 1e-3) / 1e9
         solver_gbs = acc["active_dofs"] * 6 * eb / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
-        tag = "cg_stencil_phase_%s_64cube" % ("f32_v4" if eb == 4 else "f64")
+        tag = "cg_stencil_phase_%s_64cube" % ("f32_tma" if eb == 4 else "f64")
         tpd = traffic_per_dof(tag)
         launch_dofs = acc["active_dofs"] / acc["samples"]
         res = {"bound": "hbm", "achieved": round(a_st_gbs, 1), "peak": peak, "unit": "GB/s",
                "frac": round(a_st_gbs / peak, 4), "peak_kind": peak_kind,
                "traffic": None if tpd is None else tpd * launch_dofs,
-               "kernel": ("k_cg_a_v4 (FP32, 4 nodes/thread: p = s + beta p, q = A p, p.q)" if eb == 4
-                          else "k_cg_a<double> (p = s + beta p, q = A p, p.q)"),
+               "kernel": ("k_cg_a_tma (FP32, TMA-staged planes, 4 nodes/thread: p = s + beta p, q = A p, p.q)"
+                          if eb == 4 else "k_cg_a<double> (p = s + beta p, q = A p, p.q)"),
                "algorithmic_bytes_per_dof": alg_stencil,
                "stencil_ms_per_launch": acc["stencil_ms"] / acc["samples"],
                "update_kernel_frac": round(a_up_gbs / peak, 4),

@@ -51,7 +51,7 @@ typedef enum {
   RBWS_ERR_CUDA = -3,
   RBWS_ERR_NO_BASIS = -4,      /* a reduced basis / surrogate is required first */
   RBWS_ERR_NOT_SPD = -5,       /* a reduced matrix failed its Cholesky factorisation */
-  RBWS_ERR_DEVICE_TIMEOUT = -6,
+  RBWS_ERR_DEVICE_TIMEOUT = -6, /* a bounded device-side wait ran out (no result) */
   RBWS_ERR_STATE = -7,
   RBWS_ERR_UNSUPPORTED = -8
 } rbws_status;
@@ -245,8 +245,9 @@ RBWS_API rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t 
 /* Autotuner of the FP32 PCG phase kernels for batches of B instances on this
  * problem's grid (needs nx % 4 == 0): times each candidate tile (4*tx x ty
  * nodes, tx in {32,16,8,4}, 64..256 threads), z-chunk (8..64 planes) and
- * iteration schedule (32 bytes per DoF: s formed on the fly, A p recomputed;
- * or 44 bytes per DoF: s and A p stored) on the GPU with CUDA events, and
+ * iteration schedule (0: 44 bytes per DoF with s and A p stored; 1: 32 bytes,
+ * s formed on the fly and A p recomputed; 2: schedule 0 with its stencil
+ * phase fed by TMA) on the GPU with CUDA events, and
  * keeps the fastest for later FP32_IR solves with B instances.  cache_path
  * (may be NULL): a text file of "grid/B/fp32 tx ty zc ms schedule" lines; a
  * matching line is used without timing, a new choice is appended.  Outputs

@@ -118,7 +118,7 @@ struct rbws_problem_s {
   struct Tuned {
     int tx, ty, zc;
     double ms;
-    int sched;  // 1: 32-byte schedule, 0: 44-byte schedule
+    int sched;  // 0: 44-byte schedule, 1: 32-byte schedule, 2: 44-byte with TMA stencil phase
   };
   std::map<int, Tuned> tuned32;  // batch size -> tuned FP32 tile
 
@@ -527,22 +527,37 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   float* coef32 = nullptr;
   CKI(coef_tables(p, d_mu, B, &coef64, &coef32));
   Tile t4 = choose_tile_v4(p->nx, p->ny);
-  // The 44-byte schedule is the default: its update phase is a pure stream
+  // Schedules: 0 = 44 bytes per DoF-iteration (s and A p stored), stencil
+  // phase with register prefetch; 2 = the same with the stencil phase fed by
+  // TMA (default where the tensor maps can be built); 1 = 32 bytes (s formed
+  // on the fly, A p recomputed).  The 44-byte update phase is a pure stream
   // (97% of HBM on the 64^3 workload) while both 32-byte phases are stencil
-  // kernels (about 45%); the autotuner picks the 32-byte one where it wins.
-  int zc_force = 0, sched32 = 0;
+  // kernels; the autotuner picks whichever is fastest.
+  int zc_force = 0, sched = 2;
   auto tu = p->tuned32.find(B);
   if (t4.tx > 0 && tu != p->tuned32.end()) {
     t4 = Tile{tu->second.tx, tu->second.ty};
     zc_force = tu->second.zc;
-    sched32 = tu->second.sched;
+    sched = tu->second.sched;
   }
   const bool v4 = t4.tx > 0;
-  if (!v4) sched32 = 0;
+  if (!v4) sched = 0;
   const Tile t = v4 ? t4 : choose_tile(p->nx);
+  if (sched == 2 && !tma_supported(p->geo, t)) sched = 0;
+  if (sched == 2) tma_prepare();
+  const int sched32 = sched == 1;
+  int* tma_err = nullptr;
+  {
+    int e2 = 0;
+    tma_err = (int*)p->buf("tma_err", sizeof(int), &e2);
+    if (e2) return (rbws_status)e2;
+    CK(cudaMemsetAsync(tma_err, 0, sizeof(int), p->cur));
+  }
   auto phase_a = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
-    if (sched32) launch_cg_a32_v4(aa, t, par, ss);
-    else if (v4) launch_cg_a_v4(aa, t, par, ss);
+    if (sched == 1) launch_cg_a32_v4(aa, t, par, ss);
+    else if (sched == 2) {
+      if (launch_cg_a_tma(aa, t, par, tma_err, ss)) launch_cg_a_v4(aa, t, par, ss);
+    } else if (v4) launch_cg_a_v4(aa, t, par, ss);
     else launch_cg_a<float>(aa, t, par, ss);
   };
   auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
@@ -668,6 +683,15 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (rc != RBWS_OK) return rc;
+  {
+    int terr = 0;
+    CK(cudaMemcpyAsync(&terr, tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (terr) {
+      set_error("a TMA stage wait ran out of time in the FP32 stencil phase");
+      return RBWS_ERR_DEVICE_TIMEOUT;
+    }
+  }
   // instances stopped by max_iters or breakdown still hold a correction in d
   std::vector<InstState> h(B);
   CK(cudaMemcpyAsync(h.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
@@ -1618,6 +1642,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
   float* d = (float*)p->buf("ir_d", sizeof(float) * (size_t)B * p->n, &err);
   if (err) return (rbws_status)err;
   rbws_problem_s::Tuned best{0, 0, 0, 1e30, 0};
+  (void)0;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1651,12 +1676,21 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
           return (rbws_status)err;
         }
         a.alpha = alpha;
-        for (int sched = 0; sched < 2; sched++) {
+        int* terr = (int*)p->buf("tma_err", sizeof(int), &err);
+        if (err) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return (rbws_status)err;
+        }
+        tma_prepare();
+        for (int sched = 0; sched < 3; sched++) {
+          if (sched == 2 && !tma_supported(p->geo, Tile{tx, ty})) continue;
           float ta = 0.f, tb = 0.f;
           for (int rep = 0; rep < 3; rep++) {
             launch_tune_prep(a, s);
             cudaEventRecord(e0, s);
-            if (sched) launch_cg_a32_v4(a, Tile{tx, ty}, 0, s);
+            if (sched == 1) launch_cg_a32_v4(a, Tile{tx, ty}, 0, s);
+            else if (sched == 2) launch_cg_a_tma(a, Tile{tx, ty}, 0, terr, s);
             else launch_cg_a_v4(a, Tile{tx, ty}, 0, s);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
@@ -1664,7 +1698,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
             cudaEventElapsedTime(&t1, e0, e1);
             launch_tune_prep(a, s);
             cudaEventRecord(e0, s);
-            if (sched) launch_cg_b32_v4(a, Tile{tx, ty}, 0, s);
+            if (sched == 1) launch_cg_b32_v4(a, Tile{tx, ty}, 0, s);
             else launch_cg_b_v4(a, Tile{tx, ty}, 0, s);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);

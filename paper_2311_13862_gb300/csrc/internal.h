@@ -158,6 +158,12 @@ void launch_ru_reset_v4(const CGArgs<float>& a, Tile t, int start, cudaStream_t 
 // r, p (halo) and writes r (A p recomputed); 32 B per DoF and iteration.
 void launch_cg_a32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
 void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
+// TMA-fed FP32 stencil phase (stencil_tma.cu): same result as
+// launch_cg_a_v4.  Returns -1 if the tensor maps cannot be built.
+bool tma_supported(const Geo& g, Tile t);
+size_t tma_smem_bytes(Tile t);
+int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s);
+void tma_prepare();  // kernel attributes; call outside stream capture
 // Autotuning: puts every instance in a runnable state with benign scalars
 // (status ACTIVE, rho = 1, ||r||^2 huge, gamma = 1) so one phase kernel can be timed.
 void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s);

@@ -1,0 +1,339 @@
+// stencil_tma.cu -- FP32 PCG stencil phase fed by the Tensor Memory Accelerator.
+//
+// Same arithmetic as k_cg_a_v4 (p = s + beta p_old, q = A p, partial p.q), but
+// the (s, p_old) tiles of each z plane -- a (4*tx + 8) x (ty + 2) box that
+// includes the x/y halo -- are copied into a ring of kStages shared-memory
+// stages by cp.async.bulk.tensor, issued by one thread and completed on one
+// mbarrier per stage.  Up to kStages planes are in flight per CTA without
+// holding registers, and the tensor map's zero fill supplies the Dirichlet
+// halo at the domain faces (boxes may start at x = -4, y = -1, z = -1; x
+// starts stay 16-byte aligned because tiles start at multiples of 4 nodes).
+// p at the neighbours is formed from the staged s and p_old when it is read.
+//
+// Every mbarrier wait is bounded (about 2 s of clock64 time).  A CTA whose
+// wait runs out sets *err, lets its outstanding copies land (again bounded)
+// and returns; the host reports RBWS_ERR_DEVICE_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rbws {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false if it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ double warp_sum_down(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double2 sum_partials2(const double2* part, int P, int lane) {
+  double x = 0.0, y = 0.0;
+  for (int c = lane; c < P; c += 32) {
+    double2 v = part[c];
+    x += v.x;
+    y += v.y;
+  }
+  return make_double2(warp_sum_down(x), warp_sum_down(y));
+}
+
+__device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float f4(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256, 3)
+    k_cg_a_tma(const __grid_constant__ CUtensorMap tm_s, const __grid_constant__ CUtensorMap tm_p0,
+               const __grid_constant__ CUtensorMap tm_p1, CGArgs<float> a, int parity, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ double red[64];
+  __shared__ double s_beta;
+  __shared__ int s_run;
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tiles_x = a.tiles_x;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  const int x0 = (blockIdx.x % tiles_x) * TXN, y0 = (blockIdx.x / tiles_x) * TY;
+  const int z0 = blockIdx.y * a.zc, z1 = min(a.g.nz, z0 + a.zc);
+  const int part = blockIdx.y * gridDim.x + blockIdx.x;
+  const bool leader = part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double2 cur = make_double2(0.0, 0.0);
+    double prev = 0.0;
+    if (status == ST_ACTIVE) {
+      cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      prev = sum_partials2(a.rho_rr + ((int64_t)(parity ^ 1) * a.B + b) * a.P, a.P, tid).x;
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE) {
+        const double rel = sqrt(cur.y) / a.fnorm[b];
+        if (rel < a.tol) {
+          if (leader) {
+            st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
+            st->relres = rel;
+            st->t_done = global_ns();
+            atomicSub(a.active, 1);
+          }
+        } else if (st->iters >= a.max_iters || !(rel == rel)) {
+          if (leader) {
+            st->status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
+            st->relres = rel;
+            st->t_done = global_ns();
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_beta = cur.x / prev;
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const float beta = (float)s_beta;
+  const Geo& g = a.g;
+  const int BX = TXN + 8, BY = TY + 2;
+  const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float));
+  const int arr_floats = ((BX * BY * 4 + 127) / 128) * 32;  // 128-byte aligned arrays
+  float* stage_base = reinterpret_cast<float*>(smem_raw);
+  auto s_tile = [&](int st) { return stage_base + (2 * st) * arr_floats; };
+  auto p_tile = [&](int st) { return stage_base + (2 * st + 1) * arr_floats; };
+  const CUtensorMap* mp = parity ? &tm_p1 : &tm_p0;
+  const int nq = z1 - z0 + 2;  // planes z0-1 .. z1
+  auto issue = [&](int j) {    // plane z0-1+j into stage j % kStages (thread 0 only)
+    const int st = j % kStages;
+    mbar_expect_tx(&bars[st], 2 * box_bytes);
+    tma_load_4d(s_tile(st), &tm_s, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+    tma_load_4d(p_tile(st), mp, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+  };
+  if (tid == 0) {
+    for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int n_issued = 0;  // meaningful in thread 0 only
+  int next_wait = 0; // first plane index not yet waited for (uniform)
+  if (tid == 0)
+    for (int j = 0; j < kStages && j < nq; j++) {
+      issue(j);
+      n_issued = j + 1;
+    }
+
+  const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
+  const int i = x0 + lx, jn = y0 + ly;
+  const bool own = i < g.nx && jn < g.ny;
+  const int cofs = (ly + 1) * BX + lx + 4;  // own group in a box
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)jn * g.nx + i;
+  float* pnew = (parity ? a.p0 : a.p1) + (int64_t)b * g.n;
+  float* qb = a.q + (int64_t)b * g.n;
+  auto own_p = [&](int st) { return fma4(beta, ld4s(p_tile(st) + cofs), ld4s(s_tile(st) + cofs)); };
+
+  // prologue: planes z0-1 (own column only) and z0
+  bool timed_out = !mbar_wait(&bars[0], 0);
+  float4 xm = own_p(0);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  float4 xc = own_p(1 % kStages);
+  if (__syncthreads_or(timed_out)) goto abort;
+  next_wait = 2;
+  if (tid == 0 && kStages < nq) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(kStages);  // stage 0 is free again
+    n_issued = kStages + 1;
+  }
+  {
+    float c[4][7];
+    int zcls_cur = -1;
+    float gam = 0.f;
+    for (int z = z0; z < z1; ++z) {
+      const int k = z - z0 + 1;  // index of plane z; plane z+1 is k+1
+      const int sk = k % kStages, sn = (k + 1) % kStages;
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      if (!to && own) {
+        const float4 xp = own_p(sn);
+        const int zcl = g.cz[z];
+        if (zcl != zcls_cur) {
+          zcls_cur = zcl;
+          const int yc = (int)g.cy[jn];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+#pragma unroll
+            for (int m = 0; m < 7; m++) c[e][m] = row[m];
+          }
+        }
+        const float* S = s_tile(sk);
+        const float* Pp = p_tile(sk);
+        const float left = fmaf(beta, Pp[cofs - 1], S[cofs - 1]);
+        const float right = fmaf(beta, Pp[cofs + 4], S[cofs + 4]);
+        const float4 sth = fma4(beta, ld4s(Pp + cofs - BX), ld4s(S + cofs - BX));
+        const float4 nth = fma4(beta, ld4s(Pp + cofs + BX), ld4s(S + cofs + BX));
+        float y[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float xce = f4(xc, e);
+          const float xw = e == 0 ? left : f4(xc, e - 1);
+          const float xe = e == 3 ? right : f4(xc, e + 1);
+          float v = c[e][6] * xce;
+          v = fmaf(c[e][0], xw, v);
+          v = fmaf(c[e][1], xe, v);
+          v = fmaf(c[e][2], f4(sth, e), v);
+          v = fmaf(c[e][3], f4(nth, e), v);
+          v = fmaf(c[e][4], f4(xm, e), v);
+          v = fmaf(c[e][5], f4(xp, e), v);
+          y[e] = v;
+          gam = fmaf(xce, v, gam);
+        }
+        *reinterpret_cast<float4*>(pnew + z * plane + col) = xc;
+        *reinterpret_cast<float4*>(qb + z * plane + col) = make_float4(y[0], y[1], y[2], y[3]);
+        xm = xc;
+        xc = xp;
+      } else if (!to) {
+        xm = xc;
+        xc = own_p(sn);
+      }
+      if (__syncthreads_or(to)) goto abort;
+      next_wait = k + 2;
+      // plane z's stage is free: refill it with plane index k + kStages
+      if (tid == 0 && k + kStages < nq) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k + kStages);
+        n_issued = k + kStages + 1;
+      }
+    }
+    double dg = (double)gam, dummy = 0.0;
+    // deterministic block sum (same tree as the other kernels)
+    const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+    dg = warp_sum_down(dg);
+    if (lane == 0) red[warp] = dg;
+    __syncthreads();
+    if (warp == 0) {
+      double x = lane < nw ? red[lane] : 0.0;
+      x = warp_sum_down(x);
+      if (lane == 0) a.gam[(int64_t)b * a.P + part] = x;
+    }
+    (void)dummy;
+  }
+  return;
+abort:
+  // a wait ran out: flag it and let the copies already issued land before returning
+  if (tid == 0) {
+    atomicExch(err, 1);
+    // copies issued for planes next_wait .. n_issued-1 may still be landing
+    for (int j = next_wait; j < n_issued; j++) mbar_wait(&bars[j % kStages], (j / kStages) & 1);
+  }
+  __syncthreads();
+}
+
+// Host side: tensor maps over [B][nz][ny][nx] float arrays with a box of
+// (4*tx + 8) x (ty + 2) x 1 x 1 and zero fill outside the tensor.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+static int make_map(CUtensorMap* m, const float* base, const Geo& g, int B, Tile t) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return -1;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)g.n * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)(4 * t.tx + 8), (cuuint32_t)(t.ty + 2), 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+size_t tma_smem_bytes(Tile t) {
+  const int BX = 4 * t.tx + 8, BY = t.ty + 2;
+  const size_t arr = (size_t)((BX * BY * 4 + 127) / 128) * 128;
+  return 2 * kStages * arr + 128;
+}
+
+bool tma_supported(const Geo& g, Tile t) {
+  return encode_fn() != nullptr && g.nx % 4 == 0 && 4 * t.tx + 8 <= 256 && t.ty + 2 <= 256 &&
+         tma_smem_bytes(t) <= 200 * 1024;
+}
+
+// Once per process and device, outside any stream capture.
+void tma_prepare() {
+  cudaFuncSetAttribute(k_cg_a_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
+  CUtensorMap ms, m0, m1;
+  const float* sarr = a.precond != RBWS_PREC_NONE ? a.s : a.r;
+  if (make_map(&ms, sarr, a.g, a.B, t) || make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t))
+    return -1;
+  const size_t smem = tma_smem_bytes(t);
+  k_cg_a_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), smem, s>>>(ms, m0, m1, a, parity, err);
+  return 0;
+}
+
+}  // namespace rbws
