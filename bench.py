@@ -285,9 +285,9 @@ def main():
     u = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
     prec = {"fp32ir": rbws.FP32_IR, "fp64": rbws.FP64}
 
-    def run(warm, precision, steps, warmup, profile=False):
+    def run(warm, precision, steps, warmup, profile=False, precond=rbws.PREC_JACOBI):
         prof = rbws.rbws_profile()
-        o = rbws.rbws_options_default(precision=precision, stream=stream.cuda_stream)
+        o = rbws.rbws_options_default(precision=precision, stream=stream.cuda_stream, precond=precond)
         out = None
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -364,38 +364,68 @@ def main():
                    "epochs": args.mlp_epochs, "hidden": 256}
         arm_list += [("learned_" + args.precision, rbws.WARM_LEARNED, headline),
                      ("learned_corrected_" + args.precision, rbws.WARM_LEARNED_CORRECTED, headline)]
+    if args.arm_steps > 0:
+        # the RB-preconditioned start: Galerkin start, then PCG with the MSRB preconditioner
+        # (Algorithm 3, FP64 only)
+        arm_list.append(("msrb_fp64", rbws.WARM_GALERKIN, rbws.FP64))
     for name, warm, pr in arm_list:
         if name.startswith("galerkin_" + args.precision):
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
         else:
-            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1)
+            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1,
+                                             precond=rbws.PREC_MSRB if name == "msrb_fp64" else rbws.PREC_JACOBI)
         arms[name] = {"solves_per_s": B * world / (a_ms / 1e3), "ms_per_step": a_ms,
                       "iters_mean": float(np.mean(a_it)), "iters_max": int(np.max(a_it)),
                       "relres_max": float(np.max(a_rel)), "all_converged": bool(np.all(a_st == 0))}
 
-    # ---- roofline of the dominant kernel (stencil phase of the PCG iteration) ----
+    # ---- roofline of the dominant kernel, with the stencil phase beside it ----
     peak, peak_kind = peaks()
     eb = acc["elem_bytes"] or 8
-    alg_stencil = 4 * eb   # reads s, p_old; writes p, q
-    alg_update = 7 * eb    # reads u, p, r, q; writes u, r, s
+    alg_stencil = 4 * eb   # stencil phase: reads s, p_old; writes p, q
+    alg_update = 7 * eb    # update phase: reads u, p, r, q; writes u, r, s
     res = {}
     if acc["samples"] > 0:
-        a_st_gbs = acc["active_dofs"] * alg_stencil / (acc["stencil_ms"] * 1e-3) / 1e9
-        a_up_gbs = acc["active_dofs"] * alg_update / (acc["update_ms"] * 1e-3) / 1e9
-        solver_gbs = acc["active_dofs"] * 6 * eb / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
-        tag = "cg_stencil_phase_%s_64cube" % ("f32_tma" if eb == 4 else "f64")
-        tpd = traffic_per_dof(tag)
         launch_dofs = acc["active_dofs"] / acc["samples"]
-        res = {"bound": "hbm", "achieved": round(a_st_gbs, 1), "peak": peak, "unit": "GB/s",
-               "frac": round(a_st_gbs / peak, 4), "peak_kind": peak_kind,
-               "traffic": None if tpd is None else tpd * launch_dofs,
-               "kernel": ("k_cg_a_tma (FP32, TMA-staged planes, 4 nodes/thread: p = s + beta p, q = A p, p.q)"
-                          if eb == 4 else "k_cg_a<double> (p = s + beta p, q = A p, p.q)"),
-               "algorithmic_bytes_per_dof": alg_stencil,
-               "stencil_ms_per_launch": acc["stencil_ms"] / acc["samples"],
-               "update_kernel_frac": round(a_up_gbs / peak, 4),
-               "solver_frac_minimal_bytes": round(solver_gbs / peak, 4),
-               "sampled_launches": acc["samples"]}
+        st_gbs = acc["active_dofs"] * alg_stencil / (acc["stencil_ms"] * 1e-3) / 1e9
+        up_gbs = acc["active_dofs"] * alg_update / (acc["update_ms"] * 1e-3) / 1e9
+        solver_gbs = acc["active_dofs"] * 6 * eb / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
+        f32 = eb == 4
+        st_name = ("k_cg_a_tma (FP32 stencil phase, TMA-staged planes: p = s + beta p, q = A p, p.q)" if f32
+                   else "k_cg_a<double> (FP64 stencil phase)")
+        up_name = ("k_cg_b_v4 (FP32 update phase: u += alpha p, r -= alpha q, s = D^-1 r, r.s, r.r)" if f32
+                   else "k_cg_b<double> (FP64 update phase)")
+        st_t = traffic_per_dof("cg_stencil_phase_f32_tma_64cube" if f32 else "cg_phases_f64_64cube_a")
+        up_t = traffic_per_dof("cg_update_phase_f32_v4_64cube" if f32 else "cg_phases_f64_64cube_b")
+        stencil = {"kernel": st_name, "achieved": round(st_gbs, 1), "frac": round(st_gbs / peak, 4),
+                   "algorithmic_bytes_per_dof": alg_stencil, "ms_per_launch": acc["stencil_ms"] / acc["samples"],
+                   "traffic": None if st_t is None else st_t * launch_dofs}
+        update = {"kernel": up_name, "achieved": round(up_gbs, 1), "frac": round(up_gbs / peak, 4),
+                  "algorithmic_bytes_per_dof": alg_update, "ms_per_launch": acc["update_ms"] / acc["samples"],
+                  "traffic": None if up_t is None else up_t * launch_dofs}
+        dom = update if acc["update_ms"] >= acc["stencil_ms"] else stencil
+        if not f32:
+            # FP64 kernels are bound by GB300's FP64 issue rate, not HBM: report them against the
+            # FP64 FMA peak (1.25 TFLOP/s nominal; 1.196 measured on this machine's GB300 by a
+            # dependent-free DFMA loop).  Flops per DoF: stencil phase 17 (p update 2, stencil
+            # 13, p.q 2), update phase 9 (u 2, r 2, s 1, r.s 2, r.r 2).
+            fp64_peak = 1196.0
+            st_gf = acc["active_dofs"] * 17 / (acc["stencil_ms"] * 1e-3) / 1e9
+            up_gf = acc["active_dofs"] * 9 / (acc["update_ms"] * 1e-3) / 1e9
+            dom_gf = up_gf if dom is update else st_gf
+            res = {"bound": "alu", "achieved": round(dom_gf, 1), "peak": fp64_peak, "unit": "GFLOP/s",
+                   "frac": round(dom_gf / fp64_peak, 4), "traffic": dom["traffic"], "kernel": dom["kernel"],
+                   "peak_kind": "FP64 FMA loop measured on GB300 (no MEASURED_PEAKS entry for FP64)",
+                   "stencil_phase_gflops": round(st_gf, 1), "update_phase_gflops": round(up_gf, 1),
+                   "hbm_stencil_phase": stencil, "hbm_update_phase": update, "sampled_launches": acc["samples"]}
+            dom = None
+    if acc["samples"] > 0 and dom is not None:
+        res = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
+               "traffic": dom["traffic"], "kernel": dom["kernel"], "peak_kind": peak_kind,
+               "algorithmic_bytes_per_dof": dom["algorithmic_bytes_per_dof"],
+               "dominant_share": round(max(acc["update_ms"], acc["stencil_ms"]) /
+                                       (acc["update_ms"] + acc["stencil_ms"]), 3),
+               "stencil_phase": stencil, "update_phase": update,
+               "solver_frac_minimal_bytes": round(solver_gbs / peak, 4), "sampled_launches": acc["samples"]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -61,3 +61,28 @@ def test_autotune_picks_a_valid_tile_and_caches_it(tmp_path):
         uh = u.cpu().numpy()
     for b in range(8):
         assert np.linalg.norm(np.ones(op.n) - op.matvec(mu[b], uh[b])) / np.sqrt(op.n) < 1e-10
+
+
+@pytest.mark.parametrize("sched", [0, 1, 2])
+def test_each_fp32_schedule_reaches_the_fp64_residual(tmp_path, sched):
+    """Forces each FP32 iteration schedule through an autotuner cache entry (0: 44 bytes per
+    DoF with register prefetch, 1: 32 bytes with recomputed A p, 2: 44 bytes with the TMA-fed
+    stencil phase) and checks the solutions with the oracle's FP64 operator."""
+    grid, blocks = (64, 40, 36), (2, 2, 1)
+    op = O.assemble(grid, blocks)
+    B = 6
+    mu = inputs.log_uniform(93, B, 4, 0.1, 10.0)
+    cache = tmp_path / "tiles.txt"
+    cache.write_text("%dx%dx%d/B%d/fp32 16 8 16 1.0 %d\n" % (grid + (B, sched)))
+    with rbws.Problem(grid, blocks) as P:
+        assert rbws.rbws_autotune(P.h, B, cache)[:3] == (16, 8, 16)
+        u = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
+        rc, it, rel, st = rbws.rbws_solve_batch(P.h, mu, 1e-10, rbws.WARM_ZERO, u,
+                                                rbws.rbws_options_default(precision=rbws.FP32_IR))
+        assert rc == 0 and np.all(st == 0)
+        uh = u.cpu().numpy()
+    ref = O.solve_batch(op, mu, warm=O.WARM_ZERO, tol=1e-13)
+    for b in range(B):
+        assert np.linalg.norm(np.ones(op.n) - op.matvec(mu[b], uh[b])) / np.sqrt(op.n) < 1e-10
+    assert np.all(np.linalg.norm(uh - ref.u, axis=1) / np.linalg.norm(ref.u, axis=1) < 1e-8)
+    print("schedule", sched, "iterations", it.tolist())

@@ -64,3 +64,31 @@ def test_grid_96_with_27_blocks():
             uh = u.cpu().numpy()
             for b in (0, 7, 15):
                 assert true_relres(op, mu[b], uh[b]) < w.tol
+
+
+def test_plain_method_16cube_two_halves():
+    """The plain method at 16^3: greedy RB (N <= 10) over 64 training parameters, then 8 test
+    parameters solved by plain CG (no preconditioner) to rel-res 1e-12 from zero and from the
+    RB warm start, against the oracle doing the same."""
+    w = inputs.WORKLOADS["c1"]
+    op = O.assemble(w.grid, w.blocks)
+    ref_basis = O.greedy(op, inputs.train_mu(w), w.n_max)
+    mu = inputs.test_mu(w)
+    opt = rbws.rbws_options_default(precond=rbws.PREC_NONE)
+    with rbws.Problem(w.grid, w.blocks) as P:
+        N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
+        assert N == ref_basis.N
+        u = torch.empty((len(mu), P.n), dtype=torch.float64, device="cuda")
+        res = {}
+        for name, warm in [("zero", rbws.WARM_ZERO), ("warm", rbws.WARM_GALERKIN)]:
+            rc, it, rel, st = rbws.rbws_solve_batch(P.h, mu, w.tol, warm, u, opt)
+            assert rc == 0 and np.all(st == 0)
+            res[name] = (it, u.cpu().numpy())
+    z = O.solve_batch(op, mu, warm=O.WARM_ZERO, precond=O.PREC_NONE, tol=w.tol)
+    g = O.solve_batch(op, mu, warm=O.WARM_GALERKIN, basis=ref_basis, precond=O.PREC_NONE, tol=w.tol)
+    assert np.all(np.abs(res["zero"][0] - z.iters) <= 2)
+    assert np.all(np.abs(res["warm"][0] - g.iters) <= 2)
+    for (it, u), ref in ((res["zero"], z), (res["warm"], g)):
+        assert np.all(np.linalg.norm(u - ref.u, axis=1) / np.linalg.norm(ref.u, axis=1) <= 1e-10)
+    assert res["warm"][0].mean() < res["zero"][0].mean()
+    print("16^3 plain CG iterations: zero", res["zero"][0].tolist(), "warm", res["warm"][0].tolist())
