@@ -180,7 +180,7 @@ def bench_requests(args):
         t2 = time.perf_counter()
         tile = rbws.rbws_autotune(P.h, 32)
         offline[nm] = {"N": N, "greedy_s": t1 - t0, "train_s": t2 - t1, "train_loss": loss,
-                       "eta_last": float(eta[-1]), "tile": tile[:3], "tile_pair_ms": tile[3]}
+                       "eta_last": float(eta[-1]), "tile": tile[:3], "schedule": tile[4], "tile_pair_ms": tile[3]}
         probs.append((w, P))
     order = [k % 3 for k in range(96)]  # 96^3, 128^3, 256^3, 96^3, ...
     mus = [None] * 96
@@ -241,6 +241,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
                     help="c2: the 64^3 batched workload (default line); c5: 96 requests on 96^3/128^3/256^3")
     ap.add_argument("--c5-train", type=int, default=256, help="greedy training parameters per grid (c5)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the built-in FP32 tile/schedule instead of the autotuned one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -281,6 +283,11 @@ def main():
     torch.cuda.synchronize()
     t_off = time.perf_counter() - t0
 
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tx, ty, zc, pair_ms, sched = rbws.rbws_autotune(P.h, B)
+        tuned = {"tile": [tx, ty, zc], "schedule": sched, "pair_ms": pair_ms, "tune_s": time.perf_counter() - t0}
     stream = torch.cuda.Stream()
     u = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
     prec = {"fp32ir": rbws.FP32_IR, "fp64": rbws.FP64}
@@ -298,6 +305,7 @@ def main():
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             acc = {"launches": 0, "samples": 0, "stencil_ms": 0.0, "update_ms": 0.0, "active_dofs": 0.0}
+            acc_schedule = None
             torch.cuda.nvtx.range_push("timed")
             e0.record(stream)
             for _ in range(steps):
@@ -305,6 +313,7 @@ def main():
                 if profile:
                     for k in acc:
                         acc[k] += getattr(prof, k)
+                    acc_schedule = prof.schedule
             e1.record(stream)
             torch.cuda.nvtx.range_pop()
             barrier()
@@ -315,6 +324,7 @@ def main():
             ms = float(t.item())
         rc, it, rel, st = out
         acc["elem_bytes"] = prof.elem_bytes
+        acc["schedule"] = acc_schedule
         return ms, it, rel, st, acc
 
     headline = prec[args.precision]
@@ -381,21 +391,35 @@ def main():
     # ---- roofline of the dominant kernel, with the stencil phase beside it ----
     peak, peak_kind = peaks()
     eb = acc["elem_bytes"] or 8
-    alg_stencil = 4 * eb   # stencil phase: reads s, p_old; writes p, q
-    alg_update = 7 * eb    # update phase: reads u, p, r, q; writes u, r, s
+    sched = acc.get("schedule")
+    f32 = eb == 4
+    # kernels of each schedule: (stencil-phase name, bytes/DoF, profile tag), (update-phase ...)
+    kernels = {
+        -1: (("k_cg_a<float> (one node per thread)", 16, None), ("k_cg_b<float>", 28, None)),
+        0: (("k_cg_a_v4 (register prefetch: p = s + beta p, q = A p, p.q)", 16, None),
+            ("k_cg_b_v4 (u += alpha p, r -= alpha q, s = D^-1 r, r.s, r.r)", 28, "cg_update_phase_f32_v4_64cube")),
+        1: (("k_cg_a32_v4 (u += alpha' p_old, p = D^-1 r + beta p, p.A p)", 20, None),
+            ("k_cg_b32_v4 (r -= alpha A p recomputed, r.s, r.r)", 12, None)),
+        2: (("k_cg_a_tma (TMA-staged planes: p = s + beta p, q = A p, p.q)", 16, "cg_stencil_phase_f32_tma_64cube"),
+            ("k_cg_b_v4 (u += alpha p, r -= alpha q, s = D^-1 r, r.s, r.r)", 28, "cg_update_phase_f32_v4_64cube")),
+        3: (("k_cg_a_tma<1> (TMA-staged: u += alpha' p_old, p = s + beta p, p.A p)", 20,
+             "cg_stencil_phase_f32_stma_64cube"),
+            ("k_cg_b_s_tma (TMA-staged: s -= alpha D^-1 A p, r = D s, r.s, r.r)", 12, "cg_update_phase_f32_stma_64cube")),
+    }
+    if f32:
+        (st_name, alg_stencil, st_tag), (up_name, alg_update, up_tag) = kernels[sched if sched in kernels else -1]
+    else:
+        st_name, alg_stencil, st_tag = "k_cg_a<double> (FP64 stencil phase)", 32, None
+        up_name, alg_update, up_tag = "k_cg_b<double> (FP64 update phase)", 56, None
+    minimal = 6 * eb  # u, r, p read and written once per iteration
     res = {}
     if acc["samples"] > 0:
         launch_dofs = acc["active_dofs"] / acc["samples"]
         st_gbs = acc["active_dofs"] * alg_stencil / (acc["stencil_ms"] * 1e-3) / 1e9
         up_gbs = acc["active_dofs"] * alg_update / (acc["update_ms"] * 1e-3) / 1e9
-        solver_gbs = acc["active_dofs"] * 6 * eb / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
-        f32 = eb == 4
-        st_name = ("k_cg_a_tma (FP32 stencil phase, TMA-staged planes: p = s + beta p, q = A p, p.q)" if f32
-                   else "k_cg_a<double> (FP64 stencil phase)")
-        up_name = ("k_cg_b_v4 (FP32 update phase: u += alpha p, r -= alpha q, s = D^-1 r, r.s, r.r)" if f32
-                   else "k_cg_b<double> (FP64 update phase)")
-        st_t = traffic_per_dof("cg_stencil_phase_f32_tma_64cube" if f32 else "cg_phases_f64_64cube_a")
-        up_t = traffic_per_dof("cg_update_phase_f32_v4_64cube" if f32 else "cg_phases_f64_64cube_b")
+        solver_gbs = acc["active_dofs"] * minimal / ((acc["stencil_ms"] + acc["update_ms"]) * 1e-3) / 1e9
+        st_t = traffic_per_dof(st_tag) if st_tag else None
+        up_t = traffic_per_dof(up_tag) if up_tag else None
         stencil = {"kernel": st_name, "achieved": round(st_gbs, 1), "frac": round(st_gbs / peak, 4),
                    "algorithmic_bytes_per_dof": alg_stencil, "ms_per_launch": acc["stencil_ms"] / acc["samples"],
                    "traffic": None if st_t is None else st_t * launch_dofs}
@@ -420,7 +444,7 @@ def main():
             dom = None
     if acc["samples"] > 0 and dom is not None:
         res = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
-               "traffic": dom["traffic"], "kernel": dom["kernel"], "peak_kind": peak_kind,
+               "traffic": dom["traffic"], "kernel": dom["kernel"], "peak_kind": peak_kind, "schedule": sched,
                "algorithmic_bytes_per_dof": dom["algorithmic_bytes_per_dof"],
                "dominant_share": round(max(acc["update_ms"], acc["stencil_ms"]) /
                                        (acc["update_ms"] + acc["stencil_ms"]), 3),
@@ -440,7 +464,7 @@ def main():
             "e2e": {"value": B * world / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(B * w.Q * 8),
                     "d2h_bytes_per_step": int(B * P.n * 8 + B * (4 + 8 + 4))},
-            "arms": arms, "learned_training": learned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "arms": arms, "learned_training": learned, "autotune": tuned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
             "iters_mean": float(np.mean(it)), "relres_max": float(np.max(rel))}
     if "zero_fp64" in arms:
         line["speedup_vs_zero_fp64"] = value / arms["zero_fp64"]["solves_per_s"]

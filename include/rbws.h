@@ -95,7 +95,8 @@ typedef struct {
   double update_ms;    /* summed durations of the sampled update-phase launches      */
   double active_dofs;  /* summed (active instances x n_dof) over the sampled launches */
   int32_t elem_bytes;  /* 8: FP64 CG kernels were sampled; 4: FP32 inner kernels     */
-  int32_t pad;
+  int32_t schedule;    /* FP32 kernels: -1 one node per thread, else the autotuner's
+                          schedule (0..3, see rbws_autotune); -1 for FP64            */
 } rbws_profile;
 
 typedef struct {
@@ -247,14 +248,16 @@ RBWS_API rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t 
  * nodes, tx in {32,16,8,4}, 64..256 threads), z-chunk (8..64 planes) and
  * iteration schedule (0: 44 bytes per DoF with s and A p stored; 1: 32 bytes,
  * s formed on the fly and A p recomputed; 2: schedule 0 with its stencil
- * phase fed by TMA) on the GPU with CUDA events, and
+ * phase fed by TMA; 3: 32 bytes with s = D^{-1} r stored and both phases fed
+ * by TMA) on the GPU with CUDA events, and
  * keeps the fastest for later FP32_IR solves with B instances.  cache_path
  * (may be NULL): a text file of "grid/B/fp32 tx ty zc ms schedule" lines; a
  * matching line is used without timing, a new choice is appended.  Outputs
  * (may be NULL): the chosen tile, chunk and the mean time in ms of one
  * stencil-phase plus update-phase pair. */
 RBWS_API rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int32_t* tx_out,
-                                   int32_t* ty_out, int32_t* zc_out, double* ms_out);
+                                   int32_t* ty_out, int32_t* zc_out, int32_t* schedule_out,
+                                   double* ms_out);
 
 /* Solves n_req single-parameter requests that may live on different grids
  * (problems) in one call: the requests of each problem form one batch, and

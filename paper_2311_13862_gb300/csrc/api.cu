@@ -118,7 +118,7 @@ struct rbws_problem_s {
   struct Tuned {
     int tx, ty, zc;
     double ms;
-    int sched;  // 0: 44-byte schedule, 1: 32-byte schedule, 2: 44-byte with TMA stencil phase
+    int sched;  // 0: 44 B, 1: 32 B, 2: 44 B with TMA stencil phase, 3: 32 B s-form, both phases TMA
   };
   std::map<int, Tuned> tuned32;  // batch size -> tuned FP32 tile
 
@@ -312,6 +312,7 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
     }
   } else {
     prof->elem_bytes = (int32_t)sizeof(T);
+    prof->schedule = -1;
   }
   rbws_status rc = RBWS_OK;
   for (;;) {
@@ -530,7 +531,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   // Schedules: 0 = 44 bytes per DoF-iteration (s and A p stored), stencil
   // phase with register prefetch; 2 = the same with the stencil phase fed by
   // TMA (default where the tensor maps can be built); 1 = 32 bytes (s formed
-  // on the fly, A p recomputed).  The 44-byte update phase is a pure stream
+  // on the fly, A p recomputed); 3 = 32 bytes with s = D^{-1} r as the stored
+  // residual and both phases fed by TMA.  The 44-byte update phase is a pure stream
   // (97% of HBM on the 64^3 workload) while both 32-byte phases are stencil
   // kernels; the autotuner picks whichever is fastest.
   int zc_force = 0, sched = 2;
@@ -543,25 +545,21 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   const bool v4 = t4.tx > 0;
   if (!v4) sched = 0;
   const Tile t = v4 ? t4 : choose_tile(p->nx);
-  if (sched == 2 && !tma_supported(p->geo, t)) sched = 0;
-  if (sched == 2) tma_prepare();
-  const int sched32 = sched == 1;
-  int* tma_err = nullptr;
-  {
-    int e2 = 0;
-    tma_err = (int*)p->buf("tma_err", sizeof(int), &e2);
-    if (e2) return (rbws_status)e2;
-    CK(cudaMemsetAsync(tma_err, 0, sizeof(int), p->cur));
-  }
+  if ((sched == 2 || sched == 3) && !tma_supported(p->geo, t)) sched = 0;
+  if (sched == 2 || sched == 3) tma_prepare();
+  const int sched32 = sched == 1 || sched == 3;
+  int* tma_err = nullptr;  // set by make_cg_args below: the third int of the counter block
   auto phase_a = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
     if (sched == 1) launch_cg_a32_v4(aa, t, par, ss);
     else if (sched == 2) {
       if (launch_cg_a_tma(aa, t, par, tma_err, ss)) launch_cg_a_v4(aa, t, par, ss);
-    } else if (v4) launch_cg_a_v4(aa, t, par, ss);
+    } else if (sched == 3) launch_cg_a_s_tma(aa, t, par, tma_err, ss);
+    else if (v4) launch_cg_a_v4(aa, t, par, ss);
     else launch_cg_a<float>(aa, t, par, ss);
   };
   auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
-    if (sched32) launch_cg_b32_v4(aa, t, par, ss);
+    if (sched == 1) launch_cg_b32_v4(aa, t, par, ss);
+    else if (sched == 3) launch_cg_b_s_tma(aa, t, par, tma_err, ss);
     else if (v4) launch_cg_b_v4(aa, t, par, ss);
     else launch_cg_b<float>(aa, t, par, ss);
   };
@@ -579,6 +577,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   if (err) return (rbws_status)err;
   CGArgs<float> a{};
   CKI(make_cg_args<float>(p, B, t, coef32, d, &a, "f_", v4 ? 4 : 1, zc_force));
+  tma_err = a.active + 2;  // counters: active, pending, TMA error flag
   a.f = nullptr;
   a.tol = tol;
   a.max_iters = o.max_iters;
@@ -602,7 +601,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   // start: every instance takes an update from u (restarting its direction)
   std::vector<int> two(B, 2);
   CK(cudaMemcpyAsync(upd, two.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(a.active, 0, 2 * sizeof(int), s));
+  CK(cudaMemsetAsync(a.active, 0, 3 * sizeof(int), s));
   CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
   reset(a, 1, s);
   p->launches += 2;
@@ -610,7 +609,10 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   int M = o.check_every > 0 ? o.check_every : 8;
   if (M % 2) M++;
   rbws_profile* prof = o.profile;
-  if (prof) prof->elem_bytes = 4;
+  if (prof) {
+    prof->elem_bytes = 4;
+    prof->schedule = v4 ? sched : -1;
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaError_t ce;
@@ -631,13 +633,14 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     }
   }
   rbws_status rc = RBWS_OK;
-  int counts[2];
+  int counts[3];
   for (;;) {
-    cudaMemcpyAsync(counts, a.active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(counts, a.active, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
     if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
       rc = (rbws_status)cuda_fail(ce, "solve loop");
       break;
     }
+    if (counts[2]) break;  // a TMA stage wait ran out; reported below
     const int active = counts[0], pending = counts[1];
     if (pending > 0) {
       // FP64 reliable update of the flagged instances
@@ -1599,7 +1602,7 @@ rbws_status rbws_solve_batch(rbws_problem p, const double* mu, int32_t B, double
 }
 
 rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int32_t* tx_out,
-                          int32_t* ty_out, int32_t* zc_out, double* ms_out) {
+                          int32_t* ty_out, int32_t* zc_out, int32_t* schedule_out, double* ms_out) {
   if (!p || B < 1 || B > 65535) {
     set_error("rbws_autotune: invalid argument");
     return RBWS_ERR_INVALID_ARG;
@@ -1624,6 +1627,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
         if (tx_out) *tx_out = it->second.tx;
         if (ty_out) *ty_out = it->second.ty;
         if (zc_out) *zc_out = it->second.zc;
+        if (schedule_out) *schedule_out = it->second.sched;
         if (ms_out) *ms_out = it->second.ms;
         return RBWS_OK;
       }
@@ -1676,21 +1680,18 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
           return (rbws_status)err;
         }
         a.alpha = alpha;
-        int* terr = (int*)p->buf("tma_err", sizeof(int), &err);
-        if (err) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return (rbws_status)err;
-        }
+        int* terr = a.active + 2;
+        cudaMemsetAsync(terr, 0, sizeof(int), s);
         tma_prepare();
-        for (int sched = 0; sched < 3; sched++) {
-          if (sched == 2 && !tma_supported(p->geo, Tile{tx, ty})) continue;
+        for (int sched = 0; sched < 4; sched++) {
+          if (sched >= 2 && !tma_supported(p->geo, Tile{tx, ty})) continue;
           float ta = 0.f, tb = 0.f;
           for (int rep = 0; rep < 3; rep++) {
             launch_tune_prep(a, s);
             cudaEventRecord(e0, s);
             if (sched == 1) launch_cg_a32_v4(a, Tile{tx, ty}, 0, s);
             else if (sched == 2) launch_cg_a_tma(a, Tile{tx, ty}, 0, terr, s);
+            else if (sched == 3) launch_cg_a_s_tma(a, Tile{tx, ty}, 0, terr, s);
             else launch_cg_a_v4(a, Tile{tx, ty}, 0, s);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
@@ -1699,6 +1700,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
             launch_tune_prep(a, s);
             cudaEventRecord(e0, s);
             if (sched == 1) launch_cg_b32_v4(a, Tile{tx, ty}, 0, s);
+            else if (sched == 3) launch_cg_b_s_tma(a, Tile{tx, ty}, 0, terr, s);
             else launch_cg_b_v4(a, Tile{tx, ty}, 0, s);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
@@ -1737,6 +1739,7 @@ rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_path, int
   if (tx_out) *tx_out = best.tx;
   if (ty_out) *ty_out = best.ty;
   if (zc_out) *zc_out = best.zc;
+  if (schedule_out) *schedule_out = best.sched;
   if (ms_out) *ms_out = best.ms;
   return RBWS_OK;
 }

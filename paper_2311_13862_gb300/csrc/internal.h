@@ -164,6 +164,12 @@ bool tma_supported(const Geo& g, Tile t);
 size_t tma_smem_bytes(Tile t);
 int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s);
 void tma_prepare();  // kernel attributes; call outside stream capture
+// 32-byte s-form schedule with both phases TMA-fed (schedule 3): the stored
+// residual is s = D^{-1} r; phase A: p = s + beta p_old, u += alpha_{k-1} p_old,
+// partial p.A p (20 B/DoF); phase B: s -= alpha D^{-1} A p (A p recomputed),
+// partials r.s and r.r with r = D s (12 B/DoF).
+int launch_cg_a_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s);
+int launch_cg_b_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s);
 // Autotuning: puts every instance in a runnable state with benign scalars
 // (status ACTIVE, rho = 1, ||r||^2 huge, gamma = 1) so one phase kernel can be timed.
 void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s);

@@ -87,13 +87,17 @@ __device__ __forceinline__ float f4(const float4& v, int e) {
 
 }  // namespace
 
+// kMode 0: 44-byte schedule (writes p and q = A p).
+// kMode 1: 32-byte s-form schedule (writes p; q is not stored; also applies
+//          the update u += alpha_{k-1} p_{k-1} deferred by phase B, own nodes).
+template <int kMode>
 __global__ void __launch_bounds__(256, 3)
     k_cg_a_tma(const __grid_constant__ CUtensorMap tm_s, const __grid_constant__ CUtensorMap tm_p0,
                const __grid_constant__ CUtensorMap tm_p1, CGArgs<float> a, int parity, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ double red[64];
-  __shared__ double s_beta;
+  __shared__ double s_beta, s_alpha;
   __shared__ int s_run;
   const int b = blockIdx.z;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -114,12 +118,14 @@ __global__ void __launch_bounds__(256, 3)
     }
     if (tid == 0) {
       int run = 0;
-      if (status == ST_ACTIVE) {
+      // an earlier CTA's wait ran out: do not wait again (decided by one thread, shared below)
+      if (status == ST_ACTIVE && !*reinterpret_cast<volatile int*>(err)) {
         const double rel = sqrt(cur.y) / a.fnorm[b];
         if (rel < a.tol) {
           if (leader) {
             st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
             st->relres = rel;
+            st->pad = parity;  // kMode 1: the update alpha[parity] * p_old is still pending
             st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
@@ -127,12 +133,14 @@ __global__ void __launch_bounds__(256, 3)
           if (leader) {
             st->status = (rel == rel) ? ST_MAX_ITERS : ST_BREAKDOWN;
             st->relres = rel;
+            st->pad = parity;
             st->t_done = global_ns();
             atomicSub(a.active, 1);
           }
         } else {
           run = 1;
           s_beta = cur.x / prev;
+          s_alpha = kMode == 1 ? a.alpha[(int64_t)parity * a.B + b] : 0.0;
         }
       }
       s_run = run;
@@ -141,6 +149,7 @@ __global__ void __launch_bounds__(256, 3)
   __syncthreads();
   if (!s_run) return;
   const float beta = (float)s_beta;
+  const float alpha_prev = (float)s_alpha;
   const Geo& g = a.g;
   const int BX = TXN + 8, BY = TY + 2;
   const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float));
@@ -178,6 +187,7 @@ __global__ void __launch_bounds__(256, 3)
   const int64_t col = (int64_t)jn * g.nx + i;
   float* pnew = (parity ? a.p0 : a.p1) + (int64_t)b * g.n;
   float* qb = a.q + (int64_t)b * g.n;
+  float* ub = a.u + (int64_t)b * g.n;
   auto own_p = [&](int st) { return fma4(beta, ld4s(p_tile(st) + cofs), ld4s(s_tile(st) + cofs)); };
 
   // prologue: planes z0-1 (own column only) and z0
@@ -199,6 +209,8 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z < z1; ++z) {
       const int k = z - z0 + 1;  // index of plane z; plane z+1 is k+1
       const int sk = k % kStages, sn = (k + 1) % kStages;
+      float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kMode == 1 && own) u4 = *reinterpret_cast<const float4*>(ub + z * plane + col);  // in flight
       bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
       if (!to && own) {
         const float4 xp = own_p(sn);
@@ -236,7 +248,12 @@ __global__ void __launch_bounds__(256, 3)
           gam = fmaf(xce, v, gam);
         }
         *reinterpret_cast<float4*>(pnew + z * plane + col) = xc;
-        *reinterpret_cast<float4*>(qb + z * plane + col) = make_float4(y[0], y[1], y[2], y[3]);
+        if (kMode == 0) {
+          *reinterpret_cast<float4*>(qb + z * plane + col) = make_float4(y[0], y[1], y[2], y[3]);
+        } else {
+          const float4 po4 = ld4s(Pp + cofs);  // own p_old of plane z, from the stage
+          *reinterpret_cast<float4*>(ub + z * plane + col) = fma4(alpha_prev, po4, u4);
+        }
         xm = xc;
         xc = xp;
       } else if (!to) {
@@ -271,6 +288,200 @@ abort:
   if (tid == 0) {
     atomicExch(err, 1);
     // copies issued for planes next_wait .. n_issued-1 may still be landing
+    for (int j = next_wait; j < n_issued; j++) mbar_wait(&bars[j % kStages], (j / kStages) & 1);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Phase B of the 32-byte s-form schedule.  The stored residual is
+// s = D^{-1} r (s = r without a preconditioner).  alpha_k = rho_k / gamma_k;
+// s -= alpha_k D^{-1} A p_k with A p_k recomputed from TMA-staged planes of
+// p_k; r = D s; partials rho_{k+1} = r.s and ||r||^2.  Reads s (own) and p
+// (halo from L2), writes s: 12 bytes per DoF.  alpha_k goes to
+// a.alpha[parity ^ 1][b] for the next phase A.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 3)
+    k_cg_b_s_tma(const __grid_constant__ CUtensorMap tm_p0, const __grid_constant__ CUtensorMap tm_p1,
+                 CGArgs<float> a, int parity, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ double red[64];
+  __shared__ double s_alpha;
+  __shared__ int s_run;
+  const int b = blockIdx.z;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tiles_x = a.tiles_x;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  const int x0 = (blockIdx.x % tiles_x) * TXN, y0 = (blockIdx.x / tiles_x) * TY;
+  const int z0 = blockIdx.y * a.zc, z1 = min(a.g.nz, z0 + a.zc);
+  const int part = blockIdx.y * gridDim.x + blockIdx.x;
+  const bool leader = part == 0;
+  if (tid < 32) {
+    InstState* st = a.st + b;
+    const int status = st->status;
+    double rho = 0.0, gam = 0.0, rr = 0.0;
+    if (status == ST_ACTIVE) {
+      const double2 cur = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, tid);
+      rho = cur.x;
+      rr = cur.y;
+      double gs = 0.0;
+      for (int c = tid; c < a.P; c += 32) gs += a.gam[(int64_t)b * a.P + c];
+      gam = warp_sum_down(gs);
+    }
+    if (tid == 0) {
+      int run = 0;
+      if (status == ST_ACTIVE && !*reinterpret_cast<volatile int*>(err)) {
+        const double alpha = rho / gam;
+        if (!(gam > 0.0) || !(alpha == alpha) || alpha == INFINITY) {
+          if (leader) {
+            st->status = ST_BREAKDOWN;
+            st->relres = sqrt(rr) / a.fnorm[b];
+            st->pad = parity ^ 1;  // no valid alpha_k: nothing pending
+            a.alpha[(int64_t)(parity ^ 1) * a.B + b] = 0.0;
+            st->t_done = global_ns();
+            atomicSub(a.active, 1);
+          }
+        } else {
+          run = 1;
+          s_alpha = alpha;
+          if (leader) {
+            st->iters += 1;
+            a.alpha[(int64_t)(parity ^ 1) * a.B + b] = alpha;
+          }
+        }
+      }
+      s_run = run;
+    }
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const float alpha = (float)s_alpha;
+  const Geo& g = a.g;
+  const bool jac = a.precond != RBWS_PREC_NONE;
+  const int BX = TXN + 8, BY = TY + 2;
+  const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float));
+  const int arr_floats = ((BX * BY * 4 + 127) / 128) * 32;
+  float* stage_base = reinterpret_cast<float*>(smem_raw);
+  auto p_tile = [&](int st) { return stage_base + st * arr_floats; };
+  const CUtensorMap* mp = parity ? &tm_p0 : &tm_p1;  // p_k = pbuf[parity ^ 1]
+  const int nq = z1 - z0 + 2;
+  auto issue = [&](int j) {
+    const int st = j % kStages;
+    mbar_expect_tx(&bars[st], box_bytes);
+    tma_load_4d(p_tile(st), mp, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+  };
+  if (tid == 0) {
+    for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int n_issued = 0, next_wait = 0;
+  if (tid == 0)
+    for (int j = 0; j < kStages && j < nq; j++) {
+      issue(j);
+      n_issued = j + 1;
+    }
+  const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
+  const int i = x0 + lx, jn = y0 + ly;
+  const bool own = i < g.nx && jn < g.ny;
+  const int cofs = (ly + 1) * BX + lx + 4;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)jn * g.nx + i;
+  float* sb = a.s + (int64_t)b * g.n;
+  float rho = 0.f, rr = 0.f;
+  bool timed_out = !mbar_wait(&bars[0], 0);
+  float4 xm = ld4s(p_tile(0) + cofs);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  float4 xc = ld4s(p_tile(1 % kStages) + cofs);
+  if (__syncthreads_or(timed_out)) goto abort;
+  next_wait = 2;
+  if (tid == 0 && kStages < nq) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(kStages);
+    n_issued = kStages + 1;
+  }
+  {
+    float c[4][8];
+    int zcls_cur = -1;
+    for (int z = z0; z < z1; ++z) {
+      const int k = z - z0 + 1;
+      const int sk = k % kStages, sn = (k + 1) % kStages;
+      float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (own) s4 = *reinterpret_cast<const float4*>(sb + z * plane + col);  // in flight over the wait
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      if (!to && own) {
+        const float4 xp = ld4s(p_tile(sn) + cofs);
+        const int zcl = g.cz[z];
+        if (zcl != zcls_cur) {
+          zcls_cur = zcl;
+          const int yc = (int)g.cy[jn];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+#pragma unroll
+            for (int m = 0; m < 8; m++) c[e][m] = row[m];
+          }
+        }
+        const float* Pp = p_tile(sk);
+        const float left = Pp[cofs - 1], right = Pp[cofs + 4];
+        const float4 sth = ld4s(Pp + cofs - BX), nth = ld4s(Pp + cofs + BX);
+        float sn4[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float xce = f4(xc, e);
+          const float xw = e == 0 ? left : f4(xc, e - 1);
+          const float xe = e == 3 ? right : f4(xc, e + 1);
+          float v = c[e][6] * xce;
+          v = fmaf(c[e][0], xw, v);
+          v = fmaf(c[e][1], xe, v);
+          v = fmaf(c[e][2], f4(sth, e), v);
+          v = fmaf(c[e][3], f4(nth, e), v);
+          v = fmaf(c[e][4], f4(xm, e), v);
+          v = fmaf(c[e][5], f4(xp, e), v);
+          const float dinv = jac ? c[e][7] : 1.f;
+          const float snew = fmaf(-alpha * dinv, v, f4(s4, e));
+          const float rnew = jac ? c[e][6] * snew : snew;
+          rho = fmaf(rnew, snew, rho);
+          rr = fmaf(rnew, rnew, rr);
+          sn4[e] = snew;
+        }
+        *reinterpret_cast<float4*>(sb + z * plane + col) = make_float4(sn4[0], sn4[1], sn4[2], sn4[3]);
+        xm = xc;
+        xc = xp;
+      } else if (!to) {
+        xm = xc;
+        xc = ld4s(p_tile(sn) + cofs);
+      }
+      if (__syncthreads_or(to)) goto abort;
+      next_wait = k + 2;
+      if (tid == 0 && k + kStages < nq) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k + kStages);
+        n_issued = k + kStages + 1;
+      }
+    }
+    double drho = (double)rho, drr = (double)rr;
+    const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+    drho = warp_sum_down(drho);
+    drr = warp_sum_down(drr);
+    if (lane == 0) {
+      red[warp] = drho;
+      red[32 + warp] = drr;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double x = lane < nw ? red[lane] : 0.0, y = lane < nw ? red[32 + lane] : 0.0;
+      x = warp_sum_down(x);
+      y = warp_sum_down(y);
+      if (lane == 0) a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + part] = make_double2(x, y);
+    }
+  }
+  return;
+abort:
+  if (tid == 0) {
+    atomicExch(err, 1);
     for (int j = next_wait; j < n_issued; j++) mbar_wait(&bars[j % kStages], (j / kStages) & 1);
   }
   __syncthreads();
@@ -323,7 +534,9 @@ bool tma_supported(const Geo& g, Tile t) {
 
 // Once per process and device, outside any stream capture.
 void tma_prepare() {
-  cudaFuncSetAttribute(k_cg_a_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_cg_a_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_cg_a_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_cg_b_s_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
@@ -332,7 +545,24 @@ int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaSt
   if (make_map(&ms, sarr, a.g, a.B, t) || make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t))
     return -1;
   const size_t smem = tma_smem_bytes(t);
-  k_cg_a_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), smem, s>>>(ms, m0, m1, a, parity, err);
+  k_cg_a_tma<0><<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), smem, s>>>(ms, m0, m1, a, parity, err);
+  return 0;
+}
+
+int launch_cg_a_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
+  CUtensorMap ms, m0, m1;
+  if (make_map(&ms, a.s, a.g, a.B, t) || make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t))
+    return -1;
+  k_cg_a_tma<1><<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), tma_smem_bytes(t), s>>>(
+      ms, m0, m1, a, parity, err);
+  return 0;
+}
+
+int launch_cg_b_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
+  CUtensorMap m0, m1;
+  if (make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t)) return -1;
+  k_cg_b_s_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), tma_smem_bytes(t) / 2 + 128, s>>>(
+      m0, m1, a, parity, err);
   return 0;
 }
 

@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start)
       float4 sv = rv;
       if (jac) sv = make_float4(dinv[0] * rv.x, dinv[1] * rv.y, dinv[2] * rv.z, dinv[3] * rv.w);
       st4(a.r + idx, rv);
-      if (jac) st4(a.s + idx, sv);
+      st4(a.s + idx, sv);  // s = r without a preconditioner (the s-form schedule reads s)
       if (restart) st4(a.p0 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
       rho = fmaf(rv.x, sv.x, fmaf(rv.y, sv.y, fmaf(rv.z, sv.z, fmaf(rv.w, sv.w, rho))));
       rr = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, rr))));

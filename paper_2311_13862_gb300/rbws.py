@@ -44,7 +44,7 @@ class rbws_blocks(C.Structure):
 class rbws_profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("samples", C.c_int64), ("stencil_ms", C.c_double),
                 ("update_ms", C.c_double), ("active_dofs", C.c_double), ("elem_bytes", C.c_int32),
-                ("pad", C.c_int32)]
+                ("schedule", C.c_int32)]
 
 
 class rbws_options(C.Structure):
@@ -84,7 +84,7 @@ def _lib():
         L.rbws_surrogate_loss_grad.argtypes = [P, P, P, i32, C.POINTER(d), P]
         L.rbws_solve_requests.argtypes = [i32, P, P, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
         L.rbws_autotune.argtypes = [P, i32, C.c_char_p, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
-                                    C.POINTER(d)]
+                                    C.POINTER(i32), C.POINTER(d)]
         for name in ("rbws_problem_create", "rbws_problem_info", "rbws_apply_operator", "rbws_apply_operator_static",
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
@@ -272,12 +272,12 @@ def rbws_solve_requests(handles, mus, u_outs, tol, warm, options: rbws_options |
 
 
 def rbws_autotune(h, B, cache_path=None):
-    """Returns (tx, ty, zc, ms) of the fastest FP32 tile for batches of B."""
-    tx, ty, zc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+    """Returns (tx, ty, zc, ms, schedule) of the fastest FP32 configuration for batches of B."""
+    tx, ty, zc, sc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
     path = None if cache_path is None else str(cache_path).encode()
-    _check(_lib().rbws_autotune(h, B, path, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(ms)),
+    _check(_lib().rbws_autotune(h, B, path, C.byref(tx), C.byref(ty), C.byref(zc), C.byref(sc), C.byref(ms)),
            "rbws_autotune")
-    return tx.value, ty.value, zc.value, ms.value
+    return tx.value, ty.value, zc.value, ms.value, sc.value
 
 
 class Problem:

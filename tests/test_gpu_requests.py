@@ -49,11 +49,11 @@ def test_autotune_picks_a_valid_tile_and_caches_it(tmp_path):
     cache = tmp_path / "tiles.txt"
     mu = inputs.log_uniform(92, 8, 4, 0.1, 10.0)
     with rbws.Problem(grid, blocks) as P:
-        tx, ty, zc, ms = rbws.rbws_autotune(P.h, 8, cache)
-        assert tx in (4, 8, 16, 32) and 64 <= tx * ty <= 256 and zc >= 1 and ms > 0
+        tx, ty, zc, ms, sched = rbws.rbws_autotune(P.h, 8, cache)
+        assert tx in (4, 8, 16, 32) and 64 <= tx * ty <= 256 and zc >= 1 and ms > 0 and sched in (0, 1, 2, 3)
         assert cache.read_text().split()[1:4] == [str(tx), str(ty), str(zc)]
         again = rbws.rbws_autotune(P.h, 8, cache)  # read back from the cache
-        assert again[:3] == (tx, ty, zc)
+        assert again[:3] == (tx, ty, zc) and again[4] == sched
         u = torch.empty((8, P.n), dtype=torch.float64, device="cuda")
         rc, it, rel, st = rbws.rbws_solve_batch(P.h, mu, 1e-10, rbws.WARM_ZERO, u,
                                                 rbws.rbws_options_default(precision=rbws.FP32_IR))
@@ -63,11 +63,12 @@ def test_autotune_picks_a_valid_tile_and_caches_it(tmp_path):
         assert np.linalg.norm(np.ones(op.n) - op.matvec(mu[b], uh[b])) / np.sqrt(op.n) < 1e-10
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2])
+@pytest.mark.parametrize("sched", [0, 1, 2, 3])
 def test_each_fp32_schedule_reaches_the_fp64_residual(tmp_path, sched):
     """Forces each FP32 iteration schedule through an autotuner cache entry (0: 44 bytes per
     DoF with register prefetch, 1: 32 bytes with recomputed A p, 2: 44 bytes with the TMA-fed
-    stencil phase) and checks the solutions with the oracle's FP64 operator."""
+    stencil phase, 3: 32 bytes in s-form with both phases TMA-fed) and checks the solutions
+    with the oracle's FP64 operator."""
     grid, blocks = (64, 40, 36), (2, 2, 1)
     op = O.assemble(grid, blocks)
     B = 6
