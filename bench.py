@@ -243,6 +243,8 @@ def main():
     ap.add_argument("--c5-train", type=int, default=256, help="greedy training parameters per grid (c5)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in FP32 tile/schedule instead of the autotuned one")
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="force an FP32 schedule (0..3) with the built-in tile instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -284,7 +286,14 @@ def main():
     t_off = time.perf_counter() - t0
 
     tuned = None
-    if not args.no_autotune:
+    if args.schedule >= 0:
+        # a one-line tuning cache forces the schedule (tile 16x16, z-chunks of 16)
+        path = os.path.join(tempfile.mkdtemp(), "tiles.txt")
+        with open(path, "w") as f:
+            f.write("%dx%dx%d/B%d/fp32 16 16 16 1.0 %d\n" % (w.grid + (B, args.schedule)))
+        tx, ty, zc, pair_ms, sched = rbws.rbws_autotune(P.h, B, path)
+        tuned = {"tile": [tx, ty, zc], "schedule": sched, "forced": True}
+    elif not args.no_autotune:
         t0 = time.perf_counter()
         tx, ty, zc, pair_ms, sched = rbws.rbws_autotune(P.h, B)
         tuned = {"tile": [tx, ty, zc], "schedule": sched, "pair_ms": pair_ms, "tune_s": time.perf_counter() - t0}

@@ -164,19 +164,28 @@ RBWS_API rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu
                                                 const void* x, void* y, int32_t precision,
                                                 void* stream);
 
-/* Offline greedy (Algorithm 5's loop with the Galerkin RB of Sec. 2.3 and a
- * residual indicator): first parameter = mu_train[0]; snapshot solves by
+/* Error indicators of the offline greedy. */
+typedef enum {
+  RBWS_INDICATOR_RESIDUAL = 0, /* eta(mu) = ||f - A(mu) W c(mu)|| / ||f|| (full-order residual) */
+  RBWS_INDICATOR_L1 = 1        /* ||R^{-1} c(mu)||_1: the L1 norm of the RB coefficients with
+                                  respect to the unorthogonalised snapshots (Sec. 3.1), R the
+                                  Gram-Schmidt factor (u_k = sum_j R[j][k] w_j)               */
+} rbws_indicator;
+
+/* Offline greedy (Algorithm 5's loop with the Galerkin RB of Sec. 2.3 and the
+ * chosen indicator): first parameter = mu_train[0]; snapshot solves by
  * Jacobi-PCG to snapshot_tol (a snapshot that stalls above snapshot_tol at
  * the rounding floor of the FP64 residual is used if its true relative
  * residual is below 1e-9); Gram-Schmidt applied twice; the next parameter
- * maximises eta(mu) = ||f - A(mu) W c(mu)|| / ||f|| over the training points
- * not yet selected (ties: smallest index).  Stops at n_max, when max eta <
+ * maximises the indicator over the training points not yet selected (ties:
+ * smallest index).  Stops at n_max, when max indicator <
  * greedy_tol, or when a snapshot adds no new direction (||w|| < 1e-10 ||u||).
  * Replaces any previous basis; 1 <= n_max <= 160.  selected_out [n_max], eta_hist_out [n_max]
  * (eta_hist[k] = max eta once the basis has k+1 vectors) may be NULL. */
 RBWS_API rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
                                 int32_t n_max, double greedy_tol, double snapshot_tol,
-                                int32_t* selected_out, double* eta_hist_out, int32_t* n_out);
+                                int32_t indicator, int32_t* selected_out, double* eta_hist_out,
+                                int32_t* n_out);
 
 /* Installs a reduced basis computed elsewhere: W host [N][n_dof] (orthonormal
  * columns stored one after another), ANq host [Q][N][N] = W^T A_q W,
@@ -273,6 +282,16 @@ RBWS_API rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* prob
                                          int32_t warm, const rbws_options* opt, int32_t* iters_out,
                                          double* relres_out, int32_t* status_out,
                                          double* latency_ms_out);
+
+/* Checkpoint of the offline stage (the paper's offline/online split): writes
+ * the problem description (grid, blocks, f), the reduced basis W, A_N^q, f_N
+ * and the surrogate network (if any) to `path` in a versioned binary format
+ * with an FNV-1a checksum.  Synchronous; the problem is unchanged. */
+RBWS_API rbws_status rbws_save(rbws_problem p, const char* path);
+/* Creates a problem on `device` from a checkpoint written by rbws_save.
+ * Returns RBWS_ERR_STATE with a message if the file is not a checkpoint, has
+ * another version, is truncated, or fails its checksum. */
+RBWS_API rbws_status rbws_load(const char* path, int device, rbws_problem* out);
 
 /* Thread-local message for the last error (never NULL). */
 RBWS_API const char* rbws_last_error(void);

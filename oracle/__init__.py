@@ -51,7 +51,7 @@ def lib():
         L.orc_cholesky_solve.argtypes = [i32, P, P]
         L.orc_rb_solve.argtypes = [i32, i32, i32, P, P, P, P]
         L.orc_pcg.argtypes = [i64, P, P, P, P, P, i32, P, d, i32, i32, P, P, P]
-        L.orc_greedy.argtypes = [i64, P, P, P, i32, i64, P, P, i32, i32, d, d, P, P, P, P, P, P]
+        L.orc_greedy.argtypes = [i64, P, P, P, i32, i64, P, P, i32, i32, d, d, i32, P, P, P, P, P, P]
         L.orc_rb_indicator.argtypes = [i64, P, P, P, i32, i64, P, P, i32, i32, P, P, P]
         L.orc_rb_indicator.restype = d
         L.orc_solve_batch.argtypes = ([i64, P, P, P, i32, i64, P, P, i32, i32, P, i32, i32, P, P, P,
@@ -216,8 +216,9 @@ class Basis:
     N: int
 
 
-def greedy(op: Operator, mu_train, n_max, f=None, greedy_tol=0.0, snapshot_tol=1e-12) -> Basis:
-    """Greedy reduced basis (Algorithm 5 skeleton, Galerkin RB, residual indicator)."""
+def greedy(op: Operator, mu_train, n_max, f=None, greedy_tol=0.0, snapshot_tol=1e-12, indicator=0) -> Basis:
+    """Greedy reduced basis (Algorithm 5 skeleton, Galerkin RB).  indicator 0: FOM residual;
+    1: L1 norm of the coefficients w.r.t. the unorthogonalised snapshots (Sec. 3.1)."""
     n = op.n
     f = np.ones(n) if f is None else _f64(f)
     mu_train = _f64(mu_train)
@@ -229,7 +230,7 @@ def greedy(op: Operator, mu_train, n_max, f=None, greedy_tol=0.0, snapshot_tol=1
     eta = np.full(n_max, np.nan)
     nout = C.c_int(0)
     rc = lib().orc_greedy(n, _p(op.row_ptr), _p(op.col), _p(op.vals_q), op.Q, op.nnz, _p(f),
-                          _p(mu_train), n_train, n_max, greedy_tol, snapshot_tol, _p(W), _p(ANq),
+                          _p(mu_train), n_train, n_max, greedy_tol, snapshot_tol, indicator, _p(W), _p(ANq),
                           _p(fN), _p(sel), _p(eta), C.byref(nout))
     if rc != 0:
         raise RuntimeError("orc_greedy failed: %d" % rc)

@@ -323,11 +323,26 @@ double orc_rb_indicator(int64_t n, const int64_t* row_ptr, const int32_t* col, c
   return eta;
 }
 
+/* L1 indicator: c w.r.t. W -> x = R^{-1} c w.r.t. the snapshots (U = W R,
+ * R upper triangular [Nmax][Nmax]); returns sum |x_j|. */
+static double l1_indicator(int N, int Nmax, const double* R, const double* c) {
+  double x[512];
+  for (int i = N - 1; i >= 0; i--) {
+    double s = c[i];
+    for (int k = i + 1; k < N; k++) s -= R[i * Nmax + k] * x[k];
+    x[i] = s / R[i * Nmax + i];
+  }
+  double l1 = 0.0;
+  for (int i = 0; i < N; i++) l1 += fabs(x[i]);
+  return l1;
+}
+
 int orc_greedy(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* vals_q, int Q,
                int64_t nnz, const double* f, const double* mu_train, int n_train, int n_max,
-               double greedy_tol, double snapshot_tol, double* W, double* ANq, double* fN,
-               int32_t* selected, double* eta_hist, int* n_out) {
-  if (n_max < 1 || n_max > 512 || n_train < 1) return -1;
+               double greedy_tol, double snapshot_tol, int indicator, double* W, double* ANq,
+               double* fN, int32_t* selected, double* eta_hist, int* n_out) {
+  if (n_max < 1 || n_max > 512 || n_train < 1 || indicator < 0 || indicator > 1) return -1;
+  double* R = (double*)calloc((size_t)n_max * n_max, sizeof(double));
   double* val = (double*)malloc(sizeof(double) * nnz);
   double* u = (double*)malloc(sizeof(double) * n);
   double* w = (double*)malloc(sizeof(double) * n);
@@ -350,15 +365,20 @@ int orc_greedy(int64_t n, const int64_t* row_ptr, const int32_t* col, const doub
     int st = orc_pcg(n, row_ptr, col, val, f, u, ORC_PREC_JACOBI, NULL, snapshot_tol, 100000, 3,
                      &it, &rel, NULL);
     if (st != ORC_CONVERGED) { rc = -2; break; }
-    /* classical Gram-Schmidt, applied twice: w = (I - W W^T)^2 u */
+    /* classical Gram-Schmidt, applied twice: w = (I - W W^T)^2 u; the
+     * coefficients of both passes form column N of R (u = W R[:,N]) */
     for (int64_t i = 0; i < n; i++) w[i] = u[i];
+    for (int j = 0; j < N; j++) R[j * n_max + N] = 0.0;
     for (int pass = 0; pass < 2; pass++) {
       for (int j = 0; j < N; j++) coef[j] = dot(n, W + (int64_t)j * n, w);
-      for (int j = 0; j < N; j++)
+      for (int j = 0; j < N; j++) {
+        R[j * n_max + N] += coef[j];
         for (int64_t i = 0; i < n; i++) w[i] -= coef[j] * W[(int64_t)j * n + i];
+      }
     }
     double wn = norm2(n, w);
     if (wn < 1e-10 * norm2(n, u)) break; /* basis numerically complete */
+    R[N * n_max + N] = wn;
     for (int64_t i = 0; i < n; i++) W[(int64_t)N * n + i] = w[i] / wn;
     selected[N] = next;
     taken[next] = 1;
@@ -378,9 +398,17 @@ int orc_greedy(int64_t n, const int64_t* row_ptr, const int32_t* col, const doub
     int any = 0;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int t = 0; t < n_train; t++) {
-      eta[t] = taken[t] ? -1.0
-                        : orc_rb_indicator(n, row_ptr, col, vals_q, Q, nnz, f, W, N, n_max, ANq,
-                                           fN, mu_train + (int64_t)t * Q);
+      if (taken[t]) {
+        eta[t] = -1.0;
+      } else if (indicator == 0) {
+        eta[t] = orc_rb_indicator(n, row_ptr, col, vals_q, Q, nnz, f, W, N, n_max, ANq, fN,
+                                  mu_train + (int64_t)t * Q);
+      } else {
+        double c[512];
+        eta[t] = orc_rb_solve(N, n_max, Q, ANq, fN, mu_train + (int64_t)t * Q, c) == 0
+                     ? l1_indicator(N, n_max, R, c)
+                     : INFINITY;
+      }
     }
     double best = -1.0;
     next = -1;
@@ -393,7 +421,7 @@ int orc_greedy(int64_t n, const int64_t* row_ptr, const int32_t* col, const doub
     if (!any || best < greedy_tol) break;
   }
   *n_out = N;
-  free(val); free(u); free(w); free(v); free(eta); free(taken);
+  free(val); free(u); free(w); free(v); free(eta); free(taken); free(R);
   return rc;
 }
 

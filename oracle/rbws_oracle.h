@@ -98,16 +98,19 @@ int orc_pcg(int64_t n, const int64_t* row_ptr, const int32_t* col, const double*
  * [n_train][Q]: first parameter = index 0; snapshot by Jacobi-PCG to
  * snapshot_tol; classical Gram-Schmidt applied twice; stop on breakdown
  * (||w|| < 1e-10 ||u||), at n_max, or when max eta < greedy_tol; next
- * parameter = argmax over not-yet-selected training points of the residual
- * indicator eta(mu) = ||f - A(mu) W c(mu)|| / ||f|| (ties: smallest index).
+ * parameter = argmax over not-yet-selected training points of the indicator
+ * (ties: smallest index): indicator 0 = residual eta(mu) = ||f - A(mu) W c(mu)||
+ * / ||f||; indicator 1 = the L1 norm of the RB coefficients with respect to the
+ * unorthogonalised snapshots (Sec. 3.1), ||R^{-1} c(mu)||_1 with U = W R from
+ * the Gram-Schmidt steps.
  * Outputs: W [n_max][n], ANq [Q][n_max][n_max], fN [n_max], selected [n_max],
  * eta_hist [n_max] (eta_hist[k] = max eta over the unselected training set
  * once the basis has k+1 vectors; NaN if that set is empty),
  * n_out = final N.  Returns 0 or a negative error. */
 int orc_greedy(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* vals_q, int Q,
                int64_t nnz, const double* f, const double* mu_train, int n_train, int n_max,
-               double greedy_tol, double snapshot_tol, double* W, double* ANq, double* fN,
-               int32_t* selected, double* eta_hist, int* n_out);
+               double greedy_tol, double snapshot_tol, int indicator, double* W, double* ANq,
+               double* fN, int32_t* selected, double* eta_hist, int* n_out);
 
 /* Residual indicator for one mu with a given basis (see orc_greedy). */
 double orc_rb_indicator(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* vals_q,

@@ -1227,9 +1227,11 @@ rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, doub
 
 rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
                                 int32_t n_max, double greedy_tol, double snapshot_tol,
-                                int32_t* selected_out, double* eta_hist_out, int32_t* n_out) {
-  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 160 || !(snapshot_tol > 0.0)) {
-    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 160, snapshot_tol > 0)");
+                                int32_t indicator, int32_t* selected_out, double* eta_hist_out,
+                                int32_t* n_out) {
+  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 160 || !(snapshot_tol > 0.0) ||
+      (indicator != RBWS_INDICATOR_RESIDUAL && indicator != RBWS_INDICATOR_L1)) {
+    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 160, snapshot_tol > 0, indicator 0 or 1)");
     return RBWS_ERR_INVALID_ARG;
   }
   StreamGuard sg(p, nullptr);
@@ -1256,7 +1258,9 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   const int scratch_len = 256 * (n_max + 2);
   double* scratch = err ? nullptr : (double*)p->buf("g_scratch", sizeof(double) * scratch_len, &err);
   double* eye = err ? nullptr : (double*)p->buf("g_eye", sizeof(double) * (size_t)Q * Q, &err);
+  double* dR = err ? nullptr : (double*)p->buf("g_R", sizeof(double) * (size_t)n_max * n_max, &err);
   if (err) return (rbws_status)err;
+  std::vector<double> Rh((size_t)n_max * n_max, 0.0);  // u_k = sum_j R[j][k] w_j (Gram-Schmidt factor)
   {
     std::vector<double> I((size_t)Q * Q, 0.0);
     for (int q = 0; q < Q; q++) I[(size_t)q * Q + q] = 1.0;
@@ -1288,11 +1292,15 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
                 std::to_string(st[0].relres) + ")");
       return RBWS_ERR_STATE;
     }
-    // w = (I - W W^T)^2 u
+    // w = (I - W W^T)^2 u; the coefficients of both passes form column N of R
     CK(cudaMemcpyAsync(w, usnap, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     for (int pass = 0; pass < 2 && N > 0; pass++) {
       launch_multi_dot(n, N, p->d_W, n, w, dots, scratch, scratch_len, s);
       launch_sub_combination(n, N, p->d_W, dots, w, s);
+      std::vector<double> cf(N);
+      CK(cudaMemcpyAsync(cf.data(), dots, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int j = 0; j < N; j++) Rh[(size_t)j * n_max + N] += cf[j];
     }
     launch_multi_dot(n, 1, w, n, w, dots, scratch, scratch_len, s);
     launch_multi_dot(n, 1, usnap, n, usnap, dots + 1, scratch, scratch_len, s);
@@ -1301,6 +1309,7 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
     CK(cudaStreamSynchronize(s));
     const double wn = std::sqrt(nn[0]), un = std::sqrt(nn[1]);
     if (!(wn >= 1e-10 * un)) break;  // no new direction
+    Rh[(size_t)N * n_max + N] = wn;
     double* wN = p->d_W + (int64_t)N * n;
     CK(cudaMemcpyAsync(wN, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(dots, &wn, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1338,18 +1347,32 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(p->d_fN, p->h_fN.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
     p->N = N;
-    // residual indicator over the training set
-    for (int64_t b0 = 0; b0 < n_train; b0 += chunk) {
-      const int Bc = (int)std::min<int64_t>(chunk, n_train - b0);
-      double* U = (double*)p->buf("g_U", sizeof(double) * (size_t)Bc * n, &err);
-      double* etad = err ? nullptr : (double*)p->buf("g_eta", sizeof(double) * (size_t)Bc, &err);
+    // indicator over the training set
+    if (indicator == RBWS_INDICATOR_L1) {
+      // ||R^{-1} c(mu)||_1: reduced solves only, no full-order work
+      CK(cudaMemcpyAsync(dR, Rh.data(), sizeof(double) * Rh.size(), cudaMemcpyHostToDevice, s));
+      double* Cd = (double*)p->buf("g_C", sizeof(double) * (size_t)n_train * N, &err);
+      int* info = err ? nullptr : (int*)p->buf("g_info", sizeof(int) * (size_t)n_train, &err);
+      double* etad = err ? nullptr : (double*)p->buf("g_eta", sizeof(double) * (size_t)n_train, &err);
       if (err) return (rbws_status)err;
-      CKI(galerkin_start(p, d_mu + b0 * Q, Bc, U));
-      double* cc = nullptr;
-      CKI(coef_tables(p, d_mu + b0 * Q, Bc, &cc, nullptr));
-      CKI(residual_norms(p, cc, Bc, U, nullptr, etad));
-      CK(cudaMemcpyAsync(eta.data() + b0, etad, sizeof(double) * Bc, cudaMemcpyDeviceToHost, s));
+      launch_reduced_solve(N, Q, p->d_ANq, p->d_fN, d_mu, n_train, Cd, info, nullptr, s);
+      launch_l1_indicator(N, n_max, dR, Cd, info, n_train, etad, s);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(eta.data(), etad, sizeof(double) * n_train, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+    } else {
+      for (int64_t b0 = 0; b0 < n_train; b0 += chunk) {
+        const int Bc = (int)std::min<int64_t>(chunk, n_train - b0);
+        double* U = (double*)p->buf("g_U", sizeof(double) * (size_t)Bc * n, &err);
+        double* etad = err ? nullptr : (double*)p->buf("g_eta", sizeof(double) * (size_t)Bc, &err);
+        if (err) return (rbws_status)err;
+        CKI(galerkin_start(p, d_mu + b0 * Q, Bc, U));
+        double* cc = nullptr;
+        CKI(coef_tables(p, d_mu + b0 * Q, Bc, &cc, nullptr));
+        CKI(residual_norms(p, cc, Bc, U, nullptr, etad));
+        CK(cudaMemcpyAsync(eta.data() + b0, etad, sizeof(double) * Bc, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      }
     }
     double best = -1.0;
     next = -1;
@@ -1842,3 +1865,171 @@ rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint: the offline products (reduced basis, reduced operators, the
+// surrogate network) and the problem description, so a later process can
+// solve online without repeating the offline stage.
+//
+// File layout (little endian): "RBWSPRB1", u32 version = 1, i32 nx ny nz bx
+// by bz Q has_f N net_H net_N, f64 mu_lo mu_hi, u64 payload bytes, then the
+// payload: f [n] (if has_f), W [N][n], ANq [Q][N][N], fN [N] (f64), network
+// parameters [P] and coefficient scales [net_N] (f32), then u64 FNV-1a of
+// the payload.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; i++) {
+      h ^= c[i];
+      h *= 1099511628211ull;
+    }
+  }
+};
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t nx, ny, nz, bx, by, bz, Q, has_f, N, net_H, net_N;
+  double mu_lo, mu_hi;
+  uint64_t payload;
+};
+
+}  // namespace
+
+extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
+  if (!p || !path) {
+    set_error("rbws_save: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  cudaSetDevice(p->device);
+  CK(cudaDeviceSynchronize());
+  const int64_t n = p->n;
+  const int N = p->N;
+  CkptHeader h{};
+  std::memcpy(h.magic, "RBWSPRB1", 8);
+  h.version = 1;
+  h.nx = p->nx;
+  h.ny = p->ny;
+  h.nz = p->nz;
+  h.bx = p->bx;
+  h.by = p->by;
+  h.bz = p->bz;
+  h.Q = p->Q;
+  h.has_f = p->d_f != nullptr;
+  h.N = N;
+  h.net_H = p->d_w32 ? p->net_H : 0;
+  h.net_N = p->d_w32 ? p->net_N : 0;
+  h.mu_lo = p->net_lo;
+  h.mu_hi = p->net_hi;
+  std::vector<double> f(h.has_f ? n : 0), W((size_t)N * n);
+  if (h.has_f) CK(cudaMemcpy(f.data(), p->d_f, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  if (N > 0) CK(cudaMemcpy(W.data(), p->d_W, sizeof(double) * W.size(), cudaMemcpyDeviceToHost));
+  std::vector<float> params(h.net_H ? p->net_P : 0), scale(h.net_N);
+  if (h.net_H) {
+    CK(cudaMemcpy(params.data(), p->d_w32, sizeof(float) * params.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(scale.data(), p->d_cscale, sizeof(float) * scale.size(), cudaMemcpyDeviceToHost));
+  }
+  const size_t szA = sizeof(double) * (N > 0 ? p->h_ANq.size() : 0), szF = sizeof(double) * (N > 0 ? N : 0);
+  h.payload = sizeof(double) * (f.size() + W.size()) + szA + szF + sizeof(float) * (params.size() + scale.size());
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) {
+    set_error(std::string("rbws_save: cannot open ") + path);
+    return RBWS_ERR_INVALID_ARG;
+  }
+  Fnv fnv;
+  bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1;
+  auto put = [&](const void* d, size_t bytes) {
+    if (!bytes || !ok) return;
+    ok = std::fwrite(d, 1, bytes, fp) == bytes;
+    fnv.add(d, bytes);
+  };
+  put(f.data(), sizeof(double) * f.size());
+  put(W.data(), sizeof(double) * W.size());
+  if (N > 0) {
+    put(p->h_ANq.data(), szA);
+    put(p->h_fN.data(), szF);
+  }
+  put(params.data(), sizeof(float) * params.size());
+  put(scale.data(), sizeof(float) * scale.size());
+  if (ok) ok = std::fwrite(&fnv.h, sizeof(fnv.h), 1, fp) == 1;
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) {
+    set_error(std::string("rbws_save: write failed for ") + path);
+    return RBWS_ERR_STATE;
+  }
+  return RBWS_OK;
+}
+
+extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out) {
+  if (!path || !out) {
+    set_error("rbws_load: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) {
+    set_error(std::string("rbws_load: cannot open ") + path);
+    return RBWS_ERR_INVALID_ARG;
+  }
+  CkptHeader h{};
+  auto fail = [&](const char* why) {
+    std::fclose(fp);
+    set_error(std::string("rbws_load: ") + why + " (" + path + ")");
+    return RBWS_ERR_STATE;
+  };
+  if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "RBWSPRB1", 8) != 0) return fail("not a checkpoint");
+  if (h.version != 1) return fail("unsupported version");
+  if (h.nx < 2 || h.ny < 2 || h.nz < 2 || h.nx > kMaxAxis || h.ny > kMaxAxis || h.nz > kMaxAxis ||
+      h.N < 0 || h.N > 160 || h.Q != h.bx * h.by * h.bz || h.net_H < 0 || h.net_H > 4096 ||
+      (h.net_H > 0 && h.net_N != h.N))
+    return fail("corrupt header");
+  const int64_t n = (int64_t)h.nx * h.ny * h.nz;
+  const int64_t P = h.net_H ? (int64_t)h.net_H * h.Q + h.net_H + 2 * ((int64_t)h.net_H * h.net_H + h.net_H) +
+                                  (int64_t)h.N * h.net_H + h.N
+                            : 0;
+  const uint64_t expect = sizeof(double) * ((h.has_f ? n : 0) + (uint64_t)h.N * n + (uint64_t)h.Q * h.N * h.N + h.N) +
+                          sizeof(float) * (P + h.net_N);
+  if (h.payload != expect) return fail("payload size does not match the header");
+  std::vector<double> f(h.has_f ? n : 0), W((size_t)h.N * n), ANq((size_t)h.Q * h.N * h.N), fN(h.N);
+  std::vector<float> params(P), scale(h.net_N);
+  Fnv fnv;
+  bool ok = true;
+  auto get = [&](void* d, size_t bytes) {
+    if (!bytes || !ok) return;
+    ok = std::fread(d, 1, bytes, fp) == bytes;
+    if (ok) fnv.add(d, bytes);
+  };
+  get(f.data(), sizeof(double) * f.size());
+  get(W.data(), sizeof(double) * W.size());
+  get(ANq.data(), sizeof(double) * ANq.size());
+  get(fN.data(), sizeof(double) * fN.size());
+  get(params.data(), sizeof(float) * params.size());
+  get(scale.data(), sizeof(float) * scale.size());
+  uint64_t sum = 0;
+  if (!ok || std::fread(&sum, sizeof(sum), 1, fp) != 1) return fail("truncated file");
+  std::fclose(fp);
+  if (sum != fnv.h) {
+    set_error(std::string("rbws_load: checksum mismatch (") + path + ")");
+    return RBWS_ERR_STATE;
+  }
+  rbws_grid g{h.nx, h.ny, h.nz};
+  rbws_blocks bl{h.bx, h.by, h.bz};
+  rbws_problem p = nullptr;
+  rbws_status rc = rbws_problem_create(&g, &bl, nullptr, h.Q, h.has_f ? f.data() : nullptr, device, &p);
+  if (rc != RBWS_OK) return rc;
+  if (h.N > 0 && (rc = rbws_set_basis(p, h.N, W.data(), ANq.data(), fN.data())) != RBWS_OK) {
+    rbws_problem_destroy(p);
+    return rc;
+  }
+  if (h.net_H > 0 &&
+      (rc = rbws_surrogate_set_params(p, h.net_H, params.data(), scale.data(), h.mu_lo, h.mu_hi)) != RBWS_OK) {
+    rbws_problem_destroy(p);
+    return rc;
+  }
+  *out = p;
+  return RBWS_OK;
+}

@@ -203,6 +203,10 @@ void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restar
 // ([B][N][N], lower triangle, upper part zero).
 void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu,
                           int B, double* c, int* info, double* L_out, cudaStream_t s);
+// eta[b] = ||R^{-1} c[b]||_1 with R upper triangular [Nmax][Nmax] (L1 indicator);
+// +inf where info[b] != 0.
+void launch_l1_indicator(int N, int Nmax, const double* R, const double* c, const int* info, int B,
+                         double* eta, cudaStream_t s);
 // u[b] = sum_j c[b][j] W[j]  (W: [N][n]).
 void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,
                  cudaStream_t s);

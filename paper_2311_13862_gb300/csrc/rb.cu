@@ -157,6 +157,29 @@ __global__ void k_norms_from_partials(const double* __restrict__ part, int B, in
   if (lane == 0) out[b] = sqrt(s) / fnorm;
 }
 
+// eta[b] = || R^{-1} c[b] ||_1 (R upper triangular [Nmax][Nmax]): the L1 norm of
+// the RB coefficients with respect to the unorthogonalised snapshots.  An
+// instance whose reduced solve failed (info[b] != 0) gets +inf.
+__global__ void k_l1_indicator(int N, int Nmax, const double* __restrict__ R, const double* __restrict__ c,
+                               const int* __restrict__ info, int B, double* __restrict__ eta) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (info[b] != 0) {
+    eta[b] = INFINITY;
+    return;
+  }
+  double x[160];
+  const double* cb = c + (int64_t)b * N;
+  double l1 = 0.0;
+  for (int i = N - 1; i >= 0; i--) {
+    double s = cb[i];
+    for (int k = i + 1; k < N; k++) s = fma(-R[i * Nmax + k], x[k], s);
+    x[i] = s / R[i * Nmax + i];
+    l1 += fabs(x[i]);
+  }
+  eta[b] = l1;
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < cap ? (g > 0 ? g : 1) : cap);
@@ -170,6 +193,11 @@ void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, con
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_reduced_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_reduced_solve<<<B, 128, smem, s>>>(N, Q, ANq, fN, mu, c, info, L_out);
+}
+
+void launch_l1_indicator(int N, int Nmax, const double* R, const double* c, const int* info, int B,
+                         double* eta, cudaStream_t s) {
+  k_l1_indicator<<<(B + 127) / 128, 128, 0, s>>>(N, Nmax, R, c, info, B, eta);
 }
 
 void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,

@@ -72,7 +72,7 @@ def _lib():
         L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
-        L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
+        L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, i32, P, P, C.POINTER(i32)]
         L.rbws_set_basis.argtypes = [P, i32, P, P, P]
         L.rbws_get_basis.argtypes = [P, P, P, P]
         L.rbws_reduced_solve.argtypes = [P, P, i32, P]
@@ -82,6 +82,8 @@ def _lib():
         L.rbws_surrogate_get_params.argtypes = [P, C.POINTER(i32), P, P]
         L.rbws_surrogate_forward.argtypes = [P, P, i32, i32, P]
         L.rbws_surrogate_loss_grad.argtypes = [P, P, P, i32, C.POINTER(d), P]
+        L.rbws_save.argtypes = [P, C.c_char_p]
+        L.rbws_load.argtypes = [C.c_char_p, C.c_int, C.POINTER(P)]
         L.rbws_solve_requests.argtypes = [i32, P, P, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
         L.rbws_autotune.argtypes = [P, i32, C.c_char_p, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                     C.POINTER(i32), C.POINTER(d)]
@@ -89,7 +91,7 @@ def _lib():
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
                      "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
-                     "rbws_solve_requests", "rbws_autotune"):
+                     "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -158,13 +160,16 @@ def rbws_apply_operator_static(h, mu, x, y, precision=FP64, stream=None):
            "rbws_apply_operator_static")
 
 
-def rbws_offline_greedy(h, mu_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12):
+INDICATOR_RESIDUAL, INDICATOR_L1 = 0, 1
+
+
+def rbws_offline_greedy(h, mu_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12, indicator=INDICATOR_RESIDUAL):
     mu = _host(np.atleast_2d(mu_train))
     sel = np.full(n_max, -1, dtype=np.int32)
     eta = np.full(n_max, np.nan)
     n_out = C.c_int32(0)
-    _check(_lib().rbws_offline_greedy(h, _hp(mu), mu.shape[0], n_max, greedy_tol, snapshot_tol, _hp(sel),
-                                      _hp(eta), C.byref(n_out)), "rbws_offline_greedy")
+    _check(_lib().rbws_offline_greedy(h, _hp(mu), mu.shape[0], n_max, greedy_tol, snapshot_tol, indicator,
+                                      _hp(sel), _hp(eta), C.byref(n_out)), "rbws_offline_greedy")
     N = n_out.value
     return N, sel[:N], eta[:N]
 
@@ -280,14 +285,29 @@ def rbws_autotune(h, B, cache_path=None):
     return tx.value, ty.value, zc.value, ms.value, sc.value
 
 
+def rbws_save(h, path):
+    _check(_lib().rbws_save(h, str(path).encode()), "rbws_save")
+
+
+def rbws_load(path, device=0):
+    h = C.c_void_p()
+    _check(_lib().rbws_load(str(path).encode(), device, C.byref(h)), "rbws_load")
+    return h
+
+
 class Problem:
     """Owning wrapper around an rbws_problem handle."""
 
-    def __init__(self, grid, blocks, f=None, device=0):
+    def __init__(self, grid, blocks, f=None, device=0, handle=None):
         self.grid, self.blocks = tuple(grid), tuple(blocks)
         self.Q = blocks[0] * blocks[1] * blocks[2]
         self.n = grid[0] * grid[1] * grid[2]
-        self.h = rbws_problem_create(grid, blocks, self.Q, f, device)
+        self.h = handle if handle is not None else rbws_problem_create(grid, blocks, self.Q, f, device)
+
+    @classmethod
+    def load(cls, path, grid, blocks, device=0):
+        """Wraps a problem restored by rbws_load (grid and blocks as saved)."""
+        return cls(grid, blocks, handle=rbws_load(path, device))
 
     def close(self):
         if self.h:

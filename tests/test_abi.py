@@ -78,3 +78,49 @@ def test_options_default_sets_every_field(lib_path):
     assert o.max_iters == 20000 and o.precond == rbws.PREC_JACOBI and o.precision == rbws.FP64
     assert o.max_restarts == 3 and o.inner_tol == 1e-2 and o.max_outer == 10 and o.check_every == 0
     assert o.stream is None and not o.profile
+
+
+def _ckpt_bytes(nx=4, ny=3, nz=2, blocks=(2, 1, 1), N=2, checksum_ok=True):
+    """A checkpoint in the library's documented layout (no network, f = 1)."""
+    import struct
+    import numpy as np
+    n = nx * ny * nz
+    Q = blocks[0] * blocks[1] * blocks[2]
+    payload = (np.arange(N * n, dtype=np.float64).tobytes() + np.ones(Q * N * N).tobytes()
+               + np.ones(N).tobytes())
+    hdr = struct.pack("<8sI11i2dQ", b"RBWSPRB1", 1, nx, ny, nz, blocks[0], blocks[1], blocks[2], Q, 0, N, 0, 0,
+                      0.0, 0.0, len(payload))
+    h = 1469598103934665603
+    for c in payload:
+        h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    if not checksum_ok:
+        h ^= 1
+    return hdr + payload + struct.pack("<Q", h)
+
+
+def test_checkpoint_loader_rejects_bad_files(tmp_path, lib_path):
+    from paper_2311_13862_gb300 import rbws
+    bad = tmp_path / "garbage.bin"
+    bad.write_bytes(b"not a checkpoint at all" * 10)
+    with pytest.raises(rbws.RbwsError, match="not a checkpoint"):
+        rbws.rbws_load(bad)
+    good = _ckpt_bytes()
+    trunc = tmp_path / "trunc.bin"
+    trunc.write_bytes(good[:-20])
+    with pytest.raises(rbws.RbwsError, match="truncated"):
+        rbws.rbws_load(trunc)
+    wrong = tmp_path / "wrong.bin"
+    wrong.write_bytes(_ckpt_bytes(checksum_ok=False))
+    with pytest.raises(rbws.RbwsError, match="checksum"):
+        rbws.rbws_load(wrong)
+
+
+def test_checkpoint_loader_accepts_a_valid_file_up_to_device_set_up(tmp_path, lib_path):
+    import torch
+    from paper_2311_13862_gb300 import rbws
+    if torch.cuda.is_available():
+        pytest.skip("GPU present: covered by the GPU checkpoint test")
+    ok = tmp_path / "ok.bin"
+    ok.write_bytes(_ckpt_bytes())
+    with pytest.raises(rbws.RbwsError, match="CUDA"):  # parsed and verified; no device here
+        rbws.rbws_load(ok)

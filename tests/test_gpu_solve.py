@@ -139,3 +139,21 @@ def test_msrb_without_basis_is_an_error():
     with rbws.Problem((8, 8, 8), (2, 1, 1)) as P:
         with pytest.raises(rbws.RbwsError, match="NO_BASIS"):
             solve(P, np.array([[1.0, 2.0]]), 1e-10, rbws.WARM_ZERO, precond=rbws.PREC_MSRB)
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """rbws_save after the offline stage (greedy + network), rbws_load in a new problem: the
+    online solves are bitwise identical."""
+    w = inputs.small(grid=(20, 16, 12), blocks=(2, 2, 1), n_max=6, n_train=16, n_test=4)
+    mu = inputs.test_mu(w)
+    path = tmp_path / "offline.rbws"
+    with rbws.Problem(w.grid, w.blocks) as P:
+        rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max)
+        rbws.rbws_train_surrogate(P.h, inputs.surrogate_mu(w, 256), hidden=32, epochs=20, batch=64,
+                                  mu_lo=w.mu_lo, mu_hi=w.mu_hi)
+        a = {m: solve(P, mu, 1e-10, m) for m in (rbws.WARM_GALERKIN, rbws.WARM_LEARNED)}
+        rbws.rbws_save(P.h, path)
+    with rbws.Problem.load(path, w.grid, w.blocks) as P2:
+        b = {m: solve(P2, mu, 1e-10, m) for m in (rbws.WARM_GALERKIN, rbws.WARM_LEARNED)}
+    for m in a:
+        assert np.array_equal(a[m][1], b[m][1]) and np.array_equal(a[m][4], b[m][4])

@@ -146,3 +146,25 @@ def test_msrb_with_empty_correction_is_jacobi():
     b = O.pcg(op, mu, f=f, precond=O.PREC_JACOBI, tol=1e-12)
     assert a.iters == b.iters
     assert np.array_equal(a.u, b.u)
+
+
+def test_l1_indicator_is_coefficient_norm_in_the_snapshot_basis():
+    """Sec. 3.1's indicator: the L1 norm of the RB solution's coefficients with respect to the
+    unorthogonalised snapshots.  Recomputed here from the snapshots themselves (least squares
+    of W c on U), independently of the Gram-Schmidt factor the oracle keeps."""
+    w = inputs.small(grid=(10, 9, 8), blocks=(2, 2, 1), n_max=5, n_train=20)
+    op = O.assemble(w.grid, w.blocks)
+    mus = inputs.train_mu(w)
+    b = O.greedy(op, mus, w.n_max, snapshot_tol=1e-13, indicator=1)
+    assert b.N == 5
+    U = np.stack([O.pcg(op, mus[i], tol=1e-13).u for i in b.selected]).T  # [n][N]
+    vals = []
+    for t in range(len(mus)):
+        if t in set(b.selected):
+            continue
+        c = O.rb_solve(b.ANq, b.fN, mus[t])
+        x, *_ = np.linalg.lstsq(U, b.W.T @ c, rcond=None)
+        vals.append(np.abs(x).sum())
+    assert b.eta_hist[-1] == pytest.approx(max(vals), rel=1e-6)
+    # the first pick is index 0 whatever the indicator, later picks maximise the L1 norm
+    assert b.selected[0] == 0
