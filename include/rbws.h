@@ -113,20 +113,36 @@ typedef struct {
                            NULL = an internal stream ordered after the legacy
                            default stream                                         */
   rbws_profile* profile; /* NULL = off; else zeroed and filled by the call        */
+  double* relres_hist;  /* NULL = off.  FP64 precision, rbws_solve_batch only:
+                           host [B][hist_len]; entry k of instance b = ||r_k||/||f||
+                           once A has been applied to k search directions (the
+                           recursive residual of Algorithm 1; at a true-residual
+                           check of Algorithm 4 the true residual replaces it).
+                           Entry 0 is the initial residual of u0.  Entries past
+                           the last iteration, or past hist_len, are NaN /
+                           not written.                                          */
+  int32_t hist_len;     /* entries per instance (>= 1 when relres_hist is set)   */
 } rbws_options;
 
 /* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64,
- * no profile). */
+ * no profile, no residual history). */
 RBWS_API void rbws_options_default(rbws_options* opt);
 
-/* Creates a problem on CUDA device `device` (Eq. 1).  The subdomain of each
- * node follows the block rule: along an axis with n nodes and b blocks, node
- * i (1..n) lies in block min(floor(b*i/(n+1)), b-1); id = (kz*by+ky)*bx+kx.
- * Exactly one of `blocks` / `subdomain_map` must be non-NULL; explicit maps
- * ([nz][ny][nx] uint8, values < Q) currently return RBWS_ERR_UNSUPPORTED.
- * Q must equal bx*by*bz and be <= 64.  f_host: host [n_dof] right-hand side,
- * or NULL for f = 1 at every interior node (copied).  Each axis needs
- * 2 <= n <= 1024. */
+/* Creates a problem on CUDA device `device` (Eq. 1; kappa = mu_q on
+ * subdomain q).  Exactly one of `blocks` / `subdomain_map` is non-NULL:
+ *  - blocks: the block rule.  Along an axis with n nodes and b blocks, node i
+ *    (1..n) lies in block min(floor(b*i/(n+1)), b-1); id = (kz*by+ky)*bx+kx;
+ *    1 <= b <= 16 per axis and Q must equal bx*by*bz.
+ *  - subdomain_map: host [nz][ny][nx] uint8, values < Q (copied), 1 <= Q <= 64.
+ *    The grid planes across which the map changes anywhere cut each axis into
+ *    segments; the map is constant on every box between them.  Supported up
+ *    to 64 segments per axis and 65536 coefficient classes (a node's class is
+ *    its own and its two neighbours' segments along each axis, so a segment
+ *    yields up to 3 classes per axis); larger maps return
+ *    RBWS_ERR_UNSUPPORTED, a value >= Q returns RBWS_ERR_INVALID_ARG.  Both
+ *    checks run before any device is touched.
+ * f_host: host [n_dof] right-hand side, or NULL for f = 1 at every interior
+ * node (copied).  Each axis needs 2 <= n <= 1024. */
 RBWS_API rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
                                 const uint8_t* subdomain_map, int32_t Q, const double* f_host,
                                 int device, rbws_problem* out);
@@ -275,8 +291,9 @@ RBWS_API rbws_status rbws_autotune(rbws_problem p, int32_t B, const char* cache_
  * probs[r]] float64.  iters_out (host [n_req]); relres_out, status_out and
  * latency_ms_out (host [n_req]) may be NULL.  latency_ms_out[r] = time from
  * the start of the earliest batch to the moment request r reached its final
- * status, from the GPU's global timer.  opt->stream and opt->profile must be
- * NULL.  A problem must not be used by another call meanwhile. */
+ * status, from the GPU's global timer.  opt->stream, opt->profile and
+ * opt->relres_hist must be NULL.  A problem must not be used by another call
+ * meanwhile. */
 RBWS_API rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs,
                                          const double* const* mu, void* const* u_out, double tol,
                                          int32_t warm, const rbws_options* opt, int32_t* iters_out,

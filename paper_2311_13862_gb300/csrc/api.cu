@@ -52,15 +52,14 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-AxisClasses make_axis(int n, int b) {
+// Classes of one axis from the segment of every node (seg: [n], values < b).
+AxisClasses make_axis_segments(const std::vector<int>& seg, int b) {
+  const int n = (int)seg.size();
   AxisClasses a;
   a.n = n;
   a.b = b;
   a.cls.resize(n);
-  auto blk = [&](int i) {  // i: 1..n
-    int k = (int)(((int64_t)b * i) / (n + 1));
-    return k < b - 1 ? k : b - 1;
-  };
+  auto blk = [&](int i) { return seg[i - 1]; };  // i: 1..n
   std::map<std::tuple<int, int, int>, int> ids;
   for (int i = 1; i <= n; i++) {
     const int own = blk(i), lo = i > 1 ? blk(i - 1) : -1, hi = i < n ? blk(i + 1) : -1;
@@ -81,6 +80,56 @@ AxisClasses make_axis(int n, int b) {
   return a;
 }
 
+// Block rule: along an axis with n nodes and b blocks, node i (1..n) lies in
+// block min(floor(b*i/(n+1)), b-1).
+AxisClasses make_axis(int n, int b) {
+  std::vector<int> seg(n);
+  for (int i = 1; i <= n; i++) {
+    const int k = (int)(((int64_t)b * i) / (n + 1));
+    seg[i - 1] = k < b - 1 ? k : b - 1;
+  }
+  return make_axis_segments(seg, b);
+}
+
+// An explicit map [nz][ny][nx] is cut by every grid plane across which it
+// changes somewhere; between consecutive cuts the map does not change along
+// any axis, so it is constant on each box of that tensor-product partition
+// and the per-axis class machinery of the block rule applies unchanged.
+// Fills the per-axis segments and the box -> subdomain table; returns "" or
+// the reason the map is rejected.
+constexpr int kMaxSegments = 64;       // per axis (class ids stay below 256)
+constexpr int kMaxClasses = 1 << 16;   // coefficient rows per instance
+
+std::string map_segments(int nx, int ny, int nz, const uint8_t* map, int Q, std::vector<int>& sx,
+                         std::vector<int>& sy, std::vector<int>& sz, std::vector<uint8_t>& segq) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t t = 0; t < n; t++)
+    if (map[t] >= Q) return "map value " + std::to_string(map[t]) + " >= Q";
+  auto at = [&](int i, int j, int k) { return map[((int64_t)k * ny + j) * nx + i]; };
+  std::vector<char> cx(nx, 0), cy(ny, 0), cz(nz, 0);  // cut before node index
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        const uint8_t v = at(i, j, k);
+        if (i > 0 && at(i - 1, j, k) != v) cx[i] = 1;
+        if (j > 0 && at(i, j - 1, k) != v) cy[j] = 1;
+        if (k > 0 && at(i, j, k - 1) != v) cz[k] = 1;
+      }
+  auto segs = [](const std::vector<char>& c, std::vector<int>& s) {
+    s.assign(c.size(), 0);
+    for (size_t i = 1; i < c.size(); i++) s[i] = s[i - 1] + c[i];
+    return s.back() + 1;
+  };
+  const int bx = segs(cx, sx), by = segs(cy, sy), bz = segs(cz, sz);
+  if (bx > kMaxSegments || by > kMaxSegments || bz > kMaxSegments)
+    return "the map needs more than " + std::to_string(kMaxSegments) + " segments along an axis";
+  segq.assign((size_t)bx * by * bz, 0);
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) segq[((size_t)sz[k] * by + sy[j]) * bx + sx[i]] = at(i, j, k);
+  return "";
+}
+
 }  // namespace
 
 struct rbws_problem_s {
@@ -91,6 +140,8 @@ struct rbws_problem_s {
   AxisClasses ax, ay, az;
   uint8_t* d_cls = nullptr;  // cx | cy | cz
   int8_t* d_keys = nullptr;  // kx | ky | kz
+  std::vector<uint8_t> h_map;  // explicit subdomain map [n] (empty: block rule)
+  uint8_t* d_segq = nullptr;   // explicit map: box (bx*by*bz segments) -> subdomain
   Geo geo{};
   double* d_f = nullptr;     // nullptr: f == 1
   double* d_ones = nullptr;  // ones vector (for W^T f when f == 1)
@@ -217,7 +268,7 @@ rbws_status coef_tables(rbws_problem p, const double* d_mu, int B, double** c64,
   const int8_t* kx = p->d_keys;
   const int8_t* ky = kx + p->ax.key.size();
   const int8_t* kz = ky + p->ay.key.size();
-  launch_coef_tables(p->geo, kx, ky, kz, p->bx, p->by, p->sx, p->sy, p->sz, p->Q, d_mu, B, *c64,
+  launch_coef_tables(p->geo, kx, ky, kz, p->bx, p->by, p->d_segq, p->sx, p->sy, p->sz, p->Q, d_mu, B, *c64,
                      c32 ? *c32 : nullptr, p->cur);
   p->launches += 1;
   CK(cudaGetLastError());
@@ -507,9 +558,20 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
   }
   fill((double*)a.fnorm, B, p->fnorm, p->cur);
   p->launches += 1;
+  if (o.relres_hist) {
+    int err = 0;
+    a.hist_len = o.hist_len;
+    a.hist = (double*)p->buf("hist", sizeof(double) * (size_t)B * o.hist_len, &err);
+    if (err) return (rbws_status)err;
+    fill(a.hist, (int64_t)B * o.hist_len, std::nan(""), p->cur);
+    p->launches += 1;
+  }
   CKI(run_pcg<double>(p, a, t, o.max_restarts, o.check_every, nullptr, true, o.profile));
   st.resize(B);
   CK(cudaMemcpyAsync(st.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, p->cur));
+  if (o.relres_hist)
+    CK(cudaMemcpyAsync(o.relres_hist, a.hist, sizeof(double) * (size_t)B * o.hist_len, cudaMemcpyDeviceToHost,
+                       p->cur));
   CK(cudaStreamSynchronize(p->cur));
   return RBWS_OK;
 }
@@ -918,6 +980,10 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
     set_error("solve: unknown precision");
     return RBWS_ERR_INVALID_ARG;
   }
+  if (o.relres_hist && (o.precision != RBWS_FP64 || o.hist_len < 1)) {
+    set_error("solve: the residual history needs FP64 precision and hist_len >= 1");
+    return RBWS_ERR_INVALID_ARG;
+  }
   return RBWS_OK;
 }
 
@@ -966,6 +1032,8 @@ void rbws_options_default(rbws_options* o) {
   o->check_every = 0;
   o->stream = nullptr;
   o->profile = nullptr;
+  o->relres_hist = nullptr;
+  o->hist_len = 0;
 }
 
 rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
@@ -980,24 +1048,42 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
     set_error("rbws_problem_create: give exactly one of blocks / subdomain_map");
     return RBWS_ERR_INVALID_ARG;
   }
-  if (subdomain_map) {
-    set_error("rbws_problem_create: explicit subdomain maps are not supported by the CUDA path");
-    return RBWS_ERR_UNSUPPORTED;
-  }
   const int dims[3] = {grid->nx, grid->ny, grid->nz};
   for (int d : dims)
     if (d < 2 || d > kMaxAxis) {
       set_error("rbws_problem_create: each axis needs 2..1024 interior nodes");
       return RBWS_ERR_INVALID_ARG;
     }
-  if (blocks->bx < 1 || blocks->by < 1 || blocks->bz < 1 || blocks->bx > 16 || blocks->by > 16 ||
-      blocks->bz > 16 || Q != blocks->bx * blocks->by * blocks->bz || Q > kMaxQ) {
-    set_error("rbws_problem_create: need 1 <= b <= 16 per axis and Q = bx*by*bz <= 64");
-    return RBWS_ERR_INVALID_ARG;
-  }
-  if (blocks->bx > grid->nx || blocks->by > grid->ny || blocks->bz > grid->nz) {
-    set_error("rbws_problem_create: more blocks than nodes along an axis");
-    return RBWS_ERR_INVALID_ARG;
+  std::vector<int> segx, segy, segz;
+  std::vector<uint8_t> segq;
+  if (subdomain_map) {
+    if (Q < 1 || Q > kMaxQ) {
+      set_error("rbws_problem_create: need 1 <= Q <= 64");
+      return RBWS_ERR_INVALID_ARG;
+    }
+    const std::string why = map_segments(grid->nx, grid->ny, grid->nz, subdomain_map, Q, segx, segy, segz, segq);
+    if (!why.empty()) {
+      set_error("rbws_problem_create: " + why);
+      return why.compare(0, 9, "map value") == 0 ? RBWS_ERR_INVALID_ARG : RBWS_ERR_UNSUPPORTED;
+    }
+    const int64_t ncls = (int64_t)make_axis_segments(segx, segx.back() + 1).ncls() *
+                         make_axis_segments(segy, segy.back() + 1).ncls() *
+                         make_axis_segments(segz, segz.back() + 1).ncls();
+    if (ncls > kMaxClasses) {
+      set_error("rbws_problem_create: the map has " + std::to_string(ncls) + " coefficient classes (at most " +
+                std::to_string(kMaxClasses) + ")");
+      return RBWS_ERR_UNSUPPORTED;
+    }
+  } else {
+    if (blocks->bx < 1 || blocks->by < 1 || blocks->bz < 1 || blocks->bx > 16 || blocks->by > 16 ||
+        blocks->bz > 16 || Q != blocks->bx * blocks->by * blocks->bz || Q > kMaxQ) {
+      set_error("rbws_problem_create: need 1 <= b <= 16 per axis and Q = bx*by*bz <= 64");
+      return RBWS_ERR_INVALID_ARG;
+    }
+    if (blocks->bx > grid->nx || blocks->by > grid->ny || blocks->bz > grid->nz) {
+      set_error("rbws_problem_create: more blocks than nodes along an axis");
+      return RBWS_ERR_INVALID_ARG;
+    }
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -1010,17 +1096,30 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   p->nx = grid->nx;
   p->ny = grid->ny;
   p->nz = grid->nz;
-  p->bx = blocks->bx;
-  p->by = blocks->by;
-  p->bz = blocks->bz;
+  if (subdomain_map) {
+    p->bx = segx.back() + 1;
+    p->by = segy.back() + 1;
+    p->bz = segz.back() + 1;
+    p->h_map.assign(subdomain_map, subdomain_map + (int64_t)grid->nx * grid->ny * grid->nz);
+  } else {
+    p->bx = blocks->bx;
+    p->by = blocks->by;
+    p->bz = blocks->bz;
+  }
   p->Q = Q;
   p->n = (int64_t)p->nx * p->ny * p->nz;
   p->sx = (double)(p->nx + 1) * (p->nx + 1);
   p->sy = (double)(p->ny + 1) * (p->ny + 1);
   p->sz = (double)(p->nz + 1) * (p->nz + 1);
-  p->ax = make_axis(p->nx, p->bx);
-  p->ay = make_axis(p->ny, p->by);
-  p->az = make_axis(p->nz, p->bz);
+  if (subdomain_map) {
+    p->ax = make_axis_segments(segx, p->bx);
+    p->ay = make_axis_segments(segy, p->by);
+    p->az = make_axis_segments(segz, p->bz);
+  } else {
+    p->ax = make_axis(p->nx, p->bx);
+    p->ay = make_axis(p->ny, p->by);
+    p->az = make_axis(p->nz, p->bz);
+  }
   auto fail = [&](cudaError_t e, const char* w) {
     cuda_fail(e, w);
     rbws_problem_destroy(p);
@@ -1045,6 +1144,10 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   if ((e = cudaMalloc(&p->d_keys, keys.size())) != cudaSuccess) return fail(e, "cudaMalloc");
   cudaMemcpy(p->d_cls, cls.data(), cls.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_keys, keys.data(), keys.size(), cudaMemcpyHostToDevice);
+  if (!segq.empty()) {
+    if ((e = cudaMalloc(&p->d_segq, segq.size())) != cudaSuccess) return fail(e, "cudaMalloc");
+    cudaMemcpy(p->d_segq, segq.data(), segq.size(), cudaMemcpyHostToDevice);
+  }
   Geo& g = p->geo;
   g.nx = p->nx;
   g.ny = p->ny;
@@ -1088,6 +1191,7 @@ void rbws_problem_destroy(rbws_problem p) {
     if (kv.second.ptr) cudaFree(kv.second.ptr);
   cudaFree(p->d_cls);
   cudaFree(p->d_keys);
+  cudaFree(p->d_segq);
   cudaFree(p->d_f);
   cudaFree(p->d_ones);
   cudaFree(p->d_W);
@@ -1149,8 +1253,9 @@ rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu, int32_t
   const int8_t* kx = p->d_keys;
   const int8_t* ky = kx + p->ax.key.size();
   const int8_t* kz = ky + p->ay.key.size();
-  return (rbws_status)apply_operator_static(p->device, p->geo, kx, ky, kz, p->bx, p->by, p->sx, p->sy, p->sz,
-                                            p->Q, mu, B, x, y, precision, p->cur, choose_tile(p->nx));
+  return (rbws_status)apply_operator_static(p->device, p->geo, kx, ky, kz, p->bx, p->by, p->d_segq, p->sx,
+                                            p->sy, p->sz, p->Q, mu, B, x, y, precision, p->cur,
+                                            choose_tile(p->nx));
 }
 
 rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const double* ANq,
@@ -1784,8 +1889,9 @@ rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const 
       return RBWS_ERR_INVALID_ARG;
     }
   CKI(check_solve_options(o, tol, warm));
-  if (o.stream || o.profile) {
-    set_error("rbws_solve_requests: runs each grid on its problem's own stream; stream and profile must be NULL");
+  if (o.stream || o.profile || o.relres_hist) {
+    set_error("rbws_solve_requests: runs each grid on its problem's own stream; stream, profile and "
+              "relres_hist must be NULL");
     return RBWS_ERR_INVALID_ARG;
   }
   // group the requests by problem (one batched solve per grid)
@@ -1871,9 +1977,10 @@ rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const 
 // surrogate network) and the problem description, so a later process can
 // solve online without repeating the offline stage.
 //
-// File layout (little endian): "RBWSPRB1", u32 version = 1, i32 nx ny nz bx
-// by bz Q has_f N net_H net_N, f64 mu_lo mu_hi, u64 payload bytes, then the
-// payload: f [n] (if has_f), W [N][n], ANq [Q][N][N], fN [N] (f64), network
+// File layout (little endian): "RBWSPRB1", u32 version = 2, i32 nx ny nz bx
+// by bz Q has_f N net_H net_N has_map, f64 mu_lo mu_hi, u64 payload bytes,
+// then the payload: the subdomain map [n] (u8, if has_map; bx by bz are then
+// ignored), f [n] (if has_f), W [N][n], ANq [Q][N][N], fN [N] (f64), network
 // parameters [P] and coefficient scales [net_N] (f32), then u64 FNV-1a of
 // the payload.
 // ---------------------------------------------------------------------------
@@ -1893,7 +2000,7 @@ struct Fnv {
 struct CkptHeader {
   char magic[8];
   uint32_t version;
-  int32_t nx, ny, nz, bx, by, bz, Q, has_f, N, net_H, net_N;
+  int32_t nx, ny, nz, bx, by, bz, Q, has_f, N, net_H, net_N, has_map;
   double mu_lo, mu_hi;
   uint64_t payload;
 };
@@ -1911,7 +2018,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   const int N = p->N;
   CkptHeader h{};
   std::memcpy(h.magic, "RBWSPRB1", 8);
-  h.version = 1;
+  h.version = 2;
   h.nx = p->nx;
   h.ny = p->ny;
   h.nz = p->nz;
@@ -1920,6 +2027,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   h.bz = p->bz;
   h.Q = p->Q;
   h.has_f = p->d_f != nullptr;
+  h.has_map = !p->h_map.empty();
   h.N = N;
   h.net_H = p->d_w32 ? p->net_H : 0;
   h.net_N = p->d_w32 ? p->net_N : 0;
@@ -1934,7 +2042,8 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
     CK(cudaMemcpy(scale.data(), p->d_cscale, sizeof(float) * scale.size(), cudaMemcpyDeviceToHost));
   }
   const size_t szA = sizeof(double) * (N > 0 ? p->h_ANq.size() : 0), szF = sizeof(double) * (N > 0 ? N : 0);
-  h.payload = sizeof(double) * (f.size() + W.size()) + szA + szF + sizeof(float) * (params.size() + scale.size());
+  h.payload = p->h_map.size() + sizeof(double) * (f.size() + W.size()) + szA + szF +
+              sizeof(float) * (params.size() + scale.size());
   FILE* fp = std::fopen(path, "wb");
   if (!fp) {
     set_error(std::string("rbws_save: cannot open ") + path);
@@ -1947,6 +2056,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
     ok = std::fwrite(d, 1, bytes, fp) == bytes;
     fnv.add(d, bytes);
   };
+  put(p->h_map.data(), p->h_map.size());
   put(f.data(), sizeof(double) * f.size());
   put(W.data(), sizeof(double) * W.size());
   if (N > 0) {
@@ -1982,18 +2092,21 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
     return RBWS_ERR_STATE;
   };
   if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "RBWSPRB1", 8) != 0) return fail("not a checkpoint");
-  if (h.version != 1) return fail("unsupported version");
+  if (h.version != 2) return fail("unsupported version");
   if (h.nx < 2 || h.ny < 2 || h.nz < 2 || h.nx > kMaxAxis || h.ny > kMaxAxis || h.nz > kMaxAxis ||
-      h.N < 0 || h.N > 160 || h.Q != h.bx * h.by * h.bz || h.net_H < 0 || h.net_H > 4096 ||
+      h.N < 0 || h.N > 160 || h.Q < 1 || h.Q > kMaxQ || (h.has_map != 0 && h.has_map != 1) ||
+      (!h.has_map && h.Q != h.bx * h.by * h.bz) || h.net_H < 0 || h.net_H > 4096 ||
       (h.net_H > 0 && h.net_N != h.N))
     return fail("corrupt header");
   const int64_t n = (int64_t)h.nx * h.ny * h.nz;
   const int64_t P = h.net_H ? (int64_t)h.net_H * h.Q + h.net_H + 2 * ((int64_t)h.net_H * h.net_H + h.net_H) +
                                   (int64_t)h.N * h.net_H + h.N
                             : 0;
-  const uint64_t expect = sizeof(double) * ((h.has_f ? n : 0) + (uint64_t)h.N * n + (uint64_t)h.Q * h.N * h.N + h.N) +
+  const uint64_t expect = (h.has_map ? (uint64_t)n : 0) +
+                          sizeof(double) * ((h.has_f ? n : 0) + (uint64_t)h.N * n + (uint64_t)h.Q * h.N * h.N + h.N) +
                           sizeof(float) * (P + h.net_N);
   if (h.payload != expect) return fail("payload size does not match the header");
+  std::vector<uint8_t> map(h.has_map ? n : 0);
   std::vector<double> f(h.has_f ? n : 0), W((size_t)h.N * n), ANq((size_t)h.Q * h.N * h.N), fN(h.N);
   std::vector<float> params(P), scale(h.net_N);
   Fnv fnv;
@@ -2003,6 +2116,7 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
     ok = std::fread(d, 1, bytes, fp) == bytes;
     if (ok) fnv.add(d, bytes);
   };
+  get(map.data(), map.size());
   get(f.data(), sizeof(double) * f.size());
   get(W.data(), sizeof(double) * W.size());
   get(ANq.data(), sizeof(double) * ANq.size());
@@ -2019,7 +2133,8 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
   rbws_grid g{h.nx, h.ny, h.nz};
   rbws_blocks bl{h.bx, h.by, h.bz};
   rbws_problem p = nullptr;
-  rbws_status rc = rbws_problem_create(&g, &bl, nullptr, h.Q, h.has_f ? f.data() : nullptr, device, &p);
+  rbws_status rc = rbws_problem_create(&g, h.has_map ? nullptr : &bl, h.has_map ? map.data() : nullptr, h.Q,
+                                       h.has_f ? f.data() : nullptr, device, &p);
   if (rc != RBWS_OK) return rc;
   if (h.N > 0 && (rc = rbws_set_basis(p, h.N, W.data(), ANq.data(), fN.data())) != RBWS_OK) {
     rbws_problem_destroy(p);

@@ -30,9 +30,9 @@ constexpr int kMaxAxis = 1024;
 constexpr int kMaxClassPerAxis = 3 * 16 + 2;
 
 struct AxisClasses {
-  int n = 0, b = 0;
+  int n = 0, b = 0;           // nodes, segments (blocks) along the axis
   std::vector<uint8_t> cls;   // [n] class id of each node
-  std::vector<int8_t> key;    // [ncls][3] (own, lo, hi) blocks, -1 = boundary
+  std::vector<int8_t> key;    // [ncls][3] (own, lo, hi) segments, -1 = boundary
   int ncls() const { return (int)key.size() / 3; }
 };
 
@@ -123,6 +123,9 @@ struct CGArgs {
   // 32-byte FP32 schedule (k_cg_a32_v4 / k_cg_b32_v4): s is never stored and
   // the u update of iteration k is applied by phase A of iteration k+1.
   double* alpha;        // [2][B] alpha_k by parity; 0 = no pending update
+  // residual history (FP64 iteration): hist[b][k] = ||r_k|| / ||f||
+  double* hist;         // [B][hist_len] or nullptr
+  int hist_len;
 };
 
 // ---------------------------------------------------------------------------
@@ -133,11 +136,13 @@ struct Tile {
 };
 
 // Builds per-instance coefficient tables: coef64 [B][ncls][8] (and coef32 if
-// non-null) from mu [B][Q] on the device.
+// non-null) from mu [B][Q] on the device.  The subdomain of segment box
+// (sx, sy, sz) is segq[(sz*by + sy)*bx + sx], or that index itself when segq
+// is null (the block rule).
 void launch_coef_tables(const Geo& g, const int8_t* keys_x, const int8_t* keys_y,
-                        const int8_t* keys_z, int bx, int by, double sx, double sy, double sz,
-                        int Q, const double* mu, int B, double* coef64, float* coef32,
-                        cudaStream_t s);
+                        const int8_t* keys_z, int bx, int by, const uint8_t* segq, double sx,
+                        double sy, double sz, int Q, const double* mu, int B, double* coef64,
+                        float* coef32, cudaStream_t s);
 
 // y[b] = A(mu_b) x[b]; x_stride = 0 broadcasts one x to every instance.
 template <typename T>
@@ -263,8 +268,9 @@ void launch_reduced_cg_step(int N, int Q, const double* ANq, const double* fN, c
 size_t static_scratch_need(int Q, int ncls, int B, bool fp32);
 size_t static_scratch_capacity();
 int apply_operator_static(int device, const Geo& g, const int8_t* kx, const int8_t* ky, const int8_t* kz,
-                          int bx, int by, double sx, double sy, double sz, int Q, const double* mu_host,
-                          int B, const void* x, void* y, int precision, cudaStream_t s, Tile t);
+                          int bx, int by, const uint8_t* segq, double sx, double sy, double sz, int Q,
+                          const double* mu_host, int B, const void* x, void* y, int precision,
+                          cudaStream_t s, Tile t);
 
 // ---------------------------------------------------------------------------
 // Error reporting

@@ -73,7 +73,8 @@ size_t static_scratch_capacity() { return kStaticScratchBytes; }
 // the problem struct).  g: the problem's geometry; keys: per-axis class keys
 // on the device; d_first_*: sizes of the key arrays.
 int apply_operator_static(int device, const Geo& g, const int8_t* kx, const int8_t* ky, const int8_t* kz,
-                          int bx, int by, double sx, double sy, double sz, int Q, const double* mu_host,
+                          int bx, int by, const uint8_t* segq, double sx, double sy, double sz, int Q,
+                          const double* mu_host,
                           int B, const void* x, void* y, int precision, cudaStream_t s, Tile t) {
   const int ncls = g.ncls();
   const bool fp32 = precision == RBWS_FP32_IR;
@@ -93,7 +94,7 @@ int apply_operator_static(int device, const Geo& g, const int8_t* kx, const int8
                     : nullptr;
   cudaError_t e = cudaMemcpyAsync(d_mu, mu_host, sizeof(double) * (size_t)B * Q, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "rbws_apply_operator_static: copy mu");
-  launch_coef_tables(g, kx, ky, kz, bx, by, sx, sy, sz, Q, d_mu, B, c64, c32, s);
+  launch_coef_tables(g, kx, ky, kz, bx, by, segq, sx, sy, sz, Q, d_mu, B, c64, c32, s);
   if (fp32)
     launch_apply<float>(g, t, c32, B, static_cast<const float*>(x), g.n, static_cast<float*>(y), s);
   else

@@ -183,9 +183,10 @@ __device__ __forceinline__ TilePos tile_pos(const Geo& g, int tiles_x, int zc) {
 // Coefficient tables
 // ---------------------------------------------------------------------------
 __global__ void k_coef_tables(Geo g, const int8_t* __restrict__ kx, const int8_t* __restrict__ ky,
-                              const int8_t* __restrict__ kz, int bx, int by, double sx, double sy,
-                              double sz, int Q, const double* __restrict__ mu, int B,
-                              double* __restrict__ coef64, float* __restrict__ coef32) {
+                              const int8_t* __restrict__ kz, int bx, int by,
+                              const uint8_t* __restrict__ segq, double sx, double sy, double sz, int Q,
+                              const double* __restrict__ mu, int B, double* __restrict__ coef64,
+                              float* __restrict__ coef32) {
   const int ncls = g.ncls();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)ncls * B) return;
@@ -195,7 +196,10 @@ __global__ void k_coef_tables(Geo g, const int8_t* __restrict__ kx, const int8_t
   const int oy = ky[3 * cyi], ly = ky[3 * cyi + 1], hy = ky[3 * cyi + 2];
   const int oz = kz[3 * czi], lz = kz[3 * czi + 1], hz = kz[3 * czi + 2];
   const double* m = mu + (int64_t)b * Q;
-  auto kap = [&](int ax, int ay, int az) { return m[(az * by + ay) * bx + ax]; };
+  auto kap = [&](int ax, int ay, int az) {
+    const int box = (az * by + ay) * bx + ax;
+    return m[segq ? segq[box] : box];
+  };
   const double kc = kap(ox, oy, oz);
   // face coefficient: arithmetic mean of the two kappas; boundary face: own kappa
   auto face = [&](int nb_ok, double knb, double s) { return nb_ok ? 0.5 * (kc + knb) * s : kc * s; };
@@ -344,6 +348,10 @@ __global__ void k_cg_finalize(CGArgs<T> a, int parity, int mode, int max_restart
   if (lane != 0) return;
   InstState& s = a.st[b];
   const double rel = sqrt(v.y) / a.fnorm[b];
+  if (a.hist) {
+    const int k = mode == 0 ? 0 : s.iters;
+    if (k < a.hist_len) a.hist[(int64_t)b * a.hist_len + k] = rel;
+  }
   if (mode == 0) {
     s.relres0 = rel;
     s.relres = rel;
@@ -397,6 +405,7 @@ __global__ void k_cg_a(CGArgs<T> a, int parity) {
       int run = 0;
       if (status == ST_ACTIVE) {
         const double rel = sqrt(cur.y) / a.fnorm[b];
+        if (leader && a.hist && st->iters < a.hist_len) a.hist[(int64_t)b * a.hist_len + st->iters] = rel;
         if (rel < a.tol) {
           if (leader) {
             st->status = a.ru ? ST_PAUSED : ST_CONVERGED;
@@ -782,12 +791,13 @@ dim3 cg_grid(const CGArgs<T>& a) {
 // Launchers
 // ---------------------------------------------------------------------------
 void launch_coef_tables(const Geo& g, const int8_t* kx, const int8_t* ky, const int8_t* kz, int bx,
-                        int by, double sx, double sy, double sz, int Q, const double* mu, int B,
-                        double* coef64, float* coef32, cudaStream_t s) {
+                        int by, const uint8_t* segq, double sx, double sy, double sz, int Q,
+                        const double* mu, int B, double* coef64, float* coef32, cudaStream_t s) {
   const int64_t total = (int64_t)g.ncls() * B;
   const int threads = 128;
   const int blocks = (int)((total + threads - 1) / threads);
-  k_coef_tables<<<blocks, threads, 0, s>>>(g, kx, ky, kz, bx, by, sx, sy, sz, Q, mu, B, coef64, coef32);
+  k_coef_tables<<<blocks, threads, 0, s>>>(g, kx, ky, kz, bx, by, segq, sx, sy, sz, Q, mu, B, coef64,
+                                           coef32);
 }
 
 template <typename T>

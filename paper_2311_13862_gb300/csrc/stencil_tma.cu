@@ -93,7 +93,8 @@ __device__ __forceinline__ float f4(const float4& v, int e) {
 template <int kMode>
 __global__ void __launch_bounds__(256, 3)
     k_cg_a_tma(const __grid_constant__ CUtensorMap tm_s, const __grid_constant__ CUtensorMap tm_p0,
-               const __grid_constant__ CUtensorMap tm_p1, CGArgs<float> a, int parity, int* err) {
+               const __grid_constant__ CUtensorMap tm_p1, const __grid_constant__ CUtensorMap tm_u,
+               CGArgs<float> a, int parity, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ double red[64];
@@ -154,16 +155,23 @@ __global__ void __launch_bounds__(256, 3)
   const int BX = TXN + 8, BY = TY + 2;
   const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float));
   const int arr_floats = ((BX * BY * 4 + 127) / 128) * 32;  // 128-byte aligned arrays
+  // kMode 1 also stages the own (halo-free) TXN x TY tile of u for planes z0 .. z1-1
+  const unsigned own_bytes = (unsigned)(TXN * TY * sizeof(float));
+  const int own_floats = kMode == 1 ? ((TXN * TY * 4 + 127) / 128) * 32 : 0;
+  const int stage_floats = 2 * arr_floats + own_floats;
   float* stage_base = reinterpret_cast<float*>(smem_raw);
-  auto s_tile = [&](int st) { return stage_base + (2 * st) * arr_floats; };
-  auto p_tile = [&](int st) { return stage_base + (2 * st + 1) * arr_floats; };
+  auto s_tile = [&](int st) { return stage_base + st * stage_floats; };
+  auto p_tile = [&](int st) { return stage_base + st * stage_floats + arr_floats; };
+  auto u_tile = [&](int st) { return stage_base + st * stage_floats + 2 * arr_floats; };
   const CUtensorMap* mp = parity ? &tm_p1 : &tm_p0;
   const int nq = z1 - z0 + 2;  // planes z0-1 .. z1
   auto issue = [&](int j) {    // plane z0-1+j into stage j % kStages (thread 0 only)
     const int st = j % kStages;
-    mbar_expect_tx(&bars[st], 2 * box_bytes);
+    const bool with_u = kMode == 1 && j >= 1 && j <= nq - 2;
+    mbar_expect_tx(&bars[st], 2 * box_bytes + (with_u ? own_bytes : 0u));
     tma_load_4d(s_tile(st), &tm_s, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
     tma_load_4d(p_tile(st), mp, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+    if (with_u) tma_load_4d(u_tile(st), &tm_u, x0, y0, z0 - 1 + j, b, &bars[st]);
   };
   if (tid == 0) {
     for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(256, 3)
   const int i = x0 + lx, jn = y0 + ly;
   const bool own = i < g.nx && jn < g.ny;
   const int cofs = (ly + 1) * BX + lx + 4;  // own group in a box
+  const int lofs = ly * TXN + lx;           // own group in an own-tile array
   const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
   const int64_t plane = (int64_t)g.nx * g.ny;
   const int64_t col = (int64_t)jn * g.nx + i;
@@ -209,8 +218,6 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z < z1; ++z) {
       const int k = z - z0 + 1;  // index of plane z; plane z+1 is k+1
       const int sk = k % kStages, sn = (k + 1) % kStages;
-      float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (kMode == 1 && own) u4 = *reinterpret_cast<const float4*>(ub + z * plane + col);  // in flight
       bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
       if (!to && own) {
         const float4 xp = own_p(sn);
@@ -251,8 +258,8 @@ __global__ void __launch_bounds__(256, 3)
         if (kMode == 0) {
           *reinterpret_cast<float4*>(qb + z * plane + col) = make_float4(y[0], y[1], y[2], y[3]);
         } else {
-          const float4 po4 = ld4s(Pp + cofs);  // own p_old of plane z, from the stage
-          *reinterpret_cast<float4*>(ub + z * plane + col) = fma4(alpha_prev, po4, u4);
+          const float4 po4 = ld4s(Pp + cofs);  // own p_old and u of plane z, from the stage
+          *reinterpret_cast<float4*>(ub + z * plane + col) = fma4(alpha_prev, po4, ld4s(u_tile(sk) + lofs));
         }
         xm = xc;
         xc = xp;
@@ -297,13 +304,13 @@ abort:
 // Phase B of the 32-byte s-form schedule.  The stored residual is
 // s = D^{-1} r (s = r without a preconditioner).  alpha_k = rho_k / gamma_k;
 // s -= alpha_k D^{-1} A p_k with A p_k recomputed from TMA-staged planes of
-// p_k; r = D s; partials rho_{k+1} = r.s and ||r||^2.  Reads s (own) and p
-// (halo from L2), writes s: 12 bytes per DoF.  alpha_k goes to
-// a.alpha[parity ^ 1][b] for the next phase A.
+// p_k; r = D s; partials rho_{k+1} = r.s and ||r||^2.  Reads s (own tile,
+// staged in the same ring) and p (halo from L2), writes s: 12 bytes per DoF.
+// alpha_k goes to a.alpha[parity ^ 1][b] for the next phase A.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 3)
     k_cg_b_s_tma(const __grid_constant__ CUtensorMap tm_p0, const __grid_constant__ CUtensorMap tm_p1,
-                 CGArgs<float> a, int parity, int* err) {
+                 const __grid_constant__ CUtensorMap tm_s, CGArgs<float> a, int parity, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ double red[64];
@@ -362,14 +369,19 @@ __global__ void __launch_bounds__(256, 3)
   const int BX = TXN + 8, BY = TY + 2;
   const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float));
   const int arr_floats = ((BX * BY * 4 + 127) / 128) * 32;
+  const unsigned own_bytes = (unsigned)(TXN * TY * sizeof(float));
+  const int stage_floats = arr_floats + ((TXN * TY * 4 + 127) / 128) * 32;
   float* stage_base = reinterpret_cast<float*>(smem_raw);
-  auto p_tile = [&](int st) { return stage_base + st * arr_floats; };
+  auto p_tile = [&](int st) { return stage_base + st * stage_floats; };
+  auto s_tile = [&](int st) { return stage_base + st * stage_floats + arr_floats; };
   const CUtensorMap* mp = parity ? &tm_p0 : &tm_p1;  // p_k = pbuf[parity ^ 1]
   const int nq = z1 - z0 + 2;
-  auto issue = [&](int j) {
+  auto issue = [&](int j) {  // p of plane z0-1+j with its halo; s of it for planes z0 .. z1-1
     const int st = j % kStages;
-    mbar_expect_tx(&bars[st], box_bytes);
+    const bool with_s = j >= 1 && j <= nq - 2;
+    mbar_expect_tx(&bars[st], box_bytes + (with_s ? own_bytes : 0u));
     tma_load_4d(p_tile(st), mp, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+    if (with_s) tma_load_4d(s_tile(st), &tm_s, x0, y0, z0 - 1 + j, b, &bars[st]);
   };
   if (tid == 0) {
     for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
@@ -386,6 +398,7 @@ __global__ void __launch_bounds__(256, 3)
   const int i = x0 + lx, jn = y0 + ly;
   const bool own = i < g.nx && jn < g.ny;
   const int cofs = (ly + 1) * BX + lx + 4;
+  const int lofs = ly * TXN + lx;
   const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
   const int64_t plane = (int64_t)g.nx * g.ny;
   const int64_t col = (int64_t)jn * g.nx + i;
@@ -408,11 +421,10 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z < z1; ++z) {
       const int k = z - z0 + 1;
       const int sk = k % kStages, sn = (k + 1) % kStages;
-      float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (own) s4 = *reinterpret_cast<const float4*>(sb + z * plane + col);  // in flight over the wait
       bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
       if (!to && own) {
         const float4 xp = ld4s(p_tile(sn) + cofs);
+        const float4 s4 = ld4s(s_tile(sk) + lofs);
         const int zcl = g.cz[z];
         if (zcl != zcls_cur) {
           zcls_cur = zcl;
@@ -508,12 +520,14 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-static int make_map(CUtensorMap* m, const float* base, const Geo& g, int B, Tile t) {
+// halo = true: the (4*tx + 8) x (ty + 2) box of a stencil operand; false: the
+// 4*tx x ty own tile of a streamed operand.
+static int make_map(CUtensorMap* m, const float* base, const Geo& g, int B, Tile t, bool halo = true) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return -1;
   const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)B};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)g.n * 4};
-  const cuuint32_t box[4] = {(cuuint32_t)(4 * t.tx + 8), (cuuint32_t)(t.ty + 2), 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)(4 * t.tx + (halo ? 8 : 0)), (cuuint32_t)(t.ty + (halo ? 2 : 0)), 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -521,11 +535,16 @@ static int make_map(CUtensorMap* m, const float* base, const Geo& g, int B, Tile
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-size_t tma_smem_bytes(Tile t) {
+// Dynamic shared memory of the ring: halo boxes per stage (2 for phase A, 1
+// for phase B) and own tiles per stage (1 for the s-form phases, else 0).
+static size_t ring_bytes(Tile t, int halo_boxes, int own_tiles) {
   const int BX = 4 * t.tx + 8, BY = t.ty + 2;
   const size_t arr = (size_t)((BX * BY * 4 + 127) / 128) * 128;
-  return 2 * kStages * arr + 128;
+  const size_t own = (size_t)((4 * t.tx * t.ty * 4 + 127) / 128) * 128;
+  return kStages * (halo_boxes * arr + own_tiles * own) + 128;
 }
+
+size_t tma_smem_bytes(Tile t) { return ring_bytes(t, 2, 1); }
 
 bool tma_supported(const Geo& g, Tile t) {
   return encode_fn() != nullptr && g.nx % 4 == 0 && 4 * t.tx + 8 <= 256 && t.ty + 2 <= 256 &&
@@ -544,25 +563,28 @@ int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaSt
   const float* sarr = a.precond != RBWS_PREC_NONE ? a.s : a.r;
   if (make_map(&ms, sarr, a.g, a.B, t) || make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t))
     return -1;
-  const size_t smem = tma_smem_bytes(t);
-  k_cg_a_tma<0><<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), smem, s>>>(ms, m0, m1, a, parity, err);
+  // the own-tile map is unused in this mode: any valid map fills the slot
+  k_cg_a_tma<0><<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), ring_bytes(t, 2, 0), s>>>(
+      ms, m0, m1, ms, a, parity, err);
   return 0;
 }
 
 int launch_cg_a_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
-  CUtensorMap ms, m0, m1;
-  if (make_map(&ms, a.s, a.g, a.B, t) || make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t))
+  CUtensorMap ms, m0, m1, mu;
+  if (make_map(&ms, a.s, a.g, a.B, t) || make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t) ||
+      make_map(&mu, a.u, a.g, a.B, t, false))
     return -1;
-  k_cg_a_tma<1><<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), tma_smem_bytes(t), s>>>(
-      ms, m0, m1, a, parity, err);
+  k_cg_a_tma<1><<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), ring_bytes(t, 2, 1), s>>>(
+      ms, m0, m1, mu, a, parity, err);
   return 0;
 }
 
 int launch_cg_b_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
-  CUtensorMap m0, m1;
-  if (make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t)) return -1;
-  k_cg_b_s_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), tma_smem_bytes(t) / 2 + 128, s>>>(
-      m0, m1, a, parity, err);
+  CUtensorMap m0, m1, ms;
+  if (make_map(&m0, a.p0, a.g, a.B, t) || make_map(&m1, a.p1, a.g, a.B, t) || make_map(&ms, a.s, a.g, a.B, t, false))
+    return -1;
+  k_cg_b_s_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), ring_bytes(t, 1, 1), s>>>(
+      m0, m1, ms, a, parity, err);
   return 0;
 }
 

@@ -79,6 +79,20 @@ def random_field(seed: int, shape) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(shape)
 
 
+def inclusion_map(grid, seed: int) -> np.ndarray:
+    """Subdomain map [nz][ny][nx] (uint8, Q = 3) with the structure of a layered medium
+    holding one inclusion: two layers split at a seeded z plane (ids 0 and 1) and a
+    seeded box (id 2) that crosses the layer interface."""
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed)
+    m = np.zeros((nz, ny, nx), dtype=np.uint8)
+    m[int(rng.integers(1, nz)):, :, :] = 1
+    lo = [int(rng.integers(0, max(1, n // 2))) for n in (nz, ny, nx)]
+    hi = [l + int(rng.integers(1, max(2, n - l))) for l, n in zip(lo, (nz, ny, nx))]
+    m[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] = 2
+    return m
+
+
 def small(grid=(9, 7, 5), blocks=(2, 1, 1), lo=0.1, hi=10.0, n_max=6, n_train=16, n_test=4,
           tol=1e-12, seed_base=11, name="small") -> Workload:
     """A tiny ragged workload for fast CPU and parity tests."""

@@ -51,7 +51,7 @@ class rbws_options(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32),
                 ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
                 ("check_every", C.c_int32), ("stream", C.c_void_p),
-                ("profile", C.POINTER(rbws_profile))]
+                ("profile", C.POINTER(rbws_profile)), ("relres_hist", C.c_void_p), ("hist_len", C.c_int32)]
 
 
 _L = None
@@ -126,13 +126,23 @@ def rbws_options_default(**kw) -> rbws_options:
     return o
 
 
-def rbws_problem_create(grid, blocks, Q=None, f=None, device=0):
+def rbws_problem_create(grid, blocks, Q=None, f=None, device=0, subdomain_map=None):
+    """blocks: (bx, by, bz) for the block rule, or None with subdomain_map = a uint8 [nz][ny][nx]
+    array of subdomain ids < Q."""
     g = rbws_grid(*grid)
-    b = rbws_blocks(*blocks)
-    Q = blocks[0] * blocks[1] * blocks[2] if Q is None else Q
+    if subdomain_map is not None:
+        if blocks is not None or Q is None:
+            raise ValueError("give either blocks, or subdomain_map with Q")
+        m = np.ascontiguousarray(subdomain_map, dtype=np.uint8).reshape(-1)
+        if m.size != grid[0] * grid[1] * grid[2]:
+            raise ValueError("subdomain_map must have nx*ny*nz entries")
+        bref, mp = None, m.ctypes.data_as(C.c_void_p)
+    else:
+        bref, mp = C.byref(rbws_blocks(*blocks)), None
+        Q = blocks[0] * blocks[1] * blocks[2] if Q is None else Q
     fh = None if f is None else _host(f)
     h = C.c_void_p()
-    _check(_lib().rbws_problem_create(C.byref(g), C.byref(b), None, Q, _hp(fh), device, C.byref(h)),
+    _check(_lib().rbws_problem_create(C.byref(g), bref, mp, Q, _hp(fh), device, C.byref(h)),
            "rbws_problem_create")
     return h
 
@@ -206,6 +216,22 @@ def rbws_solve_batch(h, mu, tol, warm, u_out, options: rbws_options | None = Non
     rc = _check(_lib().rbws_solve_batch(h, _hp(mu), B, tol, warm, None if options is None else C.byref(options),
                                         _dp(u_out), _hp(it), _hp(rel), _hp(st)), "rbws_solve_batch")
     return rc, it, rel, st
+
+
+def rbws_solve_batch_history(h, mu, tol, warm, u_out, hist_len, options: rbws_options | None = None):
+    """rbws_solve_batch with the FP64 residual history: returns (status, iters, relres,
+    inst_status, hist) with hist [B][hist_len] (NaN past each instance's last iteration)."""
+    B = np.atleast_2d(mu).shape[0]
+    hist = np.full((B, hist_len), np.nan)
+    o = options if options is not None else rbws_options_default()
+    o.relres_hist = hist.ctypes.data_as(C.c_void_p)
+    o.hist_len = hist_len
+    try:
+        rc, it, rel, st = rbws_solve_batch(h, mu, tol, warm, u_out, o)
+    finally:
+        o.relres_hist = None
+        o.hist_len = 0
+    return rc, it, rel, st, hist
 
 
 def mlp_param_count(p, H, N):
@@ -298,16 +324,27 @@ def rbws_load(path, device=0):
 class Problem:
     """Owning wrapper around an rbws_problem handle."""
 
-    def __init__(self, grid, blocks, f=None, device=0, handle=None):
-        self.grid, self.blocks = tuple(grid), tuple(blocks)
-        self.Q = blocks[0] * blocks[1] * blocks[2]
+    def __init__(self, grid, blocks=None, f=None, device=0, handle=None, subdomain_map=None, Q=None):
+        self.grid = tuple(grid)
         self.n = grid[0] * grid[1] * grid[2]
-        self.h = handle if handle is not None else rbws_problem_create(grid, blocks, self.Q, f, device)
+        if subdomain_map is not None:
+            self.blocks, self.Q = None, int(Q)
+        else:
+            self.blocks = tuple(blocks)
+            self.Q = blocks[0] * blocks[1] * blocks[2]
+        if handle is not None:
+            self.h = handle
+        else:
+            self.h = rbws_problem_create(grid, self.blocks, self.Q, f, device, subdomain_map)
 
     @classmethod
-    def load(cls, path, grid, blocks, device=0):
-        """Wraps a problem restored by rbws_load (grid and blocks as saved)."""
-        return cls(grid, blocks, handle=rbws_load(path, device))
+    def load(cls, path, device=0):
+        """Wraps a problem restored by rbws_load."""
+        h = rbws_load(path, device)
+        n, Q, _ = rbws_problem_info(h)
+        obj = cls.__new__(cls)
+        obj.grid, obj.blocks, obj.n, obj.Q, obj.h = None, None, n, Q, h
+        return obj
 
     def close(self):
         if self.h:

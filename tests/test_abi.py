@@ -77,19 +77,22 @@ def test_options_default_sets_every_field(lib_path):
     rbws._lib().rbws_options_default(C.byref(o))
     assert o.max_iters == 20000 and o.precond == rbws.PREC_JACOBI and o.precision == rbws.FP64
     assert o.max_restarts == 3 and o.inner_tol == 1e-2 and o.max_outer == 10 and o.check_every == 0
-    assert o.stream is None and not o.profile
+    assert o.stream is None and not o.profile and o.relres_hist is None and o.hist_len == 0
 
 
-def _ckpt_bytes(nx=4, ny=3, nz=2, blocks=(2, 1, 1), N=2, checksum_ok=True):
-    """A checkpoint in the library's documented layout (no network, f = 1)."""
+def _ckpt_bytes(nx=4, ny=3, nz=2, blocks=(2, 1, 1), N=2, checksum_ok=True, submap=None, Q=None):
+    """A checkpoint in the library's documented layout (no network, f = 1; the subdomain map
+    submap [n] uint8 with Q subdomains if given, else the block rule)."""
     import struct
     import numpy as np
     n = nx * ny * nz
-    Q = blocks[0] * blocks[1] * blocks[2]
-    payload = (np.arange(N * n, dtype=np.float64).tobytes() + np.ones(Q * N * N).tobytes()
+    Q = blocks[0] * blocks[1] * blocks[2] if submap is None else Q
+    payload = ((b"" if submap is None else np.asarray(submap, dtype=np.uint8).tobytes())
+               + np.arange(N * n, dtype=np.float64).tobytes() + np.ones(Q * N * N).tobytes()
                + np.ones(N).tobytes())
-    hdr = struct.pack("<8sI11i2dQ", b"RBWSPRB1", 1, nx, ny, nz, blocks[0], blocks[1], blocks[2], Q, 0, N, 0, 0,
-                      0.0, 0.0, len(payload))
+    # i32 fields: nx ny nz bx by bz Q has_f N net_H net_N has_map, then 4 bytes of padding
+    hdr = struct.pack("<8sI12i4x2dQ", b"RBWSPRB1", 2, nx, ny, nz, blocks[0], blocks[1], blocks[2], Q, 0, N, 0, 0,
+                      int(submap is not None), 0.0, 0.0, len(payload))
     h = 1469598103934665603
     for c in payload:
         h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
@@ -124,3 +127,35 @@ def test_checkpoint_loader_accepts_a_valid_file_up_to_device_set_up(tmp_path, li
     ok.write_bytes(_ckpt_bytes())
     with pytest.raises(rbws.RbwsError, match="CUDA"):  # parsed and verified; no device here
         rbws.rbws_load(ok)
+    # with an explicit map: the map travels in the payload and reaches device set-up
+    ok.write_bytes(_ckpt_bytes(submap=[0, 1, 1, 0] + [0] * 20, Q=2))
+    with pytest.raises(rbws.RbwsError, match="CUDA"):
+        rbws.rbws_load(ok)
+    ok.write_bytes(_ckpt_bytes(submap=[0, 2, 1, 0] + [0] * 20, Q=2))
+    with pytest.raises(rbws.RbwsError, match="INVALID_ARG"):  # map value 2 >= Q
+        rbws.rbws_load(ok)
+
+
+def test_explicit_maps_are_checked_before_the_device(lib_path):
+    """Explicit maps are cut into boxes by their interface planes; the limits (segments per
+    axis, coefficient classes) and value checks run on the host, visible without a GPU."""
+    import numpy as np
+    import torch
+    from paper_2311_13862_gb300 import rbws
+    grid = (6, 5, 4)
+    m = np.zeros((4, 5, 6), dtype=np.uint8)
+    m[:, :, 2:] = 1
+    m[1:3, 1:3, 2:4] = 2                 # an inclusion: boxes between the cut planes
+    with pytest.raises(rbws.RbwsError, match="INVALID_ARG"):
+        rbws.rbws_problem_create(grid, None, Q=2, subdomain_map=m)  # value 2 >= Q
+    many = np.zeros((4, 5, 70), dtype=np.uint8)
+    many[:, :, ::2] = 1                  # 70 segments along x: more than the limit
+    with pytest.raises(rbws.RbwsError, match="UNSUPPORTED.*segments"):
+        rbws.rbws_problem_create((70, 5, 4), None, Q=2, subdomain_map=many)
+    i = np.arange(60) // 2 % 2           # 30 segments of 2 nodes per axis: 60^3 classes
+    cb = (i[:, None, None] ^ i[None, :, None] ^ i[None, None, :]).astype(np.uint8)
+    with pytest.raises(rbws.RbwsError, match="UNSUPPORTED.*classes"):
+        rbws.rbws_problem_create((60, 60, 60), None, Q=2, subdomain_map=cb)
+    if not torch.cuda.is_available():
+        with pytest.raises(rbws.RbwsError, match="CUDA"):  # accepted; no device here
+            rbws.rbws_problem_create(grid, None, Q=3, subdomain_map=m)

@@ -153,7 +153,7 @@ def test_checkpoint_round_trip(tmp_path):
                                   mu_lo=w.mu_lo, mu_hi=w.mu_hi)
         a = {m: solve(P, mu, 1e-10, m) for m in (rbws.WARM_GALERKIN, rbws.WARM_LEARNED)}
         rbws.rbws_save(P.h, path)
-    with rbws.Problem.load(path, w.grid, w.blocks) as P2:
+    with rbws.Problem.load(path) as P2:
         b = {m: solve(P2, mu, 1e-10, m) for m in (rbws.WARM_GALERKIN, rbws.WARM_LEARNED)}
     for m in a:
         assert np.array_equal(a[m][1], b[m][1]) and np.array_equal(a[m][4], b[m][4])
