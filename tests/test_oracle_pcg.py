@@ -52,6 +52,21 @@ def test_one_iteration_for_an_eigenvector():
     # Jacobi with constant kappa scales the residual uniformly: still one iteration
     rj = O.pcg(op, [m, m], f=v, precond=O.PREC_JACOBI, tol=1e-13)
     assert rj.iters == 1
+    # the residual history: ||f|| / ||f|| = 1 from u0 = 0, then the exact solve
+    assert r.hist[0] == 1.0 and r.hist[1] < 1e-14 and len(r.hist) == 2
+
+
+def test_residual_history_entries():
+    # entry 0 is the initial residual of the given u0 (recomputed here with the CSR operator),
+    # the last one the reported residual, one entry per application of A
+    op = O.assemble((10, 9, 8), (2, 2, 1))
+    mu = inputs.log_uniform(91, 1, 4, 0.1, 10.0)[0]
+    u0 = inputs.random_field(92, op.n)
+    r = O.pcg(op, mu, u0=u0, precond=O.PREC_NONE, tol=1e-12)
+    f = np.ones(op.n)
+    assert r.hist[0] == pytest.approx(np.linalg.norm(f - op.matvec(mu, u0)) / np.linalg.norm(f), rel=1e-14)
+    assert r.hist[-1] == pytest.approx(r.relres, rel=1e-6) and len(r.hist) == r.iters + 1
+    assert np.all(r.hist > 0) and r.hist[-1] < 1e-12
 
 
 def test_closed_form_solution_unit_source():
