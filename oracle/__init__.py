@@ -13,6 +13,7 @@ Function map (paper passage -> function):
   Algorithm 3 (MSRB preconditioner)    pcg(precond=MSRB), solve_batch(precond=MSRB)
   Algorithm 5 skeleton (greedy)        greedy()
   Algorithm 4 over a batch             solve_batch()
+  Algorithm 2 (MG V-cycle), MGCG       oracle.mg: Hierarchy, vcycle(), mgcg() (numpy/scipy)
   learned warm start network           mlp_forward(), mlp_loss_grad()
 Parity status: all pinned by CPU tests except trained network weights
 ("parity unpinned": only forward/backward are pinned).
