@@ -387,12 +387,15 @@ def main():
         # the RB-preconditioned start: Galerkin start, then PCG with the MSRB preconditioner
         # (Algorithm 3, FP64 only)
         arm_list.append(("msrb_fp64", rbws.WARM_GALERKIN, rbws.FP64))
+        # MGCG (Algorithm 2 as the preconditioner, FP64), from zero and from the RB initial value
+        arm_list += [("mgcg_zero_fp64", rbws.WARM_ZERO, rbws.FP64), ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, rbws.FP64)]
+    precond_of = {"msrb_fp64": rbws.PREC_MSRB, "mgcg_zero_fp64": rbws.PREC_MG, "mgcg_galerkin_fp64": rbws.PREC_MG}
     for name, warm, pr in arm_list:
         if name.startswith("galerkin_" + args.precision):
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
         else:
             a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1,
-                                             precond=rbws.PREC_MSRB if name == "msrb_fp64" else rbws.PREC_JACOBI)
+                                             precond=precond_of.get(name, rbws.PREC_JACOBI))
         arms[name] = {"solves_per_s": B * world / (a_ms / 1e3), "ms_per_step": a_ms,
                       "iters_mean": float(np.mean(a_it)), "iters_max": int(np.max(a_it)),
                       "relres_max": float(np.max(a_rel)), "all_converged": bool(np.all(a_st == 0))}

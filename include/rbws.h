@@ -68,7 +68,14 @@ typedef enum {
 typedef enum {
   RBWS_PREC_NONE = 0,   /* plain CG                                           */
   RBWS_PREC_JACOBI = 1, /* P(r) = D^{-1} r, D = diag(A(mu))                      */
-  RBWS_PREC_MSRB = 2    /* Algorithm 3: one Jacobi sweep + RB correction (W)     */
+  RBWS_PREC_MSRB = 2,   /* Algorithm 3: one Jacobi sweep + RB correction (W)     */
+  RBWS_PREC_MG = 3      /* Algorithm 2: one multigrid V-cycle (MGCG).  Levels:
+                           each axis coarsened to n // 2 nodes (the even fine
+                           nodes) while the level has more than 64 unknowns and
+                           every axis at least 2 nodes; linear interpolation P
+                           per axis; Galerkin coarse operators P^T A P; damped
+                           Jacobi smoothing (omega = 2/3), 2 pre- and 2 post-
+                           steps; exact solve on the coarsest level.  FP64 only */
 } rbws_precond;
 
 typedef enum {
@@ -157,6 +164,16 @@ RBWS_API rbws_status rbws_problem_info(rbws_problem p, int64_t* n_dof, int32_t* 
  * (RBWS_FP32_IR selects the FP32 kernel).  stream: cudaStream_t or NULL. */
 RBWS_API rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, const void* x,
                                 void* y, int32_t precision, void* stream);
+
+/* y[b] = P(mu[b]) x[b]: the preconditioner of Algorithm 1 applied to B
+ * vectors (device [B][n_dof] FP64; x and y distinct, x unchanged).  precond:
+ * RBWS_PREC_JACOBI (D^{-1} x) or RBWS_PREC_MG (one V-cycle of Algorithm 2 from
+ * a zero initial value, the operator RBWS_PREC_MG uses inside PCG).  Other
+ * preconditioners return RBWS_ERR_UNSUPPORTED, as does RBWS_PREC_MG on a grid
+ * whose coarsest level would exceed 1024 unknowns.  stream: cudaStream_t or
+ * NULL; returns after the work completed. */
+RBWS_API rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t B, int32_t precond,
+                                               const void* x, void* y, void* stream);
 
 /* rbws_apply_operator for callers that cannot allocate device memory after
  * start-up: services that run inside a fixed device-memory budget shared with

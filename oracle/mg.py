@@ -12,8 +12,9 @@ Readings where the paper leaves a choice open:
   * grid hierarchy: along an axis with n nodes the coarse grid has m = n // 2 nodes, at the
     fine nodes 2, 4, ..., 2m (1-based); P is linear interpolation along each axis (tensor
     product), with the Dirichlet boundary contributing zero;
-  * depth: coarsen while the level has more than MAX_COARSE unknowns and every axis has at
-    least 4 nodes (64^3 gives 4 levels, J = 3, the depth of the paper's experiments);
+  * depth: coarsen while the level has more than MAX_COARSE = 64 unknowns and every axis has
+    at least 2 nodes (64^3 gives 5 levels, J = 4, down to 4^3; the paper's experiments used
+    J = 3 on their meshes);
   * smoother: damped Jacobi u <- u + omega D^-1 (b - A u), omega = 2/3, nu = 2 pre- and
     post-smoothing steps, the pre-smoothing starting from zero;
   * coarsest level: exact solve by dense Cholesky;
@@ -28,7 +29,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-MAX_COARSE = 512
+MAX_COARSE = 64
 OMEGA = 2.0 / 3.0
 NU = 2
 
@@ -58,7 +59,7 @@ def level_grids(grid) -> list:
     dims = [tuple(grid)]
     while True:
         nx, ny, nz = dims[-1]
-        if nx * ny * nz <= MAX_COARSE or min(nx, ny, nz) < 4:
+        if nx * ny * nz <= MAX_COARSE or min(nx, ny, nz) < 2:
             break
         dims.append((nx // 2, ny // 2, nz // 2))
     return dims[::-1]

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <thread>
 #include <string>
 #include <vector>
@@ -141,7 +142,11 @@ struct rbws_problem_s {
   uint8_t* d_cls = nullptr;  // cx | cy | cz
   int8_t* d_keys = nullptr;  // kx | ky | kz
   std::vector<uint8_t> h_map;  // explicit subdomain map [n] (empty: block rule)
-  uint8_t* d_segq = nullptr;   // explicit map: box (bx*by*bz segments) -> subdomain
+  std::vector<uint8_t> h_segq; // explicit map: box (bx*by*bz segments) -> subdomain
+  uint8_t* d_segq = nullptr;
+  std::unique_ptr<MGPlan> mg;  // multigrid hierarchy, built on first use
+  std::string mg_err;
+  bool mg_tried = false;
   Geo geo{};
   double* d_f = nullptr;     // nullptr: f == 1
   double* d_ones = nullptr;  // ones vector (for W^T f when f == 1)
@@ -305,6 +310,11 @@ int launch_iteration(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s) {
       launch_msrb_apply(a, t, parity ^ 1, s);
       return 6;
     }
+    if (a.precond == RBWS_PREC_MG) {
+      const int l = launch_mg_vcycle(*a.mg, a.r, a.s, s);
+      launch_precond_rho(a, t, parity ^ 1, s);
+      return 3 + l;
+    }
   }
   return 2;
 }
@@ -316,6 +326,11 @@ int launch_precond_start(const CGArgs<T>& a, Tile t, cudaStream_t s) {
     if (a.precond == RBWS_PREC_MSRB) {
       launch_msrb_apply(a, t, 0, s);
       return 4;
+    }
+    if (a.precond == RBWS_PREC_MG) {
+      const int l = launch_mg_vcycle(*a.mg, a.r, a.s, s);
+      launch_precond_rho(a, t, 0, s);
+      return 1 + l;
     }
   }
   return 0;
@@ -389,6 +404,10 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
           if (a.precond == RBWS_PREC_MSRB) {
             launch_msrb_apply(a, t, 1, s);
             per_iter = 6;
+          }
+          if (a.precond == RBWS_PREC_MG) {
+            per_iter = 3 + launch_mg_vcycle(*a.mg, a.r, a.s, s);
+            launch_precond_rho(a, t, 1, s);
           }
         }
         for (int k = 1; k < M; k++) launch_iteration<T>(a, t, k & 1, s);
@@ -517,6 +536,81 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u)
   return RBWS_OK;
 }
 
+// The multigrid hierarchy of the problem (built on first use).
+rbws_status mg_plan(rbws_problem p, const MGPlan** out) {
+  if (!p->mg_tried) {
+    p->mg_tried = true;
+    auto plan = std::make_unique<MGPlan>();
+    p->mg_err = mg_build_plan(p->ax, p->ay, p->az, p->bx, p->by, p->h_segq.empty() ? nullptr : p->h_segq.data(),
+                              p->Q, p->sx, p->sy, p->sz, plan.get());
+    if (p->mg_err.empty()) p->mg = std::move(plan);
+  }
+  if (!p->mg) {
+    set_error(p->mg_err);
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  *out = p->mg.get();
+  return RBWS_OK;
+}
+
+// Per-batch V-cycle state: level views, work vectors, coarse tables and the
+// level-0 inverses for B parameters (device mu), finest tables coef64.
+rbws_status mg_batch(rbws_problem p, const double* d_mu, int B, const double* coef64, const InstState* st,
+                     MGBatch* m) {
+  const MGPlan* plan = nullptr;
+  CKI(mg_plan(p, &plan));
+  m->plan = plan;
+  m->B = B;
+  m->st = st;
+  int err = 0;
+  double* tables[kMGMaxLevels] = {};
+  for (int i = 0; i <= plan->J && !err; i++) {
+    const MGPlan::Level& L = plan->lv[i];
+    MGLevel& v = m->lv[i];
+    v.nx = L.nx, v.ny = L.ny, v.nz = L.nz, v.n = L.n;
+    v.ncx = L.ncx, v.ncy = L.ncy, v.ncz = L.ncz;
+    const std::string k = std::to_string(i);
+    const size_t vec = sizeof(double) * (size_t)B * L.n;
+    if (i == plan->J) {
+      v.cx = p->geo.cx, v.cy = p->geo.cy, v.cz = p->geo.cz;
+      v.coef = coef64;
+      v.stride = kCoefStride;
+    } else {
+      v.cx = plan->d_cls[i], v.cy = v.cx + L.nx, v.cz = v.cy + L.ny;
+      v.stride = 28;
+      m->rhs[i] = (double*)p->buf("mg_rhs" + k, vec, &err);
+      if (!err) m->sol[i] = (double*)p->buf("mg_sol" + k, vec, &err);
+      if (i >= 1 && !err) {
+        tables[i] = (double*)p->buf("mg_tab" + k, sizeof(double) * (size_t)B * L.ncls() * 28, &err);
+        v.coef = tables[i];
+      }
+    }
+    if (i >= 1 && !err) {
+      m->w1[i] = (double*)p->buf("mg_w1_" + k, vec, &err);
+      if (!err) m->w2[i] = (double*)p->buf("mg_w2_" + k, vec, &err);
+    }
+  }
+  const size_t dense = sizeof(double) * (size_t)B * plan->n0 * plan->n0;
+  double* da = err ? nullptr : (double*)p->buf("mg_dense_a", dense, &err);
+  double* dl = err ? nullptr : (double*)p->buf("mg_dense_l", dense, &err);
+  double* ai = err ? nullptr : (double*)p->buf("mg_dense_inv", dense, &err);
+  int* info = err ? nullptr : (int*)p->buf("mg_info", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  m->ainv = ai;
+  launch_mg_setup(*plan, d_mu, B, tables, da, dl, ai, info, p->cur);
+  p->launches += plan->J + 1;
+  CK(cudaGetLastError());
+  std::vector<int> h(B);
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  for (int b = 0; b < B; b++)
+    if (h[b]) {
+      set_error("multigrid: coarsest-level matrix not positive definite");
+      return RBWS_ERR_NOT_SPD;
+    }
+  return RBWS_OK;
+}
+
 rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, const rbws_options& o,
                        double* u, std::vector<InstState>& st) {
   double* coef64 = nullptr;
@@ -555,6 +649,11 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
         set_error("MSRB: A_N(mu) not positive definite");
         return RBWS_ERR_NOT_SPD;
       }
+  }
+  MGBatch mgb;  // outlives run_pcg: the launchers read it while capturing
+  if (o.precond == RBWS_PREC_MG) {
+    CKI(mg_batch(p, d_mu, B, coef64, a.st, &mgb));
+    a.mg = &mgb;
   }
   fill((double*)a.fnorm, B, p->fnorm, p->cur);
   p->launches += 1;
@@ -964,12 +1063,13 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
     set_error("solve: invalid tolerance or limits");
     return RBWS_ERR_INVALID_ARG;
   }
-  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI && o.precond != RBWS_PREC_MSRB) {
+  if (o.precond != RBWS_PREC_NONE && o.precond != RBWS_PREC_JACOBI && o.precond != RBWS_PREC_MSRB &&
+      o.precond != RBWS_PREC_MG) {
     set_error("solve: unknown preconditioner");
     return RBWS_ERR_INVALID_ARG;
   }
-  if (o.precond == RBWS_PREC_MSRB && o.precision != RBWS_FP64) {
-    set_error("solve: the MSRB preconditioner runs in FP64 only");
+  if ((o.precond == RBWS_PREC_MSRB || o.precond == RBWS_PREC_MG) && o.precision != RBWS_FP64) {
+    set_error("solve: the MSRB and multigrid preconditioners run in FP64 only");
     return RBWS_ERR_UNSUPPORTED;
   }
   if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_LEARNED_CORRECTED) {
@@ -1145,6 +1245,7 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   cudaMemcpy(p->d_cls, cls.data(), cls.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_keys, keys.data(), keys.size(), cudaMemcpyHostToDevice);
   if (!segq.empty()) {
+    p->h_segq = segq;
     if ((e = cudaMalloc(&p->d_segq, segq.size())) != cudaSuccess) return fail(e, "cudaMalloc");
     cudaMemcpy(p->d_segq, segq.data(), segq.size(), cudaMemcpyHostToDevice);
   }
@@ -1192,6 +1293,7 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_cls);
   cudaFree(p->d_keys);
   cudaFree(p->d_segq);
+  p->mg.reset();
   cudaFree(p->d_f);
   cudaFree(p->d_ones);
   cudaFree(p->d_W);
@@ -1237,6 +1339,36 @@ rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, con
     launch_apply<double>(p->geo, t, c64, B, (const double*)x, p->n, (double*)y, p->cur);
   else
     launch_apply<float>(p->geo, t, c32, B, (const float*)x, p->n, (float*)y, p->cur);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t B, int32_t precond,
+                                      const void* x, void* y, void* stream) {
+  if (!p || !mu || !x || !y || x == y || B < 1 || B > 65535) {
+    set_error("rbws_apply_preconditioner: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (precond != RBWS_PREC_JACOBI && precond != RBWS_PREC_MG) {
+    set_error("rbws_apply_preconditioner: only the Jacobi and multigrid preconditioners act alone");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  StreamGuard sg(p, stream);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_precond"));
+  double* c64 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &c64, nullptr));
+  if (precond == RBWS_PREC_JACOBI) {
+    MGLevel L{p->nx, p->ny, p->nz, p->n, p->geo.ncx, p->geo.ncy, p->geo.ncz, p->geo.cx, p->geo.cy, p->geo.cz,
+              c64, kCoefStride};
+    launch_diag_inverse(L, B, (const double*)x, (double*)y, p->cur);
+    p->launches += 1;
+  } else {
+    MGBatch m;
+    CKI(mg_batch(p, d_mu, B, c64, nullptr, &m));
+    p->launches += launch_mg_vcycle(m, (const double*)x, (double*)y, p->cur);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->cur));
   return RBWS_OK;

@@ -126,6 +126,8 @@ struct CGArgs {
   // residual history (FP64 iteration): hist[b][k] = ||r_k|| / ||f||
   double* hist;         // [B][hist_len] or nullptr
   int hist_len;
+  // multigrid preconditioner (host pointer, read by the launchers only)
+  const struct MGBatch* mg;
 };
 
 // ---------------------------------------------------------------------------
@@ -261,6 +263,88 @@ void launch_scale_targets(const double* c, const float* scale, int B, int N, flo
 void launch_unscale(const float* y, const float* scale, int B, int N, double* c, cudaStream_t s);
 void launch_reduced_cg_step(int N, int Q, const double* ANq, const double* fN, const double* mu, int B,
                             double* c, cudaStream_t s);
+
+// rho = r.s partials after an external preconditioner wrote s (stencil.cu).
+void launch_precond_rho(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Multigrid V-cycle preconditioner, Algorithm 2 (mg.cu)
+//
+// Every level's operator is stored the way the finest one is: by per-axis
+// node classes and a per-instance table of rows by class.  The finest level
+// uses the 7-point tables of k_coef_tables; a coarse node's class along an
+// axis is the tuple of fine classes at fine nodes 2J-2 .. 2J+2 (or "outside"),
+// which fixes its Galerkin row (P^T A P), a 27-point stencil.  The rows of
+// each affine term are formed once on the host; per instance a table is the
+// mu-combination of them.  The coarsest level is solved with an explicit
+// inverse per instance.
+// ---------------------------------------------------------------------------
+constexpr int kMGMaxLevels = 12;
+constexpr int kMGCoarsest = 64;     // coarsen while a level has more unknowns than this
+constexpr int kMGMaxDense = 1024;   // largest coarsest level accepted
+constexpr int kMGNu = 2;            // pre- and post-smoothing steps
+constexpr double kMGOmega = 2.0 / 3.0;
+
+struct MGPlan {
+  struct Level {
+    int nx = 0, ny = 0, nz = 0;
+    int64_t n = 0;
+    int ncx = 0, ncy = 0, ncz = 0;
+    std::vector<uint8_t> cx, cy, cz;  // class of each node along each axis
+    std::vector<double> tq;           // [Q][ncls][27] rows by class (offset (dz+1)*9+(dy+1)*3+dx+1)
+    int ncls() const { return ncx * ncy * ncz; }
+  };
+  int J = -1;  // finest level; levels 0 (coarsest) .. J
+  int Q = 0;
+  int n0 = 0;  // unknowns on level 0
+  std::vector<Level> lv;
+  std::vector<double> a0q;  // [Q][n0][n0] level-0 matrices of the affine terms
+  // device copies
+  uint8_t* d_cls[kMGMaxLevels] = {};
+  double* d_tq[kMGMaxLevels] = {};
+  double* d_a0q = nullptr;
+  ~MGPlan();
+};
+
+// Builds the hierarchy from the finest grid's axis classes; "" or the reason
+// multigrid is not available for this grid.  Device copies are made here.
+std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az, int bx,
+                          int by, const uint8_t* segq_host, int Q, double sx, double sy, double sz,
+                          MGPlan* plan);
+
+// Device view of one level for the V-cycle kernels.
+struct MGLevel {
+  int nx, ny, nz;
+  int64_t n;
+  int ncx, ncy, ncz;
+  const uint8_t* cx;
+  const uint8_t* cy;
+  const uint8_t* cz;
+  const double* coef;  // [B][ncls][stride]
+  int stride;          // 8: the finest 7-point table; 28: 27 entries + 1/diagonal
+};
+
+// Per-batch state of the V-cycle: level views, work vectors, level-0 inverses.
+struct MGBatch {
+  const MGPlan* plan = nullptr;
+  int B = 0;
+  const InstState* st = nullptr;  // instances whose status is not ACTIVE are skipped
+  MGLevel lv[kMGMaxLevels];
+  double* rhs[kMGMaxLevels] = {};
+  double* sol[kMGMaxLevels] = {};
+  double* w1[kMGMaxLevels] = {};
+  double* w2[kMGMaxLevels] = {};
+  double* ainv = nullptr;  // [B][n0][n0]
+};
+
+// Per-instance coarse tables and level-0 inverses for B parameters (device mu
+// [B][Q]); info[b] != 0 where a level-0 matrix is not positive definite.
+void launch_mg_setup(const MGPlan& plan, const double* mu, int B, double* const* tables, double* dense_a,
+                     double* dense_l, double* ainv, int* info, cudaStream_t s);
+// out = MG(rhs) on the finest level (Algorithm 2 at level J); returns launches.
+int launch_mg_vcycle(const MGBatch& m, const double* rhs, double* out, cudaStream_t s);
+// y = D^-1 x on level view L (instances all active).
+void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Operator apply with static scratch (static_scratch.cu)

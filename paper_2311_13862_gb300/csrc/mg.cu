@@ -1,0 +1,514 @@
+// mg.cu -- multigrid V-cycle preconditioner (Algorithm 2) for the batched PCG.
+//
+// Grid hierarchy: along an axis with n nodes the next coarser level has
+// m = n / 2 nodes, at the fine nodes 2, 4, ..., 2m (1-based); P_i is linear
+// interpolation along each axis with the Dirichlet boundary as zero, and the
+// coarse operators are the Galerkin products A^i = P_i^T A^{i+1} P_i.
+//
+// Every level's operator is kept in the class form of the finest one: the
+// row of a node depends only on its class triple (x, y, z).  On the finest
+// level a class is (own, lower, upper) segment along the axis.  On a coarse
+// level the class of coarse node J along an axis is the tuple of fine classes
+// at fine nodes 2J-2 .. 2J+2 ("outside" beyond the grid): the Galerkin row of
+// J only involves fine rows 2J-1 .. 2J+1, their neighbours 2J-2 .. 2J+2 and
+// the interpolation weights there, all fixed by that tuple.  So each level is
+// a small table of 27-point rows per class, formed once per affine term on
+// the host (A^i(mu) = sum_q mu_q A_q^i because P does not depend on mu), and
+// combined per instance on the device.  The coarsest level (at most 64
+// unknowns for cubes) is solved with an explicit inverse per instance.
+//
+// Smoothing is damped Jacobi, u <- u + omega D^-1 (b - A u) with omega = 2/3,
+// two steps before and two after the coarse correction, the first from zero.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+
+namespace rbws {
+
+// ---------------------------------------------------------------------------
+// Host: the hierarchy
+// ---------------------------------------------------------------------------
+namespace {
+
+inline int off27(int dx, int dy, int dz) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
+
+// Classes of the coarse axis from the fine axis classes.
+void coarsen_axis(const std::vector<uint8_t>& fine, std::vector<uint8_t>& coarse, int* ncls) {
+  const int n = (int)fine.size(), m = n / 2;
+  coarse.assign(m, 0);
+  std::map<std::vector<int>, int> ids;
+  for (int J = 1; J <= m; J++) {
+    std::vector<int> key(5);
+    for (int t = 0; t < 5; t++) {
+      const int i = 2 * J - 2 + t;  // 1-based fine node
+      key[t] = (i >= 1 && i <= n) ? fine[i - 1] : -1;
+    }
+    auto it = ids.find(key);
+    const int id = it == ids.end() ? (int)ids.size() : it->second;
+    if (it == ids.end()) ids[key] = id;
+    coarse[J - 1] = (uint8_t)std::min(id, 255);  // more than 256 classes is rejected by the caller
+  }
+  *ncls = (int)ids.size();
+}
+
+// Interpolation weights of fine node l (1-based) from the coarse nodes of an
+// axis with m coarse nodes: (K, w) pairs, K 1-based.
+int pweights(int l, int m, int K[2], double w[2]) {
+  if (l % 2 == 0) {
+    K[0] = l / 2;
+    w[0] = 1.0;
+    return 1;
+  }
+  int c = 0;
+  if ((l - 1) / 2 >= 1) K[c] = (l - 1) / 2, w[c++] = 0.5;
+  if ((l + 1) / 2 <= m) K[c] = (l + 1) / 2, w[c++] = 0.5;
+  return c;
+}
+
+// First node (1-based) of each class along an axis.
+std::vector<int> representatives(const std::vector<uint8_t>& cls, int ncls) {
+  std::vector<int> rep(ncls, 0);
+  for (int i = (int)cls.size(); i >= 1; i--) rep[cls[i - 1]] = i;
+  return rep;
+}
+
+}  // namespace
+
+MGPlan::~MGPlan() {
+  for (auto p : d_cls) cudaFree(p);
+  for (auto p : d_tq) cudaFree(p);
+  cudaFree(d_a0q);
+}
+
+std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az, int bx,
+                          int by, const uint8_t* segq, int Q, double sx, double sy, double sz,
+                          MGPlan* plan) {
+  // level grids, finest first
+  std::vector<std::array<int, 3>> dims{{ax.n, ay.n, az.n}};
+  for (;;) {
+    const auto d = dims.back();
+    if ((int64_t)d[0] * d[1] * d[2] <= kMGCoarsest || std::min({d[0], d[1], d[2]}) < 2) break;
+    if ((int)dims.size() == kMGMaxLevels) return "multigrid: too many levels";
+    dims.push_back({d[0] / 2, d[1] / 2, d[2] / 2});
+  }
+  const int L = (int)dims.size();
+  plan->J = L - 1;
+  plan->Q = Q;
+  plan->lv.assign(L, {});
+  const auto& d0 = dims.back();
+  plan->n0 = d0[0] * d0[1] * d0[2];
+  if (plan->n0 > kMGMaxDense) return "multigrid: the coarsest level would have more than 1024 unknowns";
+  // finest level: the 7-point rows of each affine term (kappa = e_q) by class
+  MGPlan::Level& F = plan->lv[plan->J];
+  F.nx = ax.n, F.ny = ay.n, F.nz = az.n;
+  F.n = (int64_t)F.nx * F.ny * F.nz;
+  F.cx = ax.cls, F.cy = ay.cls, F.cz = az.cls;
+  F.ncx = ax.ncls(), F.ncy = ay.ncls(), F.ncz = az.ncls();
+  F.tq.assign((size_t)Q * F.ncls() * 27, 0.0);
+  for (int q = 0; q < Q; q++)
+    for (int czi = 0; czi < F.ncz; czi++)
+      for (int cyi = 0; cyi < F.ncy; cyi++)
+        for (int cxi = 0; cxi < F.ncx; cxi++) {
+          const int ox = ax.key[3 * cxi], lx = ax.key[3 * cxi + 1], hx = ax.key[3 * cxi + 2];
+          const int oy = ay.key[3 * cyi], ly = ay.key[3 * cyi + 1], hy = ay.key[3 * cyi + 2];
+          const int oz = az.key[3 * czi], lz = az.key[3 * czi + 1], hz = az.key[3 * czi + 2];
+          auto kap = [&](int a, int b, int c) {
+            const int box = (c * by + b) * bx + a;
+            return (segq ? segq[box] : box) == q ? 1.0 : 0.0;
+          };
+          const double kc = kap(ox, oy, oz);
+          auto face = [&](int nb, double knb, double s) { return nb >= 0 ? 0.5 * (kc + knb) * s : kc * s; };
+          const double kW = face(lx, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx);
+          const double kE = face(hx, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx);
+          const double kS = face(ly, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy);
+          const double kN = face(hy, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy);
+          const double kD = face(lz, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz);
+          const double kU = face(hz, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz);
+          double* row = &F.tq[(((size_t)q * F.ncz + czi) * F.ncy + cyi) * F.ncx * 27 + (size_t)cxi * 27];
+          row[off27(0, 0, 0)] = kW + kE + kS + kN + kD + kU;
+          row[off27(-1, 0, 0)] = -kW;
+          row[off27(1, 0, 0)] = -kE;
+          row[off27(0, -1, 0)] = -kS;
+          row[off27(0, 1, 0)] = -kN;
+          row[off27(0, 0, -1)] = -kD;
+          row[off27(0, 0, 1)] = -kU;
+        }
+  // coarse levels: classes and Galerkin rows from the next finer level
+  for (int i = plan->J - 1; i >= 0; i--) {
+    const MGPlan::Level& f = plan->lv[i + 1];
+    MGPlan::Level& c = plan->lv[i];
+    c.nx = f.nx / 2, c.ny = f.ny / 2, c.nz = f.nz / 2;
+    c.n = (int64_t)c.nx * c.ny * c.nz;
+    coarsen_axis(f.cx, c.cx, &c.ncx);
+    coarsen_axis(f.cy, c.cy, &c.ncy);
+    coarsen_axis(f.cz, c.cz, &c.ncz);
+    if (c.ncx > 255 || c.ncy > 255 || c.ncz > 255) return "multigrid: too many coarse classes along an axis";
+    if ((int64_t)c.ncls() > (1 << 20)) return "multigrid: too many coarse classes";
+    const std::vector<int> rx = representatives(c.cx, c.ncx), ry = representatives(c.cy, c.ncy),
+                           rz = representatives(c.cz, c.ncz);
+    c.tq.assign((size_t)Q * c.ncls() * 27, 0.0);
+    for (int q = 0; q < Q; q++)
+      for (int czi = 0; czi < c.ncz; czi++)
+        for (int cyi = 0; cyi < c.ncy; cyi++)
+          for (int cxi = 0; cxi < c.ncx; cxi++) {
+            const int Jx = rx[cxi], Jy = ry[cyi], Jz = rz[czi];
+            double* row = &c.tq[(((size_t)q * c.ncz + czi) * c.ncy + cyi) * c.ncx * 27 + (size_t)cxi * 27];
+            // row J of P^T A P = sum_i P[i][J] sum_l A[i][l] P[l][K]
+            for (int iz = 2 * Jz - 1; iz <= 2 * Jz + 1; iz++) {
+              if (iz < 1 || iz > f.nz) continue;
+              const double wz = iz == 2 * Jz ? 1.0 : 0.5;
+              for (int iy = 2 * Jy - 1; iy <= 2 * Jy + 1; iy++) {
+                if (iy < 1 || iy > f.ny) continue;
+                const double wy = iy == 2 * Jy ? 1.0 : 0.5;
+                for (int ix = 2 * Jx - 1; ix <= 2 * Jx + 1; ix++) {
+                  if (ix < 1 || ix > f.nx) continue;
+                  const double wi = (ix == 2 * Jx ? 1.0 : 0.5) * wy * wz;
+                  const int fcls = (f.cz[iz - 1] * f.ncy + f.cy[iy - 1]) * f.ncx + f.cx[ix - 1];
+                  const double* frow = &f.tq[((size_t)q * f.ncls() + fcls) * 27];
+                  for (int dz = -1; dz <= 1; dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                      for (int dx = -1; dx <= 1; dx++) {
+                        const double a = frow[off27(dx, dy, dz)];
+                        const int lx = ix + dx, ly = iy + dy, lz = iz + dz;
+                        if (a == 0.0 || lx < 1 || lx > f.nx || ly < 1 || ly > f.ny || lz < 1 || lz > f.nz) continue;
+                        int Kx[2], Ky[2], Kz[2];
+                        double wx_[2], wy_[2], wz_[2];
+                        const int nkx = pweights(lx, c.nx, Kx, wx_), nky = pweights(ly, c.ny, Ky, wy_),
+                                  nkz = pweights(lz, c.nz, Kz, wz_);
+                        for (int a3 = 0; a3 < nkz; a3++)
+                          for (int a2 = 0; a2 < nky; a2++)
+                            for (int a1 = 0; a1 < nkx; a1++)
+                              row[off27(Kx[a1] - Jx, Ky[a2] - Jy, Kz[a3] - Jz)] +=
+                                  wi * a * wx_[a1] * wy_[a2] * wz_[a3];
+                      }
+                }
+              }
+            }
+          }
+  }
+  // level 0 as dense matrices of the affine terms
+  const MGPlan::Level& c0 = plan->lv[0];
+  const int n0 = plan->n0;
+  plan->a0q.assign((size_t)Q * n0 * n0, 0.0);
+  for (int q = 0; q < Q; q++)
+    for (int k = 0; k < c0.nz; k++)
+      for (int j = 0; j < c0.ny; j++)
+        for (int i = 0; i < c0.nx; i++) {
+          const int row_id = (k * c0.ny + j) * c0.nx + i;
+          const int cls = (c0.cz[k] * c0.ncy + c0.cy[j]) * c0.ncx + c0.cx[i];
+          const double* r = &c0.tq[((size_t)q * c0.ncls() + cls) * 27];
+          for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+              for (int dx = -1; dx <= 1; dx++) {
+                const int x = i + dx, y = j + dy, z = k + dz;
+                if (x < 0 || x >= c0.nx || y < 0 || y >= c0.ny || z < 0 || z >= c0.nz) continue;
+                plan->a0q[((size_t)q * n0 + row_id) * n0 + (z * c0.ny + y) * c0.nx + x] += r[off27(dx, dy, dz)];
+              }
+        }
+  // device copies (levels below the finest; the finest uses the solver's tables and Geo)
+  for (int i = 0; i < plan->J; i++) {
+    const MGPlan::Level& c = plan->lv[i];
+    std::vector<uint8_t> cls(c.cx);
+    cls.insert(cls.end(), c.cy.begin(), c.cy.end());
+    cls.insert(cls.end(), c.cz.begin(), c.cz.end());
+    if (cudaMalloc(&plan->d_cls[i], cls.size()) != cudaSuccess ||
+        cudaMalloc(&plan->d_tq[i], sizeof(double) * c.tq.size()) != cudaSuccess)
+      return "multigrid: out of device memory";
+    cudaMemcpy(plan->d_cls[i], cls.data(), cls.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(plan->d_tq[i], c.tq.data(), sizeof(double) * c.tq.size(), cudaMemcpyHostToDevice);
+  }
+  if (cudaMalloc(&plan->d_a0q, sizeof(double) * plan->a0q.size()) != cudaSuccess)
+    return "multigrid: out of device memory";
+  cudaMemcpy(plan->d_a0q, plan->a0q.data(), sizeof(double) * plan->a0q.size(), cudaMemcpyHostToDevice);
+  return "";
+}
+
+// ---------------------------------------------------------------------------
+// Device: per-instance set-up
+// ---------------------------------------------------------------------------
+namespace {
+
+// out[b][c][0..26] = sum_q mu[b][q] tq[q][c][..];  out[b][c][27] = 1 / diagonal.
+__global__ void k_mg_tables(int Q, int ncls, const double* __restrict__ tq, const double* __restrict__ mu,
+                            int B, double* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B * ncls) return;
+  const int b = (int)(t / ncls), c = (int)(t % ncls);
+  double* o = out + t * 28;
+  for (int k = 0; k < 27; k++) {
+    double v = 0.0;
+    for (int q = 0; q < Q; q++) v = fma(mu[(int64_t)b * Q + q], tq[((int64_t)q * ncls + c) * 27 + k], v);
+    o[k] = v;
+  }
+  o[27] = 1.0 / o[13];
+}
+
+// Level-0 matrix of one instance per CTA: A = sum_q mu_q A0_q, lower Cholesky
+// in place, L^-1 column by column, then A^-1 = L^-T L^-1.
+__global__ void k_mg_dense_setup(int Q, int n0, const double* __restrict__ a0q, const double* __restrict__ mu,
+                                 double* __restrict__ A_all, double* __restrict__ Li_all,
+                                 double* __restrict__ Ai_all, int* __restrict__ info) {
+  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int64_t nn = (int64_t)n0 * n0;
+  double* A = A_all + b * nn;
+  double* Li = Li_all + b * nn;
+  double* Ai = Ai_all + b * nn;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  for (int64_t e = tid; e < nn; e += nt) {
+    double v = 0.0;
+    for (int q = 0; q < Q; q++) v = fma(mu[(int64_t)b * Q + q], a0q[q * nn + e], v);
+    A[e] = v;
+    Li[e] = 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n0; k++) {
+    if (tid == 0) {
+      const double d = A[(int64_t)k * n0 + k];
+      if (!(d > 0.0)) bad = 1;
+      A[(int64_t)k * n0 + k] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double piv = A[(int64_t)k * n0 + k];
+    for (int i = k + 1 + tid; i < n0; i += nt) A[(int64_t)i * n0 + k] /= piv;
+    __syncthreads();
+    const int m = n0 - k - 1;  // trailing lower triangle, row-major pairs (i >= j)
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+      const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      if (j <= i) A[(int64_t)i * n0 + j] -= A[(int64_t)i * n0 + k] * A[(int64_t)j * n0 + k];
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < n0; j += nt) {  // column j of L^-1
+    Li[(int64_t)j * n0 + j] = 1.0 / A[(int64_t)j * n0 + j];
+    for (int i = j + 1; i < n0; i++) {
+      double s = 0.0;
+      for (int k = j; k < i; k++) s = fma(A[(int64_t)i * n0 + k], Li[(int64_t)k * n0 + j], s);
+      Li[(int64_t)i * n0 + j] = -s / A[(int64_t)i * n0 + i];
+    }
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < nn; e += nt) {
+    const int i = (int)(e / n0), j = (int)(e % n0);
+    double s = 0.0;
+    for (int k = max(i, j); k < n0; k++) s = fma(Li[(int64_t)k * n0 + i], Li[(int64_t)k * n0 + j], s);
+    Ai[e] = s;
+  }
+  if (tid == 0) info[b] = bad;
+}
+
+}  // namespace
+
+void launch_mg_setup(const MGPlan& plan, const double* mu, int B, double* const* tables, double* dense_a,
+                     double* dense_l, double* ainv, int* info, cudaStream_t s) {
+  for (int i = 1; i < plan.J; i++) {
+    const int ncls = plan.lv[i].ncls();
+    const int64_t total = (int64_t)B * ncls;
+    k_mg_tables<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(plan.Q, ncls, plan.d_tq[i], mu, B, tables[i]);
+  }
+  k_mg_dense_setup<<<B, 256, 0, s>>>(plan.Q, plan.n0, plan.d_a0q, mu, dense_a, dense_l, ainv, info);
+}
+
+// ---------------------------------------------------------------------------
+// Device: the V-cycle
+// ---------------------------------------------------------------------------
+namespace {
+
+template <bool kSeven>
+__device__ __forceinline__ double mg_row_apply(const double* __restrict__ row, const double* __restrict__ x,
+                                               int i, int j, int k, int nx, int ny, int nz) {
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const int64_t c = ((int64_t)k * ny + j) * nx + i;
+  if (kSeven) {  // -kW, -kE, -kS, -kN, -kD, -kU, D
+    double v = row[6] * x[c];
+    if (i > 0) v = fma(row[0], x[c - 1], v);
+    if (i < nx - 1) v = fma(row[1], x[c + 1], v);
+    if (j > 0) v = fma(row[2], x[c - sy], v);
+    if (j < ny - 1) v = fma(row[3], x[c + sy], v);
+    if (k > 0) v = fma(row[4], x[c - sz], v);
+    if (k < nz - 1) v = fma(row[5], x[c + sz], v);
+    return v;
+  }
+  double v = 0.0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; dz++) {
+    if (k + dz < 0 || k + dz >= nz) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+      if (j + dy < 0 || j + dy >= ny) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; dx++) {
+        if (i + dx < 0 || i + dx >= nx) continue;
+        v = fma(row[(dz + 1) * 9 + (dy + 1) * 3 + dx + 1], x[c + dz * sz + dy * sy + dx], v);
+      }
+    }
+  }
+  return v;
+}
+
+// mode 0: out = omega D^-1 rhs (smoothing from zero)
+// mode 1: out = x + omega D^-1 (rhs - A x)
+// mode 2: out = rhs - A x (residual)
+template <bool kSeven>
+__global__ void __launch_bounds__(256) k_mg_level(MGLevel L, const InstState* __restrict__ st, int mode,
+                                                  const double* __restrict__ rhs, const double* __restrict__ x,
+                                                  double* __restrict__ out, double omega) {
+  const int b = blockIdx.y;
+  if (st && st[b].status != ST_ACTIVE) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= L.n) return;
+  const int i = (int)(t % L.nx), j = (int)((t / L.nx) % L.ny), k = (int)(t / ((int64_t)L.nx * L.ny));
+  const int cls = (L.cz[k] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
+  const double* row = L.coef + ((int64_t)b * L.ncx * L.ncy * L.ncz + cls) * L.stride;
+  const int64_t off = (int64_t)b * L.n;
+  const double dinv = row[L.stride - 1];
+  const double bv = rhs[off + t];
+  if (mode == 0) {
+    out[off + t] = omega * dinv * bv;
+    return;
+  }
+  const double ax = mg_row_apply<kSeven>(row, x + off, i, j, k, L.nx, L.ny, L.nz);
+  out[off + t] = mode == 1 ? fma(omega * dinv, bv - ax, x[off + t]) : bv - ax;
+}
+
+// rc = P^T rf (coarse node J gathers fine nodes 2J-1 .. 2J+1 per axis).
+__global__ void __launch_bounds__(256) k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
+                                                     const InstState* __restrict__ st,
+                                                     const double* __restrict__ rf, double* __restrict__ rc) {
+  const int b = blockIdx.y;
+  if (st && st[b].status != ST_ACTIVE) return;
+  const int64_t cn = (int64_t)cnx * cny * cnz;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= cn) return;
+  const int I = (int)(t % cnx), Jy = (int)((t / cnx) % cny), K = (int)(t / ((int64_t)cnx * cny));
+  const int64_t fn = (int64_t)fnx * fny * fnz;
+  const double* r = rf + (int64_t)b * fn;
+  double v = 0.0;
+  for (int dz = -1; dz <= 1; dz++) {
+    const int z = 2 * K + 1 + dz;  // 0-based fine index of 1-based 2(K+1)+dz
+    if (z < 0 || z >= fnz) continue;
+    const double wz = dz == 0 ? 1.0 : 0.5;
+    for (int dy = -1; dy <= 1; dy++) {
+      const int y = 2 * Jy + 1 + dy;
+      if (y < 0 || y >= fny) continue;
+      const double wy = dy == 0 ? wz : 0.5 * wz;
+      for (int dx = -1; dx <= 1; dx++) {
+        const int x = 2 * I + 1 + dx;
+        if (x < 0 || x >= fnx) continue;
+        v = fma(dx == 0 ? wy : 0.5 * wy, r[((int64_t)z * fny + y) * fnx + x], v);
+      }
+    }
+  }
+  rc[(int64_t)b * cn + t] = v;
+}
+
+// uf += P ec (fine node i takes coarse i/2 if i is even, else half of each
+// coarse neighbour (i-1)/2 and (i+1)/2 that exists; 1-based).
+__device__ __forceinline__ int pw(int i0, int m, int K[2], double w[2]) {
+  const int i = i0 + 1;
+  if (i % 2 == 0) {
+    K[0] = i / 2 - 1;
+    w[0] = 1.0;
+    return 1;
+  }
+  int c = 0;
+  if ((i - 1) / 2 >= 1) K[c] = (i - 1) / 2 - 1, w[c++] = 0.5;
+  if ((i + 1) / 2 <= m) K[c] = (i + 1) / 2 - 1, w[c++] = 0.5;
+  return c;
+}
+
+__global__ void __launch_bounds__(256) k_mg_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
+                                                        const InstState* __restrict__ st,
+                                                        const double* __restrict__ ec, double* __restrict__ uf) {
+  const int b = blockIdx.y;
+  if (st && st[b].status != ST_ACTIVE) return;
+  const int64_t fn = (int64_t)fnx * fny * fnz;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= fn) return;
+  const int i = (int)(t % fnx), j = (int)((t / fnx) % fny), k = (int)(t / ((int64_t)fnx * fny));
+  int Kx[2], Ky[2], Kz[2];
+  double wx[2], wy[2], wz[2];
+  const int nx_ = pw(i, cnx, Kx, wx), ny_ = pw(j, cny, Ky, wy), nz_ = pw(k, cnz, Kz, wz);
+  const double* e = ec + (int64_t)b * cnx * cny * cnz;
+  double v = 0.0;
+  for (int c = 0; c < nz_; c++)
+    for (int bq = 0; bq < ny_; bq++)
+      for (int a = 0; a < nx_; a++)
+        v = fma(wx[a] * wy[bq] * wz[c], e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
+  uf[(int64_t)b * fn + t] += v;
+}
+
+// x0 = A0^-1 b0 per instance (one CTA per instance).
+__global__ void k_mg_dense_apply(int n0, const double* __restrict__ ainv, const InstState* __restrict__ st,
+                                 const double* __restrict__ rhs, double* __restrict__ out) {
+  const int b = blockIdx.x;
+  if (st && st[b].status != ST_ACTIVE) return;
+  const double* Ai = ainv + (int64_t)b * n0 * n0;
+  const double* r = rhs + (int64_t)b * n0;
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    double v = 0.0;
+    for (int j = 0; j < n0; j++) v = fma(Ai[(int64_t)i * n0 + j], r[j], v);
+    out[(int64_t)b * n0 + i] = v;
+  }
+}
+
+inline dim3 level_grid(int64_t n, int B) { return dim3((unsigned)((n + 255) / 256), (unsigned)B); }
+
+int level_op(const MGBatch& m, int i, int mode, const double* rhs, const double* x, double* out, cudaStream_t s) {
+  const MGLevel& L = m.lv[i];
+  if (L.stride == 8)
+    k_mg_level<true><<<level_grid(L.n, m.B), 256, 0, s>>>(L, m.st, mode, rhs, x, out, kMGOmega);
+  else
+    k_mg_level<false><<<level_grid(L.n, m.B), 256, 0, s>>>(L, m.st, mode, rhs, x, out, kMGOmega);
+  return 1;
+}
+
+// out = MG(rhs, A^i, i)
+int vcycle(const MGBatch& m, int i, const double* rhs, double* out, cudaStream_t s) {
+  const MGPlan& P = *m.plan;
+  if (i == 0) {
+    k_mg_dense_apply<<<m.B, 128, 0, s>>>(P.n0, m.ainv, m.st, rhs, out);
+    return 1;
+  }
+  int launches = 0;
+  double* cur = m.w1[i];
+  double* nxt = m.w2[i];
+  launches += level_op(m, i, 0, rhs, nullptr, cur, s);  // pre-smoothing from zero
+  for (int k = 1; k < kMGNu; k++) {
+    launches += level_op(m, i, 1, rhs, cur, nxt, s);
+    std::swap(cur, nxt);
+  }
+  launches += level_op(m, i, 2, rhs, cur, nxt, s);       // residual into the free buffer
+  const MGLevel& F = m.lv[i];
+  const MGLevel& C = m.lv[i - 1];
+  k_mg_restrict<<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, nxt, m.rhs[i - 1]);
+  launches += 1;
+  launches += vcycle(m, i - 1, m.rhs[i - 1], m.sol[i - 1], s);
+  k_mg_prolong_add<<<level_grid(F.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.sol[i - 1], cur);
+  launches += 1;
+  for (int k = 1; k <= kMGNu; k++) {                      // post-smoothing
+    double* dst = k == kMGNu ? out : nxt;
+    launches += level_op(m, i, 1, rhs, cur, dst, s);
+    if (k < kMGNu) std::swap(cur, nxt);
+  }
+  return launches;
+}
+
+}  // namespace
+
+int launch_mg_vcycle(const MGBatch& m, const double* rhs, double* out, cudaStream_t s) {
+  return vcycle(m, m.plan->J, rhs, out, s);
+}
+
+void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s) {
+  if (L.stride == 8)
+    k_mg_level<true><<<level_grid(L.n, B), 256, 0, s>>>(L, nullptr, 0, x, nullptr, y, 1.0);
+  else
+    k_mg_level<false><<<level_grid(L.n, B), 256, 0, s>>>(L, nullptr, 0, x, nullptr, y, 1.0);
+}
+
+}  // namespace rbws

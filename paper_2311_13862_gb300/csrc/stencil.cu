@@ -288,7 +288,8 @@ __global__ void k_cg_init(CGArgs<T> a, int parity) {
   T* rb = a.r + off;
   T* sb = a.s + off;
   const bool jac = a.precond != RBWS_PREC_NONE;  // Jacobi, or D^{-1} r as MSRB's first sweep
-  const bool msrb = a.precond == RBWS_PREC_MSRB;
+  // MSRB and MG compute s and rho = r.s in their own passes
+  const bool msrb = a.precond == RBWS_PREC_MSRB || a.precond == RBWS_PREC_MG;
   T rho = T(0), rr = T(0);
   if (a.rhs64 == nullptr) {
     zmarch<T>(
@@ -501,7 +502,7 @@ __global__ void k_cg_b(CGArgs<T> a, int parity) {
   T* rb = a.r + off;
   T* sb = a.s + off;
   const bool jac = a.precond != RBWS_PREC_NONE;
-  const bool msrb = a.precond == RBWS_PREC_MSRB;
+  const bool msrb = a.precond == RBWS_PREC_MSRB || a.precond == RBWS_PREC_MG;
   const Column cl = make_column(a.g, tp.x0, tp.y0);
   const int64_t plane = (int64_t)a.g.nx * a.g.ny;
   T rho = T(0), rr = T(0);
@@ -652,6 +653,28 @@ __global__ void k_msrb_lift(CGArgs<double> a, int slot) {
       rho = fma(a.r[off + idx], sv, rho);
     }
   }
+  double dummy = 0.0;
+  block_sum2(rho, dummy, red);
+  if (tid == 0) a.rho_rr[((int64_t)slot * a.B + b) * a.P + tp.part].x = rho;
+}
+
+// Partials of rho = r.s after an external preconditioner (the MG V-cycle) has
+// written s; same tiling and slot layout as the update phase.
+__global__ void k_precond_rho(CGArgs<double> a, int slot) {
+  __shared__ double red[64];
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const int64_t off = (int64_t)b * a.g.n;
+  const Column cl = make_column(a.g, tp.x0, tp.y0);
+  const int64_t plane = (int64_t)a.g.nx * a.g.ny;
+  double rho = 0.0;
+  if (cl.own)
+    for (int z = tp.z0; z < tp.z1; ++z) {
+      const int64_t idx = off + (int64_t)z * plane + cl.col;
+      rho = fma(a.r[idx], a.s[idx], rho);
+    }
   double dummy = 0.0;
   block_sum2(rho, dummy, red);
   if (tid == 0) a.rho_rr[((int64_t)slot * a.B + b) * a.P + tp.part].x = rho;
@@ -854,6 +877,10 @@ void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s) {
 }
 void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s) {
   k_ru_reset<<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, start);
+}
+
+void launch_precond_rho(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s) {
+  k_precond_rho<<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, slot);
 }
 
 void launch_msrb_apply(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s) {

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "WARN_NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ER
                 -4: "ERR_NO_BASIS", -5: "ERR_NOT_SPD", -6: "ERR_DEVICE_TIMEOUT", -7: "ERR_STATE",
                 -8: "ERR_UNSUPPORTED"}
 WARM_ZERO, WARM_GALERKIN, WARM_LEARNED, WARM_LEARNED_CORRECTED = 0, 1, 2, 3
-PREC_NONE, PREC_JACOBI, PREC_MSRB = 0, 1, 2
+PREC_NONE, PREC_JACOBI, PREC_MSRB, PREC_MG = 0, 1, 2, 3
 FP64, FP32_IR = 0, 1
 
 
@@ -71,6 +71,7 @@ def _lib():
         L.rbws_problem_destroy.argtypes = [P]
         L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
+        L.rbws_apply_preconditioner.argtypes = [P, P, i32, i32, P, P, P]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, i32, P, P, C.POINTER(i32)]
         L.rbws_set_basis.argtypes = [P, i32, P, P, P]
@@ -91,7 +92,7 @@ def _lib():
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
                      "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
-                     "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load"):
+                     "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load", "rbws_apply_preconditioner"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -155,6 +156,13 @@ def rbws_problem_info(h):
     n, Q, N = C.c_int64(), C.c_int32(), C.c_int32()
     _check(_lib().rbws_problem_info(h, C.byref(n), C.byref(Q), C.byref(N)), "rbws_problem_info")
     return n.value, Q.value, N.value
+
+
+def rbws_apply_preconditioner(h, mu, x, y, precond=PREC_MG, stream=None):
+    """y[b] = P(mu_b) x[b] (Jacobi or one multigrid V-cycle); x, y CUDA float64 [B][n]."""
+    mu = _host(np.atleast_2d(mu))
+    _check(_lib().rbws_apply_preconditioner(h, _hp(mu), mu.shape[0], precond, _dp(x), _dp(y), stream),
+           "rbws_apply_preconditioner")
 
 
 def rbws_apply_operator(h, mu, x, y, precision=FP64, stream=None):

@@ -1,0 +1,107 @@
+"""Parity of the CUDA multigrid V-cycle (Algorithm 2) and MGCG with the oracle's
+(oracle.mg: scipy Galerkin products, dense Cholesky on the coarsest level)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import mg
+from paper_2311_13862_gb300 import inputs, rbws
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [((16, 16, 16), (2, 1, 1)),     # 3 levels
+         ((24, 20, 18), (2, 2, 1)),     # 4 levels, odd and even axes
+         ((33, 17, 20), (2, 2, 2)),     # ragged
+         ((40, 36, 32), (3, 3, 3)),     # 27 subdomains, node on no interface
+         ((4, 4, 3), (2, 1, 1)),        # one level: the exact solve
+         ((130, 9, 3), (3, 1, 1))]      # an axis reaches one node: coarsest level of 260
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2311_13862_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("grid,blocks", GRIDS)
+def test_vcycle_matches_oracle(grid, blocks):
+    op = O.assemble(grid, blocks)
+    H = mg.Hierarchy(op)
+    B = 3
+    mu = inputs.log_uniform(101, B, op.Q, 0.01, 100.0)
+    x = inputs.random_field(102, (B, op.n))
+    ref = np.stack([mg.vcycle(H.operators(mu[b]), x[b]) for b in range(B)])
+    with rbws.Problem(grid, blocks) as P:
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        rbws.rbws_apply_preconditioner(P.h, mu, xd, yd, rbws.PREC_MG)
+        y = yd.cpu().numpy()
+        assert torch.equal(xd.cpu(), torch.from_numpy(x))  # the input is left alone
+    err = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= 1e-11), err
+
+
+def test_jacobi_preconditioner_is_the_inverse_diagonal():
+    grid, blocks = (33, 17, 20), (2, 2, 2)
+    op = O.assemble(grid, blocks)
+    mu = inputs.log_uniform(103, 2, op.Q, 0.01, 100.0)
+    x = inputs.random_field(104, (2, op.n))
+    with rbws.Problem(grid, blocks) as P:
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        rbws.rbws_apply_preconditioner(P.h, mu, xd, yd, rbws.PREC_JACOBI)
+        y = yd.cpu().numpy()
+    for b in range(2):
+        d = O.mg.Hierarchy(op).operators(mu[b]).A[mg.Hierarchy(op).J].diagonal()
+        assert np.allclose(y[b], x[b] / d, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("grid,blocks", GRIDS[:4])
+def test_mgcg_matches_oracle(grid, blocks):
+    op = O.assemble(grid, blocks)
+    H = mg.Hierarchy(op)
+    mu = inputs.log_uniform(105, 4, op.Q, 0.01, 100.0)
+    with rbws.Problem(grid, blocks) as P:
+        u = torch.empty((len(mu), P.n), dtype=torch.float64, device="cuda")
+        rc, it, rel, st = rbws.rbws_solve_batch(P.h, mu, 1e-12, rbws.WARM_ZERO, u,
+                                                rbws.rbws_options_default(precond=rbws.PREC_MG))
+        u = u.cpu().numpy()
+    assert rc == 0 and np.all(st == 0)
+    for b in range(len(mu)):
+        ref = mg.mgcg(op, mu[b], tol=1e-12, hier=H)
+        assert abs(it[b] - ref.iters) <= 2, (it[b], ref.iters)
+        assert np.linalg.norm(u[b] - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+        assert it[b] < 40
+
+
+def test_rb_warm_started_mgcg_matches_oracle():
+    """RBI-MGCG: the Galerkin RB initial value (Algorithm 4) with the MG preconditioner."""
+    w = inputs.small(grid=(24, 20, 18), blocks=(2, 2, 1), n_max=8, n_train=24, n_test=4)
+    op = O.assemble(w.grid, w.blocks)
+    H = mg.Hierarchy(op)
+    basis = O.greedy(op, inputs.train_mu(w), w.n_max)
+    mu = inputs.test_mu(w)
+    with rbws.Problem(w.grid, w.blocks) as P:
+        rbws.rbws_set_basis(P.h, basis.W, basis.ANq, basis.fN)
+        u = torch.empty((len(mu), P.n), dtype=torch.float64, device="cuda")
+        opt = rbws.rbws_options_default(precond=rbws.PREC_MG)
+        rc, it, rel, st = rbws.rbws_solve_batch(P.h, mu, 1e-12, rbws.WARM_GALERKIN, u, opt)
+        u0 = torch.empty_like(u)
+        _, it0, _, _ = rbws.rbws_solve_batch(P.h, mu, 1e-12, rbws.WARM_ZERO, u0, opt)
+        u = u.cpu().numpy()
+    assert rc == 0 and np.all(st == 0)
+    for b in range(len(mu)):
+        c = O.rb_solve(basis.ANq, basis.fN, mu[b])
+        ref = mg.mgcg(op, mu[b], u0=basis.W.T @ c, tol=1e-12, hier=H)
+        assert abs(it[b] - ref.iters) <= 2, (it[b], ref.iters)
+        assert np.linalg.norm(u[b] - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+    assert it.mean() < it0.mean()
+
+
+def test_mg_rejects_mixed_precision():
+    with rbws.Problem((16, 16, 16), (2, 1, 1)) as P:
+        u = torch.empty((1, P.n), dtype=torch.float64, device="cuda")
+        with pytest.raises(rbws.RbwsError, match="UNSUPPORTED"):
+            rbws.rbws_solve_batch(P.h, np.array([[1.0, 2.0]]), 1e-10, rbws.WARM_ZERO, u,
+                                  rbws.rbws_options_default(precond=rbws.PREC_MG, precision=rbws.FP32_IR))

@@ -54,9 +54,11 @@ def test_galerkin_coarse_operator_has_the_kronecker_form():
 
 
 def test_level_rule():
-    assert mg.level_grids((64, 64, 64)) == [(8, 8, 8), (16, 16, 16), (32, 32, 32), (64, 64, 64)]
-    assert mg.level_grids((9, 7, 5)) == [(9, 7, 5)]
-    assert mg.level_grids((24, 20, 18)) == [(6, 5, 4), (12, 10, 9), (24, 20, 18)]
+    assert mg.level_grids((64, 64, 64)) == [(4, 4, 4), (8, 8, 8), (16, 16, 16), (32, 32, 32), (64, 64, 64)]
+    assert mg.level_grids((4, 4, 4)) == [(4, 4, 4)]
+    assert mg.level_grids((9, 7, 5)) == [(4, 3, 2), (9, 7, 5)]
+    assert mg.level_grids((24, 20, 18)) == [(3, 2, 2), (6, 5, 4), (12, 10, 9), (24, 20, 18)]
+    assert mg.level_grids((130, 9, 3)) == [(65, 4, 1), (130, 9, 3)]  # an axis reached 1 node
 
 
 def test_vcycle_is_symmetric_positive_definite():
@@ -70,7 +72,7 @@ def test_vcycle_is_symmetric_positive_definite():
 
 
 def test_smoother_first_step_and_one_level_cycle():
-    op = O.assemble((9, 7, 5), (2, 1, 1))
+    op = O.assemble((4, 4, 3), (2, 1, 1))
     mu = np.array([0.3, 4.0])
     H = mg.Hierarchy(op)
     assert H.J == 0
