@@ -388,8 +388,12 @@ def main():
         # (Algorithm 3, FP64 only)
         arm_list.append(("msrb_fp64", rbws.WARM_GALERKIN, rbws.FP64))
         # MGCG (Algorithm 2 as the preconditioner, FP64), from zero and from the RB initial value
-        arm_list += [("mgcg_zero_fp64", rbws.WARM_ZERO, rbws.FP64), ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, rbws.FP64)]
-    precond_of = {"msrb_fp64": rbws.PREC_MSRB, "mgcg_zero_fp64": rbws.PREC_MG, "mgcg_galerkin_fp64": rbws.PREC_MG}
+        arm_list += [("mgcg_zero_fp64", rbws.WARM_ZERO, rbws.FP64), ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, rbws.FP64),
+                     ("mgcg_zero_fp32ir", rbws.WARM_ZERO, rbws.FP32_IR),
+                     ("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN, rbws.FP32_IR)]
+    precond_of = {"msrb_fp64": rbws.PREC_MSRB}
+    precond_of.update({k: rbws.PREC_MG for k in ("mgcg_zero_fp64", "mgcg_galerkin_fp64", "mgcg_zero_fp32ir",
+                                                "mgcg_galerkin_fp32ir")})
     for name, warm, pr in arm_list:
         if name.startswith("galerkin_" + args.precision):
             a_ms, a_it, a_rel, a_st = ms, it, rel, st

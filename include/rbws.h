@@ -75,7 +75,9 @@ typedef enum {
                            every axis at least 2 nodes; linear interpolation P
                            per axis; Galerkin coarse operators P^T A P; damped
                            Jacobi smoothing (omega = 2/3), 2 pre- and 2 post-
-                           steps; exact solve on the coarsest level.  FP64 only */
+                           steps; exact solve on the coarsest level.  FP64, or
+                           FP32 inside RBWS_FP32_IR (the inner iteration's
+                           V-cycle in FP32, coarsest inverse formed in FP64)  */
 } rbws_precond;
 
 typedef enum {
@@ -115,7 +117,9 @@ typedef struct {
                            taken each time an instance's FP32 residual has
                            fallen by this factor since its last one (1e-2)      */
   int32_t max_outer;    /* reserved (10)                                         */
-  int32_t check_every;  /* iterations between host convergence polls (0 = auto)  */
+  int32_t check_every;  /* iterations between host convergence polls and, in
+                           FP32_IR, reliable-update tests (0 = auto: 8, or 2
+                           for FP32_IR with RBWS_PREC_MG)                      */
   void* stream;         /* cudaStream_t: all GPU work of the call is issued on it;
                            NULL = an internal stream ordered after the legacy
                            default stream                                         */

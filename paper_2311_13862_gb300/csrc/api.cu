@@ -312,7 +312,7 @@ int launch_iteration(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s) {
     }
     if (a.precond == RBWS_PREC_MG) {
       const int l = launch_mg_vcycle(*a.mg, a.r, a.s, s);
-      launch_precond_rho(a, t, parity ^ 1, s);
+      launch_precond_rho<double>(a, t, parity ^ 1, nullptr, s);
       return 3 + l;
     }
   }
@@ -329,7 +329,7 @@ int launch_precond_start(const CGArgs<T>& a, Tile t, cudaStream_t s) {
     }
     if (a.precond == RBWS_PREC_MG) {
       const int l = launch_mg_vcycle(*a.mg, a.r, a.s, s);
-      launch_precond_rho(a, t, 0, s);
+      launch_precond_rho<double>(a, t, 0, nullptr, s);
       return 1 + l;
     }
   }
@@ -407,7 +407,7 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
           }
           if (a.precond == RBWS_PREC_MG) {
             per_iter = 3 + launch_mg_vcycle(*a.mg, a.r, a.s, s);
-            launch_precond_rho(a, t, 1, s);
+            launch_precond_rho<double>(a, t, 1, nullptr, s);
           }
         }
         for (int k = 1; k < M; k++) launch_iteration<T>(a, t, k & 1, s);
@@ -554,50 +554,55 @@ rbws_status mg_plan(rbws_problem p, const MGPlan** out) {
 }
 
 // Per-batch V-cycle state: level views, work vectors, coarse tables and the
-// level-0 inverses for B parameters (device mu), finest tables coef64.
-rbws_status mg_batch(rbws_problem p, const double* d_mu, int B, const double* coef64, const InstState* st,
+// level-0 inverses for B parameters (device mu); coef = the finest level's
+// tables, FP32 (fp32 = 1, the mixed-precision inner iteration) or FP64.
+rbws_status mg_batch(rbws_problem p, const double* d_mu, int B, const void* coef, int fp32, const InstState* st,
                      MGBatch* m) {
   const MGPlan* plan = nullptr;
   CKI(mg_plan(p, &plan));
   m->plan = plan;
   m->B = B;
+  m->fp32 = fp32;
   m->st = st;
+  const size_t el = fp32 ? sizeof(float) : sizeof(double);
+  const std::string tag = fp32 ? "mg32_" : "mg64_";
   int err = 0;
-  double* tables[kMGMaxLevels] = {};
+  void* tables[kMGMaxLevels] = {};
   for (int i = 0; i <= plan->J && !err; i++) {
     const MGPlan::Level& L = plan->lv[i];
     MGLevel& v = m->lv[i];
     v.nx = L.nx, v.ny = L.ny, v.nz = L.nz, v.n = L.n;
     v.ncx = L.ncx, v.ncy = L.ncy, v.ncz = L.ncz;
     const std::string k = std::to_string(i);
-    const size_t vec = sizeof(double) * (size_t)B * L.n;
+    const size_t vec = el * (size_t)B * L.n;
     if (i == plan->J) {
       v.cx = p->geo.cx, v.cy = p->geo.cy, v.cz = p->geo.cz;
-      v.coef = coef64;
+      v.coef = coef;
       v.stride = kCoefStride;
     } else {
       v.cx = plan->d_cls[i], v.cy = v.cx + L.nx, v.cz = v.cy + L.ny;
       v.stride = 28;
-      m->rhs[i] = (double*)p->buf("mg_rhs" + k, vec, &err);
-      if (!err) m->sol[i] = (double*)p->buf("mg_sol" + k, vec, &err);
+      m->rhs[i] = p->buf(tag + "rhs" + k, vec, &err);
+      if (!err) m->sol[i] = p->buf(tag + "sol" + k, vec, &err);
       if (i >= 1 && !err) {
-        tables[i] = (double*)p->buf("mg_tab" + k, sizeof(double) * (size_t)B * L.ncls() * 28, &err);
+        tables[i] = p->buf(tag + "tab" + k, el * (size_t)B * L.ncls() * 28, &err);
         v.coef = tables[i];
       }
     }
     if (i >= 1 && !err) {
-      m->w1[i] = (double*)p->buf("mg_w1_" + k, vec, &err);
-      if (!err) m->w2[i] = (double*)p->buf("mg_w2_" + k, vec, &err);
+      m->w1[i] = p->buf(tag + "w1_" + k, vec, &err);
+      if (!err) m->w2[i] = p->buf(tag + "w2_" + k, vec, &err);
     }
   }
-  const size_t dense = sizeof(double) * (size_t)B * plan->n0 * plan->n0;
-  double* da = err ? nullptr : (double*)p->buf("mg_dense_a", dense, &err);
-  double* dl = err ? nullptr : (double*)p->buf("mg_dense_l", dense, &err);
-  double* ai = err ? nullptr : (double*)p->buf("mg_dense_inv", dense, &err);
+  const size_t dense = (size_t)B * plan->n0 * plan->n0;
+  double* da = err ? nullptr : (double*)p->buf("mg_dense_a", sizeof(double) * dense, &err);
+  double* dl = err ? nullptr : (double*)p->buf("mg_dense_l", sizeof(double) * dense, &err);
+  double* ai = err ? nullptr : (double*)p->buf("mg_dense_inv", sizeof(double) * dense, &err);
+  float* ai32 = (err || !fp32) ? nullptr : (float*)p->buf("mg_dense_inv32", sizeof(float) * dense, &err);
   int* info = err ? nullptr : (int*)p->buf("mg_info", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
-  m->ainv = ai;
-  launch_mg_setup(*plan, d_mu, B, tables, da, dl, ai, info, p->cur);
+  m->ainv = fp32 ? (const void*)ai32 : (const void*)ai;
+  launch_mg_setup(*plan, d_mu, B, fp32, tables, da, dl, ai, ai32, info, p->cur);
   p->launches += plan->J + 1;
   CK(cudaGetLastError());
   std::vector<int> h(B);
@@ -652,7 +657,7 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
   }
   MGBatch mgb;  // outlives run_pcg: the launchers read it while capturing
   if (o.precond == RBWS_PREC_MG) {
-    CKI(mg_batch(p, d_mu, B, coef64, a.st, &mgb));
+    CKI(mg_batch(p, d_mu, B, coef64, 0, a.st, &mgb));
     a.mg = &mgb;
   }
   fill((double*)a.fnorm, B, p->fnorm, p->cur);
@@ -705,6 +710,9 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   }
   const bool v4 = t4.tx > 0;
   if (!v4) sched = 0;
+  const bool mg = o.precond == RBWS_PREC_MG;
+  if (mg && sched == 1) sched = 0;  // the 32-byte schedules store no separate s: Jacobi only
+  if (mg && sched == 3) sched = 2;
   const Tile t = v4 ? t4 : choose_tile(p->nx);
   if ((sched == 2 || sched == 3) && !tma_supported(p->geo, t)) sched = 0;
   if (sched == 2 || sched == 3) tma_prepare();
@@ -718,15 +726,32 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     else if (v4) launch_cg_a_v4(aa, t, par, ss);
     else launch_cg_a<float>(aa, t, par, ss);
   };
+  MGBatch mgb;  // FP32 V-cycle state; outlives the captured graph's launches
+  int mg_launches = 0;
+  // s = MG(r) and the partials of rho = r.s into `slot`, for the instances in
+  // mgb.mask (all when null)
+  auto mg_apply = [&](const CGArgs<float>& aa, int slot, cudaStream_t ss) {
+    int l = launch_mg_vcycle(mgb, aa.r, aa.s, ss);
+    if (v4) launch_precond_rho_v4(aa, t, slot, mgb.mask, ss);
+    else launch_precond_rho<float>(aa, t, slot, mgb.mask, ss);
+    return l + 1;
+  };
   auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
     if (sched == 1) launch_cg_b32_v4(aa, t, par, ss);
     else if (sched == 3) launch_cg_b_s_tma(aa, t, par, tma_err, ss);
     else if (v4) launch_cg_b_v4(aa, t, par, ss);
     else launch_cg_b<float>(aa, t, par, ss);
+    if (mg) mg_launches = mg_apply(aa, par ^ 1, ss);
   };
+  int* upd_mask = nullptr;  // set below: instances taking a reliable update
   auto reset = [&](const CGArgs<float>& aa, int start, cudaStream_t ss) {
     if (v4) launch_ru_reset_v4(aa, t, start, ss);
     else launch_ru_reset(aa, t, start, ss);
+    if (mg) {  // the reset instances need s = MG(r) and rho again
+      mgb.mask = upd_mask;
+      mg_apply(aa, 0, ss);
+      mgb.mask = nullptr;
+    }
   };
   cudaStream_t s = p->cur;
   int err = 0;
@@ -752,6 +777,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.u64 = u;
   a.r64 = r64;
   a.rel64 = rel;
+  upd_mask = upd;
+  if (mg) CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
   if (sched32) {
     a.alpha = (double*)p->buf("ir_alpha", sizeof(double) * 2 * (size_t)B, &err);
     if (err) return (rbws_status)err;
@@ -767,7 +794,11 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   reset(a, 1, s);
   p->launches += 2;
   CK(cudaGetLastError());
-  int M = o.check_every > 0 ? o.check_every : 8;
+  // The reliable-update test runs at block boundaries.  A multigrid-preconditioned
+  // iteration gains about a decade per step, so blocks of 8 would carry the FP32
+  // recursion far below its own accuracy floor (it then stagnates or breaks down);
+  // with MG the blocks are 2 iterations long.
+  int M = o.check_every > 0 ? o.check_every : (mg ? 2 : 8);
   if (M % 2) M++;
   rbws_profile* prof = o.profile;
   if (prof) {
@@ -809,7 +840,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
       reset(a, 0, s);
       CK(cudaMemsetAsync(a.pending, 0, sizeof(int), s));
-      p->launches += 4;
+      p->launches += 4 + mg_launches;
       continue;
     }
     if (active == 0) break;
@@ -842,7 +873,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       prof->active_dofs += (double)active * (double)p->n;
       prof->samples += 1;
     }
-    p->launches += 2 * M + 1;
+    p->launches += (2 + mg_launches) * M + 1;
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -1068,8 +1099,8 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
     set_error("solve: unknown preconditioner");
     return RBWS_ERR_INVALID_ARG;
   }
-  if ((o.precond == RBWS_PREC_MSRB || o.precond == RBWS_PREC_MG) && o.precision != RBWS_FP64) {
-    set_error("solve: the MSRB and multigrid preconditioners run in FP64 only");
+  if (o.precond == RBWS_PREC_MSRB && o.precision != RBWS_FP64) {
+    set_error("solve: the MSRB preconditioner runs in FP64 only");
     return RBWS_ERR_UNSUPPORTED;
   }
   if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_LEARNED_CORRECTED) {
@@ -1361,12 +1392,12 @@ rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t 
   CKI(coef_tables(p, d_mu, B, &c64, nullptr));
   if (precond == RBWS_PREC_JACOBI) {
     MGLevel L{p->nx, p->ny, p->nz, p->n, p->geo.ncx, p->geo.ncy, p->geo.ncz, p->geo.cx, p->geo.cy, p->geo.cz,
-              c64, kCoefStride};
+              (const void*)c64, kCoefStride};
     launch_diag_inverse(L, B, (const double*)x, (double*)y, p->cur);
     p->launches += 1;
   } else {
     MGBatch m;
-    CKI(mg_batch(p, d_mu, B, c64, nullptr, &m));
+    CKI(mg_batch(p, d_mu, B, c64, 0, nullptr, &m));
     p->launches += launch_mg_vcycle(m, (const double*)x, (double*)y, p->cur);
   }
   CK(cudaGetLastError());

@@ -264,8 +264,12 @@ void launch_unscale(const float* y, const float* scale, int B, int N, double* c,
 void launch_reduced_cg_step(int N, int Q, const double* ANq, const double* fN, const double* mu, int B,
                             double* c, cudaStream_t s);
 
-// rho = r.s partials after an external preconditioner wrote s (stencil.cu).
-void launch_precond_rho(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s);
+// rho = r.s partials after an external preconditioner wrote s, in slot `slot`
+// of the phase kernels' partials (one-node tiling: stencil.cu; v4 tiling:
+// stencil_v4.cu); instances with mask[b] == 0 are skipped (mask may be null).
+template <typename T>
+void launch_precond_rho(const CGArgs<T>& a, Tile t, int slot, const int* mask, cudaStream_t s);
+void launch_precond_rho_v4(const CGArgs<float>& a, Tile t, int slot, const int* mask, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Multigrid V-cycle preconditioner, Algorithm 2 (mg.cu)
@@ -312,7 +316,7 @@ std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const Ax
                           int by, const uint8_t* segq_host, int Q, double sx, double sy, double sz,
                           MGPlan* plan);
 
-// Device view of one level for the V-cycle kernels.
+// Device view of one level for the V-cycle kernels (element type: the batch's).
 struct MGLevel {
   int nx, ny, nz;
   int64_t n;
@@ -320,30 +324,36 @@ struct MGLevel {
   const uint8_t* cx;
   const uint8_t* cy;
   const uint8_t* cz;
-  const double* coef;  // [B][ncls][stride]
-  int stride;          // 8: the finest 7-point table; 28: 27 entries + 1/diagonal
+  const void* coef;  // [B][ncls][stride]
+  int stride;        // 8: the finest 7-point table; 28: 27 entries + 1/diagonal
 };
 
 // Per-batch state of the V-cycle: level views, work vectors, level-0 inverses.
+// fp32: every vector, table and inverse is float (the inner iteration of the
+// mixed-precision solver), else double.
 struct MGBatch {
   const MGPlan* plan = nullptr;
   int B = 0;
+  int fp32 = 0;
   const InstState* st = nullptr;  // instances whose status is not ACTIVE are skipped
+  const int* mask = nullptr;      // and, if set, those with mask[b] == 0
   MGLevel lv[kMGMaxLevels];
-  double* rhs[kMGMaxLevels] = {};
-  double* sol[kMGMaxLevels] = {};
-  double* w1[kMGMaxLevels] = {};
-  double* w2[kMGMaxLevels] = {};
-  double* ainv = nullptr;  // [B][n0][n0]
+  void* rhs[kMGMaxLevels] = {};
+  void* sol[kMGMaxLevels] = {};
+  void* w1[kMGMaxLevels] = {};
+  void* w2[kMGMaxLevels] = {};
+  const void* ainv = nullptr;  // [B][n0][n0]
 };
 
-// Per-instance coarse tables and level-0 inverses for B parameters (device mu
-// [B][Q]); info[b] != 0 where a level-0 matrix is not positive definite.
-void launch_mg_setup(const MGPlan& plan, const double* mu, int B, double* const* tables, double* dense_a,
-                     double* dense_l, double* ainv, int* info, cudaStream_t s);
+// Per-instance coarse tables (element type per fp32) and level-0 inverses
+// for B parameters (device mu [B][Q]).  The inverses are formed in FP64
+// (dense_a, dense_l, ainv64) and, with fp32, rounded into ainv32.  info[b] != 0
+// where a level-0 matrix is not positive definite.
+void launch_mg_setup(const MGPlan& plan, const double* mu, int B, int fp32, void* const* tables, double* dense_a,
+                     double* dense_l, double* ainv64, float* ainv32, int* info, cudaStream_t s);
 // out = MG(rhs) on the finest level (Algorithm 2 at level J); returns launches.
-int launch_mg_vcycle(const MGBatch& m, const double* rhs, double* out, cudaStream_t s);
-// y = D^-1 x on level view L (instances all active).
+int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, cudaStream_t s);
+// y = D^-1 x on the FP64 level view L (instances all active).
 void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -233,25 +233,29 @@ std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const Ax
 namespace {
 
 // out[b][c][0..26] = sum_q mu[b][q] tq[q][c][..];  out[b][c][27] = 1 / diagonal.
+template <typename T>
 __global__ void k_mg_tables(int Q, int ncls, const double* __restrict__ tq, const double* __restrict__ mu,
-                            int B, double* __restrict__ out) {
+                            int B, T* __restrict__ out) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)B * ncls) return;
   const int b = (int)(t / ncls), c = (int)(t % ncls);
-  double* o = out + t * 28;
+  T* o = out + t * 28;
+  double diag = 1.0;
   for (int k = 0; k < 27; k++) {
     double v = 0.0;
     for (int q = 0; q < Q; q++) v = fma(mu[(int64_t)b * Q + q], tq[((int64_t)q * ncls + c) * 27 + k], v);
-    o[k] = v;
+    o[k] = (T)v;
+    if (k == 13) diag = v;
   }
-  o[27] = 1.0 / o[13];
+  o[27] = (T)(1.0 / diag);
 }
 
 // Level-0 matrix of one instance per CTA: A = sum_q mu_q A0_q, lower Cholesky
-// in place, L^-1 column by column, then A^-1 = L^-T L^-1.
+// in place, L^-1 column by column, then A^-1 = L^-T L^-1 (FP64; also rounded
+// to FP32 when ai32 is set).
 __global__ void k_mg_dense_setup(int Q, int n0, const double* __restrict__ a0q, const double* __restrict__ mu,
                                  double* __restrict__ A_all, double* __restrict__ Li_all,
-                                 double* __restrict__ Ai_all, int* __restrict__ info) {
+                                 double* __restrict__ Ai_all, float* __restrict__ ai32, int* __restrict__ info) {
   const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int64_t nn = (int64_t)n0 * n0;
   double* A = A_all + b * nn;
@@ -276,7 +280,7 @@ __global__ void k_mg_dense_setup(int Q, int n0, const double* __restrict__ a0q, 
     const double piv = A[(int64_t)k * n0 + k];
     for (int i = k + 1 + tid; i < n0; i += nt) A[(int64_t)i * n0 + k] /= piv;
     __syncthreads();
-    const int m = n0 - k - 1;  // trailing lower triangle, row-major pairs (i >= j)
+    const int m = n0 - k - 1;  // trailing lower triangle (pairs i >= j)
     for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
       const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
       if (j <= i) A[(int64_t)i * n0 + j] -= A[(int64_t)i * n0 + k] * A[(int64_t)j * n0 + k];
@@ -297,20 +301,25 @@ __global__ void k_mg_dense_setup(int Q, int n0, const double* __restrict__ a0q, 
     double s = 0.0;
     for (int k = max(i, j); k < n0; k++) s = fma(Li[(int64_t)k * n0 + i], Li[(int64_t)k * n0 + j], s);
     Ai[e] = s;
+    if (ai32) ai32[b * nn + e] = (float)s;
   }
   if (tid == 0) info[b] = bad;
 }
 
 }  // namespace
 
-void launch_mg_setup(const MGPlan& plan, const double* mu, int B, double* const* tables, double* dense_a,
-                     double* dense_l, double* ainv, int* info, cudaStream_t s) {
+void launch_mg_setup(const MGPlan& plan, const double* mu, int B, int fp32, void* const* tables, double* dense_a,
+                     double* dense_l, double* ainv64, float* ainv32, int* info, cudaStream_t s) {
   for (int i = 1; i < plan.J; i++) {
     const int ncls = plan.lv[i].ncls();
-    const int64_t total = (int64_t)B * ncls;
-    k_mg_tables<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(plan.Q, ncls, plan.d_tq[i], mu, B, tables[i]);
+    const unsigned blocks = (unsigned)(((int64_t)B * ncls + 127) / 128);
+    if (fp32)
+      k_mg_tables<float><<<blocks, 128, 0, s>>>(plan.Q, ncls, plan.d_tq[i], mu, B, (float*)tables[i]);
+    else
+      k_mg_tables<double><<<blocks, 128, 0, s>>>(plan.Q, ncls, plan.d_tq[i], mu, B, (double*)tables[i]);
   }
-  k_mg_dense_setup<<<B, 256, 0, s>>>(plan.Q, plan.n0, plan.d_a0q, mu, dense_a, dense_l, ainv, info);
+  k_mg_dense_setup<<<B, 256, 0, s>>>(plan.Q, plan.n0, plan.d_a0q, mu, dense_a, dense_l, ainv64,
+                                     fp32 ? ainv32 : nullptr, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,13 +327,17 @@ void launch_mg_setup(const MGPlan& plan, const double* mu, int B, double* const*
 // ---------------------------------------------------------------------------
 namespace {
 
-template <bool kSeven>
-__device__ __forceinline__ double mg_row_apply(const double* __restrict__ row, const double* __restrict__ x,
-                                               int i, int j, int k, int nx, int ny, int nz) {
+__device__ __forceinline__ bool mg_skip(const InstState* st, const int* mask, int b) {
+  return (st && st[b].status != ST_ACTIVE) || (mask && !mask[b]);
+}
+
+template <typename T, bool kSeven>
+__device__ __forceinline__ T mg_row_apply(const T* __restrict__ row, const T* __restrict__ x, int i, int j, int k,
+                                          int nx, int ny, int nz) {
   const int64_t sy = nx, sz = (int64_t)nx * ny;
   const int64_t c = ((int64_t)k * ny + j) * nx + i;
   if (kSeven) {  // -kW, -kE, -kS, -kN, -kD, -kU, D
-    double v = row[6] * x[c];
+    T v = row[6] * x[c];
     if (i > 0) v = fma(row[0], x[c - 1], v);
     if (i < nx - 1) v = fma(row[1], x[c + 1], v);
     if (j > 0) v = fma(row[2], x[c - sy], v);
@@ -333,7 +346,7 @@ __device__ __forceinline__ double mg_row_apply(const double* __restrict__ row, c
     if (k < nz - 1) v = fma(row[5], x[c + sz], v);
     return v;
   }
-  double v = 0.0;
+  T v = T(0);
 #pragma unroll
   for (int dz = -1; dz <= 1; dz++) {
     if (k + dz < 0 || k + dz >= nz) continue;
@@ -353,53 +366,55 @@ __device__ __forceinline__ double mg_row_apply(const double* __restrict__ row, c
 // mode 0: out = omega D^-1 rhs (smoothing from zero)
 // mode 1: out = x + omega D^-1 (rhs - A x)
 // mode 2: out = rhs - A x (residual)
-template <bool kSeven>
-__global__ void __launch_bounds__(256) k_mg_level(MGLevel L, const InstState* __restrict__ st, int mode,
-                                                  const double* __restrict__ rhs, const double* __restrict__ x,
-                                                  double* __restrict__ out, double omega) {
+template <typename T, bool kSeven>
+__global__ void __launch_bounds__(256) k_mg_level(MGLevel L, const InstState* __restrict__ st,
+                                                  const int* __restrict__ mask, int mode,
+                                                  const T* __restrict__ rhs, const T* __restrict__ x,
+                                                  T* __restrict__ out, T omega) {
   const int b = blockIdx.y;
-  if (st && st[b].status != ST_ACTIVE) return;
+  if (mg_skip(st, mask, b)) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= L.n) return;
   const int i = (int)(t % L.nx), j = (int)((t / L.nx) % L.ny), k = (int)(t / ((int64_t)L.nx * L.ny));
   const int cls = (L.cz[k] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
-  const double* row = L.coef + ((int64_t)b * L.ncx * L.ncy * L.ncz + cls) * L.stride;
+  const T* row = (const T*)L.coef + ((int64_t)b * L.ncx * L.ncy * L.ncz + cls) * L.stride;
   const int64_t off = (int64_t)b * L.n;
-  const double dinv = row[L.stride - 1];
-  const double bv = rhs[off + t];
+  const T dinv = row[L.stride - 1];
+  const T bv = rhs[off + t];
   if (mode == 0) {
     out[off + t] = omega * dinv * bv;
     return;
   }
-  const double ax = mg_row_apply<kSeven>(row, x + off, i, j, k, L.nx, L.ny, L.nz);
+  const T ax = mg_row_apply<T, kSeven>(row, x + off, i, j, k, L.nx, L.ny, L.nz);
   out[off + t] = mode == 1 ? fma(omega * dinv, bv - ax, x[off + t]) : bv - ax;
 }
 
 // rc = P^T rf (coarse node J gathers fine nodes 2J-1 .. 2J+1 per axis).
+template <typename T>
 __global__ void __launch_bounds__(256) k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
-                                                     const InstState* __restrict__ st,
-                                                     const double* __restrict__ rf, double* __restrict__ rc) {
+                                                     const InstState* __restrict__ st, const int* __restrict__ mask,
+                                                     const T* __restrict__ rf, T* __restrict__ rc) {
   const int b = blockIdx.y;
-  if (st && st[b].status != ST_ACTIVE) return;
+  if (mg_skip(st, mask, b)) return;
   const int64_t cn = (int64_t)cnx * cny * cnz;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cn) return;
   const int I = (int)(t % cnx), Jy = (int)((t / cnx) % cny), K = (int)(t / ((int64_t)cnx * cny));
   const int64_t fn = (int64_t)fnx * fny * fnz;
-  const double* r = rf + (int64_t)b * fn;
-  double v = 0.0;
+  const T* r = rf + (int64_t)b * fn;
+  T v = T(0);
   for (int dz = -1; dz <= 1; dz++) {
     const int z = 2 * K + 1 + dz;  // 0-based fine index of 1-based 2(K+1)+dz
     if (z < 0 || z >= fnz) continue;
-    const double wz = dz == 0 ? 1.0 : 0.5;
+    const T wz = dz == 0 ? T(1) : T(0.5);
     for (int dy = -1; dy <= 1; dy++) {
       const int y = 2 * Jy + 1 + dy;
       if (y < 0 || y >= fny) continue;
-      const double wy = dy == 0 ? wz : 0.5 * wz;
+      const T wy = dy == 0 ? wz : T(0.5) * wz;
       for (int dx = -1; dx <= 1; dx++) {
         const int x = 2 * I + 1 + dx;
         if (x < 0 || x >= fnx) continue;
-        v = fma(dx == 0 ? wy : 0.5 * wy, r[((int64_t)z * fny + y) * fnx + x], v);
+        v = fma(dx == 0 ? wy : T(0.5) * wy, r[((int64_t)z * fny + y) * fnx + x], v);
       }
     }
   }
@@ -408,49 +423,52 @@ __global__ void __launch_bounds__(256) k_mg_restrict(int fnx, int fny, int fnz, 
 
 // uf += P ec (fine node i takes coarse i/2 if i is even, else half of each
 // coarse neighbour (i-1)/2 and (i+1)/2 that exists; 1-based).
-__device__ __forceinline__ int pw(int i0, int m, int K[2], double w[2]) {
+__device__ __forceinline__ int pw(int i0, int m, int K[2], float w[2]) {
   const int i = i0 + 1;
   if (i % 2 == 0) {
     K[0] = i / 2 - 1;
-    w[0] = 1.0;
+    w[0] = 1.f;
     return 1;
   }
   int c = 0;
-  if ((i - 1) / 2 >= 1) K[c] = (i - 1) / 2 - 1, w[c++] = 0.5;
-  if ((i + 1) / 2 <= m) K[c] = (i + 1) / 2 - 1, w[c++] = 0.5;
+  if ((i - 1) / 2 >= 1) K[c] = (i - 1) / 2 - 1, w[c++] = 0.5f;
+  if ((i + 1) / 2 <= m) K[c] = (i + 1) / 2 - 1, w[c++] = 0.5f;
   return c;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) k_mg_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
                                                         const InstState* __restrict__ st,
-                                                        const double* __restrict__ ec, double* __restrict__ uf) {
+                                                        const int* __restrict__ mask, const T* __restrict__ ec,
+                                                        T* __restrict__ uf) {
   const int b = blockIdx.y;
-  if (st && st[b].status != ST_ACTIVE) return;
+  if (mg_skip(st, mask, b)) return;
   const int64_t fn = (int64_t)fnx * fny * fnz;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= fn) return;
   const int i = (int)(t % fnx), j = (int)((t / fnx) % fny), k = (int)(t / ((int64_t)fnx * fny));
   int Kx[2], Ky[2], Kz[2];
-  double wx[2], wy[2], wz[2];
+  float wx[2], wy[2], wz[2];  // 1 or 1/2: exact in either type
   const int nx_ = pw(i, cnx, Kx, wx), ny_ = pw(j, cny, Ky, wy), nz_ = pw(k, cnz, Kz, wz);
-  const double* e = ec + (int64_t)b * cnx * cny * cnz;
-  double v = 0.0;
+  const T* e = ec + (int64_t)b * cnx * cny * cnz;
+  T v = T(0);
   for (int c = 0; c < nz_; c++)
     for (int bq = 0; bq < ny_; bq++)
       for (int a = 0; a < nx_; a++)
-        v = fma(wx[a] * wy[bq] * wz[c], e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
+        v = fma((T)(wx[a] * wy[bq] * wz[c]), e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
   uf[(int64_t)b * fn + t] += v;
 }
 
 // x0 = A0^-1 b0 per instance (one CTA per instance).
-__global__ void k_mg_dense_apply(int n0, const double* __restrict__ ainv, const InstState* __restrict__ st,
-                                 const double* __restrict__ rhs, double* __restrict__ out) {
+template <typename T>
+__global__ void k_mg_dense_apply(int n0, const T* __restrict__ ainv, const InstState* __restrict__ st,
+                                 const int* __restrict__ mask, const T* __restrict__ rhs, T* __restrict__ out) {
   const int b = blockIdx.x;
-  if (st && st[b].status != ST_ACTIVE) return;
-  const double* Ai = ainv + (int64_t)b * n0 * n0;
-  const double* r = rhs + (int64_t)b * n0;
+  if (mg_skip(st, mask, b)) return;
+  const T* Ai = ainv + (int64_t)b * n0 * n0;
+  const T* r = rhs + (int64_t)b * n0;
   for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-    double v = 0.0;
+    T v = T(0);
     for (int j = 0; j < n0; j++) v = fma(Ai[(int64_t)i * n0 + j], r[j], v);
     out[(int64_t)b * n0 + i] = v;
   }
@@ -458,41 +476,47 @@ __global__ void k_mg_dense_apply(int n0, const double* __restrict__ ainv, const 
 
 inline dim3 level_grid(int64_t n, int B) { return dim3((unsigned)((n + 255) / 256), (unsigned)B); }
 
-int level_op(const MGBatch& m, int i, int mode, const double* rhs, const double* x, double* out, cudaStream_t s) {
+template <typename T>
+int level_op(const MGBatch& m, int i, int mode, const T* rhs, const T* x, T* out, cudaStream_t s) {
   const MGLevel& L = m.lv[i];
   if (L.stride == 8)
-    k_mg_level<true><<<level_grid(L.n, m.B), 256, 0, s>>>(L, m.st, mode, rhs, x, out, kMGOmega);
+    k_mg_level<T, true><<<level_grid(L.n, m.B), 256, 0, s>>>(L, m.st, m.mask, mode, rhs, x, out, (T)kMGOmega);
   else
-    k_mg_level<false><<<level_grid(L.n, m.B), 256, 0, s>>>(L, m.st, mode, rhs, x, out, kMGOmega);
+    k_mg_level<T, false><<<level_grid(L.n, m.B), 256, 0, s>>>(L, m.st, m.mask, mode, rhs, x, out, (T)kMGOmega);
   return 1;
 }
 
 // out = MG(rhs, A^i, i)
-int vcycle(const MGBatch& m, int i, const double* rhs, double* out, cudaStream_t s) {
+template <typename T>
+int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
   const MGPlan& P = *m.plan;
   if (i == 0) {
-    k_mg_dense_apply<<<m.B, 128, 0, s>>>(P.n0, m.ainv, m.st, rhs, out);
+    k_mg_dense_apply<T><<<m.B, 128, 0, s>>>(P.n0, (const T*)m.ainv, m.st, m.mask, rhs, out);
     return 1;
   }
   int launches = 0;
-  double* cur = m.w1[i];
-  double* nxt = m.w2[i];
-  launches += level_op(m, i, 0, rhs, nullptr, cur, s);  // pre-smoothing from zero
+  T* cur = (T*)m.w1[i];
+  T* nxt = (T*)m.w2[i];
+  launches += level_op<T>(m, i, 0, rhs, nullptr, cur, s);  // pre-smoothing from zero
   for (int k = 1; k < kMGNu; k++) {
-    launches += level_op(m, i, 1, rhs, cur, nxt, s);
+    launches += level_op<T>(m, i, 1, rhs, cur, nxt, s);
     std::swap(cur, nxt);
   }
-  launches += level_op(m, i, 2, rhs, cur, nxt, s);       // residual into the free buffer
+  launches += level_op<T>(m, i, 2, rhs, cur, nxt, s);       // residual into the free buffer
   const MGLevel& F = m.lv[i];
   const MGLevel& C = m.lv[i - 1];
-  k_mg_restrict<<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, nxt, m.rhs[i - 1]);
+  T* crhs = (T*)m.rhs[i - 1];
+  T* csol = (T*)m.sol[i - 1];
+  k_mg_restrict<T><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, nxt,
+                                                        crhs);
   launches += 1;
-  launches += vcycle(m, i - 1, m.rhs[i - 1], m.sol[i - 1], s);
-  k_mg_prolong_add<<<level_grid(F.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.sol[i - 1], cur);
+  launches += vcycle<T>(m, i - 1, crhs, csol, s);
+  k_mg_prolong_add<T><<<level_grid(F.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask,
+                                                           csol, cur);
   launches += 1;
-  for (int k = 1; k <= kMGNu; k++) {                      // post-smoothing
-    double* dst = k == kMGNu ? out : nxt;
-    launches += level_op(m, i, 1, rhs, cur, dst, s);
+  for (int k = 1; k <= kMGNu; k++) {                         // post-smoothing
+    T* dst = k == kMGNu ? out : nxt;
+    launches += level_op<T>(m, i, 1, rhs, cur, dst, s);
     if (k < kMGNu) std::swap(cur, nxt);
   }
   return launches;
@@ -500,15 +524,16 @@ int vcycle(const MGBatch& m, int i, const double* rhs, double* out, cudaStream_t
 
 }  // namespace
 
-int launch_mg_vcycle(const MGBatch& m, const double* rhs, double* out, cudaStream_t s) {
-  return vcycle(m, m.plan->J, rhs, out, s);
+int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, cudaStream_t s) {
+  if (m.fp32) return vcycle<float>(m, m.plan->J, (const float*)rhs, (float*)out, s);
+  return vcycle<double>(m, m.plan->J, (const double*)rhs, (double*)out, s);
 }
 
 void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s) {
   if (L.stride == 8)
-    k_mg_level<true><<<level_grid(L.n, B), 256, 0, s>>>(L, nullptr, 0, x, nullptr, y, 1.0);
+    k_mg_level<double, true><<<level_grid(L.n, B), 256, 0, s>>>(L, nullptr, nullptr, 0, x, nullptr, y, 1.0);
   else
-    k_mg_level<false><<<level_grid(L.n, B), 256, 0, s>>>(L, nullptr, 0, x, nullptr, y, 1.0);
+    k_mg_level<double, false><<<level_grid(L.n, B), 256, 0, s>>>(L, nullptr, nullptr, 0, x, nullptr, y, 1.0);
 }
 
 }  // namespace rbws

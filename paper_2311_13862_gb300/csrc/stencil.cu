@@ -660,10 +660,11 @@ __global__ void k_msrb_lift(CGArgs<double> a, int slot) {
 
 // Partials of rho = r.s after an external preconditioner (the MG V-cycle) has
 // written s; same tiling and slot layout as the update phase.
-__global__ void k_precond_rho(CGArgs<double> a, int slot) {
+template <typename T>
+__global__ void k_precond_rho(CGArgs<T> a, int slot, const int* mask) {
   __shared__ double red[64];
   const int b = blockIdx.z;
-  if (a.st[b].status != ST_ACTIVE) return;
+  if (a.st[b].status != ST_ACTIVE || (mask && !mask[b])) return;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
   const int64_t off = (int64_t)b * a.g.n;
@@ -673,7 +674,7 @@ __global__ void k_precond_rho(CGArgs<double> a, int slot) {
   if (cl.own)
     for (int z = tp.z0; z < tp.z1; ++z) {
       const int64_t idx = off + (int64_t)z * plane + cl.col;
-      rho = fma(a.r[idx], a.s[idx], rho);
+      rho = fma((double)a.r[idx], (double)a.s[idx], rho);
     }
   double dummy = 0.0;
   block_sum2(rho, dummy, red);
@@ -792,7 +793,8 @@ __global__ void k_ru_reset(CGArgs<float> a, int start) {
       rr = fmaf(rv, rv, rr);
     }
   }
-  double drho = (double)rho, drr = (double)rr;
+  // with MG, s and rho follow from a V-cycle after the reset
+  double drho = a.precond == RBWS_PREC_MG ? 0.0 : (double)rho, drr = (double)rr;
   block_sum2(drho, drr, red);
   if (tid == 0) {
     a.rho_rr[(int64_t)b * a.P + tp.part] = make_double2(drho, drr);
@@ -879,9 +881,12 @@ void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s) 
   k_ru_reset<<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, start);
 }
 
-void launch_precond_rho(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s) {
-  k_precond_rho<<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, slot);
+template <typename T>
+void launch_precond_rho(const CGArgs<T>& a, Tile t, int slot, const int* mask, cudaStream_t s) {
+  k_precond_rho<T><<<cg_grid(a), dim3(t.tx, t.ty), 0, s>>>(a, slot, mask);
 }
+template void launch_precond_rho<double>(const CGArgs<double>&, Tile, int, const int*, cudaStream_t);
+template void launch_precond_rho<float>(const CGArgs<float>&, Tile, int, const int*, cudaStream_t);
 
 void launch_msrb_apply(const CGArgs<double>& a, Tile t, int slot, cudaStream_t s) {
   k_msrb_residual<<<cg_grid(a), dim3(t.tx, t.ty), plane_smem(t, sizeof(double)), s>>>(a);

@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(256, 4) k_cg_b_v4(CGArgs<float> a, int parity)
   float* ub = a.u + off;
   float* rb = a.r + off;
   float* sb = a.s + off;
-  const bool jac = a.precond != RBWS_PREC_NONE;
+  const bool mg = a.precond == RBWS_PREC_MG;  // the V-cycle writes s and rho after this phase
+  const bool jac = a.precond != RBWS_PREC_NONE && !mg;
   const int64_t plane = (int64_t)g.nx * g.ny;
   const int64_t col = (int64_t)ps.j * g.nx + ps.i;
   float rho = 0.f, rr = 0.f;
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(256, 4) k_cg_b_v4(CGArgs<float> a, int parity)
       }
     }
   }
-  double drho = (double)rho, drr = (double)rr;
+  double drho = mg ? 0.0 : (double)rho, drr = (double)rr;
   block_sum2(drho, drr, red);
   if (tid == 0) a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + ps.part] = make_double2(drho, drr);
 }
@@ -482,6 +483,7 @@ __global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start)
   const Geo& g = a.g;
   const int64_t off = (int64_t)b * g.n;
   const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const bool mg = a.precond == RBWS_PREC_MG;  // s and rho follow from a V-cycle after the reset
   const bool jac = a.precond != RBWS_PREC_NONE;
   const int64_t plane = (int64_t)g.nx * g.ny;
   const int64_t col = (int64_t)ps.j * g.nx + ps.i;
@@ -505,19 +507,42 @@ __global__ void __launch_bounds__(256) k_ru_reset_v4(CGArgs<float> a, int start)
       float4 sv = rv;
       if (jac) sv = make_float4(dinv[0] * rv.x, dinv[1] * rv.y, dinv[2] * rv.z, dinv[3] * rv.w);
       st4(a.r + idx, rv);
-      st4(a.s + idx, sv);  // s = r without a preconditioner (the s-form schedule reads s)
+      if (!mg) st4(a.s + idx, sv);  // s = r without a preconditioner (the s-form schedule reads s)
       if (restart) st4(a.p0 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
       rho = fmaf(rv.x, sv.x, fmaf(rv.y, sv.y, fmaf(rv.z, sv.z, fmaf(rv.w, sv.w, rho))));
       rr = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, rr))));
     }
   }
-  double drho = (double)rho, drr = (double)rr;
+  double drho = mg ? 0.0 : (double)rho, drr = (double)rr;
   block_sum2(drho, drr, red);
   if (tid == 0) {
     a.rho_rr[(int64_t)b * a.P + ps.part] = make_double2(drho, drr);
     if (restart)
       a.rho_rr[((int64_t)a.B + b) * a.P + ps.part] = make_double2(ps.part == 0 ? 1.0 : 0.0, 0.0);
   }
+}
+
+// Partials of rho = r.s after the FP32 V-cycle wrote s, with the v4 tiling of
+// the update phase (slot `slot`); instances with mask[b] == 0 are skipped.
+__global__ void __launch_bounds__(256) k_precond_rho_v4(CGArgs<float> a, int slot, const int* mask) {
+  __shared__ double red[64];
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE || (mask && !mask[b])) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const int64_t off = (int64_t)b * a.g.n;
+  const int64_t plane = (int64_t)a.g.nx * a.g.ny;
+  const int64_t col = (int64_t)ps.j * a.g.nx + ps.i;
+  float rho = 0.f;
+  if (ps.own)
+    for (int z = ps.z0; z < ps.z1; ++z) {
+      const int64_t idx = off + z * plane + col;
+      const float4 rv = ld4(a.r + idx), sv = ld4(a.s + idx);
+      rho = fmaf(rv.x, sv.x, fmaf(rv.y, sv.y, fmaf(rv.z, sv.z, fmaf(rv.w, sv.w, rho))));
+    }
+  double drho = (double)rho, dummy = 0.0;
+  block_sum2(drho, dummy, red);
+  if (tid == 0) a.rho_rr[((int64_t)slot * a.B + b) * a.P + ps.part].x = drho;
 }
 
 __global__ void k_tune_prep(CGArgs<float> a) {
@@ -843,6 +868,10 @@ void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) 
 void launch_cg_b_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
   k_cg_b_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), 0, s>>>(a, parity);
 }
+void launch_precond_rho_v4(const CGArgs<float>& a, Tile t, int slot, const int* mask, cudaStream_t s) {
+  k_precond_rho_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), 0, s>>>(a, slot, mask);
+}
+
 void launch_ru_reset_v4(const CGArgs<float>& a, Tile t, int start, cudaStream_t s) {
   k_ru_reset_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), 0, s>>>(a, start);
 }

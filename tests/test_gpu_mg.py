@@ -99,9 +99,35 @@ def test_rb_warm_started_mgcg_matches_oracle():
     assert it.mean() < it0.mean()
 
 
-def test_mg_rejects_mixed_precision():
+@pytest.mark.parametrize("grid,blocks", [((40, 36, 32), (2, 2, 2)),   # 4-node FP32 kernels
+                                         ((33, 17, 20), (2, 2, 2)),   # nx % 4 != 0: one-node kernels
+                                         ((64, 48, 40), (2, 2, 1))])
+@pytest.mark.parametrize("warm", [rbws.WARM_ZERO, rbws.WARM_GALERKIN])
+def test_fp32_mgcg_with_reliable_updates_reaches_the_fp64_residual(grid, blocks, warm):
+    op = O.assemble(grid, blocks)
+    H = mg.Hierarchy(op)
+    mu = inputs.log_uniform(107, 4, op.Q, 0.01, 100.0)
+    with rbws.Problem(grid, blocks) as P:
+        if warm == rbws.WARM_GALERKIN:
+            rbws.rbws_offline_greedy(P.h, inputs.log_uniform(108, 16, op.Q, 0.01, 100.0), 6, 0.0, 1e-12)
+        u = torch.empty((len(mu), P.n), dtype=torch.float64, device="cuda")
+        rc, it, rel, st = rbws.rbws_solve_batch(
+            P.h, mu, 1e-10, warm, u, rbws.rbws_options_default(precond=rbws.PREC_MG, precision=rbws.FP32_IR))
+        u = u.cpu().numpy()
+    assert rc == 0 and np.all(st == 0)
+    for b in range(len(mu)):
+        true_rel = np.linalg.norm(np.ones(op.n) - op.matvec(mu[b], u[b])) / np.sqrt(op.n)
+        assert true_rel < 1e-10
+        assert rel[b] == pytest.approx(true_rel, rel=1e-6)
+        ref = mg.mgcg(op, mu[b], tol=1e-13, hier=H)
+        assert np.linalg.norm(u[b] - ref.u) <= 1e-7 * np.linalg.norm(ref.u)
+        # FP32 inner iterations track the FP64 MGCG count closely
+        assert it[b] <= 2 * mg.mgcg(op, mu[b], tol=1e-10, hier=H).iters + 4
+
+
+def test_msrb_rejects_mixed_precision():
     with rbws.Problem((16, 16, 16), (2, 1, 1)) as P:
         u = torch.empty((1, P.n), dtype=torch.float64, device="cuda")
         with pytest.raises(rbws.RbwsError, match="UNSUPPORTED"):
             rbws.rbws_solve_batch(P.h, np.array([[1.0, 2.0]]), 1e-10, rbws.WARM_ZERO, u,
-                                  rbws.rbws_options_default(precond=rbws.PREC_MG, precision=rbws.FP32_IR))
+                                  rbws.rbws_options_default(precond=rbws.PREC_MSRB, precision=rbws.FP32_IR))
