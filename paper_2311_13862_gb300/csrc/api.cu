@@ -311,7 +311,7 @@ int launch_iteration(const CGArgs<T>& a, Tile t, int parity, cudaStream_t s) {
       return 6;
     }
     if (a.precond == RBWS_PREC_MG) {
-      const int l = launch_mg_vcycle(*a.mg, a.r, a.s, s);
+      const int l = launch_mg_vcycle(*a.mg, a.r, a.s, -1, s);
       launch_precond_rho<double>(a, t, parity ^ 1, nullptr, s);
       return 3 + l;
     }
@@ -328,7 +328,7 @@ int launch_precond_start(const CGArgs<T>& a, Tile t, cudaStream_t s) {
       return 4;
     }
     if (a.precond == RBWS_PREC_MG) {
-      const int l = launch_mg_vcycle(*a.mg, a.r, a.s, s);
+      const int l = launch_mg_vcycle(*a.mg, a.r, a.s, -1, s);
       launch_precond_rho<double>(a, t, 0, nullptr, s);
       return 1 + l;
     }
@@ -406,7 +406,7 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
             per_iter = 6;
           }
           if (a.precond == RBWS_PREC_MG) {
-            per_iter = 3 + launch_mg_vcycle(*a.mg, a.r, a.s, s);
+            per_iter = 3 + launch_mg_vcycle(*a.mg, a.r, a.s, -1, s);
             launch_precond_rho<double>(a, t, 1, nullptr, s);
           }
         }
@@ -731,7 +731,9 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   // s = MG(r) and the partials of rho = r.s into `slot`, for the instances in
   // mgb.mask (all when null)
   auto mg_apply = [&](const CGArgs<float>& aa, int slot, cudaStream_t ss) {
-    int l = launch_mg_vcycle(mgb, aa.r, aa.s, ss);
+    const bool fused = mgb.fine_cg && mgb.plan->J > 0;  // the fused finest level writes rho itself
+    int l = launch_mg_vcycle(mgb, aa.r, aa.s, fused ? slot : -1, ss);
+    if (fused) return l;
     if (v4) launch_precond_rho_v4(aa, t, slot, mgb.mask, ss);
     else launch_precond_rho<float>(aa, t, slot, mgb.mask, ss);
     return l + 1;
@@ -778,7 +780,13 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.r64 = r64;
   a.rel64 = rel;
   upd_mask = upd;
-  if (mg) CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
+  if (mg) {
+    CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
+    if (v4) {
+      mgb.fine_cg = &a;
+      mgb.fine_tile = t;
+    }
+  }
   if (sched32) {
     a.alpha = (double*)p->buf("ir_alpha", sizeof(double) * 2 * (size_t)B, &err);
     if (err) return (rbws_status)err;
@@ -1398,7 +1406,7 @@ rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t 
   } else {
     MGBatch m;
     CKI(mg_batch(p, d_mu, B, c64, 0, nullptr, &m));
-    p->launches += launch_mg_vcycle(m, (const double*)x, (double*)y, p->cur);
+    p->launches += launch_mg_vcycle(m, (const double*)x, (double*)y, -1, p->cur);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->cur));

@@ -337,6 +337,10 @@ struct MGBatch {
   int fp32 = 0;
   const InstState* st = nullptr;  // instances whose status is not ACTIVE are skipped
   const int* mask = nullptr;      // and, if set, those with mask[b] == 0
+  // FP32 iteration with the v4 tiles: the finest level runs fused steps with
+  // the iteration's tiling and writes the rho partials itself
+  const CGArgs<float>* fine_cg = nullptr;
+  Tile fine_tile{0, 0};
   MGLevel lv[kMGMaxLevels];
   void* rhs[kMGMaxLevels] = {};
   void* sol[kMGMaxLevels] = {};
@@ -352,7 +356,23 @@ struct MGBatch {
 void launch_mg_setup(const MGPlan& plan, const double* mu, int B, int fp32, void* const* tables, double* dense_a,
                      double* dense_l, double* ainv64, float* ainv32, int* info, cudaStream_t s);
 // out = MG(rhs) on the finest level (Algorithm 2 at level J); returns launches.
-int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, cudaStream_t s);
+// With m.fine_cg set the partials of rho = rhs . out go to slot `slot` too.
+int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, int slot, cudaStream_t s);
+// Fine-level FP32 multigrid steps with the v4 tiles (stencil_v4.cu).
+struct MGFineArgs {
+  const float* rhs;  // [B][n] right-hand side of the level (the iteration's r)
+  const float* xin;  // staged input (stages 0, 2)
+  float* out;
+  const float* ec;   // coarse correction [B][cnx*cny*cnz] (stage 2)
+  int cnx, cny, cnz;
+  const int* mask;   // skip instances with mask[b] == 0 (may be null)
+  float omega;
+  int slot;          // partial slot of rho (output kind 2)
+};
+// stage 0: x = xin, 1: x = omega D^-1 rhs, 2: x = xin + P ec;  outk 0: Jacobi
+// step, 1: residual, 2: Jacobi step and rho partials.  Returns -1 for a
+// combination that is not built.
+int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s);
 // y = D^-1 x on the FP64 level view L (instances all active).
 void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s);
 

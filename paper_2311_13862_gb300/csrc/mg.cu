@@ -325,6 +325,12 @@ void launch_mg_setup(const MGPlan& plan, const double* mu, int B, int fp32, void
 // ---------------------------------------------------------------------------
 // Device: the V-cycle
 // ---------------------------------------------------------------------------
+// The finest level with fused FP32 steps (two pre- and two post-smoothing
+// steps): Y = S(0, r, 2) with the first step formed on the fly; R = r - A Y;
+// restriction; coarse cycle e; X = Y + P e + omega D^-1 (r - A (Y + P e));
+// out = X + omega D^-1 (r - A X) with the rho partials.
+int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, cudaStream_t s);
+
 namespace {
 
 __device__ __forceinline__ bool mg_skip(const InstState* st, const int* mask, int b) {
@@ -490,6 +496,9 @@ int level_op(const MGBatch& m, int i, int mode, const T* rhs, const T* x, T* out
 template <typename T>
 int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
   const MGPlan& P = *m.plan;
+  if constexpr (sizeof(T) == 4) {
+    if (i == P.J && i > 0 && m.fine_cg) return vcycle_fine_fused(m, rhs, out, -1, s);
+  }
   if (i == 0) {
     k_mg_dense_apply<T><<<m.B, 128, 0, s>>>(P.n0, (const T*)m.ainv, m.st, m.mask, rhs, out);
     return 1;
@@ -524,8 +533,39 @@ int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
 
 }  // namespace
 
-int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, cudaStream_t s) {
-  if (m.fp32) return vcycle<float>(m, m.plan->J, (const float*)rhs, (float*)out, s);
+int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, cudaStream_t s) {
+  static_assert(kMGNu == 2, "the fused finest level does two pre- and two post-smoothing steps");
+  const int J = m.plan->J;
+  const MGLevel& F = m.lv[J];
+  const MGLevel& C = m.lv[J - 1];
+  float* Y = (float*)m.w1[J];
+  float* W = (float*)m.w2[J];
+  float* crhs = (float*)m.rhs[J - 1];
+  float* csol = (float*)m.sol[J - 1];
+  MGFineArgs fa{rhs, nullptr, Y, nullptr, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot};
+  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 1, 0, fa, s);  // Y = two smoothing steps from zero
+  fa.xin = Y;
+  fa.out = W;
+  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 0, 1, fa, s);  // W = r - A Y
+  k_mg_restrict<float><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
+                                                            crhs);
+  int launches = 3 + vcycle<float>(m, J - 1, crhs, csol, s);
+  fa.xin = Y;
+  fa.ec = csol;
+  fa.out = W;
+  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 2, 0, fa, s);  // W = smoothing step from Y + P e
+  fa.xin = W;
+  fa.ec = nullptr;
+  fa.out = out;
+  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 0, slot >= 0 ? 2 : 0, fa, s);  // out = last step (+ rho)
+  return launches + 2;
+}
+
+int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, int slot, cudaStream_t s) {
+  if (m.fp32) {
+    if (m.fine_cg && m.plan->J > 0) return vcycle_fine_fused(m, (const float*)rhs, (float*)out, slot, s);
+    return vcycle<float>(m, m.plan->J, (const float*)rhs, (float*)out, s);
+  }
   return vcycle<double>(m, m.plan->J, (const double*)rhs, (double*)out, s);
 }
 

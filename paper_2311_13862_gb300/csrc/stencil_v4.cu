@@ -862,6 +862,173 @@ void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s
   k_cg_b32_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), v4_plane_smem(t), s>>>(a, parity);
 }
 
+// ---------------------------------------------------------------------------
+// Fine-level multigrid steps (Algorithm 2 on the finest grid) with the v4
+// tiles and the iteration's tiling, FP32.  The staged field x is
+//   kStage 0: xin;   kStage 1: omega D^-1 rhs (the first smoothing step from
+//   zero, formed where it is staged);   kStage 2: xin + P e (the coarse
+//   correction prolongated where it is staged; e has cnx x cny x cnz nodes);
+// and the output is
+//   kOut 0: out = x + omega D^-1 (rhs - A x)      (a damped Jacobi step)
+//   kOut 1: out = rhs - A x                        (the residual)
+//   kOut 2: as 0, plus the partials of rho = rhs . out into slot `slot` of
+//           the iteration's partials (out is the preconditioned residual s).
+// ---------------------------------------------------------------------------
+namespace {
+
+// (P e) at fine node (i, j, k) (0-based): per axis, an even 1-based index takes
+// coarse i/2, an odd one half of each existing coarse neighbour.
+__device__ __forceinline__ float prolong_at(const float* e, int cnx, int cny, int cnz, int i, int j, int k) {
+  int Kx[2], Ky[2], Kz[2];
+  float wx[2], wy[2], wz[2];
+  auto pw = [](int i0, int m, int* K, float* w) {
+    const int t = i0 + 1;
+    if (t % 2 == 0) {
+      K[0] = t / 2 - 1;
+      w[0] = 1.f;
+      return 1;
+    }
+    int c = 0;
+    if ((t - 1) / 2 >= 1) K[c] = (t - 1) / 2 - 1, w[c++] = 0.5f;
+    if ((t + 1) / 2 <= m) K[c] = (t + 1) / 2 - 1, w[c++] = 0.5f;
+    return c;
+  };
+  const int nx_ = pw(i, cnx, Kx, wx), ny_ = pw(j, cny, Ky, wy), nz_ = pw(k, cnz, Kz, wz);
+  float v = 0.f;
+  for (int c = 0; c < nz_; c++)
+    for (int bq = 0; bq < ny_; bq++)
+      for (int a = 0; a < nx_; a++)
+        v = fmaf(wx[a] * wy[bq] * wz[c], e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
+  return v;
+}
+
+}  // namespace
+
+template <int kStage, int kOut>
+__global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineArgs m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE || (m.mask && !m.mask[b])) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const Pos4 ps = pos4(a.g, a.tiles_x, a.zc);
+  const Geo& g = a.g;
+  const int64_t off = (int64_t)b * g.n;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const float* rhs = m.rhs + off;
+  const float* xin = kStage == 1 ? nullptr : m.xin + off;
+  const float* ec = kStage == 2 ? m.ec + (int64_t)b * m.cnx * m.cny * m.cnz : nullptr;
+  float* out = m.out + off;
+  const float omega = m.omega;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  Plane pl{TXN + 8, 0};
+  pl.PS = pl.PW * (TY + 2);
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  const Halo4 h = halo4(g, ps, pl, tid);
+  const int oslot = pl.at(4 * (int)threadIdx.x, (int)threadIdx.y);
+  const int gi = ps.x0 + h.hx, gj = ps.y0 + h.hy;
+
+  // raw loads of plane z (register prefetch): the array the staged field is
+  // formed from, for the own group and the halo element(s)
+  const float* src = kStage == 1 ? rhs : xin;
+  float4 v_own, v_h;
+  auto fetch = [&](int z) {
+    v_own = v_h = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (z < 0 || z >= g.nz) return;
+    if (ps.own) v_own = ld4(src + z * plane + col);
+    if (h.in) {
+      if (h.kind == 1) v_h = ld4(src + z * plane + h.col);
+      else v_h.x = src[z * plane + h.col];
+    }
+  };
+  // the staged value of one node at (i, j, z) from its raw value
+  auto staged = [&](float raw, int i, int j, int z) -> float {
+    if (kStage == 1) return omega * dinv_at(g, cb, g.cz[z], i, j) * raw;
+    if (kStage == 2) return raw + prolong_at(ec, m.cnx, m.cny, m.cnz, i, j, z);
+    return raw;
+  };
+  auto commit = [&](float* P, int z) -> float4 {
+    const bool zin = z >= 0 && z < g.nz;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (zin && ps.own)
+      v = make_float4(staged(v_own.x, ps.i, ps.j, z), staged(v_own.y, ps.i + 1, ps.j, z),
+                      staged(v_own.z, ps.i + 2, ps.j, z), staged(v_own.w, ps.i + 3, ps.j, z));
+    st4(P + oslot, v);
+    if (h.kind == 1) {
+      float4 hv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (zin && h.in)
+        hv = make_float4(staged(v_h.x, gi, gj, z), staged(v_h.y, gi + 1, gj, z), staged(v_h.z, gi + 2, gj, z),
+                         staged(v_h.w, gi + 3, gj, z));
+      st4(P + h.slot, hv);
+    } else if (h.kind == 2) {
+      P[h.slot] = (zin && h.in) ? staged(v_h.x, gi, gj, z) : 0.f;
+    }
+    return v;
+  };
+
+  float c[4][7];
+  float dinv[4] = {0.f, 0.f, 0.f, 0.f};
+  int zcls_cur = -1;
+  const int z0 = ps.z0, z1 = ps.z1;
+  float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (z0 > 0 && ps.own) {
+    const float4 raw = ld4(src + (z0 - 1) * plane + col);
+    xm = make_float4(staged(raw.x, ps.i, ps.j, z0 - 1), staged(raw.y, ps.i + 1, ps.j, z0 - 1),
+                     staged(raw.z, ps.i + 2, ps.j, z0 - 1), staged(raw.w, ps.i + 3, ps.j, z0 - 1));
+  }
+  fetch(z0);
+  float4 xc = commit(sm + (z0 % 3) * pl.PS, z0);
+  fetch(z0 + 1);
+  float rho = 0.f;
+  for (int z = z0; z < z1; ++z) {
+    const float4 xp = commit(sm + ((z + 1) % 3) * pl.PS, z + 1);  // plane z+1 (zeros past nz)
+    fetch(z + 2);                                                  // in flight during plane z
+    __syncthreads();
+    const float* P = sm + (z % 3) * pl.PS;
+    const int zcl = g.cz[z];
+    if (zcl != zcls_cur && ps.own) {
+      zcls_cur = zcl;
+      load_coef4(g, cb, zcl, ps.i, ps.j, c);
+#pragma unroll
+      for (int e = 0; e < 4; e++) dinv[e] = dinv_at(g, cb, zcl, ps.i + e, ps.j);
+    }
+    if (ps.own) {
+      float y[4];
+      stencil4(P, pl, oslot, c, xm, xc, xp, y);
+      const float4 bv = ld4(rhs + z * plane + col);
+      float4 o;
+      if (kOut == 1) {
+        o = make_float4(bv.x - y[0], bv.y - y[1], bv.z - y[2], bv.w - y[3]);
+      } else {
+        o = make_float4(fmaf(omega * dinv[0], bv.x - y[0], xc.x), fmaf(omega * dinv[1], bv.y - y[1], xc.y),
+                        fmaf(omega * dinv[2], bv.z - y[2], xc.z), fmaf(omega * dinv[3], bv.w - y[3], xc.w));
+        if (kOut == 2) rho = fmaf(bv.x, o.x, fmaf(bv.y, o.y, fmaf(bv.z, o.z, fmaf(bv.w, o.w, rho))));
+      }
+      st4(out + z * plane + col, o);
+    }
+    xm = xc;
+    xc = xp;
+  }
+  if (kOut == 2) {
+    double drho = (double)rho, dummy = 0.0;
+    block_sum2(drho, dummy, red);
+    if (tid == 0) a.rho_rr[((int64_t)m.slot * a.B + b) * a.P + ps.part].x = drho;
+  }
+}
+
+int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s) {
+  const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
+  const size_t smem = v4_plane_smem(t);
+  if (stage == 1 && outk == 0) k_mg_fine_v4<1, 0><<<grid, block, smem, s>>>(a, m);
+  else if (stage == 0 && outk == 1) k_mg_fine_v4<0, 1><<<grid, block, smem, s>>>(a, m);
+  else if (stage == 2 && outk == 0) k_mg_fine_v4<2, 0><<<grid, block, smem, s>>>(a, m);
+  else if (stage == 0 && outk == 2) k_mg_fine_v4<0, 2><<<grid, block, smem, s>>>(a, m);
+  else return -1;
+  return 0;
+}
+
 void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s) {
   k_cg_a_v4<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), v4_plane_smem(t), s>>>(a, parity);
 }
