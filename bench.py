@@ -25,6 +25,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import types
 
 import numpy as np
 
@@ -111,8 +112,29 @@ def traffic_per_dof(kernel_tag):
     return None
 
 
-def cpu_baseline(w, n_solves, threads, tol, n_train_sample, reference_steps=None):
-    """Times the CPU FP64 oracle (unchanged) on a bounded sample of the workload."""
+_MG_STATE = {}
+
+
+def _mg_worker_init(grid, blocks):
+    """Oracle operator and multigrid hierarchy, once per worker process."""
+    import oracle as O
+    from oracle import mg
+    op = O.assemble(grid, blocks)
+    _MG_STATE["op"], _MG_STATE["hier"] = op, mg.Hierarchy(op)
+
+
+def _mg_worker_solve(task):
+    """One oracle MGCG solve (Algorithm 1 with Algorithm 2 as preconditioner) from u0."""
+    from oracle import mg
+    mu, u0, tol = task
+    r = mg.mgcg(_MG_STATE["op"], mu, u0=u0, tol=tol, hier=_MG_STATE["hier"])
+    return r.iters, r.status
+
+
+def cpu_baseline(w, n_solves, threads, tol, n_train_sample, reference_steps=None, precond="jacobi"):
+    """Times the CPU FP64 oracle (unchanged) on a bounded sample of the workload: the Galerkin RB
+    start, then Jacobi-PCG (the oracle's C solver, OpenMP across instances) or MGCG (the oracle's
+    scipy multigrid, one spawned process per core)."""
     import oracle as O
     from paper_2311_13862_gb300 import inputs
     op = O.assemble(w.grid, w.blocks)
@@ -122,6 +144,27 @@ def cpu_baseline(w, n_solves, threads, tol, n_train_sample, reference_steps=None
     mus = inputs.test_mu(w)[:n_solves]
     res = []
     times = []
+    if precond == "mg":
+        import multiprocessing as mp
+        u0 = [basis.W.T @ O.rb_solve(basis.ANq, basis.fN, m) for m in mus]
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ.update({"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1"})
+        try:
+            with mp.get_context("spawn").Pool(threads, initializer=_mg_worker_init,
+                                              initargs=(w.grid, w.blocks)) as pool:
+                pool.map(_mg_worker_solve, [(mus[0], u0[0], 1e-2)] * threads)  # workers up and warm
+                for _ in range(reference_steps or 1):
+                    t0 = time.perf_counter()
+                    out = pool.map(_mg_worker_solve, [(m, u, tol) for m, u in zip(mus, u0)])
+                    times.append(time.perf_counter() - t0)
+                    res.append(types.SimpleNamespace(iters=np.array([o[0] for o in out])))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        return basis, res, times, t_off
     for _ in range(reference_steps or 1):
         t0 = time.perf_counter()
         r = O.solve_batch(op, mus, warm=O.WARM_GALERKIN, basis=basis, tol=tol, n_threads=threads)
@@ -141,7 +184,7 @@ def reference_arm(args):
     threads = O.default_threads()
     n_solves = max(threads, 16)
     basis, res, times, t_off = cpu_baseline(w, n_solves, threads, w.tol, 32,
-                                            reference_steps=args.warmup + args.steps)
+                                            reference_steps=args.warmup + args.steps, precond=args.precond)
     timed = times[args.warmup:]
     total = sum(timed)
     value = n_solves * len(timed) / total
@@ -150,10 +193,11 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "batch": n_solves, "warm": "galerkin",
-                                            "precision": "fp64", "sample": True},
+                                            "precision": "fp64", "precond": args.precond, "sample": True},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": "%d of the 256 test mu per step, Galerkin warm start from an oracle "
-                                       "greedy over the first 32 training mu (N=%d)" % (n_solves, basis.N)},
+                                       "greedy over the first 32 training mu (N=%d), then %s to 1e-10" %
+                                       (n_solves, basis.N, "MGCG" if args.precond == "mg" else "Jacobi-PCG")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "iters_mean": float(its.mean()), "t_off_s": t_off}
     print(json.dumps(line), flush=True)
@@ -233,6 +277,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32ir", choices=["fp32ir", "fp64"])
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="FP32_IR reliable-update factor (0: the library default)")
+    ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
+                    help="preconditioner of the headline arm: multigrid V-cycle (MGCG) or Jacobi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arm-steps", type=int, default=2, help="timed steps of each side arm (0: skip arms)")
     ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
@@ -304,6 +352,8 @@ def main():
     def run(warm, precision, steps, warmup, profile=False, precond=rbws.PREC_JACOBI):
         prof = rbws.rbws_profile()
         o = rbws.rbws_options_default(precision=precision, stream=stream.cuda_stream, precond=precond)
+        if args.inner_tol > 0:
+            o.inner_tol = args.inner_tol
         out = None
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -313,7 +363,9 @@ def main():
                 o.profile = ctypes.pointer(prof)
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            acc = {"launches": 0, "samples": 0, "stencil_ms": 0.0, "update_ms": 0.0, "active_dofs": 0.0}
+            acc = {"launches": 0, "samples": 0, "stencil_ms": 0.0, "update_ms": 0.0, "active_dofs": 0.0,
+                   "precond_ms": 0.0}
+            acc_fine = [0.0] * 4
             acc_schedule = None
             torch.cuda.nvtx.range_push("timed")
             e0.record(stream)
@@ -322,6 +374,8 @@ def main():
                 if profile:
                     for k in acc:
                         acc[k] += getattr(prof, k)
+                    for k in range(4):
+                        acc_fine[k] += prof.mg_fine_ms[k]
                     acc_schedule = prof.schedule
             e1.record(stream)
             torch.cuda.nvtx.range_pop()
@@ -334,19 +388,25 @@ def main():
         rc, it, rel, st = out
         acc["elem_bytes"] = prof.elem_bytes
         acc["schedule"] = acc_schedule
+        acc["mg_fine_ms"] = acc_fine
         return ms, it, rel, st, acc
 
     headline = prec[args.precision]
+    head_pc = rbws.PREC_MG if args.precond == "mg" else rbws.PREC_JACOBI
+    head_name = ("mgcg_galerkin_" if args.precond == "mg" else "galerkin_") + args.precision
     # ---- timed region of the headline arm, clocks sampled meanwhile ----
     with ClockSampler(local) as clk:
-        ms, it, rel, st, acc = run(rbws.WARM_GALERKIN, headline, args.steps, args.warmup, profile=True)
+        ms, it, rel, st, acc = run(rbws.WARM_GALERKIN, headline, args.steps, args.warmup, profile=True,
+                                   precond=head_pc)
     clocks = clk.summary()
     value = B * world / (ms / 1e3)
 
     # ---- end to end: host parameters in, solution and counts back to pinned host memory ----
     u_host = torch.empty((B, P.n), dtype=torch.float64, pin_memory=True)
     mu_pinned = torch.from_numpy(mus.copy()).pin_memory()
-    o = rbws.rbws_options_default(precision=headline, stream=stream.cuda_stream)
+    o = rbws.rbws_options_default(precision=headline, stream=stream.cuda_stream, precond=head_pc)
+    if args.inner_tol > 0:
+        o.inner_tol = args.inner_tol
     e2e_steps = max(2, args.steps // 2)
     with torch.cuda.stream(stream):
         barrier()
@@ -395,7 +455,7 @@ def main():
     precond_of.update({k: rbws.PREC_MG for k in ("mgcg_zero_fp64", "mgcg_galerkin_fp64", "mgcg_zero_fp32ir",
                                                 "mgcg_galerkin_fp32ir")})
     for name, warm, pr in arm_list:
-        if name.startswith("galerkin_" + args.precision):
+        if name == head_name:
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
         else:
             a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1,
@@ -424,6 +484,10 @@ def main():
     }
     if f32:
         (st_name, alg_stencil, st_tag), (up_name, alg_update, up_tag) = kernels[sched if sched in kernels else -1]
+        if args.precond == "mg" and sched in (0, 2):
+            # with the V-cycle as preconditioner the update phase stores no s
+            up_name, alg_update, up_tag = ("k_cg_b_v4 (u += alpha p, r -= alpha q, r.r; s from the V-cycle)", 24,
+                                           "cg_update_phase_f32_v4_mg_64cube")
     else:
         st_name, alg_stencil, st_tag = "k_cg_a<double> (FP64 stencil phase)", 32, None
         up_name, alg_update, up_tag = "k_cg_b<double> (FP64 update phase)", 56, None
@@ -458,14 +522,38 @@ def main():
                    "stencil_phase_gflops": round(st_gf, 1), "update_phase_gflops": round(up_gf, 1),
                    "hbm_stencil_phase": stencil, "hbm_update_phase": update, "sampled_launches": acc["samples"]}
             dom = None
+    fine = []
+    if acc["samples"] > 0 and dom is not None and args.precond == "mg" and sum(acc["mg_fine_ms"]) > 0:
+        # the four fused finest-level steps of each V-cycle: algorithmic bytes per DoF (FP32):
+        # read r, write Y (8); read Y, r, write R (12); read Y, r, write X, plus the coarse
+        # correction at 1/8 of the nodes (12.5); read X, r, write s (12)
+        fine_kernels = [("k_mg_fine_v4<1,0> (two damped Jacobi steps from zero)", 8.0, "mg_fine_smooth_pre_f32_64cube"),
+                        ("k_mg_fine_v4<0,1> (residual r - A Y)", 12.0, "mg_fine_residual_f32_64cube"),
+                        ("k_mg_fine_v4<2,0> (prolongation + damped Jacobi step)", 12.5,
+                         "mg_fine_prolong_smooth_f32_64cube"),
+                        ("k_mg_fine_v4<0,2> (damped Jacobi step + rho partials)", 12.0,
+                         "mg_fine_smooth_rho_f32_64cube")]
+        for (name, alg, tag), t_ms in zip(fine_kernels, acc["mg_fine_ms"]):
+            gbs = acc["active_dofs"] * alg / (t_ms * 1e-3) / 1e9
+            tr = traffic_per_dof(tag)
+            fine.append({"kernel": name, "achieved": round(gbs, 1), "frac": round(gbs / peak, 4),
+                         "algorithmic_bytes_per_dof": alg, "ms_per_launch": t_ms / acc["samples"],
+                         "traffic": None if tr is None else tr * launch_dofs, "ms_total": t_ms})
+        phases = [dict(stencil, ms_total=acc["stencil_ms"]), dict(update, ms_total=acc["update_ms"])] + fine
+        dom = max(phases, key=lambda k: k["ms_total"])
     if acc["samples"] > 0 and dom is not None:
+        total_ms = acc["update_ms"] + acc["stencil_ms"] + acc["precond_ms"]
         res = {"bound": "hbm", "achieved": dom["achieved"], "peak": peak, "unit": "GB/s", "frac": dom["frac"],
                "traffic": dom["traffic"], "kernel": dom["kernel"], "peak_kind": peak_kind, "schedule": sched,
                "algorithmic_bytes_per_dof": dom["algorithmic_bytes_per_dof"],
-               "dominant_share": round(max(acc["update_ms"], acc["stencil_ms"]) /
-                                       (acc["update_ms"] + acc["stencil_ms"]), 3),
+               "dominant_share": round(dom.get("ms_total", max(acc["update_ms"], acc["stencil_ms"])) / total_ms, 3),
                "stencil_phase": stencil, "update_phase": update,
                "solver_frac_minimal_bytes": round(solver_gbs / peak, 4), "sampled_launches": acc["samples"]}
+        if fine:
+            res["mg_fine_steps"] = [{k: v for k, v in f.items() if k != "ms_total"} for f in fine]
+            res["vcycle_ms_per_iteration"] = acc["precond_ms"] / acc["samples"]
+            res.pop("solver_frac_minimal_bytes")
+            res["dominant_share_of"] = "the sampled iterations: phase A + phase B + V-cycle"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -473,7 +561,7 @@ def main():
             "dtype": "f32 inner / f64 outer" if headline == rbws.FP32_IR else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch_per_gpu": B, "N": int(N), "warm": "galerkin",
-                       "precision": args.precision, "precond": "jacobi", "tol": w.tol,
+                       "precision": args.precision, "precond": args.precond, "tol": w.tol,
                        "l2": "no flush: solver working set ~1.3 GB > 129 MB L2",
                        "parallelism": "independent batches per GPU (no collective)"},
             "roofline": res, "gpu_launches": int(acc["launches"]), "clocks": clocks,
@@ -503,12 +591,14 @@ def main():
         import oracle as O
         threads = O.default_threads()
         n_solves = max(threads, 16)
-        basis, r, times, cpu_off = cpu_baseline(w, n_solves, threads, w.tol, 32)
-        line["cpu_baseline"] = {"value": n_solves / times[0], "unit": UNIT, "cores": r[0].threads,
-                                "kind": "oracle",
+        basis, r, times, cpu_off = cpu_baseline(w, n_solves, threads, w.tol, 32, precond=args.precond)
+        line["cpu_baseline"] = {"value": n_solves / times[0], "unit": UNIT,
+                                "cores": getattr(r[0], "threads", threads), "kind": "oracle",
                                 "sample": "%d of the 256 test mu, Galerkin warm start from an oracle greedy "
-                                          "over the first 32 training mu (N=%d), Jacobi-PCG FP64 to 1e-10; "
-                                          "greedy took %.1f s (not in the rate)" % (n_solves, basis.N, cpu_off),
+                                          "over the first 32 training mu (N=%d), %s FP64 to 1e-10; "
+                                          "greedy took %.1f s (not in the rate)" %
+                                          (n_solves, basis.N, "MGCG" if args.precond == "mg" else "Jacobi-PCG",
+                                           cpu_off),
                                 "iters_mean": float(r[0].iters.mean())}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -106,6 +106,11 @@ typedef struct {
   int32_t elem_bytes;  /* 8: FP64 CG kernels were sampled; 4: FP32 inner kernels     */
   int32_t schedule;    /* FP32 kernels: -1 one node per thread, else the autotuner's
                           schedule (0..3, see rbws_autotune); -1 for FP64            */
+  double precond_ms;   /* FP32_IR with RBWS_PREC_MG: summed durations of the V-cycles
+                          of the sampled iterations (after the update phase)         */
+  double mg_fine_ms[4]; /* ... and of their four fused finest-level steps: two
+                          smoothing steps from zero, residual, prolongation + one
+                          smoothing step, last smoothing step + rho partials        */
 } rbws_profile;
 
 typedef struct {
@@ -115,7 +120,8 @@ typedef struct {
   int32_t max_restarts; /* true-residual restarts of Algorithm 4 (default 3)     */
   double inner_tol;     /* FP32_IR: an FP64 refinement step (reliable update) is
                            taken each time an instance's FP32 residual has
-                           fallen by this factor since its last one (1e-2)      */
+                           fallen by this factor since its last one (0 = auto:
+                           1e-2, or 1e-3 with RBWS_PREC_MG)                      */
   int32_t max_outer;    /* reserved (10)                                         */
   int32_t check_every;  /* iterations between host convergence polls and, in
                            FP32_IR, reliable-update tests (0 = auto: 8, or 2

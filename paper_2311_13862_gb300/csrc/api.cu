@@ -154,12 +154,14 @@ struct rbws_problem_s {
   cudaStream_t stream = nullptr;  // internal stream (used when the caller passes none)
   cudaStream_t cur = nullptr;     // work stream of the current call
   cudaEvent_t ev = nullptr;
-  cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};  // profiling events
+  cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // profiling events
+  cudaEvent_t mgev[8] = {};                                  // ... of the fused MG steps
   int64_t launches = 0;           // kernels launched by the current call
   int* h_active = nullptr;   // pinned
   // reduced basis
   int N = 0;
   double* d_W = nullptr;    // [N][n]
+  float* d_W32 = nullptr;   // FP32 copy of W for the mixed-precision start (built on first use)
   double* d_ANq = nullptr;  // [Q][N][N]
   double* d_fN = nullptr;   // [N]
   std::vector<double> h_ANq, h_fN;  // packed [Q][N][N], [N]
@@ -512,7 +514,23 @@ rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const do
 }
 
 // Galerkin warm start u[b] = W A_N(mu_b)^{-1} fN.
-rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u) {
+// u = W c; fp32: with the FP32 copy of W (the mixed-precision solver's start).
+rbws_status lift(rbws_problem p, const double* C, int B, double* u, bool fp32) {
+  if (fp32) {
+    if (!p->d_W32) {
+      CK(cudaMalloc(&p->d_W32, sizeof(float) * (size_t)p->N * p->n));
+      launch_to_f32((int64_t)p->N * p->n, p->d_W, p->d_W32, p->cur);
+      p->launches += 1;
+    }
+    launch_lift32(p->n, p->N, p->d_W32, C, B, u, p->cur);
+  } else {
+    launch_lift(p->n, p->N, p->d_W, C, B, u, p->cur);
+  }
+  p->launches += 1;
+  return RBWS_OK;
+}
+
+rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u, bool fp32 = false) {
   if (p->N <= 0) {
     set_error("no reduced basis: run rbws_offline_greedy or rbws_set_basis first");
     return RBWS_ERR_NO_BASIS;
@@ -522,8 +540,8 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u)
   int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
   launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, nullptr, p->cur);
-  launch_lift(p->n, p->N, p->d_W, C, B, u, p->cur);
-  p->launches += 2;
+  p->launches += 1;
+  CKI(lift(p, C, B, u, fp32));
   CK(cudaGetLastError());
   std::vector<int> h(B);
   CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
@@ -738,11 +756,14 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     else launch_precond_rho<float>(aa, t, slot, mgb.mask, ss);
     return l + 1;
   };
-  auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
+  auto phase_b_core = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
     if (sched == 1) launch_cg_b32_v4(aa, t, par, ss);
     else if (sched == 3) launch_cg_b_s_tma(aa, t, par, tma_err, ss);
     else if (v4) launch_cg_b_v4(aa, t, par, ss);
     else launch_cg_b<float>(aa, t, par, ss);
+  };
+  auto phase_b = [&](const CGArgs<float>& aa, int par, cudaStream_t ss) {
+    phase_b_core(aa, par, ss);
     if (mg) mg_launches = mg_apply(aa, par ^ 1, ss);
   };
   int* upd_mask = nullptr;  // set below: instances taking a reliable update
@@ -771,7 +792,10 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.max_iters = o.max_iters;
   a.precond = o.precond;
   a.ru = 1;
-  const double delta = (o.inner_tol > 0.0 && o.inner_tol < 1.0) ? o.inner_tol : 1e-2;
+  // auto: 1e-2 with Jacobi; with MG, whose iterations gain about a decade each,
+  // 1e-3 (fewer FP64 updates; blocks of 2 iterations keep the FP32 recursion
+  // within a few decades of its last update)
+  const double delta = (o.inner_tol > 0.0 && o.inner_tol < 1.0) ? o.inner_tol : (mg ? 1e-3 : 1e-2);
   a.ru_delta2 = delta * delta;
   a.rr_ref = rr_ref;
   a.pending = a.active + 1;
@@ -861,23 +885,39 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       cudaEventRecord(p->tev[0], s);
       phase_a(a, 0, s);
       cudaEventRecord(p->tev[1], s);
-      phase_b(a, 0, s);
+      phase_b_core(a, 0, s);
       cudaEventRecord(p->tev[2], s);
+      if (mg) {
+        if (mgb.fine_cg && mgb.plan->J > 0) mgb.ev = p->mgev;
+        mg_launches = mg_apply(a, 1, s);
+        mgb.ev = nullptr;
+      }
+      cudaEventRecord(p->tev[3], s);
       for (int k = 1; k < M; k++) {
         phase_a(a, k & 1, s);
         phase_b(a, k & 1, s);
       }
       cudaMemsetAsync(a.pending, 0, sizeof(int), s);
       launch_ru_decide(a, s);
-      if ((ce = cudaEventSynchronize(p->tev[2])) != cudaSuccess) {
+      if ((ce = cudaEventSynchronize(p->tev[3])) != cudaSuccess) {
         rc = (rbws_status)cuda_fail(ce, "profile events");
         break;
       }
-      float ta = 0.f, tb = 0.f;
+      float ta = 0.f, tb = 0.f, tp = 0.f;
       cudaEventElapsedTime(&ta, p->tev[0], p->tev[1]);
       cudaEventElapsedTime(&tb, p->tev[1], p->tev[2]);
+      cudaEventElapsedTime(&tp, p->tev[2], p->tev[3]);
       prof->stencil_ms += ta;
       prof->update_ms += tb;
+      if (mg) {
+        prof->precond_ms += tp;
+        if (mgb.fine_cg && mgb.plan->J > 0)
+          for (int k = 0; k < 4; k++) {
+            float tk = 0.f;
+            cudaEventElapsedTime(&tk, p->mgev[2 * k], p->mgev[2 * k + 1]);
+            prof->mg_fine_ms[k] += tk;
+          }
+      }
       prof->active_dofs += (double)active * (double)p->n;
       prof->samples += 1;
     }
@@ -1067,13 +1107,12 @@ rbws_status net_predict(rbws_problem p, const double* d_mu, int B, double* c, bo
   return RBWS_OK;
 }
 
-rbws_status learned_start(rbws_problem p, const double* d_mu, int B, double* u, bool corrected) {
+rbws_status learned_start(rbws_problem p, const double* d_mu, int B, double* u, bool corrected, bool fp32) {
   int err = 0;
   double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * (p->N > 0 ? p->N : 1), &err);
   if (err) return (rbws_status)err;
   CKI(net_predict(p, d_mu, B, C, corrected));
-  launch_lift(p->n, p->N, p->d_W, C, B, u, p->cur);
-  p->launches += 1;
+  CKI(lift(p, C, B, u, fp32));
   CK(cudaGetLastError());
   return RBWS_OK;
 }
@@ -1136,9 +1175,9 @@ rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol
   if (warm == RBWS_WARM_ZERO) {
     CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->cur));
   } else if (warm == RBWS_WARM_GALERKIN) {
-    CKI(galerkin_start(p, d_mu, B, u));
+    CKI(galerkin_start(p, d_mu, B, u, o.precision == RBWS_FP32_IR));
   } else {
-    CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED));
+    CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED, o.precision == RBWS_FP32_IR));
   }
   if (o.precision == RBWS_FP64) {
     CKI(solve_fp64(p, d_mu, B, tol, o, u, st));
@@ -1166,7 +1205,7 @@ void rbws_options_default(rbws_options* o) {
   o->precond = RBWS_PREC_JACOBI;
   o->precision = RBWS_FP64;
   o->max_restarts = 3;
-  o->inner_tol = 1e-2;
+  o->inner_tol = 0.0;
   o->max_outer = 10;
   o->check_every = 0;
   o->stream = nullptr;
@@ -1313,6 +1352,8 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(e, "set-up");
   for (auto& te : p->tev)
     if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
+  for (auto& te : p->mgev)
+    if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
   p->cur = p->stream;
   if (!(p->fnorm > 0.0)) {
     set_error("rbws_problem_create: f must be nonzero");
@@ -1336,6 +1377,7 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_f);
   cudaFree(p->d_ones);
   cudaFree(p->d_W);
+  cudaFree(p->d_W32);
   cudaFree(p->d_ANq);
   cudaFree(p->d_fN);
   cudaFree(p->d_w32);
@@ -1344,6 +1386,8 @@ void rbws_problem_destroy(rbws_problem p) {
   if (p->h_active) cudaFreeHost(p->h_active);
   if (p->ev) cudaEventDestroy(p->ev);
   for (auto& e : p->tev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : p->mgev)
     if (e) cudaEventDestroy(e);
   if (p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -1438,9 +1482,11 @@ rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const dou
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   cudaFree(p->d_W);
+  cudaFree(p->d_W32);
   cudaFree(p->d_ANq);
   cudaFree(p->d_fN);
   p->d_W = p->d_ANq = p->d_fN = nullptr;
+  p->d_W32 = nullptr;
   p->N = 0;
   CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)N * p->n));
   CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)p->Q * N * N));
@@ -1518,9 +1564,11 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   // Drop any previous basis; the new one is built in place.
   cudaStreamSynchronize(s);
   cudaFree(p->d_W);
+  cudaFree(p->d_W32);
   cudaFree(p->d_ANq);
   cudaFree(p->d_fN);
   p->d_W = p->d_ANq = p->d_fN = nullptr;
+  p->d_W32 = nullptr;
   p->N = 0;
   CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)n_max * n));
   CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)Q * n_max * n_max));

@@ -214,6 +214,10 @@ void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, con
 // +inf where info[b] != 0.
 void launch_l1_indicator(int N, int Nmax, const double* R, const double* c, const int* info, int B,
                          double* eta, cudaStream_t s);
+// u = W c with an FP32 copy of W and FP32 accumulation (u written in FP64).
+void launch_lift32(int64_t n, int N, const float* W, const double* c, int B, double* u, cudaStream_t s);
+// y = (float) x.
+void launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
 // u[b] = sum_j c[b][j] W[j]  (W: [N][n]).
 void launch_lift(int64_t n, int N, const double* W, const double* c, int B, double* u,
                  cudaStream_t s);
@@ -341,6 +345,7 @@ struct MGBatch {
   // the iteration's tiling and writes the rho partials itself
   const CGArgs<float>* fine_cg = nullptr;
   Tile fine_tile{0, 0};
+  cudaEvent_t* ev = nullptr;  // if set: 8 events bracketing the four fused finest-level steps
   MGLevel lv[kMGMaxLevels];
   void* rhs[kMGMaxLevels] = {};
   void* sol[kMGMaxLevels] = {};

@@ -480,6 +480,119 @@ __global__ void k_mg_dense_apply(int n0, const T* __restrict__ ainv, const InstS
   }
 }
 
+// Coarse-level fused steps (27-point Galerkin rows): one thread per (x, y)
+// column marching through a chunk of z planes; planes are staged with their
+// x/y halo in a 4-slot shared-memory ring.  The staged field is xin (kStage
+// 0), omega D^-1 rhs (1) or xin + P e (2); the output a damped Jacobi step
+// (kOut 0) or the residual rhs - A x (kOut 1) -- as on the finest level.
+template <typename T>
+__device__ __forceinline__ T prolong_node(const T* __restrict__ e, int cnx, int cny, int cnz, int i, int j, int k) {
+  int Kx[2], Ky[2], Kz[2];
+  float wx[2], wy[2], wz[2];
+  const int nx_ = pw(i, cnx, Kx, wx), ny_ = pw(j, cny, Ky, wy), nz_ = pw(k, cnz, Kz, wz);
+  T v = T(0);
+#pragma unroll
+  for (int c = 0; c < 2; c++) {
+    if (c >= nz_) break;
+#pragma unroll
+    for (int bq = 0; bq < 2; bq++) {
+      if (bq >= ny_) break;
+#pragma unroll
+      for (int a = 0; a < 2; a++) {
+        if (a >= nx_) break;
+        v = fma((T)(wx[a] * wy[bq] * wz[c]), e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
+      }
+    }
+  }
+  return v;
+}
+
+template <typename T, int kStage, int kOut>
+__global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* __restrict__ st,
+                                                   const int* __restrict__ mask, const T* __restrict__ rhs,
+                                                   const T* __restrict__ xin, T* __restrict__ out,
+                                                   const T* __restrict__ ec, int cnx, int cny, int cnz, T omega,
+                                                   int tiles_x, int zc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.z;
+  if (mg_skip(st, mask, b)) return;
+  const int TX = blockDim.x, TY = blockDim.y;
+  const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+  const int z0 = blockIdx.y * zc, z1 = min(L.nz, z0 + zc);
+  const int PW = TX + 2, PS = PW * (TY + 2);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int64_t plane = (int64_t)L.nx * L.ny, off = (int64_t)b * L.n;
+  const int ncls = L.ncx * L.ncy * L.ncz;
+  const T* tab = (const T*)L.coef + (int64_t)b * ncls * 28;
+  const T* rb = rhs + off;
+  const T* xb = kStage == 1 ? nullptr : xin + off;
+  const T* eb = kStage == 2 ? ec + (int64_t)b * cnx * cny * cnz : nullptr;
+  // staged value of node (i, j, z) inside the grid
+  auto staged = [&](int i, int j, int z) -> T {
+    const int64_t idx = (int64_t)z * plane + (int64_t)j * L.nx + i;
+    if (kStage == 1) {
+      const int cls = (L.cz[z] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
+      return omega * tab[(int64_t)cls * 28 + 27] * rb[idx];
+    }
+    if (kStage == 2) return xb[idx] + prolong_node<T>(eb, cnx, cny, cnz, i, j, z);
+    return xb[idx];
+  };
+  // stage plane z (zeros outside the grid) into slot z & 3: (TX+2) x (TY+2) with halo
+  auto stage = [&](int z) {
+    T* Pl = sm + (z & 3) * PS;
+    for (int t = tid; t < PS; t += TX * TY) {
+      const int hx = t % PW - 1, hy = t / PW - 1;
+      const int i = x0 + hx, j = y0 + hy;
+      T v = T(0);
+      if (z >= 0 && z < L.nz && i >= 0 && i < L.nx && j >= 0 && j < L.ny) v = staged(i, j, z);
+      Pl[t] = v;
+    }
+  };
+  const int i = x0 + (int)threadIdx.x, j = y0 + (int)threadIdx.y;
+  const bool own = i < L.nx && j < L.ny;
+  const int oslot = ((int)threadIdx.y + 1) * PW + (int)threadIdx.x + 1;
+  T c[27];
+  T dinv = T(0);
+  int zcls_cur = -1;
+  stage(z0 - 1);
+  stage(z0);
+  for (int z = z0; z < z1; ++z) {
+    stage(z + 1);
+    __syncthreads();
+    if (own) {
+      const int zcl = L.cz[z];
+      if (zcl != zcls_cur) {
+        zcls_cur = zcl;
+        const T* row = tab + (int64_t)((zcl * L.ncy + L.cy[j]) * L.ncx + L.cx[i]) * 28;
+#pragma unroll
+        for (int k = 0; k < 27; k++) c[k] = row[k];
+        dinv = row[27];
+      }
+      T ax = T(0);
+#pragma unroll
+      for (int dz = -1; dz <= 1; dz++) {
+        const T* Pl = sm + ((z + dz) & 3) * PS;
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+          for (int dx = -1; dx <= 1; dx++)
+            ax = fma(c[(dz + 1) * 9 + (dy + 1) * 3 + dx + 1], Pl[oslot + dy * PW + dx], ax);
+      }
+      const int64_t idx = off + (int64_t)z * plane + (int64_t)j * L.nx + i;
+      const T bv = rhs[idx];
+      if (kOut == 1) {
+        out[idx] = bv - ax;
+      } else {
+        const T xc = sm[(z & 3) * PS + oslot];
+        out[idx] = fma(omega * dinv, bv - ax, xc);
+      }
+    }
+    // no second barrier: the next iteration restages slot (z + 2) & 3, which
+    // held plane z - 2; every thread finished with it before this iteration's barrier
+  }
+}
+
 inline dim3 level_grid(int64_t n, int B) { return dim3((unsigned)((n + 255) / 256), (unsigned)B); }
 
 template <typename T>
@@ -492,12 +605,55 @@ int level_op(const MGBatch& m, int i, int mode, const T* rhs, const T* x, T* out
   return 1;
 }
 
+// Fused coarse-level step on level view L (27-point rows).
+template <typename T>
+void coarse_step(const MGBatch& m, const MGLevel& L, int stage, int outk, const T* rhs, const T* xin, T* out,
+                 const T* ec, const MGLevel* C, cudaStream_t s) {
+  const int TX = L.nx >= 32 ? 32 : (L.nx >= 16 ? 16 : 8);
+  const int TY = std::max(1, std::min(256 / TX, L.ny));
+  const int tiles_x = (L.nx + TX - 1) / TX, tiles_y = (L.ny + TY - 1) / TY;
+  int nzc = 1;
+  while ((int64_t)tiles_x * tiles_y * nzc * m.B < 4 * 152 && nzc * 2 <= L.nz / 4) nzc *= 2;
+  const int zc = (L.nz + nzc - 1) / nzc;
+  nzc = (L.nz + zc - 1) / zc;
+  const dim3 grid(tiles_x * tiles_y, nzc, m.B), block(TX, TY);
+  const size_t smem = sizeof(T) * 4 * (TX + 2) * (TY + 2);
+  const int cnx = C ? C->nx : 0, cny = C ? C->ny : 0, cnz = C ? C->nz : 0;
+  const T om = (T)kMGOmega;
+#define RBWS_MG_COARSE(S, O) \
+  k_mg_coarse<T, S, O><<<grid, block, smem, s>>>(L, m.st, m.mask, rhs, xin, out, ec, cnx, cny, cnz, om, tiles_x, zc)
+  if (stage == 1 && outk == 0) RBWS_MG_COARSE(1, 0);
+  else if (stage == 0 && outk == 1) RBWS_MG_COARSE(0, 1);
+  else if (stage == 2 && outk == 0) RBWS_MG_COARSE(2, 0);
+  else RBWS_MG_COARSE(0, 0);
+#undef RBWS_MG_COARSE
+}
+
 // out = MG(rhs, A^i, i)
 template <typename T>
 int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
   const MGPlan& P = *m.plan;
   if constexpr (sizeof(T) == 4) {
     if (i == P.J && i > 0 && m.fine_cg) return vcycle_fine_fused(m, rhs, out, -1, s);
+  }
+  if (i > 0 && i < P.J) {
+    // coarse level with fused 27-point steps (kMGNu = 2): Y = S(0, rhs, 2);
+    // W = rhs - A Y; restriction; coarse cycle e; W = step from Y + P e; out = step from W
+    static_assert(kMGNu == 2, "the fused levels do two pre- and two post-smoothing steps");
+    const MGLevel& F = m.lv[i];
+    const MGLevel& C = m.lv[i - 1];
+    T* Y = (T*)m.w1[i];
+    T* W = (T*)m.w2[i];
+    T* crhs = (T*)m.rhs[i - 1];
+    T* csol = (T*)m.sol[i - 1];
+    coarse_step<T>(m, F, 1, 0, rhs, nullptr, Y, nullptr, nullptr, s);
+    coarse_step<T>(m, F, 0, 1, rhs, Y, W, nullptr, nullptr, s);
+    k_mg_restrict<T><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
+                                                          crhs);
+    int launches = 3 + vcycle<T>(m, i - 1, crhs, csol, s);
+    coarse_step<T>(m, F, 2, 0, rhs, Y, W, csol, &C, s);
+    coarse_step<T>(m, F, 0, 0, rhs, W, out, nullptr, nullptr, s);
+    return launches + 2;
   }
   if (i == 0) {
     k_mg_dense_apply<T><<<m.B, 128, 0, s>>>(P.n0, (const T*)m.ainv, m.st, m.mask, rhs, out);
@@ -543,21 +699,26 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   float* crhs = (float*)m.rhs[J - 1];
   float* csol = (float*)m.sol[J - 1];
   MGFineArgs fa{rhs, nullptr, Y, nullptr, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot};
-  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 1, 0, fa, s);  // Y = two smoothing steps from zero
+  auto fine = [&](int k, int stage, int outk) {  // k: index of the step for the optional events
+    if (m.ev) cudaEventRecord(m.ev[2 * k], s);
+    launch_mg_fine_v4(*m.fine_cg, m.fine_tile, stage, outk, fa, s);
+    if (m.ev) cudaEventRecord(m.ev[2 * k + 1], s);
+  };
+  fine(0, 1, 0);  // Y = two smoothing steps from zero
   fa.xin = Y;
   fa.out = W;
-  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 0, 1, fa, s);  // W = r - A Y
+  fine(1, 0, 1);  // W = r - A Y
   k_mg_restrict<float><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
                                                             crhs);
   int launches = 3 + vcycle<float>(m, J - 1, crhs, csol, s);
   fa.xin = Y;
   fa.ec = csol;
   fa.out = W;
-  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 2, 0, fa, s);  // W = smoothing step from Y + P e
+  fine(2, 2, 0);  // W = smoothing step from Y + P e
   fa.xin = W;
   fa.ec = nullptr;
   fa.out = out;
-  launch_mg_fine_v4(*m.fine_cg, m.fine_tile, 0, slot >= 0 ? 2 : 0, fa, s);  // out = last step (+ rho)
+  fine(3, 0, slot >= 0 ? 2 : 0);  // out = last step (+ rho)
   return launches + 2;
 }
 

@@ -97,6 +97,36 @@ __global__ void k_lift(int64_t n, int N, const double* __restrict__ W, const dou
   }
 }
 
+// The same with an FP32 copy of W and FP32 accumulation (u to about 1e-7
+// relative: the start of the mixed-precision solver, whose FP64 residual is
+// formed from the u actually written).
+__global__ void k_lift32(int64_t n, int N, const float* __restrict__ W, const double* __restrict__ c, int B,
+                         double* __restrict__ u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* cs = reinterpret_cast<float*>(smem_raw);  // [kLiftB][N]
+  const int b0 = blockIdx.y * kLiftB;
+  const int nb = min(kLiftB, B - b0);
+  for (int e = threadIdx.x; e < nb * N; e += blockDim.x) cs[e] = (float)c[(int64_t)b0 * N + e];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float acc[kLiftB];
+#pragma unroll
+    for (int k = 0; k < kLiftB; k++) acc[k] = 0.f;
+    for (int j = 0; j < N; j++) {
+      const float w = W[(int64_t)j * n + i];
+#pragma unroll
+      for (int k = 0; k < kLiftB; k++) acc[k] = fmaf(cs[k * N + j], w, acc[k]);
+    }
+    for (int k = 0; k < nb; k++) u[(int64_t)(b0 + k) * n + i] = (double)acc[k];
+  }
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 // Stage 1 of out[k] = X[k].y: partial sums over fixed chunks.
 __global__ void k_dot_stage1(int64_t n, const double* __restrict__ X, int64_t ldx,
                              const double* __restrict__ y, double* __restrict__ part, int chunks) {
@@ -205,6 +235,16 @@ void launch_lift(int64_t n, int N, const double* W, const double* c, int B, doub
   const int threads = 256;
   dim3 grid(grid_for(n, threads, 152 * 4), (B + kLiftB - 1) / kLiftB);
   k_lift<<<grid, threads, sizeof(double) * kLiftB * N, s>>>(n, N, W, c, B, u);
+}
+
+void launch_lift32(int64_t n, int N, const float* W, const double* c, int B, double* u, cudaStream_t s) {
+  const int threads = 256;
+  dim3 grid(grid_for(n, threads, 152 * 4), (B + kLiftB - 1) / kLiftB);
+  k_lift32<<<grid, threads, sizeof(float) * kLiftB * N, s>>>(n, N, W, c, B, u);
+}
+
+void launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t s) {
+  k_to_f32<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, x, y);
 }
 
 void launch_multi_dot(int64_t n, int K, const double* X, int64_t ldx, const double* y, double* out,

@@ -876,30 +876,25 @@ void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s
 // ---------------------------------------------------------------------------
 namespace {
 
-// (P e) at fine node (i, j, k) (0-based): per axis, an even 1-based index takes
-// coarse i/2, an odd one half of each existing coarse neighbour.
-__device__ __forceinline__ float prolong_at(const float* e, int cnx, int cny, int cnz, int i, int j, int k) {
-  int Kx[2], Ky[2], Kz[2];
-  float wx[2], wy[2], wz[2];
-  auto pw = [](int i0, int m, int* K, float* w) {
-    const int t = i0 + 1;
-    if (t % 2 == 0) {
-      K[0] = t / 2 - 1;
-      w[0] = 1.f;
-      return 1;
-    }
-    int c = 0;
-    if ((t - 1) / 2 >= 1) K[c] = (t - 1) / 2 - 1, w[c++] = 0.5f;
-    if ((t + 1) / 2 <= m) K[c] = (t + 1) / 2 - 1, w[c++] = 0.5f;
-    return c;
-  };
-  const int nx_ = pw(i, cnx, Kx, wx), ny_ = pw(j, cny, Ky, wy), nz_ = pw(k, cnz, Kz, wz);
-  float v = 0.f;
-  for (int c = 0; c < nz_; c++)
-    for (int bq = 0; bq < ny_; bq++)
-      for (int a = 0; a < nx_; a++)
-        v = fmaf(wx[a] * wy[bq] * wz[c], e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
-  return v;
+// Interpolation weights along one axis: fine node j (0-based) of an axis whose
+// coarse grid has m nodes takes coarse k0 (weight w0) and, if k1 >= 0, coarse
+// k1 (weight w1).  An even 1-based index takes its coarse node whole, an odd
+// one half of each neighbour that exists (the boundary contributes zero).
+struct PRows {
+  int k0, k1;
+  float w0, w1;
+};
+__device__ __forceinline__ PRows prows(int j, int m) {
+  const int t = j + 1;
+  PRows r{-1, -1, 0.f, 0.f};
+  if (t % 2 == 0) {
+    r.k0 = t / 2 - 1;
+    r.w0 = 1.f;
+  } else {
+    if ((t - 1) / 2 >= 1) r.k0 = (t - 1) / 2 - 1, r.w0 = 0.5f;
+    if ((t + 1) / 2 <= m) r.k1 = (t + 1) / 2 - 1, r.w1 = 0.5f;
+  }
+  return r;
 }
 
 }  // namespace
@@ -930,6 +925,83 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   const int oslot = pl.at(4 * (int)threadIdx.x, (int)threadIdx.y);
   const int gi = ps.x0 + h.hx, gj = ps.y0 + h.hy;
 
+  // kStage 2: planes of the coarse correction, staged over the tile's coarse
+  // footprint (x: x0/2 - 1 .. x0/2 + TXN/2; y: floor((y0-2)/2) .. floor((y0+TY)/2))
+  // in a 2-slot ring after the fine planes.  Fine plane z reads coarse planes
+  // floor((z-1)/2) and floor(z/2) only.
+  float* csm = sm + 3 * pl.PS;
+  const int cx_lo = ps.x0 / 2 - 1, cy_lo = ps.y0 >= 2 ? (ps.y0 - 2) / 2 : -1;
+  const int CW = TXN / 2 + 2, CH = (ps.y0 + TY) / 2 - cy_lo + 1;
+  int cp0 = -1000, cp1 = -1000;  // coarse plane held by slot 0 / 1 (the same in every thread)
+  auto stage_coarse = [&](int kz) {
+    float* C = csm + (kz & 1) * CW * CH;
+    for (int t = tid; t < CW * CH; t += blockDim.x * blockDim.y) {
+      const int cxx = cx_lo + t % CW, cyy = cy_lo + t / CW;
+      C[t] = (cxx >= 0 && cxx < m.cnx && cyy >= 0 && cyy < m.cny)
+                 ? ec[((int64_t)kz * m.cny + cyy) * m.cnx + cxx] : 0.f;
+    }
+    if (kz & 1) cp1 = kz;
+    else cp0 = kz;
+  };
+  auto held = [&](int kz) { return ((kz & 1) ? cp1 : cp0) == kz; };
+  // stages the coarse planes fine plane z needs; true if it wrote any
+  auto ensure_coarse = [&](int z) -> bool {
+    bool wrote = false;
+    if (z < 0 || z >= g.nz) return false;
+    const int ka = z >= 1 ? (z - 1) / 2 : -1, kb = z / 2;
+    if (ka >= 0 && ka < m.cnz && !held(ka)) stage_coarse(ka), wrote = true;
+    if (kb < m.cnz && !held(kb)) stage_coarse(kb), wrote = true;
+    return wrote;
+  };
+  auto cval = [&](int kz, int ky, int kx) -> float {
+    return csm[(kz & 1) * CW * CH + (ky - cy_lo) * CW + (kx - cx_lo)];
+  };
+  // (P e) at the 4-node group x = i0 .. i0+3 of row j, plane z, from the staged planes
+  auto prolong4s = [&](int i0, int j, int z) -> float4 {
+    const PRows ry = prows(j, m.cny), rz = prows(z, m.cnz);
+    const int c1 = i0 / 2;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int aa = 0; aa < 2; aa++) {
+      const int kz = aa ? rz.k1 : rz.k0;
+      if (kz < 0) continue;
+      const float wz = aa ? rz.w1 : rz.w0;
+#pragma unroll
+      for (int bq = 0; bq < 2; bq++) {
+        const int ky = bq ? ry.k1 : ry.k0;
+        if (ky < 0) continue;
+        const float w = wz * (bq ? ry.w1 : ry.w0);
+        const float e0 = cval(kz, ky, c1 - 1), e1 = cval(kz, ky, c1), e2 = cval(kz, ky, c1 + 1);
+        v.x = fmaf(w, 0.5f * (e0 + e1), v.x);
+        v.y = fmaf(w, e1, v.y);
+        v.z = fmaf(w, 0.5f * (e1 + e2), v.z);
+        v.w = fmaf(w, e2, v.w);
+      }
+    }
+    return v;
+  };
+  auto prolong1s = [&](int i, int j, int z) -> float {
+    const PRows rx = prows(i, m.cnx), ry = prows(j, m.cny), rz = prows(z, m.cnz);
+    float v = 0.f;
+#pragma unroll
+    for (int aa = 0; aa < 2; aa++) {
+      const int kz = aa ? rz.k1 : rz.k0;
+      if (kz < 0) continue;
+#pragma unroll
+      for (int bq = 0; bq < 2; bq++) {
+        const int ky = bq ? ry.k1 : ry.k0;
+        if (ky < 0) continue;
+        const float wyz = (aa ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+        if (rx.k0 >= 0) v = fmaf(wyz * rx.w0, cval(kz, ky, rx.k0), v);
+        if (rx.k1 >= 0) v = fmaf(wyz * rx.w1, cval(kz, ky, rx.k1), v);
+      }
+    }
+    return v;
+  };
+  (void)ensure_coarse;
+  (void)prolong4s;
+  (void)prolong1s;
+
   // raw loads of plane z (register prefetch): the array the staged field is
   // formed from, for the own group and the halo element(s)
   const float* src = kStage == 1 ? rhs : xin;
@@ -943,27 +1015,56 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
       else v_h.x = src[z * plane + h.col];
     }
   };
-  // the staged value of one node at (i, j, z) from its raw value
-  auto staged = [&](float raw, int i, int j, int z) -> float {
-    if (kStage == 1) return omega * dinv_at(g, cb, g.cz[z], i, j) * raw;
-    if (kStage == 2) return raw + prolong_at(ec, m.cnx, m.cny, m.cnz, i, j, z);
-    return raw;
-  };
+  // staged values from raw ones: omega D^-1 raw (kStage 1; 1/D cached per z
+  // class for the own group and the halo element), raw + P e (kStage 2)
+  int own_zc = -1, h_zc = -1;
+  float own_di[4] = {0.f, 0.f, 0.f, 0.f}, h_di[4] = {0.f, 0.f, 0.f, 0.f};
   auto commit = [&](float* P, int z) -> float4 {
     const bool zin = z >= 0 && z < g.nz;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (zin && ps.own)
-      v = make_float4(staged(v_own.x, ps.i, ps.j, z), staged(v_own.y, ps.i + 1, ps.j, z),
-                      staged(v_own.z, ps.i + 2, ps.j, z), staged(v_own.w, ps.i + 3, ps.j, z));
+    if (zin && ps.own) {
+      if (kStage == 1) {
+        const int zc = g.cz[z];
+        if (zc != own_zc) {
+          own_zc = zc;
+#pragma unroll
+          for (int e = 0; e < 4; e++) own_di[e] = omega * dinv_at(g, cb, zc, ps.i + e, ps.j);
+        }
+        v = make_float4(own_di[0] * v_own.x, own_di[1] * v_own.y, own_di[2] * v_own.z, own_di[3] * v_own.w);
+      } else if (kStage == 2) {
+        const float4 pe = prolong4s(ps.i, ps.j, z);
+        v = make_float4(v_own.x + pe.x, v_own.y + pe.y, v_own.z + pe.z, v_own.w + pe.w);
+      } else {
+        v = v_own;
+      }
+    }
     st4(P + oslot, v);
-    if (h.kind == 1) {
+    if (h.kind != 0) {
       float4 hv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (zin && h.in)
-        hv = make_float4(staged(v_h.x, gi, gj, z), staged(v_h.y, gi + 1, gj, z), staged(v_h.z, gi + 2, gj, z),
-                         staged(v_h.w, gi + 3, gj, z));
-      st4(P + h.slot, hv);
-    } else if (h.kind == 2) {
-      P[h.slot] = (zin && h.in) ? staged(v_h.x, gi, gj, z) : 0.f;
+      if (zin && h.in) {
+        const int nh = h.kind == 1 ? 4 : 1;
+        if (kStage == 1) {
+          const int zc = g.cz[z];
+          if (zc != h_zc) {
+            h_zc = zc;
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+              if (e < nh) h_di[e] = omega * dinv_at(g, cb, zc, gi + e, gj);
+          }
+          hv = make_float4(h_di[0] * v_h.x, h_di[1] * v_h.y, h_di[2] * v_h.z, h_di[3] * v_h.w);
+        } else if (kStage == 2) {
+          if (h.kind == 1) {
+            const float4 pe = prolong4s(gi, gj, z);
+            hv = make_float4(v_h.x + pe.x, v_h.y + pe.y, v_h.z + pe.z, v_h.w + pe.w);
+          } else {
+            hv.x = v_h.x + prolong1s(gi, gj, z);
+          }
+        } else {
+          hv = v_h;
+        }
+      }
+      if (h.kind == 1) st4(P + h.slot, hv);
+      else P[h.slot] = hv.x;
     }
     return v;
   };
@@ -973,16 +1074,31 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   int zcls_cur = -1;
   const int z0 = ps.z0, z1 = ps.z1;
   float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (z0 > 0 && ps.own) {
+  if (kStage == 2) {  // coarse planes of fine planes z0 - 1 and z0 (two at most)
+    ensure_coarse(z0 - 1);
+    ensure_coarse(z0);
+    __syncthreads();
+  }
+  if (z0 > 0 && ps.own) {  // plane z0 - 1 of the own column, staged like the others
     const float4 raw = ld4(src + (z0 - 1) * plane + col);
-    xm = make_float4(staged(raw.x, ps.i, ps.j, z0 - 1), staged(raw.y, ps.i + 1, ps.j, z0 - 1),
-                     staged(raw.z, ps.i + 2, ps.j, z0 - 1), staged(raw.w, ps.i + 3, ps.j, z0 - 1));
+    if (kStage == 1) {
+      const int zc = g.cz[z0 - 1];
+      xm = make_float4(omega * dinv_at(g, cb, zc, ps.i, ps.j) * raw.x, omega * dinv_at(g, cb, zc, ps.i + 1, ps.j) * raw.y,
+                       omega * dinv_at(g, cb, zc, ps.i + 2, ps.j) * raw.z,
+                       omega * dinv_at(g, cb, zc, ps.i + 3, ps.j) * raw.w);
+    } else if (kStage == 2) {
+      const float4 pe = prolong4s(ps.i, ps.j, z0 - 1);
+      xm = make_float4(raw.x + pe.x, raw.y + pe.y, raw.z + pe.z, raw.w + pe.w);
+    } else {
+      xm = raw;
+    }
   }
   fetch(z0);
   float4 xc = commit(sm + (z0 % 3) * pl.PS, z0);
   fetch(z0 + 1);
   float rho = 0.f;
   for (int z = z0; z < z1; ++z) {
+    if (kStage == 2 && ensure_coarse(z + 1)) __syncthreads();    // the same decision in every thread
     const float4 xp = commit(sm + ((z + 1) % 3) * pl.PS, z + 1);  // plane z+1 (zeros past nz)
     fetch(z + 2);                                                  // in flight during plane z
     __syncthreads();
@@ -1021,9 +1137,11 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
 int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s) {
   const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
   const size_t smem = v4_plane_smem(t);
+  // two coarse planes of (2 tx + 2) x (ty/2 + 3) for the prolongation
+  const size_t smem_c = smem + sizeof(float) * 2 * (size_t)(2 * t.tx + 2) * (t.ty / 2 + 3);
   if (stage == 1 && outk == 0) k_mg_fine_v4<1, 0><<<grid, block, smem, s>>>(a, m);
   else if (stage == 0 && outk == 1) k_mg_fine_v4<0, 1><<<grid, block, smem, s>>>(a, m);
-  else if (stage == 2 && outk == 0) k_mg_fine_v4<2, 0><<<grid, block, smem, s>>>(a, m);
+  else if (stage == 2 && outk == 0) k_mg_fine_v4<2, 0><<<grid, block, smem_c, s>>>(a, m);
   else if (stage == 0 && outk == 2) k_mg_fine_v4<0, 2><<<grid, block, smem, s>>>(a, m);
   else return -1;
   return 0;

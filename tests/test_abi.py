@@ -76,7 +76,7 @@ def test_options_default_sets_every_field(lib_path):
     C.memset(C.byref(o), 0xAB, C.sizeof(o))
     rbws._lib().rbws_options_default(C.byref(o))
     assert o.max_iters == 20000 and o.precond == rbws.PREC_JACOBI and o.precision == rbws.FP64
-    assert o.max_restarts == 3 and o.inner_tol == 1e-2 and o.max_outer == 10 and o.check_every == 0
+    assert o.max_restarts == 3 and o.inner_tol == 0.0 and o.max_outer == 10 and o.check_every == 0
     assert o.stream is None and not o.profile and o.relres_hist is None and o.hist_len == 0
 
 
