@@ -290,6 +290,7 @@ void launch_precond_rho_v4(const CGArgs<float>& a, Tile t, int slot, const int* 
 constexpr int kMGMaxLevels = 12;
 constexpr int kMGCoarsest = 64;     // coarsen while a level has more unknowns than this
 constexpr int kMGMaxDense = 1024;   // largest coarsest level accepted
+constexpr int kMGTailMax = 4096;    // levels up to this size run in one kernel per V-cycle
 constexpr int kMGNu = 2;            // pre- and post-smoothing steps
 constexpr double kMGOmega = 2.0 / 3.0;
 

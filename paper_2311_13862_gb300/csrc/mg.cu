@@ -308,8 +308,11 @@ __global__ void k_mg_dense_setup(int Q, int n0, const double* __restrict__ a0q, 
 
 }  // namespace
 
+void mg_tail_prepare();  // kernel attributes of the one-kernel tail (below)
+
 void launch_mg_setup(const MGPlan& plan, const double* mu, int B, int fp32, void* const* tables, double* dense_a,
                      double* dense_l, double* ainv64, float* ainv32, int* info, cudaStream_t s) {
+  mg_tail_prepare();
   for (int i = 1; i < plan.J; i++) {
     const int ncls = plan.lv[i].ncls();
     const unsigned blocks = (unsigned)(((int64_t)B * ncls + 127) / 128);
@@ -485,23 +488,41 @@ __global__ void k_mg_dense_apply(int n0, const T* __restrict__ ainv, const InstS
 // x/y halo in a 4-slot shared-memory ring.  The staged field is xin (kStage
 // 0), omega D^-1 rhs (1) or xin + P e (2); the output a damped Jacobi step
 // (kOut 0) or the residual rhs - A x (kOut 1) -- as on the finest level.
+// Interpolation weights along one axis (registers only): fine node j of an
+// axis with m coarse nodes takes coarse k0 (w0) and, if k1 >= 0, k1 (w1).
+struct Pw {
+  int k0, k1;
+  float w0, w1;
+};
+__device__ __forceinline__ Pw pweight(int j, int m) {
+  const int t = j + 1;
+  Pw r{-1, -1, 0.f, 0.f};
+  if (t % 2 == 0) {
+    r.k0 = t / 2 - 1;
+    r.w0 = 1.f;
+  } else {
+    if ((t - 1) / 2 >= 1) r.k0 = (t - 1) / 2 - 1, r.w0 = 0.5f;
+    if ((t + 1) / 2 <= m) r.k1 = (t + 1) / 2 - 1, r.w1 = 0.5f;
+  }
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T prolong_node(const T* __restrict__ e, int cnx, int cny, int cnz, int i, int j, int k) {
-  int Kx[2], Ky[2], Kz[2];
-  float wx[2], wy[2], wz[2];
-  const int nx_ = pw(i, cnx, Kx, wx), ny_ = pw(j, cny, Ky, wy), nz_ = pw(k, cnz, Kz, wz);
+  const Pw rx = pweight(i, cnx), ry = pweight(j, cny), rz = pweight(k, cnz);
   T v = T(0);
 #pragma unroll
   for (int c = 0; c < 2; c++) {
-    if (c >= nz_) break;
+    const int kz = c ? rz.k1 : rz.k0;
+    if (kz < 0) continue;
 #pragma unroll
     for (int bq = 0; bq < 2; bq++) {
-      if (bq >= ny_) break;
-#pragma unroll
-      for (int a = 0; a < 2; a++) {
-        if (a >= nx_) break;
-        v = fma((T)(wx[a] * wy[bq] * wz[c]), e[((int64_t)Kz[c] * cny + Ky[bq]) * cnx + Kx[a]], v);
-      }
+      const int ky = bq ? ry.k1 : ry.k0;
+      if (ky < 0) continue;
+      const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+      const T* row = e + ((int64_t)kz * cny + ky) * cnx;
+      if (rx.k0 >= 0) v = fma((T)(wyz * rx.w0), row[rx.k0], v);
+      if (rx.k1 >= 0) v = fma((T)(wyz * rx.w1), row[rx.k1], v);
     }
   }
   return v;
@@ -521,7 +542,6 @@ __global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* _
   const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
   const int z0 = blockIdx.y * zc, z1 = min(L.nz, z0 + zc);
   const int PW = TX + 2, PS = PW * (TY + 2);
-  const int tid = threadIdx.y * TX + threadIdx.x;
   const int64_t plane = (int64_t)L.nx * L.ny, off = (int64_t)b * L.n;
   const int ncls = L.ncx * L.ncy * L.ncz;
   const T* tab = (const T*)L.coef + (int64_t)b * ncls * 28;
@@ -541,13 +561,14 @@ __global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* _
   // stage plane z (zeros outside the grid) into slot z & 3: (TX+2) x (TY+2) with halo
   auto stage = [&](int z) {
     T* Pl = sm + (z & 3) * PS;
-    for (int t = tid; t < PS; t += TX * TY) {
-      const int hx = t % PW - 1, hy = t / PW - 1;
-      const int i = x0 + hx, j = y0 + hy;
-      T v = T(0);
-      if (z >= 0 && z < L.nz && i >= 0 && i < L.nx && j >= 0 && j < L.ny) v = staged(i, j, z);
-      Pl[t] = v;
-    }
+    const bool zin = z >= 0 && z < L.nz;
+    for (int hy = (int)threadIdx.y; hy < TY + 2; hy += TY)
+      for (int hx = (int)threadIdx.x; hx < TX + 2; hx += TX) {
+        const int i = x0 + hx - 1, j = y0 + hy - 1;
+        T v = T(0);
+        if (zin && i >= 0 && i < L.nx && j >= 0 && j < L.ny) v = staged(i, j, z);
+        Pl[hy * PW + hx] = v;
+      }
   };
   const int i = x0 + (int)threadIdx.x, j = y0 + (int)threadIdx.y;
   const bool own = i < L.nx && j < L.ny;
@@ -593,6 +614,183 @@ __global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* _
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The small levels in one kernel: levels top .. 0 of the V-cycle (top has at
+// most kMGTailMax unknowns), one CTA per instance, every vector of those
+// levels in shared memory: the same steps as the per-level kernels (two
+// smoothing steps from zero, residual, restriction, the level below,
+// prolongation, two smoothing steps), with a barrier between steps.
+// ---------------------------------------------------------------------------
+struct MGTail {
+  int top;                    // highest level handled here (>= 1)
+  MGLevel lv[kMGMaxLevels];   // views of levels 0 .. top (coef: 28-wide tables, level 0 unused)
+  int off[kMGMaxLevels];      // shared-memory offset (elements) of level l's three vectors
+  int n0;
+};
+
+template <typename T>
+__device__ __forceinline__ T tail_apply(const MGLevel& L, const T* __restrict__ tab, const T* x, int t, T* dinv) {
+  const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
+  const int cls = (L.cz[k] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
+  const T* row = tab + (int64_t)cls * 28;
+  *dinv = row[27];
+  T v = T(0);
+  for (int dz = -1; dz <= 1; dz++) {
+    if (k + dz < 0 || k + dz >= L.nz) continue;
+    for (int dy = -1; dy <= 1; dy++) {
+      if (j + dy < 0 || j + dy >= L.ny) continue;
+      for (int dx = -1; dx <= 1; dx++) {
+        if (i + dx < 0 || i + dx >= L.nx) continue;
+        v = fma(row[(dz + 1) * 9 + (dy + 1) * 3 + dx + 1], x[t + (dz * L.ny + dy) * L.nx + dx], v);
+      }
+    }
+  }
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_mg_tail(MGTail tl, const InstState* __restrict__ st,
+                                                 const int* __restrict__ mask, const T* __restrict__ rhs_top,
+                                                 T* __restrict__ out_top, const T* __restrict__ ainv, T omega) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.x;
+  if (mg_skip(st, mask, b)) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto vb = [&](int l) { return sm + tl.off[l]; };                       // right-hand side
+  auto vy = [&](int l) { return sm + tl.off[l] + tl.lv[l].n; };          // smoothed iterate / solution
+  auto vt = [&](int l) { return sm + tl.off[l] + 2 * tl.lv[l].n; };      // scratch
+  auto tab = [&](int l) { return (const T*)tl.lv[l].coef + (int64_t)b * tl.lv[l].ncx * tl.lv[l].ncy * tl.lv[l].ncz * 28; };
+  // the right-hand side of the top level
+  {
+    const int n = (int)tl.lv[tl.top].n;
+    for (int t = tid; t < n; t += nt) vb(tl.top)[t] = rhs_top[(int64_t)b * n + t];
+  }
+  __syncthreads();
+  // down: smoothing, residual, restriction
+  for (int l = tl.top; l >= 1; l--) {
+    const MGLevel& L = tl.lv[l];
+    const int n = (int)L.n;
+    const T* tb = tab(l);
+    T *bb = vb(l), *yy = vy(l), *tt = vt(l);
+    for (int t = tid; t < n; t += nt) {  // tt = omega D^-1 b
+      T di;
+      const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
+      di = tb[(int64_t)((L.cz[k] * L.ncy + L.cy[j]) * L.ncx + L.cx[i]) * 28 + 27];
+      tt[t] = omega * di * bb[t];
+    }
+    __syncthreads();
+    for (int t = tid; t < n; t += nt) {  // yy = tt + omega D^-1 (b - A tt)
+      T di;
+      const T ax = tail_apply<T>(L, tb, tt, t, &di);
+      yy[t] = fma(omega * di, bb[t] - ax, tt[t]);
+    }
+    __syncthreads();
+    for (int t = tid; t < n; t += nt) {  // tt = b - A yy
+      T di;
+      tt[t] = bb[t] - tail_apply<T>(L, tb, yy, t, &di);
+    }
+    __syncthreads();
+    const MGLevel& C = tl.lv[l - 1];
+    T* cb = vb(l - 1);
+    for (int t = tid; t < (int)C.n; t += nt) {  // b_{l-1} = P^T tt
+      const int I = t % C.nx, J = (t / C.nx) % C.ny, K = t / (C.nx * C.ny);
+      T v = T(0);
+      for (int dz = -1; dz <= 1; dz++) {
+        const int z = 2 * K + 1 + dz;
+        if (z < 0 || z >= L.nz) continue;
+        for (int dy = -1; dy <= 1; dy++) {
+          const int y = 2 * J + 1 + dy;
+          if (y < 0 || y >= L.ny) continue;
+          for (int dx = -1; dx <= 1; dx++) {
+            const int x = 2 * I + 1 + dx;
+            if (x < 0 || x >= L.nx) continue;
+            const T w = (T)((dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f));
+            v = fma(w, tt[(z * L.ny + y) * L.nx + x], v);
+          }
+        }
+      }
+      cb[t] = v;
+    }
+    __syncthreads();
+  }
+  // level 0: the explicit inverse
+  {
+    const int n0 = tl.n0;
+    const T* Ai = ainv + (int64_t)b * n0 * n0;
+    const T* b0 = vb(0);
+    for (int i = tid; i < n0; i += nt) {
+      T v = T(0);
+      for (int j = 0; j < n0; j++) v = fma(Ai[(int64_t)i * n0 + j], b0[j], v);
+      vy(0)[i] = v;
+    }
+    __syncthreads();
+  }
+  // up: prolongation, smoothing
+  for (int l = 1; l <= tl.top; l++) {
+    const MGLevel& L = tl.lv[l];
+    const MGLevel& C = tl.lv[l - 1];
+    const int n = (int)L.n;
+    const T* tb = tab(l);
+    T *bb = vb(l), *yy = vy(l), *tt = vt(l);
+    const T* e = vy(l - 1);
+    for (int t = tid; t < n; t += nt) {  // yy += P e
+      const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
+      const Pw rx = pweight(i, C.nx), ry = pweight(j, C.ny), rz = pweight(k, C.nz);
+      T v = T(0);
+      for (int c = 0; c < 2; c++) {
+        const int kz = c ? rz.k1 : rz.k0;
+        if (kz < 0) continue;
+        for (int bq = 0; bq < 2; bq++) {
+          const int ky = bq ? ry.k1 : ry.k0;
+          if (ky < 0) continue;
+          const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+          const T* row = e + (kz * C.ny + ky) * C.nx;
+          if (rx.k0 >= 0) v = fma((T)(wyz * rx.w0), row[rx.k0], v);
+          if (rx.k1 >= 0) v = fma((T)(wyz * rx.w1), row[rx.k1], v);
+        }
+      }
+      yy[t] += v;
+    }
+    __syncthreads();
+    for (int t = tid; t < n; t += nt) {  // tt = yy + omega D^-1 (b - A yy)
+      T di;
+      const T ax = tail_apply<T>(L, tb, yy, t, &di);
+      tt[t] = fma(omega * di, bb[t] - ax, yy[t]);
+    }
+    __syncthreads();
+    T* dst = l == tl.top ? out_top + (int64_t)b * n : yy;
+    for (int t = tid; t < n; t += nt) {  // solution = tt + omega D^-1 (b - A tt)
+      T di;
+      const T ax = tail_apply<T>(L, tb, tt, t, &di);
+      dst[t] = fma(omega * di, bb[t] - ax, tt[t]);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+constexpr size_t kMGTailSmem = 200 * 1024;  // dynamic shared memory the tail may use
+
+void mg_tail_prepare() {
+  cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMGTailSmem);
+  cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMGTailSmem);
+}
+
+namespace {
+
+// Shared memory of the tail kernel for levels 0 .. top (elements).
+inline int tail_elems(const MGPlan& P, int top, int* off) {
+  int o = 0;
+  for (int l = 0; l <= top; l++) {
+    off[l] = o;
+    o += 3 * (int)P.lv[l].n;
+  }
+  return o;
+}
+
 inline dim3 level_grid(int64_t n, int B) { return dim3((unsigned)((n + 255) / 256), (unsigned)B); }
 
 template <typename T>
@@ -635,6 +833,17 @@ int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
   const MGPlan& P = *m.plan;
   if constexpr (sizeof(T) == 4) {
     if (i == P.J && i > 0 && m.fine_cg) return vcycle_fine_fused(m, rhs, out, -1, s);
+  }
+  if (i > 0 && i < P.J && P.lv[i].n <= kMGTailMax) {
+    MGTail tl;
+    tl.top = i;
+    tl.n0 = P.n0;
+    for (int l = 0; l <= i; l++) tl.lv[l] = m.lv[l];
+    const size_t smem = sizeof(T) * (size_t)tail_elems(P, i, tl.off);
+    if (smem <= kMGTailSmem) {
+      k_mg_tail<T><<<m.B, 512, smem, s>>>(tl, m.st, m.mask, rhs, out, (const T*)m.ainv, (T)kMGOmega);
+      return 1;
+    }
   }
   if (i > 0 && i < P.J) {
     // coarse level with fused 27-point steps (kMGNu = 2): Y = S(0, rhs, 2);
