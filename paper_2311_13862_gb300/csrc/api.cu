@@ -793,8 +793,10 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.precond = o.precond;
   a.ru = 1;
   // auto: 1e-2 with Jacobi; with MG, whose iterations gain about a decade each,
-  // 1e-3 (fewer FP64 updates; blocks of 2 iterations keep the FP32 recursion
-  // within a few decades of its last update)
+  // 1e-3 (fewer FP64 updates, each of which also costs a V-cycle for the reset
+  // residual; blocks of 2 iterations keep the FP32 recursion within about five
+  // decades of its last update.  1e-4 let an instance of a contrast-1e4 test
+  // stall in the FP32 recursion: 142 iterations instead of 17)
   const double delta = (o.inner_tol > 0.0 && o.inner_tol < 1.0) ? o.inner_tol : (mg ? 1e-3 : 1e-2);
   a.ru_delta2 = delta * delta;
   a.rr_ref = rr_ref;
@@ -807,8 +809,15 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   if (mg) {
     CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
     if (v4) {
+      mg_fine_prepare();
       mgb.fine_cg = &a;
       mgb.fine_tile = t;
+      const Tile tm = choose_tile_v4(p->nx, p->ny);
+      mgb.mg_tile = tm;
+      mgb.mg_tiles_x = (p->nx + 4 * tm.tx - 1) / (4 * tm.tx);
+      mgb.mg_tiles_y = (p->ny + tm.ty - 1) / tm.ty;
+      mgb.mg_zc = choose_zc_v4(p->nz, (int64_t)mgb.mg_tiles_x * mgb.mg_tiles_y * B);
+      mgb.mg_nzc = (p->nz + mgb.mg_zc - 1) / mgb.mg_zc;
     }
   }
   if (sched32) {

@@ -346,6 +346,9 @@ struct MGBatch {
   // the iteration's tiling and writes the rho partials itself
   const CGArgs<float>* fine_cg = nullptr;
   Tile fine_tile{0, 0};
+  // tiling of the fused steps that write no partials (wider tiles: less halo)
+  Tile mg_tile{0, 0};
+  int mg_tiles_x = 0, mg_tiles_y = 0, mg_zc = 0, mg_nzc = 0;
   cudaEvent_t* ev = nullptr;  // if set: 8 events bracketing the four fused finest-level steps
   MGLevel lv[kMGMaxLevels];
   void* rhs[kMGMaxLevels] = {};
@@ -379,6 +382,10 @@ struct MGFineArgs {
 // step, 1: residual, 2: Jacobi step and rho partials.  Returns -1 for a
 // combination that is not built.
 int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s);
+// Shared memory of the coarse planes staged by stage 2 for z-chunks of zc planes;
+// mg_fine_prepare sets the kernel attribute (call outside stream capture).
+size_t mg_fine_coarse_smem(Tile t, int zc);
+void mg_fine_prepare();
 // y = D^-1 x on the FP64 level view L (instances all active).
 void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s);
 

@@ -810,8 +810,9 @@ void coarse_step(const MGBatch& m, const MGLevel& L, int stage, int outk, const 
   const int TX = L.nx >= 32 ? 32 : (L.nx >= 16 ? 16 : 8);
   const int TY = std::max(1, std::min(256 / TX, L.ny));
   const int tiles_x = (L.nx + TX - 1) / TX, tiles_y = (L.ny + TY - 1) / TY;
+  // z-chunks: at least two waves of 4 resident CTAs per SM where the level allows
   int nzc = 1;
-  while ((int64_t)tiles_x * tiles_y * nzc * m.B < 4 * 152 && nzc * 2 <= L.nz / 4) nzc *= 2;
+  while ((int64_t)tiles_x * tiles_y * nzc * m.B < 8 * 152 && nzc * 2 <= L.nz / 4) nzc *= 2;
   const int zc = (L.nz + nzc - 1) / nzc;
   nzc = (L.nz + zc - 1) / zc;
   const dim3 grid(tiles_x * tiles_y, nzc, m.B), block(TX, TY);
@@ -908,9 +909,20 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   float* crhs = (float*)m.rhs[J - 1];
   float* csol = (float*)m.sol[J - 1];
   MGFineArgs fa{rhs, nullptr, Y, nullptr, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot};
+  // the steps that write no partials run on wider tiles (less halo); the last,
+  // with the rho partials, on the iteration's own tiling
+  CGArgs<float> am = *m.fine_cg;
+  if (m.mg_tile.tx > 0) {
+    am.tiles_x = m.mg_tiles_x;
+    am.tiles_y = m.mg_tiles_y;
+    am.zc = m.mg_zc;
+    am.nzc = m.mg_nzc;
+  }
+  const Tile tm = m.mg_tile.tx > 0 ? m.mg_tile : m.fine_tile;
   auto fine = [&](int k, int stage, int outk) {  // k: index of the step for the optional events
     if (m.ev) cudaEventRecord(m.ev[2 * k], s);
-    launch_mg_fine_v4(*m.fine_cg, m.fine_tile, stage, outk, fa, s);
+    if (outk == 2) launch_mg_fine_v4(*m.fine_cg, m.fine_tile, stage, outk, fa, s);
+    else launch_mg_fine_v4(am, tm, stage, outk, fa, s);
     if (m.ev) cudaEventRecord(m.ev[2 * k + 1], s);
   };
   fine(0, 1, 0);  // Y = two smoothing steps from zero

@@ -925,53 +925,67 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   const int oslot = pl.at(4 * (int)threadIdx.x, (int)threadIdx.y);
   const int gi = ps.x0 + h.hx, gj = ps.y0 + h.hy;
 
-  // kStage 2: planes of the coarse correction, staged over the tile's coarse
-  // footprint (x: x0/2 - 1 .. x0/2 + TXN/2; y: floor((y0-2)/2) .. floor((y0+TY)/2))
-  // in a 2-slot ring after the fine planes.  Fine plane z reads coarse planes
-  // floor((z-1)/2) and floor(z/2) only.
+  // kStage 2: the coarse correction over the tile's coarse footprint (x: x0/2 - 1
+  // .. x0/2 + TXN/2; y: floor((y0-2)/2) .. floor((y0+TY)/2)) for every coarse
+  // plane the z-chunk touches (fine plane z reads coarse planes floor((z-1)/2)
+  // and floor(z/2)), staged once after the fine planes' ring.
   float* csm = sm + 3 * pl.PS;
   const int cx_lo = ps.x0 / 2 - 1, cy_lo = ps.y0 >= 2 ? (ps.y0 - 2) / 2 : -1;
   const int CW = TXN / 2 + 2, CH = (ps.y0 + TY) / 2 - cy_lo + 1;
-  int cp0 = -1000, cp1 = -1000;  // coarse plane held by slot 0 / 1 (the same in every thread)
-  auto stage_coarse = [&](int kz) {
-    float* C = csm + (kz & 1) * CW * CH;
-    for (int t = tid; t < CW * CH; t += blockDim.x * blockDim.y) {
-      const int cxx = cx_lo + t % CW, cyy = cy_lo + t / CW;
-      C[t] = (cxx >= 0 && cxx < m.cnx && cyy >= 0 && cyy < m.cny)
-                 ? ec[((int64_t)kz * m.cny + cyy) * m.cnx + cxx] : 0.f;
+  const int kz_lo = ps.z0 >= 2 ? (ps.z0 - 2) / 2 : -1, kz_hi = min(m.cnz - 1, ps.z1 / 2);
+  if (kStage == 2) {  // row by row: one division per row, columns across threadIdx.x
+    const int nrows = (kz_hi - kz_lo + 1) * CH;
+    for (int r = (int)threadIdx.y; r < nrows; r += (int)blockDim.y) {
+      const int kz = kz_lo + r / CH, cyy = cy_lo + r % CH;
+      const bool rin = kz >= 0 && cyy >= 0 && cyy < m.cny;
+      const float* src_row = ec + ((int64_t)max(kz, 0) * m.cny + max(cyy, 0)) * m.cnx;
+      for (int c = (int)threadIdx.x; c < CW; c += (int)blockDim.x) {
+        const int cxx = cx_lo + c;
+        csm[r * CW + c] = (rin && cxx >= 0 && cxx < m.cnx) ? src_row[cxx] : 0.f;
+      }
     }
-    if (kz & 1) cp1 = kz;
-    else cp0 = kz;
+    __syncthreads();
+  }
+  // (P e) from the staged planes.  Per thread the coarse rows and columns are
+  // fixed (its own group, its halo element); per plane only the coarse z
+  // planes change.  Offsets below are within one staged coarse plane.
+  struct Rows {
+    int o0, o1;  // offset of the row (and first column) of each coarse y row, -1 = none
+    float w0, w1;
   };
-  auto held = [&](int kz) { return ((kz & 1) ? cp1 : cp0) == kz; };
-  // stages the coarse planes fine plane z needs; true if it wrote any
-  auto ensure_coarse = [&](int z) -> bool {
-    bool wrote = false;
-    if (z < 0 || z >= g.nz) return false;
-    const int ka = z >= 1 ? (z - 1) / 2 : -1, kb = z / 2;
-    if (ka >= 0 && ka < m.cnz && !held(ka)) stage_coarse(ka), wrote = true;
-    if (kb < m.cnz && !held(kb)) stage_coarse(kb), wrote = true;
-    return wrote;
+  auto rows_of = [&](int j, int xfirst) -> Rows {  // coarse rows of fine row j, starting at coarse column xfirst
+    const PRows ry = prows(j, m.cny);
+    Rows r{-1, -1, ry.w0, ry.w1};
+    if (ry.k0 >= 0) r.o0 = (ry.k0 - cy_lo) * CW + (xfirst - cx_lo);
+    if (ry.k1 >= 0) r.o1 = (ry.k1 - cy_lo) * CW + (xfirst - cx_lo);
+    return r;
   };
-  auto cval = [&](int kz, int ky, int kx) -> float {
-    return csm[(kz & 1) * CW * CH + (ky - cy_lo) * CW + (kx - cx_lo)];
+  // the 4-node group at i0: coarse columns i0/2 - 1 .. i0/2 + 1
+  const Rows own_rows = rows_of(ps.j, ps.i / 2 - 1);
+  const Rows halo_rows = h.kind == 1 ? rows_of(gj, gi / 2 - 1) : rows_of(gj, 0);
+  const PRows hx = prows(gi, m.cnx);  // x weights of a single halo node (kind 2)
+  auto planes_of = [&](int z, int* z0o, int* z1o, float* wz0, float* wz1) {
+    const PRows rz = prows(z, m.cnz);
+    *z0o = rz.k0 >= 0 ? (rz.k0 - kz_lo) * CH * CW : -1;
+    *z1o = rz.k1 >= 0 ? (rz.k1 - kz_lo) * CH * CW : -1;
+    *wz0 = rz.w0;
+    *wz1 = rz.w1;
   };
-  // (P e) at the 4-node group x = i0 .. i0+3 of row j, plane z, from the staged planes
-  auto prolong4s = [&](int i0, int j, int z) -> float4 {
-    const PRows ry = prows(j, m.cny), rz = prows(z, m.cnz);
-    const int c1 = i0 / 2;
+  auto prolong4s = [&](const Rows& r, int z) -> float4 {
+    int zo[2];
+    float wz[2];
+    planes_of(z, &zo[0], &zo[1], &wz[0], &wz[1]);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int aa = 0; aa < 2; aa++) {
-      const int kz = aa ? rz.k1 : rz.k0;
-      if (kz < 0) continue;
-      const float wz = aa ? rz.w1 : rz.w0;
+      if (zo[aa] < 0) continue;
 #pragma unroll
       for (int bq = 0; bq < 2; bq++) {
-        const int ky = bq ? ry.k1 : ry.k0;
-        if (ky < 0) continue;
-        const float w = wz * (bq ? ry.w1 : ry.w0);
-        const float e0 = cval(kz, ky, c1 - 1), e1 = cval(kz, ky, c1), e2 = cval(kz, ky, c1 + 1);
+        const int yo = bq ? r.o1 : r.o0;
+        if (yo < 0) continue;
+        const float w = wz[aa] * (bq ? r.w1 : r.w0);
+        const float* c = csm + zo[aa] + yo;
+        const float e0 = c[0], e1 = c[1], e2 = c[2];
         v.x = fmaf(w, 0.5f * (e0 + e1), v.x);
         v.y = fmaf(w, e1, v.y);
         v.z = fmaf(w, 0.5f * (e1 + e2), v.z);
@@ -980,25 +994,26 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
     }
     return v;
   };
-  auto prolong1s = [&](int i, int j, int z) -> float {
-    const PRows rx = prows(i, m.cnx), ry = prows(j, m.cny), rz = prows(z, m.cnz);
+  auto prolong1s = [&](int z) -> float {  // the kind-2 halo node (gi, gj)
+    int zo[2];
+    float wz[2];
+    planes_of(z, &zo[0], &zo[1], &wz[0], &wz[1]);
     float v = 0.f;
 #pragma unroll
     for (int aa = 0; aa < 2; aa++) {
-      const int kz = aa ? rz.k1 : rz.k0;
-      if (kz < 0) continue;
+      if (zo[aa] < 0) continue;
 #pragma unroll
       for (int bq = 0; bq < 2; bq++) {
-        const int ky = bq ? ry.k1 : ry.k0;
-        if (ky < 0) continue;
-        const float wyz = (aa ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
-        if (rx.k0 >= 0) v = fmaf(wyz * rx.w0, cval(kz, ky, rx.k0), v);
-        if (rx.k1 >= 0) v = fmaf(wyz * rx.w1, cval(kz, ky, rx.k1), v);
+        const int yo = bq ? halo_rows.o1 : halo_rows.o0;
+        if (yo < 0) continue;
+        const float wyz = wz[aa] * (bq ? halo_rows.w1 : halo_rows.w0);
+        const float* c = csm + zo[aa] + yo;
+        if (hx.k0 >= 0) v = fmaf(wyz * hx.w0, c[hx.k0], v);
+        if (hx.k1 >= 0) v = fmaf(wyz * hx.w1, c[hx.k1], v);
       }
     }
     return v;
   };
-  (void)ensure_coarse;
   (void)prolong4s;
   (void)prolong1s;
 
@@ -1032,7 +1047,7 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
         }
         v = make_float4(own_di[0] * v_own.x, own_di[1] * v_own.y, own_di[2] * v_own.z, own_di[3] * v_own.w);
       } else if (kStage == 2) {
-        const float4 pe = prolong4s(ps.i, ps.j, z);
+        const float4 pe = prolong4s(own_rows, z);
         v = make_float4(v_own.x + pe.x, v_own.y + pe.y, v_own.z + pe.z, v_own.w + pe.w);
       } else {
         v = v_own;
@@ -1054,10 +1069,10 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
           hv = make_float4(h_di[0] * v_h.x, h_di[1] * v_h.y, h_di[2] * v_h.z, h_di[3] * v_h.w);
         } else if (kStage == 2) {
           if (h.kind == 1) {
-            const float4 pe = prolong4s(gi, gj, z);
+            const float4 pe = prolong4s(halo_rows, z);
             hv = make_float4(v_h.x + pe.x, v_h.y + pe.y, v_h.z + pe.z, v_h.w + pe.w);
           } else {
-            hv.x = v_h.x + prolong1s(gi, gj, z);
+            hv.x = v_h.x + prolong1s(z);
           }
         } else {
           hv = v_h;
@@ -1074,11 +1089,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   int zcls_cur = -1;
   const int z0 = ps.z0, z1 = ps.z1;
   float4 xm = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (kStage == 2) {  // coarse planes of fine planes z0 - 1 and z0 (two at most)
-    ensure_coarse(z0 - 1);
-    ensure_coarse(z0);
-    __syncthreads();
-  }
   if (z0 > 0 && ps.own) {  // plane z0 - 1 of the own column, staged like the others
     const float4 raw = ld4(src + (z0 - 1) * plane + col);
     if (kStage == 1) {
@@ -1087,7 +1097,7 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
                        omega * dinv_at(g, cb, zc, ps.i + 2, ps.j) * raw.z,
                        omega * dinv_at(g, cb, zc, ps.i + 3, ps.j) * raw.w);
     } else if (kStage == 2) {
-      const float4 pe = prolong4s(ps.i, ps.j, z0 - 1);
+      const float4 pe = prolong4s(own_rows, z0 - 1);
       xm = make_float4(raw.x + pe.x, raw.y + pe.y, raw.z + pe.z, raw.w + pe.w);
     } else {
       xm = raw;
@@ -1098,7 +1108,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   fetch(z0 + 1);
   float rho = 0.f;
   for (int z = z0; z < z1; ++z) {
-    if (kStage == 2 && ensure_coarse(z + 1)) __syncthreads();    // the same decision in every thread
     const float4 xp = commit(sm + ((z + 1) % 3) * pl.PS, z + 1);  // plane z+1 (zeros past nz)
     fetch(z + 2);                                                  // in flight during plane z
     __syncthreads();
@@ -1134,11 +1143,19 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   }
 }
 
+size_t mg_fine_coarse_smem(Tile t, int zc) {
+  return sizeof(float) * (size_t)(zc / 2 + 3) * (2 * t.tx + 2) * (t.ty / 2 + 3);
+}
+
+void mg_fine_prepare() {
+  cudaFuncSetAttribute(k_mg_fine_v4<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s) {
   const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
   const size_t smem = v4_plane_smem(t);
-  // two coarse planes of (2 tx + 2) x (ty/2 + 3) for the prolongation
-  const size_t smem_c = smem + sizeof(float) * 2 * (size_t)(2 * t.tx + 2) * (t.ty / 2 + 3);
+  // the coarse planes of a z-chunk: (zc/2 + 3) planes of (2 tx + 2) x (ty/2 + 3)
+  const size_t smem_c = smem + mg_fine_coarse_smem(t, a.zc);
   if (stage == 1 && outk == 0) k_mg_fine_v4<1, 0><<<grid, block, smem, s>>>(a, m);
   else if (stage == 0 && outk == 1) k_mg_fine_v4<0, 1><<<grid, block, smem, s>>>(a, m);
   else if (stage == 2 && outk == 0) k_mg_fine_v4<2, 0><<<grid, block, smem_c, s>>>(a, m);
