@@ -108,9 +108,9 @@ typedef struct {
                           schedule (0..3, see rbws_autotune); -1 for FP64            */
   double precond_ms;   /* FP32_IR with RBWS_PREC_MG: summed durations of the V-cycles
                           of the sampled iterations (after the update phase)         */
-  double mg_fine_ms[4]; /* ... and of their four fused finest-level steps: two
-                          smoothing steps from zero, residual, prolongation + one
-                          smoothing step, last smoothing step + rho partials        */
+  double mg_fine_ms[4]; /* ... and of their finest-level steps: two smoothing steps
+                          from zero, residual, prolongation pass + one smoothing
+                          step, last smoothing step + rho partials                  */
 } rbws_profile;
 
 typedef struct {

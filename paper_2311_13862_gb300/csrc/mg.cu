@@ -791,6 +791,47 @@ inline int tail_elems(const MGPlan& P, int top, int* off) {
   return o;
 }
 
+// uf += P ec on the finest FP32 level, four x-consecutive fine nodes per thread
+// (fnx % 4 == 0): a group at i0 reads coarse columns i0/2 - 1 .. i0/2 + 1 of each
+// coarse row it touches (see the fused prolongation).
+__global__ void __launch_bounds__(256) k_mg_prolong_add4(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
+                                                         const InstState* __restrict__ st,
+                                                         const int* __restrict__ mask, const float* __restrict__ ec,
+                                                         float* __restrict__ uf) {
+  const int b = blockIdx.y;
+  if (mg_skip(st, mask, b)) return;
+  const int gx = fnx / 4;
+  const int64_t ng = (int64_t)gx * fny * fnz;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ng) return;
+  const int i0 = 4 * (int)(t % gx), j = (int)((t / gx) % fny), k = (int)(t / ((int64_t)gx * fny));
+  const Pw ry = pweight(j, cny), rz = pweight(k, cnz);
+  const float* e = ec + (int64_t)b * cnx * cny * cnz;
+  const int c1 = i0 / 2;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 2; c++) {
+    const int kz = c ? rz.k1 : rz.k0;
+    if (kz < 0) continue;
+#pragma unroll
+    for (int bq = 0; bq < 2; bq++) {
+      const int ky = bq ? ry.k1 : ry.k0;
+      if (ky < 0) continue;
+      const float w = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+      const float* row = e + ((int64_t)kz * cny + ky) * cnx;
+      const float e0 = c1 > 0 ? row[c1 - 1] : 0.f, e1 = row[c1], e2 = row[c1 + 1];
+      v.x = fmaf(w, 0.5f * (e0 + e1), v.x);
+      v.y = fmaf(w, e1, v.y);
+      v.z = fmaf(w, 0.5f * (e1 + e2), v.z);
+      v.w = fmaf(w, e2, v.w);
+    }
+  }
+  float4* p = reinterpret_cast<float4*>(uf + (int64_t)b * fnx * fny * fnz) + t;
+  float4 u = *p;
+  u.x += v.x, u.y += v.y, u.z += v.z, u.w += v.w;
+  *p = u;
+}
+
 inline dim3 level_grid(int64_t n, int B) { return dim3((unsigned)((n + 255) / 256), (unsigned)B); }
 
 template <typename T>
@@ -861,9 +902,11 @@ int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
     k_mg_restrict<T><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
                                                           crhs);
     int launches = 3 + vcycle<T>(m, i - 1, crhs, csol, s);
-    coarse_step<T>(m, F, 2, 0, rhs, Y, W, csol, &C, s);
+    k_mg_prolong_add<T><<<level_grid(F.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask,
+                                                             csol, Y);
+    coarse_step<T>(m, F, 0, 0, rhs, Y, W, nullptr, nullptr, s);
     coarse_step<T>(m, F, 0, 0, rhs, W, out, nullptr, nullptr, s);
-    return launches + 2;
+    return launches + 3;
   }
   if (i == 0) {
     k_mg_dense_apply<T><<<m.B, 128, 0, s>>>(P.n0, (const T*)m.ainv, m.st, m.mask, rhs, out);
@@ -919,8 +962,8 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
     am.nzc = m.mg_nzc;
   }
   const Tile tm = m.mg_tile.tx > 0 ? m.mg_tile : m.fine_tile;
-  auto fine = [&](int k, int stage, int outk) {  // k: index of the step for the optional events
-    if (m.ev) cudaEventRecord(m.ev[2 * k], s);
+  auto fine = [&](int k, int stage, int outk, bool open = true) {  // k: step index for the optional events
+    if (m.ev && open) cudaEventRecord(m.ev[2 * k], s);
     if (outk == 2) launch_mg_fine_v4(*m.fine_cg, m.fine_tile, stage, outk, fa, s);
     else launch_mg_fine_v4(am, tm, stage, outk, fa, s);
     if (m.ev) cudaEventRecord(m.ev[2 * k + 1], s);
@@ -932,10 +975,15 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   k_mg_restrict<float><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
                                                             crhs);
   int launches = 3 + vcycle<float>(m, J - 1, crhs, csol, s);
+  // Y += P e (a streaming pass), then W = one smoothing step from Y (timed together)
+  if (m.ev) cudaEventRecord(m.ev[4], s);
+  k_mg_prolong_add4<<<dim3((unsigned)((F.n / 4 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(
+      F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);
+  launches += 1;
   fa.xin = Y;
-  fa.ec = csol;
+  fa.ec = nullptr;
   fa.out = W;
-  fine(2, 2, 0);  // W = smoothing step from Y + P e
+  fine(2, 0, 0, false);  // W = smoothing step from Y
   fa.xin = W;
   fa.ec = nullptr;
   fa.out = out;
