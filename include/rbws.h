@@ -121,7 +121,7 @@ typedef struct {
   double inner_tol;     /* FP32_IR: an FP64 refinement step (reliable update) is
                            taken each time an instance's FP32 residual has
                            fallen by this factor since its last one (0 = auto:
-                           1e-2, or 1e-3 with RBWS_PREC_MG)                      */
+                           1e-2)                                                  */
   int32_t max_outer;    /* reserved (10)                                         */
   int32_t check_every;  /* iterations between host convergence polls and, in
                            FP32_IR, reliable-update tests (0 = auto: 8, or 2

@@ -792,12 +792,12 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.max_iters = o.max_iters;
   a.precond = o.precond;
   a.ru = 1;
-  // auto: 1e-2 with Jacobi; with MG, whose iterations gain about a decade each,
-  // 1e-3 (fewer FP64 updates, each of which also costs a V-cycle for the reset
-  // residual; blocks of 2 iterations keep the FP32 recursion within about five
-  // decades of its last update.  1e-4 let an instance of a contrast-1e4 test
-  // stall in the FP32 recursion: 142 iterations instead of 17)
-  const double delta = (o.inner_tol > 0.0 && o.inner_tol < 1.0) ? o.inner_tol : (mg ? 1e-3 : 1e-2);
+  // auto: 1e-2.  With MG (about a decade per iteration) and blocks of 2 iterations
+  // that keeps the FP32 recursion within about four decades of its last update.
+  // Smaller factors save FP64 updates but were not robust: 1e-3 left zero-start
+  // instances of the 64^3 workload at twice the FP64 iteration count, and 1e-4
+  // let a contrast-1e4 test instance take 142 iterations instead of 17.
+  const double delta = (o.inner_tol > 0.0 && o.inner_tol < 1.0) ? o.inner_tol : 1e-2;
   a.ru_delta2 = delta * delta;
   a.rr_ref = rr_ref;
   a.pending = a.active + 1;

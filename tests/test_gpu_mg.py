@@ -131,3 +131,20 @@ def test_msrb_rejects_mixed_precision():
         with pytest.raises(rbws.RbwsError, match="UNSUPPORTED"):
             rbws.rbws_solve_batch(P.h, np.array([[1.0, 2.0]]), 1e-10, rbws.WARM_ZERO, u,
                                   rbws.rbws_options_default(precond=rbws.PREC_MSRB, precision=rbws.FP32_IR))
+
+
+@pytest.mark.parametrize("warm", [rbws.WARM_ZERO, rbws.WARM_GALERKIN])
+def test_fp32_mgcg_tracks_fp64_mgcg_on_the_64cube_workload(warm):
+    """Every instance of a 64-parameter slice of the 64^3 workload: the FP32 iteration with
+    FP64 reliable updates needs at most 3 iterations more than the FP64 MGCG."""
+    w = inputs.WORKLOADS["c2"]
+    mu = inputs.test_mu(w)[:64]
+    with rbws.Problem(w.grid, w.blocks) as P:
+        rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
+        u = torch.empty((len(mu), P.n), dtype=torch.float64, device="cuda")
+        _, it64, _, st64 = rbws.rbws_solve_batch(P.h, mu, 1e-10, warm, u,
+                                                 rbws.rbws_options_default(precond=rbws.PREC_MG))
+        _, it32, rel, st32 = rbws.rbws_solve_batch(
+            P.h, mu, 1e-10, warm, u, rbws.rbws_options_default(precond=rbws.PREC_MG, precision=rbws.FP32_IR))
+    assert np.all(st64 == 0) and np.all(st32 == 0)
+    assert np.all(it32 <= it64 + 3), (it32 - it64).max()
