@@ -14,6 +14,8 @@ Function map (paper passage -> function):
   Algorithm 5 skeleton (greedy)        greedy()
   Algorithm 4 over a batch             solve_batch()
   Algorithm 2 (MG V-cycle), MGCG       oracle.mg: Hierarchy, vcycle(), mgcg() (numpy/scipy)
+  Sec. 3.1 L1ROC (Algorithm 5, DEIM,   oracle.l1roc: offline(), colloc_solve(), l1_indicator()
+    over-collocation)                    (numpy)
   learned warm start network           mlp_forward(), mlp_loss_grad()
 Parity status: all pinned by CPU tests except trained network weights
 ("parity unpinned": only forward/backward are pinned).
