@@ -61,7 +61,10 @@ typedef enum {
   RBWS_WARM_ZERO = 0,               /* u0 = 0 (the zero-start baseline)           */
   RBWS_WARM_GALERKIN = 1,           /* u0 = W A_N(mu)^{-1} W^T f (Sec. 2.3)       */
   RBWS_WARM_LEARNED = 2,            /* u0 = W c_net(mu), surrogate network          */
-  RBWS_WARM_LEARNED_CORRECTED = 3   /* c_net plus one reduced CG step on A_N c = f_N */
+  RBWS_WARM_LEARNED_CORRECTED = 3,  /* c_net plus one reduced CG step on A_N c = f_N */
+  RBWS_WARM_L1ROC = 4               /* u0 = W c, c = argmin ||P (f - A(mu) W c)||_2 over
+                                       the collocation nodes of rbws_offline_l1roc
+                                       (Sec. 3.1, the paper's RBWS initial value)     */
 } rbws_warm_mode;
 
 /* Preconditioner P of Algorithm 1. */
@@ -206,6 +209,38 @@ RBWS_API rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu,
 RBWS_API rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu, int32_t B,
                                                 const void* x, void* y, int32_t precision,
                                                 void* stream);
+
+/* Offline L1ROC (Sec. 3.1, Algorithm 5): the RB space and the collocation nodes
+ * X^m = X_s u X_r of the over-collocation online solve.
+ *  - First parameter mu_train[0]; each snapshot by Jacobi-PCG to snapshot_tol.
+ *  - DEIM on the snapshots: with the k current vectors and their points, c solves
+ *    W[points] c = u[points]; rho = u - W c; the new point is argmax |rho| (ties:
+ *    the smaller node index) and the new vector rho / rho[point].  The space stops
+ *    growing when max |rho| <= 1e-10 max |u|.
+ *  - From the second snapshot on, DEIM also runs on the RB residual
+ *    f - A(mu) W c(mu) of the new parameter (c from the current online solve),
+ *    adding one residual point; a point already present is kept once.
+ *  - The next parameter maximises the L1 indicator ||T^-1 c(mu)||_1 over the
+ *    training points not yet selected, T upper triangular with U = W T (U the
+ *    snapshots): the L1 norm of the coefficients in the snapshot basis.
+ * The basis (not orthonormal) replaces any previous one; its Galerkin data
+ * (W^T A_q W, W^T f) are formed too, so every warm mode can use it.  n_max <= 64.
+ * selected_out / eta_hist_out: host [n_max] or NULL (eta_hist_out[k] = largest
+ * indicator once the basis has k+1 vectors, NaN if none); n_out: final N. */
+RBWS_API rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, int32_t n_train, int32_t n_max,
+                                        double snapshot_tol, int32_t* selected_out, double* eta_hist_out,
+                                        int32_t* n_out);
+
+/* The collocation data of the L1ROC basis: M_out = number of nodes; points_out
+ * (host [M] or NULL) = their node indices ((z*ny + y)*nx + x) in the order they
+ * were added; T_out (host [N][N] row-major or NULL) = T with U = W T.
+ * RBWS_ERR_NO_BASIS without an L1ROC basis. */
+RBWS_API rbws_status rbws_l1roc_info(rbws_problem p, int32_t* M_out, int64_t* points_out, double* T_out);
+
+/* Online L1ROC solve: c_out (host [B][N]) = argmin ||P (f - A(mu_b) W c)||_2, by
+ * Householder QR on the device.  RBWS_ERR_NO_BASIS without an L1ROC basis,
+ * RBWS_ERR_STATE if a collocation matrix is rank deficient. */
+RBWS_API rbws_status rbws_l1roc_coefficients(rbws_problem p, const double* mu, int32_t B, double* c_out);
 
 /* Error indicators of the offline greedy. */
 typedef enum {

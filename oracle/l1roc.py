@@ -8,8 +8,11 @@ by the product.  Shares no code with the CUDA library.
 Readings where the paper leaves a choice open:
   * first parameter: index 0 of the training set (the paper draws it at random);
   * DEIM(V, v): with V's interpolation points p, c solves V[p] c = v[p]; the residual
-    rho = v - V c vanishes at p; the new point is argmax |rho| (ties: smallest index) and the
-    new vector is rho / rho[point] (one at its own point, zero at the earlier ones);
+    rho = v - V c vanishes at p; the new point is the smallest node index with
+    |rho| >= (1 - 1e-8) max |rho| (near-ties, which mirror symmetries of the grid and the
+    blocks make exact in exact arithmetic, resolve to the smaller index whatever the
+    rounding) and the new vector is rho / rho[point] (one at its own point, zero at the
+    earlier ones);
   * the online problem minimises ||P (b - A W c)||_2 (the paper's "argmax" read as argmin)
     over the points X^m = X_s u X_r, kept in the order they were added; a point found by
     both DEIM processes is kept once;
@@ -55,7 +58,8 @@ def deim_step(V, pts, v):
     else:
         c = np.zeros(0)
         rho = v.copy()
-    x = int(np.argmax(np.abs(rho)))  # first of the largest
+    a = np.abs(rho)
+    x = int(np.flatnonzero(a >= (1.0 - 1e-8) * a.max())[0])  # first of the (near-)largest
     return rho / rho[x], x, c, float(rho[x])
 
 

@@ -144,6 +144,15 @@ struct rbws_problem_s {
   std::vector<uint8_t> h_map;  // explicit subdomain map [n] (empty: block rule)
   std::vector<uint8_t> h_segq; // explicit map: box (bx*by*bz segments) -> subdomain
   uint8_t* d_segq = nullptr;
+  // L1ROC online data (Sec. 3.1): collocation nodes, P A_q W and P f, and T
+  // with U = W T (snapshots U); empty unless the basis came from rbws_offline_l1roc
+  struct L1Roc {
+    int N = 0, M = 0;
+    std::vector<int64_t> pts;
+    std::vector<double> T;        // [N][N], row-major, upper triangular
+    double* d_PAWq = nullptr;     // [Q][M][N]
+    double* d_Pf = nullptr;       // [M]
+  } l1;
   std::unique_ptr<MGPlan> mg;  // multigrid hierarchy, built on first use
   std::string mg_err;
   bool mg_tried = false;
@@ -1159,7 +1168,7 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
     set_error("solve: the MSRB preconditioner runs in FP64 only");
     return RBWS_ERR_UNSUPPORTED;
   }
-  if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_LEARNED_CORRECTED) {
+  if (warm < RBWS_WARM_ZERO || warm > RBWS_WARM_L1ROC) {
     set_error("solve: unknown warm-start mode");
     return RBWS_ERR_INVALID_ARG;
   }
@@ -1176,6 +1185,38 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
 
 // Warm start + PCG for B parameters (host mu) on the problem's current work
 // stream; u: device [B][n].
+// L1ROC online solve (Sec. 3.1): c[b] = argmin ||P (f - A(mu_b) W c)||_2.
+rbws_status l1roc_coefficients(rbws_problem p, const double* d_mu, int B, double** C_out) {
+  if (p->l1.N <= 0 || p->l1.N != p->N) {
+    set_error("no L1ROC basis: run rbws_offline_l1roc first");
+    return RBWS_ERR_NO_BASIS;
+  }
+  int err = 0;
+  double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
+  int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  colloc_ls_prepare();
+  launch_colloc_ls(p->l1.M, p->l1.N, p->Q, p->l1.d_PAWq, p->l1.d_Pf, d_mu, B, C, info, p->cur);
+  p->launches += 1;
+  CK(cudaGetLastError());
+  std::vector<int> h(B);
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  for (int b = 0; b < B; b++)
+    if (h[b]) {
+      set_error("L1ROC: the collocation matrix is rank deficient for instance " + std::to_string(b));
+      return RBWS_ERR_STATE;
+    }
+  *C_out = C;
+  return RBWS_OK;
+}
+
+rbws_status l1roc_start(rbws_problem p, const double* d_mu, int B, double* u, bool fp32) {
+  double* C = nullptr;
+  CKI(l1roc_coefficients(p, d_mu, B, &C));
+  return lift(p, C, B, u, fp32);
+}
+
 rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol, int warm,
                              const rbws_options& o, double* u, std::vector<InstState>& st) {
   if (o.profile) std::memset(o.profile, 0, sizeof(rbws_profile));
@@ -1185,6 +1226,8 @@ rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol
     CK(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)B * p->n, p->cur));
   } else if (warm == RBWS_WARM_GALERKIN) {
     CKI(galerkin_start(p, d_mu, B, u, o.precision == RBWS_FP32_IR));
+  } else if (warm == RBWS_WARM_L1ROC) {
+    CKI(l1roc_start(p, d_mu, B, u, o.precision == RBWS_FP32_IR));
   } else {
     CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED, o.precision == RBWS_FP32_IR));
   }
@@ -1198,6 +1241,160 @@ rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol
 
 __global__ void k_stamp(unsigned long long* t) { *t = global_ns(); }
 void launch_stamp(unsigned long long* t, cudaStream_t s) { k_stamp<<<1, 1, 0, s>>>(t); }
+
+}  // namespace
+
+// ===========================================================================
+// L1ROC offline (Algorithm 5): DEIM on snapshots and on RB residuals, the
+// over-collocation RB system (Sec. 3.1), and the L1 indicator.
+// ===========================================================================
+namespace {
+
+// Solves the k x k system A x = b (row-major, partial pivoting); false if singular.
+bool small_solve(int k, std::vector<double> A, std::vector<double>& b) {
+  for (int c = 0; c < k; c++) {
+    int piv = c;
+    for (int r = c + 1; r < k; r++)
+      if (std::fabs(A[(size_t)r * k + c]) > std::fabs(A[(size_t)piv * k + c])) piv = r;
+    if (!(std::fabs(A[(size_t)piv * k + c]) > 0.0)) return false;
+    if (piv != c) {
+      for (int j = 0; j < k; j++) std::swap(A[(size_t)c * k + j], A[(size_t)piv * k + j]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < k; r++) {
+      const double f = A[(size_t)r * k + c] / A[(size_t)c * k + c];
+      for (int j = c; j < k; j++) A[(size_t)r * k + j] -= f * A[(size_t)c * k + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = k - 1; r >= 0; r--) {
+    double v = b[r];
+    for (int j = r + 1; j < k; j++) v -= A[(size_t)r * k + j] * b[j];
+    b[r] = v / A[(size_t)r * k + r];
+  }
+  return true;
+}
+
+// Device gather X[col * ld + idx] of host lists; returns the values on the host.
+rbws_status gather_host(rbws_problem p, const double* X, int64_t ld, const std::vector<int>& col,
+                        const std::vector<int64_t>& idx, std::vector<double>& out) {
+  const int L = (int)idx.size();
+  out.assign(L, 0.0);
+  if (!L) return RBWS_OK;
+  int err = 0;
+  int* dc = (int*)p->buf("l1_gcol", sizeof(int) * L, &err);
+  int64_t* di = err ? nullptr : (int64_t*)p->buf("l1_gidx", sizeof(int64_t) * L, &err);
+  double* dv = err ? nullptr : (double*)p->buf("l1_gval", sizeof(double) * L, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(dc, col.data(), sizeof(int) * L, cudaMemcpyHostToDevice, p->cur));
+  CK(cudaMemcpyAsync(di, idx.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, p->cur));
+  launch_gather(X, ld, dc, di, L, dv, p->cur);
+  p->launches += 1;
+  CK(cudaMemcpyAsync(out.data(), dv, sizeof(double) * L, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+// One DEIM step on the device vector in slot k of V (ld n): with V's k points,
+// c solves V[pts] c = v[pts]; slot k becomes rho = v - V c; returns the point of
+// the largest |rho| and rho there (slot k is left unscaled).
+rbws_status deim_device(rbws_problem p, double* V, int k, const std::vector<int64_t>& pts, std::vector<double>& c,
+                        int64_t* x, double* sval, double* d_sval) {
+  const int64_t n = p->n;
+  c.assign(k, 0.0);
+  if (k > 0) {
+    std::vector<int> col;
+    std::vector<int64_t> idx;
+    for (int i = 0; i < k; i++)  // V_j at point i (j < k), then v at the points
+      for (int j = 0; j <= k; j++) col.push_back(j), idx.push_back(pts[i]);
+    std::vector<double> g;
+    CKI(gather_host(p, V, n, col, idx, g));
+    std::vector<double> A((size_t)k * k);
+    for (int i = 0; i < k; i++) {
+      for (int j = 0; j < k; j++) A[(size_t)i * k + j] = g[(size_t)i * (k + 1) + j];
+      c[i] = g[(size_t)i * (k + 1) + k];
+    }
+    if (!small_solve(k, A, c)) {
+      set_error("L1ROC: singular DEIM interpolation matrix");
+      return RBWS_ERR_STATE;
+    }
+    int err = 0;
+    double* dc = (double*)p->buf("l1_coef", sizeof(double) * k, &err);
+    if (err) return (rbws_status)err;
+    CK(cudaMemcpyAsync(dc, c.data(), sizeof(double) * k, cudaMemcpyHostToDevice, p->cur));
+    launch_sub_combination(n, k, V, dc, V + (int64_t)k * n, p->cur);
+    p->launches += 1;
+  }
+  int err = 0;
+  const int chunks = 256;
+  double* sv = (double*)p->buf("l1_amax_v", sizeof(double) * chunks, &err);
+  int64_t* si = err ? nullptr : (int64_t*)p->buf("l1_amax_i", sizeof(int64_t) * chunks, &err);
+  int64_t* dx = err ? nullptr : (int64_t*)p->buf("l1_amax_x", sizeof(int64_t), &err);
+  if (err) return (rbws_status)err;
+  launch_argmax_abs(n, V + (int64_t)k * n, sv, si, chunks, dx, d_sval, p->cur);
+  p->launches += 4;
+  CK(cudaMemcpyAsync(x, dx, sizeof(int64_t), cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaMemcpyAsync(sval, d_sval, sizeof(double), cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+// P A_q W (first Nc columns of d_W) and P f at the nodes pts: [Q][M][Nc], [M].
+rbws_status colloc_matrices(rbws_problem p, int Nc, const std::vector<int64_t>& pts, const std::vector<double>& rows,
+                            std::vector<double>& PAWq, std::vector<double>& Pf) {
+  const int M = (int)pts.size(), Q = p->Q;
+  const int64_t nx = p->nx, ny = p->ny, nz = p->nz;
+  static const int off[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  std::vector<int> col;
+  std::vector<int64_t> idx;
+  std::vector<int> cls(M);
+  for (int i = 0; i < M; i++) {
+    const int64_t x = pts[i];
+    const int ix = (int)(x % nx), iy = (int)((x / nx) % ny), iz = (int)(x / (nx * ny));
+    cls[i] = (p->az.cls[iz] * p->ay.ncls() + p->ay.cls[iy]) * p->ax.ncls() + p->ax.cls[ix];
+    for (int j = 0; j < Nc; j++)
+      for (int o = 0; o < 7; o++) {
+        const int jx = ix + off[o][0], jy = iy + off[o][1], jz = iz + off[o][2];
+        const bool in = jx >= 0 && jx < nx && jy >= 0 && jy < ny && jz >= 0 && jz < nz;
+        col.push_back(j);
+        idx.push_back(in ? ((int64_t)jz * ny + jy) * nx + jx : -1);
+      }
+  }
+  std::vector<double> g;
+  CKI(gather_host(p, p->d_W, p->n, col, idx, g));
+  const int ncls = p->ax.ncls() * p->ay.ncls() * p->az.ncls();
+  PAWq.assign((size_t)Q * M * Nc, 0.0);
+  for (int q = 0; q < Q; q++)
+    for (int i = 0; i < M; i++) {
+      const double* row = &rows[((size_t)q * ncls + cls[i]) * 27];
+      for (int j = 0; j < Nc; j++) {
+        double v = 0.0;
+        for (int o = 0; o < 7; o++) {
+          const double a = row[(off[o][2] + 1) * 9 + (off[o][1] + 1) * 3 + off[o][0] + 1];
+          v += a * g[((size_t)i * Nc + j) * 7 + o];
+        }
+        PAWq[((size_t)q * M + i) * Nc + j] = v;
+      }
+    }
+  Pf.assign(M, 1.0);
+  if (p->d_f) {
+    std::vector<int> c0(M, 0);
+    CKI(gather_host(p, p->d_f, 0, c0, pts, Pf));
+  }
+  return RBWS_OK;
+}
+
+// Uploads P A_q W and P f into the problem's L1ROC state (device).
+rbws_status colloc_upload(rbws_problem p, int Nc, const std::vector<double>& PAWq, const std::vector<double>& Pf) {
+  int err = 0;
+  double* a = (double*)p->buf("l1_PAWq", sizeof(double) * PAWq.size(), &err);
+  double* f = err ? nullptr : (double*)p->buf("l1_Pf", sizeof(double) * Pf.size(), &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(a, PAWq.data(), sizeof(double) * PAWq.size(), cudaMemcpyHostToDevice, p->cur));
+  CK(cudaMemcpyAsync(f, Pf.data(), sizeof(double) * Pf.size(), cudaMemcpyHostToDevice, p->cur));
+  (void)Nc;
+  return RBWS_OK;
+}
 
 }  // namespace
 
@@ -1389,6 +1586,8 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_W32);
   cudaFree(p->d_ANq);
   cudaFree(p->d_fN);
+  cudaFree(p->l1.d_PAWq);
+  cudaFree(p->l1.d_Pf);
   cudaFree(p->d_w32);
   cudaFree(p->d_w16);
   cudaFree(p->d_cscale);
@@ -1496,6 +1695,7 @@ rbws_status rbws_set_basis(rbws_problem p, int32_t N, const double* W, const dou
   cudaFree(p->d_fN);
   p->d_W = p->d_ANq = p->d_fN = nullptr;
   p->d_W32 = nullptr;
+  p->l1.N = p->l1.M = 0;  // collocation data belongs to the basis it was built with
   p->N = 0;
   CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)N * p->n));
   CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)p->Q * N * N));
@@ -1578,6 +1778,7 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   cudaFree(p->d_fN);
   p->d_W = p->d_ANq = p->d_fN = nullptr;
   p->d_W32 = nullptr;
+  p->l1.N = p->l1.M = 0;  // collocation data belongs to the basis it was built with
   p->N = 0;
   CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)n_max * n));
   CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)Q * n_max * n_max));
@@ -1725,6 +1926,244 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   if (eta_hist_out) std::copy(hist.begin(), hist.end(), eta_hist_out);
   if (n_out) *n_out = N;
   // compact A_N^q to [Q][N][N] on the device (already done above)
+  return RBWS_OK;
+}
+
+rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, int32_t n_train, int32_t n_max,
+                               double snapshot_tol, int32_t* selected_out, double* eta_hist_out, int32_t* n_out) {
+  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > kL1RocMaxN || !(snapshot_tol > 0.0)) {
+    set_error("rbws_offline_l1roc: invalid argument (1 <= n_max <= 64, snapshot_tol > 0)");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  cudaStream_t s = p->cur;
+  const int64_t n = p->n;
+  const int Q = p->Q;
+  int err = 0;
+  cudaStreamSynchronize(s);
+  cudaFree(p->d_W);
+  cudaFree(p->d_W32);
+  cudaFree(p->d_ANq);
+  cudaFree(p->d_fN);
+  p->d_W = p->d_ANq = p->d_fN = nullptr;
+  p->d_W32 = nullptr;
+  p->N = 0;
+  p->l1.N = p->l1.M = 0;
+  CK(cudaMalloc(&p->d_W, sizeof(double) * (size_t)(n_max + 1) * n));  // one spare slot for DEIM
+  CK(cudaMalloc(&p->d_ANq, sizeof(double) * (size_t)Q * n_max * n_max));
+  CK(cudaMalloc(&p->d_fN, sizeof(double) * (size_t)n_max));
+  colloc_ls_prepare();
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu_train, n_train, &d_mu, "mu_train"));
+  double* R = (double*)p->buf("l1_R", sizeof(double) * (size_t)(n_max + 1) * n, &err);  // residual DEIM basis
+  double* r = err ? nullptr : (double*)p->buf("l1_r", sizeof(double) * n, &err);
+  double* d_s = err ? nullptr : (double*)p->buf("l1_s", sizeof(double), &err);
+  double* dT = err ? nullptr : (double*)p->buf("l1_T", sizeof(double) * (size_t)n_max * n_max, &err);
+  double* Cd = err ? nullptr : (double*)p->buf("l1_C", sizeof(double) * (size_t)n_train * n_max, &err);
+  int* info = err ? nullptr : (int*)p->buf("l1_info", sizeof(int) * (size_t)n_train, &err);
+  double* etad = err ? nullptr : (double*)p->buf("l1_eta", sizeof(double) * (size_t)n_train, &err);
+  double* rel = err ? nullptr : (double*)p->buf("l1_rel", sizeof(double), &err);
+  if (err) return (rbws_status)err;
+  const std::vector<double> rows =
+      fine_rows_q(p->ax, p->ay, p->az, p->bx, p->by, p->h_segq.empty() ? nullptr : p->h_segq.data(), Q, p->sx,
+                  p->sy, p->sz);
+  std::vector<int64_t> pts_s, pts_r, pts;
+  std::vector<double> T((size_t)n_max * n_max, 0.0), PAWq, Pf;
+  std::vector<int32_t> sel(n_max, -1);
+  std::vector<double> hist(n_max, NAN), eta(n_train);
+  std::vector<char> taken(n_train, 0);
+  rbws_options o;
+  rbws_options_default(&o);
+  o.max_iters = 1000000;
+  o.precond = RBWS_PREC_JACOBI;
+  int N = 0, nr = 0, next = 0;
+  double fmax = 1.0;
+  if (p->d_f) {
+    int64_t xi;
+    double* scratch = (double*)p->buf("l1_fmax", sizeof(double), &err);
+    if (err) return (rbws_status)err;
+    CK(cudaMemcpyAsync(R, p->d_f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> dummy;
+    CKI(deim_device(p, R, 0, {}, dummy, &xi, &fmax, scratch));
+    fmax = std::fabs(fmax);
+  }
+  while (N < n_max) {
+    // snapshot u(mu_next) by Jacobi-PCG from zero, into slot N of W
+    double* wN = p->d_W + (int64_t)N * n;
+    std::vector<InstState> st;
+    CK(cudaMemsetAsync(wN, 0, sizeof(double) * n, s));
+    CKI(solve_fp64(p, d_mu + (int64_t)next * Q, 1, snapshot_tol, o, wN, st));
+    if (st[0].status != ST_CONVERGED && !(st[0].status == ST_MAX_ITERS && st[0].relres < 1e-9)) {
+      set_error("rbws_offline_l1roc: snapshot solve did not converge (relative residual " +
+                std::to_string(st[0].relres) + ")");
+      return RBWS_ERR_STATE;
+    }
+    // the snapshot's largest entry (for the breakdown test), then DEIM against W
+    int64_t xu;
+    double umax, sN;
+    std::vector<double> dummy, c;
+    CKI(deim_device(p, wN, 0, {}, dummy, &xu, &umax, d_s));  // slot N seen alone: max |u|
+    int64_t x;
+    {
+      // deim_device with k = N reads slot N as v and leaves rho there
+      std::vector<int64_t> ps(pts_s.begin(), pts_s.end());
+      CKI(deim_device(p, p->d_W, N, ps, c, &x, &sN, d_s));
+    }
+    if (!(std::fabs(sN) > 1e-10 * std::fabs(umax))) break;  // the snapshot adds nothing new
+    std::vector<int64_t> new_pts{x};
+    if (N > 0) {
+      // the RB residual of the new parameter with the current space, then its DEIM point
+      launch_colloc_ls((int)pts.size(), N, Q, (const double*)p->buf("l1_PAWq", 0, &err),
+                       (const double*)p->buf("l1_Pf", 0, &err), d_mu + (int64_t)next * Q, 1, Cd, info, s);
+      launch_lift(n, N, p->d_W, Cd, 1, r, s);
+      double* cc = nullptr;
+      CKI(coef_tables(p, d_mu + (int64_t)next * Q, 1, &cc, nullptr));
+      double* rslot = R + (int64_t)nr * n;
+      CKI(residual_norms(p, cc, 1, r, rslot, rel));
+      p->launches += 2;
+      double sr;
+      int64_t xr;
+      std::vector<double> cr;
+      CKI(deim_device(p, R, nr, pts_r, cr, &xr, &sr, d_s));
+      if (std::fabs(sr) > 1e-10 * fmax) {
+        launch_scale_inv(n, d_s, rslot, s);
+        p->launches += 1;
+        pts_r.push_back(xr);
+        nr++;
+        new_pts.push_back(xr);
+      }
+    }
+    // the new basis vector: rho / rho[x] (d_s was overwritten by the residual's DEIM)
+    CK(cudaMemcpyAsync(d_s, &sN, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_inv(n, d_s, wN, s);
+    p->launches += 1;
+    for (int i = 0; i < N; i++) T[(size_t)i * n_max + N] = c[i];
+    T[(size_t)N * n_max + N] = sN;
+    pts_s.push_back(x);
+    for (int64_t q : new_pts)
+      if (std::find(pts.begin(), pts.end(), q) == pts.end()) pts.push_back(q);
+    sel[N] = next;
+    taken[next] = 1;
+    N++;
+    CKI(colloc_matrices(p, N, pts, rows, PAWq, Pf));
+    CKI(colloc_upload(p, N, PAWq, Pf));
+    bool all = true;
+    for (int t = 0; t < n_train; t++) all = all && taken[t];
+    if (all) break;
+    // L1 indicator over the training set: collocation solves, then ||T^-1 c||_1
+    CK(cudaMemcpyAsync(dT, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, s));
+    launch_colloc_ls((int)pts.size(), N, Q, (const double*)p->buf("l1_PAWq", 0, &err),
+                     (const double*)p->buf("l1_Pf", 0, &err), d_mu, n_train, Cd, info, s);
+    launch_l1_indicator(N, n_max, dT, Cd, info, n_train, etad, s);
+    p->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(eta.data(), etad, sizeof(double) * n_train, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double best = -1.0;
+    next = -1;
+    for (int t = 0; t < n_train; t++)
+      if (!taken[t] && eta[t] > best) {
+        best = eta[t];
+        next = t;
+      }
+    hist[N - 1] = best;
+    if (next < 0) break;
+  }
+  if (N == 0) {
+    set_error("rbws_offline_l1roc: no basis vector was added");
+    return RBWS_ERR_STATE;
+  }
+  // Galerkin data of the same basis (W^T A_q W, W^T f), so that every warm mode works with it
+  {
+    double* V = (double*)p->buf("g_V", sizeof(double) * (size_t)Q * n, &err);
+    double* dots = err ? nullptr : (double*)p->buf("g_dots", sizeof(double) * (size_t)(Q + 1) * (n_max + 1), &err);
+    const int scratch_len = 256 * (n_max + 2);
+    double* scratch = err ? nullptr : (double*)p->buf("g_scratch", sizeof(double) * scratch_len, &err);
+    double* eye = err ? nullptr : (double*)p->buf("g_eye", sizeof(double) * (size_t)Q * Q, &err);
+    if (err) return (rbws_status)err;
+    std::vector<double> I((size_t)Q * Q, 0.0);
+    for (int q = 0; q < Q; q++) I[(size_t)q * Q + q] = 1.0;
+    CK(cudaMemcpyAsync(eye, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, s));
+    double* c64 = nullptr;
+    CKI(coef_tables(p, eye, Q, &c64, nullptr));
+    const double* fvec = p->d_f ? p->d_f : p->d_ones;
+    std::vector<double> A((size_t)Q * N * N), fN(N), hd((size_t)Q * N);
+    for (int j = 0; j < N; j++) {
+      launch_apply<double>(p->geo, choose_tile(p->nx), c64, Q, p->d_W + (int64_t)j * n, 0, V, s);
+      for (int q = 0; q < Q; q++)
+        launch_multi_dot(n, N, p->d_W, n, V + (int64_t)q * n, dots + (int64_t)q * N, scratch, scratch_len, s);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int q = 0; q < Q; q++)
+        for (int i = 0; i < N; i++) A[((size_t)q * N + i) * N + j] = hd[(size_t)q * N + i];
+    }
+    launch_multi_dot(n, N, p->d_W, n, fvec, dots, scratch, scratch_len, s);
+    CK(cudaMemcpyAsync(fN.data(), dots, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // symmetrise the rounding (A_N^q is symmetric)
+    for (int q = 0; q < Q; q++)
+      for (int i = 0; i < N; i++)
+        for (int j = 0; j < i; j++) {
+          double& a = A[((size_t)q * N + i) * N + j];
+          double& b = A[((size_t)q * N + j) * N + i];
+          a = b = 0.5 * (a + b);
+        }
+    p->h_ANq = A;
+    p->h_fN = fN;
+    CK(cudaMemcpyAsync(p->d_ANq, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->d_fN, fN.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    p->launches += 2 * N + N * Q + 2;
+  }
+  p->N = N;
+  // the online L1ROC data of the final basis
+  p->l1.N = N;
+  p->l1.M = (int)pts.size();
+  p->l1.pts = pts;
+  p->l1.T.assign((size_t)N * N, 0.0);
+  for (int i = 0; i < N; i++)
+    for (int j = 0; j < N; j++) p->l1.T[(size_t)i * N + j] = T[(size_t)i * n_max + j];
+  cudaFree(p->l1.d_PAWq);
+  cudaFree(p->l1.d_Pf);
+  p->l1.d_PAWq = p->l1.d_Pf = nullptr;
+  CK(cudaMalloc(&p->l1.d_PAWq, sizeof(double) * PAWq.size()));
+  CK(cudaMalloc(&p->l1.d_Pf, sizeof(double) * Pf.size()));
+  CK(cudaMemcpyAsync(p->l1.d_PAWq, PAWq.data(), sizeof(double) * PAWq.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->l1.d_Pf, Pf.data(), sizeof(double) * Pf.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (selected_out) std::copy(sel.begin(), sel.end(), selected_out);
+  if (eta_hist_out) std::copy(hist.begin(), hist.end(), eta_hist_out);
+  if (n_out) *n_out = N;
+  return RBWS_OK;
+}
+
+rbws_status rbws_l1roc_info(rbws_problem p, int32_t* M_out, int64_t* points_out, double* T_out) {
+  if (!p) {
+    set_error("rbws_l1roc_info: null problem");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->l1.N <= 0) {
+    set_error("rbws_l1roc_info: no L1ROC basis (run rbws_offline_l1roc)");
+    return RBWS_ERR_NO_BASIS;
+  }
+  if (M_out) *M_out = p->l1.M;
+  if (points_out) std::copy(p->l1.pts.begin(), p->l1.pts.end(), points_out);
+  if (T_out) std::copy(p->l1.T.begin(), p->l1.T.end(), T_out);
+  return RBWS_OK;
+}
+
+rbws_status rbws_l1roc_coefficients(rbws_problem p, const double* mu, int32_t B, double* c_out) {
+  if (!p || !mu || !c_out || B < 1 || B > 65535) {
+    set_error("rbws_l1roc_coefficients: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_l1roc"));
+  double* C = nullptr;
+  CKI(l1roc_coefficients(p, d_mu, B, &C));
+  CK(cudaMemcpyAsync(c_out, C, sizeof(double) * (size_t)B * p->l1.N, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
   return RBWS_OK;
 }
 

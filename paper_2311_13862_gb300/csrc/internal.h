@@ -27,6 +27,7 @@ namespace rbws {
 constexpr int kCoefStride = 8;  // values per class entry
 constexpr int kMaxQ = 64;
 constexpr int kMaxAxis = 1024;
+constexpr int kL1RocMaxN = 64;  // L1ROC basis size limit (collocation solve in shared memory)
 constexpr int kMaxClassPerAxis = 3 * 16 + 2;
 
 struct AxisClasses {
@@ -388,6 +389,30 @@ size_t mg_fine_coarse_smem(Tile t, int zc);
 void mg_fine_prepare();
 // y = D^-1 x on the FP64 level view L (instances all active).
 void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// L1ROC (l1roc.cu): DEIM point search, gathers, over-collocation least squares
+// ---------------------------------------------------------------------------
+// (index, signed value) of the first entry of x whose magnitude is within a
+// factor 1 - 1e-8 of the largest (near-ties: the smaller index); scratch of
+// `chunks` entries each.
+void launch_argmax_abs(int64_t n, const double* x, double* scratch_v, int64_t* scratch_i, int chunks,
+                       int64_t* out_idx, double* out_val, cudaStream_t s);
+// out[t] = X[col[t] * ld + idx[t]] (0 where idx[t] < 0), t < L.
+void launch_gather(const double* X, int64_t ld, const int* col, const int64_t* idx, int L, double* out,
+                   cudaStream_t s);
+// c[b] = argmin ||sum_q mu[b][q] PAWq[q] c - Pf||_2 (PAWq [Q][M][N] row-major) by
+// Householder QR, one CTA per instance; info[b] = 1 on rank deficiency.  Needs
+// colloc_ls_smem(M, N) bytes of shared memory (colloc_ls_prepare raises the limit).
+size_t colloc_ls_smem(int M, int N);
+void colloc_ls_prepare();
+void launch_colloc_ls(int M, int N, int Q, const double* PAWq, const double* Pf, const double* mu, int B, double* c,
+                      int* info, cudaStream_t s);
+
+// Rows of each affine term on the finest grid by class: [Q][ncls][27] (offset
+// (dz+1)*9 + (dy+1)*3 + dx+1; kappa = e_q), as the coefficient tables form them.
+std::vector<double> fine_rows_q(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az, int bx, int by,
+                                const uint8_t* segq, int Q, double sx, double sy, double sz);
 
 // ---------------------------------------------------------------------------
 // Operator apply with static scratch (static_scratch.cu)

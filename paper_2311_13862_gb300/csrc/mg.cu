@@ -78,6 +78,41 @@ std::vector<int> representatives(const std::vector<uint8_t>& cls, int ncls) {
 
 }  // namespace
 
+std::vector<double> fine_rows_q(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az, int bx, int by,
+                                const uint8_t* segq, int Q, double sx, double sy, double sz) {
+  const int ncx = ax.ncls(), ncy = ay.ncls(), ncz = az.ncls();
+  std::vector<double> tq((size_t)Q * ncx * ncy * ncz * 27, 0.0);
+  for (int q = 0; q < Q; q++)
+    for (int czi = 0; czi < ncz; czi++)
+      for (int cyi = 0; cyi < ncy; cyi++)
+        for (int cxi = 0; cxi < ncx; cxi++) {
+          const int ox = ax.key[3 * cxi], lx = ax.key[3 * cxi + 1], hx = ax.key[3 * cxi + 2];
+          const int oy = ay.key[3 * cyi], ly = ay.key[3 * cyi + 1], hy = ay.key[3 * cyi + 2];
+          const int oz = az.key[3 * czi], lz = az.key[3 * czi + 1], hz = az.key[3 * czi + 2];
+          auto kap = [&](int a, int b, int c) {
+            const int box = (c * by + b) * bx + a;
+            return (segq ? segq[box] : box) == q ? 1.0 : 0.0;
+          };
+          const double kc = kap(ox, oy, oz);
+          auto face = [&](int nb, double knb, double s) { return nb >= 0 ? 0.5 * (kc + knb) * s : kc * s; };
+          const double kW = face(lx, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx);
+          const double kE = face(hx, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx);
+          const double kS = face(ly, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy);
+          const double kN = face(hy, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy);
+          const double kD = face(lz, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz);
+          const double kU = face(hz, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz);
+          double* row = &tq[(((size_t)q * ncz + czi) * ncy + cyi) * ncx * 27 + (size_t)cxi * 27];
+          row[off27(0, 0, 0)] = kW + kE + kS + kN + kD + kU;
+          row[off27(-1, 0, 0)] = -kW;
+          row[off27(1, 0, 0)] = -kE;
+          row[off27(0, -1, 0)] = -kS;
+          row[off27(0, 1, 0)] = -kN;
+          row[off27(0, 0, -1)] = -kD;
+          row[off27(0, 0, 1)] = -kU;
+        }
+  return tq;
+}
+
 MGPlan::~MGPlan() {
   for (auto p : d_cls) cudaFree(p);
   for (auto p : d_tq) cudaFree(p);
@@ -108,35 +143,7 @@ std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const Ax
   F.n = (int64_t)F.nx * F.ny * F.nz;
   F.cx = ax.cls, F.cy = ay.cls, F.cz = az.cls;
   F.ncx = ax.ncls(), F.ncy = ay.ncls(), F.ncz = az.ncls();
-  F.tq.assign((size_t)Q * F.ncls() * 27, 0.0);
-  for (int q = 0; q < Q; q++)
-    for (int czi = 0; czi < F.ncz; czi++)
-      for (int cyi = 0; cyi < F.ncy; cyi++)
-        for (int cxi = 0; cxi < F.ncx; cxi++) {
-          const int ox = ax.key[3 * cxi], lx = ax.key[3 * cxi + 1], hx = ax.key[3 * cxi + 2];
-          const int oy = ay.key[3 * cyi], ly = ay.key[3 * cyi + 1], hy = ay.key[3 * cyi + 2];
-          const int oz = az.key[3 * czi], lz = az.key[3 * czi + 1], hz = az.key[3 * czi + 2];
-          auto kap = [&](int a, int b, int c) {
-            const int box = (c * by + b) * bx + a;
-            return (segq ? segq[box] : box) == q ? 1.0 : 0.0;
-          };
-          const double kc = kap(ox, oy, oz);
-          auto face = [&](int nb, double knb, double s) { return nb >= 0 ? 0.5 * (kc + knb) * s : kc * s; };
-          const double kW = face(lx, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx);
-          const double kE = face(hx, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx);
-          const double kS = face(ly, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy);
-          const double kN = face(hy, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy);
-          const double kD = face(lz, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz);
-          const double kU = face(hz, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz);
-          double* row = &F.tq[(((size_t)q * F.ncz + czi) * F.ncy + cyi) * F.ncx * 27 + (size_t)cxi * 27];
-          row[off27(0, 0, 0)] = kW + kE + kS + kN + kD + kU;
-          row[off27(-1, 0, 0)] = -kW;
-          row[off27(1, 0, 0)] = -kE;
-          row[off27(0, -1, 0)] = -kS;
-          row[off27(0, 1, 0)] = -kN;
-          row[off27(0, 0, -1)] = -kD;
-          row[off27(0, 0, 1)] = -kU;
-        }
+  F.tq = fine_rows_q(ax, ay, az, bx, by, segq, Q, sx, sy, sz);
   // coarse levels: classes and Galerkin rows from the next finer level
   for (int i = plan->J - 1; i >= 0; i--) {
     const MGPlan::Level& f = plan->lv[i + 1];

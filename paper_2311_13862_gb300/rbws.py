@@ -21,7 +21,7 @@ RBWS_WARN_NOT_CONVERGED = 1
 STATUS_NAMES = {0: "OK", 1: "WARN_NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
                 -4: "ERR_NO_BASIS", -5: "ERR_NOT_SPD", -6: "ERR_DEVICE_TIMEOUT", -7: "ERR_STATE",
                 -8: "ERR_UNSUPPORTED"}
-WARM_ZERO, WARM_GALERKIN, WARM_LEARNED, WARM_LEARNED_CORRECTED = 0, 1, 2, 3
+WARM_ZERO, WARM_GALERKIN, WARM_LEARNED, WARM_LEARNED_CORRECTED, WARM_L1ROC = 0, 1, 2, 3, 4
 PREC_NONE, PREC_JACOBI, PREC_MSRB, PREC_MG = 0, 1, 2, 3
 FP64, FP32_IR = 0, 1
 
@@ -72,6 +72,9 @@ def _lib():
         L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_apply_preconditioner.argtypes = [P, P, i32, i32, P, P, P]
+        L.rbws_offline_l1roc.argtypes = [P, P, i32, i32, d, P, P, C.POINTER(i32)]
+        L.rbws_l1roc_info.argtypes = [P, C.POINTER(i32), P, P]
+        L.rbws_l1roc_coefficients.argtypes = [P, P, i32, P]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, i32, P, P, C.POINTER(i32)]
         L.rbws_set_basis.argtypes = [P, i32, P, P, P]
@@ -92,7 +95,8 @@ def _lib():
                      "rbws_offline_greedy", "rbws_set_basis", "rbws_get_basis", "rbws_reduced_solve",
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
                      "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
-                     "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load", "rbws_apply_preconditioner"):
+                     "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load", "rbws_apply_preconditioner",
+                     "rbws_offline_l1roc", "rbws_l1roc_info", "rbws_l1roc_coefficients"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -179,6 +183,37 @@ def rbws_apply_operator_static(h, mu, x, y, precision=FP64, stream=None):
 
 
 INDICATOR_RESIDUAL, INDICATOR_L1 = 0, 1
+
+
+def rbws_offline_l1roc(h, mu_train, n_max, snapshot_tol=1e-12):
+    """Offline L1ROC (Algorithm 5): returns (N, selected [n_max], eta_hist [n_max])."""
+    mu = _host(np.atleast_2d(mu_train))
+    sel = np.full(n_max, -1, dtype=np.int32)
+    eta = np.full(n_max, np.nan)
+    n_out = C.c_int32(0)
+    _check(_lib().rbws_offline_l1roc(h, _hp(mu), mu.shape[0], n_max, snapshot_tol, _hp(sel), _hp(eta),
+                                     C.byref(n_out)), "rbws_offline_l1roc")
+    return n_out.value, sel, eta
+
+
+def rbws_l1roc_info(h):
+    """(collocation node indices [M], T [N][N]) of the L1ROC basis."""
+    _, _, N = rbws_problem_info(h)
+    M = C.c_int32(0)
+    _check(_lib().rbws_l1roc_info(h, C.byref(M), None, None), "rbws_l1roc_info")
+    pts = np.zeros(M.value, dtype=np.int64)
+    T = np.zeros((N, N))
+    _check(_lib().rbws_l1roc_info(h, C.byref(M), _hp(pts), _hp(T)), "rbws_l1roc_info")
+    return pts, T
+
+
+def rbws_l1roc_coefficients(h, mu):
+    """Online L1ROC coefficients c [B][N]."""
+    mu = _host(np.atleast_2d(mu))
+    _, _, N = rbws_problem_info(h)
+    c = np.empty((mu.shape[0], N))
+    _check(_lib().rbws_l1roc_coefficients(h, _hp(mu), mu.shape[0], _hp(c)), "rbws_l1roc_coefficients")
+    return c
 
 
 def rbws_offline_greedy(h, mu_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12, indicator=INDICATOR_RESIDUAL):
