@@ -451,10 +451,22 @@ def main():
         arm_list += [("mgcg_zero_fp64", rbws.WARM_ZERO, rbws.FP64), ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, rbws.FP64),
                      ("mgcg_zero_fp32ir", rbws.WARM_ZERO, rbws.FP32_IR),
                      ("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN, rbws.FP32_IR)]
-    precond_of = {"msrb_fp64": rbws.PREC_MSRB}
+    if args.arm_steps > 0:
+        # the paper's own RBWS start: L1ROC (DEIM points, over-collocation), then MGCG; its offline
+        # greedy replaces the Galerkin basis, so this arm runs last
+        arm_list.append(("l1roc_mgcg_fp32ir", rbws.WARM_L1ROC, rbws.FP32_IR))
+    precond_of = {"msrb_fp64": rbws.PREC_MSRB, "l1roc_mgcg_fp32ir": rbws.PREC_MG}
     precond_of.update({k: rbws.PREC_MG for k in ("mgcg_zero_fp64", "mgcg_galerkin_fp64", "mgcg_zero_fp32ir",
                                                 "mgcg_galerkin_fp32ir")})
+    l1roc_off = None
     for name, warm, pr in arm_list:
+        if name == "l1roc_mgcg_fp32ir":
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            N1, _, eta1 = rbws.rbws_offline_l1roc(P.h, inputs.train_mu(w), w.n_max, 1e-12)
+            torch.cuda.synchronize()
+            l1roc_off = {"t_off_s": time.perf_counter() - t0, "N": int(N1),
+                         "collocation_points": int(len(rbws.rbws_l1roc_info(P.h)[0]))}
         if name == head_name:
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
         else:
@@ -569,7 +581,7 @@ def main():
             "e2e": {"value": B * world / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(B * w.Q * 8),
                     "d2h_bytes_per_step": int(B * P.n * 8 + B * (4 + 8 + 4))},
-            "arms": arms, "learned_training": learned, "autotune": tuned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "arms": arms, "l1roc_offline": l1roc_off, "learned_training": learned, "autotune": tuned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
             "iters_mean": float(np.mean(it)), "relres_max": float(np.max(rel))}
     if "zero_fp64" in arms:
         line["speedup_vs_zero_fp64"] = value / arms["zero_fp64"]["solves_per_s"]
