@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "converged solves/s at rel-res 1e-10, warm vs zero start; stencil % of HBM BW"
 UNIT = "solves/s"
 WORKLOAD = ("64^3 interior grid (262,144 DoFs), 2x2x1 blocks (p=4), mu log-uniform in [0.1,10]^4, "
-            "RB N<=20 by greedy over 256 training mu, 256 test mu per step, Jacobi-PCG to rel-res 1e-10")
+            "RB N<=20 by greedy over 256 training mu, 256 test mu per step, PCG to rel-res 1e-10 "
+            "(preconditioner in 'precond': MG V-cycle, or Jacobi as in the Jacobi-PCG arms)")
 FALLBACK_HBM = 6800.0
 
 
