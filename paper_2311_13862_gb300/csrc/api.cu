@@ -775,15 +775,12 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     phase_b_core(aa, par, ss);
     if (mg) mg_launches = mg_apply(aa, par ^ 1, ss);
   };
-  int* upd_mask = nullptr;  // set below: instances taking a reliable update
+  // With MG the V-cycle of a block's last iteration is deferred to the start of
+  // the next block (slot 0), after any reliable update: an instance whose FP32
+  // residual is replaced then takes one V-cycle, on its new residual, not two.
   auto reset = [&](const CGArgs<float>& aa, int start, cudaStream_t ss) {
     if (v4) launch_ru_reset_v4(aa, t, start, ss);
     else launch_ru_reset(aa, t, start, ss);
-    if (mg) {  // the reset instances need s = MG(r) and rho again
-      mgb.mask = upd_mask;
-      mg_apply(aa, 0, ss);
-      mgb.mask = nullptr;
-    }
   };
   cudaStream_t s = p->cur;
   int err = 0;
@@ -814,7 +811,6 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.u64 = u;
   a.r64 = r64;
   a.rel64 = rel;
-  upd_mask = upd;
   if (mg) {
     CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
     if (v4) {
@@ -860,9 +856,11 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   cudaError_t ce;
   if (!prof) {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    if (mg) mg_launches = mg_apply(a, 0, s);  // the previous block's last preconditioning
     for (int k = 0; k < M; k++) {
       phase_a(a, k & 1, s);
-      phase_b(a, k & 1, s);
+      if (mg && k == M - 1) phase_b_core(a, k & 1, s);
+      else phase_b(a, k & 1, s);
     }
     cudaMemsetAsync(a.pending, 0, sizeof(int), s);
     launch_ru_decide(a, s);
@@ -890,7 +888,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
       reset(a, 0, s);
       CK(cudaMemsetAsync(a.pending, 0, sizeof(int), s));
-      p->launches += 4 + mg_launches;
+      p->launches += 4;
       continue;
     }
     if (active == 0) break;
@@ -900,6 +898,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
         break;
       }
     } else {
+      if (mg) mg_launches = mg_apply(a, 0, s);
       cudaEventRecord(p->tev[0], s);
       phase_a(a, 0, s);
       cudaEventRecord(p->tev[1], s);
@@ -913,7 +912,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       cudaEventRecord(p->tev[3], s);
       for (int k = 1; k < M; k++) {
         phase_a(a, k & 1, s);
-        phase_b(a, k & 1, s);
+        if (mg && k == M - 1) phase_b_core(a, k & 1, s);
+        else phase_b(a, k & 1, s);
       }
       cudaMemsetAsync(a.pending, 0, sizeof(int), s);
       launch_ru_decide(a, s);
