@@ -491,9 +491,12 @@ __global__ void k_mg_dense_apply(int n0, const T* __restrict__ ainv, const InstS
 }
 
 // Coarse-level fused steps (27-point Galerkin rows): one thread per (x, y)
-// column marching through a chunk of z planes; planes are staged with their
-// x/y halo in a 4-slot shared-memory ring.  The staged field is xin (kStage
-// 0), omega D^-1 rhs (1) or xin + P e (2); the output a damped Jacobi step
+// column of a tile, marching through a chunk of z planes.  Every plane of the
+// chunk (with its x/y halo and the planes either side) is staged in shared
+// memory at once, so the loads of a whole chunk are in flight together; the
+// march keeps the 3 x 3 neighbourhoods of three planes in registers.  The
+// staged field is xin (kStage 0), omega D^-1 rhs (1) or xin + P e (2, e staged
+// first over the chunk's coarse footprint); the output a damped Jacobi step
 // (kOut 0) or the residual rhs - A x (kOut 1) -- as on the finest level.
 // Interpolation weights along one axis (registers only): fine node j of an
 // axis with m coarse nodes takes coarse k0 (w0) and, if k1 >= 0, k1 (w1).
@@ -514,25 +517,14 @@ __device__ __forceinline__ Pw pweight(int j, int m) {
   return r;
 }
 
-template <typename T>
-__device__ __forceinline__ T prolong_node(const T* __restrict__ e, int cnx, int cny, int cnz, int i, int j, int k) {
-  const Pw rx = pweight(i, cnx), ry = pweight(j, cny), rz = pweight(k, cnz);
-  T v = T(0);
-#pragma unroll
-  for (int c = 0; c < 2; c++) {
-    const int kz = c ? rz.k1 : rz.k0;
-    if (kz < 0) continue;
-#pragma unroll
-    for (int bq = 0; bq < 2; bq++) {
-      const int ky = bq ? ry.k1 : ry.k0;
-      if (ky < 0) continue;
-      const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
-      const T* row = e + ((int64_t)kz * cny + ky) * cnx;
-      if (rx.k0 >= 0) v = fma((T)(wyz * rx.w0), row[rx.k0], v);
-      if (rx.k1 >= 0) v = fma((T)(wyz * rx.w1), row[rx.k1], v);
-    }
-  }
-  return v;
+__device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+
+// Shared memory of one fused coarse step (elements): the staged planes z0-1 ..
+// z1 with their x/y halo, the right-hand side of the own nodes, and (kStage 2)
+// the coarse correction over the chunk's footprint.
+__host__ __device__ inline int64_t coarse_smem_elems(int TX, int TY, int zc, bool with_e) {
+  const int64_t st = (int64_t)(zc + 2) * (TX + 2) * (TY + 2) + (int64_t)zc * TX * TY;
+  return st + (with_e ? (int64_t)(TX / 2 + 3) * (TY / 2 + 3) * (zc / 2 + 3) : 0);
 }
 
 template <typename T, int kStage, int kOut>
@@ -545,82 +537,128 @@ __global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* _
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int b = blockIdx.z;
   if (mg_skip(st, mask, b)) return;
-  const int TX = blockDim.x, TY = blockDim.y;
+  const int TX = blockDim.x, TY = blockDim.y, NT = TX * TY;
+  const int tid = (int)threadIdx.y * TX + (int)threadIdx.x;
   const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
-  const int z0 = blockIdx.y * zc, z1 = min(L.nz, z0 + zc);
-  const int PW = TX + 2, PS = PW * (TY + 2);
+  const int z0 = blockIdx.y * zc, z1 = min(L.nz, z0 + zc), nzl = z1 - z0;
+  const int PW = TX + 2, PS = PW * (TY + 2), NPL = nzl + 2;
   const int64_t plane = (int64_t)L.nx * L.ny, off = (int64_t)b * L.n;
   const int ncls = L.ncx * L.ncy * L.ncz;
   const T* tab = (const T*)L.coef + (int64_t)b * ncls * 28;
   const T* rb = rhs + off;
-  const T* xb = kStage == 1 ? nullptr : xin + off;
-  const T* eb = kStage == 2 ? ec + (int64_t)b * cnx * cny * cnz : nullptr;
-  // staged value of node (i, j, z) inside the grid
-  auto staged = [&](int i, int j, int z) -> T {
-    const int64_t idx = (int64_t)z * plane + (int64_t)j * L.nx + i;
-    if (kStage == 1) {
-      const int cls = (L.cz[z] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
-      return omega * tab[(int64_t)cls * 28 + 27] * rb[idx];
+  T* srhs = sm + (int64_t)(zc + 2) * PS;  // [nzl][TY][TX]
+  T* se = srhs + (int64_t)zc * TX * TY;   // kStage 2: e over the footprint
+  // the footprint of e: fine i in [x0-1, x0+TX] uses coarse floor((i-1)/2) .. floor(i/2)
+  const int ex_lo = floor_half(x0 - 2), ey_lo = floor_half(y0 - 2), ez_lo = floor_half(z0 - 2);
+  const int EW = floor_half(x0 + TX) - ex_lo + 1, EH = floor_half(y0 + TY) - ey_lo + 1;
+  const int ED = floor_half(z1) - ez_lo + 1;
+  if (kStage == 2) {
+    const T* eb = ec + (int64_t)b * cnx * cny * cnz;
+    const int ne = EW * EH * ED;
+    for (int e = tid; e < ne; e += NT) {
+      const int ix = e % EW, iy = (e / EW) % EH, iz = e / (EW * EH);
+      const int cx = ex_lo + ix, cy = ey_lo + iy, cz = ez_lo + iz;
+      T v = T(0);
+      if (cx >= 0 && cx < cnx && cy >= 0 && cy < cny && cz >= 0 && cz < cnz)
+        v = eb[((int64_t)cz * cny + cy) * cnx + cx];
+      se[e] = v;
     }
-    if (kStage == 2) return xb[idx] + prolong_node<T>(eb, cnx, cny, cnz, i, j, z);
-    return xb[idx];
-  };
-  // stage plane z (zeros outside the grid) into slot z & 3: (TX+2) x (TY+2) with halo
-  auto stage = [&](int z) {
-    T* Pl = sm + (z & 3) * PS;
-    const bool zin = z >= 0 && z < L.nz;
-    for (int hy = (int)threadIdx.y; hy < TY + 2; hy += TY)
-      for (int hx = (int)threadIdx.x; hx < TX + 2; hx += TX) {
-        const int i = x0 + hx - 1, j = y0 + hy - 1;
-        T v = T(0);
-        if (zin && i >= 0 && i < L.nx && j >= 0 && j < L.ny) v = staged(i, j, z);
-        Pl[hy * PW + hx] = v;
+    __syncthreads();
+  }
+  // (P e) at fine node (i, j, z) from the staged footprint
+  auto prolong_s = [&](int i, int j, int z) -> T {
+    const Pw rx = pweight(i, cnx), ry = pweight(j, cny), rz = pweight(z, cnz);
+    T v = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      const int kz = c ? rz.k1 : rz.k0;
+      if (kz < 0) continue;
+#pragma unroll
+      for (int bq = 0; bq < 2; bq++) {
+        const int ky = bq ? ry.k1 : ry.k0;
+        if (ky < 0) continue;
+        const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+        const T* row = se + ((kz - ez_lo) * EH + (ky - ey_lo)) * EW - ex_lo;
+        if (rx.k0 >= 0) v = fma((T)(wyz * rx.w0), row[rx.k0], v);
+        if (rx.k1 >= 0) v = fma((T)(wyz * rx.w1), row[rx.k1], v);
       }
+    }
+    return v;
   };
+  // stage every plane of the chunk at once (loads in batches of 4 per thread),
+  // zeros outside the grid, and the right-hand side of the own nodes
+  const int nst = NPL * PS;
+  for (int e0 = tid; e0 < nst; e0 += 4 * NT) {
+    T v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int e = e0 + q * NT;
+      v[q] = T(0);
+      if (e < nst) {
+        const int hx = e % PW, hy = (e / PW) % (TY + 2), pz = e / PS;
+        const int i = x0 + hx - 1, j = y0 + hy - 1, z = z0 + pz - 1;
+        if (z >= 0 && z < L.nz && i >= 0 && i < L.nx && j >= 0 && j < L.ny) {
+          const int64_t idx = (int64_t)z * plane + (int64_t)j * L.nx + i;
+          if (kStage == 1) {
+            const int cls = (L.cz[z] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
+            v[q] = omega * tab[(int64_t)cls * 28 + 27] * rb[idx];
+          } else {
+            v[q] = xin[off + idx];
+            if (kStage == 2) v[q] += prolong_s(i, j, z);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (e0 + q * NT < nst) sm[e0 + q * NT] = v[q];
+  }
   const int i = x0 + (int)threadIdx.x, j = y0 + (int)threadIdx.y;
   const bool own = i < L.nx && j < L.ny;
+  const int64_t col = (int64_t)j * L.nx + i;
+  if (own)
+    for (int z = z0; z < z1; z++) srhs[(z - z0) * NT + tid] = rb[(int64_t)z * plane + col];
+  __syncthreads();
+  if (!own) return;
+  // march in z with the 3 x 3 neighbourhoods of planes z-1, z, z+1 in registers
   const int oslot = ((int)threadIdx.y + 1) * PW + (int)threadIdx.x + 1;
+  T w[3][9];
+#pragma unroll
+  for (int pz = 0; pz < 2; pz++)
+#pragma unroll
+    for (int q = 0; q < 9; q++) w[pz][q] = sm[pz * PS + oslot + (q / 3 - 1) * PW + (q % 3 - 1)];
   T c[27];
   T dinv = T(0);
   int zcls_cur = -1;
-  stage(z0 - 1);
-  stage(z0);
+  const int cxy = L.cy[j] * L.ncx + L.cx[i];
   for (int z = z0; z < z1; ++z) {
-    stage(z + 1);
-    __syncthreads();
-    if (own) {
-      const int zcl = L.cz[z];
-      if (zcl != zcls_cur) {
-        zcls_cur = zcl;
-        const T* row = tab + (int64_t)((zcl * L.ncy + L.cy[j]) * L.ncx + L.cx[i]) * 28;
+    const T* Pn = sm + (z - z0 + 2) * PS + oslot;
 #pragma unroll
-        for (int k = 0; k < 27; k++) c[k] = row[k];
-        dinv = row[27];
-      }
-      T ax = T(0);
+    for (int q = 0; q < 9; q++) w[2][q] = Pn[(q / 3 - 1) * PW + (q % 3 - 1)];
+    const int zcl = L.cz[z];
+    if (zcl != zcls_cur) {
+      zcls_cur = zcl;
+      const T* row = tab + (int64_t)(zcl * L.ncy * L.ncx + cxy) * 28;
 #pragma unroll
-      for (int dz = -1; dz <= 1; dz++) {
-        const T* Pl = sm + ((z + dz) & 3) * PS;
-#pragma unroll
-        for (int dy = -1; dy <= 1; dy++)
-#pragma unroll
-          for (int dx = -1; dx <= 1; dx++)
-            ax = fma(c[(dz + 1) * 9 + (dy + 1) * 3 + dx + 1], Pl[oslot + dy * PW + dx], ax);
-      }
-      const int64_t idx = off + (int64_t)z * plane + (int64_t)j * L.nx + i;
-      const T bv = rhs[idx];
-      if (kOut == 1) {
-        out[idx] = bv - ax;
-      } else {
-        const T xc = sm[(z & 3) * PS + oslot];
-        out[idx] = fma(omega * dinv, bv - ax, xc);
-      }
+      for (int k = 0; k < 27; k++) c[k] = row[k];
+      dinv = row[27];
     }
-    // no second barrier: the next iteration restages slot (z + 2) & 3, which
-    // held plane z - 2; every thread finished with it before this iteration's barrier
+    T ax = T(0);
+#pragma unroll
+    for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+      for (int q = 0; q < 9; q++) ax = fma(c[dz * 9 + q], w[dz][q], ax);
+    const T bv = srhs[(z - z0) * NT + tid];
+    const int64_t idx = off + (int64_t)z * plane + col;
+    if (kOut == 1) out[idx] = bv - ax;
+    else out[idx] = fma(omega * dinv, bv - ax, w[1][4]);
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      w[0][q] = w[1][q];
+      w[1][q] = w[2][q];
+    }
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // The small levels in one kernel: levels top .. 0 of the V-cycle (top has at
@@ -858,13 +896,15 @@ void coarse_step(const MGBatch& m, const MGLevel& L, int stage, int outk, const 
   const int TX = L.nx >= 32 ? 32 : (L.nx >= 16 ? 16 : 8);
   const int TY = std::max(1, std::min(256 / TX, L.ny));
   const int tiles_x = (L.nx + TX - 1) / TX, tiles_y = (L.ny + TY - 1) / TY;
-  // z-chunks: at least two waves of 4 resident CTAs per SM where the level allows
+  // z-chunks: at least two waves of 4 resident CTAs per SM where the level allows,
+  // and the whole chunk's staging within 48 KB of shared memory
   int nzc = 1;
   while ((int64_t)tiles_x * tiles_y * nzc * m.B < 8 * 152 && nzc * 2 <= L.nz / 4) nzc *= 2;
-  const int zc = (L.nz + nzc - 1) / nzc;
+  int zc = (L.nz + nzc - 1) / nzc;
+  while (zc > 1 && sizeof(T) * coarse_smem_elems(TX, TY, zc, stage == 2) > 48 * 1024) zc = (zc + 1) / 2;
   nzc = (L.nz + zc - 1) / zc;
   const dim3 grid(tiles_x * tiles_y, nzc, m.B), block(TX, TY);
-  const size_t smem = sizeof(T) * 4 * (TX + 2) * (TY + 2);
+  const size_t smem = sizeof(T) * coarse_smem_elems(TX, TY, zc, stage == 2);
   const int cnx = C ? C->nx : 0, cny = C ? C->ny : 0, cnz = C ? C->nz : 0;
   const T om = (T)kMGOmega;
 #define RBWS_MG_COARSE(S, O) \
@@ -909,11 +949,9 @@ int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
     k_mg_restrict<T><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
                                                           crhs);
     int launches = 3 + vcycle<T>(m, i - 1, crhs, csol, s);
-    k_mg_prolong_add<T><<<level_grid(F.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask,
-                                                             csol, Y);
-    coarse_step<T>(m, F, 0, 0, rhs, Y, W, nullptr, nullptr, s);
+    coarse_step<T>(m, F, 2, 0, rhs, Y, W, csol, &C, s);  // W = step from Y + P e
     coarse_step<T>(m, F, 0, 0, rhs, W, out, nullptr, nullptr, s);
-    return launches + 3;
+    return launches + 2;
   }
   if (i == 0) {
     k_mg_dense_apply<T><<<m.B, 128, 0, s>>>(P.n0, (const T*)m.ainv, m.st, m.mask, rhs, out);
