@@ -815,6 +815,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
     if (v4) {
       mg_fine_prepare();
+      tma_prepare();  // the TMA-fed residual + restriction of the finest level
       mgb.fine_cg = &a;
       mgb.fine_tile = t;
       const Tile tm = choose_tile_v4(p->nx, p->ny);

@@ -380,9 +380,15 @@ struct MGFineArgs {
   int slot;          // partial slot of rho (output kind 2)
 };
 // stage 0: x = xin, 1: x = omega D^-1 rhs, 2: x = xin + P ec;  outk 0: Jacobi
-// step, 1: residual, 2: Jacobi step and rho partials.  Returns -1 for a
-// combination that is not built.
+// step, 1: residual, 2: Jacobi step and rho partials, 3 (stage 0): the
+// restricted residual P^T (rhs - A x) into out (the coarse grid cnx x cny x
+// cnz).  Returns -1 for a combination that is not built, or (outk 3) a tiling
+// it does not take.
 int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s);
+// outk 3 of the above: the TMA-fed residual + restriction kernel (stencil_tma.cu).
+// Needs an even ty and zc, tensor-map support and tma_prepare(); -1 otherwise.
+// A stage wait that runs out sets the error flag a.active[2].
+int launch_mg_fine_rr_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, cudaStream_t s);
 // Shared memory of the coarse planes staged by stage 2 for z-chunks of zc planes;
 // mg_fine_prepare sets the kernel attribute (call outside stream capture).
 size_t mg_fine_coarse_smem(Tile t, int zc);

@@ -552,72 +552,109 @@ __global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* _
   const int ex_lo = floor_half(x0 - 2), ey_lo = floor_half(y0 - 2), ez_lo = floor_half(z0 - 2);
   const int EW = floor_half(x0 + TX) - ex_lo + 1, EH = floor_half(y0 + TY) - ey_lo + 1;
   const int ED = floor_half(z1) - ez_lo + 1;
+  constexpr int KB = kStage == 2 ? 8 : 16;  // loads in flight per thread while staging
   if (kStage == 2) {
     const T* eb = ec + (int64_t)b * cnx * cny * cnz;
     const int ne = EW * EH * ED;
-    for (int e = tid; e < ne; e += NT) {
-      const int ix = e % EW, iy = (e / EW) % EH, iz = e / (EW * EH);
-      const int cx = ex_lo + ix, cy = ey_lo + iy, cz = ez_lo + iz;
-      T v = T(0);
-      if (cx >= 0 && cx < cnx && cy >= 0 && cy < cny && cz >= 0 && cz < cnz)
-        v = eb[((int64_t)cz * cny + cy) * cnx + cx];
-      se[e] = v;
+    for (int e0 = tid; e0 < ne; e0 += KB * NT) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; q++) {
+        const int e = e0 + q * NT;
+        v[q] = T(0);
+        if (e < ne) {
+          const int ix = e % EW, iy = (e / EW) % EH, iz = e / (EW * EH);
+          const int cx = ex_lo + ix, cy = ey_lo + iy, cz = ez_lo + iz;
+          if (cx >= 0 && cx < cnx && cy >= 0 && cy < cny && cz >= 0 && cz < cnz)
+            v[q] = eb[((int64_t)cz * cny + cy) * cnx + cx];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < KB; q++)
+        if (e0 + q * NT < ne) se[e0 + q * NT] = v[q];
     }
     __syncthreads();
   }
-  // (P e) at fine node (i, j, z) from the staged footprint
-  auto prolong_s = [&](int i, int j, int z) -> T {
-    const Pw rx = pweight(i, cnx), ry = pweight(j, cny), rz = pweight(z, cnz);
-    T v = T(0);
+  // stage every plane of the chunk at once (zeros outside the grid): a thread
+  // owns the cells (tx + c TX, ty + a TY) of each staged plane, c, a in {0, 1},
+  // and issues the loads of PB planes before their stores
+  const int i = x0 + (int)threadIdx.x, j = y0 + (int)threadIdx.y;
+  const bool own = i < L.nx && j < L.ny;
+  const int64_t col = (int64_t)j * L.nx + i;
+  int cell_s[4], cell_cx[4], cell_cy[4];  // smem offset in a plane (-1: no cell); classes (kStage 1)
+  int cell_col[4];                        // grid column j*nx + i, -1 outside the grid
+  int cell_i[4], cell_j[4];               // grid position (kStage 2)
 #pragma unroll
-    for (int c = 0; c < 2; c++) {
-      const int kz = c ? rz.k1 : rz.k0;
-      if (kz < 0) continue;
+  for (int c = 0; c < 4; c++) {
+    const int hx = (int)threadIdx.x + (c & 1) * TX, hy = (int)threadIdx.y + (c >> 1) * TY;
+    const bool cell = hx < TX + 2 && hy < TY + 2;
+    const int ii = x0 + hx - 1, jj = y0 + hy - 1;
+    const bool in = cell && ii >= 0 && ii < L.nx && jj >= 0 && jj < L.ny;
+    cell_s[c] = cell ? hy * PW + hx : -1;
+    cell_col[c] = in ? jj * L.nx + ii : -1;
+    cell_cx[c] = in && kStage == 1 ? L.cx[ii] : 0;
+    cell_cy[c] = in && kStage == 1 ? L.cy[jj] : 0;
+    cell_i[c] = ii;
+    cell_j[c] = jj;
+  }
+  constexpr int PB = kStage == 2 ? 2 : 4;
+  for (int p0 = 0; p0 < NPL; p0 += PB) {
+    T v[PB][4];
 #pragma unroll
-      for (int bq = 0; bq < 2; bq++) {
-        const int ky = bq ? ry.k1 : ry.k0;
-        if (ky < 0) continue;
-        const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
-        const T* row = se + ((kz - ez_lo) * EH + (ky - ey_lo)) * EW - ex_lo;
-        if (rx.k0 >= 0) v = fma((T)(wyz * rx.w0), row[rx.k0], v);
-        if (rx.k1 >= 0) v = fma((T)(wyz * rx.w1), row[rx.k1], v);
-      }
-    }
-    return v;
-  };
-  // stage every plane of the chunk at once (loads in batches of 4 per thread),
-  // zeros outside the grid, and the right-hand side of the own nodes
-  const int nst = NPL * PS;
-  for (int e0 = tid; e0 < nst; e0 += 4 * NT) {
-    T v[4];
+    for (int q = 0; q < PB; q++) {
+      const int z = z0 + p0 + q - 1;
+      const bool zin = p0 + q < NPL && z >= 0 && z < L.nz;
+      const int zcl = zin && kStage == 1 ? L.cz[z] : 0;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int e = e0 + q * NT;
-      v[q] = T(0);
-      if (e < nst) {
-        const int hx = e % PW, hy = (e / PW) % (TY + 2), pz = e / PS;
-        const int i = x0 + hx - 1, j = y0 + hy - 1, z = z0 + pz - 1;
-        if (z >= 0 && z < L.nz && i >= 0 && i < L.nx && j >= 0 && j < L.ny) {
-          const int64_t idx = (int64_t)z * plane + (int64_t)j * L.nx + i;
+      for (int c = 0; c < 4; c++) {
+        v[q][c] = T(0);
+        if (zin && cell_col[c] >= 0) {
+          const int64_t idx = (int64_t)z * plane + cell_col[c];
           if (kStage == 1) {
-            const int cls = (L.cz[z] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
-            v[q] = omega * tab[(int64_t)cls * 28 + 27] * rb[idx];
+            const int cls = (zcl * L.ncy + cell_cy[c]) * L.ncx + cell_cx[c];
+            v[q][c] = omega * tab[(int64_t)cls * 28 + 27] * rb[idx];
           } else {
-            v[q] = xin[off + idx];
-            if (kStage == 2) v[q] += prolong_s(i, j, z);
+            v[q][c] = xin[off + idx];
+            if (kStage == 2) {  // + (P e) from the staged footprint
+              const Pw rz = pweight(z, cnz), rx = pweight(cell_i[c], cnx), ry = pweight(cell_j[c], cny);
+              T pe = T(0);
+#pragma unroll
+              for (int cz = 0; cz < 2; cz++) {
+                const int kz = cz ? rz.k1 : rz.k0;
+                if (kz < 0) continue;
+#pragma unroll
+                for (int bq = 0; bq < 2; bq++) {
+                  const int ky = bq ? ry.k1 : ry.k0;
+                  if (ky < 0) continue;
+                  const float wyz = (cz ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+                  const T* row = se + ((kz - ez_lo) * EH + (ky - ey_lo)) * EW - ex_lo;
+                  if (rx.k0 >= 0) pe = fma((T)(wyz * rx.w0), row[rx.k0], pe);
+                  if (rx.k1 >= 0) pe = fma((T)(wyz * rx.w1), row[rx.k1], pe);
+                }
+              }
+              v[q][c] += pe;
+            }
           }
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; q++)
-      if (e0 + q * NT < nst) sm[e0 + q * NT] = v[q];
+    for (int q = 0; q < PB; q++)
+      if (p0 + q < NPL)
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+          if (cell_s[c] >= 0) sm[(p0 + q) * PS + cell_s[c]] = v[q][c];
   }
-  const int i = x0 + (int)threadIdx.x, j = y0 + (int)threadIdx.y;
-  const bool own = i < L.nx && j < L.ny;
-  const int64_t col = (int64_t)j * L.nx + i;
+  // the right-hand side of the own node, 16 planes of loads in flight
   if (own)
-    for (int z = z0; z < z1; z++) srhs[(z - z0) * NT + tid] = rb[(int64_t)z * plane + col];
+    for (int q0 = 0; q0 < nzl; q0 += 16) {
+      T v[16];
+#pragma unroll
+      for (int q = 0; q < 16; q++) v[q] = q0 + q < nzl ? rb[(int64_t)(z0 + q0 + q) * plane + col] : T(0);
+#pragma unroll
+      for (int q = 0; q < 16; q++)
+        if (q0 + q < nzl) srhs[(q0 + q) * NT + tid] = v[q];
+    }
   __syncthreads();
   if (!own) return;
   // march in z with the 3 x 3 neighbourhoods of planes z-1, z, z+1 in registers
@@ -1015,11 +1052,20 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   };
   fine(0, 1, 0);  // Y = two smoothing steps from zero
   fa.xin = Y;
-  fa.out = W;
-  fine(1, 0, 1);  // W = r - A Y
-  k_mg_restrict<float><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
-                                                            crhs);
-  int launches = 3 + vcycle<float>(m, J - 1, crhs, csol, s);
+  int launches = 2;
+  // coarse right-hand side P^T (r - A Y) in one pass where the tiling allows
+  fa.out = crhs;
+  if (m.ev) cudaEventRecord(m.ev[2], s);
+  const bool fused_rr = launch_mg_fine_v4(am, tm, 0, 3, fa, s) == 0;
+  if (!fused_rr) {
+    fa.out = W;
+    launch_mg_fine_v4(am, tm, 0, 1, fa, s);  // W = r - A Y
+    k_mg_restrict<float><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
+                                                              crhs);
+    launches += 1;
+  }
+  if (m.ev) cudaEventRecord(m.ev[3], s);
+  launches += vcycle<float>(m, J - 1, crhs, csol, s);
   // Y += P e (a streaming pass), then W = one smoothing step from Y (timed together)
   if (m.ev) cudaEventRecord(m.ev[4], s);
   k_mg_prolong_add4<<<dim3((unsigned)((F.n / 4 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(

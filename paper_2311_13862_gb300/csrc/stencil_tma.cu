@@ -499,6 +499,209 @@ abort:
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Finest multigrid level: the residual r = rhs - A x and its restriction
+// rc = P^T r in one pass (the residual and restriction steps of Algorithm 2),
+// without storing r.  A CTA owns the coarse nodes whose centre (fine node
+// 2I+1, 0-based) lies in its tile and z-chunk; their support reaches one fine
+// node past the tile on the high side of each axis, so the residual is also
+// formed on the extra column x0+TXN, the extra row y0+TY and the extra plane
+// z1.  Each plane of x (a (TXN+8) x (TY+3) box from x0-4, y0-1) and of rhs (a
+// (TXN+4) x (TY+1) box from x0, y0) arrives by TMA in a ring of kStages
+// stages.  The residuals of a plane go to one of two shared-memory planes;
+// after one barrier each thread sums the x/y weights (1/2, 1, 1/2) of its
+// coarse column, and the z weights are applied as the march passes the
+// coarse planes.  Requires an even TY and zc (tile origins on even nodes).
+// ---------------------------------------------------------------------------
+// Two CTAs per SM: the ring keeps about three planes per CTA in flight without
+// registers, so occupancy is not what feeds HBM here.
+__global__ void __launch_bounds__(256, 2)
+    k_mg_fine_rr_tma(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_r,
+                     CGArgs<float> a, MGFineArgs m, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ int s_go;
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE || (m.mask && !m.mask[b])) return;
+  const Geo& g = a.g;
+  const int TXT = blockDim.x, TY = blockDim.y, TXN = 4 * TXT;
+  const int tid = (int)threadIdx.y * TXT + (int)threadIdx.x;
+  // an earlier CTA's wait ran out: do not wait again (read by one thread, shared)
+  if (tid == 0) s_go = !*reinterpret_cast<volatile int*>(err);
+  __syncthreads();
+  if (!s_go) return;
+  const int x0 = (blockIdx.x % a.tiles_x) * TXN, y0 = (blockIdx.x / a.tiles_x) * TY;
+  const int z0 = blockIdx.y * a.zc, z1 = min(g.nz, z0 + a.zc), zlast = min(z1, g.nz - 1);
+  const int PW = TXN + 8, RP = TXN + 4;  // row pitch of the x box and of the rhs box (and R)
+  const int xfl = ((PW * (TY + 3) * 4 + 127) / 128) * 32, rfl = ((RP * (TY + 1) * 4 + 127) / 128) * 32;
+  float* base = reinterpret_cast<float*>(smem_raw);
+  auto xs = [&](int st) { return base + st * (xfl + rfl); };
+  auto rs = [&](int st) { return base + st * (xfl + rfl) + xfl; };
+  const int rpl = RP * (TY + 1);
+  float* R = base + kStages * (xfl + rfl);  // two residual planes [TY+1][RP]
+  float* exc_all = R + 2 * rpl;             // 8 floats per extra node: its cached coefficients
+  const unsigned xbytes = (unsigned)(PW * (TY + 3) * 4), rbytes = (unsigned)(RP * (TY + 1) * 4);
+  const int nq = zlast - z0 + 3;  // planes z0-1 .. zlast+1
+  auto issue = [&](int j) {       // plane z0-1+j into stage j % kStages (thread 0 only)
+    const int st = j % kStages;
+    const bool with_r = j >= 1 && j <= nq - 2;
+    mbar_expect_tx(&bars[st], xbytes + (with_r ? rbytes : 0u));
+    tma_load_4d(xs(st), &tm_x, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+    if (with_r) tma_load_4d(rs(st), &tm_r, x0, y0, z0 - 1 + j, b, &bars[st]);
+  };
+  if (tid == 0) {
+    for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int n_issued = 0;   // thread 0 only
+  int next_wait = 0;  // first plane index not yet waited for (uniform)
+  if (tid == 0)
+    for (int j = 0; j < kStages && j < nq; j++) {
+      issue(j);
+      n_issued = j + 1;
+    }
+  // duties: own group; extra-row group (tid < TXT) or extra-column node (the
+  // next TY + 1 threads); coarse column (every thread: 2 TXT x TY/2 of them)
+  const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
+  const int i = x0 + lx, j = y0 + ly;
+  const bool own = i < g.nx && j < g.ny;
+  const int xo = (ly + 1) * PW + 4 + lx, ro = ly * RP + lx;
+  const int ex_kind = tid < TXT ? 1 : (tid < TXT + TY + 1 ? 2 : 0);
+  const int exl = ex_kind == 1 ? 4 * tid : TXN, eyl = ex_kind == 1 ? TY : tid - TXT;
+  const int exi = x0 + exl, exj = y0 + eyl;
+  const bool ex_in = ex_kind != 0 && exi < g.nx && exj < g.ny;
+  float* exc = exc_all + (ex_kind == 1 ? 4 * tid : TXN + eyl) * 8;
+  const int Il = tid % (2 * TXT), Jl = tid / (2 * TXT);
+  const int I = x0 / 2 + Il, J = y0 / 2 + Jl;
+  const bool cown = I < m.cnx && J < m.cny;
+  float* rc = m.out + (int64_t)b * m.cnx * m.cny * m.cnz + (int64_t)J * m.cnx + I;
+  const int64_t cplane = (int64_t)m.cnx * m.cny;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+
+  bool to = !mbar_wait(&bars[0], 0);
+  if (!to) to = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  if (__syncthreads_or(to)) goto abort;
+  next_wait = 2;
+  {
+    float c[4][7];
+    int zcls_cur = -1, ex_zcls = -1;
+    float acc = 0.f;
+    for (int z = z0; z <= zlast; ++z) {
+      const int k = z - z0 + 1;  // plane index of z
+      const int sm_ = (k - 1) % kStages, sk = k % kStages, sn = (k + 1) % kStages;
+      to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      float* Rz = R + (z & 1) * rpl;
+      if (!to) {
+        const float* Pm = xs(sm_);
+        const float* Pc = xs(sk);
+        const float* Pp = xs(sn);
+        const float* Rh = rs(sk);
+        const int zcl = g.cz[z];
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (own) {
+          if (zcl != zcls_cur) {
+            zcls_cur = zcl;
+            const int yc = (int)g.cy[j];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+#pragma unroll
+              for (int q = 0; q < 7; q++) c[e][q] = row[q];
+            }
+          }
+          const float left = Pc[xo - 1], right = Pc[xo + 4];
+          const float4 xc = ld4s(Pc + xo), sth = ld4s(Pc + xo - PW), nth = ld4s(Pc + xo + PW);
+          const float4 xm = ld4s(Pm + xo), xp = ld4s(Pp + xo), bv = ld4s(Rh + ro);
+          float y[4];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float xce = f4(xc, e);
+            const float xw = e == 0 ? left : f4(xc, e - 1);
+            const float xe = e == 3 ? right : f4(xc, e + 1);
+            float v = c[e][6] * xce;
+            v = fmaf(c[e][0], xw, v);
+            v = fmaf(c[e][1], xe, v);
+            v = fmaf(c[e][2], f4(sth, e), v);
+            v = fmaf(c[e][3], f4(nth, e), v);
+            v = fmaf(c[e][4], f4(xm, e), v);
+            v = fmaf(c[e][5], f4(xp, e), v);
+            y[e] = f4(bv, e) - v;
+          }
+          r = make_float4(y[0], y[1], y[2], y[3]);
+        }
+        *reinterpret_cast<float4*>(Rz + ro) = r;
+        if (ex_kind != 0) {
+          const int nn = ex_kind == 1 ? 4 : 1;
+          if (ex_in && zcl != ex_zcls) {  // refresh the cached coefficients at a z class change
+            ex_zcls = zcl;
+            for (int e = 0; e < nn; e++) {
+              const float* row = cb + (((int64_t)zcl * g.ncy + g.cy[exj]) * g.ncx + g.cx[exi + e]) * kCoefStride;
+#pragma unroll
+              for (int q = 0; q < 7; q++) exc[e * 8 + q] = row[q];
+            }
+          }
+          const int o = (eyl + 1) * PW + 4 + exl;
+          float rv[4] = {0.f, 0.f, 0.f, 0.f};
+          if (ex_in)
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              if (e >= nn) break;
+              const float* row = exc + e * 8;
+              const int oe = o + e;
+              float v = row[6] * Pc[oe];
+              v = fmaf(row[0], Pc[oe - 1], v);
+              v = fmaf(row[1], Pc[oe + 1], v);
+              v = fmaf(row[2], Pc[oe - PW], v);
+              v = fmaf(row[3], Pc[oe + PW], v);
+              v = fmaf(row[4], Pm[oe], v);
+              v = fmaf(row[5], Pp[oe], v);
+              rv[e] = Rh[eyl * RP + exl + e] - v;
+            }
+          float* dst = Rz + eyl * RP + exl;
+          if (ex_kind == 1) *reinterpret_cast<float4*>(dst) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+          else dst[0] = rv[0];
+        }
+      }
+      if (__syncthreads_or(to)) goto abort;
+      next_wait = k + 2;
+      // plane k-1's stage is free: refill it with plane index k-1 + kStages
+      if (tid == 0 && k - 1 + kStages < nq) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k - 1 + kStages);
+        n_issued = k + kStages;
+      }
+      // x/y weights (1/2, 1, 1/2) of the coarse column over this plane
+      const float* r0 = Rz + 2 * Jl * RP + 2 * Il;
+      const float* r1 = r0 + RP;
+      const float* r2 = r1 + RP;
+      const float qv = 0.5f * fmaf(0.5f, r0[0] + r0[2], r0[1]) + fmaf(0.5f, r1[0] + r1[2], r1[1]) +
+                       0.5f * fmaf(0.5f, r2[0] + r2[2], r2[1]);
+      if (z & 1) {
+        acc += qv;  // the centre plane of coarse K = (z - 1) / 2
+      } else {
+        if (z > z0) {  // plane z closes coarse K = z/2 - 1
+          acc = fmaf(0.5f, qv, acc);
+          const int K = z / 2 - 1;
+          if (cown && K < m.cnz) rc[K * cplane] = acc;
+        }
+        acc = 0.5f * qv;  // and opens K = z/2 (not owned when z = z1)
+      }
+    }
+    if (zlast == z1 - 1 && (zlast & 1)) {  // the last chunk of an even axis: plane nz is outside
+      const int K = (zlast - 1) / 2;
+      if (cown && K < m.cnz) rc[K * cplane] = acc;
+    }
+  }
+  return;
+abort:
+  if (tid == 0) {
+    atomicExch(err, 1);
+    for (int jq = next_wait; jq < n_issued; jq++) mbar_wait(&bars[jq % kStages], (jq / kStages) & 1);
+  }
+  __syncthreads();
+}
+
 // Host side: tensor maps over [B][nz][ny][nx] float arrays with a box of
 // (4*tx + 8) x (ty + 2) x 1 x 1 and zero fill outside the tensor.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -522,17 +725,21 @@ static EncodeTiledFn encode_fn() {
 
 // halo = true: the (4*tx + 8) x (ty + 2) box of a stencil operand; false: the
 // 4*tx x ty own tile of a streamed operand.
-static int make_map(CUtensorMap* m, const float* base, const Geo& g, int B, Tile t, bool halo = true) {
+static int make_map_box(CUtensorMap* m, const float* base, const Geo& g, int B, int bx, int by) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn) return -1;
+  if (!fn || bx > 256 || by > 256 || (bx * 4) % 16) return -1;
   const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)B};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4, (cuuint64_t)g.n * 4};
-  const cuuint32_t box[4] = {(cuuint32_t)(4 * t.tx + (halo ? 8 : 0)), (cuuint32_t)(t.ty + (halo ? 2 : 0)), 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+static int make_map(CUtensorMap* m, const float* base, const Geo& g, int B, Tile t, bool halo = true) {
+  return make_map_box(m, base, g, B, 4 * t.tx + (halo ? 8 : 0), t.ty + (halo ? 2 : 0));
 }
 
 // Dynamic shared memory of the ring: halo boxes per stage (2 for phase A, 1
@@ -556,6 +763,31 @@ void tma_prepare() {
   cudaFuncSetAttribute(k_cg_a_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_cg_a_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_cg_b_s_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_fine_rr_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+// Ring stages (x box + rhs box), two residual planes, the extra nodes' coefficients.
+static size_t rr_smem_bytes(Tile t) {
+  const int TXN = 4 * t.tx, PW = TXN + 8, RP = TXN + 4;
+  const size_t xfl = (size_t)((PW * (t.ty + 3) * 4 + 127) / 128) * 32;
+  const size_t rfl = (size_t)((RP * (t.ty + 1) * 4 + 127) / 128) * 32;
+  return sizeof(float) * (kStages * (xfl + rfl) + 2 * (size_t)RP * (t.ty + 1) + (size_t)(TXN + t.ty + 1) * 8);
+}
+
+int launch_mg_fine_rr_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, cudaStream_t s) {
+  if ((t.ty & 1) || (a.zc & 1) || a.g.nx % 4 || rr_smem_bytes(t) > 200 * 1024) return -1;
+  CUtensorMap mx, mr;
+  if (make_map_box(&mx, m.xin, a.g, a.B, 4 * t.tx + 8, t.ty + 3) ||
+      make_map_box(&mr, m.rhs, a.g, a.B, 4 * t.tx + 4, t.ty + 1))
+    return -1;
+  // the error flag is the third counter of the solve (active, pending, TMA error)
+  k_mg_fine_rr_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), rr_smem_bytes(t), s>>>(
+      mx, mr, a, m, a.active + 2);
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return 0;
 }
 
 int launch_cg_a_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cudaStream_t s) {
