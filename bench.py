@@ -538,11 +538,12 @@ def main():
     fine = []
     if acc["samples"] > 0 and dom is not None and args.precond == "mg" and sum(acc["mg_fine_ms"]) > 0:
         # the fused finest-level steps of each V-cycle: algorithmic bytes per DoF (FP32):
-        # read r, write Y (8); read Y, r, write R (12); read and write Y, the coarse correction
-        # at 1/8 of the nodes, then read Y, r, write X (8 + 0.5 + 12, two launches timed
-        # together); read X, r, write s (12)
+        # read r, write Y (8); read Y, r, write the restricted residual at 1/8 of the nodes
+        # (8.5); read and write Y, the coarse correction at 1/8 of the nodes, then read Y, r,
+        # write X (8 + 0.5 + 12, two launches timed together); read X, r, write s (12)
         fine_kernels = [("k_mg_fine_v4<1,0> (two damped Jacobi steps from zero)", 8.0, "mg_fine_smooth_pre_f32_64cube"),
-                        ("k_mg_fine_v4<0,1> (residual r - A Y)", 12.0, "mg_fine_residual_f32_64cube"),
+                        ("k_mg_fine_rr_tma (restricted residual P^T (r - A Y))", 8.5,
+                         "mg_fine_residual_restrict_f32_64cube"),
                         ("k_mg_prolong_add4 + k_mg_fine_v4<0,0> (Y += P e; damped Jacobi step)", 20.5,
                          "mg_fine_prolong_smooth_f32_64cube"),
                         ("k_mg_fine_v4<0,2> (damped Jacobi step + rho partials)", 12.0,

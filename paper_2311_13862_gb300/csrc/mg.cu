@@ -709,11 +709,35 @@ struct MGTail {
   MGLevel lv[kMGMaxLevels];   // views of levels 0 .. top (coef: 28-wide tables, level 0 unused)
   int off[kMGMaxLevels];      // shared-memory offset (elements) of level l's three vectors
   int n0;
+  MGLevel up;                 // up.n > 0: add P (top solution) into up_x on this level (top + 1)
+};
+
+// Node t = (k ny + j) nx + i of a thread's strided sweep t = tid, tid + nt, ...,
+// with (i, j, k) carried from one node to the next instead of divided out.
+struct TailPos {
+  int i, j, k, di, dj, dk, nx, ny;
+  __device__ __forceinline__ TailPos(int t, int nt, int nx_, int ny_) : nx(nx_), ny(ny_) {
+    i = t % nx;
+    j = (t / nx) % ny;
+    k = t / (nx * ny);
+    di = nt % nx;
+    dj = (nt / nx) % ny;
+    dk = nt / (nx * ny);
+  }
+  __device__ __forceinline__ void next() {
+    i += di;
+    const int ci = i >= nx;
+    if (ci) i -= nx;
+    j += dj + ci;
+    const int cj = j >= ny;
+    if (cj) j -= ny;
+    k += dk + cj;
+  }
 };
 
 template <typename T>
-__device__ __forceinline__ T tail_apply(const MGLevel& L, const T* __restrict__ tab, const T* x, int t, T* dinv) {
-  const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
+__device__ __forceinline__ T tail_apply(const MGLevel& L, const T* __restrict__ tab, const T* x, int t, int i, int j,
+                                        int k, T* dinv) {
   const int cls = (L.cz[k] * L.ncy + L.cy[j]) * L.ncx + L.cx[i];
   const T* row = tab + (int64_t)cls * 28;
   *dinv = row[27];
@@ -732,9 +756,10 @@ __device__ __forceinline__ T tail_apply(const MGLevel& L, const T* __restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_mg_tail(MGTail tl, const InstState* __restrict__ st,
+__global__ void __launch_bounds__(512, 2) k_mg_tail(MGTail tl, const InstState* __restrict__ st,
                                                  const int* __restrict__ mask, const T* __restrict__ rhs_top,
-                                                 T* __restrict__ out_top, const T* __restrict__ ainv, T omega) {
+                                                 T* __restrict__ out_top, const T* __restrict__ ainv, T omega,
+                                                 T* __restrict__ up_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int b = blockIdx.x;
@@ -756,28 +781,36 @@ __global__ void __launch_bounds__(512) k_mg_tail(MGTail tl, const InstState* __r
     const int n = (int)L.n;
     const T* tb = tab(l);
     T *bb = vb(l), *yy = vy(l), *tt = vt(l);
-    for (int t = tid; t < n; t += nt) {  // tt = omega D^-1 b
-      T di;
-      const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
-      di = tb[(int64_t)((L.cz[k] * L.ncy + L.cy[j]) * L.ncx + L.cx[i]) * 28 + 27];
-      tt[t] = omega * di * bb[t];
+    {
+      TailPos q(tid, nt, L.nx, L.ny);
+      for (int t = tid; t < n; t += nt, q.next()) {  // tt = omega D^-1 b
+        const T di = tb[(int64_t)((L.cz[q.k] * L.ncy + L.cy[q.j]) * L.ncx + L.cx[q.i]) * 28 + 27];
+        tt[t] = omega * di * bb[t];
+      }
     }
     __syncthreads();
-    for (int t = tid; t < n; t += nt) {  // yy = tt + omega D^-1 (b - A tt)
-      T di;
-      const T ax = tail_apply<T>(L, tb, tt, t, &di);
-      yy[t] = fma(omega * di, bb[t] - ax, tt[t]);
+    {
+      TailPos q(tid, nt, L.nx, L.ny);
+      for (int t = tid; t < n; t += nt, q.next()) {  // yy = tt + omega D^-1 (b - A tt)
+        T di;
+        const T ax = tail_apply<T>(L, tb, tt, t, q.i, q.j, q.k, &di);
+        yy[t] = fma(omega * di, bb[t] - ax, tt[t]);
+      }
     }
     __syncthreads();
-    for (int t = tid; t < n; t += nt) {  // tt = b - A yy
-      T di;
-      tt[t] = bb[t] - tail_apply<T>(L, tb, yy, t, &di);
+    {
+      TailPos q(tid, nt, L.nx, L.ny);
+      for (int t = tid; t < n; t += nt, q.next()) {  // tt = b - A yy
+        T di;
+        tt[t] = bb[t] - tail_apply<T>(L, tb, yy, t, q.i, q.j, q.k, &di);
+      }
     }
     __syncthreads();
     const MGLevel& C = tl.lv[l - 1];
     T* cb = vb(l - 1);
-    for (int t = tid; t < (int)C.n; t += nt) {  // b_{l-1} = P^T tt
-      const int I = t % C.nx, J = (t / C.nx) % C.ny, K = t / (C.nx * C.ny);
+    TailPos qc(tid, nt, C.nx, C.ny);
+    for (int t = tid; t < (int)C.n; t += nt, qc.next()) {  // b_{l-1} = P^T tt
+      const int I = qc.i, J = qc.j, K = qc.k;
       T v = T(0);
       for (int dz = -1; dz <= 1; dz++) {
         const int z = 2 * K + 1 + dz;
@@ -817,9 +850,9 @@ __global__ void __launch_bounds__(512) k_mg_tail(MGTail tl, const InstState* __r
     const T* tb = tab(l);
     T *bb = vb(l), *yy = vy(l), *tt = vt(l);
     const T* e = vy(l - 1);
-    for (int t = tid; t < n; t += nt) {  // yy += P e
-      const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
-      const Pw rx = pweight(i, C.nx), ry = pweight(j, C.ny), rz = pweight(k, C.nz);
+    TailPos qp(tid, nt, L.nx, L.ny);
+    for (int t = tid; t < n; t += nt, qp.next()) {  // yy += P e
+      const Pw rx = pweight(qp.i, C.nx), ry = pweight(qp.j, C.ny), rz = pweight(qp.k, C.nz);
       T v = T(0);
       for (int c = 0; c < 2; c++) {
         const int kz = c ? rz.k1 : rz.k0;
@@ -836,19 +869,96 @@ __global__ void __launch_bounds__(512) k_mg_tail(MGTail tl, const InstState* __r
       yy[t] += v;
     }
     __syncthreads();
-    for (int t = tid; t < n; t += nt) {  // tt = yy + omega D^-1 (b - A yy)
-      T di;
-      const T ax = tail_apply<T>(L, tb, yy, t, &di);
-      tt[t] = fma(omega * di, bb[t] - ax, yy[t]);
+    {
+      TailPos q(tid, nt, L.nx, L.ny);
+      for (int t = tid; t < n; t += nt, q.next()) {  // tt = yy + omega D^-1 (b - A yy)
+        T di;
+        const T ax = tail_apply<T>(L, tb, yy, t, q.i, q.j, q.k, &di);
+        tt[t] = fma(omega * di, bb[t] - ax, yy[t]);
+      }
     }
     __syncthreads();
-    T* dst = l == tl.top ? out_top + (int64_t)b * n : yy;
-    for (int t = tid; t < n; t += nt) {  // solution = tt + omega D^-1 (b - A tt)
-      T di;
-      const T ax = tail_apply<T>(L, tb, tt, t, &di);
-      dst[t] = fma(omega * di, bb[t] - ax, tt[t]);
+    T* dst = l == tl.top && tl.up.n == 0 ? out_top + (int64_t)b * n : yy;
+    {
+      TailPos q(tid, nt, L.nx, L.ny);
+      for (int t = tid; t < n; t += nt, q.next()) {  // solution = tt + omega D^-1 (b - A tt)
+        T di;
+        const T ax = tail_apply<T>(L, tb, tt, t, q.i, q.j, q.k, &di);
+        dst[t] = fma(omega * di, bb[t] - ax, tt[t]);
+      }
     }
     __syncthreads();
+  }
+  if (tl.up.n > 0) {  // up_x += P e on the level above, e = the top solution (in shared memory)
+    const MGLevel& U = tl.up;
+    const MGLevel& C = tl.lv[tl.top];
+    const T* e = vy(tl.top);
+    T* ub = up_x + (int64_t)b * U.n;
+    // threads over x (nt a multiple of U.nx: no divisions in the loop), rows and planes
+    // stepped; the read-modify-writes of up_x go in batches of KB (loads first)
+    const bool rows = nt % U.nx == 0;
+    const int i0 = rows ? tid % U.nx : 0, rstep = rows ? nt / U.nx : 1, jfirst = rows ? tid / U.nx : 0;
+    const Pw rx0 = pweight(i0, C.nx);
+    constexpr int KB = 4;
+    int k = 0, j = jfirst;  // next (plane, row) of this thread
+    if (j >= U.ny) k = U.nz;
+    while (rows && k < U.nz) {
+      int kq[KB], jq[KB];
+      T old[KB];
+#pragma unroll
+      for (int q = 0; q < KB; q++) {
+        kq[q] = k;
+        jq[q] = j;
+        old[q] = k < U.nz ? ub[((int64_t)k * U.ny + j) * U.nx + i0] : T(0);
+        if (k < U.nz) {
+          j += rstep;
+          if (j >= U.ny) {
+            j = jfirst;
+            k++;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < KB; q++) {
+        if (kq[q] >= U.nz) continue;
+        const Pw rz = pweight(kq[q], C.nz), ry = pweight(jq[q], C.ny);
+        T v = T(0);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+          const int kz = c ? rz.k1 : rz.k0;
+          if (kz < 0) continue;
+#pragma unroll
+          for (int bq = 0; bq < 2; bq++) {
+            const int ky = bq ? ry.k1 : ry.k0;
+            if (ky < 0) continue;
+            const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+            const T* row = e + (kz * C.ny + ky) * C.nx;
+            if (rx0.k0 >= 0) v = fma((T)(wyz * rx0.w0), row[rx0.k0], v);
+            if (rx0.k1 >= 0) v = fma((T)(wyz * rx0.w1), row[rx0.k1], v);
+          }
+        }
+        ub[((int64_t)kq[q] * U.ny + jq[q]) * U.nx + i0] = old[q] + v;
+      }
+    }
+    if (!rows)
+      for (int t = tid; t < (int)U.n; t += nt) {
+        const int i = t % U.nx, j = (t / U.nx) % U.ny, k = t / (U.nx * U.ny);
+        const Pw rx = pweight(i, C.nx), ry = pweight(j, C.ny), rz = pweight(k, C.nz);
+        T v = T(0);
+        for (int c = 0; c < 2; c++) {
+          const int kz = c ? rz.k1 : rz.k0;
+          if (kz < 0) continue;
+          for (int bq = 0; bq < 2; bq++) {
+            const int ky = bq ? ry.k1 : ry.k0;
+            if (ky < 0) continue;
+            const float wyz = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
+            const T* row = e + (kz * C.ny + ky) * C.nx;
+            if (rx.k0 >= 0) v = fma((T)(wyz * rx.w0), row[rx.k0], v);
+            if (rx.k1 >= 0) v = fma((T)(wyz * rx.w1), row[rx.k1], v);
+          }
+        }
+        ub[t] += v;
+      }
   }
 }
 
@@ -953,10 +1063,14 @@ void coarse_step(const MGBatch& m, const MGLevel& L, int stage, int outk, const 
 #undef RBWS_MG_COARSE
 }
 
-// out = MG(rhs, A^i, i)
+// out = MG(rhs, A^i, i).  With up (the iterate of level i + 1): where the small
+// levels run in one kernel, that kernel adds P out into up itself, does not
+// store out, and sets *added.
 template <typename T>
-int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
+int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s, T* up = nullptr,
+           bool* added = nullptr) {
   const MGPlan& P = *m.plan;
+  if (added) *added = false;
   if constexpr (sizeof(T) == 4) {
     if (i == P.J && i > 0 && m.fine_cg) return vcycle_fine_fused(m, rhs, out, -1, s);
   }
@@ -965,9 +1079,12 @@ int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
     tl.top = i;
     tl.n0 = P.n0;
     for (int l = 0; l <= i; l++) tl.lv[l] = m.lv[l];
+    tl.up = m.lv[i + 1];
+    if (!up) tl.up.n = 0;
     const size_t smem = sizeof(T) * (size_t)tail_elems(P, i, tl.off);
     if (smem <= kMGTailSmem) {
-      k_mg_tail<T><<<m.B, 512, smem, s>>>(tl, m.st, m.mask, rhs, out, (const T*)m.ainv, (T)kMGOmega);
+      k_mg_tail<T><<<m.B, 512, smem, s>>>(tl, m.st, m.mask, rhs, out, (const T*)m.ainv, (T)kMGOmega, up);
+      if (added) *added = up != nullptr;
       return 1;
     }
   }
@@ -985,8 +1102,10 @@ int vcycle(const MGBatch& m, int i, const T* rhs, T* out, cudaStream_t s) {
     coarse_step<T>(m, F, 0, 1, rhs, Y, W, nullptr, nullptr, s);
     k_mg_restrict<T><<<level_grid(C.n, m.B), 256, 0, s>>>(F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, W,
                                                           crhs);
-    int launches = 3 + vcycle<T>(m, i - 1, crhs, csol, s);
-    coarse_step<T>(m, F, 2, 0, rhs, Y, W, csol, &C, s);  // W = step from Y + P e
+    bool added = false;
+    int launches = 3 + vcycle<T>(m, i - 1, crhs, csol, s, Y, &added);
+    if (added) coarse_step<T>(m, F, 0, 0, rhs, Y, W, nullptr, nullptr, s);  // Y holds Y + P e already
+    else coarse_step<T>(m, F, 2, 0, rhs, Y, W, csol, &C, s);                 // W = step from Y + P e
     coarse_step<T>(m, F, 0, 0, rhs, W, out, nullptr, nullptr, s);
     return launches + 2;
   }
