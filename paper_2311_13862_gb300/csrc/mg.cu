@@ -498,24 +498,8 @@ __global__ void k_mg_dense_apply(int n0, const T* __restrict__ ainv, const InstS
 // staged field is xin (kStage 0), omega D^-1 rhs (1) or xin + P e (2, e staged
 // first over the chunk's coarse footprint); the output a damped Jacobi step
 // (kOut 0) or the residual rhs - A x (kOut 1) -- as on the finest level.
-// Interpolation weights along one axis (registers only): fine node j of an
-// axis with m coarse nodes takes coarse k0 (w0) and, if k1 >= 0, k1 (w1).
-struct Pw {
-  int k0, k1;
-  float w0, w1;
-};
-__device__ __forceinline__ Pw pweight(int j, int m) {
-  const int t = j + 1;
-  Pw r{-1, -1, 0.f, 0.f};
-  if (t % 2 == 0) {
-    r.k0 = t / 2 - 1;
-    r.w0 = 1.f;
-  } else {
-    if ((t - 1) / 2 >= 1) r.k0 = (t - 1) / 2 - 1, r.w0 = 0.5f;
-    if ((t + 1) / 2 <= m) r.k1 = (t + 1) / 2 - 1, r.w1 = 0.5f;
-  }
-  return r;
-}
+using Pw = PRows;
+__device__ __forceinline__ Pw pweight(int j, int m) { return prows(j, m); }
 
 __device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
 

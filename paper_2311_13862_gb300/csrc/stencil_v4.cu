@@ -876,27 +876,6 @@ void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s
 // ---------------------------------------------------------------------------
 namespace {
 
-// Interpolation weights along one axis: fine node j (0-based) of an axis whose
-// coarse grid has m nodes takes coarse k0 (weight w0) and, if k1 >= 0, coarse
-// k1 (weight w1).  An even 1-based index takes its coarse node whole, an odd
-// one half of each neighbour that exists (the boundary contributes zero).
-struct PRows {
-  int k0, k1;
-  float w0, w1;
-};
-__device__ __forceinline__ PRows prows(int j, int m) {
-  const int t = j + 1;
-  PRows r{-1, -1, 0.f, 0.f};
-  if (t % 2 == 0) {
-    r.k0 = t / 2 - 1;
-    r.w0 = 1.f;
-  } else {
-    if ((t - 1) / 2 >= 1) r.k0 = (t - 1) / 2 - 1, r.w0 = 0.5f;
-    if ((t + 1) / 2 <= m) r.k1 = (t + 1) / 2 - 1, r.w1 = 0.5f;
-  }
-  return r;
-}
-
 }  // namespace
 
 template <int kStage, int kOut>
