@@ -582,21 +582,32 @@ __global__ void __launch_bounds__(256) k_mg_coarse(MGLevel L, const InstState* _
     cell_j[c] = jj;
   }
   constexpr int PB = kStage == 2 ? 2 : 4;
+  T cell_od[4] = {T(0), T(0), T(0), T(0)};  // kStage 1: omega / D of each cell in z class cell_zc
+  int cell_zc = -1;
   for (int p0 = 0; p0 < NPL; p0 += PB) {
     T v[PB][4];
 #pragma unroll
     for (int q = 0; q < PB; q++) {
       const int z = z0 + p0 + q - 1;
       const bool zin = p0 + q < NPL && z >= 0 && z < L.nz;
-      const int zcl = zin && kStage == 1 ? L.cz[z] : 0;
+      if (kStage == 1 && zin) {
+        const int zcl = L.cz[z];
+        if (zcl != cell_zc) {  // the table is read again only where the z class changes
+          cell_zc = zcl;
+#pragma unroll
+          for (int c = 0; c < 4; c++)
+            cell_od[c] = cell_col[c] >= 0
+                             ? omega * tab[(int64_t)((zcl * L.ncy + cell_cy[c]) * L.ncx + cell_cx[c]) * 28 + 27]
+                             : T(0);
+        }
+      }
 #pragma unroll
       for (int c = 0; c < 4; c++) {
         v[q][c] = T(0);
         if (zin && cell_col[c] >= 0) {
           const int64_t idx = (int64_t)z * plane + cell_col[c];
           if (kStage == 1) {
-            const int cls = (zcl * L.ncy + cell_cy[c]) * L.ncx + cell_cx[c];
-            v[q][c] = omega * tab[(int64_t)cls * 28 + 27] * rb[idx];
+            v[q][c] = cell_od[c] * rb[idx];
           } else {
             v[q][c] = xin[off + idx];
             if (kStage == 2) {  // + (P e) from the staged footprint

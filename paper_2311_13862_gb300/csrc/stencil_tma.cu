@@ -515,7 +515,7 @@ abort:
 // ---------------------------------------------------------------------------
 // Two CTAs per SM: the ring keeps about three planes per CTA in flight without
 // registers, so occupancy is not what feeds HBM here.
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_mg_fine_rr_tma(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_r,
                      CGArgs<float> a, MGFineArgs m, int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
