@@ -333,6 +333,12 @@ def main():
     N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
     torch.cuda.synchronize()
     t_off = time.perf_counter() - t0
+    # r_N: the largest (and mean) relative residual of the Galerkin RB solutions over the test set
+    # with the first n basis vectors, n = 1..N (outside every timed region)
+    r_curve = []
+    for n in range(1, int(N) + 1):
+        rr = rbws.rbws_rb_residuals(P.h, mus, n)
+        r_curve.append([float(rr.max()), float(rr.mean())])
 
     tuned = None
     if args.schedule >= 0:
@@ -584,6 +590,7 @@ def main():
                     "h2d_bytes_per_step": int(B * w.Q * 8),
                     "d2h_bytes_per_step": int(B * P.n * 8 + B * (4 + 8 + 4))},
             "arms": arms, "l1roc_offline": l1roc_off, "learned_training": learned, "autotune": tuned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "r_N_max_mean": r_curve,
             "iters_mean": float(np.mean(it)), "relres_max": float(np.max(rel))}
     if "zero_fp64" in arms:
         line["speedup_vs_zero_fp64"] = value / arms["zero_fp64"]["solves_per_s"]

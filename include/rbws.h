@@ -231,6 +231,18 @@ RBWS_API rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, 
                                         double snapshot_tol, int32_t* selected_out, double* eta_hist_out,
                                         int32_t* n_out);
 
+/* Accuracy of the RB space as a function of its dimension (the r_N-versus-N view
+ * of Sec. 5's offline-cost discussion, and the Galerkin RB method of Sec. 2.3):
+ * relres_out[b] (host [B]) = ||f - A(mu_b) W_n c_n(mu_b)||_2 / ||f||_2, with
+ * W_n the first n_use vectors of the current basis and c_n the Galerkin
+ * coefficients (W_n^T A(mu_b) W_n) c_n = W_n^T f from the leading n_use x n_use
+ * blocks of the reduced matrices.  mu: host [B][Q].  1 <= n_use <= N, else
+ * RBWS_ERR_INVALID_ARG; RBWS_ERR_NO_BASIS without a Galerkin basis;
+ * RBWS_ERR_NOT_SPD if a reduced matrix is not positive definite.  Synchronous;
+ * allocates B FP64 vectors of the grid in library-owned scratch. */
+RBWS_API rbws_status rbws_rb_residuals(rbws_problem p, const double* mu, int32_t B, int32_t n_use,
+                                       double* relres_out);
+
 /* The collocation data of the L1ROC basis: M_out = number of nodes; points_out
  * (host [M] or NULL) = their node indices ((z*ny + y)*nx + x) in the order they
  * were added; T_out (host [N][N] row-major or NULL) = T with U = W T.

@@ -242,11 +242,16 @@ def greedy(op: Operator, mu_train, n_max, f=None, greedy_tol=0.0, snapshot_tol=1
                  eta[:N].copy(), N)
 
 
-def rb_indicator(op: Operator, basis: Basis, mu, f=None) -> float:
+def rb_indicator(op: Operator, basis: Basis, mu, f=None, n_use=None) -> float:
+    """||f - A(mu) W_n c_n|| / ||f|| of the Galerkin RB solution (Sec. 2.3) with the first n_use
+    basis vectors (default: all); the reduced system is the leading n_use block (nested spaces)."""
     n = op.n
     f = np.ones(n) if f is None else _f64(f)
+    k = basis.N if n_use is None else int(n_use)
+    if not 1 <= k <= basis.N:
+        raise ValueError("n_use must be in 1..N")
     return lib().orc_rb_indicator(n, _p(op.row_ptr), _p(op.col), _p(op.vals_q), op.Q, op.nnz, _p(f),
-                                  _p(_f64(basis.W)), basis.N, basis.N, _p(_f64(basis.ANq)),
+                                  _p(_f64(basis.W)), k, basis.N, _p(_f64(basis.ANq)),
                                   _p(_f64(basis.fN)), _p(_f64(mu)))
 
 

@@ -2153,6 +2153,54 @@ rbws_status rbws_l1roc_info(rbws_problem p, int32_t* M_out, int64_t* points_out,
   return RBWS_OK;
 }
 
+rbws_status rbws_rb_residuals(rbws_problem p, const double* mu, int32_t B, int32_t n_use, double* relres_out) {
+  if (!p || !mu || !relres_out || B < 1 || B > 65535) {
+    set_error("rbws_rb_residuals: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->N <= 0 || !p->d_ANq) {
+    set_error("rbws_rb_residuals: no reduced basis");
+    return RBWS_ERR_NO_BASIS;
+  }
+  if (n_use < 1 || n_use > p->N) {
+    set_error("rbws_rb_residuals: n_use must be in 1..N");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_rbres"));
+  const int N = p->N, n = n_use, Q = p->Q;
+  int err = 0;
+  double* ANn = (double*)p->buf("rbres_ANn", sizeof(double) * (size_t)Q * n * n, &err);
+  double* C = err ? nullptr : (double*)p->buf("rbres_C", sizeof(double) * (size_t)B * n, &err);
+  int* info = err ? nullptr : (int*)p->buf("rbres_info", sizeof(int) * (size_t)B, &err);
+  double* u = err ? nullptr : (double*)p->buf("rbres_u", sizeof(double) * (size_t)B * p->n, &err);
+  double* rel = err ? nullptr : (double*)p->buf("rbres_rel", sizeof(double) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  // the leading n x n block of each A_N^q (the reduced matrices of the first n vectors: nested spaces)
+  for (int q = 0; q < Q; q++)
+    CK(cudaMemcpy2DAsync(ANn + (size_t)q * n * n, sizeof(double) * n, p->d_ANq + (size_t)q * N * N,
+                         sizeof(double) * N, sizeof(double) * n, n, cudaMemcpyDeviceToDevice, p->cur));
+  launch_reduced_solve(n, Q, ANn, p->d_fN, d_mu, B, C, info, nullptr, p->cur);
+  launch_lift(p->n, n, p->d_W, C, B, u, p->cur);
+  p->launches += 2;
+  double* coef64 = nullptr;
+  float* coef32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &coef64, &coef32));
+  CKI(residual_norms(p, coef64, B, u, nullptr, rel));
+  std::vector<int> h(B);
+  CK(cudaMemcpyAsync(relres_out, rel, sizeof(double) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  for (int b = 0; b < B; b++)
+    if (h[b] != 0) {
+      set_error("reduced matrix of the first n_use vectors is not positive definite for instance " +
+                std::to_string(b));
+      return RBWS_ERR_NOT_SPD;
+    }
+  return RBWS_OK;
+}
+
 rbws_status rbws_l1roc_coefficients(rbws_problem p, const double* mu, int32_t B, double* c_out) {
   if (!p || !mu || !c_out || B < 1 || B > 65535) {
     set_error("rbws_l1roc_coefficients: invalid argument");

@@ -75,6 +75,7 @@ def _lib():
         L.rbws_offline_l1roc.argtypes = [P, P, i32, i32, d, P, P, C.POINTER(i32)]
         L.rbws_l1roc_info.argtypes = [P, C.POINTER(i32), P, P]
         L.rbws_l1roc_coefficients.argtypes = [P, P, i32, P]
+        L.rbws_rb_residuals.argtypes = [P, P, i32, i32, P]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, i32, P, P, C.POINTER(i32)]
         L.rbws_set_basis.argtypes = [P, i32, P, P, P]
@@ -96,7 +97,7 @@ def _lib():
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
                      "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
                      "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load", "rbws_apply_preconditioner",
-                     "rbws_offline_l1roc", "rbws_l1roc_info", "rbws_l1roc_coefficients"):
+                     "rbws_offline_l1roc", "rbws_l1roc_info", "rbws_l1roc_coefficients", "rbws_rb_residuals"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -214,6 +215,14 @@ def rbws_l1roc_coefficients(h, mu):
     c = np.empty((mu.shape[0], N))
     _check(_lib().rbws_l1roc_coefficients(h, _hp(mu), mu.shape[0], _hp(c)), "rbws_l1roc_coefficients")
     return c
+
+
+def rbws_rb_residuals(h, mu, n_use):
+    """||f - A(mu) W_n c_n|| / ||f|| [B] of the Galerkin RB solutions with the first n_use basis vectors."""
+    mu = _host(np.atleast_2d(mu))
+    rel = np.empty(mu.shape[0])
+    _check(_lib().rbws_rb_residuals(h, _hp(mu), mu.shape[0], int(n_use), _hp(rel)), "rbws_rb_residuals")
+    return rel
 
 
 def rbws_offline_greedy(h, mu_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12, indicator=INDICATOR_RESIDUAL):

@@ -68,3 +68,22 @@ def test_greedy_l1_indicator_matches_oracle():
     assert np.max(np.abs(W @ W.T - np.eye(N))) <= 1e-12
     assert np.max(np.abs(W.T @ (W @ ref.W.T) - ref.W.T)) <= 1e-8
     assert np.all(eta[:N] > 0)
+
+
+def test_rb_residuals_of_each_dimension_match_oracle():
+    """The r_N view: the residual of the Galerkin RB solution with the first n vectors, for several
+    n, against the oracle's (each on its own greedy basis; the residual depends on the span only)."""
+    grid, blocks = (24, 20, 18), (2, 2, 1)
+    w = inputs.small(grid=grid, blocks=blocks, n_max=8, n_train=32, n_test=6)
+    op = O.assemble(grid, blocks)
+    ref = O.greedy(op, inputs.train_mu(w), w.n_max, snapshot_tol=1e-12)
+    mus = inputs.test_mu(w)
+    with rbws.Problem(grid, blocks) as P:
+        N, _, _ = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
+        assert N == ref.N
+        for n in (1, 4, N):
+            got = rbws.rbws_rb_residuals(P.h, mus, n)
+            exp = np.array([O.rb_indicator(op, ref, mu, n_use=n) for mu in mus])
+            assert np.allclose(got, exp, rtol=1e-5, atol=0), (n, got, exp)
+        with pytest.raises(rbws.RbwsError, match="INVALID_ARG"):
+            rbws.rbws_rb_residuals(P.h, mus, N + 1)

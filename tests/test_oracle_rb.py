@@ -168,3 +168,28 @@ def test_l1_indicator_is_coefficient_norm_in_the_snapshot_basis():
     assert b.eta_hist[-1] == pytest.approx(max(vals), rel=1e-6)
     # the first pick is index 0 whatever the indicator, later picks maximise the L1 norm
     assert b.selected[0] == 0
+
+
+def test_rb_residual_of_a_subspace_is_the_dense_galerkin_residual(c1_small):
+    """The r_N view (residual of the Galerkin RB solution with the first n vectors): the oracle's
+    leading-block reduced solve equals a dense projection onto span(W[:n]) formed from scratch."""
+    w, op, b = c1_small
+    f = np.ones(op.n)
+    for mu in inputs.test_mu(w)[:3]:
+        A = op.dense(mu)
+        for n in (1, 3, b.N):
+            Wn = b.W[:n]
+            c = np.linalg.solve(Wn @ A @ Wn.T, Wn @ f)
+            ref = np.linalg.norm(f - A @ (Wn.T @ c)) / np.linalg.norm(f)
+            assert O.rb_indicator(op, b, mu, n_use=n) == pytest.approx(ref, rel=1e-9)
+    with pytest.raises(ValueError):
+        O.rb_indicator(op, b, inputs.test_mu(w)[0], n_use=b.N + 1)
+
+
+def test_rb_residual_vanishes_at_the_selected_parameters(c1_small):
+    """Exact reproduction: with all N vectors, the RB solution at a selected training parameter is
+    its snapshot, so the residual is at the snapshot tolerance's level."""
+    w, op, b = c1_small
+    mus = inputs.train_mu(w)
+    for t in b.selected:
+        assert O.rb_indicator(op, b, mus[t]) < 1e-9
