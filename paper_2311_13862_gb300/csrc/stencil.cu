@@ -92,10 +92,14 @@ __device__ __forceinline__ Column make_column(const Geo& g, int x0, int y0) {
 
 // The z-marching stencil skeleton.  load(idx) returns the staged field at an
 // in-domain node (idx = z*nx*ny + j*nx + i); consume(idx, x_c, y, dinv) gets
-// y = (A x)(node) for each owned node of planes [z0, z1).
-template <typename T, class Load, class Consume>
+// y = (A x)(node) for each owned node of planes [z0, z1), or with kResid
+// y = base(idx) - (A x)(node) (the terms subtracted in the same FMA chain).
+struct ZNoBase {
+  __device__ __forceinline__ double operator()(int64_t) const { return 0.0; }
+};
+template <typename T, bool kResid = false, class Load, class Consume, class Base = ZNoBase>
 __device__ __forceinline__ void zmarch(const Geo& g, const T* __restrict__ coef_b, int x0, int y0,
-                                       int z0, int z1, T* sm, Load load, Consume consume) {
+                                       int z0, int z1, T* sm, Load load, Consume consume, Base base = Base()) {
   const int TX = blockDim.x, TY = blockDim.y;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const Column cl = make_column(g, x0, y0);
@@ -150,14 +154,27 @@ __device__ __forceinline__ void zmarch(const Geo& g, const T* __restrict__ coef_
       for (int k = 0; k < kCoefStride; k++) c[k] = row[k];
     }
     if (cl.own) {
-      T y = c[6] * xc;
-      y = fma(c[0], Pl[oslot - 1], y);
-      y = fma(c[1], Pl[oslot + 1], y);
-      y = fma(c[2], Pl[oslot - PW], y);
-      y = fma(c[3], Pl[oslot + PW], y);
-      y = fma(c[4], xm, y);
-      y = fma(c[5], xp, y);
-      consume((int64_t)z * plane + cl.col, xc, y, c[7]);
+      const int64_t idx = (int64_t)z * plane + cl.col;
+      T y;
+      if (kResid) {
+        y = (T)base(idx);
+        y = fma(-c[6], xc, y);
+        y = fma(-c[0], Pl[oslot - 1], y);
+        y = fma(-c[1], Pl[oslot + 1], y);
+        y = fma(-c[2], Pl[oslot - PW], y);
+        y = fma(-c[3], Pl[oslot + PW], y);
+        y = fma(-c[4], xm, y);
+        y = fma(-c[5], xp, y);
+      } else {
+        y = c[6] * xc;
+        y = fma(c[0], Pl[oslot - 1], y);
+        y = fma(c[1], Pl[oslot + 1], y);
+        y = fma(c[2], Pl[oslot - PW], y);
+        y = fma(c[3], Pl[oslot + PW], y);
+        y = fma(c[4], xm, y);
+        y = fma(c[5], xp, y);
+      }
+      consume(idx, xc, y, c[7]);
     }
     xm = xc;
     xc = xp;
@@ -253,13 +270,13 @@ __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restric
   double* rb = r ? r + (int64_t)b * g.n : nullptr;
   const double* cb = coef + (int64_t)b * g.ncls() * kCoefStride;
   double acc = 0.0;
-  zmarch<double>(
+  zmarch<double, true>(
       g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return ub[idx]; },
-      [&](int64_t idx, double, double v, double) {
-        const double rv = (f ? f[idx] : 1.0) - v;
+      [&](int64_t idx, double, double rv, double) {  // rv = f - A u
         if (rb) rb[idx] = rv;
         acc = fma(rv, rv, acc);
-      });
+      },
+      [&](int64_t idx) { return f ? f[idx] : 1.0; });
   double dummy = 0.0;
   block_sum2(acc, dummy, red);
   if (threadIdx.x == 0 && threadIdx.y == 0) rr_part[(int64_t)b * P + tp.part] = acc;
@@ -721,13 +738,38 @@ __global__ void k_ru_fold(CGArgs<float> a) {
   const int par = mode == 1 ? 0 : a.st[b].pad;
   const double al = a.alpha ? a.alpha[(int64_t)par * a.B + b] : 0.0;
   const float* pp = (par ? a.p1 : a.p0) + (int64_t)b * a.g.n;
-  const int64_t off = (int64_t)b * a.g.n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.g.n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double v = a.u64[off + i] + (double)a.u[off + i];
+  const int64_t off = (int64_t)b * a.g.n, n = a.g.n;
+  double* u64 = a.u64 + off;
+  float* d = a.u + off;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = (n & 3) == 0 && ((reinterpret_cast<uintptr_t>(u64) | reinterpret_cast<uintptr_t>(d) |
+                                     reinterpret_cast<uintptr_t>(pp)) & 15) == 0;
+  if (vec) {  // 4 nodes per thread: 16-byte accesses
+    for (int64_t k = t0; k < (n >> 2); k += stride) {
+      const float4 dv = reinterpret_cast<const float4*>(d)[k];
+      double2 lo = reinterpret_cast<const double2*>(u64)[2 * k], hi = reinterpret_cast<const double2*>(u64)[2 * k + 1];
+      lo.x += (double)dv.x;
+      lo.y += (double)dv.y;
+      hi.x += (double)dv.z;
+      hi.y += (double)dv.w;
+      if (al != 0.0) {
+        const float4 pv = reinterpret_cast<const float4*>(pp)[k];
+        lo.x = fma(al, (double)pv.x, lo.x);
+        lo.y = fma(al, (double)pv.y, lo.y);
+        hi.x = fma(al, (double)pv.z, hi.x);
+        hi.y = fma(al, (double)pv.w, hi.y);
+      }
+      reinterpret_cast<double2*>(u64)[2 * k] = lo;
+      reinterpret_cast<double2*>(u64)[2 * k + 1] = hi;
+      reinterpret_cast<float4*>(d)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return;
+  }
+  for (int64_t i = t0; i < n; i += stride) {
+    double v = u64[i] + (double)d[i];
     if (al != 0.0) v = fma(al, (double)pp[i], v);
-    a.u64[off + i] = v;
-    a.u[off + i] = 0.f;
+    u64[i] = v;
+    d[i] = 0.f;
   }
 }
 
@@ -874,7 +916,9 @@ void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s) {
 }
 void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s) {
   const int threads = 256;
-  const int64_t blocks = std::min<int64_t>((a.g.n + threads - 1) / threads, 152 * 4);
+  const int64_t work = (a.g.n & 3) == 0 ? a.g.n / 4 : a.g.n;  // the kernel falls back to one node per
+                                                                  // thread (a grid-stride loop) if unaligned
+  const int64_t blocks = std::min<int64_t>((work + threads - 1) / threads, 152 * 4);
   k_ru_fold<<<dim3((unsigned)blocks, a.B), threads, 0, s>>>(a);
 }
 void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s) {
