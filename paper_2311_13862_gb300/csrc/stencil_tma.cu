@@ -702,6 +702,154 @@ abort:
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Finest multigrid level: one damped Jacobi step out = x + omega D^-1 (rhs - A x)
+// (Algorithm 2's smoother), kRho: also the partials of rho = rhs . out into
+// slot m.slot of the iteration's partials (the launch then uses the iteration's
+// tiling).  The x box ((4 tx + 8) x (ty + 2), halo included) and the own rhs
+// tile of each plane arrive by TMA in the kStages ring, as in phase B.
+// ---------------------------------------------------------------------------
+template <bool kRho>
+__global__ void __launch_bounds__(256, 3)
+    k_mg_smooth_tma(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_r,
+                    CGArgs<float> a, MGFineArgs m, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ double red[32];
+  __shared__ int s_go;
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE || (m.mask && !m.mask[b])) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) s_go = !*reinterpret_cast<volatile int*>(err);  // an earlier wait ran out: do not wait again
+  __syncthreads();
+  if (!s_go) return;
+  const Geo& g = a.g;
+  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  const int x0 = (blockIdx.x % a.tiles_x) * TXN, y0 = (blockIdx.x / a.tiles_x) * TY;
+  const int z0 = blockIdx.y * a.zc, z1 = min(g.nz, z0 + a.zc);
+  const int BX = TXN + 8, BY = TY + 2;
+  const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float)), own_bytes = (unsigned)(TXN * TY * sizeof(float));
+  const int arr_floats = ((BX * BY * 4 + 127) / 128) * 32;
+  const int stage_floats = arr_floats + ((TXN * TY * 4 + 127) / 128) * 32;
+  float* stage_base = reinterpret_cast<float*>(smem_raw);
+  auto x_tile = [&](int st) { return stage_base + st * stage_floats; };
+  auto r_tile = [&](int st) { return stage_base + st * stage_floats + arr_floats; };
+  const int nq = z1 - z0 + 2;
+  auto issue = [&](int j) {  // x of plane z0-1+j with its halo; rhs of it for planes z0 .. z1-1
+    const int st = j % kStages;
+    const bool with_r = j >= 1 && j <= nq - 2;
+    mbar_expect_tx(&bars[st], box_bytes + (with_r ? own_bytes : 0u));
+    tma_load_4d(x_tile(st), &tm_x, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+    if (with_r) tma_load_4d(r_tile(st), &tm_r, x0, y0, z0 - 1 + j, b, &bars[st]);
+  };
+  if (tid == 0) {
+    for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int n_issued = 0, next_wait = 0;
+  if (tid == 0)
+    for (int j = 0; j < kStages && j < nq; j++) {
+      issue(j);
+      n_issued = j + 1;
+    }
+  const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
+  const int i = x0 + lx, jn = y0 + ly;
+  const bool own = i < g.nx && jn < g.ny;
+  const int cofs = (ly + 1) * BX + lx + 4;
+  const int lofs = ly * TXN + lx;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)jn * g.nx + i;
+  float* ob = m.out + (int64_t)b * g.n;
+  const float omega = m.omega;
+  float rho = 0.f;
+  bool timed_out = !mbar_wait(&bars[0], 0);
+  float4 xm = ld4s(x_tile(0) + cofs);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  float4 xc = ld4s(x_tile(1 % kStages) + cofs);
+  if (__syncthreads_or(timed_out)) goto abort;
+  next_wait = 2;
+  if (tid == 0 && kStages < nq) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(kStages);
+    n_issued = kStages + 1;
+  }
+  {
+    float c[4][8];
+    int zcls_cur = -1;
+    for (int z = z0; z < z1; ++z) {
+      const int k = z - z0 + 1;
+      const int sk = k % kStages, sn = (k + 1) % kStages;
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      if (!to && own) {
+        const float4 xp = ld4s(x_tile(sn) + cofs);
+        const float4 bv = ld4s(r_tile(sk) + lofs);
+        const int zcl = g.cz[z];
+        if (zcl != zcls_cur) {
+          zcls_cur = zcl;
+          const int yc = (int)g.cy[jn];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+#pragma unroll
+            for (int q = 0; q < 8; q++) c[e][q] = row[q];
+          }
+        }
+        const float* X = x_tile(sk);
+        const float left = X[cofs - 1], right = X[cofs + 4];
+        const float4 sth = ld4s(X + cofs - BX), nth = ld4s(X + cofs + BX);
+        float o4[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float xce = f4(xc, e);
+          float v = c[e][6] * xce;
+          v = fmaf(c[e][0], e == 0 ? left : f4(xc, e - 1), v);
+          v = fmaf(c[e][1], e == 3 ? right : f4(xc, e + 1), v);
+          v = fmaf(c[e][2], f4(sth, e), v);
+          v = fmaf(c[e][3], f4(nth, e), v);
+          v = fmaf(c[e][4], f4(xm, e), v);
+          v = fmaf(c[e][5], f4(xp, e), v);
+          o4[e] = fmaf(omega * c[e][7], f4(bv, e) - v, xce);
+          if (kRho) rho = fmaf(f4(bv, e), o4[e], rho);
+        }
+        *reinterpret_cast<float4*>(ob + z * plane + col) = make_float4(o4[0], o4[1], o4[2], o4[3]);
+        xm = xc;
+        xc = xp;
+      } else if (!to) {
+        xm = xc;
+        xc = ld4s(x_tile(sn) + cofs);
+      }
+      if (__syncthreads_or(to)) goto abort;
+      next_wait = k + 2;
+      if (tid == 0 && k + kStages < nq) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k + kStages);
+        n_issued = k + kStages + 1;
+      }
+    }
+    if (kRho) {  // deterministic block sum of the rho partial
+      double v = (double)rho;
+      const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+      v = warp_sum_down(v);
+      if (lane == 0) red[warp] = v;
+      __syncthreads();
+      if (warp == 0) {
+        double x = lane < nw ? red[lane] : 0.0;
+        x = warp_sum_down(x);
+        if (lane == 0) a.rho_rr[((int64_t)m.slot * a.B + b) * a.P + blockIdx.y * gridDim.x + blockIdx.x].x = x;
+      }
+    }
+  }
+  return;
+abort:
+  if (tid == 0) {
+    atomicExch(err, 1);
+    for (int jq = next_wait; jq < n_issued; jq++) mbar_wait(&bars[jq % kStages], (jq / kStages) & 1);
+  }
+  __syncthreads();
+}
+
 // Host side: tensor maps over [B][nz][ny][nx] float arrays with a box of
 // (4*tx + 8) x (ty + 2) x 1 x 1 and zero fill outside the tensor.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -764,6 +912,22 @@ void tma_prepare() {
   cudaFuncSetAttribute(k_cg_a_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_cg_b_s_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mg_fine_rr_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_smooth_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_smooth_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, bool rho, cudaStream_t s) {
+  if (!tma_supported(a.g, t) || (rho && m.slot < 0)) return -1;
+  CUtensorMap mx, mr;
+  if (make_map(&mx, m.xin, a.g, a.B, t) || make_map(&mr, m.rhs, a.g, a.B, t, false)) return -1;
+  const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
+  if (rho) k_mg_smooth_tma<true><<<grid, block, ring_bytes(t, 1, 1), s>>>(mx, mr, a, m, a.active + 2);
+  else k_mg_smooth_tma<false><<<grid, block, ring_bytes(t, 1, 1), s>>>(mx, mr, a, m, a.active + 2);
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return 0;
 }
 
 // Ring stages (x box + rhs box), two residual planes, the extra nodes' coefficients.
