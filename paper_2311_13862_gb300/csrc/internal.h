@@ -413,9 +413,11 @@ int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const
 // Needs an even ty and zc, tensor-map support and tma_prepare(); -1 otherwise.
 // A stage wait that runs out sets the error flag a.active[2].
 int launch_mg_fine_rr_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, cudaStream_t s);
-// Stage 0, outk 0 / 2 of launch_mg_fine_v4 with the planes fed by TMA (stencil_tma.cu):
-// -1 where tensor maps are not available (the register-prefetch kernel runs then).
-int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, bool rho, cudaStream_t s);
+// Stages 0 and 1 with outk 0, and stage 0 with outk 2, of launch_mg_fine_v4 with the
+// planes fed by TMA (stencil_tma.cu): -1 where tensor maps or the tiling do not allow
+// it (the register-prefetch kernel runs then).
+int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, int stage, const MGFineArgs& m, bool rho,
+                         cudaStream_t s);
 // Shared memory of the coarse planes staged by stage 2 for z-chunks of zc planes;
 // mg_fine_prepare sets the kernel attribute (call outside stream capture).
 size_t mg_fine_coarse_smem(Tile t, int zc);

@@ -1180,7 +1180,9 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   }
   if (m.ev) cudaEventRecord(m.ev[3], s);
   launches += vcycle<float>(m, J - 1, crhs, csol, s);
-  // Y += P e (a streaming pass), then W = one smoothing step from Y (timed together)
+  // Y += P e (a streaming pass), then W = one smoothing step from Y (timed together).  Forming
+  // Y + P e where the step stages its planes (the coarse footprint staged per chunk) measured
+  // no faster than the separate streaming pass.
   if (m.ev) cudaEventRecord(m.ev[4], s);
   k_mg_prolong_add4<<<dim3((unsigned)((F.n / 4 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(
       F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);

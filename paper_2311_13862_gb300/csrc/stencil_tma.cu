@@ -706,10 +706,16 @@ abort:
 // Finest multigrid level: one damped Jacobi step out = x + omega D^-1 (rhs - A x)
 // (Algorithm 2's smoother), kRho: also the partials of rho = rhs . out into
 // slot m.slot of the iteration's partials (the launch then uses the iteration's
-// tiling).  The x box ((4 tx + 8) x (ty + 2), halo included) and the own rhs
-// tile of each plane arrive by TMA in the kStages ring, as in phase B.
+// tiling).  The box of each plane ((4 tx + 8) x (ty + 2), halo included) and
+// the own rhs tile arrive by TMA in the kStages ring, as in phase B.  The
+// staged field x is
+//   kStage 0: xin;
+//   kStage 1: omega D^-1 rhs (the box is rhs; the first step from zero).
+// For kStage 1 each plane is scaled in place when its copy lands (a thread: its
+// own group and, for the first 2 (tx + 2) + 2 ty threads, one halo group), one
+// plane ahead of the stencil, so one barrier per plane stays enough.
 // ---------------------------------------------------------------------------
-template <bool kRho>
+template <int kStage, bool kRho>
 __global__ void __launch_bounds__(256, 3)
     k_mg_smooth_tma(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_r,
                     CGArgs<float> a, MGFineArgs m, int* err) {
@@ -724,7 +730,7 @@ __global__ void __launch_bounds__(256, 3)
   __syncthreads();
   if (!s_go) return;
   const Geo& g = a.g;
-  const int TXN = blockDim.x * 4, TY = blockDim.y;
+  const int TXT = blockDim.x, TXN = TXT * 4, TY = blockDim.y;
   const int x0 = (blockIdx.x % a.tiles_x) * TXN, y0 = (blockIdx.x / a.tiles_x) * TY;
   const int z0 = blockIdx.y * a.zc, z1 = min(g.nz, z0 + a.zc);
   const int BX = TXN + 8, BY = TY + 2;
@@ -735,7 +741,7 @@ __global__ void __launch_bounds__(256, 3)
   auto x_tile = [&](int st) { return stage_base + st * stage_floats; };
   auto r_tile = [&](int st) { return stage_base + st * stage_floats + arr_floats; };
   const int nq = z1 - z0 + 2;
-  auto issue = [&](int j) {  // x of plane z0-1+j with its halo; rhs of it for planes z0 .. z1-1
+  auto issue = [&](int j) {  // the box of plane z0-1+j; the own rhs of it for planes z0 .. z1-1
     const int st = j % kStages;
     const bool with_r = j >= 1 && j <= nq - 2;
     mbar_expect_tx(&bars[st], box_bytes + (with_r ? own_bytes : 0u));
@@ -763,11 +769,60 @@ __global__ void __launch_bounds__(256, 3)
   const int64_t col = (int64_t)jn * g.nx + i;
   float* ob = m.out + (int64_t)b * g.n;
   const float omega = m.omega;
+  // the in-place scaling (kStage 1): own group, and a halo group for the first threads
+  // (rows -1 and TY of the box: TXT + 2 groups each; columns x0-4 and x0+TXN for rows 0..TY-1)
+  const int GW = TXT + 2;
+  int hgx = 0, hgy = 0;  // halo group: tile-local first node and row
+  bool hduty = false;
+  if (kStage != 0) {
+    if (tid < 2 * GW) {
+      hduty = true;
+      hgx = 4 * (tid % GW) - 4;
+      hgy = tid < GW ? -1 : TY;
+    } else if (tid < 2 * GW + 2 * TY) {
+      hduty = true;
+      const int t = tid - 2 * GW;
+      hgx = t < TY ? -4 : TXN;
+      hgy = t < TY ? t : t - TY;
+    }
+  }
+  const int hofs = (hgy + 1) * BX + hgx + 4;
+  const bool h_in = hduty && x0 + hgx >= 0 && x0 + hgx < g.nx && y0 + hgy >= 0 && y0 + hgy < g.ny;
+  int own_tz = -1, h_tz = -1;  // kStage 1: z class of the cached omega / D
+  float own_od[4] = {0.f, 0.f, 0.f, 0.f}, h_od[4] = {0.f, 0.f, 0.f, 0.f};
+  // scale one 4-node group at box offset o (tile-local first node gx, row gy) of plane z by omega / D
+  auto xform = [&](float* X, int o, int gx, int gy, int z, bool is_own) {
+    float4 v = ld4s(X + o);
+    const int zcl = g.cz[z];
+    float* od = is_own ? own_od : h_od;
+    int& tz = is_own ? own_tz : h_tz;
+    if (zcl != tz) {
+      tz = zcl;
+#pragma unroll
+      for (int e = 0; e < 4; e++)
+        od[e] = omega * cb[(((int64_t)zcl * g.ncy + g.cy[y0 + gy]) * g.ncx + g.cx[x0 + gx + e]) * kCoefStride + 7];
+    }
+    v = make_float4(od[0] * v.x, od[1] * v.y, od[2] * v.z, od[3] * v.w);
+    *reinterpret_cast<float4*>(X + o) = v;
+    return v;
+  };
+  // transform plane index j's stage (own group and halo duty); returns the own group
+  auto xform_plane = [&](int j) -> float4 {
+    const int z = z0 - 1 + j;
+    float* X = x_tile(j % kStages);
+    const bool zin = z >= 0 && z < g.nz;
+    float4 v = ld4s(X + cofs);
+    if (kStage != 0 && zin) {
+      if (own) v = xform(X, cofs, lx, ly, z, true);
+      if (h_in) xform(X, hofs, hgx, hgy, z, false);
+    }
+    return v;
+  };
   float rho = 0.f;
   bool timed_out = !mbar_wait(&bars[0], 0);
-  float4 xm = ld4s(x_tile(0) + cofs);
+  float4 xm = timed_out ? make_float4(0.f, 0.f, 0.f, 0.f) : xform_plane(0);
   if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
-  float4 xc = ld4s(x_tile(1 % kStages) + cofs);
+  float4 xc = timed_out ? make_float4(0.f, 0.f, 0.f, 0.f) : xform_plane(1);
   if (__syncthreads_or(timed_out)) goto abort;
   next_wait = 2;
   if (tid == 0 && kStages < nq) {
@@ -782,43 +837,42 @@ __global__ void __launch_bounds__(256, 3)
       const int k = z - z0 + 1;
       const int sk = k % kStages, sn = (k + 1) % kStages;
       bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
-      if (!to && own) {
-        const float4 xp = ld4s(x_tile(sn) + cofs);
-        const float4 bv = ld4s(r_tile(sk) + lofs);
-        const int zcl = g.cz[z];
-        if (zcl != zcls_cur) {
-          zcls_cur = zcl;
-          const int yc = (int)g.cy[jn];
+      if (!to) {
+        const float4 xp = xform_plane(k + 1);  // plane z+1, transformed (own group and halo duty)
+        if (own) {
+          const float4 bv = ld4s(r_tile(sk) + lofs);
+          const int zcl = g.cz[z];
+          if (zcl != zcls_cur) {
+            zcls_cur = zcl;
+            const int yc = (int)g.cy[jn];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+#pragma unroll
+              for (int q = 0; q < 8; q++) c[e][q] = row[q];
+            }
+          }
+          const float* X = x_tile(sk);
+          const float left = X[cofs - 1], right = X[cofs + 4];
+          const float4 sth = ld4s(X + cofs - BX), nth = ld4s(X + cofs + BX);
+          float o4[4];
 #pragma unroll
           for (int e = 0; e < 4; e++) {
-            const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
-#pragma unroll
-            for (int q = 0; q < 8; q++) c[e][q] = row[q];
+            const float xce = f4(xc, e);
+            float v = c[e][6] * xce;
+            v = fmaf(c[e][0], e == 0 ? left : f4(xc, e - 1), v);
+            v = fmaf(c[e][1], e == 3 ? right : f4(xc, e + 1), v);
+            v = fmaf(c[e][2], f4(sth, e), v);
+            v = fmaf(c[e][3], f4(nth, e), v);
+            v = fmaf(c[e][4], f4(xm, e), v);
+            v = fmaf(c[e][5], f4(xp, e), v);
+            o4[e] = fmaf(omega * c[e][7], f4(bv, e) - v, xce);
+            if (kRho) rho = fmaf(f4(bv, e), o4[e], rho);
           }
+          *reinterpret_cast<float4*>(ob + z * plane + col) = make_float4(o4[0], o4[1], o4[2], o4[3]);
         }
-        const float* X = x_tile(sk);
-        const float left = X[cofs - 1], right = X[cofs + 4];
-        const float4 sth = ld4s(X + cofs - BX), nth = ld4s(X + cofs + BX);
-        float o4[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const float xce = f4(xc, e);
-          float v = c[e][6] * xce;
-          v = fmaf(c[e][0], e == 0 ? left : f4(xc, e - 1), v);
-          v = fmaf(c[e][1], e == 3 ? right : f4(xc, e + 1), v);
-          v = fmaf(c[e][2], f4(sth, e), v);
-          v = fmaf(c[e][3], f4(nth, e), v);
-          v = fmaf(c[e][4], f4(xm, e), v);
-          v = fmaf(c[e][5], f4(xp, e), v);
-          o4[e] = fmaf(omega * c[e][7], f4(bv, e) - v, xce);
-          if (kRho) rho = fmaf(f4(bv, e), o4[e], rho);
-        }
-        *reinterpret_cast<float4*>(ob + z * plane + col) = make_float4(o4[0], o4[1], o4[2], o4[3]);
         xm = xc;
         xc = xp;
-      } else if (!to) {
-        xm = xc;
-        xc = ld4s(x_tile(sn) + cofs);
       }
       if (__syncthreads_or(to)) goto abort;
       next_wait = k + 2;
@@ -912,17 +966,24 @@ void tma_prepare() {
   cudaFuncSetAttribute(k_cg_a_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_cg_b_s_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mg_fine_rr_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_mg_smooth_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_mg_smooth_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_smooth_tma<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_smooth_tma<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_smooth_tma<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, bool rho, cudaStream_t s) {
-  if (!tma_supported(a.g, t) || (rho && m.slot < 0)) return -1;
+int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, int stage, const MGFineArgs& m, bool rho, cudaStream_t s) {
+  if (!tma_supported(a.g, t) || (rho && m.slot < 0) || (rho && stage != 0) || stage < 0 || stage > 1) return -1;
+  const int NT = t.tx * t.ty;
+  if (stage != 0 && 2 * (t.tx + 2) + 2 * t.ty > NT) return -1;  // halo groups: one per thread at most
   CUtensorMap mx, mr;
-  if (make_map(&mx, m.xin, a.g, a.B, t) || make_map(&mr, m.rhs, a.g, a.B, t, false)) return -1;
+  const float* boxed = stage == 1 ? m.rhs : m.xin;
+  if (make_map(&mx, boxed, a.g, a.B, t) || make_map(&mr, m.rhs, a.g, a.B, t, false)) return -1;
+  const size_t smem = ring_bytes(t, 1, 1);
   const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
-  if (rho) k_mg_smooth_tma<true><<<grid, block, ring_bytes(t, 1, 1), s>>>(mx, mr, a, m, a.active + 2);
-  else k_mg_smooth_tma<false><<<grid, block, ring_bytes(t, 1, 1), s>>>(mx, mr, a, m, a.active + 2);
+  int* err = a.active + 2;
+  if (rho) k_mg_smooth_tma<0, true><<<grid, block, smem, s>>>(mx, mr, a, m, err);
+  else if (stage == 0) k_mg_smooth_tma<0, false><<<grid, block, smem, s>>>(mx, mr, a, m, err);
+  else k_mg_smooth_tma<1, false><<<grid, block, smem, s>>>(mx, mr, a, m, err);
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return -1;

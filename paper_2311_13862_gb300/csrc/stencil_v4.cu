@@ -1135,13 +1135,15 @@ int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const
   const size_t smem = v4_plane_smem(t);
   // the coarse planes of a z-chunk: (zc/2 + 3) planes of (2 tx + 2) x (ty/2 + 3)
   const size_t smem_c = smem + mg_fine_coarse_smem(t, a.zc);
-  if (stage == 1 && outk == 0) k_mg_fine_v4<1, 0><<<grid, block, smem, s>>>(a, m);
+  if (stage == 1 && outk == 0) {
+    if (launch_mg_smooth_tma(a, t, 1, m, false, s)) k_mg_fine_v4<1, 0><<<grid, block, smem, s>>>(a, m);
+  }
   else if (stage == 0 && outk == 1) k_mg_fine_v4<0, 1><<<grid, block, smem, s>>>(a, m);
   else if (stage == 2 && outk == 0) k_mg_fine_v4<2, 0><<<grid, block, smem_c, s>>>(a, m);
   else if (stage == 0 && outk == 2) {
-    if (launch_mg_smooth_tma(a, t, m, true, s)) k_mg_fine_v4<0, 2><<<grid, block, smem, s>>>(a, m);
+    if (launch_mg_smooth_tma(a, t, 0, m, true, s)) k_mg_fine_v4<0, 2><<<grid, block, smem, s>>>(a, m);
   } else if (stage == 0 && outk == 0) {
-    if (launch_mg_smooth_tma(a, t, m, false, s)) k_mg_fine_v4<0, 0><<<grid, block, smem, s>>>(a, m);
+    if (launch_mg_smooth_tma(a, t, 0, m, false, s)) k_mg_fine_v4<0, 0><<<grid, block, smem, s>>>(a, m);
   }
   else if (stage == 0 && outk == 3) return launch_mg_fine_rr_tma(a, t, m, s);
   else return -1;
