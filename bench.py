@@ -547,12 +547,13 @@ def main():
         # read r, write Y (8); read Y, r, write the restricted residual at 1/8 of the nodes
         # (8.5); read and write Y, the coarse correction at 1/8 of the nodes, then read Y, r,
         # write X (8 + 0.5 + 12, two launches timed together); read X, r, write s (12)
-        fine_kernels = [("k_mg_fine_v4<1,0> (two damped Jacobi steps from zero)", 8.0, "mg_fine_smooth_pre_f32_64cube"),
+        fine_kernels = [("k_mg_smooth_tma<1,0> (two damped Jacobi steps from zero)", 8.0,
+                         "mg_fine_smooth_pre_f32_64cube"),
                         ("k_mg_fine_rr_tma (restricted residual P^T (r - A Y))", 8.5,
                          "mg_fine_residual_restrict_f32_64cube"),
-                        ("k_mg_prolong_add4 + k_mg_fine_v4<0,0> (Y += P e; damped Jacobi step)", 20.5,
+                        ("k_mg_prolong_add4 + k_mg_smooth_tma<0,0> (Y += P e; damped Jacobi step)", 20.5,
                          "mg_fine_prolong_smooth_f32_64cube"),
-                        ("k_mg_fine_v4<0,2> (damped Jacobi step + rho partials)", 12.0,
+                        ("k_mg_smooth_tma<0,1> (damped Jacobi step + rho partials)", 12.0,
                          "mg_fine_smooth_rho_f32_64cube")]
         for (name, alg, tag), t_ms in zip(fine_kernels, acc["mg_fine_ms"]):
             gbs = acc["active_dofs"] * alg / (t_ms * 1e-3) / 1e9
