@@ -1,0 +1,87 @@
+"""Per-instance right-hand sides for the oracle: the Gaussian source (a non-affine f(mu), the
+shape of the paper's Example 2, Sec. 4) and the greedy RB of Algorithm 5 with one right-hand
+side per training parameter, written plainly with numpy on top of the oracle's C operator and
+PCG.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, never by the product.  Shares no code with
+the CUDA library.
+
+Readings where the paper leaves a choice open (the same as the oracle's fixed-f greedy):
+  * first parameter: index 0 of the training set;
+  * Gram-Schmidt twice against the current basis; a snapshot whose orthogonal part is below
+    1e-10 of its norm ends the greedy (no new direction);
+  * indicator: ||f_t - A(mu_t) W c_t|| / ||f_t|| with the Galerkin coefficients
+    A_N(mu_t) c_t = W^T f_t; the largest over the training points not yet selected, ties to
+    the smallest index.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import Basis, assemble, pcg  # noqa: F401  (assemble re-exported for callers)
+
+
+def gaussian_source(grid, params) -> np.ndarray:
+    """f[b] = exp(-|x - c_b|^2 / (2 s_b^2)) at the interior nodes x = ((i+1)/(nx+1), ...), in
+    [z][y][x] order; params [B][4] = (c_x, c_y, c_z, s_b)."""
+    nx, ny, nz = grid
+    x = np.arange(1, nx + 1) / (nx + 1)
+    y = np.arange(1, ny + 1) / (ny + 1)
+    z = np.arange(1, nz + 1) / (nz + 1)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    out = []
+    for cx, cy, cz, sg in np.atleast_2d(params):
+        d2 = (X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2
+        out.append(np.exp(-d2 / (2.0 * sg * sg)).ravel())
+    return np.array(out)
+
+
+def greedy_rhs(op, mu_train, F_train, n_max, snapshot_tol=1e-12) -> Basis:
+    """Algorithm 5's loop (Galerkin RB, residual indicator) with right-hand side F_train[t] for
+    training parameter t."""
+    mu_train = np.asarray(mu_train, dtype=np.float64)
+    F = np.asarray(F_train, dtype=np.float64)
+    n_train = mu_train.shape[0]
+    W = []
+    sel, eta_hist = [], []
+    taken = np.zeros(n_train, dtype=bool)
+    nxt = 0
+    while len(W) < n_max:
+        u = pcg(op, mu_train[nxt], f=F[nxt], tol=snapshot_tol, max_iters=100000).u
+        w = u.copy()
+        for _ in range(2):
+            for v in W:
+                w -= (v @ w) * v
+        if not np.linalg.norm(w) >= 1e-10 * np.linalg.norm(u):
+            break
+        W.append(w / np.linalg.norm(w))
+        sel.append(nxt)
+        taken[nxt] = True
+        Wa = np.array(W)
+        eta = np.full(n_train, -1.0)
+        for t in range(n_train):
+            if taken[t]:
+                continue
+            AW = np.array([op.matvec(mu_train[t], v) for v in Wa])   # rows A(mu_t) w_j
+            c = np.linalg.solve(Wa @ AW.T, Wa @ F[t])
+            eta[t] = np.linalg.norm(F[t] - c @ AW) / np.linalg.norm(F[t])
+        if taken.all():
+            eta_hist.append(np.nan)
+            break
+        nxt = int(np.argmax(eta))
+        eta_hist.append(float(eta[nxt]))
+    Wa = np.array(W)
+    Q = op.Q
+    ANq = np.zeros((Q, len(W), len(W)))
+    for q in range(Q):
+        e = np.eye(Q)[q]
+        ANq[q] = Wa @ np.array([op.matvec(e, v) for v in Wa]).T
+    fN = Wa @ np.ones(op.n)
+    return Basis(Wa, ANq, fN, np.array(sel, dtype=np.int32), np.array(eta_hist), len(W))
+
+
+def rb_start(basis: Basis, mu, f) -> np.ndarray:
+    """The Galerkin RB solution W^T c with A_N(mu) c = W^T f (reduced system from the affine terms)."""
+    A = np.tensordot(np.asarray(mu, dtype=np.float64), basis.ANq, axes=1)
+    c = np.linalg.solve(A, basis.W @ np.asarray(f, dtype=np.float64))
+    return basis.W.T @ c
