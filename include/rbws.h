@@ -231,6 +231,34 @@ RBWS_API rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, 
                                         double snapshot_tol, int32_t* selected_out, double* eta_hist_out,
                                         int32_t* n_out);
 
+/* Per-instance right-hand sides (a non-affine source f(mu), the shape of the paper's
+ * Example 2, Sec. 4).  The library does not store them: the caller passes device arrays.
+ *
+ * rbws_gaussian_source: f_out (device [B][n] FP64, caller-owned) = exp(-|x - c_b|^2 /
+ * (2 s_b^2)) at the interior nodes x = ((i+1)/(nx+1), (j+1)/(ny+1), (k+1)/(nz+1)), with
+ * params (host [B][4]) = (c_x, c_y, c_z, s_b).  RBWS_ERR_INVALID_ARG if s_b <= 0. */
+RBWS_API rbws_status rbws_gaussian_source(rbws_problem p, const double* params, int32_t B, void* f_out);
+
+/* rbws_solve_batch with right-hand side f_b (device [B][n] FP64, row b) for instance b
+ * instead of the problem's f.  The relative residuals are against ||f_b||.  Warm starts:
+ * RBWS_WARM_ZERO and RBWS_WARM_GALERKIN (c_b from A_N(mu_b) c_b = W^T f_b; W^T f_b formed
+ * on the device); preconditioners other than MSRB.  Others return RBWS_ERR_UNSUPPORTED;
+ * a zero f_b RBWS_ERR_INVALID_ARG. */
+RBWS_API rbws_status rbws_solve_batch_rhs(rbws_problem p, const double* mu, int32_t B, const void* f,
+                                          double tol, int32_t warm, const rbws_options* opt, void* u_out,
+                                          int32_t* iters_out, double* relres_out, int32_t* status_out);
+
+/* rbws_offline_greedy (residual indicator) with a right-hand side f_t per training
+ * parameter (f_train: device [n_train][n] FP64): the snapshot of mu_t solves A(mu_t) u = f_t
+ * and the indicator is ||f_t - A(mu_t) W c_t|| / ||f_t|| with A_N(mu_t) c_t = W^T f_t.
+ * The basis then serves rbws_solve_batch_rhs (and rbws_solve_batch, whose reduced right-hand
+ * side stays W^T f for the problem's f).  Scratch: n_train x n_max doubles besides the
+ * greedy's own. */
+RBWS_API rbws_status rbws_offline_greedy_rhs(rbws_problem p, const double* mu_train, const void* f_train,
+                                             int32_t n_train, int32_t n_max, double greedy_tol,
+                                             double snapshot_tol, int32_t* selected_out,
+                                             double* indicator_hist_out, int32_t* n_out);
+
 /* Accuracy of the RB space as a function of its dimension (the r_N-versus-N view
  * of Sec. 5's offline-cost discussion, and the Galerkin RB method of Sec. 2.3):
  * relres_out[b] (host [B]) = ||f - A(mu_b) W_n c_n(mu_b)||_2 / ||f||_2, with

@@ -160,6 +160,16 @@ struct rbws_problem_s {
   double* d_f = nullptr;     // nullptr: f == 1
   double* d_ones = nullptr;  // ones vector (for W^T f when f == 1)
   double fnorm = 0.0;
+  // Per-instance right-hand sides of the current call (f == nullptr: the problem's f above):
+  // f_b = f + b * stride, ||f_b|| = norms[b]; the reduced right-hand sides W^T f_b at
+  // fN[b * fN_sb + j * fN_sj] when precomputed (else formed where needed).
+  struct RhsView {
+    const double* f = nullptr;
+    int64_t stride = 0;
+    const double* norms = nullptr;
+    const double* fN = nullptr;
+    int64_t fN_sb = 0, fN_sj = 1;
+  } rhs;
   cudaStream_t stream = nullptr;  // internal stream (used when the caller passes none)
   cudaStream_t cur = nullptr;     // work stream of the current call
   cudaEvent_t ev = nullptr;
@@ -515,8 +525,10 @@ rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const do
   int err = 0;
   double* part = (double*)p->buf("res_part", sizeof(double) * (size_t)B * P, &err);
   if (err) return (rbws_status)err;
-  launch_residual64(p->geo, t, zc, coef64, B, p->d_f, u, r_out, part, P, mask, p->cur);
-  launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->cur);
+  const bool own_f = p->rhs.f != nullptr;
+  launch_residual64(p->geo, t, zc, coef64, B, own_f ? p->rhs.f : p->d_f, u, r_out, part, P, mask, p->cur,
+                    own_f ? p->rhs.stride : 0);
+  launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->cur, own_f ? p->rhs.norms : nullptr);
   p->launches += 2;
   CK(cudaGetLastError());
   return RBWS_OK;
@@ -548,7 +560,26 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u,
   double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
   int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
-  launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, nullptr, p->cur);
+  if (p->rhs.f) {  // per-instance right-hand sides: W^T f_b (given, or N dot launches over the batch)
+    const double* fN = p->rhs.fN;
+    int64_t sb = p->rhs.fN_sb, sj = p->rhs.fN_sj;
+    if (!fN) {
+      double* FN = (double*)p->buf("rhs_FN", sizeof(double) * (size_t)p->N * B, &err);
+      const int scratch_len = 256 * (B + 2);
+      double* scr = err ? nullptr : (double*)p->buf("rhs_scr", sizeof(double) * scratch_len, &err);
+      if (err) return (rbws_status)err;
+      for (int j = 0; j < p->N; j++)
+        launch_multi_dot(p->n, B, p->rhs.f, p->rhs.stride, p->d_W + (int64_t)j * p->n, FN + (int64_t)j * B, scr,
+                         scratch_len, p->cur);
+      p->launches += p->N;
+      fN = FN;
+      sb = 1;
+      sj = B;
+    }
+    launch_reduced_solve(p->N, p->Q, p->d_ANq, fN, d_mu, B, C, info, nullptr, p->cur, sb, sj);
+  } else {
+    launch_reduced_solve(p->N, p->Q, p->d_ANq, p->d_fN, d_mu, B, C, info, nullptr, p->cur);
+  }
   p->launches += 1;
   CKI(lift(p, C, B, u, fp32));
   CK(cudaGetLastError());
@@ -650,7 +681,8 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
   Tile t = choose_tile(p->nx);
   CGArgs<double> a{};
   CKI(make_cg_args<double>(p, B, t, coef64, u, &a, "d_"));
-  a.f = p->d_f;
+  a.f = p->rhs.f ? p->rhs.f : p->d_f;
+  a.f_stride = p->rhs.f ? p->rhs.stride : 0;
   a.tol = tol;
   a.max_iters = o.max_iters;
   a.precond = o.precond;
@@ -687,7 +719,8 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
     CKI(mg_batch(p, d_mu, B, coef64, 0, a.st, &mgb));
     a.mg = &mgb;
   }
-  fill((double*)a.fnorm, B, p->fnorm, p->cur);
+  if (p->rhs.f) CK(cudaMemcpyAsync((double*)a.fnorm, p->rhs.norms, sizeof(double) * B, cudaMemcpyDeviceToDevice, p->cur));
+  else fill((double*)a.fnorm, B, p->fnorm, p->cur);
   p->launches += 1;
   if (o.relres_hist) {
     int err = 0;
@@ -831,7 +864,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     if (err) return (rbws_status)err;
     CK(cudaMemsetAsync(a.alpha, 0, sizeof(double) * 2 * (size_t)B, s));
   }
-  fill((double*)a.fnorm, B, p->fnorm, s);
+  if (p->rhs.f) CK(cudaMemcpyAsync((double*)a.fnorm, p->rhs.norms, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
+  else fill((double*)a.fnorm, B, p->fnorm, s);
   CK(cudaMemsetAsync(d, 0, sizeof(float) * (size_t)B * p->n, s));
   // start: every instance takes an update from u (restarting its direction)
   std::vector<int> two(B, 2);
@@ -1757,16 +1791,15 @@ rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_t B, doub
   return RBWS_OK;
 }
 
-rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
-                                int32_t n_max, double greedy_tol, double snapshot_tol,
-                                int32_t indicator, int32_t* selected_out, double* eta_hist_out,
-                                int32_t* n_out) {
-  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 160 || !(snapshot_tol > 0.0) ||
-      (indicator != RBWS_INDICATOR_RESIDUAL && indicator != RBWS_INDICATOR_L1)) {
-    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 160, snapshot_tol > 0, indicator 0 or 1)");
-    return RBWS_ERR_INVALID_ARG;
-  }
-  StreamGuard sg(p, nullptr);
+namespace {
+
+// Algorithm 5's greedy loop with Galerkin RB (the residual or the L1 indicator).  f_train
+// (device [n_train][n], or nullptr for the problem's f): a right-hand side per training
+// parameter, with norms f_norms (device [n_train]); snapshots then solve A(mu_t) u = f_t and the
+// residual indicator uses f_t and W^T f_t.
+rbws_status greedy_impl(rbws_problem p, const double* mu_train, int32_t n_train, int32_t n_max,
+                        double greedy_tol, double snapshot_tol, int32_t indicator, const double* f_train,
+                        const double* f_norms, int32_t* selected_out, double* eta_hist_out, int32_t* n_out) {
   cudaStream_t s = p->cur;
   const int64_t n = p->n;
   const int Q = p->Q;
@@ -1794,6 +1827,13 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   double* scratch = err ? nullptr : (double*)p->buf("g_scratch", sizeof(double) * scratch_len, &err);
   double* eye = err ? nullptr : (double*)p->buf("g_eye", sizeof(double) * (size_t)Q * Q, &err);
   double* dR = err ? nullptr : (double*)p->buf("g_R", sizeof(double) * (size_t)n_max * n_max, &err);
+  double* FNt = nullptr;  // [n_max][n_train]: W^T f_t of the training right-hand sides
+  double* tscratch = nullptr;
+  const int tscratch_len = 256 * (n_train + 2);
+  if (!err && f_train) {
+    FNt = (double*)p->buf("g_FNt", sizeof(double) * (size_t)n_max * n_train, &err);
+    if (!err) tscratch = (double*)p->buf("g_tscratch", sizeof(double) * tscratch_len, &err);
+  }
   if (err) return (rbws_status)err;
   std::vector<double> Rh((size_t)n_max * n_max, 0.0);  // u_k = sum_j R[j][k] w_j (Gram-Schmidt factor)
   {
@@ -1815,10 +1855,17 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   int N = 0, next = 0;
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_train, ((int64_t)1 << 28) / n));
   while (N < n_max) {
-    // snapshot u(mu_next) by Jacobi-PCG from zero
+    // snapshot u(mu_next) by Jacobi-PCG from zero (with its own right-hand side if given)
     std::vector<InstState> st;
     CK(cudaMemsetAsync(usnap, 0, sizeof(double) * n, s));
-    CKI(solve_fp64(p, d_mu + (int64_t)next * Q, 1, snapshot_tol, o, usnap, st));
+    if (f_train) {
+      p->rhs = {};
+      p->rhs.f = f_train + (int64_t)next * n;
+      p->rhs.norms = f_norms + next;
+    }
+    const rbws_status rs = solve_fp64(p, d_mu + (int64_t)next * Q, 1, snapshot_tol, o, usnap, st);
+    p->rhs = {};
+    if (rs != RBWS_OK) return rs;
     // A snapshot whose true residual stalls above snapshot_tol at the rounding
     // floor of the FP64 residual (large, high-contrast grids) is still used if
     // that residual is below 1e-9.
@@ -1857,6 +1904,8 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
       launch_multi_dot(n, N + 1, p->d_W, n, V + (int64_t)q * n, dots + (int64_t)q * (N + 1), scratch,
                        scratch_len, s);
     launch_multi_dot(n, 1, wN, n, fvec, dots + (int64_t)Q * (N + 1), scratch, scratch_len, s);
+    if (f_train)  // column N of the training set's reduced right-hand sides: FNt[N][t] = w_N . f_t
+      launch_multi_dot(n, n_train, f_train, n, wN, FNt + (int64_t)N * n_train, tscratch, tscratch_len, s);
     CK(cudaGetLastError());
     std::vector<double> hd((size_t)Q * (N + 1) + 1);
     CK(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s));
@@ -1901,10 +1950,20 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
         double* U = (double*)p->buf("g_U", sizeof(double) * (size_t)Bc * n, &err);
         double* etad = err ? nullptr : (double*)p->buf("g_eta", sizeof(double) * (size_t)Bc, &err);
         if (err) return (rbws_status)err;
-        CKI(galerkin_start(p, d_mu + b0 * Q, Bc, U));
+        if (f_train) {  // the chunk's own right-hand sides and their reduced projections
+          p->rhs.f = f_train + b0 * n;
+          p->rhs.stride = n;
+          p->rhs.norms = f_norms + b0;
+          p->rhs.fN = FNt + b0;
+          p->rhs.fN_sb = 1;
+          p->rhs.fN_sj = n_train;
+        }
+        rbws_status rs = galerkin_start(p, d_mu + b0 * Q, Bc, U);
         double* cc = nullptr;
-        CKI(coef_tables(p, d_mu + b0 * Q, Bc, &cc, nullptr));
-        CKI(residual_norms(p, cc, Bc, U, nullptr, etad));
+        if (rs == RBWS_OK) rs = coef_tables(p, d_mu + b0 * Q, Bc, &cc, nullptr);
+        if (rs == RBWS_OK) rs = residual_norms(p, cc, Bc, U, nullptr, etad);
+        p->rhs = {};
+        if (rs != RBWS_OK) return rs;
         CK(cudaMemcpyAsync(eta.data() + b0, etad, sizeof(double) * Bc, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
       }
@@ -1927,6 +1986,120 @@ rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t 
   if (eta_hist_out) std::copy(hist.begin(), hist.end(), eta_hist_out);
   if (n_out) *n_out = N;
   // compact A_N^q to [Q][N][N] on the device (already done above)
+  return RBWS_OK;
+}
+
+}  // namespace
+
+rbws_status rbws_offline_greedy(rbws_problem p, const double* mu_train, int32_t n_train,
+                                int32_t n_max, double greedy_tol, double snapshot_tol,
+                                int32_t indicator, int32_t* selected_out, double* eta_hist_out,
+                                int32_t* n_out) {
+  if (!p || !mu_train || n_train < 1 || n_max < 1 || n_max > 160 || !(snapshot_tol > 0.0) ||
+      (indicator != RBWS_INDICATOR_RESIDUAL && indicator != RBWS_INDICATOR_L1)) {
+    set_error("rbws_offline_greedy: invalid argument (1 <= n_max <= 160, snapshot_tol > 0, indicator 0 or 1)");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  return greedy_impl(p, mu_train, n_train, n_max, greedy_tol, snapshot_tol, indicator, nullptr, nullptr,
+                     selected_out, eta_hist_out, n_out);
+}
+
+namespace {
+
+// Norms ||f_b|| (device [B]) of caller right-hand sides; RBWS_ERR_INVALID_ARG if one is zero.
+rbws_status rhs_norms(rbws_problem p, const double* f, int B, const char* tag, double** out) {
+  int err = 0;
+  double* nrm = (double*)p->buf(tag, sizeof(double) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  launch_row_norms(p->n, B, f, p->n, nrm, p->cur);
+  std::vector<double> h(B);
+  CK(cudaMemcpyAsync(h.data(), nrm, sizeof(double) * B, cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  for (int b = 0; b < B; b++)
+    if (!(h[b] > 0.0) || !std::isfinite(h[b])) {
+      set_error("right-hand side " + std::to_string(b) + " is zero or not finite");
+      return RBWS_ERR_INVALID_ARG;
+    }
+  *out = nrm;
+  return RBWS_OK;
+}
+
+}  // namespace
+
+rbws_status rbws_offline_greedy_rhs(rbws_problem p, const double* mu_train, const void* f_train, int32_t n_train,
+                                    int32_t n_max, double greedy_tol, double snapshot_tol, int32_t* selected_out,
+                                    double* eta_hist_out, int32_t* n_out) {
+  if (!p || !mu_train || !f_train || n_train < 1 || n_max < 1 || n_max > 160 || !(snapshot_tol > 0.0)) {
+    set_error("rbws_offline_greedy_rhs: invalid argument (1 <= n_max <= 160, snapshot_tol > 0)");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  double* nrm = nullptr;
+  CKI(rhs_norms(p, (const double*)f_train, n_train, "g_fnorms", &nrm));
+  const rbws_status rc = greedy_impl(p, mu_train, n_train, n_max, greedy_tol, snapshot_tol, RBWS_INDICATOR_RESIDUAL,
+                                     (const double*)f_train, nrm, selected_out, eta_hist_out, n_out);
+  p->rhs = {};
+  return rc;
+}
+
+rbws_status rbws_solve_batch_rhs(rbws_problem p, const double* mu, int32_t B, const void* f, double tol,
+                                 int32_t warm, const rbws_options* opt, void* u_out, int32_t* iters_out,
+                                 double* relres_out, int32_t* status_out) {
+  rbws_options o;
+  rbws_options_default(&o);
+  if (opt) o = *opt;
+  if (!p || !mu || !f || !u_out || !iters_out || B < 1 || B > 65535) {
+    set_error("rbws_solve_batch_rhs: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  CKI(check_solve_options(o, tol, warm));
+  if ((warm != RBWS_WARM_ZERO && warm != RBWS_WARM_GALERKIN) || o.precond == RBWS_PREC_MSRB) {
+    set_error("rbws_solve_batch_rhs: per-instance right-hand sides take the zero or Galerkin start and "
+              "no MSRB preconditioner");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  StreamGuard sg(p, o.stream);
+  double* nrm = nullptr;
+  CKI(rhs_norms(p, (const double*)f, B, "rhs_norms", &nrm));
+  p->rhs = {};
+  p->rhs.f = (const double*)f;
+  p->rhs.stride = p->n;
+  p->rhs.norms = nrm;
+  std::vector<InstState> st;
+  const rbws_status rc = solve_batch_impl(p, mu, B, tol, warm, o, (double*)u_out, st);
+  p->rhs = {};
+  if (rc != RBWS_OK) return rc;
+  int warn = 0;
+  for (int b = 0; b < B; b++) {
+    iters_out[b] = st[b].iters;
+    if (relres_out) relres_out[b] = st[b].relres;
+    const int sb = st[b].status == ST_CONVERGED ? 0 : (st[b].status == ST_BREAKDOWN ? 2 : 1);
+    if (status_out) status_out[b] = sb;
+    warn |= sb != 0;
+  }
+  return warn ? RBWS_WARN_NOT_CONVERGED : RBWS_OK;
+}
+
+rbws_status rbws_gaussian_source(rbws_problem p, const double* params, int32_t B, void* f_out) {
+  if (!p || !params || !f_out || B < 1 || B > 65535) {
+    set_error("rbws_gaussian_source: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  for (int b = 0; b < B; b++)
+    if (!(params[4 * b + 3] > 0.0) || !std::isfinite(params[4 * b]) || !std::isfinite(params[4 * b + 1]) ||
+        !std::isfinite(params[4 * b + 2])) {
+      set_error("rbws_gaussian_source: the width must be positive and the centre finite");
+      return RBWS_ERR_INVALID_ARG;
+    }
+  StreamGuard sg(p, nullptr);
+  int err = 0;
+  double* d_prm = (double*)p->buf("gauss_prm", sizeof(double) * 4 * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(d_prm, params, sizeof(double) * 4 * B, cudaMemcpyHostToDevice, p->cur));
+  launch_gaussian_source(p->nx, p->ny, p->nz, d_prm, B, (double*)f_out, p->cur);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->cur));
   return RBWS_OK;
 }
 

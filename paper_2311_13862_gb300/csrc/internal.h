@@ -112,6 +112,7 @@ struct CGArgs {
   int P;                // CTAs (partials) per instance = tiles_x*tiles_y*nzc
   const T* coef;        // [B][ncls][8]
   const T* f;           // right-hand side [n] (shared) or nullptr -> 1 (init kernel only)
+  int64_t f_stride;     // 0: one f for every instance; n: f is [B][n]
   const double* rhs64;  // FP32_IR init: FP64 residual [B][n] to be scaled, else nullptr
   const double* rhs_scale; // FP32_IR init: per-instance norm of rhs64 (the inner rhs is rhs64/norm)
   T* u;                 // [B][n]
@@ -178,9 +179,10 @@ void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_
 
 // r = f - A u (FP64) per instance; rr partials [B][P] and the residual
 // written to r (if non-null); instances with mask[b] == 0 are skipped.
+// f: the right-hand side ([n], or [B][n] with f_stride = n; nullptr: f = 1).
 void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
                        const double* u, double* r, double* rr_part, int P, const int* mask,
-                       cudaStream_t s);
+                       cudaStream_t s, int64_t f_stride = 0);
 // FP32 phase kernels with 4 nodes per thread (stencil_v4.cu; nx % 4 == 0).
 // Tile: t.tx threads x 4 nodes in x, t.ty rows.
 void launch_cg_a_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s);
@@ -233,8 +235,10 @@ void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restar
 // c[b] = (sum_q mu[b][q] ANq[q])^{-1} fN; info[b] = 0 or -1 (not SPD).  If
 // L_out is non-null the Cholesky factor of each A_N(mu_b) is stored there
 // ([B][N][N], lower triangle, upper part zero).
+// fN element (b, j) at fN[b * f_sb + j * f_sj]: (0, 1) = one reduced right-hand side for all.
 void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu,
-                          int B, double* c, int* info, double* L_out, cudaStream_t s);
+                          int B, double* c, int* info, double* L_out, cudaStream_t s, int64_t f_sb = 0,
+                          int64_t f_sj = 1);
 // eta[b] = ||R^{-1} c[b]||_1 with R upper triangular [Nmax][Nmax] (L1 indicator);
 // +inf where info[b] != 0.
 void launch_l1_indicator(int N, int Nmax, const double* R, const double* c, const int* info, int B,
@@ -255,8 +259,13 @@ void launch_sub_combination(int64_t n, int K, const double* W, const double* coe
 // w *= 1/alpha (alpha device scalar)
 void launch_scale_inv(int64_t n, const double* alpha, double* w, cudaStream_t s);
 // per-instance eta[b] = sqrt(sum partials)/fnorm
+// out[b] = sqrt(sum of the P partials of b) / (fnorms ? fnorms[b] : fnorm).
 void launch_norms_from_partials(const double* part, int B, int P, double fnorm, double* out,
-                                cudaStream_t s);
+                                cudaStream_t s, const double* fnorms = nullptr);
+// out[b] = ||X[b]||_2, rows of length n with stride ldx.
+void launch_row_norms(int64_t n, int B, const double* X, int64_t ldx, double* out, cudaStream_t s);
+// f[b] = the Gaussian source exp(-|x - c_b|^2 / (2 s_b^2)) on the interior nodes, prm device [B][4].
+void launch_gaussian_source(int nx, int ny, int nz, const double* prm, int B, double* f, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Learned warm start (mlp.cu)

@@ -3,6 +3,8 @@
 // greedy (projections W^T y, Gram-Schmidt updates).  All FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace rbws {
@@ -19,8 +21,8 @@ __device__ __forceinline__ double warp_sum_down(double v) {
 // One CTA per parameter: A = sum_q mu_q ANq[q] in shared memory, right-looking
 // Cholesky, then the two triangular solves for c = A^{-1} fN.
 __global__ void k_reduced_solve(int N, int Q, const double* __restrict__ ANq,
-                                const double* __restrict__ fN, const double* __restrict__ mu,
-                                double* __restrict__ c, int* __restrict__ info,
+                                const double* __restrict__ fN, int64_t f_sb, int64_t f_sj,
+                                const double* __restrict__ mu, double* __restrict__ c, int* __restrict__ info,
                                 double* __restrict__ L_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* A = reinterpret_cast<double*>(smem_raw);  // N*N
@@ -33,7 +35,7 @@ __global__ void k_reduced_solve(int N, int Q, const double* __restrict__ ANq,
     for (int q = 0; q < Q; q++) s = fma(m[q], ANq[(int64_t)q * N * N + e], s);
     A[e] = s;
   }
-  for (int e = threadIdx.x; e < N; e += blockDim.x) x[e] = fN[e];
+  for (int e = threadIdx.x; e < N; e += blockDim.x) x[e] = fN[(int64_t)b * f_sb + (int64_t)e * f_sj];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < N; j++) {
@@ -177,14 +179,46 @@ __global__ void k_scale_inv(int64_t n, const double* __restrict__ alpha, double*
 }
 
 __global__ void k_norms_from_partials(const double* __restrict__ part, int B, int P, double fnorm,
-                                      double* __restrict__ out) {
+                                      const double* __restrict__ fnorms, double* __restrict__ out) {
   const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;
   double s = 0.0;
   for (int c = lane; c < P; c += 32) s += part[(int64_t)b * P + c];
   s = warp_sum_down(s);
-  if (lane == 0) out[b] = sqrt(s) / fnorm;
+  if (lane == 0) out[b] = sqrt(s) / (fnorms ? fnorms[b] : fnorm);
+}
+
+// out[b] = ||X[b]||_2 for rows of length n, stride ldx (one CTA per row, FP64).
+__global__ void k_row_norms(int64_t n, const double* __restrict__ X, int64_t ldx, double* __restrict__ out) {
+  __shared__ double red[32];
+  const double* x = X + (int64_t)blockIdx.x * ldx;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(x[i], x[i], s);
+  s = warp_sum_down(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    s = warp_sum_down(s);
+    if (lane == 0) out[blockIdx.x] = sqrt(s);
+  }
+}
+
+// f[b][node] = exp(-|x(node) - c_b|^2 / (2 s_b^2)) at the interior nodes x = ((i+1) hx,
+// (j+1) hy, (k+1) hz); prm[b] = (c_x, c_y, c_z, s_b).
+__global__ void k_gaussian_source(int nx, int ny, int nz, const double* __restrict__ prm, double* __restrict__ f) {
+  const int b = blockIdx.y;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const double cx = prm[4 * b], cy = prm[4 * b + 1], cz = prm[4 * b + 2], sg = prm[4 * b + 3];
+  const double hx = 1.0 / (nx + 1), hy = 1.0 / (ny + 1), hz = 1.0 / (nz + 1);
+  const double inv = 1.0 / (2.0 * sg * sg);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((int64_t)nx * ny));
+    const double dx = (i + 1) * hx - cx, dy = (j + 1) * hy - cy, dz = (k + 1) * hz - cz;
+    f[(int64_t)b * n + t] = exp(-(dx * dx + dy * dy + dz * dz) * inv);
+  }
 }
 
 // eta[b] = || R^{-1} c[b] ||_1 (R upper triangular [Nmax][Nmax]): the L1 norm of
@@ -218,11 +252,11 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 }  // namespace
 
 void launch_reduced_solve(int N, int Q, const double* ANq, const double* fN, const double* mu, int B,
-                          double* c, int* info, double* L_out, cudaStream_t s) {
+                          double* c, int* info, double* L_out, cudaStream_t s, int64_t f_sb, int64_t f_sj) {
   const size_t smem = sizeof(double) * ((size_t)N * N + N);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_reduced_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_reduced_solve<<<B, 128, smem, s>>>(N, Q, ANq, fN, mu, c, info, L_out);
+  k_reduced_solve<<<B, 128, smem, s>>>(N, Q, ANq, fN, f_sb, f_sj, mu, c, info, L_out);
 }
 
 void launch_l1_indicator(int N, int Nmax, const double* R, const double* c, const int* info, int B,
@@ -265,8 +299,18 @@ void launch_scale_inv(int64_t n, const double* alpha, double* w, cudaStream_t s)
 }
 
 void launch_norms_from_partials(const double* part, int B, int P, double fnorm, double* out,
-                                cudaStream_t s) {
-  k_norms_from_partials<<<(B + 3) / 4, 128, 0, s>>>(part, B, P, fnorm, out);
+                                cudaStream_t s, const double* fnorms) {
+  k_norms_from_partials<<<(B + 3) / 4, 128, 0, s>>>(part, B, P, fnorm, fnorms, out);
+}
+
+void launch_row_norms(int64_t n, int B, const double* X, int64_t ldx, double* out, cudaStream_t s) {
+  if (B > 0) k_row_norms<<<B, 256, 0, s>>>(n, X, ldx, out);
+}
+
+void launch_gaussian_source(int nx, int ny, int nz, const double* prm, int B, double* f, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  if (B > 0) k_gaussian_source<<<dim3(blocks, B), 256, 0, s>>>(nx, ny, nz, prm, f);
 }
 
 }  // namespace rbws

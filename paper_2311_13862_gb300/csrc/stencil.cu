@@ -257,7 +257,7 @@ __global__ void k_apply(Geo g, int tiles_x, int zc, const T* __restrict__ coef, 
 
 // r = f - A u in FP64 with partial sums of r.r per CTA.
 __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restrict__ coef,
-                             const double* __restrict__ f, const double* __restrict__ u,
+                             const double* __restrict__ f, int64_t f_stride, const double* __restrict__ u,
                              double* __restrict__ r, double* __restrict__ rr_part, int P,
                              const int* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -267,6 +267,7 @@ __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restric
   if (mask && !mask[b]) return;
   const TilePos tp = tile_pos(g, tiles_x, zc);
   const double* ub = u + (int64_t)b * g.n;
+  const double* fb = f ? f + (int64_t)b * f_stride : nullptr;
   double* rb = r ? r + (int64_t)b * g.n : nullptr;
   const double* cb = coef + (int64_t)b * g.ncls() * kCoefStride;
   double acc = 0.0;
@@ -276,7 +277,7 @@ __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restric
         if (rb) rb[idx] = rv;
         acc = fma(rv, rv, acc);
       },
-      [&](int64_t idx) { return f ? f[idx] : 1.0; });
+      [&](int64_t idx) { return fb ? fb[idx] : 1.0; });
   double dummy = 0.0;
   block_sum2(acc, dummy, red);
   if (threadIdx.x == 0 && threadIdx.y == 0) rr_part[(int64_t)b * P + tp.part] = acc;
@@ -312,7 +313,7 @@ __global__ void k_cg_init(CGArgs<T> a, int parity) {
     zmarch<T>(
         a.g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return ub[idx]; },
         [&](int64_t idx, T, T v, T dinv) {
-          const T rv = (a.f ? a.f[idx] : T(1)) - v;
+          const T rv = (a.f ? a.f[(int64_t)b * a.f_stride + idx] : T(1)) - v;
           const T sv = jac ? dinv * rv : rv;
           rb[idx] = rv;
           if (jac) sb[idx] = sv;
@@ -883,12 +884,12 @@ void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_
 
 void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
                        const double* u, double* r, double* rr_part, int P, const int* mask,
-                       cudaStream_t s) {
+                       cudaStream_t s, int64_t f_stride) {
   const int tiles_x = (g.nx + t.tx - 1) / t.tx, tiles_y = (g.ny + t.ty - 1) / t.ty;
   const int nzc = (g.nz + zc - 1) / zc;
   (void)P;
   dim3 grid(tiles_x * tiles_y, nzc, B), block(t.tx, t.ty);
-  k_residual64<<<grid, block, plane_smem(t, sizeof(double)), s>>>(g, tiles_x, zc, coef, f, u, r,
+  k_residual64<<<grid, block, plane_smem(t, sizeof(double)), s>>>(g, tiles_x, zc, coef, f, f_stride, u, r,
                                                                   rr_part, tiles_x * tiles_y * nzc, mask);
 }
 

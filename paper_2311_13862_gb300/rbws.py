@@ -76,6 +76,9 @@ def _lib():
         L.rbws_l1roc_info.argtypes = [P, C.POINTER(i32), P, P]
         L.rbws_l1roc_coefficients.argtypes = [P, P, i32, P]
         L.rbws_rb_residuals.argtypes = [P, P, i32, i32, P]
+        L.rbws_gaussian_source.argtypes = [P, P, i32, P]
+        L.rbws_solve_batch_rhs.argtypes = [P, P, i32, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
+        L.rbws_offline_greedy_rhs.argtypes = [P, P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
         L.rbws_offline_greedy.argtypes = [P, P, i32, i32, d, d, i32, P, P, C.POINTER(i32)]
         L.rbws_set_basis.argtypes = [P, i32, P, P, P]
@@ -97,7 +100,8 @@ def _lib():
                      "rbws_solve_batch", "rbws_train_surrogate", "rbws_surrogate_set_params",
                      "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
                      "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load", "rbws_apply_preconditioner",
-                     "rbws_offline_l1roc", "rbws_l1roc_info", "rbws_l1roc_coefficients", "rbws_rb_residuals"):
+                     "rbws_offline_l1roc", "rbws_l1roc_info", "rbws_l1roc_coefficients", "rbws_rb_residuals",
+                     "rbws_gaussian_source", "rbws_solve_batch_rhs", "rbws_offline_greedy_rhs"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -215,6 +219,38 @@ def rbws_l1roc_coefficients(h, mu):
     c = np.empty((mu.shape[0], N))
     _check(_lib().rbws_l1roc_coefficients(h, _hp(mu), mu.shape[0], _hp(c)), "rbws_l1roc_coefficients")
     return c
+
+
+def rbws_gaussian_source(h, params, f_out):
+    """f_out (CUDA float64 [B][n]) = exp(-|x - c_b|^2 / (2 s_b^2)); params [B][4] = (c_x, c_y, c_z, s_b)."""
+    prm = _host(np.atleast_2d(params))
+    _check(_lib().rbws_gaussian_source(h, _hp(prm), prm.shape[0], _dp(f_out)), "rbws_gaussian_source")
+
+
+def rbws_solve_batch_rhs(h, mu, f, tol, warm, u_out, options: rbws_options | None = None):
+    """rbws_solve_batch with right-hand sides f (CUDA float64 [B][n]); returns (status, iters, relres,
+    inst_status)."""
+    mu = _host(np.atleast_2d(mu))
+    B = mu.shape[0]
+    it = np.zeros(B, dtype=np.int32)
+    rel = np.zeros(B)
+    st = np.zeros(B, dtype=np.int32)
+    rc = _check(_lib().rbws_solve_batch_rhs(h, _hp(mu), B, _dp(f), tol, warm,
+                                            None if options is None else C.byref(options), _dp(u_out), _hp(it),
+                                            _hp(rel), _hp(st)), "rbws_solve_batch_rhs")
+    return rc, it, rel, st
+
+
+def rbws_offline_greedy_rhs(h, mu_train, f_train, n_max, greedy_tol=0.0, snapshot_tol=1e-12):
+    """Greedy with a right-hand side per training parameter (f_train: CUDA float64 [n_train][n]);
+    returns (N, selected, indicator history)."""
+    mu = _host(np.atleast_2d(mu_train))
+    sel = np.full(n_max, -1, dtype=np.int32)
+    eta = np.full(n_max, np.nan)
+    n = C.c_int32(0)
+    _check(_lib().rbws_offline_greedy_rhs(h, _hp(mu), _dp(f_train), mu.shape[0], n_max, greedy_tol, snapshot_tol,
+                                          _hp(sel), _hp(eta), C.byref(n)), "rbws_offline_greedy_rhs")
+    return n.value, sel[:n.value], eta[:n.value]
 
 
 def rbws_rb_residuals(h, mu, n_use):
