@@ -204,6 +204,68 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_gaussian(args):
+    """The second workload (non-affine source): the 64^3, 2x2x1-block operator with, per parameter,
+    a Gaussian source of its own centre.  Greedy with a source per training parameter (N <= 40),
+    then 256 test (mu, source) pairs per step: MG-preconditioned FP32 PCG inside FP64 refinement to
+    1e-10 from the Galerkin RB start (value) and from zero (arm)."""
+    import torch
+    from paper_2311_13862_gb300 import build, inputs, rbws
+    build.build()
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["c2g"]
+    P = rbws.Problem(w.grid, w.blocks)
+    ft = torch.empty((w.n_train, P.n), dtype=torch.float64, device="cuda")
+    rbws.rbws_gaussian_source(P.h, inputs.train_sources(w), ft)
+    t0 = time.perf_counter()
+    N, sel, eta = rbws.rbws_offline_greedy_rhs(P.h, inputs.train_mu(w), ft, w.n_max, 0.0, 1e-12)
+    torch.cuda.synchronize()
+    t_off = time.perf_counter() - t0
+    del ft
+    B = args.batch or w.n_test
+    mus = inputs.test_mu(w, B)
+    f = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
+    rbws.rbws_gaussian_source(P.h, inputs.test_sources(w, B), f)
+    u = torch.empty_like(f)
+    opt = rbws.rbws_options_default(precond=rbws.PREC_MG, precision=rbws.FP32_IR)
+    arms = {}
+    for name, warm in (("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN), ("mgcg_zero_fp32ir", rbws.WARM_ZERO)):
+        for _ in range(args.warmup):
+            rbws.rbws_solve_batch_rhs(P.h, mus, f, w.tol, warm, u, opt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record()
+            for _ in range(args.steps):
+                rc, it, rel, st = rbws.rbws_solve_batch_rhs(P.h, mus, f, w.tol, warm, u, opt)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        arms[name] = {"solves_per_s": B / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(np.mean(it)),
+                      "iters_max": int(np.max(it)), "relres_max": float(np.max(rel)),
+                      "all_converged": bool(np.all(st == 0)), "clocks": clk.summary()}
+    # independent check: the oracle's FP64 true residual of two solutions
+    import oracle as O
+    op = O.assemble(w.grid, w.blocks)
+    uu, ff = u.cpu().numpy(), f.cpu().numpy()
+    chk = [float(np.linalg.norm(ff[b] - op.matvec(mus[b], uu[b])) / np.linalg.norm(ff[b])) for b in (0, B - 1)]
+    head = arms["mgcg_galerkin_fp32ir"]
+    line = {"metric": METRIC, "value": head["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": "64^3 interior grid, 2x2x1 blocks, mu log-uniform in [0.1,10]^4, and per "
+                       "parameter a Gaussian source exp(-|x-c|^2/(2 0.1^2)) with c uniform in [0.25,0.75]^3; "
+                       "RB N<=40 by greedy over 256 training (mu, source) pairs; %d test pairs per step; "
+                       "MG-PCG in FP32 inside FP64 refinement to rel-res 1e-10" % B,
+                       "batch_per_gpu": B, "N": int(N), "warm": "galerkin", "precision": "fp32ir", "precond": "mg",
+                       "tol": w.tol, "l2": "no flush: solver working set > 129 MB L2"},
+            "clocks": head["clocks"], "arms": arms, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "iters_mean": head["iters_mean"], "relres_max": head["relres_max"],
+            "oracle_true_relres_sampled": chk}
+    print(json.dumps(line))
+    P.close()
+
+
 def bench_requests(args):
     """96 requests (32 each on 96^3, 128^3, 256^3 grids, 3x3x3 blocks, mu in [0.1,10]^27) per step,
     interleaved in a fixed order, in one rbws_solve_requests call: learned start with one reduced
@@ -287,8 +349,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
     ap.add_argument("--mlp-epochs", type=int, default=2000,
                     help="epochs of the learned warm start's training (0: skip the learned arms)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5"],
-                    help="c2: the 64^3 batched workload (default line); c5: 96 requests on 96^3/128^3/256^3")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c5", "c2g"],
+                    help="c2: the 64^3 batched workload (default line); c5: 96 requests on 96^3/128^3/256^3; "
+                         "c2g: the 64^3 operator with a Gaussian source per parameter")
     ap.add_argument("--c5-train", type=int, default=256, help="greedy training parameters per grid (c5)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in FP32 tile/schedule instead of the autotuned one")
@@ -301,6 +364,8 @@ def main():
         return reference_arm(args)
     if args.workload == "c5":
         return bench_requests(args)
+    if args.workload == "c2g":
+        return bench_gaussian(args)
 
     import torch
     import torch.distributed as dist

@@ -53,6 +53,10 @@ WORKLOADS = {
     "c5-96": Workload("c5-96cube-3x3x3", (96, 96, 96), (3, 3, 3), 0.1, 10.0, 60, 256, 32, 1e-10, 5),
     "c5-128": Workload("c5-128cube-3x3x3", (128, 128, 128), (3, 3, 3), 0.1, 10.0, 60, 256, 32, 1e-10, 5),
     "c5-256": Workload("c5-256cube-3x3x3", (256, 256, 256), (3, 3, 3), 0.1, 10.0, 60, 256, 32, 1e-10, 5),
+    # a second workload with a non-affine source: the c2 operator, and per parameter a Gaussian
+    # source with its own centre (gauss_params), RB N <= 40 over 256 training parameters
+    "c2g": Workload("c2g-64cube-2x2x1-gaussian-source", (64, 64, 64), (2, 2, 1), 0.1, 10.0, 40, 256, 256,
+                    1e-10, 6),
 }
 
 
@@ -72,6 +76,20 @@ def test_mu(w: Workload, n: int | None = None) -> np.ndarray:
 
 def surrogate_mu(w: Workload, n: int = 4096) -> np.ndarray:
     return log_uniform(3000 + w.seed_base, n, w.Q, w.mu_lo, w.mu_hi)
+
+
+def gauss_params(seed: int, n: int, lo: float = 0.25, hi: float = 0.75, sigma: float = 0.1) -> np.ndarray:
+    """n Gaussian-source parameter rows (c_x, c_y, c_z, sigma): centres uniform in [lo, hi]^3."""
+    rng = np.random.default_rng(seed)
+    return np.column_stack([rng.uniform(lo, hi, size=(n, 3)), np.full(n, sigma)])
+
+
+def train_sources(w: Workload, n: int | None = None) -> np.ndarray:
+    return gauss_params(4000 + w.seed_base, w.n_train if n is None else n)
+
+
+def test_sources(w: Workload, n: int | None = None) -> np.ndarray:
+    return gauss_params(5000 + w.seed_base, w.n_test if n is None else n)
 
 
 def random_field(seed: int, shape) -> np.ndarray:
