@@ -101,7 +101,8 @@ def test_rb_warm_started_mgcg_matches_oracle():
 
 @pytest.mark.parametrize("grid,blocks", [((40, 36, 32), (2, 2, 2)),   # 4-node FP32 kernels
                                          ((33, 17, 20), (2, 2, 2)),   # nx % 4 != 0: one-node kernels
-                                         ((64, 48, 40), (2, 2, 1))])
+                                         ((64, 48, 40), (2, 2, 1)),
+                                         ((64, 48, 34), (2, 2, 1))])  # odd z-chunk: unfused restriction
 @pytest.mark.parametrize("warm", [rbws.WARM_ZERO, rbws.WARM_GALERKIN])
 def test_fp32_mgcg_with_reliable_updates_reaches_the_fp64_residual(grid, blocks, warm):
     op = O.assemble(grid, blocks)
