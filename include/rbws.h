@@ -188,6 +188,14 @@ RBWS_API rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32
 RBWS_API rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t B, int32_t precond,
                                                const void* x, void* y, void* stream);
 
+/* One FP32 multigrid V-cycle y = MG(x) (Algorithm 2) exactly as the mixed-precision
+ * iteration applies it (finest level on the 4-node tiles with TMA-fed steps where the grid
+ * allows): x, y device [B][n] FP32, x != y.  A test and analysis entry point; allocates
+ * the FP32 iteration's buffers for B instances in library-owned scratch.  Synchronous on
+ * stream (NULL: the problem's own).  RBWS_ERR_DEVICE_TIMEOUT if a stage wait ran out. */
+RBWS_API rbws_status rbws_apply_mg32(rbws_problem p, const double* mu, int32_t B, const void* x, void* y,
+                                     void* stream);
+
 /* rbws_apply_operator for callers that cannot allocate device memory after
  * start-up: services that run inside a fixed device-memory budget shared with
  * another framework's caching allocator, or latency-sensitive code that

@@ -740,6 +740,27 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
   return RBWS_OK;
 }
 
+// The FP32 V-cycle state for a batch: the level tables and vectors, and with the
+// 4-node kernels (v4) the finest level fused on the iteration's arguments a (tile t)
+// and the wider MG tiles of the steps that write no partials.
+rbws_status mg_fp32_batch(rbws_problem p, const double* d_mu, int B, const float* coef32, bool v4, Tile t,
+                          CGArgs<float>* a, MGBatch* mgb) {
+  CKI(mg_batch(p, d_mu, B, coef32, 1, a->st, mgb));
+  if (v4) {
+    mg_fine_prepare();
+    tma_prepare();  // the TMA-fed finest-level steps
+    mgb->fine_cg = a;
+    mgb->fine_tile = t;
+    const Tile tm = choose_tile_v4(p->nx, p->ny);
+    mgb->mg_tile = tm;
+    mgb->mg_tiles_x = (p->nx + 4 * tm.tx - 1) / (4 * tm.tx);
+    mgb->mg_tiles_y = (p->ny + tm.ty - 1) / tm.ty;
+    mgb->mg_zc = choose_zc_v4(p->nz, (int64_t)mgb->mg_tiles_x * mgb->mg_tiles_y * B);
+    mgb->mg_nzc = (p->nz + mgb->mg_zc - 1) / mgb->mg_zc;
+  }
+  return RBWS_OK;
+}
+
 // FP32 Jacobi-PCG inside FP64 iterative refinement, with reliable updates:
 // the FP32 iteration accumulates its correction d; whenever an instance's
 // FP32 residual has dropped by the factor inner_tol since its last update (or
@@ -844,21 +865,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.u64 = u;
   a.r64 = r64;
   a.rel64 = rel;
-  if (mg) {
-    CKI(mg_batch(p, d_mu, B, coef32, 1, a.st, &mgb));
-    if (v4) {
-      mg_fine_prepare();
-      tma_prepare();  // the TMA-fed residual + restriction of the finest level
-      mgb.fine_cg = &a;
-      mgb.fine_tile = t;
-      const Tile tm = choose_tile_v4(p->nx, p->ny);
-      mgb.mg_tile = tm;
-      mgb.mg_tiles_x = (p->nx + 4 * tm.tx - 1) / (4 * tm.tx);
-      mgb.mg_tiles_y = (p->ny + tm.ty - 1) / tm.ty;
-      mgb.mg_zc = choose_zc_v4(p->nz, (int64_t)mgb.mg_tiles_x * mgb.mg_tiles_y * B);
-      mgb.mg_nzc = (p->nz + mgb.mg_zc - 1) / mgb.mg_zc;
-    }
-  }
+  if (mg) CKI(mg_fp32_batch(p, d_mu, B, coef32, v4, t, &a, &mgb));
   if (sched32) {
     a.alpha = (double*)p->buf("ir_alpha", sizeof(double) * 2 * (size_t)B, &err);
     if (err) return (rbws_status)err;
@@ -1697,6 +1704,44 @@ rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t 
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+rbws_status rbws_apply_mg32(rbws_problem p, const double* mu, int32_t B, const void* x, void* y, void* stream) {
+  if (!p || !mu || !x || !y || x == y || B < 1 || B > 65535) {
+    set_error("rbws_apply_mg32: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, stream);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_mg32"));
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &c64, &c32));
+  Tile t = choose_tile_v4(p->nx, p->ny);
+  const bool v4 = t.tx > 0;
+  if (!v4) t = choose_tile(p->nx);
+  int err = 0;
+  float* d = (float*)p->buf("mg32_u", sizeof(float) * (size_t)B * p->n, &err);
+  if (err) return (rbws_status)err;
+  CGArgs<float> a{};
+  CKI(make_cg_args<float>(p, B, t, c32, d, &a, "m32_", v4 ? 4 : 1, 0));
+  a.precond = RBWS_PREC_MG;
+  std::vector<InstState> h(B);
+  for (auto& e : h) e = InstState{ST_ACTIVE, 0, 0, 0, 0.0, 0.0, 0ull};
+  CK(cudaMemcpyAsync(a.st, h.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice, p->cur));
+  CK(cudaMemsetAsync(a.active, 0, 4 * sizeof(int), p->cur));  // the third counter: the TMA error flag
+  MGBatch mgb;
+  CKI(mg_fp32_batch(p, d_mu, B, c32, v4, t, &a, &mgb));
+  p->launches += launch_mg_vcycle(mgb, x, y, -1, p->cur);
+  CK(cudaGetLastError());
+  int counts[3];
+  CK(cudaMemcpyAsync(counts, a.active, sizeof(counts), cudaMemcpyDeviceToHost, p->cur));
+  CK(cudaStreamSynchronize(p->cur));
+  if (counts[2]) {
+    set_error("rbws_apply_mg32: a TMA stage wait ran out of time");
+    return RBWS_ERR_DEVICE_TIMEOUT;
+  }
   return RBWS_OK;
 }
 

@@ -77,6 +77,7 @@ def _lib():
         L.rbws_l1roc_coefficients.argtypes = [P, P, i32, P]
         L.rbws_rb_residuals.argtypes = [P, P, i32, i32, P]
         L.rbws_gaussian_source.argtypes = [P, P, i32, P]
+        L.rbws_apply_mg32.argtypes = [P, P, i32, P, P, P]
         L.rbws_solve_batch_rhs.argtypes = [P, P, i32, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
         L.rbws_offline_greedy_rhs.argtypes = [P, P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
@@ -101,7 +102,7 @@ def _lib():
                      "rbws_surrogate_get_params", "rbws_surrogate_forward", "rbws_surrogate_loss_grad",
                      "rbws_solve_requests", "rbws_autotune", "rbws_save", "rbws_load", "rbws_apply_preconditioner",
                      "rbws_offline_l1roc", "rbws_l1roc_info", "rbws_l1roc_coefficients", "rbws_rb_residuals",
-                     "rbws_gaussian_source", "rbws_solve_batch_rhs", "rbws_offline_greedy_rhs"):
+                     "rbws_gaussian_source", "rbws_solve_batch_rhs", "rbws_offline_greedy_rhs", "rbws_apply_mg32"):
             getattr(L, name).restype = C.c_int
         _L = L
     return _L
@@ -219,6 +220,12 @@ def rbws_l1roc_coefficients(h, mu):
     c = np.empty((mu.shape[0], N))
     _check(_lib().rbws_l1roc_coefficients(h, _hp(mu), mu.shape[0], _hp(c)), "rbws_l1roc_coefficients")
     return c
+
+
+def rbws_apply_mg32(h, mu, x, y, stream=None):
+    """One FP32 V-cycle y = MG(x) as the mixed-precision iteration applies it (x, y CUDA float32 [B][n])."""
+    mu = _host(np.atleast_2d(mu))
+    _check(_lib().rbws_apply_mg32(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), stream), "rbws_apply_mg32")
 
 
 def rbws_gaussian_source(h, params, f_out):

@@ -149,3 +149,26 @@ def test_fp32_mgcg_tracks_fp64_mgcg_on_the_64cube_workload(warm):
             P.h, mu, 1e-10, warm, u, rbws.rbws_options_default(precond=rbws.PREC_MG, precision=rbws.FP32_IR))
     assert np.all(st64 == 0) and np.all(st32 == 0)
     assert np.all(it32 <= it64 + 3), (it32 - it64).max()
+
+
+@pytest.mark.parametrize("grid,blocks", [((40, 36, 32), (2, 2, 2)),   # TMA-fed finest level, ragged tiles
+                                         ((64, 48, 34), (2, 2, 1)),   # odd z-chunks: unfused restriction
+                                         ((24, 20, 18), (2, 2, 1)),   # 4 levels
+                                         ((33, 17, 20), (2, 2, 2))])  # nx % 4 != 0: one-node kernels
+def test_fp32_vcycle_as_the_iteration_applies_it_matches_oracle(grid, blocks):
+    """One FP32 V-cycle through the mixed-precision iteration's kernels (TMA-fed smoothing
+    steps, the residual + restriction pass, the 32^3-style coarse steps and the tail) against
+    the oracle's FP64 V-cycle, at FP32 accuracy."""
+    op = O.assemble(grid, blocks)
+    H = mg.Hierarchy(op)
+    B = 3
+    mu = inputs.log_uniform(111, B, op.Q, 0.01, 100.0)
+    x = inputs.random_field(112, (B, op.n))
+    ref = np.stack([mg.vcycle(H.operators(mu[b]), x[b]) for b in range(B)])
+    with rbws.Problem(grid, blocks) as P:
+        xd = torch.from_numpy(x).float().cuda()
+        yd = torch.empty_like(xd)
+        rbws.rbws_apply_mg32(P.h, mu, xd, yd)
+        y = yd.double().cpu().numpy()
+    err = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= 2e-5), err
