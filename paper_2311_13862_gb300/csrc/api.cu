@@ -898,6 +898,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   cudaError_t ce;
   if (!prof) {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const int64_t launches0 = p->launches;
     if (mg) mg_launches = mg_apply(a, 0, s);  // the previous block's last preconditioning
     for (int k = 0; k < M; k++) {
       phase_a(a, k & 1, s);
@@ -906,7 +907,17 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     }
     cudaMemsetAsync(a.pending, 0, sizeof(int), s);
     launch_ru_decide(a, s);
+    // the FP64 reliable update of the instances decide flagged, in the same graph (the
+    // others leave these kernels at once), so the host waits once per block
+    launch_ru_fold(a, s);
+    const rbws_status rr = residual_norms(p, coef64, B, u, r64, rel, upd);
+    reset(a, 0, s);
+    p->launches = launches0;
     ce = cudaStreamEndCapture(s, &graph);
+    if (rr != RBWS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rr;
+    }
     if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
     ce = cudaGraphInstantiate(&exec, graph, 0);
     if (ce != cudaSuccess) {
@@ -923,16 +934,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       break;
     }
     if (counts[2]) break;  // a TMA stage wait ran out; reported below
-    const int active = counts[0], pending = counts[1];
-    if (pending > 0) {
-      // FP64 reliable update of the flagged instances
-      launch_ru_fold(a, s);
-      if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
-      reset(a, 0, s);
-      CK(cudaMemsetAsync(a.pending, 0, sizeof(int), s));
-      p->launches += 4;
-      continue;
-    }
+    const int active = counts[0];
     if (active == 0) break;
     if (!prof) {
       if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) {
@@ -959,6 +961,9 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       }
       cudaMemsetAsync(a.pending, 0, sizeof(int), s);
       launch_ru_decide(a, s);
+      launch_ru_fold(a, s);
+      if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
+      reset(a, 0, s);
       if ((ce = cudaEventSynchronize(p->tev[3])) != cudaSuccess) {
         rc = (rbws_status)cuda_fail(ce, "profile events");
         break;
@@ -981,7 +986,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       prof->active_dofs += (double)active * (double)p->n;
       prof->samples += 1;
     }
-    p->launches += (2 + mg_launches) * M + 1;
+    p->launches += (2 + mg_launches) * M + 1 + 4;  // + fold, residual, norms, reset
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
