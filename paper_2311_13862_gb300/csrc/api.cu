@@ -747,7 +747,6 @@ rbws_status mg_fp32_batch(rbws_problem p, const double* d_mu, int B, const float
                           CGArgs<float>* a, MGBatch* mgb) {
   CKI(mg_batch(p, d_mu, B, coef32, 1, a->st, mgb));
   if (v4) {
-    mg_fine_prepare();
     tma_prepare();  // the TMA-fed finest-level steps
     mgb->fine_cg = a;
     mgb->fine_tile = t;

@@ -404,15 +404,14 @@ int launch_mg_vcycle(const MGBatch& m, const void* rhs, void* out, int slot, cud
 // Fine-level FP32 multigrid steps with the v4 tiles (stencil_v4.cu).
 struct MGFineArgs {
   const float* rhs;  // [B][n] right-hand side of the level (the iteration's r)
-  const float* xin;  // staged input (stages 0, 2)
+  const float* xin;  // staged input (stage 0)
   float* out;
-  const float* ec;   // coarse correction [B][cnx*cny*cnz] (stage 2)
-  int cnx, cny, cnz;
+  int cnx, cny, cnz;  // the coarse grid of output kind 3
   const int* mask;   // skip instances with mask[b] == 0 (may be null)
   float omega;
   int slot;          // partial slot of rho (output kind 2)
 };
-// stage 0: x = xin, 1: x = omega D^-1 rhs, 2: x = xin + P ec;  outk 0: Jacobi
+// stage 0: x = xin, 1: x = omega D^-1 rhs;  outk 0: Jacobi
 // step, 1: residual, 2: Jacobi step and rho partials, 3 (stage 0): the
 // restricted residual P^T (rhs - A x) into out (the coarse grid cnx x cny x
 // cnz).  Returns -1 for a combination that is not built, or (outk 3) a tiling
@@ -427,10 +426,6 @@ int launch_mg_fine_rr_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, c
 // it (the register-prefetch kernel runs then).
 int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, int stage, const MGFineArgs& m, bool rho,
                          cudaStream_t s);
-// Shared memory of the coarse planes staged by stage 2 for z-chunks of zc planes;
-// mg_fine_prepare sets the kernel attribute (call outside stream capture).
-size_t mg_fine_coarse_smem(Tile t, int zc);
-void mg_fine_prepare();
 // y = D^-1 x on the FP64 level view L (instances all active).
 void launch_diag_inverse(const MGLevel& L, int B, const double* x, double* y, cudaStream_t s);
 

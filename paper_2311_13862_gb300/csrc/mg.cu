@@ -1147,7 +1147,7 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   float* W = (float*)m.w2[J];
   float* crhs = (float*)m.rhs[J - 1];
   float* csol = (float*)m.sol[J - 1];
-  MGFineArgs fa{rhs, nullptr, Y, nullptr, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot};
+  MGFineArgs fa{rhs, nullptr, Y, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot};
   // the steps that write no partials run on wider tiles (less halo); the last,
   // with the rho partials, on the iteration's own tiling
   CGArgs<float> am = *m.fine_cg;
@@ -1188,11 +1188,9 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
       F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);
   launches += 1;
   fa.xin = Y;
-  fa.ec = nullptr;
   fa.out = W;
   fine(2, 0, 0, false);  // W = smoothing step from Y
   fa.xin = W;
-  fa.ec = nullptr;
   fa.out = out;
   fine(3, 0, slot >= 0 ? 2 : 0);  // out = last step (+ rho)
   return launches + 2;

@@ -866,18 +866,13 @@ void launch_cg_b32_v4(const CGArgs<float>& a, Tile t, int parity, cudaStream_t s
 // Fine-level multigrid steps (Algorithm 2 on the finest grid) with the v4
 // tiles and the iteration's tiling, FP32.  The staged field x is
 //   kStage 0: xin;   kStage 1: omega D^-1 rhs (the first smoothing step from
-//   zero, formed where it is staged);   kStage 2: xin + P e (the coarse
-//   correction prolongated where it is staged; e has cnx x cny x cnz nodes);
+//   zero, formed where it is staged);
 // and the output is
 //   kOut 0: out = x + omega D^-1 (rhs - A x)      (a damped Jacobi step)
 //   kOut 1: out = rhs - A x                        (the residual)
 //   kOut 2: as 0, plus the partials of rho = rhs . out into slot `slot` of
 //           the iteration's partials (out is the preconditioned residual s).
 // ---------------------------------------------------------------------------
-namespace {
-
-}  // namespace
-
 template <int kStage, int kOut>
 __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineArgs m) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -892,7 +887,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
   const float* rhs = m.rhs + off;
   const float* xin = kStage == 1 ? nullptr : m.xin + off;
-  const float* ec = kStage == 2 ? m.ec + (int64_t)b * m.cnx * m.cny * m.cnz : nullptr;
   float* out = m.out + off;
   const float omega = m.omega;
   const int TXN = blockDim.x * 4, TY = blockDim.y;
@@ -903,98 +897,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   const Halo4 h = halo4(g, ps, pl, tid);
   const int oslot = pl.at(4 * (int)threadIdx.x, (int)threadIdx.y);
   const int gi = ps.x0 + h.hx, gj = ps.y0 + h.hy;
-
-  // kStage 2: the coarse correction over the tile's coarse footprint (x: x0/2 - 1
-  // .. x0/2 + TXN/2; y: floor((y0-2)/2) .. floor((y0+TY)/2)) for every coarse
-  // plane the z-chunk touches (fine plane z reads coarse planes floor((z-1)/2)
-  // and floor(z/2)), staged once after the fine planes' ring.
-  float* csm = sm + 3 * pl.PS;
-  const int cx_lo = ps.x0 / 2 - 1, cy_lo = ps.y0 >= 2 ? (ps.y0 - 2) / 2 : -1;
-  const int CW = TXN / 2 + 2, CH = (ps.y0 + TY) / 2 - cy_lo + 1;
-  const int kz_lo = ps.z0 >= 2 ? (ps.z0 - 2) / 2 : -1, kz_hi = min(m.cnz - 1, ps.z1 / 2);
-  if (kStage == 2) {  // row by row: one division per row, columns across threadIdx.x
-    const int nrows = (kz_hi - kz_lo + 1) * CH;
-    for (int r = (int)threadIdx.y; r < nrows; r += (int)blockDim.y) {
-      const int kz = kz_lo + r / CH, cyy = cy_lo + r % CH;
-      const bool rin = kz >= 0 && cyy >= 0 && cyy < m.cny;
-      const float* src_row = ec + ((int64_t)max(kz, 0) * m.cny + max(cyy, 0)) * m.cnx;
-      for (int c = (int)threadIdx.x; c < CW; c += (int)blockDim.x) {
-        const int cxx = cx_lo + c;
-        csm[r * CW + c] = (rin && cxx >= 0 && cxx < m.cnx) ? src_row[cxx] : 0.f;
-      }
-    }
-    __syncthreads();
-  }
-  // (P e) from the staged planes.  Per thread the coarse rows and columns are
-  // fixed (its own group, its halo element); per plane only the coarse z
-  // planes change.  Offsets below are within one staged coarse plane.
-  struct Rows {
-    int o0, o1;  // offset of the row (and first column) of each coarse y row, -1 = none
-    float w0, w1;
-  };
-  auto rows_of = [&](int j, int xfirst) -> Rows {  // coarse rows of fine row j, starting at coarse column xfirst
-    const PRows ry = prows(j, m.cny);
-    Rows r{-1, -1, ry.w0, ry.w1};
-    if (ry.k0 >= 0) r.o0 = (ry.k0 - cy_lo) * CW + (xfirst - cx_lo);
-    if (ry.k1 >= 0) r.o1 = (ry.k1 - cy_lo) * CW + (xfirst - cx_lo);
-    return r;
-  };
-  // the 4-node group at i0: coarse columns i0/2 - 1 .. i0/2 + 1
-  const Rows own_rows = rows_of(ps.j, ps.i / 2 - 1);
-  const Rows halo_rows = h.kind == 1 ? rows_of(gj, gi / 2 - 1) : rows_of(gj, 0);
-  const PRows hx = prows(gi, m.cnx);  // x weights of a single halo node (kind 2)
-  auto planes_of = [&](int z, int* z0o, int* z1o, float* wz0, float* wz1) {
-    const PRows rz = prows(z, m.cnz);
-    *z0o = rz.k0 >= 0 ? (rz.k0 - kz_lo) * CH * CW : -1;
-    *z1o = rz.k1 >= 0 ? (rz.k1 - kz_lo) * CH * CW : -1;
-    *wz0 = rz.w0;
-    *wz1 = rz.w1;
-  };
-  auto prolong4s = [&](const Rows& r, int z) -> float4 {
-    int zo[2];
-    float wz[2];
-    planes_of(z, &zo[0], &zo[1], &wz[0], &wz[1]);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int aa = 0; aa < 2; aa++) {
-      if (zo[aa] < 0) continue;
-#pragma unroll
-      for (int bq = 0; bq < 2; bq++) {
-        const int yo = bq ? r.o1 : r.o0;
-        if (yo < 0) continue;
-        const float w = wz[aa] * (bq ? r.w1 : r.w0);
-        const float* c = csm + zo[aa] + yo;
-        const float e0 = c[0], e1 = c[1], e2 = c[2];
-        v.x = fmaf(w, 0.5f * (e0 + e1), v.x);
-        v.y = fmaf(w, e1, v.y);
-        v.z = fmaf(w, 0.5f * (e1 + e2), v.z);
-        v.w = fmaf(w, e2, v.w);
-      }
-    }
-    return v;
-  };
-  auto prolong1s = [&](int z) -> float {  // the kind-2 halo node (gi, gj)
-    int zo[2];
-    float wz[2];
-    planes_of(z, &zo[0], &zo[1], &wz[0], &wz[1]);
-    float v = 0.f;
-#pragma unroll
-    for (int aa = 0; aa < 2; aa++) {
-      if (zo[aa] < 0) continue;
-#pragma unroll
-      for (int bq = 0; bq < 2; bq++) {
-        const int yo = bq ? halo_rows.o1 : halo_rows.o0;
-        if (yo < 0) continue;
-        const float wyz = wz[aa] * (bq ? halo_rows.w1 : halo_rows.w0);
-        const float* c = csm + zo[aa] + yo;
-        if (hx.k0 >= 0) v = fmaf(wyz * hx.w0, c[hx.k0], v);
-        if (hx.k1 >= 0) v = fmaf(wyz * hx.w1, c[hx.k1], v);
-      }
-    }
-    return v;
-  };
-  (void)prolong4s;
-  (void)prolong1s;
 
   // raw loads of plane z (register prefetch): the array the staged field is
   // formed from, for the own group and the halo element(s)
@@ -1010,7 +912,7 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
     }
   };
   // staged values from raw ones: omega D^-1 raw (kStage 1; 1/D cached per z
-  // class for the own group and the halo element), raw + P e (kStage 2)
+  // class for the own group and the halo element)
   int own_zc = -1, h_zc = -1;
   float own_di[4] = {0.f, 0.f, 0.f, 0.f}, h_di[4] = {0.f, 0.f, 0.f, 0.f};
   auto commit = [&](float* P, int z) -> float4 {
@@ -1025,9 +927,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
           for (int e = 0; e < 4; e++) own_di[e] = omega * dinv_at(g, cb, zc, ps.i + e, ps.j);
         }
         v = make_float4(own_di[0] * v_own.x, own_di[1] * v_own.y, own_di[2] * v_own.z, own_di[3] * v_own.w);
-      } else if (kStage == 2) {
-        const float4 pe = prolong4s(own_rows, z);
-        v = make_float4(v_own.x + pe.x, v_own.y + pe.y, v_own.z + pe.z, v_own.w + pe.w);
       } else {
         v = v_own;
       }
@@ -1046,13 +945,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
               if (e < nh) h_di[e] = omega * dinv_at(g, cb, zc, gi + e, gj);
           }
           hv = make_float4(h_di[0] * v_h.x, h_di[1] * v_h.y, h_di[2] * v_h.z, h_di[3] * v_h.w);
-        } else if (kStage == 2) {
-          if (h.kind == 1) {
-            const float4 pe = prolong4s(halo_rows, z);
-            hv = make_float4(v_h.x + pe.x, v_h.y + pe.y, v_h.z + pe.z, v_h.w + pe.w);
-          } else {
-            hv.x = v_h.x + prolong1s(z);
-          }
         } else {
           hv = v_h;
         }
@@ -1075,9 +967,6 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
       xm = make_float4(omega * dinv_at(g, cb, zc, ps.i, ps.j) * raw.x, omega * dinv_at(g, cb, zc, ps.i + 1, ps.j) * raw.y,
                        omega * dinv_at(g, cb, zc, ps.i + 2, ps.j) * raw.z,
                        omega * dinv_at(g, cb, zc, ps.i + 3, ps.j) * raw.w);
-    } else if (kStage == 2) {
-      const float4 pe = prolong4s(own_rows, z0 - 1);
-      xm = make_float4(raw.x + pe.x, raw.y + pe.y, raw.z + pe.z, raw.w + pe.w);
     } else {
       xm = raw;
     }
@@ -1122,24 +1011,13 @@ __global__ void __launch_bounds__(256, 3) k_mg_fine_v4(CGArgs<float> a, MGFineAr
   }
 }
 
-size_t mg_fine_coarse_smem(Tile t, int zc) {
-  return sizeof(float) * (size_t)(zc / 2 + 3) * (2 * t.tx + 2) * (t.ty / 2 + 3);
-}
-
-void mg_fine_prepare() {
-  cudaFuncSetAttribute(k_mg_fine_v4<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-}
-
 int launch_mg_fine_v4(const CGArgs<float>& a, Tile t, int stage, int outk, const MGFineArgs& m, cudaStream_t s) {
   const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
   const size_t smem = v4_plane_smem(t);
-  // the coarse planes of a z-chunk: (zc/2 + 3) planes of (2 tx + 2) x (ty/2 + 3)
-  const size_t smem_c = smem + mg_fine_coarse_smem(t, a.zc);
   if (stage == 1 && outk == 0) {
     if (launch_mg_smooth_tma(a, t, 1, m, false, s)) k_mg_fine_v4<1, 0><<<grid, block, smem, s>>>(a, m);
   }
   else if (stage == 0 && outk == 1) k_mg_fine_v4<0, 1><<<grid, block, smem, s>>>(a, m);
-  else if (stage == 2 && outk == 0) k_mg_fine_v4<2, 0><<<grid, block, smem_c, s>>>(a, m);
   else if (stage == 0 && outk == 2) {
     if (launch_mg_smooth_tma(a, t, 0, m, true, s)) k_mg_fine_v4<0, 2><<<grid, block, smem, s>>>(a, m);
   } else if (stage == 0 && outk == 0) {
