@@ -978,24 +978,30 @@ inline int tail_elems(const MGPlan& P, int top, int* off) {
   return o;
 }
 
-// uf += P ec on the finest FP32 level, four x-consecutive fine nodes per thread
-// (fnx % 4 == 0): a group at i0 reads coarse columns i0/2 - 1 .. i0/2 + 1 of each
-// coarse row it touches (see the fused prolongation).
+// uf += P ec on the finest FP32 level, 4G x-consecutive fine nodes per thread
+// (fnx % 4G == 0, so cnx = fnx / 2): a group of four at i0 reads coarse columns
+// i0/2 - 1 .. i0/2 + 1 of each coarse row it touches, and G = 2 groups share the
+// middle column.  The G float4 loads of uf are issued before the coarse reads, so
+// each thread keeps 16G bytes of the stream in flight.
+template <int G>
 __global__ void __launch_bounds__(256) k_mg_prolong_add4(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
                                                          const InstState* __restrict__ st,
                                                          const int* __restrict__ mask, const float* __restrict__ ec,
                                                          float* __restrict__ uf) {
   const int b = blockIdx.y;
   if (mg_skip(st, mask, b)) return;
-  const int gx = fnx / 4;
+  const int gx = fnx / (4 * G);
   const int64_t ng = (int64_t)gx * fny * fnz;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= ng) return;
-  const int i0 = 4 * (int)(t % gx), j = (int)((t / gx) % fny), k = (int)(t / ((int64_t)gx * fny));
+  float4* p = reinterpret_cast<float4*>(uf + (int64_t)b * fnx * fny * fnz) + G * t;
+  float4 u[G];
+#pragma unroll
+  for (int q = 0; q < G; q++) u[q] = p[q];
+  const int i0 = 4 * G * (int)(t % gx), j = (int)((t / gx) % fny), k = (int)(t / ((int64_t)gx * fny));
   const Pw ry = pweight(j, cny), rz = pweight(k, cnz);
   const float* e = ec + (int64_t)b * cnx * cny * cnz;
   const int c1 = i0 / 2;
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int c = 0; c < 2; c++) {
     const int kz = c ? rz.k1 : rz.k0;
@@ -1005,18 +1011,23 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add4(int fnx, int fny, int f
       const int ky = bq ? ry.k1 : ry.k0;
       if (ky < 0) continue;
       const float w = (c ? rz.w1 : rz.w0) * (bq ? ry.w1 : ry.w0);
-      const float* row = e + ((int64_t)kz * cny + ky) * cnx;
-      const float e0 = c1 > 0 ? row[c1 - 1] : 0.f, e1 = row[c1], e2 = row[c1 + 1];
-      v.x = fmaf(w, 0.5f * (e0 + e1), v.x);
-      v.y = fmaf(w, e1, v.y);
-      v.z = fmaf(w, 0.5f * (e1 + e2), v.z);
-      v.w = fmaf(w, e2, v.w);
+      const float* row = e + ((int64_t)kz * cny + ky) * cnx + c1;
+      float ev[2 * G + 1];
+      ev[0] = c1 > 0 ? row[-1] : 0.f;
+#pragma unroll
+      for (int q = 1; q <= 2 * G; q++) ev[q] = row[q - 1];
+#pragma unroll
+      for (int q = 0; q < G; q++) {
+        const float e0 = ev[2 * q], e1 = ev[2 * q + 1], e2 = ev[2 * q + 2];
+        u[q].x = fmaf(w, 0.5f * (e0 + e1), u[q].x);
+        u[q].y = fmaf(w, e1, u[q].y);
+        u[q].z = fmaf(w, 0.5f * (e1 + e2), u[q].z);
+        u[q].w = fmaf(w, e2, u[q].w);
+      }
     }
   }
-  float4* p = reinterpret_cast<float4*>(uf + (int64_t)b * fnx * fny * fnz) + t;
-  float4 u = *p;
-  u.x += v.x, u.y += v.y, u.z += v.z, u.w += v.w;
-  *p = u;
+#pragma unroll
+  for (int q = 0; q < G; q++) p[q] = u[q];
 }
 
 inline dim3 level_grid(int64_t n, int B) { return dim3((unsigned)((n + 255) / 256), (unsigned)B); }
@@ -1184,8 +1195,12 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   // Y + P e where the step stages its planes (the coarse footprint staged per chunk) measured
   // no faster than the separate streaming pass.
   if (m.ev) cudaEventRecord(m.ev[4], s);
-  k_mg_prolong_add4<<<dim3((unsigned)((F.n / 4 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(
-      F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);
+  if (F.nx % 8 == 0)
+    k_mg_prolong_add4<2><<<dim3((unsigned)((F.n / 8 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(
+        F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);
+  else
+    k_mg_prolong_add4<1><<<dim3((unsigned)((F.n / 4 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(
+        F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);
   launches += 1;
   fa.xin = Y;
   fa.out = W;

@@ -154,6 +154,7 @@ def test_fp32_mgcg_tracks_fp64_mgcg_on_the_64cube_workload(warm):
 @pytest.mark.parametrize("grid,blocks", [((40, 36, 32), (2, 2, 2)),   # TMA-fed finest level, ragged tiles
                                          ((64, 48, 34), (2, 2, 1)),   # odd z-chunks: unfused restriction
                                          ((24, 20, 18), (2, 2, 1)),   # 4 levels
+                                         ((36, 28, 24), (2, 2, 1)),   # nx % 8 == 4: 4-node prolongation
                                          ((33, 17, 20), (2, 2, 2))])  # nx % 4 != 0: one-node kernels
 def test_fp32_vcycle_as_the_iteration_applies_it_matches_oracle(grid, blocks):
     """One FP32 V-cycle through the mixed-precision iteration's kernels (TMA-fed smoothing
