@@ -369,11 +369,10 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2311_13862_gb300 import build, inputs, rbws
+    from paper_2311_13862_gb300 import build, inputs, ranks, rbws
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ri = ranks.rank_info()
+    world, rank, local = ri.world, ri.rank, ri.local
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -391,8 +390,7 @@ def main():
     w = inputs.WORKLOADS["c2"]
     B = args.batch or w.n_test
     # each rank solves its own batch of B parameters (weak scaling, no collective on the data path)
-    mus_all = inputs.test_mu(w, B * world)
-    mus = mus_all[rank * B:(rank + 1) * B]
+    mus = ranks.shard(inputs.test_mu(w, B * world), B, rank, world)
     P = rbws.Problem(w.grid, w.blocks, device=local)
     t0 = time.perf_counter()
     N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
@@ -470,11 +468,7 @@ def main():
             e1.record(stream)
             torch.cuda.nvtx.range_pop()
             barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = ranks.max_over_ranks(e0.elapsed_time(e1) / steps, "cuda")
         rc, it, rel, st = out
         acc["elem_bytes"] = prof.elem_bytes
         acc["schedule"] = acc_schedule
@@ -489,7 +483,7 @@ def main():
         ms, it, rel, st, acc = run(rbws.WARM_GALERKIN, headline, args.steps, args.warmup, profile=True,
                                    precond=head_pc)
     clocks = clk.summary()
-    value = B * world / (ms / 1e3)
+    value = ranks.job_rate(B, world, ms)
 
     # ---- end to end: host parameters in, solution and counts back to pinned host memory ----
     u_host = torch.empty((B, P.n), dtype=torch.float64, pin_memory=True)
@@ -507,10 +501,7 @@ def main():
         stream.synchronize()
         barrier()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = ranks.max_over_ranks(e2e_ms, "cuda")
 
     # ---- side arms: zero start and the other precision ----
     arms = {}
@@ -562,7 +553,7 @@ def main():
         else:
             a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1,
                                              precond=precond_of.get(name, rbws.PREC_JACOBI))
-        arms[name] = {"solves_per_s": B * world / (a_ms / 1e3), "ms_per_step": a_ms,
+        arms[name] = {"solves_per_s": ranks.job_rate(B, world, a_ms), "ms_per_step": a_ms,
                       "iters_mean": float(np.mean(a_it)), "iters_max": int(np.max(a_it)),
                       "relres_max": float(np.max(a_rel)), "all_converged": bool(np.all(a_st == 0))}
 
@@ -670,7 +661,7 @@ def main():
                        "l2": "no flush: solver working set ~1.3 GB > 129 MB L2",
                        "parallelism": "independent batches per GPU (no collective)"},
             "roofline": res, "gpu_launches": int(acc["launches"]), "clocks": clocks,
-            "e2e": {"value": B * world / (e2e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": ranks.job_rate(B, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(B * w.Q * 8),
                     "d2h_bytes_per_step": int(B * P.n * 8 + B * (4 + 8 + 4))},
             "arms": arms, "l1roc_offline": l1roc_off, "learned_training": learned, "autotune": tuned, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
