@@ -250,8 +250,11 @@ RBWS_API rbws_status rbws_gaussian_source(rbws_problem p, const double* params, 
 /* rbws_solve_batch with right-hand side f_b (device [B][n] FP64, row b) for instance b
  * instead of the problem's f.  The relative residuals are against ||f_b||.  Warm starts:
  * RBWS_WARM_ZERO and RBWS_WARM_GALERKIN (c_b from A_N(mu_b) c_b = W^T f_b; W^T f_b formed
- * on the device); preconditioners other than MSRB.  Others return RBWS_ERR_UNSUPPORTED;
- * a zero f_b RBWS_ERR_INVALID_ARG. */
+ * on the device: in FP64 by dot products for RBWS_FP64, and for RBWS_FP32_IR in one pass
+ * over the sources with the FP32 copy of W that the mixed-precision lift also uses, FP32
+ * products summed in FP64, so the start matches the FP64 one to FP32 rounding while
+ * convergence is still decided on the FP64 residual); preconditioners other than MSRB.
+ * Others return RBWS_ERR_UNSUPPORTED; a zero f_b RBWS_ERR_INVALID_ARG. */
 RBWS_API rbws_status rbws_solve_batch_rhs(rbws_problem p, const double* mu, int32_t B, const void* f,
                                           double tol, int32_t warm, const rbws_options* opt, void* u_out,
                                           int32_t* iters_out, double* relres_out, int32_t* status_out);

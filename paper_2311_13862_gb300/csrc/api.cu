@@ -536,13 +536,19 @@ rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const do
 
 // Galerkin warm start u[b] = W A_N(mu_b)^{-1} fN.
 // u = W c; fp32: with the FP32 copy of W (the mixed-precision solver's start).
+// The FP32 copy of W used by the mixed-precision start (built on first use).
+rbws_status ensure_w32(rbws_problem p) {
+  if (!p->d_W32) {
+    CK(cudaMalloc(&p->d_W32, sizeof(float) * (size_t)p->N * p->n));
+    launch_to_f32((int64_t)p->N * p->n, p->d_W, p->d_W32, p->cur);
+    p->launches += 1;
+  }
+  return RBWS_OK;
+}
+
 rbws_status lift(rbws_problem p, const double* C, int B, double* u, bool fp32) {
   if (fp32) {
-    if (!p->d_W32) {
-      CK(cudaMalloc(&p->d_W32, sizeof(float) * (size_t)p->N * p->n));
-      launch_to_f32((int64_t)p->N * p->n, p->d_W, p->d_W32, p->cur);
-      p->launches += 1;
-    }
+    CKI(ensure_w32(p));
     launch_lift32(p->n, p->N, p->d_W32, C, B, u, p->cur);
   } else {
     launch_lift(p->n, p->N, p->d_W, C, B, u, p->cur);
@@ -560,18 +566,34 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u,
   double* C = (double*)p->buf("C", sizeof(double) * (size_t)B * p->N, &err);
   int* info = err ? nullptr : (int*)p->buf("info", sizeof(int) * (size_t)B, &err);
   if (err) return (rbws_status)err;
-  if (p->rhs.f) {  // per-instance right-hand sides: W^T f_b (given, or N dot launches over the batch)
+  if (p->rhs.f) {  // per-instance right-hand sides: W^T f_b (given, or formed over the batch)
     const double* fN = p->rhs.fN;
     int64_t sb = p->rhs.fN_sb, sj = p->rhs.fN_sj;
     if (!fN) {
       double* FN = (double*)p->buf("rhs_FN", sizeof(double) * (size_t)p->N * B, &err);
-      const int scratch_len = 256 * (B + 2);
-      double* scr = err ? nullptr : (double*)p->buf("rhs_scr", sizeof(double) * scratch_len, &err);
       if (err) return (rbws_status)err;
-      for (int j = 0; j < p->N; j++)
-        launch_multi_dot(p->n, B, p->rhs.f, p->rhs.stride, p->d_W + (int64_t)j * p->n, FN + (int64_t)j * B, scr,
-                         scratch_len, p->cur);
-      p->launches += p->N;
+      if (fp32) {
+        // the mixed-precision start: one pass over the sources with the FP32 copy of W (as
+        // its lift uses), FP32 products and FP64 sums.  The start is a starting guess; the
+        // FP64 residual of u0 is what the iteration corrects, so its accuracy is not at stake.
+        CKI(ensure_w32(p));
+        double* part = (double*)p->buf("rhs_proj",
+                                       sizeof(double) * (size_t)project32_splits(p->n, B) * p->N * B, &err);
+        if (err) return (rbws_status)err;
+        if (launch_project32(p->n, p->N, B, p->d_W32, p->rhs.f, p->rhs.stride, part, FN, p->cur)) {
+          set_error("reduced basis too large for the projection (N > 160)");
+          return RBWS_ERR_INVALID_ARG;
+        }
+        p->launches += 2;
+      } else {  // FP64: N dot launches over the batch
+        const int scratch_len = 256 * (B + 2);
+        double* scr = (double*)p->buf("rhs_scr", sizeof(double) * scratch_len, &err);
+        if (err) return (rbws_status)err;
+        for (int j = 0; j < p->N; j++)
+          launch_multi_dot(p->n, B, p->rhs.f, p->rhs.stride, p->d_W + (int64_t)j * p->n, FN + (int64_t)j * B,
+                           scr, scratch_len, p->cur);
+        p->launches += p->N;
+      }
       fN = FN;
       sb = 1;
       sj = B;

@@ -264,6 +264,13 @@ void launch_norms_from_partials(const double* part, int B, int P, double fnorm, 
                                 cudaStream_t s, const double* fnorms = nullptr);
 // out[b] = ||X[b]||_2, rows of length n with stride ldx.
 void launch_row_norms(int64_t n, int B, const double* X, int64_t ldx, double* out, cudaStream_t s);
+// FN[j * B + b] = (W^T f_b)_j from the FP32 copy of W (device [N][n]) and the FP64 sources
+// F (row b at F + b * ldf): FP32 products, summed in FP32 over runs of 128 nodes and in
+// FP64 across runs and splits (fixed order).  part: device scratch of
+// project32_splits(n, B) * N * B doubles.  N in 1..160; returns -1 otherwise.  Two launches.
+int project32_splits(int64_t n, int B);
+int launch_project32(int64_t n, int N, int B, const float* W, const double* F, int64_t ldf, double* part,
+                     double* FN, cudaStream_t s);
 // f[b] = the Gaussian source exp(-|x - c_b|^2 / (2 s_b^2)) on the interior nodes, prm device [B][4].
 void launch_gaussian_source(int nx, int ny, int nz, const double* prm, int B, double* f, cudaStream_t s);
 

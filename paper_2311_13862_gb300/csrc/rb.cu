@@ -244,6 +244,75 @@ __global__ void k_l1_indicator(int N, int Nmax, const double* __restrict__ R, co
   eta[b] = l1;
 }
 
+// The reduced right-hand sides of per-instance sources for the mixed-precision start,
+// FN[j][b] = (W^T f_b)_j, from the FP32 copy of W: products of FP32 values, summed in FP32
+// over runs of kProjRun nodes and in FP64 across runs.  A CTA takes kProjInst instances
+// (one per lane) and one split of the nodes; warp w accumulates the basis vectors
+// j = w, w + 8, ... (JPT of them).  The run's sources are staged node-major (row pitch
+// kProjInst + 1: no bank conflicts), W row-major; part[s][j][b] receives the split's sum.
+constexpr int kProjRun = 128;
+constexpr int kProjInst = 32;
+template <int JPT>
+__global__ void __launch_bounds__(256) k_project32(int64_t n, int N, int B, const float* __restrict__ W,
+                                                  const double* __restrict__ F, int64_t ldf, int64_t per_split,
+                                                  double* __restrict__ part) {
+  __shared__ float Fs[kProjRun][kProjInst + 1];
+  extern __shared__ __align__(16) float Ws[];  // [N][kProjRun]
+  const int sp = blockIdx.x, b0 = blockIdx.y * kProjInst;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t lo = (int64_t)sp * per_split, hi = min(n, lo + per_split);
+  double acc[JPT];
+#pragma unroll
+  for (int q = 0; q < JPT; q++) acc[q] = 0.0;
+  for (int64_t i0 = lo; i0 < hi; i0 += kProjRun) {
+    const int len = (int)min((int64_t)kProjRun, hi - i0);
+#pragma unroll 4
+    for (int e = tid; e < kProjInst * kProjRun; e += 256) {
+      const int r = e / kProjRun, c = e % kProjRun, bb = b0 + r;
+      Fs[c][r] = (bb < B && c < len) ? (float)F[(int64_t)bb * ldf + i0 + c] : 0.f;
+    }
+    for (int e = tid; e < N * kProjRun; e += 256) {
+      const int j = e / kProjRun, c = e % kProjRun;
+      Ws[e] = c < len ? W[(int64_t)j * n + i0 + c] : 0.f;
+    }
+    __syncthreads();
+    float a32[JPT];
+#pragma unroll
+    for (int q = 0; q < JPT; q++) a32[q] = 0.f;
+    for (int c = 0; c < kProjRun; c += 4) {
+      const float f0 = Fs[c][lane], f1 = Fs[c + 1][lane], f2 = Fs[c + 2][lane], f3 = Fs[c + 3][lane];
+#pragma unroll
+      for (int q = 0; q < JPT; q++) {
+        const int j = warp + 8 * q;
+        if (j < N) {
+          const float4 w4 = *reinterpret_cast<const float4*>(Ws + j * kProjRun + c);
+          a32[q] = fmaf(w4.x, f0, a32[q]);
+          a32[q] = fmaf(w4.y, f1, a32[q]);
+          a32[q] = fmaf(w4.z, f2, a32[q]);
+          a32[q] = fmaf(w4.w, f3, a32[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < JPT; q++) acc[q] += (double)a32[q];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < JPT; q++) {
+    const int j = warp + 8 * q;
+    if (j < N && b0 + lane < B) part[((int64_t)sp * N + j) * B + b0 + lane] = acc[q];
+  }
+}
+
+// FN[j * B + b] = sum over the S splits, in split order.
+__global__ void k_project_reduce(int S, int N, int B, const double* __restrict__ part, double* __restrict__ FN) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * B) return;
+  double v = 0.0;
+  for (int sp = 0; sp < S; sp++) v += part[(int64_t)sp * N * B + t];
+  FN[t] = v;
+}
+
 inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
   int64_t g = (n + threads - 1) / threads;
   return (int)(g < cap ? (g > 0 ? g : 1) : cap);
@@ -305,6 +374,38 @@ void launch_norms_from_partials(const double* part, int B, int P, double fnorm, 
 
 void launch_row_norms(int64_t n, int B, const double* X, int64_t ldx, double* out, cudaStream_t s) {
   if (B > 0) k_row_norms<<<B, 256, 0, s>>>(n, X, ldx, out);
+}
+
+int project32_splits(int64_t n, int B) {
+  const int groups = (B + kProjInst - 1) / kProjInst;
+  int64_t S = std::max<int64_t>(1, (4 * 152 + groups - 1) / groups);
+  S = std::min<int64_t>(S, (n + kProjRun - 1) / kProjRun);
+  return (int)std::max<int64_t>(S, 1);
+}
+
+int launch_project32(int64_t n, int N, int B, const float* W, const double* F, int64_t ldf, double* part,
+                     double* FN, cudaStream_t s) {
+  if (N < 1 || N > 160 || B < 1) return -1;
+  const int S = project32_splits(n, B);
+  int64_t per = (n + S - 1) / S;
+  per = (per + kProjRun - 1) / kProjRun * kProjRun;
+  const int Sused = (int)((n + per - 1) / per);
+  const dim3 grid((unsigned)Sused, (unsigned)((B + kProjInst - 1) / kProjInst));
+  const size_t smem = sizeof(float) * (size_t)N * kProjRun;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_project32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_project32<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_project32<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_project32<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  if (N <= 16) k_project32<2><<<grid, 256, smem, s>>>(n, N, B, W, F, ldf, per, part);
+  else if (N <= 40) k_project32<5><<<grid, 256, smem, s>>>(n, N, B, W, F, ldf, per, part);
+  else if (N <= 80) k_project32<10><<<grid, 256, smem, s>>>(n, N, B, W, F, ldf, per, part);
+  else k_project32<20><<<grid, 256, smem, s>>>(n, N, B, W, F, ldf, per, part);
+  k_project_reduce<<<(N * B + 255) / 256, 256, 0, s>>>(Sused, N, B, part, FN);
+  return 0;
 }
 
 void launch_gaussian_source(int nx, int ny, int nz, const double* prm, int B, double* f, cudaStream_t s) {

@@ -83,6 +83,14 @@ def test_greedy_with_per_training_sources_matches_oracle_and_warm_starts():
         for b in range(len(mtest)):
             exp = R.rb_start(ref, mtest[b], Fs[b])
             assert np.linalg.norm(u0[b] - exp) <= 1e-8 * np.linalg.norm(exp)
+        # the mixed-precision start forms W^T f_b from the FP32 copy of W (FP32 products, FP64
+        # sums): the same start to FP32 rounding
+        rbws.rbws_solve_batch_rhs(P.h, mtest, f, 1e-12, rbws.WARM_GALERKIN, u,
+                                  rbws.rbws_options_default(max_iters=0, precision=rbws.FP32_IR))
+        u0 = u.cpu().numpy()
+        for b in range(len(mtest)):
+            exp = R.rb_start(ref, mtest[b], Fs[b])
+            assert np.linalg.norm(u0[b] - exp) <= 1e-5 * np.linalg.norm(exp)
         # and the MG-preconditioned FP32 solve from it reaches the FP64 residual
         rc, it, rel, st = rbws.rbws_solve_batch_rhs(
             P.h, mtest, f, 1e-10, rbws.WARM_GALERKIN, u,
@@ -92,6 +100,37 @@ def test_greedy_with_per_training_sources_matches_oracle_and_warm_starts():
     for b in range(len(mtest)):
         true_rel = np.linalg.norm(Fs[b] - op.matvec(mtest[b], uu[b])) / np.linalg.norm(Fs[b])
         assert true_rel < 1e-10
+
+
+@pytest.mark.parametrize("N", [17, 45, 100])  # 5, 10 and 20 basis vectors per warp of the projection
+def test_mixed_precision_start_projection_matches_oracle(N):
+    """W^T f_b for the mixed-precision start (one pass over the sources, FP32 products) with an
+    installed orthonormal basis of N vectors: the start equals the oracle's Galerkin RB solution
+    to FP32 rounding, and the FP64 start to FP64 rounding."""
+    grid, blocks = (24, 20, 18), (2, 2, 1)
+    op = O.assemble(grid, blocks)
+    rng = np.random.default_rng(100 + N)
+    W = np.linalg.qr(rng.standard_normal((op.n, N)))[0].T.copy()      # [N][n], orthonormal rows
+    ANq = np.stack([W @ np.stack([op.matvec(np.eye(op.Q)[q], W[j]) for j in range(N)]).T
+                    for q in range(op.Q)])
+    fN = W @ np.ones(op.n)
+    basis = O.Basis(W, ANq, fN, np.zeros(0, np.int32), np.zeros(0), N)
+    B = 37  # two instance groups of the projection, the second ragged
+    mu = inputs.log_uniform(16, B, op.Q, 0.1, 10.0)
+    Fs = R.gaussian_source(grid, gauss_params(17, B))
+    exp = np.stack([R.rb_start(basis, mu[b], Fs[b]) for b in range(B)])
+    with rbws.Problem(grid, blocks) as P:
+        rbws.rbws_set_basis(P.h, W, ANq, fN)
+        f = torch.from_numpy(Fs).cuda()
+        u = torch.empty_like(f)
+        got = {}
+        for name, prec in (("fp32ir", rbws.FP32_IR), ("fp64", rbws.FP64)):
+            rbws.rbws_solve_batch_rhs(P.h, mu, f, 1e-12, rbws.WARM_GALERKIN, u,
+                                      rbws.rbws_options_default(max_iters=0, precision=prec))
+            got[name] = u.cpu().numpy()
+    rel = lambda x: np.linalg.norm(x - exp, axis=1) / np.linalg.norm(exp, axis=1)
+    assert np.all(rel(got["fp32ir"]) <= 1e-5), rel(got["fp32ir"]).max()
+    assert np.all(rel(got["fp64"]) <= 1e-10), rel(got["fp64"]).max()
 
 
 def test_unsupported_starts_are_refused():
