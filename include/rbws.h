@@ -89,7 +89,7 @@ typedef enum {
                        correction is folded into the FP64 solution and the
                        FP64 residual f - A u replaces the FP32 one every
                        inner_tol reduction (reliable updates); the search
-                       direction is kept; convergence is judged on the FP64
+                       direction is kept; convergence is decided on the FP64
                        residual                                                 */
 } rbws_precision;
 
