@@ -208,12 +208,14 @@ RBWS_API rbws_status rbws_apply_mg32(rbws_problem p, const double* mu, int32_t B
  * 8*B*Q + 64*B*C bytes (+ 32*B*C for float32), each part rounded up to 256,
  * where C is the number of coefficient classes of the grid (at most
  * (3*bx+2)*(3*by+2)*(3*bz+2)); larger requests return RBWS_ERR_INVALID_ARG
- * with the sizes in the message.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents; every call overwrites what it reads, so nothing needs to
- * start at zero.  Calls whose GPU work overlaps (from two threads, two
- * problems on one device, or two streams) race on the array.  Synchronous. */
+ * with the sizes in the message.  The first call on a device (and the first
+ * after the caller reset that device's context) sets up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * every call overwrites what it reads, so nothing needs to start at zero.
+ * Calls whose GPU work overlaps (from two threads, two problems on one
+ * device, or two streams) race on the array.  Synchronous: the call returns
+ * after its GPU work has completed. */
 RBWS_API rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu, int32_t B,
                                                 const void* x, void* y, int32_t precision,
                                                 void* stream);

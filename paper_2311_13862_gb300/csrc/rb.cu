@@ -392,13 +392,14 @@ int launch_project32(int64_t n, int N, int B, const float* W, const double* F, i
   const int Sused = (int)((n + per - 1) / per);
   const dim3 grid((unsigned)Sused, (unsigned)((B + kProjInst - 1) / kProjInst));
   const size_t smem = sizeof(float) * (size_t)N * kProjRun;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_project32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_project32<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_project32<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(k_project32<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
+  // The shared-memory limit is a per-device attribute of each kernel: set it on every call
+  // (cheap), so a problem on any device, and concurrent callers, launch with it raised.
+  auto raise = [](const void* k) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); };
+  if (smem > 48 * 1024) {
+    if (N <= 16) raise((const void*)k_project32<2>);
+    else if (N <= 40) raise((const void*)k_project32<5>);
+    else if (N <= 80) raise((const void*)k_project32<10>);
+    else raise((const void*)k_project32<20>);
   }
   if (N <= 16) k_project32<2><<<grid, 256, smem, s>>>(n, N, B, W, F, ldf, per, part);
   else if (N <= 40) k_project32<5><<<grid, 256, smem, s>>>(n, N, B, W, F, ldf, per, part);

@@ -31,18 +31,42 @@ constexpr int kMaxDevices = 64;
 // symbol; kernels must be given the address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
+// cuCtxGetCurrent through the runtime's driver entry-point query (the library links
+// only the CUDA runtime).
+typedef int (*CtxGetCurrentFn)(void**);
+
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+void* g_scratch_ctx[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on `device` (which must be current).
-// Looked up once per device; returns nullptr and sets the error on failure.
+// Set up once per device: the address is looked up with cudaGetSymbolAddress
+// the first time and kept together with the context it belongs to.  If the
+// caller has torn that context down since (cudaDeviceReset), the module is
+// loaded again in the new context and the address is looked up again.
+// Returns nullptr and sets the error on failure.
 void* scratch_address(int device) {
   if (device < 0 || device >= kMaxDevices) {
     set_error("rbws_apply_operator_static: device index out of range");
     return nullptr;
   }
+  void* ctx = nullptr;
+  CtxGetCurrentFn cur = ctx_get_current();
+  if (cur && cur(&ctx) != 0) ctx = nullptr;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[device]) {
+  if (!g_scratch_addr[device] || !cur || ctx != g_scratch_ctx[device]) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess) {
@@ -50,6 +74,7 @@ void* scratch_address(int device) {
       return nullptr;
     }
     g_scratch_addr[device] = ptr;
+    g_scratch_ctx[device] = ctx;
   }
   return g_scratch_addr[device];
 }
