@@ -7,7 +7,7 @@ rbws_oracle.c (plain C, FP64, explicit CSR), and this module only marshals
 numpy arrays through ctypes.
 
 Function map (paper passage -> function):
-  Eq. (1), Sec. 4 model problem        assemble(), Operator.matvec()
+  Eq. (1), Sec. 4 model problem        assemble(), Operator.matvec(); assemble_mu() (one mu)
   Algorithm 1 (PCG), Algorithm 4       pcg()
   Sec. 2.3 RB system (Galerkin)        rb_solve(), cholesky()
   Algorithm 3 (MSRB preconditioner)    pcg(precond=MSRB), solve_batch(precond=MSRB)
@@ -48,6 +48,7 @@ def lib():
         L.orc_csr_nnz.argtypes = [i32] * 3
         L.orc_csr_nnz.restype = i64
         L.orc_assemble_affine.argtypes = [i32, i32, i32, P, i32, P, P, P]
+        L.orc_assemble_mu.argtypes = [i32, i32, i32, P, i32, P, P, P, P]
         L.orc_csr_combine.argtypes = [i64, i32, P, P, P]
         L.orc_csr_matvec.argtypes = [i64, P, P, P, P, P]
         L.orc_cholesky.argtypes = [i32, P]
@@ -150,6 +151,30 @@ def assemble(grid, blocks=None, submap=None, Q=None) -> Operator:
     if rc != 0:
         raise ValueError("orc_assemble_affine failed: %d" % rc)
     return Operator(tuple(grid), Q, row_ptr, col, vals)
+
+
+def assemble_mu(grid, mu, blocks=None, submap=None, Q=None) -> Operator:
+    """A(mu) for one parameter, assembled directly (orc_assemble_mu), as a one-term operator:
+    its matvec and mg.Hierarchy take the coefficient [1.0].  Holds one value array instead of
+    Q, for grids where Q arrays of the affine terms do not fit in memory."""
+    nx, ny, nz = grid
+    if submap is None:
+        submap = block_map(grid, blocks)
+        Q = blocks[0] * blocks[1] * blocks[2]
+    submap = np.ascontiguousarray(submap, dtype=np.uint8)
+    mu = _f64(mu)
+    if mu.shape != (Q,):
+        raise ValueError("mu must have Q = %d entries" % Q)
+    L = lib()
+    nnz = L.orc_csr_nnz(nx, ny, nz)
+    n = nx * ny * nz
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    vals = np.zeros((1, nnz))
+    rc = L.orc_assemble_mu(nx, ny, nz, _p(submap), Q, _p(mu), _p(row_ptr), _p(col), _p(vals))
+    if rc != 0:
+        raise ValueError("orc_assemble_mu failed: %d" % rc)
+    return Operator(tuple(grid), 1, row_ptr, col, vals)
 
 
 def cholesky(a) -> np.ndarray:

@@ -106,6 +106,56 @@ int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
   return pos == nnz ? 0 : -2;
 }
 
+int orc_assemble_mu(int nx, int ny, int nz, const uint8_t* map, int Q, const double* mu,
+                    int64_t* row_ptr, int32_t* col, double* vals) {
+  /* Eq. (1) for one parameter, written out directly: kappa(node) = mu[map(node)],
+   * face coefficient (kappa_self + kappa_nb)/2 (a boundary face: kappa_self),
+   * scaled by 1/h^2 of its axis; the face adds to the diagonal and its negative
+   * goes to the neighbour's column.  Same sparsity pattern and column order as
+   * orc_assemble_affine. */
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t nnz = orc_csr_nnz(nx, ny, nz);
+  const double sx = (double)(nx + 1) * (nx + 1);
+  const double sy = (double)(ny + 1) * (ny + 1);
+  const double sz = (double)(nz + 1) * (nz + 1);
+  for (int64_t e = 0; e < n; e++)
+    if (map[e] >= Q) return -1;
+  int64_t pos = 0;
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        const int64_t row = ((int64_t)k * ny + j) * nx + i;
+        const double kap = mu[map[row]];
+        /* neighbours in increasing column order: z-1, y-1, x-1, (self), x+1, y+1, z+1 */
+        const int di[6] = {0, 0, -1, 1, 0, 0};
+        const int dj[6] = {0, -1, 0, 0, 1, 0};
+        const int dk[6] = {-1, 0, 0, 0, 0, 1};
+        const double sc[6] = {sz, sy, sx, sx, sy, sz};
+        row_ptr[row] = pos;
+        double diag = 0.0;
+        int64_t diag_pos = -1;
+        for (int t = 0; t < 6; t++) {
+          if (t == 3) { /* the diagonal sits between x-1 and x+1 */
+            diag_pos = pos;
+            col[pos++] = (int32_t)row;
+          }
+          const int ii = i + di[t], jj = j + dj[t], kk = k + dk[t];
+          const int interior = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+          const int64_t nb = ((int64_t)kk * ny + jj) * nx + ii;
+          const double kf = interior ? 0.5 * (kap + mu[map[nb]]) * sc[t] : kap * sc[t];
+          diag += kf;
+          if (interior) {
+            col[pos] = (int32_t)nb;
+            vals[pos] = -kf;
+            pos++;
+          }
+        }
+        vals[diag_pos] = diag;
+      }
+  row_ptr[n] = pos;
+  return pos == nnz ? 0 : -2;
+}
+
 void orc_csr_combine(int64_t nnz, int Q, const double* vals_q, const double* mu, double* vals_out) {
   for (int64_t e = 0; e < nnz; e++) {
     double s = 0.0;

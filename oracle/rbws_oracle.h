@@ -44,6 +44,13 @@ int64_t orc_csr_nnz(int nx, int ny, int nz);
 int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
                         int64_t* row_ptr, int32_t* col, double* vals);
 
+/* CSR of A(mu) for one parameter, assembled directly from kappa = mu[map]
+ * (Eq. 1; the same face rule as above, so A(mu) = sum_q mu_q A_q up to
+ * rounding).  One value array instead of Q: the memory-light form for large
+ * grids with many subdomains.  Returns 0, or -1 if a map entry is >= Q. */
+int orc_assemble_mu(int nx, int ny, int nz, const uint8_t* map, int Q, const double* mu,
+                    int64_t* row_ptr, int32_t* col, double* vals);
+
 /* vals_out[e] = sum_q mu[q] * vals_q[q][e]  (A(mu) = sum_q mu_q A_q). */
 void orc_csr_combine(int64_t nnz, int Q, const double* vals_q, const double* mu, double* vals_out);
 

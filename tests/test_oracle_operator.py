@@ -87,3 +87,35 @@ def test_face_coefficient_is_arithmetic_mean():
     assert A[1, 2] == pytest.approx(-4.0 / h2, rel=1e-15)
     # node 0: two x faces with kappa 2 (one to the boundary) + four y/z faces to the boundary
     assert A[0, 0] == pytest.approx((2 * 2.0 / h2) + 4 * 2.0 / (1 / 2) ** 2, rel=1e-15)
+
+
+@pytest.mark.parametrize("grid,blocks", [((4, 4, 4), (2, 1, 1)), ((6, 5, 7), (2, 2, 2)),
+                                         ((7, 7, 7), (3, 3, 3)), ((9, 4, 6), (3, 1, 2))])
+def test_direct_assembly_equals_the_affine_sum(grid, blocks):
+    """orc_assemble_mu writes Eq. (1) for one mu directly; it must equal sum_q mu_q A_q of the
+    affine terms (same pattern, values to rounding) and, at mu = 1, the textbook Laplacian."""
+    op = O.assemble(grid, blocks)
+    for seed in (11, 12):
+        mu = inputs.log_uniform(seed, 1, op.Q, 0.01, 100.0)[0]
+        one = O.assemble_mu(grid, mu, blocks=blocks)
+        assert np.array_equal(one.row_ptr, op.row_ptr) and np.array_equal(one.col, op.col)
+        ref = op.values(mu)
+        assert np.max(np.abs(one.vals_q[0] - ref)) <= 4e-16 * np.max(np.abs(ref))
+        A = sp.csr_matrix((one.vals_q[0], one.col, one.row_ptr)).toarray()
+        assert np.array_equal(A, A.T)
+    lap = O.assemble_mu(grid, np.ones(op.Q), blocks=blocks)
+    A1 = sp.csr_matrix((lap.vals_q[0], lap.col, lap.row_ptr)).toarray()
+    L = laplacian_3d(*grid).toarray()
+    assert np.max(np.abs(A1 - L)) <= 1e-12 * np.max(np.abs(L))
+
+
+def test_direct_assembly_with_an_explicit_map():
+    grid = (6, 5, 4)
+    m = inputs.random_field(13, 6 * 5 * 4)
+    submap = (np.abs(m) * 7).astype(np.uint8) % 3
+    op = O.assemble(grid, submap=submap, Q=3)
+    mu = np.array([0.5, 3.0, 40.0])
+    one = O.assemble_mu(grid, mu, submap=submap, Q=3)
+    x = inputs.random_field(14, op.n)
+    y_ref = op.matvec(mu, x)
+    assert np.linalg.norm(one.matvec([1.0], x) - y_ref) <= 1e-14 * np.linalg.norm(y_ref)
