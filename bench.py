@@ -244,11 +244,25 @@ def bench_gaussian(args):
         arms[name] = {"solves_per_s": B / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(np.mean(it)),
                       "iters_max": int(np.max(it)), "relres_max": float(np.max(rel)),
                       "all_converged": bool(np.all(st == 0)), "clocks": clk.summary()}
-    # independent check: the oracle's FP64 true residual of two solutions
-    import oracle as O
-    op = O.assemble(w.grid, w.blocks)
-    uu, ff = u.cpu().numpy(), f.cpu().numpy()
-    chk = [float(np.linalg.norm(ff[b] - op.matvec(mus[b], uu[b])) / np.linalg.norm(ff[b])) for b in (0, B - 1)]
+    # error of every solution against the oracle: its own Gaussian sources, its FP64 MGCG
+    # solutions from zero to 1e-13, and the relative L2 error and true residual of each GPU
+    # solution (the Galerkin arm's, which u holds after the zero arm: re-solved once here)
+    oracle_error = None
+    if not args.no_oracle_check:
+        from oracle import batch as O_batch
+        from oracle import rhs as O_rhs
+        f_or = O_rhs.gaussian_source(w.grid, inputs.test_sources(w, B))
+        U_ref, _, r_rel, r_st, r_s, r_p = O_batch.reference_solutions(w.grid, mus, blocks=w.blocks, f=f_or,
+                                                                      tol=1e-13)
+        errs = {}
+        for name, warm in (("mgcg_zero_fp32ir", rbws.WARM_ZERO), ("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN)):
+            rbws.rbws_solve_batch_rhs(P.h, mus, f, w.tol, warm, u, opt)
+            es = O_batch.error_summary(w.grid, mus, u.cpu().numpy(), U_ref, blocks=w.blocks, f=f_or)
+            errs[name] = {k: v for k, v in es.items() if k not in ("relL2", "true_relres")}
+        oracle_error = {"arms": errs, "reference": {"solver": "oracle MGCG (FP64) from zero, oracle Gaussian "
+                                                              "sources", "tol": 1e-13, "relres_max": float(r_rel.max()),
+                                                    "all_converged": bool(np.all(r_st == 0)), "processes": r_p,
+                                                    "seconds": r_s}}
     head = arms["mgcg_galerkin_fp32ir"]
     line = {"metric": METRIC, "value": head["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
@@ -261,7 +275,7 @@ def bench_gaussian(args):
                        "tol": w.tol, "l2": "no flush: solver working set > 129 MB L2"},
             "clocks": head["clocks"], "arms": arms, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
             "iters_mean": head["iters_mean"], "relres_max": head["relres_max"],
-            "oracle_true_relres_sampled": chk}
+            "oracle_error": oracle_error}
     print(json.dumps(line))
     P.close()
 
@@ -269,12 +283,27 @@ def bench_gaussian(args):
 def bench_requests(args):
     """96 requests (32 each on 96^3, 128^3, 256^3 grids, 3x3x3 blocks, mu in [0.1,10]^27) per step,
     interleaved in a fixed order, in one rbws_solve_requests call: learned start with one reduced
-    correction, FP32 PCG inside FP64 refinement to 1e-10; per-request latency p50/p99."""
+    correction, MG-preconditioned FP32 PCG inside FP64 refinement to 1e-10; per-request latency
+    p50/p99; every request's error against the oracle's FP64 solution."""
     import torch
     from paper_2311_13862_gb300 import build, inputs, rbws
     build.build()
     torch.cuda.set_device(0)
     names = ["c5-96", "c5-128", "c5-256"]
+    order = [k % 3 for k in range(96)]  # 96^3, 128^3, 256^3, 96^3, ...
+    per = [order.count(k) for k in range(3)]
+    # the oracle's FP64 solutions of every request, before any GPU work (MGCG from zero to 1e-12 on
+    # A(mu) assembled per request; 8 worker processes for the 256^3 grid, about 7 GB each)
+    refs = {}
+    if not args.no_oracle_check:
+        from oracle import batch as O_batch
+        for k, nm in enumerate(names):
+            w = inputs.WORKLOADS[nm]
+            procs = 8 if w.grid[0] >= 256 else None
+            U, _, r_rel, r_st, r_s, r_p = O_batch.reference_solutions(w.grid, inputs.test_mu(w)[:per[k]],
+                                                                      blocks=w.blocks, tol=1e-12, processes=procs)
+            refs[nm] = (U, {"relres_max": float(r_rel.max()), "all_converged": bool(np.all(r_st == 0)),
+                            "seconds": r_s, "processes": r_p})
     probs, offline = [], {}
     for nm in names:
         w = inputs.WORKLOADS[nm]
@@ -289,7 +318,6 @@ def bench_requests(args):
         offline[nm] = {"N": N, "greedy_s": t1 - t0, "train_s": t2 - t1, "train_loss": loss,
                        "eta_last": float(eta[-1]), "tile": tile[:3], "schedule": tile[4], "tile_pair_ms": tile[3]}
         probs.append((w, P))
-    order = [k % 3 for k in range(96)]  # 96^3, 128^3, 256^3, 96^3, ...
     mus = [None] * 96
     count = [0, 0, 0]
     for r, k in enumerate(order):
@@ -297,7 +325,7 @@ def bench_requests(args):
         count[k] += 1
     handles = [probs[k][1].h for k in order]
     outs = [torch.empty(probs[k][1].n, dtype=torch.float64, device="cuda") for k in order]
-    opt = rbws.rbws_options_default(precision=rbws.FP32_IR)
+    opt = rbws.rbws_options_default(precision=rbws.FP32_IR, precond=rbws.PREC_MG)
     for _ in range(args.warmup):
         rbws.rbws_solve_requests(handles, mus, outs, 1e-10, rbws.WARM_LEARNED_CORRECTED, opt)
     torch.cuda.synchronize()
@@ -317,13 +345,24 @@ def bench_requests(args):
     per_grid = {}
     for k, nm in enumerate(names):
         sel_k = np.array([order[r] == k for r in range(96)] * args.steps)
-        per_grid[nm] = {"iters_mean": float(it[sel_k].mean()), "latency_ms_p50": float(np.percentile(lat[sel_k], 50))}
+        per_grid[nm] = {"iters_mean": float(it[sel_k].mean()), "iters_max": int(it[sel_k].max()),
+                        "latency_ms_p50": float(np.percentile(lat[sel_k], 50)),
+                        "latency_ms_p99": float(np.percentile(lat[sel_k], 99))}
+        if nm in refs:
+            w = probs[k][0]
+            rows = [r for r in range(96) if order[r] == k]
+            U = np.stack([outs[r].cpu().numpy() for r in rows])
+            es = O_batch.error_summary(w.grid, np.stack([mus[r] for r in rows]), U, refs[nm][0], blocks=w.blocks)
+            per_grid[nm]["oracle_error"] = {kk: v for kk, v in es.items() if kk not in ("relL2", "true_relres")}
+            per_grid[nm]["oracle_error"]["reference"] = dict(refs[nm][1], solver="oracle MGCG (FP64) from zero",
+                                                             tol=1e-12)
     line = {"metric": METRIC, "value": 96 / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
             "config": {"workload": "96 requests per step: 32 each on 96^3, 128^3, 256^3 interior grids, 3x3x3 "
                                    "blocks (p=27), mu log-uniform in [0.1,10]^27, RB N<=60 per grid, learned "
-                                   "start + one reduced correction, FP32 PCG in FP64 refinement to 1e-10",
+                                   "start + one reduced correction, MG-preconditioned FP32 PCG in FP64 "
+                                   "refinement to 1e-10",
                        "timing": "host wall clock around each rbws_solve_requests call (synchronous)"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
@@ -331,6 +370,93 @@ def bench_requests(args):
     print(json.dumps(line), flush=True)
     for w, P in probs:
         P.close()
+
+
+def bench_c3(args):
+    """The mixed-precision workload: 128^3 interior grid (2,097,152 DoFs), 2x2x2 octants, mu
+    log-uniform in [0.01,100]^8 (contrast up to 1e4), RB N<=40 by greedy over 256 training mu,
+    64 test mu per step.  Headline: Galerkin RB start, MG-preconditioned FP32 PCG inside FP64
+    refinement to 1e-10.  Arms: zero start, FP64, and the learned start (8 -> 256 -> 256 -> 256
+    -> N network trained on the GPU on the Galerkin coefficients of 4096 parameters), with and
+    without one reduced correction.  Every solution of every arm is measured against the
+    oracle's FP64 solution."""
+    import torch
+    from paper_2311_13862_gb300 import build, inputs, rbws
+    w = inputs.WORKLOADS["c3"]
+    B = args.batch or w.n_test
+    mus = inputs.test_mu(w, B)
+    U_ref, ref_info = None, None
+    if not args.no_oracle_check:
+        from oracle import batch as O_batch
+        U_ref, _, r_rel, r_st, r_s, r_p = O_batch.reference_solutions(w.grid, mus, blocks=w.blocks, tol=1e-12)
+        ref_info = {"solver": "oracle MGCG (FP64) from zero", "tol": 1e-12, "relres_max": float(r_rel.max()),
+                    "all_converged": bool(np.all(r_st == 0)), "processes": r_p, "seconds": r_s}
+    build.build()
+    torch.cuda.set_device(0)
+    P = rbws.Problem(w.grid, w.blocks)
+    t0 = time.perf_counter()
+    N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
+    torch.cuda.synchronize()
+    t_off = time.perf_counter() - t0
+    tile = rbws.rbws_autotune(P.h, B)
+    t0 = time.perf_counter()
+    loss = rbws.rbws_train_surrogate(P.h, inputs.surrogate_mu(w, 4096), hidden=256, epochs=args.mlp_epochs,
+                                     batch=256, lr=1e-3, mu_lo=w.mu_lo, mu_hi=w.mu_hi, seed=3003)
+    torch.cuda.synchronize()
+    learned = {"train_s": time.perf_counter() - t0, "final_loss": loss, "samples": 4096,
+               "epochs": args.mlp_epochs, "hidden": 256, "layers": "%d -> 256 -> 256 -> 256 -> %d" % (w.Q, N)}
+    u = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
+    M, FP32, FP64 = rbws.PREC_MG, rbws.FP32_IR, rbws.FP64
+    arm_list = [("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN, FP32), ("mgcg_zero_fp32ir", rbws.WARM_ZERO, FP32),
+                ("mgcg_learned_fp32ir", rbws.WARM_LEARNED, FP32),
+                ("mgcg_learned_corrected_fp32ir", rbws.WARM_LEARNED_CORRECTED, FP32),
+                ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, FP64), ("mgcg_zero_fp64", rbws.WARM_ZERO, FP64)]
+    arms, head_err, clocks = {}, None, None
+    for name, warm, pr in arm_list:
+        steps = args.steps if name == "mgcg_galerkin_fp32ir" else max(1, args.arm_steps)
+        opt = rbws.rbws_options_default(precision=pr, precond=M)
+        for _ in range(args.warmup if name == "mgcg_galerkin_fp32ir" else 1):
+            rbws.rbws_solve_batch(P.h, mus, w.tol, warm, u, opt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record()
+            for _ in range(steps):
+                rc, it, rel, st = rbws.rbws_solve_batch(P.h, mus, w.tol, warm, u, opt)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        arms[name] = {"solves_per_s": B / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(np.mean(it)),
+                      "iters_max": int(np.max(it)), "relres_max": float(np.max(rel)),
+                      "all_converged": bool(np.all(st == 0))}
+        if name == "mgcg_galerkin_fp32ir":
+            clocks = clk.summary()
+        if U_ref is not None:
+            uh = u.cpu().numpy()
+            if name == "mgcg_galerkin_fp32ir":
+                es = O_batch.error_summary(w.grid, mus, uh, U_ref, blocks=w.blocks)
+                head_err = {k: v for k, v in es.items() if k not in ("relL2", "true_relres")}
+                head_err["reference"] = ref_info
+                arms[name]["oracle_relL2_max"], arms[name]["oracle_relL2_mean"] = es["relL2_max"], es["relL2_mean"]
+            else:
+                e = O_batch.relL2(uh, U_ref)
+                arms[name]["oracle_relL2_max"], arms[name]["oracle_relL2_mean"] = float(e.max()), float(e.mean())
+    head = arms["mgcg_galerkin_fp32ir"]
+    line = {"metric": METRIC, "value": head["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": "128^3 interior grid (2,097,152 DoFs), 2x2x2 octants (p=8), mu log-uniform in "
+                                   "[0.01,100]^8, RB N<=40 by greedy over 256 training mu, %d test mu per step, "
+                                   "MG-PCG in FP32 inside FP64 refinement to rel-res 1e-10" % B,
+                       "batch_per_gpu": B, "N": int(N), "warm": "galerkin", "precision": "fp32ir",
+                       "precond": "mg", "tol": w.tol, "l2": "no flush: solver working set > 129 MB L2"},
+            "clocks": clocks, "arms": arms, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "autotune": {"tile": list(tile[:3]), "schedule": tile[4]}, "learned_training": learned,
+            "iters_mean": head["iters_mean"], "relres_max": head["relres_max"], "oracle_error": head_err}
+    if "mgcg_zero_fp64" in arms:
+        line["speedup_vs_mgcg_zero_fp64"] = head["solves_per_s"] / arms["mgcg_zero_fp64"]["solves_per_s"]
+    print(json.dumps(line), flush=True)
+    P.close()
 
 
 def main():
@@ -345,13 +471,16 @@ def main():
     ap.add_argument("--precond", default="mg", choices=["mg", "jacobi"],
                     help="preconditioner of the headline arm: multigrid V-cycle (MGCG) or Jacobi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle's reference solutions (per-instance errors of every result)")
     ap.add_argument("--arm-steps", type=int, default=2, help="timed steps of each side arm (0: skip arms)")
     ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
     ap.add_argument("--mlp-epochs", type=int, default=2000,
                     help="epochs of the learned warm start's training (0: skip the learned arms)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c5", "c2g"],
-                    help="c2: the 64^3 batched workload (default line); c5: 96 requests on 96^3/128^3/256^3; "
-                         "c2g: the 64^3 operator with a Gaussian source per parameter")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "c2g"],
+                    help="c2: the 64^3 batched workload (default line); c3: 128^3 octants, contrast 1e4, 64 mu; "
+                         "c5: 96 requests on 96^3/128^3/256^3; c2g: the 64^3 operator with a Gaussian source "
+                         "per parameter")
     ap.add_argument("--c5-train", type=int, default=256, help="greedy training parameters per grid (c5)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in FP32 tile/schedule instead of the autotuned one")
@@ -366,6 +495,8 @@ def main():
         return bench_requests(args)
     if args.workload == "c2g":
         return bench_gaussian(args)
+    if args.workload == "c3":
+        return bench_c3(args)
 
     import torch
     import torch.distributed as dist
@@ -391,6 +522,16 @@ def main():
     B = args.batch or w.n_test
     # each rank solves its own batch of B parameters (weak scaling, no collective on the data path)
     mus = ranks.shard(inputs.test_mu(w, B * world), B, rank, world)
+    # the oracle's FP64 solutions of this rank's parameters (MGCG from zero to 1e-13, spawned
+    # worker processes, before any timed region): every solution of every arm is measured
+    # against them below
+    from oracle import batch as O_batch
+    U_ref, oracle_ref = None, None
+    if rank == 0 and not args.no_oracle_check:
+        U_ref, r_it, r_rel, r_st, r_s, r_p = O_batch.reference_solutions(w.grid, mus, blocks=w.blocks, tol=1e-13)
+        oracle_ref = {"solver": "oracle MGCG (FP64, scipy CSR) from zero", "tol": 1e-13, "instances": int(B),
+                      "relres_max": float(r_rel.max()), "all_converged": bool(np.all(r_st == 0)),
+                      "processes": r_p, "seconds": r_s}
     P = rbws.Problem(w.grid, w.blocks, device=local)
     t0 = time.perf_counter()
     N, sel, eta = rbws.rbws_offline_greedy(P.h, inputs.train_mu(w), w.n_max, 0.0, 1e-12)
@@ -520,18 +661,17 @@ def main():
     u_host = u_hosts[(e2e_steps - 1) % 2]
     e2e_ms = ranks.max_over_ranks(e2e_ms, "cuda")
 
-    # ---- side arms: zero start and the other precision ----
+    # ---- side arms: zero start, the other precision, the learned starts, MSRB, L1ROC ----
     arms = {}
+    J, M, PJ, PG = rbws.PREC_JACOBI, rbws.PREC_MG, rbws.FP32_IR, rbws.FP64
     arm_list = [] if args.arm_steps <= 0 else [
-        ("galerkin_" + args.precision, rbws.WARM_GALERKIN, headline),
-        ("zero_fp64", rbws.WARM_ZERO, rbws.FP64),
-        ("galerkin_fp64" if args.precision != "fp64" else "galerkin_fp32ir",
-         rbws.WARM_GALERKIN, rbws.FP32_IR if args.precision == "fp64" else rbws.FP64),
-        ("zero_fp32ir", rbws.WARM_ZERO, rbws.FP32_IR)]
+        ("galerkin_fp32ir", rbws.WARM_GALERKIN, PJ, J), ("zero_fp64", rbws.WARM_ZERO, PG, J),
+        ("galerkin_fp64", rbws.WARM_GALERKIN, PG, J), ("zero_fp32ir", rbws.WARM_ZERO, PJ, J)]
     learned = None
     if args.arm_steps > 0 and args.mlp_epochs > 0:
         # learned warm start (same 64^3 problem): p -> 256 -> 256 -> 256 -> N network trained on
-        # the GPU on the reduced Galerkin coefficients of 4096 seeded parameters
+        # the GPU on the reduced Galerkin coefficients of 4096 seeded parameters; its arms run with
+        # the headline's preconditioner and precision
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         loss = rbws.rbws_train_surrogate(P.h, inputs.surrogate_mu(inputs.WORKLOADS["c4"], 4096), hidden=256,
@@ -539,25 +679,21 @@ def main():
                                          mu_hi=w.mu_hi, seed=3004)
         learned = {"train_s": time.perf_counter() - t0, "final_loss": loss, "samples": 4096,
                    "epochs": args.mlp_epochs, "hidden": 256}
-        arm_list += [("learned_" + args.precision, rbws.WARM_LEARNED, headline),
-                     ("learned_corrected_" + args.precision, rbws.WARM_LEARNED_CORRECTED, headline)]
+        pre = "mgcg_" if args.precond == "mg" else ""
+        arm_list += [(pre + "learned_" + args.precision, rbws.WARM_LEARNED, headline, head_pc),
+                     (pre + "learned_corrected_" + args.precision, rbws.WARM_LEARNED_CORRECTED, headline, head_pc)]
     if args.arm_steps > 0:
         # the RB-preconditioned start: Galerkin start, then PCG with the MSRB preconditioner
         # (Algorithm 3, FP64 only)
-        arm_list.append(("msrb_fp64", rbws.WARM_GALERKIN, rbws.FP64))
-        # MGCG (Algorithm 2 as the preconditioner, FP64), from zero and from the RB initial value
-        arm_list += [("mgcg_zero_fp64", rbws.WARM_ZERO, rbws.FP64), ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, rbws.FP64),
-                     ("mgcg_zero_fp32ir", rbws.WARM_ZERO, rbws.FP32_IR),
-                     ("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN, rbws.FP32_IR)]
-    if args.arm_steps > 0:
+        arm_list.append(("msrb_fp64", rbws.WARM_GALERKIN, PG, rbws.PREC_MSRB))
+        # MGCG (Algorithm 2 as the preconditioner), from zero and from the RB initial value
+        arm_list += [("mgcg_zero_fp64", rbws.WARM_ZERO, PG, M), ("mgcg_galerkin_fp64", rbws.WARM_GALERKIN, PG, M),
+                     ("mgcg_zero_fp32ir", rbws.WARM_ZERO, PJ, M), ("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN, PJ, M)]
         # the paper's own RBWS start: L1ROC (DEIM points, over-collocation), then MGCG; its offline
         # greedy replaces the Galerkin basis, so this arm runs last
-        arm_list.append(("l1roc_mgcg_fp32ir", rbws.WARM_L1ROC, rbws.FP32_IR))
-    precond_of = {"msrb_fp64": rbws.PREC_MSRB, "l1roc_mgcg_fp32ir": rbws.PREC_MG}
-    precond_of.update({k: rbws.PREC_MG for k in ("mgcg_zero_fp64", "mgcg_galerkin_fp64", "mgcg_zero_fp32ir",
-                                                "mgcg_galerkin_fp32ir")})
+        arm_list.append(("l1roc_mgcg_fp32ir", rbws.WARM_L1ROC, PJ, M))
     l1roc_off = None
-    for name, warm, pr in arm_list:
+    for name, warm, pr, pc in arm_list:
         if name == "l1roc_mgcg_fp32ir":
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -567,12 +703,17 @@ def main():
                          "collocation_points": int(len(rbws.rbws_l1roc_info(P.h)[0]))}
         if name == head_name:
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
+            a_err = None
         else:
-            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1,
-                                             precond=precond_of.get(name, rbws.PREC_JACOBI))
+            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1, precond=pc)
+            # error of this arm's solutions against the oracle's FP64 solutions (every instance)
+            a_err = None if U_ref is None else O_batch.relL2(u.cpu().numpy(), U_ref)
         arms[name] = {"solves_per_s": ranks.job_rate(B, world, a_ms), "ms_per_step": a_ms,
                       "iters_mean": float(np.mean(a_it)), "iters_max": int(np.max(a_it)),
                       "relres_max": float(np.max(a_rel)), "all_converged": bool(np.all(a_st == 0))}
+        if a_err is not None:
+            arms[name]["oracle_relL2_max"] = float(a_err.max())
+            arms[name]["oracle_relL2_mean"] = float(a_err.mean())
 
     # ---- roofline of the dominant kernel, with the stencil phase beside it ----
     peak, peak_kind = peaks()
@@ -690,15 +831,15 @@ def main():
         t_warm = 1.0 / (value / world)
         line["bep_solves"] = t_off / (t_zero - t_warm) if t_zero > t_warm else None
 
-    # ---- sampled independent check: oracle FP64 true residual of two GPU solutions ----
-    if rank == 0:
-        import oracle as O
-        op = O.assemble(w.grid, w.blocks)
-        uu = u_host.numpy()
-        chk = []
-        for b in (0, B - 1):
-            chk.append(float(np.linalg.norm(np.ones(P.n) - op.matvec(mus[b], uu[b])) / np.sqrt(P.n)))
-        line["oracle_true_relres_sampled"] = chk
+    # ---- error of every headline solution against the oracle: relative L2 error against the
+    # oracle's FP64 solution and the oracle's true relative residual (CSR operator) ----
+    if U_ref is not None:
+        es = O_batch.error_summary(w.grid, mus, u_host.numpy(), U_ref, blocks=w.blocks)
+        line["oracle_error"] = {k: v for k, v in es.items() if k not in ("relL2", "true_relres")}
+        line["oracle_error"]["reference"] = oracle_ref
+        if head_name in arms:
+            arms[head_name]["oracle_relL2_max"] = es["relL2_max"]
+            arms[head_name]["oracle_relL2_mean"] = es["relL2_mean"]
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1) ----
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

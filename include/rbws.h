@@ -142,6 +142,15 @@ typedef struct {
                            the last iteration, or past hist_len, are NaN /
                            not written.                                          */
   int32_t hist_len;     /* entries per instance (>= 1 when relres_hist is set)   */
+  int64_t wait_cycles;  /* bound of each device-side wait of the TMA-fed FP32
+                           kernels (an mbarrier wait for a staged plane), in SM
+                           clock cycles; 0 = the default, 4e9 (about 2 s at
+                           2 GHz).  When a wait runs out the kernel flags it,
+                           lets its copies in flight land and returns, and the
+                           call returns RBWS_ERR_DEVICE_TIMEOUT with no result;
+                           the problem stays usable.  A small value is a test
+                           knob that makes the waits run out on purpose.  < 0
+                           returns RBWS_ERR_INVALID_ARG.                       */
 } rbws_options;
 
 /* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64,

@@ -872,6 +872,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   a.tol = tol;
   a.max_iters = o.max_iters;
   a.precond = o.precond;
+  a.wait_cycles = o.wait_cycles;
   a.ru = 1;
   // auto: 1e-2.  With MG (about a decade per iteration) and blocks of 2 iterations
   // that keeps the FP32 recursion within about four decades of its last update.
@@ -1244,6 +1245,10 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
     set_error("solve: unknown precision");
     return RBWS_ERR_INVALID_ARG;
   }
+  if (o.wait_cycles < 0) {
+    set_error("solve: wait_cycles must be >= 0");
+    return RBWS_ERR_INVALID_ARG;
+  }
   if (o.relres_hist && (o.precision != RBWS_FP64 || o.hist_len < 1)) {
     set_error("solve: the residual history needs FP64 precision and hist_len >= 1");
     return RBWS_ERR_INVALID_ARG;
@@ -1486,6 +1491,7 @@ void rbws_options_default(rbws_options* o) {
   o->profile = nullptr;
   o->relres_hist = nullptr;
   o->hist_len = 0;
+  o->wait_cycles = 0;
 }
 
 rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,

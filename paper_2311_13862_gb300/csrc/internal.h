@@ -154,6 +154,9 @@ struct CGArgs {
   int hist_len;
   // multigrid preconditioner (host pointer, read by the launchers only)
   const struct MGBatch* mg;
+  // bound of each device-side wait in the pipelined kernels, clock64 cycles (0: the
+  // built-in default of about 2 s)
+  long long wait_cycles;
 };
 
 // ---------------------------------------------------------------------------

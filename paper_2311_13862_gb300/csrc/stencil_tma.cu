@@ -38,8 +38,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-// Bounded wait for phase `parity` of the barrier; false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Bounded wait for phase `parity` of the barrier; false if it ran out.  budget:
+// clock64 cycles (<= 0: kWaitCycles).  The waits of the normal pipeline take the
+// call's budget (rbws_options.wait_cycles); the drain after a timeout always takes
+// kWaitCycles, so that a CTA returns only once its copies in flight have landed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long budget = kWaitCycles) {
+  if (budget <= 0) budget = kWaitCycles;
   const long long t0 = clock64();
   for (;;) {
     unsigned done;
@@ -49,7 +53,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -200,9 +204,9 @@ __global__ void __launch_bounds__(256, 3)
   auto own_p = [&](int st) { return fma4(beta, ld4s(p_tile(st) + cofs), ld4s(s_tile(st) + cofs)); };
 
   // prologue: planes z0-1 (own column only) and z0
-  bool timed_out = !mbar_wait(&bars[0], 0);
+  bool timed_out = !mbar_wait(&bars[0], 0, a.wait_cycles);
   float4 xm = own_p(0);
-  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1, a.wait_cycles);
   float4 xc = own_p(1 % kStages);
   if (__syncthreads_or(timed_out)) goto abort;
   next_wait = 2;
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z < z1; ++z) {
       const int k = z - z0 + 1;  // index of plane z; plane z+1 is k+1
       const int sk = k % kStages, sn = (k + 1) % kStages;
-      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
       if (!to && own) {
         const float4 xp = own_p(sn);
         const int zcl = g.cz[z];
@@ -404,9 +408,9 @@ __global__ void __launch_bounds__(256, 3)
   const int64_t col = (int64_t)jn * g.nx + i;
   float* sb = a.s + (int64_t)b * g.n;
   float rho = 0.f, rr = 0.f;
-  bool timed_out = !mbar_wait(&bars[0], 0);
+  bool timed_out = !mbar_wait(&bars[0], 0, a.wait_cycles);
   float4 xm = ld4s(p_tile(0) + cofs);
-  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1, a.wait_cycles);
   float4 xc = ld4s(p_tile(1 % kStages) + cofs);
   if (__syncthreads_or(timed_out)) goto abort;
   next_wait = 2;
@@ -421,7 +425,7 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z < z1; ++z) {
       const int k = z - z0 + 1;
       const int sk = k % kStages, sn = (k + 1) % kStages;
-      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
       if (!to && own) {
         const float4 xp = ld4s(p_tile(sn) + cofs);
         const float4 s4 = ld4s(s_tile(sk) + lofs);
@@ -579,8 +583,8 @@ __global__ void __launch_bounds__(256, 3)
   const int64_t cplane = (int64_t)m.cnx * m.cny;
   const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
 
-  bool to = !mbar_wait(&bars[0], 0);
-  if (!to) to = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  bool to = !mbar_wait(&bars[0], 0, a.wait_cycles);
+  if (!to) to = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1, a.wait_cycles);
   if (__syncthreads_or(to)) goto abort;
   next_wait = 2;
   {
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z <= zlast; ++z) {
       const int k = z - z0 + 1;  // plane index of z
       const int sm_ = (k - 1) % kStages, sk = k % kStages, sn = (k + 1) % kStages;
-      to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
       float* Rz = R + (z & 1) * rpl;
       if (!to) {
         const float* Pm = xs(sm_);
@@ -819,9 +823,9 @@ __global__ void __launch_bounds__(256, 3)
     return v;
   };
   float rho = 0.f;
-  bool timed_out = !mbar_wait(&bars[0], 0);
+  bool timed_out = !mbar_wait(&bars[0], 0, a.wait_cycles);
   float4 xm = timed_out ? make_float4(0.f, 0.f, 0.f, 0.f) : xform_plane(0);
-  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1, a.wait_cycles);
   float4 xc = timed_out ? make_float4(0.f, 0.f, 0.f, 0.f) : xform_plane(1);
   if (__syncthreads_or(timed_out)) goto abort;
   next_wait = 2;
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(256, 3)
     for (int z = z0; z < z1; ++z) {
       const int k = z - z0 + 1;
       const int sk = k % kStages, sn = (k + 1) % kStages;
-      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1);
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
       if (!to) {
         const float4 xp = xform_plane(k + 1);  // plane z+1, transformed (own group and halo duty)
         if (own) {

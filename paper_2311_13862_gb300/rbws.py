@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "librbws.so")
 
 RBWS_OK = 0
 RBWS_WARN_NOT_CONVERGED = 1
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NO_BASIS, ERR_NOT_SPD, ERR_DEVICE_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
 STATUS_NAMES = {0: "OK", 1: "WARN_NOT_CONVERGED", -1: "ERR_INVALID_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
                 -4: "ERR_NO_BASIS", -5: "ERR_NOT_SPD", -6: "ERR_DEVICE_TIMEOUT", -7: "ERR_STATE",
                 -8: "ERR_UNSUPPORTED"}
@@ -51,7 +53,8 @@ class rbws_options(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32),
                 ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
                 ("check_every", C.c_int32), ("stream", C.c_void_p),
-                ("profile", C.POINTER(rbws_profile)), ("relres_hist", C.c_void_p), ("hist_len", C.c_int32)]
+                ("profile", C.POINTER(rbws_profile)), ("relres_hist", C.c_void_p), ("hist_len", C.c_int32),
+                ("wait_cycles", C.c_int64)]
 
 
 _L = None

@@ -114,3 +114,20 @@ def test_mgcg_iterations_do_not_grow_with_the_grid():
     assert its[1] <= its[0] + 3, its
     jac = O.pcg(O.assemble((31, 31, 31), (1, 1, 1)), [1.0], tol=1e-10).iters
     assert its[1] * 4 < jac
+
+
+def test_batch_reference_solutions_match_direct_solves():
+    """oracle.batch spreads MGCG solves over spawned workers on the directly assembled A(mu);
+    each must equal a solve with the affine operator, and its own error summary is zero."""
+    import oracle as O
+    from oracle import batch
+    grid, blocks = (12, 10, 8), (2, 2, 1)
+    mus = inputs.log_uniform(91, 3, 4, 0.1, 10.0)
+    U, its, rel, st, _, procs = batch.reference_solutions(grid, mus, blocks=blocks, tol=1e-12, processes=2)
+    assert procs == 2 and np.all(st == 0) and np.all(rel < 1e-12)
+    op = O.assemble(grid, blocks)
+    for b in range(3):
+        r = mg.mgcg(op, mus[b], tol=1e-12)
+        assert np.linalg.norm(U[b] - r.u) <= 1e-11 * np.linalg.norm(r.u)
+    s = batch.error_summary(grid, mus, U, U, blocks=blocks)
+    assert s["relL2_max"] == 0.0 and s["true_relres_max"] < 1e-12
