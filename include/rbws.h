@@ -151,6 +151,17 @@ typedef struct {
                            the problem stays usable.  A small value is a test
                            knob that makes the waits run out on purpose.  < 0
                            returns RBWS_ERR_INVALID_ARG.                       */
+  int32_t ru_mode;      /* FP32_IR reliable updates: 0 = auto (float-float where
+                           the grid takes the 4-node kernels, nx % 4 == 0, else
+                           FP64), 1 = FP64 (u += d, r = f - A u in FP64), 2 =
+                           float-float: the solution and the true residual are
+                           kept as pairs of floats (about 48 bits) and updated
+                           as r -= A d, u += d on the FP32 pipe; an instance
+                           whose residual meets tol is converted to FP64 and
+                           its FP64 residual decides (if it fails, the tracked
+                           residual is reset from it).  2 falls back to FP64
+                           where the 4-node kernels do not apply.             */
+  int32_t reserved;     /* 0 */
 } rbws_options;
 
 /* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64,
@@ -204,6 +215,22 @@ RBWS_API rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu,
  * stream (NULL: the problem's own).  RBWS_ERR_DEVICE_TIMEOUT if a stage wait ran out. */
 RBWS_API rbws_status rbws_apply_mg32(rbws_problem p, const double* mu, int32_t B, const void* x, void* y,
                                      void* stream);
+
+/* One reliable update of the mixed-precision iteration (the FP32 iteration
+ * inside FP64 refinement, RBWS_FP32_IR) in float-float arithmetic, exactly as
+ * rbws_solve_batch applies it with ru_mode 0 or 2 (a test entry point: it pins
+ * the float-float arithmetic against an FP64 residual).  The solution and the
+ * true residual are carried as pairs of floats (hi + lo); the call starts from
+ * u = u0, r = f - A(mu) u0 (u0 taken at FP32 precision, as the mixed-precision
+ * starts provide it) and applies one update with the correction d:
+ *   r <- r - A(mu) d,   u <- u + d,
+ * with the coefficients split into float pairs, Knuth's TwoSum for the sums and
+ * the fused multiply-add for the exact product error.  u0: device [B][n] FP64
+ * (values representable in FP32); d: device [B][n] FP32; u_out, r_out: device
+ * [B][n] FP64 = hi + lo of u and r.  Needs nx % 4 == 0 (else
+ * RBWS_ERR_UNSUPPORTED).  Synchronous; library-owned scratch. */
+RBWS_API rbws_status rbws_update_ff(rbws_problem p, const double* mu, int32_t B, const void* u0, const void* d,
+                                    void* u_out, void* r_out);
 
 /* rbws_apply_operator for callers that cannot allocate device memory after
  * start-up: services that run inside a fixed device-memory budget shared with

@@ -895,14 +895,52 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   }
   if (p->rhs.f) CK(cudaMemcpyAsync((double*)a.fnorm, p->rhs.norms, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
   else fill((double*)a.fnorm, B, p->fnorm, s);
+  // Reliable updates in float-float on the FP32 pipe (ru_ff.cu) with the 4-node tiles; FP64
+  // updates otherwise or when asked for.  Either way convergence is decided in FP64.
+  const bool ffu = v4 && o.ru_mode != 1;
+  FFState ff{};
+  if (ffu) {
+    const size_t vb = sizeof(float) * (size_t)B * p->n;
+    ff.uh = (float*)p->buf("ff_uh", vb, &err);
+    if (!err) ff.ul = (float*)p->buf("ff_ul", vb, &err);
+    if (!err) ff.rh = (float*)p->buf("ff_rh", vb, &err);
+    if (!err) ff.rl = (float*)p->buf("ff_rl", vb, &err);
+    float* cff = err ? nullptr
+                     : (float*)p->buf("ff_coef", sizeof(float) * 2 * kCoefStride * (size_t)B * p->geo.ncls(), &err);
+    if (!err) ff.part = (double*)p->buf("ff_part", sizeof(double) * (size_t)B * a.P, &err);
+    if (!err) ff.rel = (double*)p->buf("ff_rel", sizeof(double) * (size_t)B, &err);
+    if (!err) ff.chk = (int*)p->buf("ff_chk", sizeof(int) * (size_t)B, &err);
+    if (err) return (rbws_status)err;
+    ff.coef = cff;
+    ff.f = p->rhs.f ? p->rhs.f : p->d_f;
+    ff.f_stride = p->rhs.f ? p->rhs.stride : 0;
+    launch_coef_ff(coef64, (int64_t)B * p->geo.ncls(), cff, s);
+    p->launches += 1;
+  }
+  // one reliable update of the flagged instances (upd), inside or outside a capture:
+  // float-float r -= A d, u += d; the FP64 check of those meeting tol; the reset
+  auto update_ff = [&](bool start, cudaStream_t ss) -> rbws_status {
+    launch_ru_ff(a, t, ff, start, ss);
+    launch_norms_from_partials(ff.part, B, a.P, p->fnorm, ff.rel, ss, a.fnorm);
+    launch_ru_mark(a, ff, ss);
+    launch_ff_to64(a, ff, ff.chk, ss);
+    const rbws_status rr = residual_norms(p, coef64, B, u, r64, rel, ff.chk);
+    launch_ru_reset_ff(a, t, ff, start ? 1 : 0, ss);
+    return rr;
+  };
   CK(cudaMemsetAsync(d, 0, sizeof(float) * (size_t)B * p->n, s));
   // start: every instance takes an update from u (restarting its direction)
   std::vector<int> two(B, 2);
   CK(cudaMemcpyAsync(upd, two.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(a.active, 0, 3 * sizeof(int), s));
-  CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
-  reset(a, 1, s);
-  p->launches += 2;
+  if (ffu) {
+    CKI(update_ff(true, s));
+    p->launches += 6;
+  } else {
+    CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
+    reset(a, 1, s);
+    p->launches += 2;
+  }
   CK(cudaGetLastError());
   // The reliable-update test runs at block boundaries.  A multigrid-preconditioned
   // iteration gains about a decade per step, so blocks of 8 would carry the FP32
@@ -929,11 +967,16 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     }
     cudaMemsetAsync(a.pending, 0, sizeof(int), s);
     launch_ru_decide(a, s);
-    // the FP64 reliable update of the instances decide flagged, in the same graph (the
-    // others leave these kernels at once), so the host waits once per block
-    launch_ru_fold(a, s);
-    const rbws_status rr = residual_norms(p, coef64, B, u, r64, rel, upd);
-    reset(a, 0, s);
+    // the reliable update of the instances decide flagged, in the same graph (the others
+    // leave these kernels at once), so the host waits once per block
+    rbws_status rr;
+    if (ffu) {
+      rr = update_ff(false, s);
+    } else {
+      launch_ru_fold(a, s);
+      rr = residual_norms(p, coef64, B, u, r64, rel, upd);
+      reset(a, 0, s);
+    }
     p->launches = launches0;
     ce = cudaStreamEndCapture(s, &graph);
     if (rr != RBWS_OK) {
@@ -983,9 +1026,13 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       }
       cudaMemsetAsync(a.pending, 0, sizeof(int), s);
       launch_ru_decide(a, s);
-      launch_ru_fold(a, s);
-      if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
-      reset(a, 0, s);
+      if (ffu) {
+        if ((rc = update_ff(false, s)) != RBWS_OK) break;
+      } else {
+        launch_ru_fold(a, s);
+        if ((rc = residual_norms(p, coef64, B, u, r64, rel, upd)) != RBWS_OK) break;
+        reset(a, 0, s);
+      }
       if ((ce = cudaEventSynchronize(p->tev[3])) != cudaSuccess) {
         rc = (rbws_status)cuda_fail(ce, "profile events");
         break;
@@ -1008,7 +1055,9 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
       prof->active_dofs += (double)active * (double)p->n;
       prof->samples += 1;
     }
-    p->launches += (2 + mg_launches) * M + 1 + 4;  // + fold, residual, norms, reset
+    // + decide and the update: fold, residual, norms, reset (FP64); or the float-float
+    // update, norms, mark, conversion, FP64 residual and norms (masked), reset
+    p->launches += (2 + mg_launches) * M + 1 + (ffu ? 7 : 4);
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -1032,7 +1081,13 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   for (int b = 0; b < B; b++) nfin += (fin[b] = (h[b].status == ST_MAX_ITERS || h[b].status == ST_BREAKDOWN) ? 2 : 0) != 0;
   if (nfin) {
     CK(cudaMemcpyAsync(upd, fin.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
-    launch_ru_fold(a, s);
+    if (ffu) {
+      launch_ff_fold(a, ff, s);
+      launch_ff_to64(a, ff, upd, s);
+      p->launches += 1;
+    } else {
+      launch_ru_fold(a, s);
+    }
     CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
     std::vector<double> hr(B);
     CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
@@ -1243,6 +1298,10 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
   }
   if (o.precision != RBWS_FP64 && o.precision != RBWS_FP32_IR) {
     set_error("solve: unknown precision");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (o.ru_mode < 0 || o.ru_mode > 2) {
+    set_error("solve: ru_mode must be 0, 1 or 2");
     return RBWS_ERR_INVALID_ARG;
   }
   if (o.wait_cycles < 0) {
@@ -1492,6 +1551,8 @@ void rbws_options_default(rbws_options* o) {
   o->relres_hist = nullptr;
   o->hist_len = 0;
   o->wait_cycles = 0;
+  o->ru_mode = 0;
+  o->reserved = 0;
 }
 
 rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
@@ -1706,6 +1767,65 @@ rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, con
     launch_apply<float>(p->geo, t, c32, B, (const float*)x, p->n, (float*)y, p->cur);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+rbws_status rbws_update_ff(rbws_problem p, const double* mu, int32_t B, const void* u0, const void* d, void* u_out,
+                           void* r_out) {
+  if (!p || !mu || !u0 || !d || !u_out || !r_out || B < 1 || B > 65535) {
+    set_error("rbws_update_ff: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  const Tile t = choose_tile_v4(p->nx, p->ny);
+  if (t.tx == 0) {
+    set_error("rbws_update_ff: needs nx % 4 == 0 (the 4-node tiles)");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  StreamGuard sg(p, nullptr);
+  cudaStream_t s = p->cur;
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_ff"));
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &c64, &c32));
+  int err = 0;
+  const size_t vb = sizeof(float) * (size_t)B * p->n;
+  float* dd = (float*)p->buf("ffu_d", vb, &err);
+  int* upd = err ? nullptr : (int*)p->buf("ffu_upd", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  CGArgs<float> a{};
+  CKI(make_cg_args<float>(p, B, t, c32, dd, &a, "ffu_", 4));
+  a.upd = upd;
+  a.u64 = (double*)u0;
+  FFState ff{};
+  ff.uh = (float*)p->buf("ffu_uh", vb, &err);
+  if (!err) ff.ul = (float*)p->buf("ffu_ul", vb, &err);
+  if (!err) ff.rh = (float*)p->buf("ffu_rh", vb, &err);
+  if (!err) ff.rl = (float*)p->buf("ffu_rl", vb, &err);
+  float* cff = err ? nullptr : (float*)p->buf("ffu_coef", sizeof(float) * 2 * kCoefStride * (size_t)B * p->geo.ncls(), &err);
+  if (!err) ff.part = (double*)p->buf("ffu_part", sizeof(double) * (size_t)B * a.P, &err);
+  int* ones = err ? nullptr : (int*)p->buf("ffu_ones", sizeof(int) * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  ff.coef = cff;
+  ff.f = p->d_f;
+  ff.f_stride = 0;
+  std::vector<int> one(B, 1);
+  CK(cudaMemcpyAsync(upd, one.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ones, one.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  launch_coef_ff(c64, (int64_t)B * p->geo.ncls(), cff, s);
+  launch_ru_ff(a, t, ff, true, s);  // u = u0, r = f - A u0
+  CK(cudaMemcpyAsync(dd, d, vb, cudaMemcpyDeviceToDevice, s));
+  launch_ru_ff(a, t, ff, false, s);  // r -= A d, u += d
+  CGArgs<float> out = a;
+  out.u64 = (double*)u_out;
+  launch_ff_to64(out, ff, ones, s);
+  FFState rv = ff;
+  rv.uh = ff.rh;
+  rv.ul = ff.rl;
+  out.u64 = (double*)r_out;
+  launch_ff_to64(out, rv, ones, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
   return RBWS_OK;
 }
 

@@ -210,6 +210,29 @@ int launch_cg_b_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cuda
 // Autotuning: puts every instance in a runnable state with benign scalars
 // (status ACTIVE, rho = 1, ||r||^2 huge, gamma = 1) so one phase kernel can be timed.
 void launch_tune_prep(const CGArgs<float>& a, cudaStream_t s);
+// Float-float reliable updates (ru_ff.cu): the solution and the tracked true
+// residual as hi + lo float pairs, updated on the FP32 pipe; FP64 only for the
+// convergence check.
+struct FFState {
+  float* uh;           // [B][n] solution, hi parts
+  float* ul;           //        lo parts
+  float* rh;           // [B][n] tracked residual f - A u, hi parts
+  float* rl;           //        lo parts
+  const float* coef;   // [B][ncls][16]: hi parts of the FP64 table values, then lo parts
+  double* part;        // [B][P] partials of ||r||^2 (v4 tiling)
+  double* rel;         // [B] ||r|| / ||f|| from part
+  int* chk;            // [B] 1: the instance takes the FP64 check
+  const double* f;     // right-hand side (nullptr: f = 1); row b at f + b * f_stride
+  int64_t f_stride;
+};
+void launch_coef_ff(const double* coef64, int64_t entries, float* coefff, cudaStream_t s);
+// r -= A d', u += d' for instances with upd[b] != 0 (start: from u0 = a.u64, u = 0, r = f)
+void launch_ru_ff(const CGArgs<float>& a, Tile t, const FFState& ff, bool start, cudaStream_t s);
+void launch_ru_mark(const CGArgs<float>& a, const FFState& ff, cudaStream_t s);
+void launch_ff_to64(const CGArgs<float>& a, const FFState& ff, const int* mask, cudaStream_t s);
+void launch_ff_fold(const CGArgs<float>& a, const FFState& ff, cudaStream_t s);
+void launch_ru_reset_ff(const CGArgs<float>& a, Tile t, const FFState& ff, int start, cudaStream_t s);
+
 // Reliable-update kernels of the FP32 path (see stencil.cu).
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s);
 void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s);

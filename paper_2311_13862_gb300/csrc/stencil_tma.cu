@@ -44,14 +44,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
 // kWaitCycles, so that a CTA returns only once its copies in flight have landed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long budget = kWaitCycles) {
   if (budget <= 0) budget = kWaitCycles;
+  // try_wait may suspend the thread for a while before it returns false, so a
+  // short budget (a test of the timeout path) polls with the non-blocking test_wait
+  const bool poll = budget < 1000000;
   const long long t0 = clock64();
   for (;;) {
     unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
+    if (poll)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
     if (done) return true;
     if (clock64() - t0 > budget) return false;
   }

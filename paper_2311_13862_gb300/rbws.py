@@ -54,7 +54,7 @@ class rbws_options(C.Structure):
                 ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
                 ("check_every", C.c_int32), ("stream", C.c_void_p),
                 ("profile", C.POINTER(rbws_profile)), ("relres_hist", C.c_void_p), ("hist_len", C.c_int32),
-                ("wait_cycles", C.c_int64)]
+                ("wait_cycles", C.c_int64), ("ru_mode", C.c_int32), ("reserved", C.c_int32)]
 
 
 _L = None
@@ -81,6 +81,7 @@ def _lib():
         L.rbws_rb_residuals.argtypes = [P, P, i32, i32, P]
         L.rbws_gaussian_source.argtypes = [P, P, i32, P]
         L.rbws_apply_mg32.argtypes = [P, P, i32, P, P, P]
+        L.rbws_update_ff.argtypes = [P, P, i32, P, P, P, P]
         L.rbws_solve_batch_rhs.argtypes = [P, P, i32, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
         L.rbws_offline_greedy_rhs.argtypes = [P, P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
@@ -182,6 +183,14 @@ def rbws_apply_operator(h, mu, x, y, precision=FP64, stream=None):
     mu = _host(np.atleast_2d(mu))
     _check(_lib().rbws_apply_operator(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), precision, stream),
            "rbws_apply_operator")
+
+
+def rbws_update_ff(h, mu, u0, d, u_out, r_out):
+    """One float-float reliable update from u0 with correction d (test entry point):
+    u_out = u0 + d, r_out = f - A(mu)(u0 + d), both FP64 device tensors [B][n]."""
+    mu = _host(np.atleast_2d(mu))
+    _check(_lib().rbws_update_ff(h, _hp(mu), mu.shape[0], _dp(u0), _dp(d), _dp(u_out), _dp(r_out)),
+           "rbws_update_ff")
 
 
 def rbws_apply_operator_static(h, mu, x, y, precision=FP64, stream=None):
