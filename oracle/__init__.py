@@ -48,6 +48,9 @@ def lib():
         L.orc_csr_nnz.argtypes = [i32] * 3
         L.orc_csr_nnz.restype = i64
         L.orc_assemble_affine.argtypes = [i32, i32, i32, P, i32, P, P, P]
+        L.orc_assemble_ex.argtypes = [i32, i32, i32, P, i32, P, P, P, P, P]
+        L.orc_node_weights.argtypes = [i32, i32, i32, P, P]
+        L.orc_block_map_ex.argtypes = [i32] * 6 + [P, P]
         L.orc_assemble_mu.argtypes = [i32, i32, i32, P, i32, P, P, P, P]
         L.orc_csr_combine.argtypes = [i64, i32, P, P, P]
         L.orc_csr_matvec.argtypes = [i64, P, P, P, P, P]
@@ -81,11 +84,24 @@ class _MSRB(C.Structure):
     _fields_ = [("N", C.c_int), ("n", C.c_int64), ("W", C.c_void_p), ("chol_AN", C.c_void_p)]
 
 
-def block_map(grid, blocks) -> np.ndarray:
+def block_map(grid, blocks, neumann=(0, 0, 0)) -> np.ndarray:
     nx, ny, nz = grid
     m = np.zeros(nx * ny * nz, dtype=np.uint8)
-    lib().orc_block_map(nx, ny, nz, blocks[0], blocks[1], blocks[2], _p(m))
+    if any(neumann):
+        nm = np.ascontiguousarray(neumann, dtype=np.int32)
+        lib().orc_block_map_ex(nx, ny, nz, blocks[0], blocks[1], blocks[2], _p(nm), _p(m))
+    else:
+        lib().orc_block_map(nx, ny, nz, blocks[0], blocks[1], blocks[2], _p(m))
     return m
+
+
+def node_weights(grid, neumann=(0, 0, 0)) -> np.ndarray:
+    """Relative control volume of each node (the source weight in the right-hand side)."""
+    nx, ny, nz = grid
+    w = np.zeros(nx * ny * nz)
+    nm = np.ascontiguousarray(neumann, dtype=np.int32)
+    lib().orc_node_weights(nx, ny, nz, _p(nm), _p(w))
+    return w
 
 
 @dataclasses.dataclass
@@ -135,10 +151,12 @@ class Operator:
         return A
 
 
-def assemble(grid, blocks=None, submap=None, Q=None) -> Operator:
+def assemble(grid, blocks=None, submap=None, Q=None, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)) -> Operator:
+    """Affine terms A_q; kscale: diffusion tensor diagonal; neumann: per axis, 1 for a homogeneous
+    Neumann face at coordinate 1 (orc_assemble_ex)."""
     nx, ny, nz = grid
     if submap is None:
-        submap = block_map(grid, blocks)
+        submap = block_map(grid, blocks, neumann)
         Q = blocks[0] * blocks[1] * blocks[2]
     submap = np.ascontiguousarray(submap, dtype=np.uint8)
     L = lib()
@@ -147,16 +165,25 @@ def assemble(grid, blocks=None, submap=None, Q=None) -> Operator:
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     col = np.zeros(nnz, dtype=np.int32)
     vals = np.zeros((Q, nnz))
-    rc = L.orc_assemble_affine(nx, ny, nz, _p(submap), Q, _p(row_ptr), _p(col), _p(vals))
+    if tuple(kscale) == (1.0, 1.0, 1.0) and not any(neumann):
+        rc = L.orc_assemble_affine(nx, ny, nz, _p(submap), Q, _p(row_ptr), _p(col), _p(vals))
+    else:
+        ks = np.ascontiguousarray(kscale, dtype=np.float64)
+        nm = np.ascontiguousarray(neumann, dtype=np.int32)
+        rc = L.orc_assemble_ex(nx, ny, nz, _p(submap), Q, _p(ks), _p(nm), _p(row_ptr), _p(col), _p(vals))
     if rc != 0:
         raise ValueError("orc_assemble_affine failed: %d" % rc)
     return Operator(tuple(grid), Q, row_ptr, col, vals)
 
 
-def assemble_mu(grid, mu, blocks=None, submap=None, Q=None) -> Operator:
+def assemble_mu(grid, mu, blocks=None, submap=None, Q=None, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)) -> Operator:
     """A(mu) for one parameter, assembled directly (orc_assemble_mu), as a one-term operator:
     its matvec and mg.Hierarchy take the coefficient [1.0].  Holds one value array instead of
-    Q, for grids where Q arrays of the affine terms do not fit in memory."""
+    Q, for grids where Q arrays of the affine terms do not fit in memory.  With an anisotropy
+    or a Neumann face: the affine terms of assemble(), combined."""
+    if tuple(kscale) != (1.0, 1.0, 1.0) or any(neumann):
+        op = assemble(grid, blocks=blocks, submap=submap, Q=Q, kscale=kscale, neumann=neumann)
+        return Operator(tuple(grid), 1, op.row_ptr, op.col, op.values(mu)[None, :])
     nx, ny, nz = grid
     if submap is None:
         submap = block_map(grid, blocks)

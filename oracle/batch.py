@@ -24,22 +24,26 @@ from . import assemble_mu
 _STATE = {}
 
 
-def _init(grid, blocks, submap, Q):
+def _init(grid, blocks, submap, Q, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)):
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     _STATE["grid"], _STATE["blocks"], _STATE["submap"], _STATE["Q"] = grid, blocks, submap, Q
+    _STATE["kscale"], _STATE["neumann"] = tuple(kscale), tuple(neumann)
 
 
 def _solve(task):
     from . import mg
     mu, f, tol = task
-    op = assemble_mu(_STATE["grid"], mu, blocks=_STATE["blocks"], submap=_STATE["submap"], Q=_STATE["Q"])
+    op = assemble_mu(_STATE["grid"], mu, blocks=_STATE["blocks"], submap=_STATE["submap"], Q=_STATE["Q"],
+                     kscale=_STATE["kscale"], neumann=_STATE["neumann"])
     r = mg.mgcg(op, [1.0], f=f, tol=tol, max_iters=400)
     return r.u, r.iters, r.relres, r.status
 
 
-def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol=1e-13, processes=None):
-    """Oracle FP64 MGCG solutions u_b of A(mu_b) u = f_b (f: None = ones, [n] shared, or [B][n]).
+def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol=1e-13, processes=None,
+                        kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)):
+    """Oracle FP64 MGCG solutions u_b of A(mu_b) u = f_b (f: None = ones, [n] shared, or [B][n];
+    kscale, neumann: the operator's anisotropy and Neumann faces, as oracle.assemble takes them).
     Returns (U [B][n], iters [B], relres [B], status [B], seconds, processes)."""
     mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
     B = mus.shape[0]
@@ -57,11 +61,11 @@ def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol
     try:
         tasks = [(mus[b], fb[b], tol) for b in range(B)]
         if processes == 1:
-            _init(tuple(grid), blocks, submap, Q)
+            _init(tuple(grid), blocks, submap, Q, kscale, neumann)
             out = [_solve(t) for t in tasks]
         else:
             with mp.get_context("spawn").Pool(processes, initializer=_init,
-                                              initargs=(tuple(grid), blocks, submap, Q)) as pool:
+                                              initargs=(tuple(grid), blocks, submap, Q, kscale, neumann)) as pool:
                 out = pool.map(_solve, tasks, chunksize=1)
     finally:
         for k, v in saved.items():
@@ -76,12 +80,13 @@ def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol
     return U, its, rel, st, time.perf_counter() - t0, processes
 
 
-def true_relres(grid, mus, U, blocks=None, submap=None, Q=None, f=None) -> np.ndarray:
+def true_relres(grid, mus, U, blocks=None, submap=None, Q=None, f=None, kscale=(1.0, 1.0, 1.0),
+                neumann=(0, 0, 0)) -> np.ndarray:
     """||f_b - A(mu_b) u_b|| / ||f_b|| with the oracle's CSR operator, per instance."""
     mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
     out = np.empty(mus.shape[0])
     for b in range(mus.shape[0]):
-        op = assemble_mu(grid, mus[b], blocks=blocks, submap=submap, Q=Q)
+        op = assemble_mu(grid, mus[b], blocks=blocks, submap=submap, Q=Q, kscale=kscale, neumann=neumann)
         fb = np.ones(op.n) if f is None else (f[b] if np.ndim(f) == 2 else f)
         out[b] = np.linalg.norm(fb - op.matvec([1.0], U[b])) / np.linalg.norm(fb)
     return out
@@ -93,12 +98,13 @@ def relL2(U, U_ref) -> np.ndarray:
     return np.linalg.norm(U - U_ref, axis=1) / np.linalg.norm(U_ref, axis=1)
 
 
-def error_summary(grid, mus, U, U_ref, blocks=None, submap=None, Q=None, f=None) -> dict:
+def error_summary(grid, mus, U, U_ref, blocks=None, submap=None, Q=None, f=None, kscale=(1.0, 1.0, 1.0),
+                  neumann=(0, 0, 0)) -> dict:
     """Per-instance relative L2 error of U against the oracle solutions U_ref and the oracle's
     true relative residual of U; max and mean of each, and the per-instance lists."""
     U = np.asarray(U, dtype=np.float64)
     err = relL2(U, U_ref)
-    res = true_relres(grid, mus, U, blocks=blocks, submap=submap, Q=Q, f=f)
+    res = true_relres(grid, mus, U, blocks=blocks, submap=submap, Q=Q, f=f, kscale=kscale, neumann=neumann)
     return {"n": int(U.shape[0]), "relL2_max": float(err.max()), "relL2_mean": float(err.mean()),
             "true_relres_max": float(res.max()), "true_relres_mean": float(res.mean()),
             "relL2": [float(x) for x in err], "true_relres": [float(x) for x in res]}

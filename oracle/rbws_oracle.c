@@ -34,6 +34,18 @@ void orc_block_map(int nx, int ny, int nz, int bx, int by, int bz, uint8_t* map)
       }
 }
 
+void orc_block_map_ex(int nx, int ny, int nz, int bx, int by, int bz, const int* neumann, uint8_t* map) {
+  for (int k = 1; k <= nz; k++)
+    for (int j = 1; j <= ny; j++)
+      for (int i = 1; i <= nx; i++) {
+        /* node i of an axis sits at i/(n+1), or at i/n on an axis with a Neumann face */
+        const int kx = block_of(i, neumann[0] ? nx - 1 : nx, bx);
+        const int ky = block_of(j, neumann[1] ? ny - 1 : ny, by);
+        const int kz = block_of(k, neumann[2] ? nz - 1 : nz, bz);
+        map[((int64_t)(k - 1) * ny + (j - 1)) * nx + (i - 1)] = (uint8_t)((kz * by + ky) * bx + kx);
+      }
+}
+
 int64_t orc_csr_nnz(int nx, int ny, int nz) {
   int64_t n = (int64_t)nx * ny * nz;
   /* diagonal + one entry per interior-interior face, counted from both ends */
@@ -42,13 +54,24 @@ int64_t orc_csr_nnz(int nx, int ny, int nz) {
   return n + 2 * faces;
 }
 
-int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
-                        int64_t* row_ptr, int32_t* col, double* vals) {
+int orc_assemble_ex(int nx, int ny, int nz, const uint8_t* map, int Q, const double* kscale,
+                    const int* neumann, int64_t* row_ptr, int32_t* col, double* vals) {
+  /* Node-centred finite volumes on the unit cube.  Along axis a with n nodes:
+   * Dirichlet at both ends, h = 1/(n+1), nodes at i*h (i = 1..n); or, with a
+   * homogeneous Neumann face at coordinate 1, h = 1/n and the last node lies on
+   * that face with a half control volume.  The flux through a face is
+   * kf * (u_self - u_nb) / h_a^2 times the face's area relative to a full cell;
+   * kf = kscale[a] * (kappa_self + kappa_nb) / 2, a Dirichlet boundary face taking
+   * kappa_self.  With no Neumann face and kscale = 1 this is the 7-point FD
+   * operator of the Sec. 4 diffusion model. */
+  const int n3[3] = {nx, ny, nz};
   const int64_t n = (int64_t)nx * ny * nz;
   const int64_t nnz = orc_csr_nnz(nx, ny, nz);
-  const double hx2 = 1.0 / ((double)(nx + 1) * (nx + 1));
-  const double hy2 = 1.0 / ((double)(ny + 1) * (ny + 1));
-  const double hz2 = 1.0 / ((double)(nz + 1) * (nz + 1));
+  double inv_h2[3];
+  for (int a = 0; a < 3; a++) {
+    const double cells = neumann[a] ? (double)n3[a] : (double)(n3[a] + 1);
+    inv_h2[a] = 1.0 / ((1.0 / cells) * (1.0 / cells));
+  }
   for (int64_t e = 0; e < n; e++)
     if (map[e] >= Q) return -1;
   memset(vals, 0, sizeof(double) * (size_t)Q * (size_t)nnz);
@@ -59,12 +82,16 @@ int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
       for (int i = 0; i < nx; i++) {
         const int64_t row = ((int64_t)k * ny + j) * nx + i;
         const int q_self = map[row];
+        const int idx[3] = {i, j, k};
+        /* relative width of the control volume along each axis: 1/2 on a Neumann face */
+        double wid[3];
+        for (int a = 0; a < 3; a++) wid[a] = (neumann[a] && idx[a] == n3[a] - 1) ? 0.5 : 1.0;
         row_ptr[row] = pos;
-        /* the six neighbours: (di,dj,dk) and the axis scaling 1/h^2 */
+        /* the six neighbours: (di,dj,dk) and the axis of each */
         const int di[6] = {0, 0, 0, 0, -1, 1};
         const int dj[6] = {0, 0, -1, 1, 0, 0};
         const int dk[6] = {-1, 1, 0, 0, 0, 0};
-        const double sc[6] = {1.0 / hz2, 1.0 / hz2, 1.0 / hy2, 1.0 / hy2, 1.0 / hx2, 1.0 / hx2};
+        const int ax[6] = {2, 2, 1, 1, 0, 0};
         /* Columns in increasing order: z-1, y-1, x-1, self, x+1, y+1, z+1. */
         const int order[7] = {0, 2, 4, -1, 5, 3, 1};
         int64_t diag_pos = -1;
@@ -82,20 +109,23 @@ int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
           col[pos] = (int32_t)(((int64_t)kk * ny + jj) * nx + ii);
           pos++;
         }
-        /* Face coefficients.  Each face contributes kappa_f/h^2 to the
-         * diagonal and -kappa_f/h^2 to the neighbour's column, with
-         * kappa_f = (kappa_self + kappa_nb)/2 and kappa = e_q for term q. */
         int64_t p = row_ptr[row];
         for (int t = 0; t < 7; t++) {
           int f = order[t];
           if (f < 0) { p++; continue; }
+          const int a = ax[f];
           int ii = i + di[f], jj = j + dj[f], kk = k + dk[f];
           int interior = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+          /* past the last node of a Neumann axis there is no face at all */
+          const int step = a == 0 ? di[f] : (a == 1 ? dj[f] : dk[f]);
+          if (!interior && neumann[a] && step > 0) continue;
+          /* area of the face relative to a full cell face: the widths across it */
+          const double area = wid[(a + 1) % 3] * wid[(a + 2) % 3];
           int q_nb = interior ? map[((int64_t)kk * ny + jj) * nx + ii] : q_self;
           for (int q = 0; q < Q; q++) {
             double kap_self = (q == q_self) ? 1.0 : 0.0;
             double kap_nb = (q == q_nb) ? 1.0 : 0.0;
-            double kf = 0.5 * (kap_self + kap_nb) * sc[f];
+            double kf = 0.5 * (kap_self + kap_nb) * kscale[a] * inv_h2[a] * area;
             vals[(int64_t)q * nnz + diag_pos] += kf;
             if (interior) vals[(int64_t)q * nnz + p] -= kf;
           }
@@ -104,6 +134,26 @@ int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
       }
   row_ptr[n] = pos;
   return pos == nnz ? 0 : -2;
+}
+
+void orc_node_weights(int nx, int ny, int nz, const int* neumann, double* w) {
+  /* volume of each node's control volume relative to a full cell */
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        double v = 1.0;
+        if (neumann[0] && i == nx - 1) v *= 0.5;
+        if (neumann[1] && j == ny - 1) v *= 0.5;
+        if (neumann[2] && k == nz - 1) v *= 0.5;
+        w[((int64_t)k * ny + j) * nx + i] = v;
+      }
+}
+
+int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
+                        int64_t* row_ptr, int32_t* col, double* vals) {
+  const double one[3] = {1.0, 1.0, 1.0};
+  const int none[3] = {0, 0, 0};
+  return orc_assemble_ex(nx, ny, nz, map, Q, one, none, row_ptr, col, vals);
 }
 
 int orc_assemble_mu(int nx, int ny, int nz, const uint8_t* map, int Q, const double* mu,

@@ -32,6 +32,9 @@ extern "C" {
  * n interior nodes split into b blocks, node i (1..n) belongs to block
  * min(floor(b*i/(n+1)), b-1).  id = (kz*by + ky)*bx + kx.  map: [nz][ny][nx]. */
 void orc_block_map(int nx, int ny, int nz, int bx, int by, int bz, uint8_t* map);
+/* The same by coordinate on axes with a Neumann face (node i at i/n there):
+ * block min(floor(b*i/n), b-1) on such an axis. */
+void orc_block_map_ex(int nx, int ny, int nz, int bx, int by, int bz, const int* neumann, uint8_t* map);
 
 /* Number of nonzeros of the 7-point pattern on an nx*ny*nz interior grid. */
 int64_t orc_csr_nnz(int nx, int ny, int nz);
@@ -43,6 +46,21 @@ int64_t orc_csr_nnz(int nx, int ny, int nz);
  * Returns 0, or -1 if a map entry is >= Q. */
 int orc_assemble_affine(int nx, int ny, int nz, const uint8_t* map, int Q,
                         int64_t* row_ptr, int32_t* col, double* vals);
+
+/* The general form of orc_assemble_affine: diffusion tensor diag(kscale) times
+ * kappa, and per axis either Dirichlet data at both ends (neumann[a] = 0:
+ * h = 1/(n+1), nodes i*h, i = 1..n) or a homogeneous Neumann face at coordinate
+ * 1 (neumann[a] = 1: h = 1/n, the last node on the face).  Node-centred finite
+ * volumes: a node on a Neumann face has half a control volume, so its face
+ * areas across the other axes and its right-hand side weight are halved (the
+ * rows stay symmetric).  Face coefficient kscale[a] (kappa_i + kappa_j)/2 / h_a^2,
+ * times the face's relative area.  (The mixed boundary value problem of the
+ * paper's Example 2, Sec. 4: K = nu diag(1, 1, 1e-2), Neumann face x = 1.) */
+int orc_assemble_ex(int nx, int ny, int nz, const uint8_t* map, int Q, const double* kscale,
+                    const int* neumann, int64_t* row_ptr, int32_t* col, double* vals);
+/* Relative control volume of each node (1, 1/2 on a Neumann face, 1/4 on an
+ * edge of two): the weight of the source term in the right-hand side. */
+void orc_node_weights(int nx, int ny, int nz, const int* neumann, double* w);
 
 /* CSR of A(mu) for one parameter, assembled directly from kappa = mu[map]
  * (Eq. 1; the same face rule as above, so A(mu) = sum_q mu_q A_q up to

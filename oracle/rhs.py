@@ -36,6 +36,27 @@ def gaussian_source(grid, params) -> np.ndarray:
     return np.array(out)
 
 
+def node_coordinates(grid, neumann=(0, 0, 0)):
+    """Coordinates of the nodes along each axis: i/(n+1), or i/n on an axis with a Neumann face
+    at coordinate 1 (i = 1..n)."""
+    return [np.arange(1, n + 1) / (n if nm else n + 1) for n, nm in zip(grid, neumann)]
+
+
+def example2_source(grid, params, neumann=(1, 0, 0)) -> np.ndarray:
+    """The source of the paper's Example 2 (Sec. 4), f = mu7 + exp(-|x - (mu4, mu5, mu6)|^2 / mu7) / mu7,
+    at the nodes, times each node's relative control volume (the right-hand side of the
+    finite-volume system of orc_assemble_ex); params [B][4] = (mu4, mu5, mu6, mu7)."""
+    from . import node_weights
+    x, y, z = node_coordinates(grid, neumann)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    w = node_weights(grid, neumann)
+    out = []
+    for c4, c5, c6, m7 in np.atleast_2d(params):
+        d2 = (X - c4) ** 2 + (Y - c5) ** 2 + (Z - c6) ** 2
+        out.append((m7 + np.exp(-d2 / m7) / m7).ravel() * w)
+    return np.array(out)
+
+
 def greedy_rhs(op, mu_train, F_train, n_max, snapshot_tol=1e-12) -> Basis:
     """Algorithm 5's loop (Galerkin RB, residual indicator) with right-hand side F_train[t] for
     training parameter t."""
