@@ -96,6 +96,25 @@ typedef enum {
 typedef struct { int32_t nx, ny, nz; } rbws_grid;   /* interior nodes per axis */
 typedef struct { int32_t bx, by, bz; } rbws_blocks; /* block rule, Q = bx*by*bz */
 
+/* Axes of the mixed boundary value problem (the shape of the paper's Example 2,
+ * Sec. 4: diffusion tensor K = kappa diag(1, 1, 1e-2), homogeneous Neumann
+ * face x = 1, homogeneous Dirichlet data elsewhere).  kappa_scale[a]: the
+ * tensor's diagonal entry for axis a (> 0).  neumann_hi[a] = 1: the face at
+ * coordinate 1 of axis a is a homogeneous Neumann face; the axis then has
+ * h = 1/n with nodes at i/n (i = 1..n, the last one on the face) instead of
+ * h = 1/(n+1).  The operator is the node-centred finite-volume form: face
+ * coefficient kappa_scale[a] (kappa_i + kappa_j)/2 / h_a^2 times the face's
+ * area relative to a full cell, where a node on a Neumann face has half a
+ * control volume (its faces across the other axes have half the area), so A
+ * stays symmetric; the matching right-hand side of a source s is s times the
+ * node's relative control volume (1, 1/2 on a Neumann face, 1/4 on an edge of
+ * two).  All ones / zeros: the Sec. 4 model problem of rbws_problem_create. */
+typedef struct {
+  double kappa_scale[3];
+  int32_t neumann_hi[3];
+  int32_t reserved;      /* 0 */
+} rbws_axes;
+
 /* Optional measurement record filled by rbws_solve_batch (options.profile).
  * With profiling on, iterations are launched one by one instead of as a
  * captured CUDA graph, and the first iteration of every block of check_every
@@ -186,6 +205,18 @@ RBWS_API void rbws_options_default(rbws_options* opt);
 RBWS_API rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
                                 const uint8_t* subdomain_map, int32_t Q, const double* f_host,
                                 int device, rbws_problem* out);
+/* rbws_problem_create with the axes of a mixed boundary value problem (see
+ * rbws_axes; NULL = rbws_problem_create).  Blocks follow the block rule by
+ * coordinate: on an axis with a Neumann face node i (at i/n) lies in block
+ * min(floor(b*i/n), b-1).  f_host NULL: a unit source, i.e. the right-hand
+ * side holds each node's relative control volume.  RBWS_ERR_INVALID_ARG for a
+ * kappa_scale that is not positive and finite or a neumann_hi other than 0/1.
+ * The multigrid preconditioner coarsens a Neumann axis like any other (n // 2
+ * nodes at the even fine nodes); with n even its last coarse node lies on the
+ * face. */
+RBWS_API rbws_status rbws_problem_create_ex(const rbws_grid* grid, const rbws_blocks* blocks,
+                                            const uint8_t* subdomain_map, int32_t Q, const double* f_host,
+                                            const rbws_axes* axes, int device, rbws_problem* out);
 RBWS_API void rbws_problem_destroy(rbws_problem p);
 
 /* Problem sizes: n_dof, Q and the current reduced basis dimension N (0 if
@@ -282,8 +313,18 @@ RBWS_API rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, 
  *
  * rbws_gaussian_source: f_out (device [B][n] FP64, caller-owned) = exp(-|x - c_b|^2 /
  * (2 s_b^2)) at the interior nodes x = ((i+1)/(nx+1), (j+1)/(ny+1), (k+1)/(nz+1)), with
- * params (host [B][4]) = (c_x, c_y, c_z, s_b).  RBWS_ERR_INVALID_ARG if s_b <= 0. */
+ * params (host [B][4]) = (c_x, c_y, c_z, s_b).  RBWS_ERR_INVALID_ARG if s_b <= 0.  On a
+ * problem with a Neumann face (rbws_problem_create_ex) the node coordinates and control-volume
+ * weights of rbws_gaussian_source_ex apply. */
 RBWS_API rbws_status rbws_gaussian_source(rbws_problem p, const double* params, int32_t B, void* f_out);
+/* The general form: f_out[b] = (offset + amplitude exp(-|x - c_b|^2 / width))
+ * times each node's relative control volume (rbws_axes), params host [B][6] =
+ * (c_x, c_y, c_z, width, amplitude, offset), node coordinates i/(n+1), or i/n
+ * on an axis with a Neumann face.  The paper's Example 2 source mu7 +
+ * exp(-|x - (mu4, mu5, mu6)|^2 / mu7) / mu7 is (mu4, mu5, mu6, mu7, 1/mu7, mu7).
+ * rbws_gaussian_source is (c, 2 s^2, 1, 0).  RBWS_ERR_INVALID_ARG if a width is
+ * not positive or a parameter not finite. */
+RBWS_API rbws_status rbws_gaussian_source_ex(rbws_problem p, const double* params, int32_t B, void* f_out);
 
 /* rbws_solve_batch with right-hand side f_b (device [B][n] FP64, row b) for instance b
  * instead of the problem's f.  The relative residuals are against ||f_b||.  Warm starts:
@@ -452,9 +493,11 @@ RBWS_API rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* prob
                                          double* latency_ms_out);
 
 /* Checkpoint of the offline stage (the paper's offline/online split): writes
- * the problem description (grid, blocks, f), the reduced basis W, A_N^q, f_N
- * and the surrogate network (if any) to `path` in a versioned binary format
- * with an FNV-1a checksum.  Synchronous; the problem is unchanged. */
+ * the problem description (grid, blocks or map, axes, f), the reduced basis W,
+ * A_N^q, f_N and the surrogate network (if any) to `path` in a versioned
+ * binary format (version 3; rbws_load also reads version 2, written before the
+ * axes existed) with an FNV-1a checksum.  Synchronous; the problem is
+ * unchanged. */
 RBWS_API rbws_status rbws_save(rbws_problem p, const char* path);
 /* Creates a problem on `device` from a checkpoint written by rbws_save.
  * Returns RBWS_ERR_STATE with a message if the file is not a checkpoint, has

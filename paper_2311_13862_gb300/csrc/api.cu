@@ -54,7 +54,9 @@ struct DevBuf {
 };
 
 // Classes of one axis from the segment of every node (seg: [n], values < b).
-AxisClasses make_axis_segments(const std::vector<int>& seg, int b) {
+// Keys (own, lo, hi): lo / hi the neighbour's segment, -1 past a Dirichlet boundary, -2
+// past the last node of an axis whose face at coordinate 1 is a Neumann face.
+AxisClasses make_axis_segments(const std::vector<int>& seg, int b, bool neumann = false) {
   const int n = (int)seg.size();
   AxisClasses a;
   a.n = n;
@@ -63,7 +65,7 @@ AxisClasses make_axis_segments(const std::vector<int>& seg, int b) {
   auto blk = [&](int i) { return seg[i - 1]; };  // i: 1..n
   std::map<std::tuple<int, int, int>, int> ids;
   for (int i = 1; i <= n; i++) {
-    const int own = blk(i), lo = i > 1 ? blk(i - 1) : -1, hi = i < n ? blk(i + 1) : -1;
+    const int own = blk(i), lo = i > 1 ? blk(i - 1) : -1, hi = i < n ? blk(i + 1) : (neumann ? -2 : -1);
     auto key = std::make_tuple(own, lo, hi);
     auto it = ids.find(key);
     int id;
@@ -82,14 +84,16 @@ AxisClasses make_axis_segments(const std::vector<int>& seg, int b) {
 }
 
 // Block rule: along an axis with n nodes and b blocks, node i (1..n) lies in
-// block min(floor(b*i/(n+1)), b-1).
-AxisClasses make_axis(int n, int b) {
+// block min(floor(b*i/(n+1)), b-1); on an axis with a Neumann face (nodes at i/n)
+// in block min(floor(b*i/n), b-1): blocks by coordinate either way.
+AxisClasses make_axis(int n, int b, bool neumann = false) {
   std::vector<int> seg(n);
+  const int64_t cells = neumann ? n : n + 1;
   for (int i = 1; i <= n; i++) {
-    const int k = (int)(((int64_t)b * i) / (n + 1));
+    const int k = (int)(((int64_t)b * i) / cells);
     seg[i - 1] = k < b - 1 ? k : b - 1;
   }
-  return make_axis_segments(seg, b);
+  return make_axis_segments(seg, b, neumann);
 }
 
 // An explicit map [nz][ny][nx] is cut by every grid plane across which it
@@ -136,6 +140,9 @@ std::string map_segments(int nx, int ny, int nz, const uint8_t* map, int Q, std:
 struct rbws_problem_s {
   int device = 0;
   int nx = 0, ny = 0, nz = 0, bx = 1, by = 1, bz = 1, Q = 1;
+  double kscale[3] = {1.0, 1.0, 1.0};  // diagonal of the diffusion tensor
+  int neumann[3] = {0, 0, 0};          // Neumann face at coordinate 1 of each axis
+  bool default_f = false;              // f = the node weights (no f given, a Neumann face)
   int64_t n = 0;
   double sx = 0, sy = 0, sz = 0;
   AxisClasses ax, ay, az;
@@ -1558,11 +1565,25 @@ void rbws_options_default(rbws_options* o) {
 rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
                                 const uint8_t* subdomain_map, int32_t Q, const double* f_host,
                                 int device, rbws_problem* out) {
+  return rbws_problem_create_ex(grid, blocks, subdomain_map, Q, f_host, nullptr, device, out);
+}
+
+rbws_status rbws_problem_create_ex(const rbws_grid* grid, const rbws_blocks* blocks,
+                                   const uint8_t* subdomain_map, int32_t Q, const double* f_host,
+                                   const rbws_axes* axes, int device, rbws_problem* out) {
   if (!out || !grid) {
     set_error("rbws_problem_create: null argument");
     return RBWS_ERR_INVALID_ARG;
   }
   *out = nullptr;
+  rbws_axes ax_def{{1.0, 1.0, 1.0}, {0, 0, 0}, 0};
+  const rbws_axes& axs = axes ? *axes : ax_def;
+  for (int a = 0; a < 3; a++)
+    if (!(axs.kappa_scale[a] > 0.0) || !std::isfinite(axs.kappa_scale[a]) ||
+        (axs.neumann_hi[a] != 0 && axs.neumann_hi[a] != 1)) {
+      set_error("rbws_problem_create: kappa_scale must be positive and neumann_hi 0 or 1");
+      return RBWS_ERR_INVALID_ARG;
+    }
   if ((blocks == nullptr) == (subdomain_map == nullptr)) {
     set_error("rbws_problem_create: give exactly one of blocks / subdomain_map");
     return RBWS_ERR_INVALID_ARG;
@@ -1585,9 +1606,9 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
       set_error("rbws_problem_create: " + why);
       return why.compare(0, 9, "map value") == 0 ? RBWS_ERR_INVALID_ARG : RBWS_ERR_UNSUPPORTED;
     }
-    const int64_t ncls = (int64_t)make_axis_segments(segx, segx.back() + 1).ncls() *
-                         make_axis_segments(segy, segy.back() + 1).ncls() *
-                         make_axis_segments(segz, segz.back() + 1).ncls();
+    const int64_t ncls = (int64_t)make_axis_segments(segx, segx.back() + 1, axs.neumann_hi[0]).ncls() *
+                         make_axis_segments(segy, segy.back() + 1, axs.neumann_hi[1]).ncls() *
+                         make_axis_segments(segz, segz.back() + 1, axs.neumann_hi[2]).ncls();
     if (ncls > kMaxClasses) {
       set_error("rbws_problem_create: the map has " + std::to_string(ncls) + " coefficient classes (at most " +
                 std::to_string(kMaxClasses) + ")");
@@ -1627,17 +1648,26 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   }
   p->Q = Q;
   p->n = (int64_t)p->nx * p->ny * p->nz;
-  p->sx = (double)(p->nx + 1) * (p->nx + 1);
-  p->sy = (double)(p->ny + 1) * (p->ny + 1);
-  p->sz = (double)(p->nz + 1) * (p->nz + 1);
+  for (int a = 0; a < 3; a++) {
+    p->kscale[a] = axs.kappa_scale[a];
+    p->neumann[a] = axs.neumann_hi[a];
+  }
+  // 1/h^2 per axis (h = 1/(n+1), or 1/n with a Neumann face) times the tensor's entry
+  auto inv_h2 = [&](int n, int a) {
+    const double cells = p->neumann[a] ? (double)n : (double)(n + 1);
+    return p->kscale[a] * (cells * cells);
+  };
+  p->sx = inv_h2(p->nx, 0);
+  p->sy = inv_h2(p->ny, 1);
+  p->sz = inv_h2(p->nz, 2);
   if (subdomain_map) {
-    p->ax = make_axis_segments(segx, p->bx);
-    p->ay = make_axis_segments(segy, p->by);
-    p->az = make_axis_segments(segz, p->bz);
+    p->ax = make_axis_segments(segx, p->bx, p->neumann[0]);
+    p->ay = make_axis_segments(segy, p->by, p->neumann[1]);
+    p->az = make_axis_segments(segz, p->bz, p->neumann[2]);
   } else {
-    p->ax = make_axis(p->nx, p->bx);
-    p->ay = make_axis(p->ny, p->by);
-    p->az = make_axis(p->nz, p->bz);
+    p->ax = make_axis(p->nx, p->bx, p->neumann[0]);
+    p->ay = make_axis(p->ny, p->by, p->neumann[1]);
+    p->az = make_axis(p->nz, p->bz, p->neumann[2]);
   }
   auto fail = [&](cudaError_t e, const char* w) {
     cuda_fail(e, w);
@@ -1679,6 +1709,19 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   g.cx = p->d_cls;
   g.cy = p->d_cls + p->nx;
   g.cz = p->d_cls + p->nx + p->ny;
+  std::vector<double> fw;
+  if (!f_host && (p->neumann[0] || p->neumann[1] || p->neumann[2])) {
+    // a unit source: the right-hand side is each node's relative control volume
+    fw.resize(p->n);
+    for (int k = 0; k < p->nz; k++)
+      for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++)
+          fw[((int64_t)k * p->ny + j) * p->nx + i] = (p->neumann[0] && i == p->nx - 1 ? 0.5 : 1.0) *
+                                                     (p->neumann[1] && j == p->ny - 1 ? 0.5 : 1.0) *
+                                                     (p->neumann[2] && k == p->nz - 1 ? 0.5 : 1.0);
+    f_host = fw.data();
+    p->default_f = true;
+  }
   if (f_host) {
     if ((e = cudaMalloc(&p->d_f, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc f");
     cudaMemcpy(p->d_f, f_host, sizeof(double) * p->n, cudaMemcpyHostToDevice);
@@ -2278,26 +2321,47 @@ rbws_status rbws_solve_batch_rhs(rbws_problem p, const double* mu, int32_t B, co
   return warn ? RBWS_WARN_NOT_CONVERGED : RBWS_OK;
 }
 
+rbws_status rbws_gaussian_source_ex(rbws_problem p, const double* params, int32_t B, void* f_out) {
+  if (!p || !params || !f_out || B < 1 || B > 65535) {
+    set_error("rbws_gaussian_source: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  for (int b = 0; b < B; b++) {
+    const double* pr = params + 6 * b;
+    if (!(pr[3] > 0.0) || !std::isfinite(pr[3]) || !std::isfinite(pr[0]) || !std::isfinite(pr[1]) ||
+        !std::isfinite(pr[2]) || !std::isfinite(pr[4]) || !std::isfinite(pr[5])) {
+      set_error("rbws_gaussian_source: the width must be positive and every parameter finite");
+      return RBWS_ERR_INVALID_ARG;
+    }
+  }
+  StreamGuard sg(p, nullptr);
+  int err = 0;
+  double* d_prm = (double*)p->buf("gauss_prm", sizeof(double) * 6 * (size_t)B, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(d_prm, params, sizeof(double) * 6 * B, cudaMemcpyHostToDevice, p->cur));
+  launch_gaussian_source(p->nx, p->ny, p->nz, p->neumann, d_prm, B, (double*)f_out, p->cur);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
 rbws_status rbws_gaussian_source(rbws_problem p, const double* params, int32_t B, void* f_out) {
   if (!p || !params || !f_out || B < 1 || B > 65535) {
     set_error("rbws_gaussian_source: invalid argument");
     return RBWS_ERR_INVALID_ARG;
   }
-  for (int b = 0; b < B; b++)
-    if (!(params[4 * b + 3] > 0.0) || !std::isfinite(params[4 * b]) || !std::isfinite(params[4 * b + 1]) ||
-        !std::isfinite(params[4 * b + 2])) {
+  // exp(-|x - c|^2 / (2 s^2)): width 2 s^2, amplitude 1, offset 0
+  std::vector<double> p6((size_t)B * 6);
+  for (int b = 0; b < B; b++) {
+    const double* pr = params + 4 * b;
+    if (!(pr[3] > 0.0)) {
       set_error("rbws_gaussian_source: the width must be positive and the centre finite");
       return RBWS_ERR_INVALID_ARG;
     }
-  StreamGuard sg(p, nullptr);
-  int err = 0;
-  double* d_prm = (double*)p->buf("gauss_prm", sizeof(double) * 4 * (size_t)B, &err);
-  if (err) return (rbws_status)err;
-  CK(cudaMemcpyAsync(d_prm, params, sizeof(double) * 4 * B, cudaMemcpyHostToDevice, p->cur));
-  launch_gaussian_source(p->nx, p->ny, p->nz, d_prm, B, (double*)f_out, p->cur);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(p->cur));
-  return RBWS_OK;
+    double* q = &p6[(size_t)6 * b];
+    q[0] = pr[0], q[1] = pr[1], q[2] = pr[2], q[3] = 2.0 * pr[3] * pr[3], q[4] = 1.0, q[5] = 0.0;
+  }
+  return rbws_gaussian_source_ex(p, p6.data(), B, f_out);
 }
 
 rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, int32_t n_train, int32_t n_max,
@@ -3104,7 +3168,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   const int N = p->N;
   CkptHeader h{};
   std::memcpy(h.magic, "RBWSPRB1", 8);
-  h.version = 2;
+  h.version = 3;  // 3: the payload starts with the axes (kappa_scale[3], neumann_hi[3], a zero int32)
   h.nx = p->nx;
   h.ny = p->ny;
   h.nz = p->nz;
@@ -3112,7 +3176,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   h.by = p->by;
   h.bz = p->bz;
   h.Q = p->Q;
-  h.has_f = p->d_f != nullptr;
+  h.has_f = p->d_f != nullptr && !p->default_f;
   h.has_map = !p->h_map.empty();
   h.N = N;
   h.net_H = p->d_w32 ? p->net_H : 0;
@@ -3128,7 +3192,8 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
     CK(cudaMemcpy(scale.data(), p->d_cscale, sizeof(float) * scale.size(), cudaMemcpyDeviceToHost));
   }
   const size_t szA = sizeof(double) * (N > 0 ? p->h_ANq.size() : 0), szF = sizeof(double) * (N > 0 ? N : 0);
-  h.payload = p->h_map.size() + sizeof(double) * (f.size() + W.size()) + szA + szF +
+  rbws_axes axes{{p->kscale[0], p->kscale[1], p->kscale[2]}, {p->neumann[0], p->neumann[1], p->neumann[2]}, 0};
+  h.payload = sizeof(axes) + p->h_map.size() + sizeof(double) * (f.size() + W.size()) + szA + szF +
               sizeof(float) * (params.size() + scale.size());
   FILE* fp = std::fopen(path, "wb");
   if (!fp) {
@@ -3142,6 +3207,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
     ok = std::fwrite(d, 1, bytes, fp) == bytes;
     fnv.add(d, bytes);
   };
+  put(&axes, sizeof(axes));
   put(p->h_map.data(), p->h_map.size());
   put(f.data(), sizeof(double) * f.size());
   put(W.data(), sizeof(double) * W.size());
@@ -3178,7 +3244,7 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
     return RBWS_ERR_STATE;
   };
   if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "RBWSPRB1", 8) != 0) return fail("not a checkpoint");
-  if (h.version != 2) return fail("unsupported version");
+  if (h.version != 2 && h.version != 3) return fail("unsupported version");
   if (h.nx < 2 || h.ny < 2 || h.nz < 2 || h.nx > kMaxAxis || h.ny > kMaxAxis || h.nz > kMaxAxis ||
       h.N < 0 || h.N > 160 || h.Q < 1 || h.Q > kMaxQ || (h.has_map != 0 && h.has_map != 1) ||
       (!h.has_map && h.Q != h.bx * h.by * h.bz) || h.net_H < 0 || h.net_H > 4096 ||
@@ -3188,7 +3254,7 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
   const int64_t P = h.net_H ? (int64_t)h.net_H * h.Q + h.net_H + 2 * ((int64_t)h.net_H * h.net_H + h.net_H) +
                                   (int64_t)h.N * h.net_H + h.N
                             : 0;
-  const uint64_t expect = (h.has_map ? (uint64_t)n : 0) +
+  const uint64_t expect = (h.version >= 3 ? sizeof(rbws_axes) : 0) + (h.has_map ? (uint64_t)n : 0) +
                           sizeof(double) * ((h.has_f ? n : 0) + (uint64_t)h.N * n + (uint64_t)h.Q * h.N * h.N + h.N) +
                           sizeof(float) * (P + h.net_N);
   if (h.payload != expect) return fail("payload size does not match the header");
@@ -3202,6 +3268,8 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
     ok = std::fread(d, 1, bytes, fp) == bytes;
     if (ok) fnv.add(d, bytes);
   };
+  rbws_axes axes{{1.0, 1.0, 1.0}, {0, 0, 0}, 0};
+  if (h.version >= 3) get(&axes, sizeof(axes));
   get(map.data(), map.size());
   get(f.data(), sizeof(double) * f.size());
   get(W.data(), sizeof(double) * W.size());
@@ -3219,8 +3287,8 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
   rbws_grid g{h.nx, h.ny, h.nz};
   rbws_blocks bl{h.bx, h.by, h.bz};
   rbws_problem p = nullptr;
-  rbws_status rc = rbws_problem_create(&g, h.has_map ? nullptr : &bl, h.has_map ? map.data() : nullptr, h.Q,
-                                       h.has_f ? f.data() : nullptr, device, &p);
+  rbws_status rc = rbws_problem_create_ex(&g, h.has_map ? nullptr : &bl, h.has_map ? map.data() : nullptr, h.Q,
+                                          h.has_f ? f.data() : nullptr, &axes, device, &p);
   if (rc != RBWS_OK) return rc;
   if (h.N > 0 && (rc = rbws_set_basis(p, h.N, W.data(), ANq.data(), fN.data())) != RBWS_OK) {
     rbws_problem_destroy(p);

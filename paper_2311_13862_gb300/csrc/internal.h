@@ -297,8 +297,11 @@ void launch_row_norms(int64_t n, int B, const double* X, int64_t ldx, double* ou
 int project32_splits(int64_t n, int B);
 int launch_project32(int64_t n, int N, int B, const float* W, const double* F, int64_t ldf, double* part,
                      double* FN, cudaStream_t s);
-// f[b] = the Gaussian source exp(-|x - c_b|^2 / (2 s_b^2)) on the interior nodes, prm device [B][4].
-void launch_gaussian_source(int nx, int ny, int nz, const double* prm, int B, double* f, cudaStream_t s);
+// f[b] = (offset + amplitude exp(-|x - c_b|^2 / width)) times each node's relative control
+// volume, prm device [B][6] = (c_x, c_y, c_z, width, amplitude, offset); neumann (host [3]):
+// the axes with a Neumann face at coordinate 1 (node coordinates i/n there).
+void launch_gaussian_source(int nx, int ny, int nz, const int* neumann, const double* prm, int B, double* f,
+                            cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Learned warm start (mlp.cu)

@@ -94,13 +94,18 @@ std::vector<double> fine_rows_q(const AxisClasses& ax, const AxisClasses& ay, co
             return (segq ? segq[box] : box) == q ? 1.0 : 0.0;
           };
           const double kc = kap(ox, oy, oz);
-          auto face = [&](int nb, double knb, double s) { return nb >= 0 ? 0.5 * (kc + knb) * s : kc * s; };
-          const double kW = face(lx, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx);
-          const double kE = face(hx, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx);
-          const double kS = face(ly, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy);
-          const double kN = face(hy, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy);
-          const double kD = face(lz, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz);
-          const double kU = face(hz, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz);
+          // the face rule of k_coef_tables: mean / Dirichlet boundary (-1) / none past a
+          // Neumann face (-2), areas halved across the axes of a Neumann face
+          auto face = [&](int nb, double knb, double s) {
+            return nb >= 0 ? 0.5 * (kc + knb) * s : (nb == -1 ? kc * s : 0.0);
+          };
+          const double wx = hx == -2 ? 0.5 : 1.0, wy = hy == -2 ? 0.5 : 1.0, wz = hz == -2 ? 0.5 : 1.0;
+          const double kW = face(lx, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx) * (wy * wz);
+          const double kE = face(hx, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx) * (wy * wz);
+          const double kS = face(ly, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy) * (wx * wz);
+          const double kN = face(hy, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy) * (wx * wz);
+          const double kD = face(lz, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz) * (wx * wy);
+          const double kU = face(hz, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz) * (wx * wy);
           double* row = &tq[(((size_t)q * ncz + czi) * ncy + cyi) * ncx * 27 + (size_t)cxi * 27];
           row[off27(0, 0, 0)] = kW + kE + kS + kN + kD + kU;
           row[off27(-1, 0, 0)] = -kW;

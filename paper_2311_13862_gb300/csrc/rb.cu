@@ -208,16 +208,24 @@ __global__ void k_row_norms(int64_t n, const double* __restrict__ X, int64_t ldx
 
 // f[b][node] = exp(-|x(node) - c_b|^2 / (2 s_b^2)) at the interior nodes x = ((i+1) hx,
 // (j+1) hy, (k+1) hz); prm[b] = (c_x, c_y, c_z, s_b).
-__global__ void k_gaussian_source(int nx, int ny, int nz, const double* __restrict__ prm, double* __restrict__ f) {
+// f[b] = (offset + amplitude exp(-|x - c|^2 / width)) times the node's relative control
+// volume; prm [B][6] = (c_x, c_y, c_z, width, amplitude, offset).  Node coordinates along an
+// axis: (i+1)/(n+1), or (i+1)/n on an axis with a Neumann face (nm = 1), where the last
+// node has half a control volume.
+__global__ void k_gaussian_source(int nx, int ny, int nz, int nmx, int nmy, int nmz, const double* __restrict__ prm,
+                                  double* __restrict__ f) {
   const int b = blockIdx.y;
   const int64_t n = (int64_t)nx * ny * nz;
-  const double cx = prm[4 * b], cy = prm[4 * b + 1], cz = prm[4 * b + 2], sg = prm[4 * b + 3];
-  const double hx = 1.0 / (nx + 1), hy = 1.0 / (ny + 1), hz = 1.0 / (nz + 1);
-  const double inv = 1.0 / (2.0 * sg * sg);
+  const double* pr = prm + 6 * b;
+  const double cx = pr[0], cy = pr[1], cz = pr[2], amp = pr[4], off = pr[5];
+  const double hx = 1.0 / (nmx ? nx : nx + 1), hy = 1.0 / (nmy ? ny : ny + 1), hz = 1.0 / (nmz ? nz : nz + 1);
+  const double inv = 1.0 / pr[3];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(t % nx), j = (int)((t / nx) % ny), k = (int)(t / ((int64_t)nx * ny));
     const double dx = (i + 1) * hx - cx, dy = (j + 1) * hy - cy, dz = (k + 1) * hz - cz;
-    f[(int64_t)b * n + t] = exp(-(dx * dx + dy * dy + dz * dz) * inv);
+    const double w = (nmx && i == nx - 1 ? 0.5 : 1.0) * (nmy && j == ny - 1 ? 0.5 : 1.0) *
+                     (nmz && k == nz - 1 ? 0.5 : 1.0);
+    f[(int64_t)b * n + t] = (off + amp * exp(-(dx * dx + dy * dy + dz * dz) * inv)) * w;
   }
 }
 
@@ -409,10 +417,12 @@ int launch_project32(int64_t n, int N, int B, const float* W, const double* F, i
   return 0;
 }
 
-void launch_gaussian_source(int nx, int ny, int nz, const double* prm, int B, double* f, cudaStream_t s) {
+void launch_gaussian_source(int nx, int ny, int nz, const int* neumann, const double* prm, int B, double* f,
+                            cudaStream_t s) {
   const int64_t n = (int64_t)nx * ny * nz;
   const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
-  if (B > 0) k_gaussian_source<<<dim3(blocks, B), 256, 0, s>>>(nx, ny, nz, prm, f);
+  if (B > 0)
+    k_gaussian_source<<<dim3(blocks, B), 256, 0, s>>>(nx, ny, nz, neumann[0], neumann[1], neumann[2], prm, f);
 }
 
 }  // namespace rbws

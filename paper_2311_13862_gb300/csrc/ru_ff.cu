@@ -335,14 +335,18 @@ __global__ void k_ru_mark(CGArgs<float> a, FFState ff) {
   ff.chk[b] = (a.upd[b] != 0 && ff.rel[b] < a.tol) ? 1 : 0;
 }
 
-// u64 = hi + lo for the instances with mask[b] != 0.
-__global__ void k_ff_to64(int64_t n, const float* __restrict__ uh, const float* __restrict__ ul,
+// u64 = hi + lo for the instances with mask[b] != 0.  Usually few instances are
+// masked in, so one grid sweeps the instances (skipping the others) instead of a
+// grid per instance whose CTAs would mostly exit at once.
+__global__ void k_ff_to64(int64_t n, int B, const float* __restrict__ uh, const float* __restrict__ ul,
                           const int* __restrict__ mask, double* __restrict__ u64) {
-  const int b = blockIdx.y;
-  if (!mask[b]) return;
-  const int64_t off = (int64_t)b * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    u64[off + i] = (double)uh[off + i] + (double)ul[off + i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int b = 0; b < B; b++) {
+    if (!mask[b]) continue;
+    const int64_t off = (int64_t)b * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+      u64[off + i] = (double)uh[off + i] + (double)ul[off + i];
+  }
 }
 
 // u <- u + d + alpha p (float-float) and d = 0 for the instances with upd[b] != 0
@@ -486,8 +490,8 @@ void launch_ru_mark(const CGArgs<float>& a, const FFState& ff, cudaStream_t s) {
 }
 
 void launch_ff_to64(const CGArgs<float>& a, const FFState& ff, const int* mask, cudaStream_t s) {
-  const int64_t blocks = std::min<int64_t>((a.g.n + 255) / 256, 152 * 2);
-  k_ff_to64<<<dim3((unsigned)blocks, a.B), 256, 0, s>>>(a.g.n, ff.uh, ff.ul, mask, a.u64);
+  const int64_t blocks = std::min<int64_t>((a.g.n + 255) / 256, 152 * 8);
+  k_ff_to64<<<(unsigned)blocks, 256, 0, s>>>(a.g.n, a.B, ff.uh, ff.ul, mask, a.u64);
 }
 
 void launch_ff_fold(const CGArgs<float>& a, const FFState& ff, cudaStream_t s) {

@@ -218,14 +218,18 @@ __global__ void k_coef_tables(Geo g, const int8_t* __restrict__ kx, const int8_t
     return m[segq ? segq[box] : box];
   };
   const double kc = kap(ox, oy, oz);
-  // face coefficient: arithmetic mean of the two kappas; boundary face: own kappa
-  auto face = [&](int nb_ok, double knb, double s) { return nb_ok ? 0.5 * (kc + knb) * s : kc * s; };
-  const double kW = face(lx >= 0, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx);
-  const double kE = face(hx >= 0, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx);
-  const double kS = face(ly >= 0, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy);
-  const double kN = face(hy >= 0, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy);
-  const double kD = face(lz >= 0, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz);
-  const double kU = face(hz >= 0, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz);
+  // face coefficient: arithmetic mean of the two kappas; Dirichlet boundary face (key -1):
+  // own kappa; no face past a Neumann face (key -2)
+  auto face = [&](int nb, double knb, double s) { return nb >= 0 ? 0.5 * (kc + knb) * s : (nb == -1 ? kc * s : 0.0); };
+  // a node on a Neumann face has half a control volume: its faces across the other axes
+  // have half the area
+  const double wx = hx == -2 ? 0.5 : 1.0, wy = hy == -2 ? 0.5 : 1.0, wz = hz == -2 ? 0.5 : 1.0;
+  const double kW = face(lx, lx >= 0 ? kap(lx, oy, oz) : 0.0, sx) * (wy * wz);
+  const double kE = face(hx, hx >= 0 ? kap(hx, oy, oz) : 0.0, sx) * (wy * wz);
+  const double kS = face(ly, ly >= 0 ? kap(ox, ly, oz) : 0.0, sy) * (wx * wz);
+  const double kN = face(hy, hy >= 0 ? kap(ox, hy, oz) : 0.0, sy) * (wx * wz);
+  const double kD = face(lz, lz >= 0 ? kap(ox, oy, lz) : 0.0, sz) * (wx * wy);
+  const double kU = face(hz, hz >= 0 ? kap(ox, oy, hz) : 0.0, sz) * (wx * wy);
   const double D = kW + kE + kS + kN + kD + kU;
   const double v[kCoefStride] = {-kW, -kE, -kS, -kN, -kD, -kU, D, 1.0 / D};
   double* o64 = coef64 + ((int64_t)b * ncls + e) * kCoefStride;

@@ -49,6 +49,10 @@ class rbws_profile(C.Structure):
                 ("schedule", C.c_int32), ("precond_ms", C.c_double), ("mg_fine_ms", C.c_double * 4)]
 
 
+class rbws_axes(C.Structure):
+    _fields_ = [("kappa_scale", C.c_double * 3), ("neumann_hi", C.c_int32 * 3), ("reserved", C.c_int32)]
+
+
 class rbws_options(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("precond", C.c_int32), ("precision", C.c_int32),
                 ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
@@ -71,6 +75,9 @@ def _lib():
         L.rbws_options_default.argtypes = [C.POINTER(rbws_options)]
         L.rbws_problem_create.argtypes = [C.POINTER(rbws_grid), C.POINTER(rbws_blocks), P, i32, P, C.c_int,
                                           C.POINTER(P)]
+        L.rbws_problem_create_ex.argtypes = [C.POINTER(rbws_grid), C.POINTER(rbws_blocks), P, i32, P,
+                                             C.POINTER(rbws_axes), C.c_int, C.POINTER(P)]
+        L.rbws_gaussian_source_ex.argtypes = [P, P, i32, P]
         L.rbws_problem_destroy.argtypes = [P]
         L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
@@ -141,9 +148,11 @@ def rbws_options_default(**kw) -> rbws_options:
     return o
 
 
-def rbws_problem_create(grid, blocks, Q=None, f=None, device=0, subdomain_map=None):
+def rbws_problem_create(grid, blocks, Q=None, f=None, device=0, subdomain_map=None, kappa_scale=None,
+                        neumann=None):
     """blocks: (bx, by, bz) for the block rule, or None with subdomain_map = a uint8 [nz][ny][nx]
-    array of subdomain ids < Q."""
+    array of subdomain ids < Q.  kappa_scale (diffusion tensor diagonal) and neumann (per axis, 1
+    for a Neumann face at coordinate 1) select rbws_problem_create_ex."""
     g = rbws_grid(*grid)
     if subdomain_map is not None:
         if blocks is not None or Q is None:
@@ -157,8 +166,13 @@ def rbws_problem_create(grid, blocks, Q=None, f=None, device=0, subdomain_map=No
         Q = blocks[0] * blocks[1] * blocks[2] if Q is None else Q
     fh = None if f is None else _host(f)
     h = C.c_void_p()
-    _check(_lib().rbws_problem_create(C.byref(g), bref, mp, Q, _hp(fh), device, C.byref(h)),
-           "rbws_problem_create")
+    if kappa_scale is None and neumann is None:
+        _check(_lib().rbws_problem_create(C.byref(g), bref, mp, Q, _hp(fh), device, C.byref(h)),
+               "rbws_problem_create")
+    else:
+        ax = rbws_axes((C.c_double * 3)(*(kappa_scale or (1.0, 1.0, 1.0))), (C.c_int32 * 3)(*(neumann or (0, 0, 0))), 0)
+        _check(_lib().rbws_problem_create_ex(C.byref(g), bref, mp, Q, _hp(fh), C.byref(ax), device, C.byref(h)),
+               "rbws_problem_create_ex")
     return h
 
 
@@ -244,6 +258,13 @@ def rbws_gaussian_source(h, params, f_out):
     """f_out (CUDA float64 [B][n]) = exp(-|x - c_b|^2 / (2 s_b^2)); params [B][4] = (c_x, c_y, c_z, s_b)."""
     prm = _host(np.atleast_2d(params))
     _check(_lib().rbws_gaussian_source(h, _hp(prm), prm.shape[0], _dp(f_out)), "rbws_gaussian_source")
+
+
+def rbws_gaussian_source_ex(h, params, f_out):
+    """f_out (CUDA float64 [B][n]) = (offset + amplitude exp(-|x - c_b|^2 / width)) times each node's
+    relative control volume; params [B][6] = (c_x, c_y, c_z, width, amplitude, offset)."""
+    prm = _host(np.atleast_2d(params))
+    _check(_lib().rbws_gaussian_source_ex(h, _hp(prm), prm.shape[0], _dp(f_out)), "rbws_gaussian_source_ex")
 
 
 def rbws_solve_batch_rhs(h, mu, f, tol, warm, u_out, options: rbws_options | None = None):
@@ -431,7 +452,8 @@ def rbws_load(path, device=0):
 class Problem:
     """Owning wrapper around an rbws_problem handle."""
 
-    def __init__(self, grid, blocks=None, f=None, device=0, handle=None, subdomain_map=None, Q=None):
+    def __init__(self, grid, blocks=None, f=None, device=0, handle=None, subdomain_map=None, Q=None,
+                 kappa_scale=None, neumann=None):
         self.grid = tuple(grid)
         self.n = grid[0] * grid[1] * grid[2]
         if subdomain_map is not None:
@@ -442,7 +464,7 @@ class Problem:
         if handle is not None:
             self.h = handle
         else:
-            self.h = rbws_problem_create(grid, self.blocks, self.Q, f, device, subdomain_map)
+            self.h = rbws_problem_create(grid, self.blocks, self.Q, f, device, subdomain_map, kappa_scale, neumann)
 
     @classmethod
     def load(cls, path, device=0):
