@@ -578,9 +578,10 @@ def main():
     u = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
     prec = {"fp32ir": rbws.FP32_IR, "fp64": rbws.FP64}
 
-    def run(warm, precision, steps, warmup, profile=False, precond=rbws.PREC_JACOBI):
+    def run(warm, precision, steps, warmup, profile=False, precond=rbws.PREC_JACOBI, persistent=0):
         prof = rbws.rbws_profile()
-        o = rbws.rbws_options_default(precision=precision, stream=stream.cuda_stream, precond=precond)
+        o = rbws.rbws_options_default(precision=precision, stream=stream.cuda_stream, precond=precond,
+                                      persistent=persistent)
         if args.inner_tol > 0:
             o.inner_tol = args.inner_tol
         out = None
@@ -666,7 +667,9 @@ def main():
     J, M, PJ, PG = rbws.PREC_JACOBI, rbws.PREC_MG, rbws.FP32_IR, rbws.FP64
     arm_list = [] if args.arm_steps <= 0 else [
         ("galerkin_fp32ir", rbws.WARM_GALERKIN, PJ, J), ("zero_fp64", rbws.WARM_ZERO, PG, J),
-        ("galerkin_fp64", rbws.WARM_GALERKIN, PG, J), ("zero_fp32ir", rbws.WARM_ZERO, PJ, J)]
+        ("galerkin_fp64", rbws.WARM_GALERKIN, PG, J), ("zero_fp32ir", rbws.WARM_ZERO, PJ, J),
+        # the same FP64 Jacobi-PCG as one persistent cooperative launch per solve
+        ("galerkin_fp64_persistent", rbws.WARM_GALERKIN, PG, J), ("zero_fp64_persistent", rbws.WARM_ZERO, PG, J)]
     learned = None
     if args.arm_steps > 0 and args.mlp_epochs > 0:
         # learned warm start (same 64^3 problem): p -> 256 -> 256 -> 256 -> N network trained on
@@ -705,7 +708,8 @@ def main():
             a_ms, a_it, a_rel, a_st = ms, it, rel, st
             a_err = None
         else:
-            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1, precond=pc)
+            a_ms, a_it, a_rel, a_st, _ = run(warm, pr, args.arm_steps, 1, precond=pc,
+                                             persistent=int(name.endswith("_persistent")))
             # error of this arm's solutions against the oracle's FP64 solutions (every instance)
             a_err = None if U_ref is None else O_batch.relL2(u.cpu().numpy(), U_ref)
         arms[name] = {"solves_per_s": ranks.job_rate(B, world, a_ms), "ms_per_step": a_ms,

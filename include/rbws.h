@@ -180,7 +180,17 @@ typedef struct {
                            its FP64 residual decides (if it fails, the tracked
                            residual is reset from it).  2 falls back to FP64
                            where the 4-node kernels do not apply.             */
-  int32_t reserved;     /* 0 */
+  int32_t persistent;   /* 1: an FP64 solve with the Jacobi preconditioner or none
+                           runs as ONE persistent cooperative kernel: start,
+                           iterations, true-residual checks and restarts, with
+                           the convergence loop on the device (no host polling,
+                           no graph); its grid barriers are bounded by
+                           wait_cycles (RBWS_ERR_DEVICE_TIMEOUT when one runs
+                           out).  rbws_solve_requests then solves the batches of
+                           every grid in that one launch.  0 (default): captured
+                           CUDA graphs of the phase kernels, polled by the host
+                           between blocks of check_every iterations.  Ignored
+                           for other precisions and preconditioners.          */
 } rbws_options;
 
 /* Fills *opt with the defaults listed above (max_iters 20000, Jacobi, FP64,

@@ -703,18 +703,31 @@ rbws_status mg_batch(rbws_problem p, const double* d_mu, int B, const void* coef
   return RBWS_OK;
 }
 
-rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, const rbws_options& o,
-                       double* u, std::vector<InstState>& st) {
+// The FP64 iteration state of one problem's batch, ready for the PCG loop.
+struct Fp64Batch {
+  CGArgs<double> a{};
+  Tile t{0, 0};
+  MGBatch mgb;  // outlives the loop: the launchers read it while capturing
+};
+
+bool persistent_ok(const rbws_options& o) {
+  return o.persistent != 0 && o.precision == RBWS_FP64 && !o.profile &&
+         (o.precond == RBWS_PREC_NONE || o.precond == RBWS_PREC_JACOBI);
+}
+
+rbws_status prepare_fp64(rbws_problem p, const double* d_mu, int B, double tol, const rbws_options& o, double* u,
+                         Fp64Batch* fb, Tile t) {
   double* coef64 = nullptr;
   CKI(coef_tables(p, d_mu, B, &coef64, nullptr));
-  Tile t = choose_tile(p->nx);
-  CGArgs<double> a{};
+  fb->t = t;
+  CGArgs<double>& a = fb->a;
   CKI(make_cg_args<double>(p, B, t, coef64, u, &a, "d_"));
   a.f = p->rhs.f ? p->rhs.f : p->d_f;
   a.f_stride = p->rhs.f ? p->rhs.stride : 0;
   a.tol = tol;
   a.max_iters = o.max_iters;
   a.precond = o.precond;
+  a.wait_cycles = o.wait_cycles;
   if (o.precond == RBWS_PREC_MSRB) {
     if (p->N <= 0) {
       set_error("MSRB preconditioner needs a reduced basis");
@@ -743,10 +756,9 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
         return RBWS_ERR_NOT_SPD;
       }
   }
-  MGBatch mgb;  // outlives run_pcg: the launchers read it while capturing
   if (o.precond == RBWS_PREC_MG) {
-    CKI(mg_batch(p, d_mu, B, coef64, 0, a.st, &mgb));
-    a.mg = &mgb;
+    CKI(mg_batch(p, d_mu, B, coef64, 0, a.st, &fb->mgb));
+    a.mg = &fb->mgb;
   }
   if (p->rhs.f) CK(cudaMemcpyAsync((double*)a.fnorm, p->rhs.norms, sizeof(double) * B, cudaMemcpyDeviceToDevice, p->cur));
   else fill((double*)a.fnorm, B, p->fnorm, p->cur);
@@ -759,7 +771,47 @@ rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, co
     fill(a.hist, (int64_t)B * o.hist_len, std::nan(""), p->cur);
     p->launches += 1;
   }
-  CKI(run_pcg<double>(p, a, t, o.max_restarts, o.check_every, nullptr, true, o.profile));
+  return RBWS_OK;
+}
+
+// One cooperative launch of the persistent FP64 PCG over the prepared batches (one per
+// problem), on the stream s; returns after it completed.
+rbws_status run_persistent(rbws_problem p, const std::vector<CGArgs<double>>& args, Tile t, const rbws_options& o,
+                           cudaStream_t s) {
+  int err = 0;
+  int* ctl = (int*)p->buf("pcg_ctl", sizeof(int) * 4, &err);
+  void* tasks = err ? nullptr : p->buf("pcg_tasks", pcg_persistent_task_bytes() * args.size(), &err);
+  if (err) return (rbws_status)err;
+  int max_it = 0;
+  for (const auto& a : args) max_it = std::max(max_it, a.max_iters);
+  // each round is one iteration or one true-residual check
+  const int rounds = (int)std::min<int64_t>((int64_t)(max_it + 2) * (o.max_restarts + 2), 1 << 30);
+  if (launch_pcg_persistent(args, t, ctl, ctl + 2, o.wait_cycles, o.max_restarts, rounds, tasks, s) < 0) {
+    cudaGetLastError();
+    set_error("persistent PCG: the cooperative launch failed");
+    return RBWS_ERR_CUDA;
+  }
+  p->launches += 1;
+  int terr = 0;
+  CK(cudaMemcpyAsync(&terr, ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (terr) {
+    set_error("persistent PCG: a grid barrier wait ran out of time");
+    return RBWS_ERR_DEVICE_TIMEOUT;
+  }
+  return RBWS_OK;
+}
+
+rbws_status solve_fp64(rbws_problem p, const double* d_mu, int B, double tol, const rbws_options& o,
+                       double* u, std::vector<InstState>& st) {
+  Fp64Batch fb;
+  CKI(prepare_fp64(p, d_mu, B, tol, o, u, &fb, choose_tile(p->nx)));
+  CGArgs<double>& a = fb.a;
+  if (persistent_ok(o)) {
+    CKI(run_persistent(p, {a}, fb.t, o, p->cur));
+  } else {
+    CKI(run_pcg<double>(p, a, fb.t, o.max_restarts, o.check_every, nullptr, true, o.profile));
+  }
   st.resize(B);
   CK(cudaMemcpyAsync(st.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, p->cur));
   if (o.relres_hist)
@@ -1307,6 +1359,10 @@ rbws_status check_solve_options(const rbws_options& o, double tol, int warm) {
     set_error("solve: unknown precision");
     return RBWS_ERR_INVALID_ARG;
   }
+  if (o.persistent != 0 && o.persistent != 1) {
+    set_error("solve: persistent must be 0 or 1");
+    return RBWS_ERR_INVALID_ARG;
+  }
   if (o.ru_mode < 0 || o.ru_mode > 2) {
     set_error("solve: ru_mode must be 0, 1 or 2");
     return RBWS_ERR_INVALID_ARG;
@@ -1356,9 +1412,9 @@ rbws_status l1roc_start(rbws_problem p, const double* d_mu, int B, double* u, bo
   return lift(p, C, B, u, fp32);
 }
 
-rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol, int warm,
-                             const rbws_options& o, double* u, std::vector<InstState>& st) {
-  if (o.profile) std::memset(o.profile, 0, sizeof(rbws_profile));
+// The parameters on the device and the initial value u0 (Algorithm 4, line 2).
+rbws_status warm_start(rbws_problem p, const double* mu, int B, int warm, const rbws_options& o, double* u,
+                       double** d_mu_out) {
   double* d_mu = nullptr;
   CKI(upload_mu(p, mu, B, &d_mu, "mu_solve"));
   if (warm == RBWS_WARM_ZERO) {
@@ -1370,6 +1426,15 @@ rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol
   } else {
     CKI(learned_start(p, d_mu, B, u, warm == RBWS_WARM_LEARNED_CORRECTED, o.precision == RBWS_FP32_IR));
   }
+  *d_mu_out = d_mu;
+  return RBWS_OK;
+}
+
+rbws_status solve_batch_impl(rbws_problem p, const double* mu, int B, double tol, int warm,
+                             const rbws_options& o, double* u, std::vector<InstState>& st) {
+  if (o.profile) std::memset(o.profile, 0, sizeof(rbws_profile));
+  double* d_mu = nullptr;
+  CKI(warm_start(p, mu, B, warm, o, u, &d_mu));
   if (o.precision == RBWS_FP64) {
     CKI(solve_fp64(p, d_mu, B, tol, o, u, st));
   } else {
@@ -1559,7 +1624,7 @@ void rbws_options_default(rbws_options* o) {
   o->hist_len = 0;
   o->wait_cycles = 0;
   o->ru_mode = 0;
-  o->reserved = 0;
+  o->persistent = 0;
 }
 
 rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks,
@@ -3061,6 +3126,51 @@ rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const 
   std::vector<std::string> msg(G);
   std::vector<std::vector<InstState>> st(G);
   std::vector<unsigned long long> t0(G, 0);
+  if (persistent_ok(o)) {
+    // one persistent cooperative launch for the batches of every grid: each problem's
+    // start on its own stream, then the launch on the first problem's stream after them
+    int nxmin = groups[0]->nx;
+    for (size_t g = 1; g < G; g++) nxmin = std::min(nxmin, groups[g]->nx);
+    const Tile t = choose_tile(nxmin);  // one CTA shape for every grid
+    std::vector<Fp64Batch> fbs(G);
+    std::vector<CGArgs<double>> args;
+    std::vector<double*> ubuf(G, nullptr);
+    std::vector<unsigned long long*> stamps(G, nullptr);
+    cudaStream_t s0 = groups[0]->stream;
+    for (size_t g = 0; g < G; g++) {
+      rbws_problem p = groups[g];
+      const std::vector<int>& mem = members[g];
+      const int B = (int)mem.size();
+      StreamGuard sg(p, nullptr);
+      int err = 0;
+      ubuf[g] = (double*)p->buf("req_u", sizeof(double) * (size_t)B * p->n, &err);
+      stamps[g] = err ? nullptr : (unsigned long long*)p->buf("req_t0", 8, &err);
+      if (err) return (rbws_status)err;
+      launch_stamp(stamps[g], p->cur);
+      std::vector<double> hmu((size_t)B * p->Q);
+      for (int k = 0; k < B; k++) std::memcpy(&hmu[(size_t)k * p->Q], mu[mem[k]], sizeof(double) * p->Q);
+      double* d_mu = nullptr;
+      CKI(warm_start(p, hmu.data(), B, warm, o, ubuf[g], &d_mu));
+      CKI(prepare_fp64(p, d_mu, B, tol, o, ubuf[g], &fbs[g], t));
+      args.push_back(fbs[g].a);
+      if (g > 0) {
+        CK(cudaEventRecord(p->ev, p->cur));
+        CK(cudaStreamWaitEvent(s0, p->ev, 0));
+      }
+    }
+    cudaSetDevice(groups[0]->device);
+    CKI(run_persistent(groups[0], args, t, o, s0));
+    for (size_t g = 0; g < G; g++) {
+      rbws_problem p = groups[g];
+      const std::vector<int>& mem = members[g];
+      st[g].resize(mem.size());
+      for (size_t k = 0; k < mem.size(); k++)
+        CK(cudaMemcpyAsync(u_out[mem[k]], ubuf[g] + k * p->n, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, s0));
+      CK(cudaMemcpyAsync(st[g].data(), fbs[g].a.st, sizeof(InstState) * mem.size(), cudaMemcpyDeviceToHost, s0));
+      CK(cudaMemcpyAsync(&t0[g], stamps[g], 8, cudaMemcpyDeviceToHost, s0));
+    }
+    CK(cudaStreamSynchronize(s0));
+  } else {
   auto run_group = [&](size_t g) {
     rbws_problem p = groups[g];
     const std::vector<int>& mem = members[g];
@@ -3103,6 +3213,7 @@ rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const 
       set_error(msg[g]);
       return (rbws_status)rc[g];
     }
+  }
   unsigned long long start = t0[0];
   for (size_t g = 1; g < G; g++) start = std::min(start, t0[g]);
   int warn = 0;

@@ -238,6 +238,15 @@ void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s);
 void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s);
 void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s);
 
+// Persistent FP64 PCG (preconditioner none or Jacobi) of one or several problems in one
+// cooperative launch: start, iterations and true-residual checks with restarts, until no
+// instance is active.  bar (device int[2]) and err (device int) are the grid barrier and its
+// timeout flag; d_tasks: device scratch of args.size() * pcg_persistent_task_bytes().
+// Returns the grid size, or -1 if the launch could not be made.
+int launch_pcg_persistent(const std::vector<CGArgs<double>>& args, Tile t, int* bar, int* err,
+                          long long wait_cycles, int max_restarts, int max_rounds, void* d_tasks, cudaStream_t s);
+size_t pcg_persistent_task_bytes();
+
 template <typename T>
 void launch_cg_init(const CGArgs<T>& a, Tile t, int parity, int only_status, cudaStream_t s);
 template <typename T>

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.h"
 
@@ -185,6 +186,23 @@ struct TilePos {
   int x0, y0, z0, z1, part;
 };
 
+// The block a kernel body works on: blockIdx and gridDim.x of an ordinary launch, or a
+// work item of the persistent iteration kernel.
+struct VBlk {
+  int x, y, z, gx;
+  __device__ __forceinline__ static VBlk here() { return VBlk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x}; }
+};
+
+__device__ __forceinline__ TilePos tile_pos_v(const Geo& g, int tiles_x, int zc, const VBlk& v) {
+  TilePos t;
+  t.x0 = (v.x % tiles_x) * blockDim.x;
+  t.y0 = (v.x / tiles_x) * blockDim.y;
+  t.z0 = v.y * zc;
+  t.z1 = min(g.nz, t.z0 + zc);
+  t.part = v.y * v.gx + v.x;
+  return t;
+}
+
 __device__ __forceinline__ TilePos tile_pos(const Geo& g, int tiles_x, int zc) {
   TilePos t;
   const int tile = blockIdx.x;
@@ -297,12 +315,12 @@ __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restric
 // pbuf[parity^1]; rho/rr partials ping-pong the same way.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_cg_init(CGArgs<T> a, int parity) {
+__device__ __forceinline__ void cg_init_body(const CGArgs<T>& a, int parity, const VBlk& v) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int b = blockIdx.z;
-  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const int b = v.z;
+  const TilePos tp = tile_pos_v(a.g, a.tiles_x, a.zc, v);
   const int64_t off = (int64_t)b * a.g.n;
   const T* cb = a.coef + (int64_t)b * a.g.ncls() * kCoefStride;
   T* pold = (parity ? a.p1 : a.p0) + off;
@@ -363,9 +381,14 @@ __global__ void k_cg_init(CGArgs<T> a, int parity) {
 }
 
 template <typename T>
-__global__ void k_cg_finalize(CGArgs<T> a, int parity, int mode, int max_restarts) {
-  const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__global__ void k_cg_init(CGArgs<T> a, int parity) {
+  cg_init_body<T>(a, parity, VBlk::here());
+}
+
+// Called by a full warp (lane 0..31) for instance b.
+template <typename T>
+__device__ __forceinline__ void cg_finalize_body(const CGArgs<T>& a, int parity, int mode, int max_restarts, int b,
+                                                 int lane) {
   if (b >= a.B) return;
   const double2 v = sum_partials2(a.rho_rr + ((int64_t)parity * a.B + b) * a.P, a.P, lane);
   if (lane != 0) return;
@@ -404,15 +427,21 @@ __global__ void k_cg_finalize(CGArgs<T> a, int parity, int mode, int max_restart
 }
 
 template <typename T>
-__global__ void k_cg_a(CGArgs<T> a, int parity) {
+__global__ void k_cg_finalize(CGArgs<T> a, int parity, int mode, int max_restarts) {
+  cg_finalize_body<T>(a, parity, mode, max_restarts, (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)),
+                      (int)(threadIdx.x & 31));
+}
+
+template <typename T>
+__device__ __forceinline__ void cg_a_body(const CGArgs<T>& a, int parity, const VBlk& v) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[64];
   __shared__ double s_beta;
   __shared__ int s_run;
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int b = blockIdx.z;
+  const int b = v.z;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const TilePos tp = tile_pos_v(a.g, a.tiles_x, a.zc, v);
   const bool leader = tp.part == 0;
   if (tid < 32) {
     InstState* st = a.st + b;
@@ -475,13 +504,18 @@ __global__ void k_cg_a(CGArgs<T> a, int parity) {
 }
 
 template <typename T>
-__global__ void k_cg_b(CGArgs<T> a, int parity) {
+__global__ void k_cg_a(CGArgs<T> a, int parity) {
+  cg_a_body<T>(a, parity, VBlk::here());
+}
+
+template <typename T>
+__device__ __forceinline__ void cg_b_body(const CGArgs<T>& a, int parity, const VBlk& v) {
   __shared__ double red[64];
   __shared__ double s_alpha;
   __shared__ int s_run;
-  const int b = blockIdx.z;
+  const int b = v.z;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const TilePos tp = tile_pos(a.g, a.tiles_x, a.zc);
+  const TilePos tp = tile_pos_v(a.g, a.tiles_x, a.zc, v);
   const bool leader = tp.part == 0;
   if (tid < 32) {
     InstState* st = a.st + b;
@@ -556,6 +590,11 @@ __global__ void k_cg_b(CGArgs<T> a, int parity) {
   block_sum2(drho, drr, red);
   if (tid == 0)
     a.rho_rr[((int64_t)(parity ^ 1) * a.B + b) * a.P + tp.part] = make_double2(drho, drr);
+}
+
+template <typename T>
+__global__ void k_cg_b(CGArgs<T> a, int parity) {
+  cg_b_body<T>(a, parity, VBlk::here());
 }
 
 // ---------------------------------------------------------------------------
@@ -850,6 +889,135 @@ __global__ void k_ru_reset(CGArgs<float> a, int start) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent FP64 PCG: Algorithm 1 (preconditioner none or Jacobi) with the
+// true-residual check and restarts of Algorithm 4, for one or several problems
+// (grids of different sizes) in one cooperative launch.  Each CTA takes work items
+// (tile, z-chunk, instance) of every task with a grid stride; the phases are the
+// bodies of k_cg_init / k_cg_finalize / k_cg_a / k_cg_b, separated by grid
+// barriers; the loop ends on the device when no instance of any task is active.
+// Every barrier wait is bounded: when it runs out the CTA sets *err and every CTA
+// leaves at its next barrier.
+// ---------------------------------------------------------------------------
+struct PTask {
+  CGArgs<double> a;
+  int ntiles;  // tiles_x * tiles_y
+  int items;   // ntiles * nzc * B: work items of a stencil or update phase
+};
+
+struct PCtl {
+  int* bar;               // [2]: arrivals, generation
+  int* err;               // a barrier wait ran out
+  long long wait_cycles;  // bound of each barrier wait (clock64 cycles)
+  int max_restarts;
+  int max_rounds;         // cap on iterations plus checks (a safety net)
+};
+
+__device__ bool grid_sync(const PCtl& c) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile int* vgen = c.bar + 1;
+    const int gen = *vgen;  // read before arriving: the last arrival bumps it
+    __threadfence();
+    const int nb = (int)(gridDim.x * gridDim.y * gridDim.z);
+    int ok = 1;
+    if (atomicAdd(c.bar, 1) == nb - 1) {
+      atomicExch(c.bar, 0);
+      __threadfence();
+      atomicAdd(c.bar + 1, 1);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (clock64() - t0 > c.wait_cycles) {
+          ok = 0;
+          atomicExch(c.err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();  // the other CTAs' writes of the phase are visible from here on
+    s_ok = ok && *reinterpret_cast<volatile int*>(c.err) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_pcg_persistent(const PTask* __restrict__ tasks, int ntasks, PCtl c) {
+  int total = 0, total_fin = 0;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int warps = (blockDim.x * blockDim.y) >> 5;
+  for (int t = 0; t < ntasks; t++) {
+    total += tasks[t].items;
+    total_fin += (tasks[t].a.B + warps - 1) / warps;
+  }
+  // item -> (task, virtual block)
+  auto locate = [&](int item, int& t, VBlk& v) {
+    t = 0;
+    while (item >= tasks[t].items) item -= tasks[t++].items;
+    const PTask& k = tasks[t];
+    const int nzc = k.a.nzc;
+    v.x = item % k.ntiles;
+    v.y = (item / k.ntiles) % nzc;
+    v.z = item / (k.ntiles * nzc);
+    v.gx = k.ntiles;
+  };
+  auto init = [&]() {
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      int t;
+      VBlk v;
+      locate(item, t, v);
+      __syncthreads();
+      cg_init_body<double>(tasks[t].a, 0, v);
+    }
+  };
+  auto finalize = [&](int mode) {
+    for (int item = blockIdx.x; item < total_fin; item += gridDim.x) {
+      int t = 0, rest = item;
+      while (rest >= (tasks[t].a.B + warps - 1) / warps) rest -= (tasks[t++].a.B + warps - 1) / warps;
+      cg_finalize_body<double>(tasks[t].a, 0, mode, c.max_restarts, rest * warps + (tid >> 5), tid & 31);
+    }
+  };
+  auto active = [&]() {
+    int n = 0;
+    for (int t = 0; t < ntasks; t++) n += *reinterpret_cast<volatile int*>(tasks[t].a.active);
+    return n;
+  };
+  init();
+  if (!grid_sync(c)) return;
+  finalize(0);
+  if (!grid_sync(c)) return;
+  int parity = 0;
+  for (int round = 0; round < c.max_rounds; round++) {
+    if (active() == 0) {
+      // every instance stopped: check the true residual f - A u, restart the failures
+      init();
+      if (!grid_sync(c)) return;
+      finalize(1);
+      if (!grid_sync(c)) return;
+      if (active() == 0) return;
+      parity = 0;
+    }
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      int t;
+      VBlk v;
+      locate(item, t, v);
+      __syncthreads();
+      cg_a_body<double>(tasks[t].a, parity, v);
+    }
+    if (!grid_sync(c)) return;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+      int t;
+      VBlk v;
+      locate(item, t, v);
+      __syncthreads();
+      cg_b_body<double>(tasks[t].a, parity, v);
+    }
+    if (!grid_sync(c)) return;
+    parity ^= 1;
+  }
+}
+
 inline size_t plane_smem(Tile t, size_t elem) { return 3 * (size_t)(t.tx + 2) * (t.ty + 2) * elem; }
 
 template <typename T>
@@ -915,6 +1083,40 @@ void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restar
   const int warps = 4;
   k_cg_finalize<T><<<(a.B + warps - 1) / warps, 32 * warps, 0, s>>>(a, parity, mode, max_restarts);
 }
+
+int launch_pcg_persistent(const std::vector<CGArgs<double>>& args, Tile t, int* bar, int* err,
+                          long long wait_cycles, int max_restarts, int max_rounds, void* d_tasks, cudaStream_t s) {
+  const int ntasks = (int)args.size();
+  std::vector<PTask> h(ntasks);
+  int total = 0;
+  for (int i = 0; i < ntasks; i++) {
+    h[i].a = args[i];
+    h[i].ntiles = args[i].tiles_x * args[i].tiles_y;
+    h[i].items = h[i].ntiles * args[i].nzc * args[i].B;
+    total += h[i].items;
+  }
+  if (cudaMemcpyAsync(d_tasks, h.data(), sizeof(PTask) * ntasks, cudaMemcpyHostToDevice, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(bar, 0, 2 * sizeof(int), s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return -1;
+  const size_t smem = plane_smem(t, sizeof(double));
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, t.tx * t.ty, smem) != cudaSuccess ||
+      per_sm < 1)
+    return -1;
+  // every CTA must be resident at once (the grid barriers): at most the occupancy limit
+  const int grid = std::max(1, std::min(total, sms * per_sm));
+  PTask* tp = static_cast<PTask*>(d_tasks);
+  PCtl c{bar, err, wait_cycles > 0 ? wait_cycles : 4000000000LL, max_restarts, max_rounds};
+  void* params[] = {&tp, (void*)&ntasks, &c};
+  if (cudaLaunchCooperativeKernel((const void*)k_pcg_persistent, dim3(grid), dim3(t.tx, t.ty), params, smem, s) !=
+      cudaSuccess)
+    return -1;
+  return grid;
+}
+
+size_t pcg_persistent_task_bytes() { return sizeof(PTask); }
 
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s) {
   k_ru_decide<<<(a.B + 3) / 4, 128, 0, s>>>(a);

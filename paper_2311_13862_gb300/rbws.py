@@ -58,7 +58,7 @@ class rbws_options(C.Structure):
                 ("max_restarts", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
                 ("check_every", C.c_int32), ("stream", C.c_void_p),
                 ("profile", C.POINTER(rbws_profile)), ("relres_hist", C.c_void_p), ("hist_len", C.c_int32),
-                ("wait_cycles", C.c_int64), ("ru_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("wait_cycles", C.c_int64), ("ru_mode", C.c_int32), ("persistent", C.c_int32)]
 
 
 _L = None

@@ -78,7 +78,7 @@ def test_options_default_sets_every_field(lib_path):
     assert o.max_iters == 20000 and o.precond == rbws.PREC_JACOBI and o.precision == rbws.FP64
     assert o.max_restarts == 3 and o.inner_tol == 0.0 and o.max_outer == 10 and o.check_every == 0
     assert o.stream is None and not o.profile and o.relres_hist is None and o.hist_len == 0
-    assert o.wait_cycles == 0 and o.ru_mode == 0 and o.reserved == 0
+    assert o.wait_cycles == 0 and o.ru_mode == 0 and o.persistent == 0
 
 
 def _ckpt_bytes(nx=4, ny=3, nz=2, blocks=(2, 1, 1), N=2, checksum_ok=True, submap=None, Q=None):
