@@ -74,10 +74,12 @@ def test_one_launch_for_uneven_grids_matches_the_oracle():
                                                             rbws.rbws_options_default(persistent=pers))
             assert rc == 0 and np.all(st == 0) and np.all(lat > 0)
             res[pers] = (it, [o.cpu().numpy() for o in outs])
-        assert np.array_equal(res[0][0], res[1][0])
+        # one launch takes one CTA shape for every grid (that of the smallest), so its partial
+        # sums are grouped differently from the per-grid launches: equal to rounding, not bitwise
+        assert np.all(np.abs(res[0][0] - res[1][0]) <= 1)
         for r, k in enumerate(which):
             u = res[1][1][r]
-            assert np.array_equal(u, res[0][1][r])
+            assert np.linalg.norm(u - res[0][1][r]) <= 1e-11 * np.linalg.norm(u)
             ref = O.pcg(ops[k], mus[r], tol=1e-13)
             assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
             assert abs(int(res[1][0][r]) - ref.iters) <= 2
