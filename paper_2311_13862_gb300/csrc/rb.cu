@@ -312,6 +312,143 @@ __global__ void __launch_bounds__(256) k_project32(int64_t n, int N, int B, cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same projection on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
+// accumulation), for N <= 48 (its staging ring is static shared memory, 48 KB at most).  part[s][j][b] = sum over split s of W[j][i] F[b][i]:
+// an M x Nb x K product with M = N (padded to 16 MT rows), Nb = 64 instances per CTA
+// (8 per warp) and K = the split's nodes.  Each operand is split into a TF32 high part
+// and the TF32 rounding of the rest, and the product keeps hi*hi + hi*lo + lo*hi (three
+// MMAs), which carries about 21 significant bits: the accuracy of FP32 products.  The
+// sources arrive in FP64 and are rounded to FP32 with integer operations (the FP64 pipe
+// is slow on this part).  FP32 sums over runs of 128 nodes, FP64 across runs, as in
+// k_project32.  Tiles of 32 nodes are staged by cp.async into a two-stage ring.
+// ---------------------------------------------------------------------------
+constexpr int kPtcK = 32;      // nodes per staged tile
+constexpr int kPtcInst = 64;   // instances per CTA
+constexpr int kPtcFp = kPtcK + 2;   // pitch (doubles) of a staged source row
+constexpr int kPtcWp = kPtcK + 4;   // pitch (floats) of a staged W row
+
+__device__ __forceinline__ float f64_to_f32_int(double x) {
+  // round toward zero to FP32 with integer operations; zero below the normal range
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(bits >> 32), lw = (unsigned)bits;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return 0.f;
+  if (e >= 255) return __uint_as_float((hw & 0x80000000u) | 0x7f800000u);
+  return __uint_as_float((hw & 0x80000000u) | ((unsigned)e << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+}
+
+__device__ __forceinline__ void tf32_split(float a, unsigned& hi, unsigned& lo) {
+  const unsigned h = __float_as_uint(a) & 0xffffe000u;  // the 10 mantissa bits the MMA reads
+  hi = h;
+  lo = __float_as_uint(a - __uint_as_float(h)) & 0xffffe000u;
+}
+
+__device__ __forceinline__ void mma_tf32(float c[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+template <int MT>
+__global__ void __launch_bounds__(256) k_project_tc(int64_t n, int N, int B, const float* __restrict__ W,
+                                                   const double* __restrict__ F, int64_t ldf, int64_t per_split,
+                                                   double* __restrict__ part) {
+  __shared__ __align__(16) double Fs[2][kPtcInst][kPtcFp];
+  __shared__ __align__(16) float Ws[2][MT * 16][kPtcWp];
+  const int sp = blockIdx.x, b0 = blockIdx.y * kPtcInst;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tig = lane & 3;
+  const int64_t lo = (int64_t)sp * per_split, hi = min(n, lo + per_split);
+  const int ntile = (int)((hi - lo + kPtcK - 1) / kPtcK);
+  // stage tile t (nodes lo + t*32 ..): sources of 64 instances (16-byte chunks of two
+  // doubles) and W rows (chunks of four floats); past the end of the split, or of B / N,
+  // the chunk is zero-filled
+  auto stage = [&](int t, int buf) {
+    const int64_t i0 = lo + (int64_t)t * kPtcK;
+    for (int c = tid; c < kPtcInst * (kPtcK / 2); c += 256) {
+      const int r = c / (kPtcK / 2), col = 2 * (c % (kPtcK / 2));
+      const int bb = b0 + r;
+      const int64_t i = i0 + col;
+      int bytes = 0;
+      if (bb < B && i < hi) bytes = i + 1 < hi ? 16 : 8;
+      const double* src = bytes ? F + (int64_t)bb * ldf + i : F;
+      cp_async16(&Fs[buf][r][col], src, bytes);
+    }
+    for (int c = tid; c < MT * 16 * (kPtcK / 4); c += 256) {
+      const int j = c / (kPtcK / 4), col = 4 * (c % (kPtcK / 4));
+      const int64_t i = i0 + col;
+      int bytes = 0;
+      if (j < N && i < hi) bytes = (int)min((int64_t)16, (hi - i) * 4);
+      const float* src = bytes ? W + (int64_t)j * n + i : W;
+      cp_async16(&Ws[buf][j][col], src, bytes);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  float c[MT][4];
+  double acc[MT][4];
+#pragma unroll
+  for (int m = 0; m < MT; m++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) c[m][q] = 0.f, acc[m][q] = 0.0;
+  if (ntile > 0) stage(0, 0);
+  for (int t = 0; t < ntile; t++) {
+    const int buf = t & 1;
+    if (t + 1 < ntile) {
+      stage(t + 1, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kPtcK / 8; ks++) {
+      const int k0 = ks * 8;
+      // B fragment (8 x 8, column major): B[k][nn] = F[b0 + 8 warp + nn][k0 + k]
+      unsigned bh[2], bl[2];
+      tf32_split(f64_to_f32_int(Fs[buf][8 * warp + g][k0 + tig]), bh[0], bl[0]);
+      tf32_split(f64_to_f32_int(Fs[buf][8 * warp + g][k0 + tig + 4]), bh[1], bl[1]);
+#pragma unroll
+      for (int m = 0; m < MT; m++) {
+        // A fragment (16 x 8, row major): A[r][k] = W[16 m + r][k0 + k]
+        unsigned ah[4], al[4];
+        tf32_split(Ws[buf][16 * m + g][k0 + tig], ah[0], al[0]);
+        tf32_split(Ws[buf][16 * m + g + 8][k0 + tig], ah[1], al[1]);
+        tf32_split(Ws[buf][16 * m + g][k0 + tig + 4], ah[2], al[2]);
+        tf32_split(Ws[buf][16 * m + g + 8][k0 + tig + 4], ah[3], al[3]);
+        mma_tf32(c[m], al, bh);
+        mma_tf32(c[m], ah, bl);
+        mma_tf32(c[m], ah, bh);
+      }
+    }
+    // FP32 runs of 128 nodes (4 tiles), FP64 across runs
+    if ((t & 3) == 3 || t + 1 == ntile) {
+#pragma unroll
+      for (int m = 0; m < MT; m++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[m][q] += (double)c[m][q], c[m][q] = 0.f;
+    }
+    __syncthreads();  // the buffer is refilled by the next iteration's stage
+  }
+  // D fragment: (row g, cols 2 tig, 2 tig + 1) and (row g + 8, same cols)
+#pragma unroll
+  for (int m = 0; m < MT; m++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int j = 16 * m + g + (q >= 2 ? 8 : 0);
+      const int bb = b0 + 8 * warp + 2 * tig + (q & 1);
+      if (j < N && bb < B) part[((int64_t)sp * N + j) * B + bb] = acc[m][q];
+    }
+}
+
 // FN[j * B + b] = sum over the S splits, in split order.
 __global__ void k_project_reduce(int S, int N, int B, const double* __restrict__ part, double* __restrict__ FN) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -394,6 +531,22 @@ int project32_splits(int64_t n, int B) {
 int launch_project32(int64_t n, int N, int B, const float* W, const double* F, int64_t ldf, double* part,
                      double* FN, cudaStream_t s) {
   if (N < 1 || N > 160 || B < 1) return -1;
+  // the tensor-core kernel needs 16-byte aligned rows for its cp.async chunks
+  const bool tc = N <= 48 && n % 4 == 0 && ldf % 2 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+  if (tc) {
+    const int S = project32_splits(n, B);
+    int64_t per = (n + S - 1) / S;
+    per = (per + kPtcK - 1) / kPtcK * kPtcK;
+    const int Sused = (int)((n + per - 1) / per);
+    const dim3 grid((unsigned)Sused, (unsigned)((B + kPtcInst - 1) / kPtcInst));
+    const int MT = (N + 15) / 16;
+    if (MT == 1) k_project_tc<1><<<grid, 256, 0, s>>>(n, N, B, W, F, ldf, per, part);
+    else if (MT == 2) k_project_tc<2><<<grid, 256, 0, s>>>(n, N, B, W, F, ldf, per, part);
+    else k_project_tc<3><<<grid, 256, 0, s>>>(n, N, B, W, F, ldf, per, part);
+    k_project_reduce<<<(N * B + 255) / 256, 256, 0, s>>>(Sused, N, B, part, FN);
+    return 0;
+  }
   const int S = project32_splits(n, B);
   int64_t per = (n + S - 1) / S;
   per = (per + kProjRun - 1) / kProjRun * kProjRun;

@@ -80,9 +80,9 @@ def test_one_launch_for_uneven_grids_matches_the_oracle():
         for r, k in enumerate(which):
             u = res[1][1][r]
             assert np.linalg.norm(u - res[0][1][r]) <= 1e-11 * np.linalg.norm(u)
-            ref = O.pcg(ops[k], mus[r], tol=1e-13)
-            assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+            ref = O.pcg(ops[k], mus[r], tol=1e-12)  # the same tolerance: iterations within 2
             assert abs(int(res[1][0][r]) - ref.iters) <= 2
+            assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
     finally:
         for P in probs:
             P.close()
