@@ -581,15 +581,11 @@ __global__ void __launch_bounds__(256, 3)
   const int i = x0 + lx, j = y0 + ly;
   const bool own = i < g.nx && j < g.ny;
   const int xo = (ly + 1) * PW + 4 + lx, ro = ly * RP + lx;
-  // the extra duties go to the first lanes of every warp (duty index lane * warps + warp),
-  // not to the first warps, so that no warp carries twice the work to each plane barrier
-  const int nthr = TXT * TY;
-  const int dix = (nthr & 31) == 0 ? (tid & 31) * (nthr >> 5) + (tid >> 5) : tid;
-  const int ex_kind = dix < TXT ? 1 : (dix < TXT + TY + 1 ? 2 : 0);
-  const int exl = ex_kind == 1 ? 4 * dix : TXN, eyl = ex_kind == 1 ? TY : dix - TXT;
+  const int ex_kind = tid < TXT ? 1 : (tid < TXT + TY + 1 ? 2 : 0);
+  const int exl = ex_kind == 1 ? 4 * tid : TXN, eyl = ex_kind == 1 ? TY : tid - TXT;
   const int exi = x0 + exl, exj = y0 + eyl;
   const bool ex_in = ex_kind != 0 && exi < g.nx && exj < g.ny;
-  float* exc = exc_all + (ex_kind == 1 ? 4 * dix : TXN + eyl) * 8;
+  float* exc = exc_all + (ex_kind == 1 ? 4 * tid : TXN + eyl) * 8;
   const int Il = tid % (2 * TXT), Jl = tid / (2 * TXT);
   const int I = x0 / 2 + Il, J = y0 / 2 + Jl;
   const bool cown = I < m.cnx && J < m.cny;
@@ -793,16 +789,13 @@ __global__ void __launch_bounds__(256, 3)
   int hgx = 0, hgy = 0;  // halo group: tile-local first node and row
   bool hduty = false;
   if (kStage != 0) {
-    // halo duties go to the first lanes of every warp (see k_mg_fine_rr_tma)
-    const int nthr = TXT * TY;
-    const int dix = (nthr & 31) == 0 ? (tid & 31) * (nthr >> 5) + (tid >> 5) : tid;
-    if (dix < 2 * GW) {
+    if (tid < 2 * GW) {
       hduty = true;
-      hgx = 4 * (dix % GW) - 4;
-      hgy = dix < GW ? -1 : TY;
-    } else if (dix < 2 * GW + 2 * TY) {
+      hgx = 4 * (tid % GW) - 4;
+      hgy = tid < GW ? -1 : TY;
+    } else if (tid < 2 * GW + 2 * TY) {
       hduty = true;
-      const int t = dix - 2 * GW;
+      const int t = tid - 2 * GW;
       hgx = t < TY ? -4 : TXN;
       hgy = t < TY ? t : t - TY;
     }
