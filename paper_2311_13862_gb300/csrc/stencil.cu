@@ -944,9 +944,24 @@ __device__ bool grid_sync(const PCtl& c) {
 }
 
 __global__ void __launch_bounds__(256) k_pcg_persistent(const PTask* __restrict__ tasks, int ntasks, PCtl c) {
+  // the arguments of the task being worked on, in shared memory: the phase bodies read
+  // them at every plane, and global loads would miss L1 after each grid barrier
+  __shared__ __align__(16) unsigned s_args[(sizeof(CGArgs<double>) + 3) / 4];
+  int cur = -1;  // task whose arguments s_args holds (the same in every thread)
+  const int nthr = blockDim.x * blockDim.y;
   int total = 0, total_fin = 0;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int warps = (blockDim.x * blockDim.y) >> 5;
+  const int warps = nthr >> 5;
+  auto args = [&](int t) -> const CGArgs<double>& {
+    if (t != cur) {
+      __syncthreads();
+      const unsigned* src = reinterpret_cast<const unsigned*>(&tasks[t].a);
+      for (int w = tid; w < (int)(sizeof(CGArgs<double>) / 4); w += nthr) s_args[w] = src[w];
+      cur = t;
+      __syncthreads();
+    }
+    return *reinterpret_cast<const CGArgs<double>*>(s_args);
+  };
   for (int t = 0; t < ntasks; t++) {
     total += tasks[t].items;
     total_fin += (tasks[t].a.B + warps - 1) / warps;
@@ -967,15 +982,17 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(const PTask* __restrict_
       int t;
       VBlk v;
       locate(item, t, v);
+      const CGArgs<double>& a = args(t);
       __syncthreads();
-      cg_init_body<double>(tasks[t].a, 0, v);
+      cg_init_body<double>(a, 0, v);
     }
   };
   auto finalize = [&](int mode) {
     for (int item = blockIdx.x; item < total_fin; item += gridDim.x) {
       int t = 0, rest = item;
       while (rest >= (tasks[t].a.B + warps - 1) / warps) rest -= (tasks[t++].a.B + warps - 1) / warps;
-      cg_finalize_body<double>(tasks[t].a, 0, mode, c.max_restarts, rest * warps + (tid >> 5), tid & 31);
+      const CGArgs<double>& a = args(t);
+      cg_finalize_body<double>(a, 0, mode, c.max_restarts, rest * warps + (tid >> 5), tid & 31);
     }
   };
   auto active = [&]() {
@@ -1002,16 +1019,18 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(const PTask* __restrict_
       int t;
       VBlk v;
       locate(item, t, v);
+      const CGArgs<double>& a = args(t);
       __syncthreads();
-      cg_a_body<double>(tasks[t].a, parity, v);
+      cg_a_body<double>(a, parity, v);
     }
     if (!grid_sync(c)) return;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
       int t;
       VBlk v;
       locate(item, t, v);
+      const CGArgs<double>& a = args(t);
       __syncthreads();
-      cg_b_body<double>(tasks[t].a, parity, v);
+      cg_b_body<double>(a, parity, v);
     }
     if (!grid_sync(c)) return;
     parity ^= 1;
