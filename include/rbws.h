@@ -239,6 +239,21 @@ RBWS_API rbws_status rbws_problem_info(rbws_problem p, int64_t* n_dof, int32_t* 
 RBWS_API rbws_status rbws_apply_operator(rbws_problem p, const double* mu, int32_t B, const void* x,
                                 void* y, int32_t precision, void* stream);
 
+/* rbws_apply_operator in the mu-interleaved layout: x, y device [nz][ny][nx][B]
+ * (element (node, b) at node*B + b, node = (k*ny + j)*nx + i), float64 or float32
+ * (RBWS_FP32_IR).  A warp takes 32 consecutive instances of one node.  The layout is an
+ * alternative for the autotuner (rbws_autotune_layout); the solvers keep the planar one.
+ * Synchronous; allocates an interleaved copy of the coefficient tables in
+ * library-owned scratch. */
+RBWS_API rbws_status rbws_apply_operator_interleaved(rbws_problem p, const double* mu, int32_t B, const void* x,
+                                                     void* y, int32_t precision, void* stream);
+/* Times y = A x for B instances in the planar layout (the z-march of the solvers) and in
+ * the mu-interleaved one (rbws_apply_operator_interleaved), best of three launches each
+ * after a warm-up, with CUDA events; planar_ms / interleaved_ms (may be NULL) receive the
+ * times and layout_out (may be NULL) 0 for planar, 1 for interleaved, the faster one. */
+RBWS_API rbws_status rbws_autotune_layout(rbws_problem p, int32_t B, int32_t precision, double* planar_ms,
+                                          double* interleaved_ms, int32_t* layout_out);
+
 /* y[b] = P(mu[b]) x[b]: the preconditioner of Algorithm 1 applied to B
  * vectors (device [B][n_dof] FP64; x and y distinct, x unchanged).  precond:
  * RBWS_PREC_JACOBI (D^{-1} x) or RBWS_PREC_MG (one V-cycle of Algorithm 2 from

@@ -1937,6 +1937,86 @@ rbws_status rbws_update_ff(rbws_problem p, const double* mu, int32_t B, const vo
   return RBWS_OK;
 }
 
+rbws_status rbws_apply_operator_interleaved(rbws_problem p, const double* mu, int32_t B, const void* x, void* y,
+                                            int32_t precision, void* stream) {
+  if (!p || !mu || !x || !y || B < 1 || B > 65535 || (precision != RBWS_FP64 && precision != RBWS_FP32_IR)) {
+    set_error("rbws_apply_operator_interleaved: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, stream);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, mu, B, &d_mu, "mu_apply"));
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  CKI(coef_tables(p, d_mu, B, &c64, precision == RBWS_FP32_IR ? &c32 : nullptr));
+  int err = 0;
+  const size_t nc = (size_t)p->geo.ncls() * kCoefStride * B;
+  void* cI = p->buf("coef_il", (precision == RBWS_FP64 ? sizeof(double) : sizeof(float)) * nc, &err);
+  if (err) return (rbws_status)err;
+  if (precision == RBWS_FP64)
+    launch_apply_interleaved<double>(p->geo, c64, B, (double*)cI, (const double*)x, (double*)y, p->cur);
+  else
+    launch_apply_interleaved<float>(p->geo, c32, B, (float*)cI, (const float*)x, (float*)y, p->cur);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->cur));
+  return RBWS_OK;
+}
+
+rbws_status rbws_autotune_layout(rbws_problem p, int32_t B, int32_t precision, double* planar_ms,
+                                 double* interleaved_ms, int32_t* layout_out) {
+  if (!p || B < 1 || B > 65535 || (precision != RBWS_FP64 && precision != RBWS_FP32_IR)) {
+    set_error("rbws_autotune_layout: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  StreamGuard sg(p, nullptr);
+  cudaStream_t s = p->cur;
+  std::vector<double> ones((size_t)B * p->Q, 1.0);
+  double* d_mu = nullptr;
+  CKI(upload_mu(p, ones.data(), B, &d_mu, "mu_tune"));
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+  const bool f32 = precision == RBWS_FP32_IR;
+  CKI(coef_tables(p, d_mu, B, &c64, f32 ? &c32 : nullptr));
+  const size_t el = f32 ? sizeof(float) : sizeof(double);
+  int err = 0;
+  void* x = p->buf("lay_x", el * (size_t)B * p->n, &err);
+  void* y = err ? nullptr : p->buf("lay_y", el * (size_t)B * p->n, &err);
+  void* cI = err ? nullptr : p->buf("coef_il", el * (size_t)p->geo.ncls() * kCoefStride * B, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemsetAsync(x, 0, el * (size_t)B * p->n, s));
+  const Tile t = choose_tile(p->nx);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto timed = [&](bool il) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {  // the first call is a warm-up
+      cudaEventRecord(e0, s);
+      if (il) {
+        if (f32) launch_apply_interleaved<float>(p->geo, c32, B, (float*)cI, (const float*)x, (float*)y, s);
+        else launch_apply_interleaved<double>(p->geo, c64, B, (double*)cI, (const double*)x, (double*)y, s);
+      } else {
+        if (f32) launch_apply<float>(p->geo, t, c32, B, (const float*)x, p->n, (float*)y, s);
+        else launch_apply<double>(p->geo, t, c64, B, (const double*)x, p->n, (double*)y, s);
+      }
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    return (double)best;
+  };
+  const double tp = timed(false), ti = timed(true);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  if (planar_ms) *planar_ms = tp;
+  if (interleaved_ms) *interleaved_ms = ti;
+  if (layout_out) *layout_out = ti < tp ? 1 : 0;
+  return RBWS_OK;
+}
+
 rbws_status rbws_apply_preconditioner(rbws_problem p, const double* mu, int32_t B, int32_t precond,
                                       const void* x, void* y, void* stream) {
   if (!p || !mu || !x || !y || x == y || B < 1 || B > 65535) {

@@ -175,6 +175,12 @@ void launch_coef_tables(const Geo& g, const int8_t* keys_x, const int8_t* keys_y
                         double sy, double sz, int Q, const double* mu, int B, double* coef64,
                         float* coef32, cudaStream_t s);
 
+// y = A x in the mu-interleaved layout [n][B] (instance fastest); coef: the planar
+// tables [B][ncls][8], coefI: device scratch of ncls * 8 * B elements for their
+// interleaved copy.  Two launches.
+template <typename T>
+void launch_apply_interleaved(const Geo& g, const T* coef, int B, T* coefI, const T* x, T* y, cudaStream_t s);
+
 // y[b] = A(mu_b) x[b]; x_stride = 0 broadcasts one x to every instance.
 template <typename T>
 void launch_apply(const Geo& g, Tile t, const T* coef, int B, const T* x, int64_t x_stride, T* y,

@@ -943,98 +943,157 @@ __device__ bool grid_sync(const PCtl& c) {
   return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(256) k_pcg_persistent(const PTask* __restrict__ tasks, int ntasks, PCtl c) {
+constexpr int kPMaxTasks = 16;
+
+// Loop-invariant state lives in shared memory, not registers: the phase bodies are
+// inlined into the loop, and every register the loop keeps live costs resident CTAs.
+struct PShared {
+  PCtl c;
+  int ntasks, total, total_fin, cur;
+  int items[kPMaxTasks], ntiles[kPMaxTasks], nzc[kPMaxTasks], fin[kPMaxTasks];
+  const PTask* tasks;
+};
+
+// Four CTAs per SM (64 registers, a few spilled): the bodies inlined into one loop need 80
+// registers otherwise, and three resident CTAs left the FP64 pipe underfed (measured: 746
+// against 667 ms for 256 solves at 64^3).
+__global__ void __launch_bounds__(256, 4) k_pcg_persistent(const PTask* __restrict__ tasks, int ntasks, PCtl c) {
   // the arguments of the task being worked on, in shared memory: the phase bodies read
   // them at every plane, and global loads would miss L1 after each grid barrier
   __shared__ __align__(16) unsigned s_args[(sizeof(CGArgs<double>) + 3) / 4];
-  int cur = -1;  // task whose arguments s_args holds (the same in every thread)
-  const int nthr = blockDim.x * blockDim.y;
-  int total = 0, total_fin = 0;
+  __shared__ PShared S;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int warps = nthr >> 5;
+  if (tid == 0) {
+    const int warps = (blockDim.x * blockDim.y) >> 5;
+    S.c = c;
+    S.tasks = tasks;
+    S.ntasks = ntasks;
+    S.total = S.total_fin = 0;
+    S.cur = -1;
+    for (int t = 0; t < ntasks; t++) {
+      S.items[t] = tasks[t].items;
+      S.ntiles[t] = tasks[t].ntiles;
+      S.nzc[t] = tasks[t].a.nzc;
+      S.fin[t] = (tasks[t].a.B + warps - 1) / warps;
+      S.total += S.items[t];
+      S.total_fin += S.fin[t];
+    }
+  }
+  __syncthreads();
   auto args = [&](int t) -> const CGArgs<double>& {
-    if (t != cur) {
+    if (t != S.cur) {  // S.cur changes only between the two barriers below: uniform
       __syncthreads();
-      const unsigned* src = reinterpret_cast<const unsigned*>(&tasks[t].a);
-      for (int w = tid; w < (int)(sizeof(CGArgs<double>) / 4); w += nthr) s_args[w] = src[w];
-      cur = t;
+      const unsigned* src = reinterpret_cast<const unsigned*>(&S.tasks[t].a);
+      for (int w = tid; w < (int)(sizeof(CGArgs<double>) / 4); w += blockDim.x * blockDim.y) s_args[w] = src[w];
+      __syncthreads();
+      if (tid == 0) S.cur = t;
       __syncthreads();
     }
     return *reinterpret_cast<const CGArgs<double>*>(s_args);
   };
-  for (int t = 0; t < ntasks; t++) {
-    total += tasks[t].items;
-    total_fin += (tasks[t].a.B + warps - 1) / warps;
-  }
   // item -> (task, virtual block)
-  auto locate = [&](int item, int& t, VBlk& v) {
+  auto locate = [&](int item, int& t) -> VBlk {
     t = 0;
-    while (item >= tasks[t].items) item -= tasks[t++].items;
-    const PTask& k = tasks[t];
-    const int nzc = k.a.nzc;
-    v.x = item % k.ntiles;
-    v.y = (item / k.ntiles) % nzc;
-    v.z = item / (k.ntiles * nzc);
-    v.gx = k.ntiles;
+    while (item >= S.items[t]) item -= S.items[t++];
+    const int nt = S.ntiles[t];
+    return VBlk{item % nt, (item / nt) % S.nzc[t], item / (nt * S.nzc[t]), nt};
+  };
+  auto active = [&]() {
+    int n = 0;
+    for (int t = 0; t < S.ntasks; t++) n += *reinterpret_cast<volatile int*>(S.tasks[t].a.active);
+    return n;
   };
   auto init = [&]() {
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    for (int item = blockIdx.x; item < S.total; item += gridDim.x) {
       int t;
-      VBlk v;
-      locate(item, t, v);
+      const VBlk v = locate(item, t);
       const CGArgs<double>& a = args(t);
       __syncthreads();
       cg_init_body<double>(a, 0, v);
     }
   };
   auto finalize = [&](int mode) {
-    for (int item = blockIdx.x; item < total_fin; item += gridDim.x) {
+    for (int item = blockIdx.x; item < S.total_fin; item += gridDim.x) {
       int t = 0, rest = item;
-      while (rest >= (tasks[t].a.B + warps - 1) / warps) rest -= (tasks[t++].a.B + warps - 1) / warps;
+      while (rest >= S.fin[t]) rest -= S.fin[t++];
       const CGArgs<double>& a = args(t);
-      cg_finalize_body<double>(a, 0, mode, c.max_restarts, rest * warps + (tid >> 5), tid & 31);
+      cg_finalize_body<double>(a, 0, mode, S.c.max_restarts, rest * ((blockDim.x * blockDim.y) >> 5) + (tid >> 5),
+                               tid & 31);
     }
   };
-  auto active = [&]() {
-    int n = 0;
-    for (int t = 0; t < ntasks; t++) n += *reinterpret_cast<volatile int*>(tasks[t].a.active);
-    return n;
-  };
   init();
-  if (!grid_sync(c)) return;
+  if (!grid_sync(S.c)) return;
   finalize(0);
-  if (!grid_sync(c)) return;
+  if (!grid_sync(S.c)) return;
   int parity = 0;
-  for (int round = 0; round < c.max_rounds; round++) {
+  for (int round = 0; round < S.c.max_rounds; round++) {
     if (active() == 0) {
       // every instance stopped: check the true residual f - A u, restart the failures
       init();
-      if (!grid_sync(c)) return;
+      if (!grid_sync(S.c)) return;
       finalize(1);
-      if (!grid_sync(c)) return;
+      if (!grid_sync(S.c)) return;
       if (active() == 0) return;
       parity = 0;
     }
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    for (int item = blockIdx.x; item < S.total; item += gridDim.x) {
       int t;
-      VBlk v;
-      locate(item, t, v);
+      const VBlk v = locate(item, t);
       const CGArgs<double>& a = args(t);
       __syncthreads();
       cg_a_body<double>(a, parity, v);
     }
-    if (!grid_sync(c)) return;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    if (!grid_sync(S.c)) return;
+    for (int item = blockIdx.x; item < S.total; item += gridDim.x) {
       int t;
-      VBlk v;
-      locate(item, t, v);
+      const VBlk v = locate(item, t);
       const CGArgs<double>& a = args(t);
       __syncthreads();
       cg_b_body<double>(a, parity, v);
     }
-    if (!grid_sync(c)) return;
+    if (!grid_sync(S.c)) return;
     parity ^= 1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// y = A x in the mu-interleaved layout [nz][ny][nx][B] (instance fastest): a warp
+// takes 32 consecutive instances of one node, so every load and store of x, y and of
+// the coefficients is one 32-element run; the 6 neighbours come through L1/L2.  The
+// coefficient table is interleaved too: cI[cls][8][B].  An alternative layout for the
+// autotuner to time against the planar z-march (rbws_autotune_layout).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_coef_interleave(const T* __restrict__ c, int ncls, int B, T* __restrict__ cI) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ncls * kCoefStride * B) return;
+  const int b = (int)(t % B), k = (int)((t / B) % kCoefStride), cls = (int)(t / ((int64_t)B * kCoefStride));
+  cI[t] = c[((int64_t)b * ncls + cls) * kCoefStride + k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_il(Geo g, int B, const T* __restrict__ cI, const T* __restrict__ x,
+                                                 T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int groups = (B + 31) >> 5;
+  const int64_t node = warp / groups;
+  if (node >= g.n) return;
+  const int b = (int)(warp % groups) * 32 + lane;
+  if (b >= B) return;
+  const int i = (int)(node % g.nx), j = (int)((node / g.nx) % g.ny), k = (int)(node / ((int64_t)g.nx * g.ny));
+  const int cls = ((int)g.cz[k] * g.ncy + (int)g.cy[j]) * g.ncx + (int)g.cx[i];
+  const T* cr = cI + (int64_t)cls * kCoefStride * B + b;
+  const int64_t sx = B, sy = (int64_t)g.nx * B, sz = (int64_t)g.nx * g.ny * B;
+  const T* xp = x + node * B + b;
+  T v = cr[6 * B] * xp[0];
+  if (i > 0) v = fma(cr[0], xp[-sx], v);
+  if (i < g.nx - 1) v = fma(cr[1 * B], xp[sx], v);
+  if (j > 0) v = fma(cr[2 * B], xp[-sy], v);
+  if (j < g.ny - 1) v = fma(cr[3 * B], xp[sy], v);
+  if (k > 0) v = fma(cr[4 * B], xp[-sz], v);
+  if (k < g.nz - 1) v = fma(cr[5 * B], xp[sz], v);
+  y[node * B + b] = v;
 }
 
 inline size_t plane_smem(Tile t, size_t elem) { return 3 * (size_t)(t.tx + 2) * (t.ty + 2) * elem; }
@@ -1106,6 +1165,7 @@ void launch_cg_finalize(const CGArgs<T>& a, int parity, int mode, int max_restar
 int launch_pcg_persistent(const std::vector<CGArgs<double>>& args, Tile t, int* bar, int* err,
                           long long wait_cycles, int max_restarts, int max_rounds, void* d_tasks, cudaStream_t s) {
   const int ntasks = (int)args.size();
+  if (ntasks < 1 || ntasks > kPMaxTasks) return -1;
   std::vector<PTask> h(ntasks);
   int total = 0;
   for (int i = 0; i < ntasks; i++) {
@@ -1136,6 +1196,18 @@ int launch_pcg_persistent(const std::vector<CGArgs<double>>& args, Tile t, int* 
 }
 
 size_t pcg_persistent_task_bytes() { return sizeof(PTask); }
+
+template <typename T>
+void launch_apply_interleaved(const Geo& g, const T* coef, int B, T* coefI, const T* x, T* y, cudaStream_t s) {
+  const int64_t nc = (int64_t)g.ncls() * kCoefStride * B;
+  k_coef_interleave<T><<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(coef, g.ncls(), B, coefI);
+  const int64_t warps = g.n * ((B + 31) / 32);
+  k_apply_il<T><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(g, B, coefI, x, y);
+}
+template void launch_apply_interleaved<double>(const Geo&, const double*, int, double*, const double*, double*,
+                                               cudaStream_t);
+template void launch_apply_interleaved<float>(const Geo&, const float*, int, float*, const float*, float*,
+                                              cudaStream_t);
 
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s) {
   k_ru_decide<<<(a.B + 3) / 4, 128, 0, s>>>(a);

@@ -89,6 +89,8 @@ def _lib():
         L.rbws_gaussian_source.argtypes = [P, P, i32, P]
         L.rbws_apply_mg32.argtypes = [P, P, i32, P, P, P]
         L.rbws_update_ff.argtypes = [P, P, i32, P, P, P, P]
+        L.rbws_apply_operator_interleaved.argtypes = [P, P, i32, P, P, i32, P]
+        L.rbws_autotune_layout.argtypes = [P, i32, i32, C.POINTER(d), C.POINTER(d), C.POINTER(i32)]
         L.rbws_solve_batch_rhs.argtypes = [P, P, i32, P, d, i32, C.POINTER(rbws_options), P, P, P, P]
         L.rbws_offline_greedy_rhs.argtypes = [P, P, P, i32, i32, d, d, P, P, C.POINTER(i32)]
         L.rbws_apply_operator_static.argtypes = [P, P, i32, P, P, i32, P]
@@ -197,6 +199,22 @@ def rbws_apply_operator(h, mu, x, y, precision=FP64, stream=None):
     mu = _host(np.atleast_2d(mu))
     _check(_lib().rbws_apply_operator(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), precision, stream),
            "rbws_apply_operator")
+
+
+def rbws_apply_operator_interleaved(h, mu, x, y, precision=FP64, stream=None):
+    """y = A(mu_b) x in the mu-interleaved layout: x, y CUDA tensors [n][B] (instance fastest)."""
+    mu = _host(np.atleast_2d(mu))
+    _check(_lib().rbws_apply_operator_interleaved(h, _hp(mu), mu.shape[0], _dp(x), _dp(y), precision, stream),
+           "rbws_apply_operator_interleaved")
+
+
+def rbws_autotune_layout(h, B, precision=FP32_IR):
+    """Times the planar and the mu-interleaved operator apply: returns (planar_ms, interleaved_ms,
+    layout) with layout 0 planar, 1 interleaved (the faster)."""
+    tp, ti, lay = C.c_double(0.0), C.c_double(0.0), C.c_int32(0)
+    _check(_lib().rbws_autotune_layout(h, B, precision, C.byref(tp), C.byref(ti), C.byref(lay)),
+           "rbws_autotune_layout")
+    return tp.value, ti.value, lay.value
 
 
 def rbws_update_ff(h, mu, u0, d, u_out, r_out):
