@@ -594,7 +594,7 @@ def main():
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             acc = {"launches": 0, "samples": 0, "stencil_ms": 0.0, "update_ms": 0.0, "active_dofs": 0.0,
-                   "precond_ms": 0.0}
+                   "precond_ms": 0.0, "mg_prolong_ms": 0.0}
             acc_fine = [0.0] * 4
             acc_schedule = None
             torch.cuda.nvtx.range_push("timed")
@@ -603,7 +603,7 @@ def main():
                 out = rbws.rbws_solve_batch(P.h, mus, w.tol, warm, u, o)
                 if profile:
                     for k in acc:
-                        acc[k] += getattr(prof, k)
+                        acc[k] += getattr(prof, k)  # every key of acc is a field of rbws_profile
                     for k in range(4):
                         acc_fine[k] += prof.mg_fine_ms[k]
                     acc_schedule = prof.schedule
@@ -783,20 +783,24 @@ def main():
         # read r, write Y (8); read Y, r, write the restricted residual at 1/8 of the nodes
         # (8.5); read and write Y, the coarse correction at 1/8 of the nodes, then read Y, r,
         # write X (8 + 0.5 + 12, two launches timed together); read X, r, write s (12)
+        # (each a single kernel, timed by CUDA events around its own launch)
         fine_kernels = [("k_mg_smooth_tma<1,0> (two damped Jacobi steps from zero)", 8.0,
                          "mg_fine_smooth_pre_f32_64cube"),
                         ("k_mg_fine_rr_tma (restricted residual P^T (r - A Y))", 8.5,
                          "mg_fine_residual_restrict_f32_64cube"),
-                        ("k_mg_prolong_add4 + k_mg_smooth_tma<0,0> (Y += P e; damped Jacobi step)", 20.5,
-                         "mg_fine_prolong_smooth_f32_64cube"),
+                        ("k_mg_prolong_add4 (Y += P e)", 8.5, None),
+                        ("k_mg_smooth_tma<0,0> (damped Jacobi step)", 12.0, None),
                         ("k_mg_smooth_tma<0,1> (damped Jacobi step + rho partials)", 12.0,
                          "mg_fine_smooth_rho_f32_64cube")]
-        for (name, alg, tag), t_ms in zip(fine_kernels, acc["mg_fine_ms"]):
+        mf = acc["mg_fine_ms"]
+        times = [mf[0], mf[1], acc["mg_prolong_ms"], mf[2] - acc["mg_prolong_ms"], mf[3]]
+        for (name, alg, tag), t_ms in zip(fine_kernels, times):
             gbs = acc["active_dofs"] * alg / (t_ms * 1e-3) / 1e9
-            tr = traffic_per_dof(tag)
+            tr = traffic_per_dof(tag) if tag else None
             fine.append({"kernel": name, "achieved": round(gbs, 1), "frac": round(gbs / peak, 4),
                          "algorithmic_bytes_per_dof": alg, "ms_per_launch": t_ms / acc["samples"],
                          "traffic": None if tr is None else tr * launch_dofs, "ms_total": t_ms})
+        # the dominant kernel: the single kernel with the largest total time of the sampled ones
         phases = [dict(stencil, ms_total=acc["stencil_ms"]), dict(update, ms_total=acc["update_ms"])] + fine
         dom = max(phases, key=lambda k: k["ms_total"])
     if acc["samples"] > 0 and dom is not None:
@@ -808,7 +812,10 @@ def main():
                "stencil_phase": stencil, "update_phase": update,
                "solver_frac_minimal_bytes": round(solver_gbs / peak, 4), "sampled_launches": acc["samples"]}
         if fine:
-            res["mg_fine_steps"] = [{k: v for k, v in f.items() if k != "ms_total"} for f in fine]
+            res["mg_fine_steps"] = [dict({k: v for k, v in f.items() if k != "ms_total"},
+                                         share=round(f["ms_total"] / total_ms, 3)) for f in fine]
+            for ph in ("stencil_phase", "update_phase"):
+                res[ph]["share"] = round(acc[ph.split("_")[0] + "_ms"] / total_ms, 3)
             res["vcycle_ms_per_iteration"] = acc["precond_ms"] / acc["samples"]
             res.pop("solver_frac_minimal_bytes")
             res["dominant_share_of"] = "the sampled iterations: phase A + phase B + V-cycle"

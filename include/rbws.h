@@ -133,6 +133,7 @@ typedef struct {
   double mg_fine_ms[4]; /* ... and of their finest-level steps: two smoothing steps
                           from zero, residual, prolongation pass + one smoothing
                           step, last smoothing step + rho partials                  */
+  double mg_prolong_ms; /* ... of the prolongation pass alone (part of mg_fine_ms[2]) */
 } rbws_profile;
 
 typedef struct {

@@ -181,7 +181,7 @@ struct rbws_problem_s {
   cudaStream_t cur = nullptr;     // work stream of the current call
   cudaEvent_t ev = nullptr;
   cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // profiling events
-  cudaEvent_t mgev[8] = {};                                  // ... of the fused MG steps
+  cudaEvent_t mgev[10] = {};                                 // ... of the fused MG steps
   int64_t launches = 0;           // kernels launched by the current call
   int* h_active = nullptr;   // pinned
   // reduced basis
@@ -1109,6 +1109,10 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
             float tk = 0.f;
             cudaEventElapsedTime(&tk, p->mgev[2 * k], p->mgev[2 * k + 1]);
             prof->mg_fine_ms[k] += tk;
+            if (k == 2) {  // the prolongation pass alone (the first part of step 2)
+              cudaEventElapsedTime(&tk, p->mgev[4], p->mgev[8]);
+              prof->mg_prolong_ms += tk;
+            }
           }
       }
       prof->active_dofs += (double)active * (double)p->n;

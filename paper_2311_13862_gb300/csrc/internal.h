@@ -434,7 +434,8 @@ struct MGBatch {
   // tiling of the fused steps that write no partials (wider tiles: less halo)
   Tile mg_tile{0, 0};
   int mg_tiles_x = 0, mg_tiles_y = 0, mg_zc = 0, mg_nzc = 0;
-  cudaEvent_t* ev = nullptr;  // if set: 8 events bracketing the four fused finest-level steps
+  cudaEvent_t* ev = nullptr;  // if set: 8 events bracketing the four fused finest-level steps, and a
+                              // ninth (ev[8]) between the prolongation pass and step 2's smoothing
   MGLevel lv[kMGMaxLevels];
   void* rhs[kMGMaxLevels] = {};
   void* sol[kMGMaxLevels] = {};

@@ -1207,6 +1207,7 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
     k_mg_prolong_add4<1><<<dim3((unsigned)((F.n / 4 + 255) / 256), (unsigned)m.B), 256, 0, s>>>(
         F.nx, F.ny, F.nz, C.nx, C.ny, C.nz, m.st, m.mask, csol, Y);
   launches += 1;
+  if (m.ev) cudaEventRecord(m.ev[8], s);  // the prolongation pass ends here
   fa.xin = Y;
   fa.out = W;
   fine(2, 0, 0, false);  // W = smoothing step from Y

@@ -46,7 +46,8 @@ class rbws_blocks(C.Structure):
 class rbws_profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("samples", C.c_int64), ("stencil_ms", C.c_double),
                 ("update_ms", C.c_double), ("active_dofs", C.c_double), ("elem_bytes", C.c_int32),
-                ("schedule", C.c_int32), ("precond_ms", C.c_double), ("mg_fine_ms", C.c_double * 4)]
+                ("schedule", C.c_int32), ("precond_ms", C.c_double), ("mg_fine_ms", C.c_double * 4),
+                ("mg_prolong_ms", C.c_double)]
 
 
 class rbws_axes(C.Structure):
