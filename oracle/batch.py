@@ -33,17 +33,18 @@ def _init(grid, blocks, submap, Q, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)):
 
 def _solve(task):
     from . import mg
-    mu, f, tol = task
+    mu, f, tol, u0 = task
     op = assemble_mu(_STATE["grid"], mu, blocks=_STATE["blocks"], submap=_STATE["submap"], Q=_STATE["Q"],
                      kscale=_STATE["kscale"], neumann=_STATE["neumann"])
-    r = mg.mgcg(op, [1.0], f=f, tol=tol, max_iters=400)
+    r = mg.mgcg(op, [1.0], f=f, u0=u0, tol=tol, max_iters=400)
     return r.u, r.iters, r.relres, r.status
 
 
 def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol=1e-13, processes=None,
-                        kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)):
+                        kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0), u0=None):
     """Oracle FP64 MGCG solutions u_b of A(mu_b) u = f_b (f: None = ones, [n] shared, or [B][n];
-    kscale, neumann: the operator's anisotropy and Neumann faces, as oracle.assemble takes them).
+    kscale, neumann: the operator's anisotropy and Neumann faces, as oracle.assemble takes them;
+    u0: None (zero start) or [B][n] initial values computed by the oracle).
     Returns (U [B][n], iters [B], relres [B], status [B], seconds, processes)."""
     mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
     B = mus.shape[0]
@@ -59,7 +60,7 @@ def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
     os.environ.update({"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1"})
     try:
-        tasks = [(mus[b], fb[b], tol) for b in range(B)]
+        tasks = [(mus[b], fb[b], tol, None if u0 is None else np.asarray(u0[b], dtype=np.float64)) for b in range(B)]
         if processes == 1:
             _init(tuple(grid), blocks, submap, Q, kscale, neumann)
             out = [_solve(t) for t in tasks]
