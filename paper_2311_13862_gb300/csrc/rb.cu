@@ -463,9 +463,13 @@ constexpr int kLtcMaxK = 64;
 
 constexpr int kLtcWp = kLtcNodes + 8;  // pitch of a staged W row (words; 8 mod 32: no bank conflicts)
 
+constexpr int kLtcDp = kLtcNodes + 4;  // pitch of an output row (floats) staged for the writes
+
 inline size_t lift_tc_smem(int N) {
   const int Kp = (N + 7) & ~7;
-  return sizeof(unsigned) * 2 * ((size_t)Kp * kLtcWp + (size_t)kLtcInst * (Kp + 4));
+  const size_t stage = sizeof(unsigned) * 2 * ((size_t)Kp * kLtcWp + (size_t)kLtcInst * (Kp + 4));
+  const size_t out = sizeof(float) * (size_t)kLtcInst * kLtcDp;  // reuses the staging space
+  return stage > out ? stage : out;
 }
 
 __global__ void __launch_bounds__(256) k_lift_tc(int64_t n, int N, const float* __restrict__ W,
@@ -514,15 +518,22 @@ __global__ void __launch_bounds__(256) k_lift_tc(int64_t n, int N, const float* 
       mma_tf32(d[t], ah, bh);
     }
   }
-  // D (16 x 8): (row g, cols 2 tig, 2 tig + 1), (row g + 8, same cols); rows are nodes
+  // D (16 x 8): (row g, cols 2 tig, 2 tig + 1), (row g + 8, same cols); rows are nodes.  The
+  // tile goes through shared memory ([instance][node]) so that each instance's 128 nodes are
+  // written as one contiguous run
+  __syncthreads();  // the staged operands are no longer read
+  float* Ds = reinterpret_cast<float*>(lsm);
 #pragma unroll
   for (int t = 0; t < 8; t++)
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int64_t i = i0 + m0 + g + (q >= 2 ? 8 : 0);
-      const int bb = b0 + 8 * t + 2 * tig + (q & 1);
-      if (i < n && bb < B) u[(int64_t)bb * n + i] = (double)d[t][q];
-    }
+    for (int q = 0; q < 4; q++)
+      Ds[(8 * t + 2 * tig + (q & 1)) * kLtcDp + m0 + g + (q >= 2 ? 8 : 0)] = d[t][q];
+  __syncthreads();
+  for (int e = tid; e < kLtcInst * kLtcNodes; e += 256) {
+    const int r = e / kLtcNodes, x = e % kLtcNodes;
+    const int64_t i = i0 + x;
+    if (b0 + r < B && i < n) u[(int64_t)(b0 + r) * n + i] = (double)Ds[r * kLtcDp + x];
+  }
 }
 
 // FN[j * B + b] = sum over the S splits, in split order.
@@ -604,12 +615,21 @@ void launch_row_norms(int64_t n, int B, const double* X, int64_t ldx, double* ou
   if (B > 0) k_row_norms<<<B, 256, 0, s>>>(n, X, ldx, out);
 }
 
-int project32_splits(int64_t n, int B) {
+// Splits of the nodes: the CUDA-core kernel's (32-instance groups) and the tensor-core
+// kernel's (64-instance groups), each about four CTAs per SM.
+int splits_cc(int64_t n, int B) {
   const int groups = (B + kProjInst - 1) / kProjInst;
   int64_t S = std::max<int64_t>(1, (4 * 152 + groups - 1) / groups);
   S = std::min<int64_t>(S, (n + kProjRun - 1) / kProjRun);
   return (int)std::max<int64_t>(S, 1);
 }
+int splits_tc(int64_t n, int B) {
+  const int groups = (B + kPtcInst - 1) / kPtcInst;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((4 * 152 + groups - 1) / groups, n / (4 * kPtcK)));
+}
+
+// The partial sums' scratch is sized for either kernel.
+int project32_splits(int64_t n, int B) { return std::max(splits_cc(n, B), splits_tc(n, B)); }
 
 int launch_project32(int64_t n, int N, int B, const float* W, const double* F, int64_t ldf, double* part,
                      double* FN, cudaStream_t s) {
@@ -618,7 +638,7 @@ int launch_project32(int64_t n, int N, int B, const float* W, const double* F, i
   const bool tc = N <= 48 && n % 4 == 0 && ldf % 2 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0 &&
                   (reinterpret_cast<uintptr_t>(W) & 15) == 0;
   if (tc) {
-    const int S = project32_splits(n, B);
+    const int S = splits_tc(n, B);
     int64_t per = (n + S - 1) / S;
     per = (per + kPtcK - 1) / kPtcK * kPtcK;
     const int Sused = (int)((n + per - 1) / per);
@@ -630,7 +650,7 @@ int launch_project32(int64_t n, int N, int B, const float* W, const double* F, i
     k_project_reduce<<<(N * B + 255) / 256, 256, 0, s>>>(Sused, N, B, part, FN);
     return 0;
   }
-  const int S = project32_splits(n, B);
+  const int S = splits_cc(n, B);
   int64_t per = (n + S - 1) / S;
   per = (per + kProjRun - 1) / kProjRun * kProjRun;
   const int Sused = (int)((n + per - 1) / per);

@@ -373,17 +373,28 @@ __global__ void k_ru_mark(CGArgs<float> a, FFState ff) {
   ff.chk[b] = (a.upd[b] != 0 && ff.rel[b] < a.tol) ? 1 : 0;
 }
 
-// u64 = hi + lo for the instances with mask[b] != 0.  Usually few instances are
-// masked in, so one grid sweeps the instances (skipping the others) instead of a
-// grid per instance whose CTAs would mostly exit at once.
-__global__ void k_ff_to64(int64_t n, int B, const float* __restrict__ uh, const float* __restrict__ ul,
-                          const int* __restrict__ mask, double* __restrict__ u64) {
+// u64 = hi + lo for the instances with mask[b] != 0.  Usually few instances are masked in:
+// each CTA compacts the mask (1024 instances at a time) into a shared list and the grid
+// sweeps the flattened (listed instance, node) range, so every element is independent work
+// instead of one instance after another.
+__global__ void __launch_bounds__(256) k_ff_to64(int64_t n, int B, const float* __restrict__ uh,
+                                                 const float* __restrict__ ul, const int* __restrict__ mask,
+                                                 double* __restrict__ u64) {
+  __shared__ int s_list[1024];
+  __shared__ int s_cnt;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int b = 0; b < B; b++) {
-    if (!mask[b]) continue;
-    const int64_t off = (int64_t)b * n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-      u64[off + i] = ff_to_f64(uh[off + i], ul[off + i]);
+  for (int c0 = 0; c0 < B; c0 += 1024) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 1024 && c0 + k < B; k += blockDim.x)
+      if (mask[c0 + k]) s_list[atomicAdd(&s_cnt, 1)] = c0 + k;
+    __syncthreads();
+    const int64_t total = (int64_t)s_cnt * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
+      const int64_t e = (int64_t)s_list[t / n] * n + t % n;
+      u64[e] = ff_to_f64(uh[e], ul[e]);
+    }
+    __syncthreads();  // the list is rebuilt for the next chunk
   }
 }
 
@@ -528,8 +539,7 @@ void launch_ru_mark(const CGArgs<float>& a, const FFState& ff, cudaStream_t s) {
 }
 
 void launch_ff_to64(const CGArgs<float>& a, const FFState& ff, const int* mask, cudaStream_t s) {
-  const int64_t blocks = std::min<int64_t>((a.g.n + 255) / 256, 152 * 8);
-  k_ff_to64<<<(unsigned)blocks, 256, 0, s>>>(a.g.n, a.B, ff.uh, ff.ul, mask, a.u64);
+  k_ff_to64<<<152 * 8, 256, 0, s>>>(a.g.n, a.B, ff.uh, ff.ul, mask, a.u64);
 }
 
 void launch_ff_fold(const CGArgs<float>& a, const FFState& ff, cudaStream_t s) {
