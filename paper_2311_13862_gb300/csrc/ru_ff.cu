@@ -374,27 +374,49 @@ __global__ void k_ru_mark(CGArgs<float> a, FFState ff) {
 }
 
 // u64 = hi + lo for the instances with mask[b] != 0.  Usually few instances are masked in:
-// each CTA compacts the mask (1024 instances at a time) into a shared list and the grid
-// sweeps the flattened (listed instance, node) range, so every element is independent work
-// instead of one instance after another.
+// each CTA compacts the mask (1024 instances at a time) into a shared list in ascending
+// order (a block-wide prefix sum, so every CTA holds the same list) and the grid sweeps the
+// flattened (listed instance, node) range, so every element is independent work instead of
+// one instance after another.
 __global__ void __launch_bounds__(256) k_ff_to64(int64_t n, int B, const float* __restrict__ uh,
                                                  const float* __restrict__ ul, const int* __restrict__ mask,
                                                  double* __restrict__ u64) {
   __shared__ int s_list[1024];
+  __shared__ int s_warp[8];
   __shared__ int s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;  // 256 threads
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int c0 = 0; c0 < B; c0 += 1024) {
-    if (threadIdx.x == 0) s_cnt = 0;
+    // thread tid takes the chunk's entries 4 tid .. 4 tid + 3
+    int flags[4], cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int b = c0 + 4 * tid + q;
+      flags[q] = b < B && mask[b] != 0;
+      cnt += flags[q];
+    }
+    int incl = cnt;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    for (int k = threadIdx.x; k < 1024 && c0 + k < B; k += blockDim.x)
-      if (mask[c0 + k]) s_list[atomicAdd(&s_cnt, 1)] = c0 + k;
+    int base = 0;
+    for (int w = 0; w < warp; w++) base += s_warp[w];
+    int pos = base + incl - cnt;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (flags[q]) s_list[pos++] = c0 + 4 * tid + q;
+    if (tid == 255) s_cnt = pos;
     __syncthreads();
     const int64_t total = (int64_t)s_cnt * n;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < total; t += stride) {
       const int64_t e = (int64_t)s_list[t / n] * n + t % n;
       u64[e] = ff_to_f64(uh[e], ul[e]);
     }
-    __syncthreads();  // the list is rebuilt for the next chunk
+    __syncthreads();  // the list and the warp sums are rebuilt for the next chunk
   }
 }
 
