@@ -449,93 +449,6 @@ __global__ void __launch_bounds__(256) k_project_tc(int64_t n, int N, int B, con
     }
 }
 
-// ---------------------------------------------------------------------------
-// The mixed-precision lift u[b][i] = sum_j c[b][j] W[j][i] on the tensor cores
-// (mma.sync m16n8k8, TF32, the three-product split of k_project_tc), for N <= 64:
-// D[i][b] with M = 128 nodes per CTA (one 16-row tile per warp), 64 instances per CTA
-// (8 column tiles per warp), K = N padded to 8.  W's tile and the coefficients arrive in
-// shared memory already split into TF32 high and low parts; u is written in FP64 (each
-// value the FP32 sum, so the mixed-precision start holds FP32 values exactly).
-// ---------------------------------------------------------------------------
-constexpr int kLtcNodes = 128;
-constexpr int kLtcInst = 64;
-constexpr int kLtcMaxK = 64;
-
-constexpr int kLtcWp = kLtcNodes + 8;  // pitch of a staged W row (words; 8 mod 32: no bank conflicts)
-
-constexpr int kLtcDp = kLtcNodes + 4;  // pitch of an output row (floats) staged for the writes
-
-inline size_t lift_tc_smem(int N) {
-  const int Kp = (N + 7) & ~7;
-  const size_t stage = sizeof(unsigned) * 2 * ((size_t)Kp * kLtcWp + (size_t)kLtcInst * (Kp + 4));
-  const size_t out = sizeof(float) * (size_t)kLtcInst * kLtcDp;  // reuses the staging space
-  return stage > out ? stage : out;
-}
-
-__global__ void __launch_bounds__(256) k_lift_tc(int64_t n, int N, const float* __restrict__ W,
-                                                const double* __restrict__ c, int B, double* __restrict__ u) {
-  extern __shared__ __align__(16) unsigned lsm[];
-  const int Kp = (N + 7) & ~7, Cp = Kp + 4;
-  // [j][node] high and low parts of W, then [instance][j] of the coefficients
-  unsigned* Wh = lsm;
-  unsigned* Wl = Wh + Kp * kLtcWp;
-  unsigned* Ch = Wl + Kp * kLtcWp;
-  unsigned* Cl = Ch + kLtcInst * Cp;
-  const int64_t i0 = (int64_t)blockIdx.x * kLtcNodes;
-  const int b0 = blockIdx.y * kLtcInst;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, tig = lane & 3;
-  for (int e = tid; e < Kp * kLtcNodes; e += 256) {
-    const int j = e / kLtcNodes, x = e % kLtcNodes;
-    const float w = (j < N && i0 + x < n) ? W[(int64_t)j * n + i0 + x] : 0.f;
-    tf32_split(w, Wh[j * kLtcWp + x], Wl[j * kLtcWp + x]);
-  }
-  for (int e = tid; e < kLtcInst * Kp; e += 256) {
-    const int r = e / Kp, j = e % Kp;
-    const float v = (j < N && b0 + r < B) ? (float)c[(int64_t)(b0 + r) * N + j] : 0.f;
-    tf32_split(v, Ch[r * Cp + j], Cl[r * Cp + j]);
-  }
-  __syncthreads();
-  float d[8][4];
-#pragma unroll
-  for (int t = 0; t < 8; t++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) d[t][q] = 0.f;
-  const int m0 = 16 * warp;  // this warp's 16 nodes
-  for (int k0 = 0; k0 < Kp; k0 += 8) {
-    // A (16 x 8, row major): A[r][k] = W[k0 + k][i0 + m0 + r]
-    const int wa = (k0 + tig) * kLtcWp + m0 + g, wb = wa + 4 * kLtcWp;
-    const unsigned ah[4] = {Wh[wa], Wh[wa + 8], Wh[wb], Wh[wb + 8]};
-    const unsigned al[4] = {Wl[wa], Wl[wa + 8], Wl[wb], Wl[wb + 8]};
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-      // B (8 x 8, column major): B[k][nn] = c[b0 + 8 t + nn][k0 + k]
-      const int cx = (8 * t + g) * Cp + k0 + tig;
-      const unsigned bh[2] = {Ch[cx], Ch[cx + 4]};
-      const unsigned bl[2] = {Cl[cx], Cl[cx + 4]};
-      mma_tf32(d[t], al, bh);
-      mma_tf32(d[t], ah, bl);
-      mma_tf32(d[t], ah, bh);
-    }
-  }
-  // D (16 x 8): (row g, cols 2 tig, 2 tig + 1), (row g + 8, same cols); rows are nodes.  The
-  // tile goes through shared memory ([instance][node]) so that each instance's 128 nodes are
-  // written as one contiguous run
-  __syncthreads();  // the staged operands are no longer read
-  float* Ds = reinterpret_cast<float*>(lsm);
-#pragma unroll
-  for (int t = 0; t < 8; t++)
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-      Ds[(8 * t + 2 * tig + (q & 1)) * kLtcDp + m0 + g + (q >= 2 ? 8 : 0)] = d[t][q];
-  __syncthreads();
-  for (int e = tid; e < kLtcInst * kLtcNodes; e += 256) {
-    const int r = e / kLtcNodes, x = e % kLtcNodes;
-    const int64_t i = i0 + x;
-    if (b0 + r < B && i < n) u[(int64_t)(b0 + r) * n + i] = (double)Ds[r * kLtcDp + x];
-  }
-}
-
 // FN[j * B + b] = sum over the S splits, in split order.
 __global__ void k_project_reduce(int S, int N, int B, const double* __restrict__ part, double* __restrict__ FN) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -573,13 +486,6 @@ void launch_lift(int64_t n, int N, const double* W, const double* c, int B, doub
 }
 
 void launch_lift32(int64_t n, int N, const float* W, const double* c, int B, double* u, cudaStream_t s) {
-  if (N <= kLtcMaxK) {  // the tensor cores; the shared-memory limit is per device: set on every call
-    const size_t smem = lift_tc_smem(N);
-    cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lift_tc_smem(kLtcMaxK));
-    k_lift_tc<<<dim3((unsigned)((n + kLtcNodes - 1) / kLtcNodes), (unsigned)((B + kLtcInst - 1) / kLtcInst)), 256,
-                smem, s>>>(n, N, W, c, B, u);
-    return;
-  }
   const int threads = 256;
   dim3 grid(grid_for(n, threads, 152 * 4), (B + kLiftB - 1) / kLiftB);
   k_lift32<<<grid, threads, sizeof(float) * kLiftB * N, s>>>(n, N, W, c, B, u);
