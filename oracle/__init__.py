@@ -50,6 +50,8 @@ def lib():
         L.orc_assemble_affine.argtypes = [i32, i32, i32, P, i32, P, P, P]
         L.orc_assemble_ex.argtypes = [i32, i32, i32, P, i32, P, P, P, P, P]
         L.orc_node_weights.argtypes = [i32, i32, i32, P, P]
+        L.orc_assemble_field.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P]
+        L.orc_dirichlet_lift.argtypes = [i32, i32, i32, i32, P, P, P, P, P]
         L.orc_block_map_ex.argtypes = [i32] * 6 + [P, P]
         L.orc_assemble_mu.argtypes = [i32, i32, i32, P, i32, P, P, P, P]
         L.orc_csr_combine.argtypes = [i64, i32, P, P, P]
@@ -174,6 +176,54 @@ def assemble(grid, blocks=None, submap=None, Q=None, kscale=(1.0, 1.0, 1.0), neu
     if rc != 0:
         raise ValueError("orc_assemble_affine failed: %d" % rc)
     return Operator(tuple(grid), Q, row_ptr, col, vals)
+
+
+def _faces(grid, kfx, kfy, kfz):
+    nx, ny, nz = grid
+    kfx = np.ascontiguousarray(kfx, dtype=np.float64)
+    Q = kfx.shape[0]
+    kfx = kfx.reshape(Q, nz, ny, nx + 1)
+    kfy = np.ascontiguousarray(kfy, dtype=np.float64).reshape(Q, nz, ny + 1, nx)
+    kfz = np.ascontiguousarray(kfz, dtype=np.float64).reshape(Q, nz + 1, ny, nx)
+    return Q, kfx, kfy, kfz
+
+
+def assemble_field(grid, kfx, kfy, kfz) -> Operator:
+    """Affine terms A_q of an operator whose coefficient kappa_q is given at the cell faces
+    (orc_assemble_field): kfx [Q][nz][ny][nx+1], kfy [Q][nz][ny+1][nx], kfz [Q][nz+1][ny][nx];
+    Dirichlet data on the whole boundary.  The paper's Example 1 (Sec. 4) has Q = 2: kappa_0 = 1
+    and kappa_1 = g(x), A(mu) = A_0 + mu_1 A_1."""
+    nx, ny, nz = grid
+    Q, kfx, kfy, kfz = _faces(grid, kfx, kfy, kfz)
+    L = lib()
+    nnz = L.orc_csr_nnz(nx, ny, nz)
+    n = nx * ny * nz
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    vals = np.zeros((Q, nnz))
+    rc = L.orc_assemble_field(nx, ny, nz, Q, _p(kfx), _p(kfy), _p(kfz), _p(row_ptr), _p(col), _p(vals))
+    if rc != 0:
+        raise ValueError("orc_assemble_field failed: %d" % rc)
+    return Operator(tuple(grid), Q, row_ptr, col, vals)
+
+
+def boundary_size(grid) -> int:
+    """Values of Dirichlet data on the six boundary planes (the layout of orc_dirichlet_lift)."""
+    nx, ny, nz = grid
+    return 2 * (nz * ny + nz * nx + ny * nx)
+
+
+def dirichlet_lift(grid, kfx, kfy, kfz, gb) -> np.ndarray:
+    """lift [Q][n]: what Dirichlet data gb (six boundary planes, orc_dirichlet_lift's layout)
+    adds to the right-hand side through each term A_q."""
+    nx, ny, nz = grid
+    Q, kfx, kfy, kfz = _faces(grid, kfx, kfy, kfz)
+    gb = np.ascontiguousarray(gb, dtype=np.float64)
+    if gb.shape != (boundary_size(grid),):
+        raise ValueError("gb must have %d values" % boundary_size(grid))
+    out = np.zeros((Q, nx * ny * nz))
+    lib().orc_dirichlet_lift(nx, ny, nz, Q, _p(kfx), _p(kfy), _p(kfz), _p(gb), _p(out))
+    return out
 
 
 def assemble_mu(grid, mu, blocks=None, submap=None, Q=None, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)) -> Operator:

@@ -19,32 +19,43 @@ import time
 
 import numpy as np
 
-from . import assemble_mu
+from . import Operator, assemble_field, assemble_mu
 
 _STATE = {}
 
 
-def _init(grid, blocks, submap, Q, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0)):
+def _init(grid, blocks, submap, Q, kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0), fields=None):
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     _STATE["grid"], _STATE["blocks"], _STATE["submap"], _STATE["Q"] = grid, blocks, submap, Q
     _STATE["kscale"], _STATE["neumann"] = tuple(kscale), tuple(neumann)
+    _STATE["field_op"] = None if fields is None else assemble_field(grid, *fields)
+
+
+def _operator(mu):
+    """A(mu) as a one-term operator: assembled directly, or combined from the face-field terms."""
+    fo = _STATE.get("field_op")
+    if fo is not None:
+        return Operator(fo.grid, 1, fo.row_ptr, fo.col, fo.values(mu)[None, :])
+    return assemble_mu(_STATE["grid"], mu, blocks=_STATE["blocks"], submap=_STATE["submap"], Q=_STATE["Q"],
+                       kscale=_STATE["kscale"], neumann=_STATE["neumann"])
 
 
 def _solve(task):
     from . import mg
     mu, f, tol, u0 = task
-    op = assemble_mu(_STATE["grid"], mu, blocks=_STATE["blocks"], submap=_STATE["submap"], Q=_STATE["Q"],
-                     kscale=_STATE["kscale"], neumann=_STATE["neumann"])
+    op = _operator(mu)
     r = mg.mgcg(op, [1.0], f=f, u0=u0, tol=tol, max_iters=400)
     return r.u, r.iters, r.relres, r.status
 
 
 def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol=1e-13, processes=None,
-                        kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0), u0=None):
+                        kscale=(1.0, 1.0, 1.0), neumann=(0, 0, 0), u0=None, fields=None):
     """Oracle FP64 MGCG solutions u_b of A(mu_b) u = f_b (f: None = ones, [n] shared, or [B][n];
     kscale, neumann: the operator's anisotropy and Neumann faces, as oracle.assemble takes them;
-    u0: None (zero start) or [B][n] initial values computed by the oracle).
+    u0: None (zero start) or [B][n] initial values computed by the oracle; fields: None, or the
+    face coefficients (kfx, kfy, kfz) of oracle.assemble_field, mus then being the [B][Q]
+    coefficients of its terms).
     Returns (U [B][n], iters [B], relres [B], status [B], seconds, processes)."""
     mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
     B = mus.shape[0]
@@ -62,11 +73,12 @@ def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol
     try:
         tasks = [(mus[b], fb[b], tol, None if u0 is None else np.asarray(u0[b], dtype=np.float64)) for b in range(B)]
         if processes == 1:
-            _init(tuple(grid), blocks, submap, Q, kscale, neumann)
+            _init(tuple(grid), blocks, submap, Q, kscale, neumann, fields)
             out = [_solve(t) for t in tasks]
         else:
             with mp.get_context("spawn").Pool(processes, initializer=_init,
-                                              initargs=(tuple(grid), blocks, submap, Q, kscale, neumann)) as pool:
+                                              initargs=(tuple(grid), blocks, submap, Q, kscale, neumann,
+                                                        fields)) as pool:
                 out = pool.map(_solve, tasks, chunksize=1)
     finally:
         for k, v in saved.items():
@@ -82,12 +94,16 @@ def reference_solutions(grid, mus, blocks=None, submap=None, Q=None, f=None, tol
 
 
 def true_relres(grid, mus, U, blocks=None, submap=None, Q=None, f=None, kscale=(1.0, 1.0, 1.0),
-                neumann=(0, 0, 0)) -> np.ndarray:
+                neumann=(0, 0, 0), fields=None) -> np.ndarray:
     """||f_b - A(mu_b) u_b|| / ||f_b|| with the oracle's CSR operator, per instance."""
     mus = np.atleast_2d(np.asarray(mus, dtype=np.float64))
     out = np.empty(mus.shape[0])
+    fo = None if fields is None else assemble_field(grid, *fields)
     for b in range(mus.shape[0]):
-        op = assemble_mu(grid, mus[b], blocks=blocks, submap=submap, Q=Q, kscale=kscale, neumann=neumann)
+        if fo is not None:
+            op = Operator(fo.grid, 1, fo.row_ptr, fo.col, fo.values(mus[b])[None, :])
+        else:
+            op = assemble_mu(grid, mus[b], blocks=blocks, submap=submap, Q=Q, kscale=kscale, neumann=neumann)
         fb = np.ones(op.n) if f is None else (f[b] if np.ndim(f) == 2 else f)
         out[b] = np.linalg.norm(fb - op.matvec([1.0], U[b])) / np.linalg.norm(fb)
     return out
@@ -100,12 +116,13 @@ def relL2(U, U_ref) -> np.ndarray:
 
 
 def error_summary(grid, mus, U, U_ref, blocks=None, submap=None, Q=None, f=None, kscale=(1.0, 1.0, 1.0),
-                  neumann=(0, 0, 0)) -> dict:
+                  neumann=(0, 0, 0), fields=None) -> dict:
     """Per-instance relative L2 error of U against the oracle solutions U_ref and the oracle's
     true relative residual of U; max and mean of each, and the per-instance lists."""
     U = np.asarray(U, dtype=np.float64)
     err = relL2(U, U_ref)
-    res = true_relres(grid, mus, U, blocks=blocks, submap=submap, Q=Q, f=f, kscale=kscale, neumann=neumann)
+    res = true_relres(grid, mus, U, blocks=blocks, submap=submap, Q=Q, f=f, kscale=kscale, neumann=neumann,
+                      fields=fields)
     return {"n": int(U.shape[0]), "relL2_max": float(err.max()), "relL2_mean": float(err.mean()),
             "true_relres_max": float(res.max()), "true_relres_mean": float(res.mean()),
             "relL2": [float(x) for x in err], "true_relres": [float(x) for x in res]}

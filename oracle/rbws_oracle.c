@@ -136,6 +136,102 @@ int orc_assemble_ex(int nx, int ny, int nz, const uint8_t* map, int Q, const dou
   return pos == nnz ? 0 : -2;
 }
 
+/* The diffusion coefficient given at the cell faces (a coefficient that varies from node to
+ * node, as in the paper's Example 1, Sec. 4).  Node (i, j, k), 0-based, sits at
+ * ((i+1) hx, (j+1) hy, (k+1) hz) with h = 1/(n+1) per axis and Dirichlet data on the whole
+ * boundary.  The x face f (0..nx) of row (j, k) lies between nodes f-1 and f (node -1 and
+ * node nx being boundary points); kfx[q][k][j][f] is kappa_q there, and likewise
+ * kfy[q][k][f][i] (f = 0..ny) and kfz[q][f][j][i] (f = 0..nz).  The flux through a face is
+ * kappa_face (u_self - u_nb) / h_a^2; a boundary face adds kappa_face / h_a^2 to the
+ * diagonal (its boundary value goes to the right-hand side, orc_dirichlet_lift). */
+static double field_face(int nx, int ny, int nz, int q, const double* kfx, const double* kfy,
+                         const double* kfz, int i, int j, int k, int dir) {
+  /* dir: 0 west, 1 east, 2 south, 3 north, 4 down, 5 up */
+  switch (dir) {
+    case 0: return kfx[(((int64_t)q * nz + k) * ny + j) * (nx + 1) + i];
+    case 1: return kfx[(((int64_t)q * nz + k) * ny + j) * (nx + 1) + i + 1];
+    case 2: return kfy[(((int64_t)q * nz + k) * (ny + 1) + j) * nx + i];
+    case 3: return kfy[(((int64_t)q * nz + k) * (ny + 1) + j + 1) * nx + i];
+    case 4: return kfz[(((int64_t)q * (nz + 1) + k) * ny + j) * nx + i];
+    default: return kfz[(((int64_t)q * (nz + 1) + k + 1) * ny + j) * nx + i];
+  }
+}
+
+int orc_assemble_field(int nx, int ny, int nz, int Q, const double* kfx, const double* kfy,
+                       const double* kfz, int64_t* row_ptr, int32_t* col, double* vals) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t nnz = orc_csr_nnz(nx, ny, nz);
+  const double inv_h2[3] = {(double)(nx + 1) * (nx + 1), (double)(ny + 1) * (ny + 1),
+                            (double)(nz + 1) * (nz + 1)};
+  memset(vals, 0, sizeof(double) * (size_t)Q * (size_t)nnz);
+  int64_t pos = 0;
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        const int64_t row = ((int64_t)k * ny + j) * nx + i;
+        row_ptr[row] = pos;
+        /* the neighbour through each face, in increasing column order:
+         * down (z-1), south (y-1), west (x-1), self, east (x+1), north (y+1), up (z+1) */
+        const int dirs[7] = {4, 2, 0, -1, 1, 3, 5};
+        const int ddx[6] = {-1, 1, 0, 0, 0, 0}, ddy[6] = {0, 0, -1, 1, 0, 0}, ddz[6] = {0, 0, 0, 0, -1, 1};
+        const int axis[6] = {0, 0, 1, 1, 2, 2};
+        int64_t diag = -1;
+        for (int t = 0; t < 7; t++) {
+          const int d = dirs[t];
+          if (d < 0) {
+            diag = pos;
+            col[pos++] = (int32_t)row;
+            continue;
+          }
+          const int ii = i + ddx[d], jj = j + ddy[d], kk = k + ddz[d];
+          if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+          col[pos++] = (int32_t)(((int64_t)kk * ny + jj) * nx + ii);
+        }
+        /* values: every face adds to the diagonal; an interior face also gives -coef */
+        int64_t p = row_ptr[row];
+        for (int t = 0; t < 7; t++) {
+          const int d = dirs[t];
+          if (d < 0) { p++; continue; }
+          const int ii = i + ddx[d], jj = j + ddy[d], kk = k + ddz[d];
+          const int interior = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+          for (int q = 0; q < Q; q++) {
+            const double c = field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, d) * inv_h2[axis[d]];
+            vals[(int64_t)q * nnz + diag] += c;
+            if (interior) vals[(int64_t)q * nnz + p] -= c;
+          }
+          if (interior) p++;
+        }
+      }
+  row_ptr[n] = pos;
+  return pos == nnz ? 0 : -2;
+}
+
+void orc_dirichlet_lift(int nx, int ny, int nz, int Q, const double* kfx, const double* kfy,
+                        const double* kfz, const double* gb, double* lift) {
+  /* gb: the Dirichlet data on the six boundary planes, concatenated:
+   * x = 0 [nz][ny], x = 1 [nz][ny], y = 0 [nz][nx], y = 1 [nz][nx], z = 0 [ny][nx], z = 1 [ny][nx],
+   * each value at the boundary point facing an interior node across one face.
+   * lift[q][node] = sum over the node's boundary faces of kappa_q(face) / h_a^2 * g. */
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t ox0 = 0, ox1 = (int64_t)nz * ny, oy0 = 2 * (int64_t)nz * ny, oy1 = oy0 + (int64_t)nz * nx,
+                oz0 = oy1 + (int64_t)nz * nx, oz1 = oz0 + (int64_t)ny * nx;
+  const double ihx = (double)(nx + 1) * (nx + 1), ihy = (double)(ny + 1) * (ny + 1),
+               ihz = (double)(nz + 1) * (nz + 1);
+  for (int q = 0; q < Q; q++)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          double v = 0.0;
+          if (i == 0) v += field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, 0) * ihx * gb[ox0 + (int64_t)k * ny + j];
+          if (i == nx - 1) v += field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, 1) * ihx * gb[ox1 + (int64_t)k * ny + j];
+          if (j == 0) v += field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, 2) * ihy * gb[oy0 + (int64_t)k * nx + i];
+          if (j == ny - 1) v += field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, 3) * ihy * gb[oy1 + (int64_t)k * nx + i];
+          if (k == 0) v += field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, 4) * ihz * gb[oz0 + (int64_t)j * nx + i];
+          if (k == nz - 1) v += field_face(nx, ny, nz, q, kfx, kfy, kfz, i, j, k, 5) * ihz * gb[oz1 + (int64_t)j * nx + i];
+          lift[(int64_t)q * n + ((int64_t)k * ny + j) * nx + i] = v;
+        }
+}
+
 void orc_node_weights(int nx, int ny, int nz, const int* neumann, double* w) {
   /* volume of each node's control volume relative to a full cell */
   for (int k = 0; k < nz; k++)

@@ -60,6 +60,22 @@ int orc_assemble_ex(int nx, int ny, int nz, const uint8_t* map, int Q, const dou
                     const int* neumann, int64_t* row_ptr, int32_t* col, double* vals);
 /* Relative control volume of each node (1, 1/2 on a Neumann face, 1/4 on an
  * edge of two): the weight of the source term in the right-hand side. */
+/* The Q affine terms of an operator whose coefficient is given at the cell faces
+ * (kappa_q(x) varying from node to node, as in the paper's Example 1, Sec. 4, where
+ * kappa = 1 + mu_1 g(x)): Dirichlet data on the whole boundary, h = 1/(n+1), node
+ * (i, j, k) at ((i+1) hx, (j+1) hy, (k+1) hz).  kfx [Q][nz][ny][nx+1] holds kappa_q on the
+ * x faces (face f between nodes f-1 and f; faces 0 and nx touch the boundary), kfy
+ * [Q][nz][ny+1][nx], kfz [Q][nz+1][ny][nx] likewise.  Face coefficient kappa_face / h_a^2;
+ * the pattern and column order are those of orc_assemble_affine.  Returns 0. */
+int orc_assemble_field(int nx, int ny, int nz, int Q, const double* kfx, const double* kfy,
+                       const double* kfz, int64_t* row_ptr, int32_t* col, double* vals);
+/* The Dirichlet lift of the same operator: lift [Q][n], the part of the right-hand side that
+ * boundary data g gives through each term, sum over a node's boundary faces of
+ * kappa_q(face) / h_a^2 times g at the boundary point across that face.  gb holds g on the six
+ * boundary planes, concatenated: x = 0 and x = 1 ([nz][ny] each), y = 0 and y = 1 ([nz][nx]),
+ * z = 0 and z = 1 ([ny][nx]). */
+void orc_dirichlet_lift(int nx, int ny, int nz, int Q, const double* kfx, const double* kfy,
+                        const double* kfz, const double* gb, double* lift);
 void orc_node_weights(int nx, int ny, int nz, const int* neumann, double* w);
 
 /* CSR of A(mu) for one parameter, assembled directly from kappa = mu[map]

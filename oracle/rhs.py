@@ -106,3 +106,20 @@ def rb_start(basis: Basis, mu, f) -> np.ndarray:
     A = np.tensordot(np.asarray(mu, dtype=np.float64), basis.ANq, axes=1)
     c = np.linalg.solve(A, basis.W @ np.asarray(f, dtype=np.float64))
     return basis.W.T @ c
+
+
+def example1_rhs(F, L1, L2, mu) -> np.ndarray:
+    """Right-hand sides of the paper's Example 1 (Sec. 4) for parameters mu [B][2]: the source
+    F [n] plus the Dirichlet lift of g_D(mu) = (1 - mu_2) G1 + mu_2 G2 through
+    A(mu) = A_0 + mu_1 A_1, with L1 = dirichlet_lift(G1), L2 = dirichlet_lift(G2) ([2][n] each):
+    b = F + (1 - mu_2) (L1_0 + mu_1 L1_1) + mu_2 (L2_0 + mu_1 L2_1)."""
+    out = []
+    for m1, m2 in np.atleast_2d(mu):
+        out.append(F + (1.0 - m2) * (L1[0] + m1 * L1[1]) + m2 * (L2[0] + m1 * L2[1]))
+    return np.array(out)
+
+
+def example1_affine(mu) -> np.ndarray:
+    """theta_A [B][2] = (1, mu_1): the coefficients of A(mu) = A_0 + mu_1 A_1 in Example 1."""
+    mu = np.atleast_2d(mu)
+    return np.column_stack([np.ones(mu.shape[0]), mu[:, 0]])

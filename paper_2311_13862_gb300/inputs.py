@@ -15,6 +15,9 @@ finite differences on an interior grid, h = 1/(n+1)):
   3  128^3, 2x2x2 octants,               mu in [0.01, 100]^8, N <= 40, 256 train, 64 test, tol 1e-10
   4  workload 2 with a learned warm start (4096 surrogate samples)
   5  3x3x3 blocks, mu in [0.1, 10]^27, grids 96^3 / 128^3 / 256^3, N <= 60, 96 requests
+
+The paper's Example 1 (Sec. 4) is problem data here too: its coefficient field, boundary
+data and source sampled on the grid (example1_*), with mu uniform on [0, 2] x [0, 1].
 """
 from __future__ import annotations
 
@@ -115,3 +118,78 @@ def small(grid=(9, 7, 5), blocks=(2, 1, 1), lo=0.1, hi=10.0, n_max=6, n_train=16
           tol=1e-12, seed_base=11, name="small") -> Workload:
     """A tiny ragged workload for fast CPU and parity tests."""
     return Workload(name, tuple(grid), tuple(blocks), lo, hi, n_max, n_train, n_test, tol, seed_base)
+
+
+# ---------------------------------------------------------------------------
+# The paper's Example 1 (Sec. 4): -div(kappa grad u) = f on the unit cube with
+# kappa = 1 + mu_1 g(x), g = sin^2(20 pi (4 (x-1/2)^2 + (y-1/2)^2 + (z-1/2)^2)),
+# f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z), and Dirichlet data
+# g_D = (1 - mu_2) cos(10 pi (4 (x-1/2)^2 + (y-1/2)^2 + (z-1/2)^2)) + mu_2 cos(10 pi (x+y+z)),
+# mu in [0, 2] x [0, 1].  Sampled on an interior grid with h = 1/(n+1) per axis, node i
+# (0-based) at (i+1) h.  Coefficients are taken at the cell faces (face f of an axis at
+# (f + 1/2) h, f = 0..n); boundary data at the boundary points across each boundary face.
+# ---------------------------------------------------------------------------
+def _example1_g(x, y, z):
+    return np.sin(20.0 * np.pi * (4.0 * (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)) ** 2
+
+
+def _axis_nodes(n):
+    return np.arange(1, n + 1) / (n + 1)
+
+
+def _axis_faces(n):
+    return (np.arange(0, n + 1) + 0.5) / (n + 1)
+
+
+def example1_faces(grid):
+    """(kfx [2][nz][ny][nx+1], kfy [2][nz][ny+1][nx], kfz [2][nz+1][ny][nx]): the two affine
+    terms of Example 1's coefficient at the cell faces, kappa_0 = 1 and kappa_1 = g."""
+    nx, ny, nz = grid
+    xn, yn, zn = _axis_nodes(nx), _axis_nodes(ny), _axis_nodes(nz)
+    xf, yf, zf = _axis_faces(nx), _axis_faces(ny), _axis_faces(nz)
+    out = []
+    for xs, ys, zs in ((xf, yn, zn), (xn, yf, zn), (xn, yn, zf)):
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        out.append(np.stack([np.ones_like(X), _example1_g(X, Y, Z)]))
+    return tuple(out)
+
+
+def boundary_points(grid):
+    """Coordinates (X, Y, Z) of the boundary points facing the interior nodes, in the layout of
+    the six boundary planes: x = 0, x = 1 ([nz][ny] each), y = 0, y = 1 ([nz][nx]), z = 0,
+    z = 1 ([ny][nx])."""
+    nx, ny, nz = grid
+    xn, yn, zn = _axis_nodes(nx), _axis_nodes(ny), _axis_nodes(nz)
+    pts = []
+    for c in (0.0, 1.0):
+        Z, Y = np.meshgrid(zn, yn, indexing="ij")
+        pts.append((np.full_like(Y, c), Y, Z))
+    for c in (0.0, 1.0):
+        Z, X = np.meshgrid(zn, xn, indexing="ij")
+        pts.append((X, np.full_like(X, c), Z))
+    for c in (0.0, 1.0):
+        Y, X = np.meshgrid(yn, xn, indexing="ij")
+        pts.append((X, Y, np.full_like(X, c)))
+    return tuple(np.concatenate([p[a].ravel() for p in pts]) for a in range(3))
+
+
+def example1_boundary(grid):
+    """(G1, G2): the two affine parts of Example 1's Dirichlet data on the boundary planes,
+    g_D(mu) = (1 - mu_2) G1 + mu_2 G2."""
+    X, Y, Z = boundary_points(grid)
+    G1 = np.cos(10.0 * np.pi * (4.0 * (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2))
+    G2 = np.cos(10.0 * np.pi * (X + Y + Z))
+    return G1, G2
+
+
+def example1_source(grid):
+    """f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) at the interior nodes, [z][y][x] order."""
+    nx, ny, nz = grid
+    Z, Y, X = np.meshgrid(_axis_nodes(nz), _axis_nodes(ny), _axis_nodes(nx), indexing="ij")
+    return (3.0 * np.pi ** 2 * np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)).ravel()
+
+
+def example1_mu(seed: int, n: int) -> np.ndarray:
+    """n parameters (mu_1, mu_2) uniform on [0, 2] x [0, 1]."""
+    rng = np.random.default_rng(seed)
+    return np.column_stack([rng.uniform(0.0, 2.0, n), rng.uniform(0.0, 1.0, n)])
