@@ -229,6 +229,44 @@ RBWS_API rbws_status rbws_problem_create_ex(const rbws_grid* grid, const rbws_bl
                                             const uint8_t* subdomain_map, int32_t Q, const double* f_host,
                                             const rbws_axes* axes, int device, rbws_problem* out);
 RBWS_API void rbws_problem_destroy(rbws_problem p);
+/* A problem whose coefficient varies from node to node: A(mu) = sum_q mu_q A_q with A_q
+ * the 7-point operator of a diffusion coefficient kappa_q(x) given at the cell faces
+ * (the paper's Example 1, Sec. 4: kappa = 1 + mu_1 g(x), i.e. Q = 2, kappa_0 = 1,
+ * kappa_1 = g, mu = (1, mu_1)).  Dirichlet data on the whole boundary, h = 1/(n+1) per
+ * axis, node (i, j, k) (0-based) at ((i+1) hx, (j+1) hy, (k+1) hz).
+ *  - kfx: host [Q][nz][ny][nx+1], kappa_q on the x faces: face f (0..nx) of row (j, k)
+ *    lies between nodes f-1 and f, faces 0 and nx touch the boundary;
+ *  - kfy: host [Q][nz][ny+1][nx], kfz: host [Q][nz+1][ny][nx], likewise (all copied).
+ * The face coefficient is kappa_face / h_a^2; a boundary face adds it to the diagonal and
+ * its boundary value reaches the right-hand side through rbws_dirichlet_lift.  Every
+ * value must be finite and >= 0, and every node needs a positive diagonal for the
+ * coefficients mu the caller will pass (mu_q >= 0 with sum_q mu_q kappa_q > 0 keeps A(mu)
+ * symmetric positive definite).  f_host: host [n] or NULL for f = 1.  Each axis needs
+ * 2 <= n <= 256 (each node is its own coefficient class, 8-bit per axis); 1 <= Q <= 64.
+ * The solvers, warm starts, the greedy, L1ROC and the multigrid preconditioner (Galerkin
+ * coarse operators of every term, one coefficient row per coarse node) all apply; the
+ * per-instance coefficient tables take n x 8 values per instance.  Not supported:
+ * rbws_apply_operator_static (RBWS_ERR_UNSUPPORTED). */
+RBWS_API rbws_status rbws_problem_create_field(const rbws_grid* grid, int32_t Q, const double* kfx,
+                                               const double* kfy, const double* kfz, const double* f_host,
+                                               int device, rbws_problem* out);
+/* The Dirichlet lift of a problem made by rbws_problem_create_field: lift_out (device
+ * [Q][n] FP64, caller-owned) gets, per term q, the right-hand side that boundary data g
+ * adds through A_q: sum over a node's boundary faces of kappa_q(face) / h_a^2 times g at
+ * the boundary point across that face (the elimination of the boundary values from
+ * -div(kappa grad u) = f).  g_host: host values on the six boundary planes, concatenated:
+ * x = 0 and x = 1 ([nz][ny] each, at (0 or 1, y_j, z_k)), y = 0 and y = 1 ([nz][nx]),
+ * z = 0 and z = 1 ([ny][nx]), 2 (nz ny + nz nx + ny nx) values.  The right-hand side of
+ * A(mu) u = f + sum_q mu_q lift_q then holds affine data g(mu) = sum_k t_k(mu) G_k by
+ * linearity (rbws_affine_sources).  RBWS_ERR_UNSUPPORTED on other problems. */
+RBWS_API rbws_status rbws_dirichlet_lift(rbws_problem p, const double* g_host, void* lift_out);
+/* f_out[b] = sum_k theta[b][k] F[k] for B instances: F device [K][n] FP64, theta host
+ * [B][K], f_out device [B][n] FP64 (caller-owned; it must not overlap F).  1 <= K <= 64.
+ * Affine right-hand sides (a source plus Dirichlet lifts, Example 1 of Sec. 4) for
+ * rbws_solve_batch_rhs and rbws_offline_greedy_rhs. */
+RBWS_API rbws_status rbws_affine_sources(rbws_problem p, const void* F, int32_t K, const double* theta,
+                                         int32_t B, void* f_out);
+
 
 /* Problem sizes: n_dof, Q and the current reduced basis dimension N (0 if
  * none).  Any pointer may be NULL. */
@@ -519,11 +557,11 @@ RBWS_API rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* prob
                                          double* latency_ms_out);
 
 /* Checkpoint of the offline stage (the paper's offline/online split): writes
- * the problem description (grid, blocks or map, axes, f), the reduced basis W,
- * A_N^q, f_N and the surrogate network (if any) to `path` in a versioned
- * binary format (version 3; rbws_load also reads version 2, written before the
- * axes existed) with an FNV-1a checksum.  Synchronous; the problem is
- * unchanged. */
+ * the problem description (grid, blocks, map or face fields, axes, f), the
+ * reduced basis W, A_N^q, f_N and the surrogate network (if any) to `path` in a
+ * versioned binary format (version 3, or 4 for a face-field problem; rbws_load
+ * also reads version 2, written before the axes existed) with an FNV-1a
+ * checksum.  Synchronous; the problem is unchanged. */
 RBWS_API rbws_status rbws_save(rbws_problem p, const char* path);
 /* Creates a problem on `device` from a checkpoint written by rbws_save.
  * Returns RBWS_ERR_STATE with a message if the file is not a checkpoint, has

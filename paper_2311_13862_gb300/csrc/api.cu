@@ -151,6 +151,14 @@ struct rbws_problem_s {
   std::vector<uint8_t> h_map;  // explicit subdomain map [n] (empty: block rule)
   std::vector<uint8_t> h_segq; // explicit map: box (bx*by*bz segments) -> subdomain
   uint8_t* d_segq = nullptr;
+  // Face-field problems (rbws_problem_create_field): every node is its own class and the
+  // coefficient rows of each term, [Q][n][7] (-kW -kE -kS -kN -kD -kU D, already scaled by
+  // 1/h^2), are combined per instance by k_field_tables; the face arrays are kept for
+  // checkpoints (kfx | kfy | kfz, each [Q][...]).
+  bool field = false;
+  std::vector<double> h_frows;
+  double* d_frows = nullptr;
+  std::vector<double> h_faces;
   // L1ROC online data (Sec. 3.1): collocation nodes, P A_q W and P f, and T
   // with U = W T (snapshots U); empty unless the basis came from rbws_offline_l1roc
   struct L1Roc {
@@ -298,11 +306,15 @@ rbws_status coef_tables(rbws_problem p, const double* d_mu, int B, double** c64,
     *c32 = (float*)p->buf("coef32", sizeof(float) * ncls * kCoefStride * B, &err);
     if (err) return (rbws_status)err;
   }
-  const int8_t* kx = p->d_keys;
-  const int8_t* ky = kx + p->ax.key.size();
-  const int8_t* kz = ky + p->ay.key.size();
-  launch_coef_tables(p->geo, kx, ky, kz, p->bx, p->by, p->d_segq, p->sx, p->sy, p->sz, p->Q, d_mu, B, *c64,
-                     c32 ? *c32 : nullptr, p->cur);
+  if (p->field) {
+    launch_field_tables(p->Q, p->n, p->d_frows, d_mu, B, *c64, c32 ? *c32 : nullptr, p->cur);
+  } else {
+    const int8_t* kx = p->d_keys;
+    const int8_t* ky = kx + p->ax.key.size();
+    const int8_t* kz = ky + p->ay.key.size();
+    launch_coef_tables(p->geo, kx, ky, kz, p->bx, p->by, p->d_segq, p->sx, p->sy, p->sz, p->Q, d_mu, B, *c64,
+                       c32 ? *c32 : nullptr, p->cur);
+  }
   p->launches += 1;
   CK(cudaGetLastError());
   return RBWS_OK;
@@ -623,13 +635,26 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u,
   return RBWS_OK;
 }
 
+// The 27-wide rows of each affine term on the finest level, by class ([Q][ncls][27]):
+// from the block description, or, for a face-field problem, each node's 7-point row.
+std::vector<double> fine_rows(rbws_problem p) {
+  if (!p->field)
+    return fine_rows_q(p->ax, p->ay, p->az, p->bx, p->by, p->h_segq.empty() ? nullptr : p->h_segq.data(), p->Q,
+                       p->sx, p->sy, p->sz);
+  std::vector<double> tq((size_t)p->Q * p->n * 27, 0.0);
+  // table order -kW -kE -kS -kN -kD -kU D; 27-wide offsets (dz+1)*9 + (dy+1)*3 + (dx+1)
+  static const int o27[7] = {12, 14, 10, 16, 4, 22, 13};
+  for (size_t r = 0; r < (size_t)p->Q * p->n; r++)
+    for (int m = 0; m < 7; m++) tq[r * 27 + o27[m]] = p->h_frows[r * 7 + m];
+  return tq;
+}
+
 // The multigrid hierarchy of the problem (built on first use).
 rbws_status mg_plan(rbws_problem p, const MGPlan** out) {
   if (!p->mg_tried) {
     p->mg_tried = true;
     auto plan = std::make_unique<MGPlan>();
-    p->mg_err = mg_build_plan(p->ax, p->ay, p->az, p->bx, p->by, p->h_segq.empty() ? nullptr : p->h_segq.data(),
-                              p->Q, p->sx, p->sy, p->sz, plan.get());
+    p->mg_err = mg_build_plan(p->ax, p->ay, p->az, fine_rows(p), p->Q, plan.get());
     if (p->mg_err.empty()) p->mg = std::move(plan);
   }
   if (!p->mg) {
@@ -1637,6 +1662,94 @@ rbws_status rbws_problem_create(const rbws_grid* grid, const rbws_blocks* blocks
   return rbws_problem_create_ex(grid, blocks, subdomain_map, Q, f_host, nullptr, device, out);
 }
 
+// Device-side set-up shared by the problem constructors: streams, events, the class maps and
+// keys, the Geo view, f and its norm.  p holds the host description (grid, axes, classes);
+// on failure p is destroyed.
+static rbws_status problem_setup(rbws_problem p, const double* f_host, rbws_problem* out) {
+  const int device = p->device;
+  auto fail = [&](cudaError_t e, const char* w) {
+    cuda_fail(e, w);
+    rbws_problem_destroy(p);
+    return RBWS_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return fail(e, "cudaSetDevice");
+  if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming)) != cudaSuccess)
+    return fail(e, "cudaEventCreate");
+  if ((e = cudaMallocHost(&p->h_active, sizeof(int))) != cudaSuccess) return fail(e, "cudaMallocHost");
+  std::vector<uint8_t> cls;
+  cls.insert(cls.end(), p->ax.cls.begin(), p->ax.cls.end());
+  cls.insert(cls.end(), p->ay.cls.begin(), p->ay.cls.end());
+  cls.insert(cls.end(), p->az.cls.begin(), p->az.cls.end());
+  std::vector<int8_t> keys;
+  keys.insert(keys.end(), p->ax.key.begin(), p->ax.key.end());
+  keys.insert(keys.end(), p->ay.key.begin(), p->ay.key.end());
+  keys.insert(keys.end(), p->az.key.begin(), p->az.key.end());
+  if ((e = cudaMalloc(&p->d_cls, cls.size())) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->d_keys, keys.size())) != cudaSuccess) return fail(e, "cudaMalloc");
+  cudaMemcpy(p->d_cls, cls.data(), cls.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_keys, keys.data(), keys.size(), cudaMemcpyHostToDevice);
+  if (!p->h_segq.empty()) {
+    if ((e = cudaMalloc(&p->d_segq, p->h_segq.size())) != cudaSuccess) return fail(e, "cudaMalloc");
+    cudaMemcpy(p->d_segq, p->h_segq.data(), p->h_segq.size(), cudaMemcpyHostToDevice);
+  }
+  if (p->field) {
+    if ((e = cudaMalloc(&p->d_frows, sizeof(double) * p->h_frows.size())) != cudaSuccess)
+      return fail(e, "cudaMalloc");
+    cudaMemcpy(p->d_frows, p->h_frows.data(), sizeof(double) * p->h_frows.size(), cudaMemcpyHostToDevice);
+  }
+  Geo& g = p->geo;
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  g.ncx = p->ax.ncls();
+  g.ncy = p->ay.ncls();
+  g.ncz = p->az.ncls();
+  g.n = p->n;
+  g.cx = p->d_cls;
+  g.cy = p->d_cls + p->nx;
+  g.cz = p->d_cls + p->nx + p->ny;
+  std::vector<double> fw;
+  if (!f_host && (p->neumann[0] || p->neumann[1] || p->neumann[2])) {
+    // a unit source: the right-hand side is each node's relative control volume
+    fw.resize(p->n);
+    for (int k = 0; k < p->nz; k++)
+      for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++)
+          fw[((int64_t)k * p->ny + j) * p->nx + i] = (p->neumann[0] && i == p->nx - 1 ? 0.5 : 1.0) *
+                                                     (p->neumann[1] && j == p->ny - 1 ? 0.5 : 1.0) *
+                                                     (p->neumann[2] && k == p->nz - 1 ? 0.5 : 1.0);
+    f_host = fw.data();
+    p->default_f = true;
+  }
+  if (f_host) {
+    if ((e = cudaMalloc(&p->d_f, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc f");
+    cudaMemcpy(p->d_f, f_host, sizeof(double) * p->n, cudaMemcpyHostToDevice);
+    double s = 0.0;
+    for (int64_t i = 0; i < p->n; i++) s += f_host[i] * f_host[i];
+    p->fnorm = std::sqrt(s);
+  } else {
+    p->fnorm = std::sqrt((double)p->n);
+  }
+  if ((e = cudaMalloc(&p->d_ones, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc");
+  fill(p->d_ones, p->n, 1.0, p->stream);
+  if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(e, "set-up");
+  for (auto& te : p->tev)
+    if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
+  for (auto& te : p->mgev)
+    if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
+  p->cur = p->stream;
+  if (!(p->fnorm > 0.0)) {
+    set_error("rbws_problem_create: f must be nonzero");
+    rbws_problem_destroy(p);
+    return RBWS_ERR_INVALID_ARG;
+  }
+  *out = p;
+  return RBWS_OK;
+}
+
 rbws_status rbws_problem_create_ex(const rbws_grid* grid, const rbws_blocks* blocks,
                                    const uint8_t* subdomain_map, int32_t Q, const double* f_host,
                                    const rbws_axes* axes, int device, rbws_problem* out) {
@@ -1738,82 +1851,126 @@ rbws_status rbws_problem_create_ex(const rbws_grid* grid, const rbws_blocks* blo
     p->ay = make_axis(p->ny, p->by, p->neumann[1]);
     p->az = make_axis(p->nz, p->bz, p->neumann[2]);
   }
-  auto fail = [&](cudaError_t e, const char* w) {
-    cuda_fail(e, w);
-    rbws_problem_destroy(p);
-    return RBWS_ERR_CUDA;
-  };
-  cudaError_t e;
-  if ((e = cudaSetDevice(device)) != cudaSuccess) return fail(e, "cudaSetDevice");
-  if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess)
-    return fail(e, "cudaStreamCreate");
-  if ((e = cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming)) != cudaSuccess)
-    return fail(e, "cudaEventCreate");
-  if ((e = cudaMallocHost(&p->h_active, sizeof(int))) != cudaSuccess) return fail(e, "cudaMallocHost");
-  std::vector<uint8_t> cls;
-  cls.insert(cls.end(), p->ax.cls.begin(), p->ax.cls.end());
-  cls.insert(cls.end(), p->ay.cls.begin(), p->ay.cls.end());
-  cls.insert(cls.end(), p->az.cls.begin(), p->az.cls.end());
-  std::vector<int8_t> keys;
-  keys.insert(keys.end(), p->ax.key.begin(), p->ax.key.end());
-  keys.insert(keys.end(), p->ay.key.begin(), p->ay.key.end());
-  keys.insert(keys.end(), p->az.key.begin(), p->az.key.end());
-  if ((e = cudaMalloc(&p->d_cls, cls.size())) != cudaSuccess) return fail(e, "cudaMalloc");
-  if ((e = cudaMalloc(&p->d_keys, keys.size())) != cudaSuccess) return fail(e, "cudaMalloc");
-  cudaMemcpy(p->d_cls, cls.data(), cls.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_keys, keys.data(), keys.size(), cudaMemcpyHostToDevice);
-  if (!segq.empty()) {
-    p->h_segq = segq;
-    if ((e = cudaMalloc(&p->d_segq, segq.size())) != cudaSuccess) return fail(e, "cudaMalloc");
-    cudaMemcpy(p->d_segq, segq.data(), segq.size(), cudaMemcpyHostToDevice);
-  }
-  Geo& g = p->geo;
-  g.nx = p->nx;
-  g.ny = p->ny;
-  g.nz = p->nz;
-  g.ncx = p->ax.ncls();
-  g.ncy = p->ay.ncls();
-  g.ncz = p->az.ncls();
-  g.n = p->n;
-  g.cx = p->d_cls;
-  g.cy = p->d_cls + p->nx;
-  g.cz = p->d_cls + p->nx + p->ny;
-  std::vector<double> fw;
-  if (!f_host && (p->neumann[0] || p->neumann[1] || p->neumann[2])) {
-    // a unit source: the right-hand side is each node's relative control volume
-    fw.resize(p->n);
-    for (int k = 0; k < p->nz; k++)
-      for (int j = 0; j < p->ny; j++)
-        for (int i = 0; i < p->nx; i++)
-          fw[((int64_t)k * p->ny + j) * p->nx + i] = (p->neumann[0] && i == p->nx - 1 ? 0.5 : 1.0) *
-                                                     (p->neumann[1] && j == p->ny - 1 ? 0.5 : 1.0) *
-                                                     (p->neumann[2] && k == p->nz - 1 ? 0.5 : 1.0);
-    f_host = fw.data();
-    p->default_f = true;
-  }
-  if (f_host) {
-    if ((e = cudaMalloc(&p->d_f, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc f");
-    cudaMemcpy(p->d_f, f_host, sizeof(double) * p->n, cudaMemcpyHostToDevice);
-    double s = 0.0;
-    for (int64_t i = 0; i < p->n; i++) s += f_host[i] * f_host[i];
-    p->fnorm = std::sqrt(s);
-  } else {
-    p->fnorm = std::sqrt((double)p->n);
-  }
-  if ((e = cudaMalloc(&p->d_ones, sizeof(double) * p->n)) != cudaSuccess) return fail(e, "cudaMalloc");
-  fill(p->d_ones, p->n, 1.0, p->stream);
-  if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(e, "set-up");
-  for (auto& te : p->tev)
-    if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
-  for (auto& te : p->mgev)
-    if ((e = cudaEventCreate(&te)) != cudaSuccess) return fail(e, "cudaEventCreate");
-  p->cur = p->stream;
-  if (!(p->fnorm > 0.0)) {
-    set_error("rbws_problem_create: f must be nonzero");
-    rbws_problem_destroy(p);
+  p->h_segq = std::move(segq);
+  return problem_setup(p, f_host, out);
+}
+
+// One class per node along an axis (a face-field problem): class i for node i.
+static AxisClasses identity_axis(int n) {
+  AxisClasses a;
+  a.n = n;
+  a.b = n;
+  a.cls.resize(n);
+  for (int i = 0; i < n; i++) a.cls[i] = (uint8_t)i;
+  a.key.assign((size_t)3 * n, 0);  // unused: the tables come from the face fields
+  return a;
+}
+
+extern "C" rbws_status rbws_problem_create_field(const rbws_grid* grid, int32_t Q, const double* kfx,
+                                                 const double* kfy, const double* kfz, const double* f_host,
+                                                 int device, rbws_problem* out) {
+  if (!out || !grid || !kfx || !kfy || !kfz) {
+    set_error("rbws_problem_create_field: null argument");
     return RBWS_ERR_INVALID_ARG;
   }
-  *out = p;
+  *out = nullptr;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  if (nx < 2 || ny < 2 || nz < 2 || nx > 256 || ny > 256 || nz > 256 || Q < 1 || Q > kMaxQ) {
+    set_error("rbws_problem_create_field: need 2 <= n <= 256 per axis and 1 <= Q <= 64");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t sfx = (int64_t)nz * ny * (nx + 1), sfy = (int64_t)nz * (ny + 1) * nx, sfz = (int64_t)(nz + 1) * ny * nx;
+  for (const auto& arr : {std::make_pair(kfx, sfx), std::make_pair(kfy, sfy), std::make_pair(kfz, sfz)})
+    for (int64_t t = 0; t < (int64_t)Q * arr.second; t++)
+      if (!(arr.first[t] >= 0.0) || !std::isfinite(arr.first[t])) {
+        set_error("rbws_problem_create_field: face coefficients must be finite and >= 0");
+        return RBWS_ERR_INVALID_ARG;
+      }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    set_error("rbws_problem_create_field: CUDA device " + std::to_string(device) + " not available");
+    return RBWS_ERR_CUDA;
+  }
+  rbws_problem p = new rbws_problem_s();
+  p->device = device;
+  p->nx = nx;
+  p->ny = ny;
+  p->nz = nz;
+  p->Q = Q;
+  p->n = n;
+  p->field = true;
+  const double ihx = (double)(nx + 1) * (nx + 1), ihy = (double)(ny + 1) * (ny + 1), ihz = (double)(nz + 1) * (nz + 1);
+  p->sx = ihx;
+  p->sy = ihy;
+  p->sz = ihz;
+  p->ax = identity_axis(nx);
+  p->ay = identity_axis(ny);
+  p->az = identity_axis(nz);
+  p->h_faces.reserve((size_t)Q * (sfx + sfy + sfz));
+  p->h_faces.insert(p->h_faces.end(), kfx, kfx + Q * sfx);
+  p->h_faces.insert(p->h_faces.end(), kfy, kfy + Q * sfy);
+  p->h_faces.insert(p->h_faces.end(), kfz, kfz + Q * sfz);
+  // the scaled 7-point rows of each term: -kW -kE -kS -kN -kD -kU D
+  p->h_frows.assign((size_t)Q * n * 7, 0.0);
+  for (int q = 0; q < Q; q++)
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+          const double* fx = kfx + q * sfx + ((int64_t)k * ny + j) * (nx + 1);
+          const double kW = fx[i] * ihx, kE = fx[i + 1] * ihx;
+          const double kS = kfy[q * sfy + ((int64_t)k * (ny + 1) + j) * nx + i] * ihy;
+          const double kN = kfy[q * sfy + ((int64_t)k * (ny + 1) + j + 1) * nx + i] * ihy;
+          const double kD = kfz[q * sfz + ((int64_t)k * ny + j) * nx + i] * ihz;
+          const double kU = kfz[q * sfz + ((int64_t)(k + 1) * ny + j) * nx + i] * ihz;
+          double* r = &p->h_frows[((size_t)q * n + ((int64_t)k * ny + j) * nx + i) * 7];
+          r[0] = -kW;
+          r[1] = -kE;
+          r[2] = -kS;
+          r[3] = -kN;
+          r[4] = -kD;
+          r[5] = -kU;
+          r[6] = kW + kE + kS + kN + kD + kU;
+        }
+  return problem_setup(p, f_host, out);
+}
+
+extern "C" rbws_status rbws_dirichlet_lift(rbws_problem p, const double* g_host, void* lift_out) {
+  if (!p || !g_host || !lift_out) {
+    set_error("rbws_dirichlet_lift: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  if (!p->field) {
+    set_error("rbws_dirichlet_lift: the problem was not made by rbws_problem_create_field");
+    return RBWS_ERR_UNSUPPORTED;
+  }
+  cudaSetDevice(p->device);
+  const size_t nb = (size_t)2 * ((size_t)p->nz * p->ny + (size_t)p->nz * p->nx + (size_t)p->ny * p->nx);
+  int err = 0;
+  double* gb = (double*)p->buf("lift_g", sizeof(double) * nb, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(gb, g_host, sizeof(double) * nb, cudaMemcpyHostToDevice, p->stream));
+  launch_dirichlet_lift(p->geo, p->Q, p->d_frows, gb, (double*)lift_out, p->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->stream));
+  return RBWS_OK;
+}
+
+extern "C" rbws_status rbws_affine_sources(rbws_problem p, const void* F, int32_t K, const double* theta,
+                                           int32_t B, void* f_out) {
+  if (!p || !F || !theta || !f_out || K < 1 || K > 64 || B < 1) {
+    set_error("rbws_affine_sources: invalid argument");
+    return RBWS_ERR_INVALID_ARG;
+  }
+  cudaSetDevice(p->device);
+  int err = 0;
+  double* th = (double*)p->buf("aff_theta", sizeof(double) * (size_t)B * K, &err);
+  if (err) return (rbws_status)err;
+  CK(cudaMemcpyAsync(th, theta, sizeof(double) * (size_t)B * K, cudaMemcpyHostToDevice, p->stream));
+  launch_affine_sources(p->n, K, (const double*)F, th, B, (double*)f_out, p->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->stream));
   return RBWS_OK;
 }
 
@@ -1826,6 +1983,7 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_cls);
   cudaFree(p->d_keys);
   cudaFree(p->d_segq);
+  cudaFree(p->d_frows);
   p->mg.reset();
   cudaFree(p->d_f);
   cudaFree(p->d_ones);
@@ -2095,6 +2253,10 @@ rbws_status rbws_apply_operator_static(rbws_problem p, const double* mu, int32_t
       (precision != RBWS_FP64 && precision != RBWS_FP32_IR)) {
     set_error("rbws_apply_operator_static: invalid argument");
     return RBWS_ERR_INVALID_ARG;
+  }
+  if (p->field) {  // its per-node tables would not fit the static array's layout
+    set_error("rbws_apply_operator_static: not available for a face-field problem");
+    return RBWS_ERR_UNSUPPORTED;
   }
   StreamGuard sg(p, stream);
   const int8_t* kx = p->d_keys;
@@ -2548,9 +2710,7 @@ rbws_status rbws_offline_l1roc(rbws_problem p, const double* mu_train, int32_t n
   double* etad = err ? nullptr : (double*)p->buf("l1_eta", sizeof(double) * (size_t)n_train, &err);
   double* rel = err ? nullptr : (double*)p->buf("l1_rel", sizeof(double), &err);
   if (err) return (rbws_status)err;
-  const std::vector<double> rows =
-      fine_rows_q(p->ax, p->ay, p->az, p->bx, p->by, p->h_segq.empty() ? nullptr : p->h_segq.data(), Q, p->sx,
-                  p->sy, p->sz);
+  const std::vector<double> rows = fine_rows(p);
   std::vector<int64_t> pts_s, pts_r, pts;
   std::vector<double> T((size_t)n_max * n_max, 0.0), PAWq, Pf;
   std::vector<int32_t> sel(n_max, -1);
@@ -3322,12 +3482,13 @@ rbws_status rbws_solve_requests(int32_t n_req, const rbws_problem* probs, const 
 // surrogate network) and the problem description, so a later process can
 // solve online without repeating the offline stage.
 //
-// File layout (little endian): "RBWSPRB1", u32 version = 2, i32 nx ny nz bx
-// by bz Q has_f N net_H net_N has_map, f64 mu_lo mu_hi, u64 payload bytes,
-// then the payload: the subdomain map [n] (u8, if has_map; bx by bz are then
-// ignored), f [n] (if has_f), W [N][n], ANq [Q][N][N], fN [N] (f64), network
-// parameters [P] and coefficient scales [net_N] (f32), then u64 FNV-1a of
-// the payload.
+// File layout (little endian): "RBWSPRB1", u32 version (2, 3 or 4), i32 nx ny
+// nz bx by bz Q has_f N net_H net_N has_map, f64 mu_lo mu_hi, u64 payload
+// bytes, then the payload: the axes (rbws_axes, version >= 3), the face arrays
+// kfx | kfy | kfz (f64, if has_map = 2: a face-field problem, version 4), the
+// subdomain map [n] (u8, if has_map = 1; bx by bz are then ignored), f [n] (if
+// has_f), W [N][n], ANq [Q][N][N], fN [N] (f64), network parameters [P] and
+// coefficient scales [net_N] (f32), then u64 FNV-1a of the payload.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -3363,7 +3524,9 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   const int N = p->N;
   CkptHeader h{};
   std::memcpy(h.magic, "RBWSPRB1", 8);
-  h.version = 3;  // 3: the payload starts with the axes (kappa_scale[3], neumann_hi[3], a zero int32)
+  // 3: the payload starts with the axes (kappa_scale[3], neumann_hi[3], a zero int32);
+  // 4: a face-field problem (has_map = 2), its face arrays following the axes
+  h.version = p->field ? 4 : 3;
   h.nx = p->nx;
   h.ny = p->ny;
   h.nz = p->nz;
@@ -3372,7 +3535,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   h.bz = p->bz;
   h.Q = p->Q;
   h.has_f = p->d_f != nullptr && !p->default_f;
-  h.has_map = !p->h_map.empty();
+  h.has_map = p->field ? 2 : !p->h_map.empty();
   h.N = N;
   h.net_H = p->d_w32 ? p->net_H : 0;
   h.net_N = p->d_w32 ? p->net_N : 0;
@@ -3388,8 +3551,8 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
   }
   const size_t szA = sizeof(double) * (N > 0 ? p->h_ANq.size() : 0), szF = sizeof(double) * (N > 0 ? N : 0);
   rbws_axes axes{{p->kscale[0], p->kscale[1], p->kscale[2]}, {p->neumann[0], p->neumann[1], p->neumann[2]}, 0};
-  h.payload = sizeof(axes) + p->h_map.size() + sizeof(double) * (f.size() + W.size()) + szA + szF +
-              sizeof(float) * (params.size() + scale.size());
+  h.payload = sizeof(axes) + sizeof(double) * p->h_faces.size() + p->h_map.size() +
+              sizeof(double) * (f.size() + W.size()) + szA + szF + sizeof(float) * (params.size() + scale.size());
   FILE* fp = std::fopen(path, "wb");
   if (!fp) {
     set_error(std::string("rbws_save: cannot open ") + path);
@@ -3403,6 +3566,7 @@ extern "C" rbws_status rbws_save(rbws_problem p, const char* path) {
     fnv.add(d, bytes);
   };
   put(&axes, sizeof(axes));
+  put(p->h_faces.data(), sizeof(double) * p->h_faces.size());
   put(p->h_map.data(), p->h_map.size());
   put(f.data(), sizeof(double) * f.size());
   put(W.data(), sizeof(double) * W.size());
@@ -3439,9 +3603,11 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
     return RBWS_ERR_STATE;
   };
   if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "RBWSPRB1", 8) != 0) return fail("not a checkpoint");
-  if (h.version != 2 && h.version != 3) return fail("unsupported version");
+  if (h.version < 2 || h.version > 4) return fail("unsupported version");
+  const bool field = h.has_map == 2;
   if (h.nx < 2 || h.ny < 2 || h.nz < 2 || h.nx > kMaxAxis || h.ny > kMaxAxis || h.nz > kMaxAxis ||
-      h.N < 0 || h.N > 160 || h.Q < 1 || h.Q > kMaxQ || (h.has_map != 0 && h.has_map != 1) ||
+      h.N < 0 || h.N > 160 || h.Q < 1 || h.Q > kMaxQ || (h.has_map != 0 && h.has_map != 1 && !field) ||
+      (field && (h.version < 4 || h.nx > 256 || h.ny > 256 || h.nz > 256)) ||
       (!h.has_map && h.Q != h.bx * h.by * h.bz) || h.net_H < 0 || h.net_H > 4096 ||
       (h.net_H > 0 && h.net_N != h.N))
     return fail("corrupt header");
@@ -3449,11 +3615,17 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
   const int64_t P = h.net_H ? (int64_t)h.net_H * h.Q + h.net_H + 2 * ((int64_t)h.net_H * h.net_H + h.net_H) +
                                   (int64_t)h.N * h.net_H + h.N
                             : 0;
-  const uint64_t expect = (h.version >= 3 ? sizeof(rbws_axes) : 0) + (h.has_map ? (uint64_t)n : 0) +
+  const uint64_t nfaces = field ? (uint64_t)h.Q * ((uint64_t)h.nz * h.ny * (h.nx + 1) +
+                                                   (uint64_t)h.nz * (h.ny + 1) * h.nx +
+                                                   (uint64_t)(h.nz + 1) * h.ny * h.nx)
+                                 : 0;
+  const uint64_t expect = (h.version >= 3 ? sizeof(rbws_axes) : 0) + sizeof(double) * nfaces +
+                          (h.has_map == 1 ? (uint64_t)n : 0) +
                           sizeof(double) * ((h.has_f ? n : 0) + (uint64_t)h.N * n + (uint64_t)h.Q * h.N * h.N + h.N) +
                           sizeof(float) * (P + h.net_N);
   if (h.payload != expect) return fail("payload size does not match the header");
-  std::vector<uint8_t> map(h.has_map ? n : 0);
+  std::vector<uint8_t> map(h.has_map == 1 ? n : 0);
+  std::vector<double> faces(nfaces);
   std::vector<double> f(h.has_f ? n : 0), W((size_t)h.N * n), ANq((size_t)h.Q * h.N * h.N), fN(h.N);
   std::vector<float> params(P), scale(h.net_N);
   Fnv fnv;
@@ -3465,6 +3637,7 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
   };
   rbws_axes axes{{1.0, 1.0, 1.0}, {0, 0, 0}, 0};
   if (h.version >= 3) get(&axes, sizeof(axes));
+  get(faces.data(), sizeof(double) * faces.size());
   get(map.data(), map.size());
   get(f.data(), sizeof(double) * f.size());
   get(W.data(), sizeof(double) * W.size());
@@ -3482,8 +3655,16 @@ extern "C" rbws_status rbws_load(const char* path, int device, rbws_problem* out
   rbws_grid g{h.nx, h.ny, h.nz};
   rbws_blocks bl{h.bx, h.by, h.bz};
   rbws_problem p = nullptr;
-  rbws_status rc = rbws_problem_create_ex(&g, h.has_map ? nullptr : &bl, h.has_map ? map.data() : nullptr, h.Q,
-                                          h.has_f ? f.data() : nullptr, &axes, device, &p);
+  rbws_status rc;
+  if (field) {
+    const double* kfx = faces.data();
+    const double* kfy = kfx + (size_t)h.Q * h.nz * h.ny * (h.nx + 1);
+    const double* kfz = kfy + (size_t)h.Q * h.nz * (h.ny + 1) * h.nx;
+    rc = rbws_problem_create_field(&g, h.Q, kfx, kfy, kfz, h.has_f ? f.data() : nullptr, device, &p);
+  } else {
+    rc = rbws_problem_create_ex(&g, h.has_map ? nullptr : &bl, h.has_map ? map.data() : nullptr, h.Q,
+                                h.has_f ? f.data() : nullptr, &axes, device, &p);
+  }
   if (rc != RBWS_OK) return rc;
   if (h.N > 0 && (rc = rbws_set_basis(p, h.N, W.data(), ANq.data(), fN.data())) != RBWS_OK) {
     rbws_problem_destroy(p);

@@ -174,6 +174,17 @@ void launch_coef_tables(const Geo& g, const int8_t* keys_x, const int8_t* keys_y
                         const int8_t* keys_z, int bx, int by, const uint8_t* segq, double sx,
                         double sy, double sz, int Q, const double* mu, int B, double* coef64,
                         float* coef32, cudaStream_t s);
+// Tables of a face-field problem (one class per node): coef[b][node] = sum_q mu[b][q]
+// rows[q][node] for the 7 stencil values, entry 7 = 1 / D (FP64 and, if coef32, FP32).
+void launch_field_tables(int Q, int64_t n, const double* rows, const double* mu, int B, double* coef64,
+                         float* coef32, cudaStream_t s);
+// lift[q][node] = sum over the node's boundary faces of -rows[q][node][face] * g there;
+// gb: the six boundary planes (device), see rbws_dirichlet_lift.
+void launch_dirichlet_lift(const Geo& g, int Q, const double* rows, const double* gb, double* lift,
+                           cudaStream_t s);
+// out[b] = sum_k theta[b][k] F[k], F [K][n], theta [B][K] (device).
+void launch_affine_sources(int64_t n, int K, const double* F, const double* theta, int B, double* out,
+                           cudaStream_t s);
 
 // y = A x in the mu-interleaved layout [n][B] (instance fastest); coef: the planar
 // tables [B][ncls][8], coefI: device scratch of ncls * 8 * B elements for their
@@ -400,11 +411,12 @@ struct MGPlan {
   ~MGPlan();
 };
 
-// Builds the hierarchy from the finest grid's axis classes; "" or the reason
-// multigrid is not available for this grid.  Device copies are made here.
-std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az, int bx,
-                          int by, const uint8_t* segq_host, int Q, double sx, double sy, double sz,
-                          MGPlan* plan);
+// Builds the hierarchy from the finest grid's axis classes and the 27-wide rows of
+// each affine term on it by class ([Q][ncls][27], fine_rows_q or a face-field
+// problem's node rows); "" or the reason multigrid is not available for this grid.
+// Device copies are made here.
+std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az,
+                          std::vector<double> fine_tq, int Q, MGPlan* plan);
 
 // Device view of one level for the V-cycle kernels (element type: the batch's).
 struct MGLevel {

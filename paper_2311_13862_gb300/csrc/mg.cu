@@ -124,9 +124,8 @@ MGPlan::~MGPlan() {
   cudaFree(d_a0q);
 }
 
-std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az, int bx,
-                          int by, const uint8_t* segq, int Q, double sx, double sy, double sz,
-                          MGPlan* plan) {
+std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const AxisClasses& az,
+                          std::vector<double> fine_tq, int Q, MGPlan* plan) {
   // level grids, finest first
   std::vector<std::array<int, 3>> dims{{ax.n, ay.n, az.n}};
   for (;;) {
@@ -148,7 +147,7 @@ std::string mg_build_plan(const AxisClasses& ax, const AxisClasses& ay, const Ax
   F.n = (int64_t)F.nx * F.ny * F.nz;
   F.cx = ax.cls, F.cy = ay.cls, F.cz = az.cls;
   F.ncx = ax.ncls(), F.ncy = ay.ncls(), F.ncz = az.ncls();
-  F.tq = fine_rows_q(ax, ay, az, bx, by, segq, Q, sx, sy, sz);
+  F.tq = std::move(fine_tq);
   // coarse levels: classes and Galerkin rows from the next finer level
   for (int i = plan->J - 1; i >= 0; i--) {
     const MGPlan::Level& f = plan->lv[i + 1];

@@ -79,6 +79,9 @@ def _lib():
         L.rbws_problem_create_ex.argtypes = [C.POINTER(rbws_grid), C.POINTER(rbws_blocks), P, i32, P,
                                              C.POINTER(rbws_axes), C.c_int, C.POINTER(P)]
         L.rbws_gaussian_source_ex.argtypes = [P, P, i32, P]
+        L.rbws_problem_create_field.argtypes = [C.POINTER(rbws_grid), i32, P, P, P, P, C.c_int, C.POINTER(P)]
+        L.rbws_dirichlet_lift.argtypes = [P, P, P]
+        L.rbws_affine_sources.argtypes = [P, P, i32, P, i32, P]
         L.rbws_problem_destroy.argtypes = [P]
         L.rbws_problem_info.argtypes = [P, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)]
         L.rbws_apply_operator.argtypes = [P, P, i32, P, P, i32, P]
@@ -177,6 +180,36 @@ def rbws_problem_create(grid, blocks, Q=None, f=None, device=0, subdomain_map=No
         _check(_lib().rbws_problem_create_ex(C.byref(g), bref, mp, Q, _hp(fh), C.byref(ax), device, C.byref(h)),
                "rbws_problem_create_ex")
     return h
+
+
+def rbws_problem_create_field(grid, kfx, kfy, kfz, f=None, device=0):
+    """A problem whose coefficient is given at the cell faces per affine term: kfx [Q][nz][ny][nx+1],
+    kfy [Q][nz][ny+1][nx], kfz [Q][nz+1][ny][nx] (host arrays, copied)."""
+    nx, ny, nz = grid
+    kfx = _host(kfx)
+    Q = kfx.shape[0]
+    kfx = kfx.reshape(Q, nz, ny, nx + 1)
+    kfy = _host(kfy).reshape(Q, nz, ny + 1, nx)
+    kfz = _host(kfz).reshape(Q, nz + 1, ny, nx)
+    fh = None if f is None else _host(f)
+    h = C.c_void_p()
+    _check(_lib().rbws_problem_create_field(C.byref(rbws_grid(*grid)), Q, _hp(kfx), _hp(kfy), _hp(kfz), _hp(fh),
+                                            device, C.byref(h)), "rbws_problem_create_field")
+    return h, Q
+
+
+def rbws_dirichlet_lift(h, g, lift_out):
+    """lift_out (CUDA float64 [Q][n]) = the right-hand side that Dirichlet data g (host, the six
+    boundary planes x=0, x=1, y=0, y=1, z=0, z=1) adds through each term of a face-field problem."""
+    gh = _host(g)
+    _check(_lib().rbws_dirichlet_lift(h, _hp(gh), _dp(lift_out)), "rbws_dirichlet_lift")
+
+
+def rbws_affine_sources(h, F, theta, f_out):
+    """f_out[b] = sum_k theta[b][k] F[k]: F CUDA float64 [K][n], theta host [B][K], f_out CUDA [B][n]."""
+    th = _host(np.atleast_2d(theta))
+    _check(_lib().rbws_affine_sources(h, _dp(F), th.shape[1], _hp(th), th.shape[0], _dp(f_out)),
+           "rbws_affine_sources")
 
 
 def rbws_problem_destroy(h):
@@ -484,6 +517,14 @@ class Problem:
             self.h = handle
         else:
             self.h = rbws_problem_create(grid, self.blocks, self.Q, f, device, subdomain_map, kappa_scale, neumann)
+
+    @classmethod
+    def field(cls, grid, kfx, kfy, kfz, f=None, device=0):
+        """A face-field problem (rbws_problem_create_field)."""
+        h, Q = rbws_problem_create_field(grid, kfx, kfy, kfz, f, device)
+        obj = cls.__new__(cls)
+        obj.grid, obj.blocks, obj.n, obj.Q, obj.h = tuple(grid), None, grid[0] * grid[1] * grid[2], Q, h
+        return obj
 
     @classmethod
     def load(cls, path, device=0):
