@@ -459,6 +459,121 @@ def bench_c3(args):
     P.close()
 
 
+def bench_ex1(args):
+    """The paper's Example 1 (Sec. 4) on a 64^3 interior grid (262,144 DoFs): kappa = 1 +
+    mu_1 g(x) given at the cell faces (two affine terms), Dirichlet data (1 - mu_2) G1 + mu_2 G2
+    eliminated into the right-hand side, source 3 pi^2 sin sin sin, mu uniform on [0,2] x [0,1].
+    Offline: greedy over 70 training mu (the paper's training-set size), each with its own
+    right-hand side, N <= 20.  Each step forms the 256 right-hand sides on the device
+    (rbws_affine_sources: source + lifts) and solves them to rel-res 1e-10.  Headline: Galerkin
+    start with the FP64 MG-PCG.  The solution depends smoothly on mu_1 and affinely on mu_2, so
+    the reduced space alone meets the tolerance for almost every instance; the mixed-precision
+    start (an FP32 lift) is accurate only to FP32 rounding and needs a few V-cycles more, and
+    with per-node coefficient tables the FP32 iteration saves little traffic.  Arms: FP32
+    refinement from the Galerkin start, zero starts in both precisions.  Every solution is
+    measured against the oracle's FP64 solution."""
+    import torch
+    from paper_2311_13862_gb300 import build, inputs, rbws
+    grid, n_max, n_train, tol = (64, 64, 64), 20, 70, 1e-10
+    B = args.batch or 256
+    mu = inputs.example1_mu(2007, B)
+    mu_t = inputs.example1_mu(1007, n_train)
+    m1, m2 = mu[:, 0], mu[:, 1]
+    th_f = np.column_stack([np.ones(B), 1.0 - m2, m1 * (1.0 - m2), m2, m1 * m2])
+    th = np.column_stack([np.ones(B), m1])
+    tt1, tt2 = mu_t[:, 0], mu_t[:, 1]
+    th_ft = np.column_stack([np.ones(n_train), 1.0 - tt2, tt1 * (1.0 - tt2), tt2, tt1 * tt2])
+    th_t = np.column_stack([np.ones(n_train), tt1])
+    faces = inputs.example1_faces(grid)
+    G1, G2 = inputs.example1_boundary(grid)
+    U_ref, ref_info, F_ref = None, None, None
+    if not args.no_oracle_check:
+        import oracle as O
+        from oracle import batch as O_batch
+        from oracle import rhs as O_rhs
+        L1, L2 = (O.dirichlet_lift(grid, *faces, G) for G in (G1, G2))
+        F_ref = O_rhs.example1_rhs(inputs.example1_source(grid), L1, L2, mu)
+        U_ref, _, r_rel, r_st, r_s, r_p = O_batch.reference_solutions(grid, th, f=F_ref, tol=1e-12, fields=faces)
+        ref_info = {"solver": "oracle MGCG (FP64) from zero", "tol": 1e-12, "relres_max": float(r_rel.max()),
+                    "all_converged": bool(np.all(r_st == 0)), "processes": r_p, "seconds": r_s}
+    build.build()
+    torch.cuda.set_device(0)
+    P = rbws.Problem.field(grid, *faces)
+    L = torch.empty((2, 2, P.n), dtype=torch.float64, device="cuda")
+    rbws.rbws_dirichlet_lift(P.h, G1, L[0])
+    rbws.rbws_dirichlet_lift(P.h, G2, L[1])
+    Fd = torch.from_numpy(inputs.example1_source(grid)).cuda()
+    Fk = torch.stack([Fd, L[0, 0], L[0, 1], L[1, 0], L[1, 1]]).contiguous()
+    t0 = time.perf_counter()
+    ft = torch.empty((n_train, P.n), dtype=torch.float64, device="cuda")
+    rbws.rbws_affine_sources(P.h, Fk, th_ft, ft)
+    N, sel, eta = rbws.rbws_offline_greedy_rhs(P.h, th_t, ft, n_max, 0.0, 1e-12)
+    torch.cuda.synchronize()
+    t_off = time.perf_counter() - t0
+    del ft
+    f = torch.empty((B, P.n), dtype=torch.float64, device="cuda")
+    u = torch.empty_like(f)
+    M, FP32, FP64 = rbws.PREC_MG, rbws.FP32_IR, rbws.FP64
+    HEAD = "mgcg_galerkin_fp64"
+    arm_list = [(HEAD, rbws.WARM_GALERKIN, FP64), ("mgcg_galerkin_fp32ir", rbws.WARM_GALERKIN, FP32),
+                ("mgcg_zero_fp32ir", rbws.WARM_ZERO, FP32), ("mgcg_zero_fp64", rbws.WARM_ZERO, FP64)]
+    if args.arm_steps == 0:
+        arm_list = arm_list[:1]
+    arms, head_err, clocks = {}, None, None
+
+    def step(warm, opt):
+        rbws.rbws_affine_sources(P.h, Fk, th_f, f)
+        return rbws.rbws_solve_batch_rhs(P.h, th, f, tol, warm, u, opt)
+
+    for name, warm, pr in arm_list:
+        head = name == HEAD
+        steps = args.steps if head else max(1, args.arm_steps)
+        opt = rbws.rbws_options_default(precision=pr, precond=M)
+        for _ in range(args.warmup if head else 1):
+            step(warm, opt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record()
+            for _ in range(steps):
+                rc, it, rel, st = step(warm, opt)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        arms[name] = {"solves_per_s": B / (ms / 1e3), "ms_per_step": ms, "iters_mean": float(np.mean(it)),
+                      "iters_max": int(np.max(it)), "relres_max": float(np.max(rel)),
+                      "all_converged": bool(np.all(st == 0))}
+        if head:
+            clocks = clk.summary()
+        if U_ref is not None:
+            uh = u.cpu().numpy()
+            if head:
+                es = O_batch.error_summary(grid, th, uh, U_ref, f=F_ref, fields=faces)
+                head_err = {k: v for k, v in es.items() if k not in ("relL2", "true_relres")}
+                head_err["reference"] = ref_info
+                arms[name]["oracle_relL2_max"], arms[name]["oracle_relL2_mean"] = es["relL2_max"], es["relL2_mean"]
+            else:
+                e = O_batch.relL2(uh, U_ref)
+                arms[name]["oracle_relL2_max"], arms[name]["oracle_relL2_mean"] = float(e.max()), float(e.mean())
+    head = arms[HEAD]
+    line = {"metric": METRIC, "value": head["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "the paper's Example 1 (Sec. 4) on a 64^3 interior grid (262,144 DoFs): kappa = "
+                                   "1 + mu_1 sin^2(20 pi r(x)) at the cell faces, affine Dirichlet data, mu uniform "
+                                   "on [0,2]x[0,1], RB N<=20 by greedy over 70 training mu, %d test mu per step; "
+                                   "each step forms the right-hand sides on the device and solves them from the "
+                                   "Galerkin start with FP64 MG-PCG to rel-res 1e-10" % B,
+                       "batch_per_gpu": B, "N": int(N), "warm": "galerkin", "precision": "fp64",
+                       "precond": "mg", "tol": tol, "l2": "no flush: solver working set > 129 MB L2"},
+            "clocks": clocks, "arms": arms, "t_off_s": t_off, "greedy_eta_last": float(eta[-1]),
+            "iters_mean": head["iters_mean"], "relres_max": head["relres_max"], "oracle_error": head_err}
+    if "mgcg_zero_fp64" in arms:
+        line["speedup_vs_mgcg_zero_fp64"] = head["solves_per_s"] / arms["mgcg_zero_fp64"]["solves_per_s"]
+    print(json.dumps(line), flush=True)
+    P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,10 +592,10 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="parameters per GPU and step (0: the workload's 256)")
     ap.add_argument("--mlp-epochs", type=int, default=2000,
                     help="epochs of the learned warm start's training (0: skip the learned arms)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "c2g"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5", "c2g", "ex1"],
                     help="c2: the 64^3 batched workload (default line); c3: 128^3 octants, contrast 1e4, 64 mu; "
                          "c5: 96 requests on 96^3/128^3/256^3; c2g: the 64^3 operator with a Gaussian source "
-                         "per parameter")
+                         "per parameter; ex1: the paper's Example 1 on 64^3")
     ap.add_argument("--c5-train", type=int, default=256, help="greedy training parameters per grid (c5)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in FP32 tile/schedule instead of the autotuned one")
@@ -493,6 +608,8 @@ def main():
         return reference_arm(args)
     if args.workload == "c5":
         return bench_requests(args)
+    if args.workload == "ex1":
+        return bench_ex1(args)
     if args.workload == "c2g":
         return bench_gaussian(args)
     if args.workload == "c3":
