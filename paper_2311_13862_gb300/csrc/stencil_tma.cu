@@ -575,17 +575,21 @@ __global__ void __launch_bounds__(256, 3)
       issue(j);
       n_issued = j + 1;
     }
-  // duties: own group; extra-row group (tid < TXT) or extra-column node (the
-  // next TY + 1 threads); coarse column (every thread: 2 TXT x TY/2 of them)
+  // duties: own group; at most one extra node (the TXN nodes of the extra row, then
+  // the TY + 1 of the extra column), extra node d going to lane d / warps of warp
+  // d % warps, so that every warp takes about the same share and runs the one-node
+  // path once per plane; coarse column (every thread: 2 TXT x TY/2 of them)
   const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
   const int i = x0 + lx, j = y0 + ly;
   const bool own = i < g.nx && j < g.ny;
   const int xo = (ly + 1) * PW + 4 + lx, ro = ly * RP + lx;
-  const int ex_kind = tid < TXT ? 1 : (tid < TXT + TY + 1 ? 2 : 0);
-  const int exl = ex_kind == 1 ? 4 * tid : TXN, eyl = ex_kind == 1 ? TY : tid - TXT;
+  const int nthr = TXT * TY;
+  const int dix = (nthr & 31) == 0 ? (tid & 31) * (nthr >> 5) + (tid >> 5) : tid;
+  const bool ex_duty = dix < TXN + TY + 1;
+  const int exl = dix < TXN ? dix : TXN, eyl = dix < TXN ? TY : dix - TXN;
   const int exi = x0 + exl, exj = y0 + eyl;
-  const bool ex_in = ex_kind != 0 && exi < g.nx && exj < g.ny;
-  float* exc = exc_all + (ex_kind == 1 ? 4 * tid : TXN + eyl) * 8;
+  const bool ex_in = ex_duty && exi < g.nx && exj < g.ny;
+  float* exc = exc_all + (dix < TXN ? dix : TXN + eyl) * 8;
   const int Il = tid % (2 * TXT), Jl = tid / (2 * TXT);
   const int I = x0 / 2 + Il, J = y0 / 2 + Jl;
   const bool cown = I < m.cnx && J < m.cny;
@@ -645,36 +649,26 @@ __global__ void __launch_bounds__(256, 3)
           r = make_float4(y[0], y[1], y[2], y[3]);
         }
         *reinterpret_cast<float4*>(Rz + ro) = r;
-        if (ex_kind != 0) {
-          const int nn = ex_kind == 1 ? 4 : 1;
+        if (ex_duty) {
           if (ex_in && zcl != ex_zcls) {  // refresh the cached coefficients at a z class change
             ex_zcls = zcl;
-            for (int e = 0; e < nn; e++) {
-              const float* row = cb + (((int64_t)zcl * g.ncy + g.cy[exj]) * g.ncx + g.cx[exi + e]) * kCoefStride;
+            const float* row = cb + (((int64_t)zcl * g.ncy + g.cy[exj]) * g.ncx + g.cx[exi]) * kCoefStride;
 #pragma unroll
-              for (int q = 0; q < 7; q++) exc[e * 8 + q] = row[q];
-            }
+            for (int q = 0; q < 7; q++) exc[q] = row[q];
           }
           const int o = (eyl + 1) * PW + 4 + exl;
-          float rv[4] = {0.f, 0.f, 0.f, 0.f};
-          if (ex_in)
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-              if (e >= nn) break;
-              const float* row = exc + e * 8;
-              const int oe = o + e;
-              float v = row[6] * Pc[oe];
-              v = fmaf(row[0], Pc[oe - 1], v);
-              v = fmaf(row[1], Pc[oe + 1], v);
-              v = fmaf(row[2], Pc[oe - PW], v);
-              v = fmaf(row[3], Pc[oe + PW], v);
-              v = fmaf(row[4], Pm[oe], v);
-              v = fmaf(row[5], Pp[oe], v);
-              rv[e] = Rh[eyl * RP + exl + e] - v;
-            }
-          float* dst = Rz + eyl * RP + exl;
-          if (ex_kind == 1) *reinterpret_cast<float4*>(dst) = make_float4(rv[0], rv[1], rv[2], rv[3]);
-          else dst[0] = rv[0];
+          float rv = 0.f;
+          if (ex_in) {
+            float v = exc[6] * Pc[o];
+            v = fmaf(exc[0], Pc[o - 1], v);
+            v = fmaf(exc[1], Pc[o + 1], v);
+            v = fmaf(exc[2], Pc[o - PW], v);
+            v = fmaf(exc[3], Pc[o + PW], v);
+            v = fmaf(exc[4], Pm[o], v);
+            v = fmaf(exc[5], Pp[o], v);
+            rv = Rh[eyl * RP + exl] - v;
+          }
+          Rz[eyl * RP + exl] = rv;
         }
       }
       if (__syncthreads_or(to)) goto abort;
@@ -725,9 +719,10 @@ abort:
 // staged field x is
 //   kStage 0: xin;
 //   kStage 1: omega D^-1 rhs (the box is rhs; the first step from zero).
-// For kStage 1 each plane is scaled in place when its copy lands (a thread: its
-// own group and, for the first 2 (tx + 2) + 2 ty threads, one halo group), one
-// plane ahead of the stencil, so one barrier per plane stays enough.
+// For kStage 1 each thread scales its own group of each plane in place when the
+// copy lands, one plane ahead of the stencil, so one barrier per plane stays
+// enough; the halo keeps the staged rhs and the tile's edge threads scale the
+// outside neighbours they read.
 // ---------------------------------------------------------------------------
 template <int kStage, bool kRho>
 __global__ void __launch_bounds__(256, 3)
@@ -783,53 +778,40 @@ __global__ void __launch_bounds__(256, 3)
   const int64_t col = (int64_t)jn * g.nx + i;
   float* ob = m.out + (int64_t)b * g.n;
   const float omega = m.omega;
-  // the in-place scaling (kStage 1): own group, and a halo group for the first threads
-  // (rows -1 and TY of the box: TXT + 2 groups each; columns x0-4 and x0+TXN for rows 0..TY-1)
-  const int GW = TXT + 2;
-  int hgx = 0, hgy = 0;  // halo group: tile-local first node and row
-  bool hduty = false;
-  if (kStage != 0) {
-    if (tid < 2 * GW) {
-      hduty = true;
-      hgx = 4 * (tid % GW) - 4;
-      hgy = tid < GW ? -1 : TY;
-    } else if (tid < 2 * GW + 2 * TY) {
-      hduty = true;
-      const int t = tid - 2 * GW;
-      hgx = t < TY ? -4 : TXN;
-      hgy = t < TY ? t : t - TY;
-    }
-  }
-  const int hofs = (hgy + 1) * BX + hgx + 4;
-  const bool h_in = hduty && x0 + hgx >= 0 && x0 + hgx < g.nx && y0 + hgy >= 0 && y0 + hgy < g.ny;
-  int own_tz = -1, h_tz = -1;  // kStage 1: z class of the cached omega / D
-  float own_od[4] = {0.f, 0.f, 0.f, 0.f}, h_od[4] = {0.f, 0.f, 0.f, 0.f};
-  // scale one 4-node group at box offset o (tile-local first node gx, row gy) of plane z by omega / D
-  auto xform = [&](float* X, int o, int gx, int gy, int z, bool is_own) {
-    float4 v = ld4s(X + o);
+  // kStage 1: each thread scales its own group of every staged plane in place by omega / D,
+  // one plane ahead of the stencil.  The halo of the box keeps the staged rhs: a thread on
+  // the tile's edge scales the outside neighbours it reads (the column x0-1 or x0+TXN, the
+  // row y0-1 or y0+TY) by their omega / D as it reads them (no thread works for the halo,
+  // so no warp carries extra work to the plane barrier).  Tiles are at least 2 x 2 threads.
+  int own_tz = -1;  // z class of the cached omega / D of the own group
+  float own_od[4] = {0.f, 0.f, 0.f, 0.f};
+  const bool eW = kStage != 0 && lx == 0, eE = kStage != 0 && lx == TXN - 4;
+  const bool eS = kStage != 0 && ly == 0, eN = kStage != 0 && ly == TY - 1;
+  const int nbx = eW ? i - 1 : i + 4, nby = eS ? jn - 1 : jn + 1;
+  const bool nbx_in = (eW || eE) && own && nbx >= 0 && nbx < g.nx;
+  const bool nby_in = (eS || eN) && own && nby >= 0 && nby < g.ny;
+  float odx = 0.f, ody[4] = {0.f, 0.f, 0.f, 0.f};  // omega / D of the outside neighbours (z class zcls_cur)
+  // scale the own group at box offset cofs of plane z by omega / D
+  auto xform = [&](float* X, int z) {
+    float4 v = ld4s(X + cofs);
     const int zcl = g.cz[z];
-    float* od = is_own ? own_od : h_od;
-    int& tz = is_own ? own_tz : h_tz;
-    if (zcl != tz) {
-      tz = zcl;
+    if (zcl != own_tz) {
+      own_tz = zcl;
 #pragma unroll
       for (int e = 0; e < 4; e++)
-        od[e] = omega * cb[(((int64_t)zcl * g.ncy + g.cy[y0 + gy]) * g.ncx + g.cx[x0 + gx + e]) * kCoefStride + 7];
+        own_od[e] = omega * cb[(((int64_t)zcl * g.ncy + g.cy[jn]) * g.ncx + g.cx[i + e]) * kCoefStride + 7];
     }
-    v = make_float4(od[0] * v.x, od[1] * v.y, od[2] * v.z, od[3] * v.w);
-    *reinterpret_cast<float4*>(X + o) = v;
+    v = make_float4(own_od[0] * v.x, own_od[1] * v.y, own_od[2] * v.z, own_od[3] * v.w);
+    *reinterpret_cast<float4*>(X + cofs) = v;
     return v;
   };
-  // transform plane index j's stage (own group and halo duty); returns the own group
+  // transform plane index j's stage (own group); returns the own group
   auto xform_plane = [&](int j) -> float4 {
     const int z = z0 - 1 + j;
     float* X = x_tile(j % kStages);
     const bool zin = z >= 0 && z < g.nz;
     float4 v = ld4s(X + cofs);
-    if (kStage != 0 && zin) {
-      if (own) v = xform(X, cofs, lx, ly, z, true);
-      if (h_in) xform(X, hofs, hgx, hgy, z, false);
-    }
+    if (kStage != 0 && zin && own) v = xform(X, z);
     return v;
   };
   float rho = 0.f;
@@ -852,7 +834,7 @@ __global__ void __launch_bounds__(256, 3)
       const int sk = k % kStages, sn = (k + 1) % kStages;
       bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
       if (!to) {
-        const float4 xp = xform_plane(k + 1);  // plane z+1, transformed (own group and halo duty)
+        const float4 xp = xform_plane(k + 1);  // plane z+1, own group transformed
         if (own) {
           const float4 bv = ld4s(r_tile(sk) + lofs);
           const int zcl = g.cz[z];
@@ -865,10 +847,23 @@ __global__ void __launch_bounds__(256, 3)
 #pragma unroll
               for (int q = 0; q < 8; q++) c[e][q] = row[q];
             }
+            if (nbx_in) odx = omega * cb[(((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[nbx]) * kCoefStride + 7];
+            if (nby_in)
+#pragma unroll
+              for (int e = 0; e < 4; e++)
+                ody[e] = i + e < g.nx
+                             ? omega * cb[(((int64_t)zcl * g.ncy + g.cy[nby]) * g.ncx + g.cx[i + e]) * kCoefStride + 7]
+                             : 0.f;
           }
           const float* X = x_tile(sk);
-          const float left = X[cofs - 1], right = X[cofs + 4];
-          const float4 sth = ld4s(X + cofs - BX), nth = ld4s(X + cofs + BX);
+          float left = X[cofs - 1], right = X[cofs + 4];
+          float4 sth = ld4s(X + cofs - BX), nth = ld4s(X + cofs + BX);
+          if (kStage != 0) {  // outside neighbours still hold the rhs: scale them now
+            if (eW) left *= odx;
+            if (eE) right *= odx;
+            if (eS) sth = make_float4(ody[0] * sth.x, ody[1] * sth.y, ody[2] * sth.z, ody[3] * sth.w);
+            if (eN) nth = make_float4(ody[0] * nth.x, ody[1] * nth.y, ody[2] * nth.z, ody[3] * nth.w);
+          }
           float o4[4];
 #pragma unroll
           for (int e = 0; e < 4; e++) {
@@ -987,11 +982,10 @@ void tma_prepare() {
 
 int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, int stage, const MGFineArgs& m, bool rho, cudaStream_t s) {
   if (!tma_supported(a.g, t) || (rho && m.slot < 0) || (rho && stage != 0) || stage < 0 || stage > 1) return -1;
-  const int NT = t.tx * t.ty;
-  if (stage != 0 && 2 * (t.tx + 2) + 2 * t.ty > NT) return -1;  // halo groups: one per thread at most
   CUtensorMap mx, mr;
   const float* boxed = stage == 1 ? m.rhs : m.xin;
   if (make_map(&mx, boxed, a.g, a.B, t) || make_map(&mr, m.rhs, a.g, a.B, t, false)) return -1;
+  if (stage == 1 && (t.tx < 2 || t.ty < 2)) return -1;  // an edge thread would face two outside neighbours
   const size_t smem = ring_bytes(t, 1, 1);
   const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
   int* err = a.active + 2;
@@ -1014,7 +1008,9 @@ static size_t rr_smem_bytes(Tile t) {
 }
 
 int launch_mg_fine_rr_tma(const CGArgs<float>& a, Tile t, const MGFineArgs& m, cudaStream_t s) {
-  if ((t.ty & 1) || (a.zc & 1) || a.g.nx % 4 || rr_smem_bytes(t) > 200 * 1024) return -1;
+  // one extra node per thread at most: the CTA needs TXN + TY + 1 threads
+  if ((t.ty & 1) || (a.zc & 1) || a.g.nx % 4 || rr_smem_bytes(t) > 200 * 1024 || t.tx * t.ty < 4 * t.tx + t.ty + 1)
+    return -1;
   CUtensorMap mx, mr;
   if (make_map_box(&mx, m.xin, a.g, a.B, 4 * t.tx + 8, t.ty + 3) ||
       make_map_box(&mr, m.rhs, a.g, a.B, 4 * t.tx + 4, t.ty + 1))
