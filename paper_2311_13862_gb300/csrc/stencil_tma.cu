@@ -432,10 +432,16 @@ __global__ void __launch_bounds__(256, 3)
   {
     float c[4][8];
     int zcls_cur = -1;
-    for (int z = z0; z < z1; ++z) {
-      const int k = z - z0 + 1;
-      const int sk = k % kStages, sn = (k + 1) % kStages;
-      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
+    // the planes in groups of kStages, so that a plane's ring stages and its wait
+    // parity's offset within the group are compile-time constants
+    for (int kb = 0; z0 + kb < z1; kb += kStages)
+#pragma unroll
+    for (int q = 0; q < kStages; q++) {
+      const int z = z0 + kb + q;
+      if (z >= z1) break;
+      const int k = kb + q + 1;
+      const int sk = (q + 1) % kStages, sn = (q + 2) % kStages;
+      bool to = !mbar_wait(&bars[sn], ((kb / kStages) + (q + 2) / kStages) & 1, a.wait_cycles);
       if (!to && own) {
         const float4 xp = ld4s(p_tile(sn) + cofs);
         const float4 s4 = ld4s(s_tile(sk) + lofs);
@@ -605,11 +611,18 @@ __global__ void __launch_bounds__(256, 3)
     float c[4][7];
     int zcls_cur = -1, ex_zcls = -1;
     float acc = 0.f;
-    for (int z = z0; z <= zlast; ++z) {
-      const int k = z - z0 + 1;  // plane index of z
-      const int sm_ = (k - 1) % kStages, sk = k % kStages, sn = (k + 1) % kStages;
-      to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
-      float* Rz = R + (z & 1) * rpl;
+    // the planes in groups of kStages: z0 is even and each group starts kStages planes
+    // after the last, so a plane's ring stages, its wait parity's offset within the group
+    // and its parity along z (the restriction's branch) are compile-time constants
+    for (int kb = 0; z0 + kb <= zlast; kb += kStages)
+#pragma unroll
+    for (int q = 0; q < kStages; q++) {
+      const int z = z0 + kb + q;
+      if (z > zlast) break;
+      const int k = kb + q + 1;  // plane index of z
+      const int sm_ = q, sk = (q + 1) % kStages, sn = (q + 2) % kStages;
+      to = !mbar_wait(&bars[sn], ((kb / kStages) + (q + 2) / kStages) & 1, a.wait_cycles);
+      float* Rz = R + (q & 1) * rpl;
       if (!to) {
         const float* Pm = xs(sm_);
         const float* Pc = xs(sk);
@@ -685,10 +698,10 @@ __global__ void __launch_bounds__(256, 3)
       const float* r2 = r1 + RP;
       const float qv = 0.5f * fmaf(0.5f, r0[0] + r0[2], r0[1]) + fmaf(0.5f, r1[0] + r1[2], r1[1]) +
                        0.5f * fmaf(0.5f, r2[0] + r2[2], r2[1]);
-      if (z & 1) {
+      if (q & 1) {
         acc += qv;  // the centre plane of coarse K = (z - 1) / 2
       } else {
-        if (z > z0) {  // plane z closes coarse K = z/2 - 1
+        if (kb + q > 0) {  // plane z closes coarse K = z/2 - 1
           acc = fmaf(0.5f, qv, acc);
           const int K = z / 2 - 1;
           if (cown && K < m.cnz) rc[K * cplane] = acc;
