@@ -842,10 +842,19 @@ __global__ void __launch_bounds__(256, 3)
   {
     float c[4][8];
     int zcls_cur = -1;
-    for (int z = z0; z < z1; ++z) {
-      const int k = z - z0 + 1;
-      const int sk = k % kStages, sn = (k + 1) % kStages;
-      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
+    // one plane per iteration (U = 1): groups of kStages planes, as in the residual +
+    // restriction pass, measured slower here (the kStage 1 body spills when unrolled, the
+    // kStage 0 steps gained nothing)
+    constexpr int U = 1;
+    for (int kb = 0; z0 + kb < z1; kb += U)
+#pragma unroll
+    for (int q = 0; q < U; q++) {
+      const int z = z0 + kb + q;
+      if (U > 1 && z >= z1) break;
+      const int k = kb + q + 1;
+      const int sk = U > 1 ? (q + 1) % kStages : k % kStages, sn = U > 1 ? (q + 2) % kStages : (k + 1) % kStages;
+      const unsigned par = U > 1 ? ((kb / kStages) + (q + 2) / kStages) & 1 : ((k + 1) / kStages) & 1;
+      bool to = !mbar_wait(&bars[sn], par, a.wait_cycles);
       if (!to) {
         const float4 xp = xform_plane(k + 1);  // plane z+1, own group transformed
         if (own) {
