@@ -897,12 +897,13 @@ def main():
     fine = []
     if acc["samples"] > 0 and dom is not None and args.precond == "mg" and sum(acc["mg_fine_ms"]) > 0:
         # the fused finest-level steps of each V-cycle: algorithmic bytes per DoF (FP32):
-        # read r, write Y (8); read Y, r, write the restricted residual at 1/8 of the nodes
+        # read r, write Y (8; the first step also reads omega/D, 4 B/DoF of traffic beyond the
+        # algorithmic bytes); read Y, r, write the restricted residual at 1/8 of the nodes
         # (8.5); read and write Y, the coarse correction at 1/8 of the nodes, then read Y, r,
         # write X (8 + 0.5 + 12, two launches timed together); read X, r, write s (12)
         # (each a single kernel, timed by CUDA events around its own launch)
-        fine_kernels = [("k_mg_smooth_tma<1,0> (two damped Jacobi steps from zero)", 8.0,
-                         "mg_fine_smooth_pre_f32_64cube"),
+        fine_kernels = [("k_mg_smooth_od_tma (two damped Jacobi steps from zero, r and omega/D staged)", 8.0,
+                         "mg_fine_smooth_od_f32_64cube"),
                         ("k_mg_fine_rr_tma (restricted residual P^T (r - A Y))", 8.5,
                          "mg_fine_residual_restrict_f32_64cube"),
                         ("k_mg_prolong_add4 (Y += P e)", 8.5, None),

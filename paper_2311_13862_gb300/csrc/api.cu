@@ -862,6 +862,16 @@ rbws_status mg_fp32_batch(rbws_problem p, const double* d_mu, int B, const float
     mgb->mg_tiles_y = (p->ny + tm.ty - 1) / tm.ty;
     mgb->mg_zc = choose_zc_v4(p->nz, (int64_t)mgb->mg_tiles_x * mgb->mg_tiles_y * B);
     mgb->mg_nzc = (p->nz + mgb->mg_zc - 1) / mgb->mg_zc;
+    // omega / D per node, staged beside the rhs by the first pre-smoothing step (nx % 4 == 0)
+    if (p->nx % 4 == 0) {
+      int err = 0;
+      float* od = (float*)p->buf("mg_od", sizeof(float) * (size_t)B * p->n, &err);
+      if (err) return (rbws_status)err;
+      launch_omega_dinv(p->geo, coef32, B, (float)kMGOmega, od, p->cur);
+      p->launches += 1;
+      CK(cudaGetLastError());
+      mgb->od = od;
+    }
   }
   return RBWS_OK;
 }

@@ -454,6 +454,7 @@ struct MGBatch {
   void* w1[kMGMaxLevels] = {};
   void* w2[kMGMaxLevels] = {};
   const void* ainv = nullptr;  // [B][n0][n0]
+  const float* od = nullptr;    // FP32 finest level: omega / D per node [B][n] (see MGFineArgs)
 };
 
 // Per-instance coarse tables (element type per fp32) and level-0 inverses
@@ -474,7 +475,11 @@ struct MGFineArgs {
   const int* mask;   // skip instances with mask[b] == 0 (may be null)
   float omega;
   int slot;          // partial slot of rho (output kind 2)
+  const float* od = nullptr;  // [B][n] omega / D of the level's nodes (stage 1 from staged od), or null
 };
+// od[b][node] = omega / D from the FP32 coefficient tables (the first pre-smoothing step's
+// scaling, staged beside the rhs).
+void launch_omega_dinv(const Geo& g, const float* coef32, int B, float omega, float* od, cudaStream_t s);
 // stage 0: x = xin, 1: x = omega D^-1 rhs;  outk 0: Jacobi
 // step, 1: residual, 2: Jacobi step and rho partials, 3 (stage 0): the
 // restricted residual P^T (rhs - A x) into out (the coarse grid cnx x cny x

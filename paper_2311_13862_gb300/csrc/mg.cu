@@ -1164,7 +1164,7 @@ int vcycle_fine_fused(const MGBatch& m, const float* rhs, float* out, int slot, 
   float* W = (float*)m.w2[J];
   float* crhs = (float*)m.rhs[J - 1];
   float* csol = (float*)m.sol[J - 1];
-  MGFineArgs fa{rhs, nullptr, Y, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot};
+  MGFineArgs fa{rhs, nullptr, Y, C.nx, C.ny, C.nz, m.mask, (float)kMGOmega, slot, m.od};
   // the steps that write no partials run on wider tiles (less halo); the last,
   // with the rho partials, on the iteration's own tiling
   CGArgs<float> am = *m.fine_cg;

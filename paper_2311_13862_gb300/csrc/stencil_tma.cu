@@ -16,6 +16,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace rbws {
@@ -935,6 +937,169 @@ abort:
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The first pre-smoothing step from the staged rhs and a staged omega / D: two
+// damped Jacobi steps from zero, Y = X1 + omega D^-1 (r - A X1) with X1 =
+// omega D^-1 r, where omega / D per node of the finest level (od, [B][n], formed
+// once per solve by k_omega_dinv) arrives by TMA beside r, so every X1 the
+// stencil needs, halo included, is one product of two staged values: no pass
+// scales a plane in place and no thread treats the tile's edge apart.  Reads r
+// and od, writes Y: 12 B/DoF.  The products and their order are those of
+// k_mg_smooth_tma<1, ...>, so its results are the same.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 3)
+    k_mg_smooth_od_tma(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtensorMap tm_d,
+                       CGArgs<float> a, MGFineArgs m, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ int s_go;
+  const int b = blockIdx.z;
+  if (a.st[b].status != ST_ACTIVE || (m.mask && !m.mask[b])) return;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) s_go = !*reinterpret_cast<volatile int*>(err);  // an earlier wait ran out: do not wait again
+  __syncthreads();
+  if (!s_go) return;
+  const Geo& g = a.g;
+  const int TXT = blockDim.x, TXN = TXT * 4, TY = blockDim.y;
+  const int x0 = (blockIdx.x % a.tiles_x) * TXN, y0 = (blockIdx.x / a.tiles_x) * TY;
+  const int z0 = blockIdx.y * a.zc, z1 = min(g.nz, z0 + a.zc);
+  const int BX = TXN + 8, BY = TY + 2;
+  const unsigned box_bytes = (unsigned)(BX * BY * sizeof(float));
+  const int arr_floats = ((BX * BY * 4 + 127) / 128) * 32;
+  float* stage_base = reinterpret_cast<float*>(smem_raw);
+  auto r_box = [&](int st) { return stage_base + st * 2 * arr_floats; };
+  auto d_box = [&](int st) { return stage_base + st * 2 * arr_floats + arr_floats; };
+  const int nq = z1 - z0 + 2;
+  auto issue = [&](int j) {  // the r and od boxes of plane z0-1+j
+    const int st = j % kStages;
+    mbar_expect_tx(&bars[st], 2 * box_bytes);
+    tma_load_4d(r_box(st), &tm_r, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+    tma_load_4d(d_box(st), &tm_d, x0 - 4, y0 - 1, z0 - 1 + j, b, &bars[st]);
+  };
+  if (tid == 0) {
+    for (int st = 0; st < kStages; st++) mbar_init(&bars[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int n_issued = 0, next_wait = 0;
+  if (tid == 0)
+    for (int j = 0; j < kStages && j < nq; j++) {
+      issue(j);
+      n_issued = j + 1;
+    }
+  const int lx = 4 * (int)threadIdx.x, ly = (int)threadIdx.y;
+  const int i = x0 + lx, jn = y0 + ly;
+  const bool own = i < g.nx && jn < g.ny;
+  const int cofs = (ly + 1) * BX + lx + 4;
+  const float* cb = a.coef + (int64_t)b * g.ncls() * kCoefStride;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  const int64_t col = (int64_t)jn * g.nx + i;
+  float* ob = m.out + (int64_t)b * g.n;
+  auto mul4 = [](float4 u, float4 v) { return make_float4(u.x * v.x, u.y * v.y, u.z * v.z, u.w * v.w); };
+  // own group of plane index j: X1 = od r, and the raw r and od
+  float4 rc, dc, rp, dp;
+  auto own_plane = [&](int j, float4& r4, float4& d4) -> float4 {
+    const int st = j % kStages;
+    r4 = ld4s(r_box(st) + cofs);
+    d4 = ld4s(d_box(st) + cofs);
+    return mul4(d4, r4);
+  };
+  bool timed_out = !mbar_wait(&bars[0], 0, a.wait_cycles);
+  float4 xm = make_float4(0.f, 0.f, 0.f, 0.f), xc = xm;
+  rc = dc = rp = dp = xm;
+  if (!timed_out) xm = own_plane(0, rp, dp);
+  if (!timed_out) timed_out = !mbar_wait(&bars[1 % kStages], (1 / kStages) & 1, a.wait_cycles);
+  if (!timed_out) xc = own_plane(1, rc, dc);
+  if (__syncthreads_or(timed_out)) goto abort;
+  next_wait = 2;
+  if (tid == 0 && kStages < nq) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(kStages);
+    n_issued = kStages + 1;
+  }
+  {
+    float c[4][7];
+    int zcls_cur = -1;
+    for (int z = z0; z < z1; ++z) {
+      const int k = z - z0 + 1;
+      const int sk = k % kStages, sn = (k + 1) % kStages;
+      bool to = !mbar_wait(&bars[sn], ((k + 1) / kStages) & 1, a.wait_cycles);
+      if (!to) {
+        const float4 xp = own_plane(k + 1, rp, dp);  // plane z+1
+        if (own) {
+          const int zcl = g.cz[z];
+          if (zcl != zcls_cur) {
+            zcls_cur = zcl;
+            const int yc = (int)g.cy[jn];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float* row = cb + (((int64_t)zcl * g.ncy + yc) * g.ncx + g.cx[i + e]) * kCoefStride;
+#pragma unroll
+              for (int q = 0; q < 7; q++) c[e][q] = row[q];
+            }
+          }
+          const float* R = r_box(sk);
+          const float* D = d_box(sk);
+          const float left = D[cofs - 1] * R[cofs - 1], right = D[cofs + 4] * R[cofs + 4];
+          const float4 sth = mul4(ld4s(D + cofs - BX), ld4s(R + cofs - BX));
+          const float4 nth = mul4(ld4s(D + cofs + BX), ld4s(R + cofs + BX));
+          float o4[4];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float xce = f4(xc, e);
+            float v = c[e][6] * xce;
+            v = fmaf(c[e][0], e == 0 ? left : f4(xc, e - 1), v);
+            v = fmaf(c[e][1], e == 3 ? right : f4(xc, e + 1), v);
+            v = fmaf(c[e][2], f4(sth, e), v);
+            v = fmaf(c[e][3], f4(nth, e), v);
+            v = fmaf(c[e][4], f4(xm, e), v);
+            v = fmaf(c[e][5], f4(xp, e), v);
+            o4[e] = fmaf(f4(dc, e), f4(rc, e) - v, xce);
+          }
+          *reinterpret_cast<float4*>(ob + z * plane + col) = make_float4(o4[0], o4[1], o4[2], o4[3]);
+        }
+        xm = xc;
+        xc = xp;
+        rc = rp;
+        dc = dp;
+      }
+      if (__syncthreads_or(to)) goto abort;
+      next_wait = k + 2;
+      if (tid == 0 && k + kStages < nq) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k + kStages);
+        n_issued = k + kStages + 1;
+      }
+    }
+  }
+  return;
+abort:
+  if (tid == 0) {
+    atomicExch(err, 1);
+    for (int jq = next_wait; jq < n_issued; jq++) mbar_wait(&bars[jq % kStages], (jq / kStages) & 1);
+  }
+  __syncthreads();
+}
+
+// od[b][node] = omega / D of the node (the FP32 table's reciprocal diagonal, times omega).
+// Four x-consecutive nodes per thread (nx % 4 == 0, as every TMA-fed step requires), one
+// 16-byte store; grid (chunks, B) with a grid-stride loop over the instance's groups.
+__global__ void k_omega_dinv(Geo g, const float* __restrict__ coef32, float omega, float* __restrict__ od) {
+  const int b = blockIdx.y;
+  const int gx = g.nx >> 2, groups = (int)(g.n >> 2);
+  const float* cb = coef32 + (int64_t)b * g.ncls() * kCoefStride;
+  float4* o = reinterpret_cast<float4*>(od + (int64_t)b * g.n);
+  for (int e4 = blockIdx.x * blockDim.x + threadIdx.x; e4 < groups; e4 += gridDim.x * blockDim.x) {
+    const int i = (e4 % gx) * 4, row = e4 / gx;
+    const int j = row % g.ny, k = row / g.ny;
+    const int cyz = ((int)g.cz[k] * g.ncy + (int)g.cy[j]) * g.ncx;
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = omega * cb[(int64_t)(cyz + (int)g.cx[i + q]) * kCoefStride + 7];
+    o[e4] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
 // Host side: tensor maps over [B][nz][ny][nx] float arrays with a box of
 // (4*tx + 8) x (ty + 2) x 1 x 1 and zero fill outside the tensor.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -997,6 +1162,7 @@ void tma_prepare() {
   cudaFuncSetAttribute(k_cg_a_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_cg_b_s_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mg_fine_rr_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_mg_smooth_od_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mg_smooth_tma<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mg_smooth_tma<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_mg_smooth_tma<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1007,6 +1173,18 @@ int launch_mg_smooth_tma(const CGArgs<float>& a, Tile t, int stage, const MGFine
   CUtensorMap mx, mr;
   const float* boxed = stage == 1 ? m.rhs : m.xin;
   if (make_map(&mx, boxed, a.g, a.B, t) || make_map(&mr, m.rhs, a.g, a.B, t, false)) return -1;
+  if (stage == 1 && m.od) {  // X1 formed from the staged omega / D (k_mg_smooth_od_tma)
+    CUtensorMap md;
+    if (make_map(&md, m.od, a.g, a.B, t)) return -1;
+    int* err = a.active + 2;
+    k_mg_smooth_od_tma<<<dim3(a.tiles_x * a.tiles_y, a.nzc, a.B), dim3(t.tx, t.ty), ring_bytes(t, 2, 0), s>>>(
+        mx, md, a, m, err);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    return 0;
+  }
   if (stage == 1 && (t.tx < 2 || t.ty < 2)) return -1;  // an edge thread would face two outside neighbours
   const size_t smem = ring_bytes(t, 1, 1);
   const dim3 grid(a.tiles_x * a.tiles_y, a.nzc, a.B), block(t.tx, t.ty);
@@ -1077,4 +1255,12 @@ int launch_cg_b_s_tma(const CGArgs<float>& a, Tile t, int parity, int* err, cuda
   return 0;
 }
 
+}  // namespace rbws
+
+namespace rbws {
+void launch_omega_dinv(const Geo& g, const float* coef32, int B, float omega, float* od, cudaStream_t s) {
+  const int64_t groups = g.n / 4;
+  const unsigned chunks = (unsigned)std::min<int64_t>((groups + 255) / 256, std::max<int64_t>(1, 152 * 8 / B));
+  k_omega_dinv<<<dim3(chunks, (unsigned)B), 256, 0, s>>>(g, coef32, omega, od);
+}
 }  // namespace rbws
