@@ -192,6 +192,10 @@ struct rbws_problem_s {
   cudaEvent_t mgev[10] = {};                                 // ... of the fused MG steps
   int64_t launches = 0;           // kernels launched by the current call
   int* h_active = nullptr;   // pinned
+  // pinned, mapped host memory for the mixed-precision solve's own small reads (read_small)
+  void* h_small = nullptr;
+  void* d_small = nullptr;
+  size_t small_bytes = 0;
   // reduced basis
   int N = 0;
   double* d_W = nullptr;    // [N][n]
@@ -295,6 +299,30 @@ struct StreamGuard {
   }
   ~StreamGuard() { p->cur = p->stream; }
 };
+
+// Reads `bytes` (a multiple of 4) of device memory into host memory: a kernel writes them to
+// pinned, mapped host memory, then the host waits for stream s.  A plain device-to-host copy
+// would take a copy engine and queue behind any large copy the caller has in flight (the
+// previous batch's solutions going back to the host while this batch solves), and the solve
+// would stall until that copy ended.
+rbws_status read_small(rbws_problem p, const void* dev, size_t bytes, void* host, cudaStream_t s) {
+  if (bytes > p->small_bytes) {
+    CK(cudaStreamSynchronize(s));  // nothing still writes the old buffer
+    if (p->h_small) cudaFreeHost(p->h_small);
+    p->h_small = p->d_small = nullptr;
+    p->small_bytes = 0;
+    const size_t nb = std::max<size_t>(bytes, 4096);
+    CK(cudaHostAlloc(&p->h_small, nb, cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer(&p->d_small, p->h_small, 0));
+    p->small_bytes = nb;
+  }
+  launch_copy_words(static_cast<const uint32_t*>(dev), static_cast<uint32_t*>(p->d_small), bytes / 4, s);
+  p->launches += 1;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  std::memcpy(host, p->h_small, bytes);
+  return RBWS_OK;
+}
 
 // Coefficient tables for B parameters already on the device.
 rbws_status coef_tables(rbws_problem p, const double* d_mu, int B, double** c64, float** c32) {
@@ -625,8 +653,7 @@ rbws_status galerkin_start(rbws_problem p, const double* d_mu, int B, double* u,
   CKI(lift(p, C, B, u, fp32));
   CK(cudaGetLastError());
   std::vector<int> h(B);
-  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
-  CK(cudaStreamSynchronize(p->cur));
+  CKI(read_small(p, info, sizeof(int) * B, h.data(), p->cur));
   for (int b = 0; b < B; b++)
     if (h[b] != 0) {
       set_error("reduced matrix A_N(mu) is not positive definite for instance " + std::to_string(b));
@@ -718,8 +745,7 @@ rbws_status mg_batch(rbws_problem p, const double* d_mu, int B, const void* coef
   p->launches += plan->J + 1;
   CK(cudaGetLastError());
   std::vector<int> h(B);
-  CK(cudaMemcpyAsync(h.data(), info, sizeof(int) * B, cudaMemcpyDeviceToHost, p->cur));
-  CK(cudaStreamSynchronize(p->cur));
+  CKI(read_small(p, info, sizeof(int) * B, h.data(), p->cur));
   for (int b = 0; b < B; b++)
     if (h[b]) {
       set_error("multigrid: coarsest-level matrix not positive definite");
@@ -1050,48 +1076,103 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaError_t ce;
-  if (!prof) {
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const int64_t launches0 = p->launches;
-    if (mg) mg_launches = mg_apply(a, 0, s);  // the previous block's last preconditioning
+  // One block: the previous block's last preconditioning, M iterations, the decision and the
+  // reliable update of the instances it flagged (the others leave those kernels at once).
+  auto record_block = [&](cudaStream_t ss) -> rbws_status {
+    if (mg) mg_launches = mg_apply(a, 0, ss);
     for (int k = 0; k < M; k++) {
-      phase_a(a, k & 1, s);
-      if (mg && k == M - 1) phase_b_core(a, k & 1, s);
-      else phase_b(a, k & 1, s);
+      phase_a(a, k & 1, ss);
+      if (mg && k == M - 1) phase_b_core(a, k & 1, ss);
+      else phase_b(a, k & 1, ss);
     }
-    cudaMemsetAsync(a.pending, 0, sizeof(int), s);
-    launch_ru_decide(a, s);
-    // the reliable update of the instances decide flagged, in the same graph (the others
-    // leave these kernels at once), so the host waits once per block
-    rbws_status rr;
-    if (ffu) {
-      rr = update_ff(false, s);
-    } else {
-      launch_ru_fold(a, s);
-      rr = residual_norms(p, coef64, B, u, r64, rel, upd);
-      reset(a, 0, s);
+    cudaMemsetAsync(a.pending, 0, sizeof(int), ss);
+    launch_ru_decide(a, ss);
+    if (ffu) return update_ff(false, ss);
+    launch_ru_fold(a, ss);
+    const rbws_status rr = residual_norms(p, coef64, B, u, r64, rel, upd);
+    reset(a, 0, ss);
+    return rr;
+  };
+  // The blocks run inside one graph launch: a conditional while node repeats the block while
+  // a one-thread kernel at its end finds instances still active (and no TMA wait ran out,
+  // and fewer than loop_cap blocks ran).  The host then reads nothing between blocks: such a
+  // read (a device-to-host copy of the counts and a wait) queues behind any large copy the
+  // caller has on the same copy engine, e.g. the previous batch's solutions going back to
+  // the host, and the GPU would idle until that copy ends.  If the driver cannot build the
+  // conditional graph, the host loop below launches one block at a time.
+  int* loop_ctr = nullptr;
+  bool in_graph_loop = false;
+  const int loop_cap = 2 * std::max(o.max_iters, 1) / M + 64;
+  if (!prof) {
+    const int64_t launches0 = p->launches;
+    int err = 0;
+    loop_ctr = (int*)p->buf("loop_ctr", sizeof(int), &err);
+    if (err) return (rbws_status)err;
+    cudaGraphConditionalHandle handle;
+    cudaGraph_t body = nullptr;
+    ce = cudaGraphCreate(&graph, 0);
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+      if (ce == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (ce == cudaSuccess) ce = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      const rbws_status rr = record_block(s);
+      launch_loop_condition(handle, a.active, loop_ctr, loop_cap, s);
+      cudaGraph_t captured = nullptr;
+      ce = cudaStreamEndCapture(s, &captured);
+      if (rr != RBWS_OK) {
+        cudaGraphDestroy(graph);
+        return rr;
+      }
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    }
+    if (ce == cudaSuccess) {
+      in_graph_loop = true;
+    } else {  // the one-block graph of the host loop
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      exec = nullptr;
+      graph = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const rbws_status rr = record_block(s);
+      ce = cudaStreamEndCapture(s, &graph);
+      if (rr != RBWS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rr;
+      }
+      if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
+      }
     }
     p->launches = launches0;
-    ce = cudaStreamEndCapture(s, &graph);
-    if (rr != RBWS_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return rr;
-    }
-    if (ce != cudaSuccess) return (rbws_status)cuda_fail(ce, "cudaStreamEndCapture");
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    if (ce != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      return (rbws_status)cuda_fail(ce, "cudaGraphInstantiate");
-    }
   }
   rbws_status rc = RBWS_OK;
   int counts[3];
-  for (;;) {
-    cudaMemcpyAsync(counts, a.active, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
-    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
-      rc = (rbws_status)cuda_fail(ce, "solve loop");
-      break;
+  if (in_graph_loop) {
+    // the counts before the first block come from the start (no block has run yet)
+    rc = read_small(p, a.active, 3 * sizeof(int), counts, s);
+    if (rc == RBWS_OK && counts[0] > 0 && !counts[2]) {
+      int blocks = 0;
+      cudaMemsetAsync(loop_ctr, 0, sizeof(int), s);
+      if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) rc = (rbws_status)cuda_fail(ce, "cudaGraphLaunch");
+      if (rc == RBWS_OK) rc = read_small(p, loop_ctr, sizeof(int), &blocks, s);
+      p->launches += (int64_t)blocks * ((2 + mg_launches) * M + 2 + (ffu ? 7 : 4));
     }
+  }
+  for (; !in_graph_loop;) {
+    if ((rc = read_small(p, a.active, 3 * sizeof(int), counts, s)) != RBWS_OK) break;
     if (counts[2]) break;  // a TMA stage wait ran out; reported below
     const int active = counts[0];
     if (active == 0) break;
@@ -1162,8 +1243,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   if (rc != RBWS_OK) return rc;
   {
     int terr = 0;
-    CK(cudaMemcpyAsync(&terr, tma_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CKI(read_small(p, tma_err, sizeof(int), &terr, s));
     if (terr) {
       set_error("a TMA stage wait ran out of time in the FP32 stencil phase");
       return RBWS_ERR_DEVICE_TIMEOUT;
@@ -1171,8 +1251,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
   }
   // instances stopped by max_iters or breakdown still hold a correction in d
   std::vector<InstState> h(B);
-  CK(cudaMemcpyAsync(h.data(), a.st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  static_assert(sizeof(InstState) % 4 == 0, "read_small copies 4-byte words");
+  CKI(read_small(p, a.st, sizeof(InstState) * B, h.data(), s));
   std::vector<int> fin(B);
   int nfin = 0;
   // mode 2: the fold adds the update still pending at the parity recorded when the instance stopped
@@ -1188,8 +1268,7 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     }
     CKI(residual_norms(p, coef64, B, u, r64, rel, upd));
     std::vector<double> hr(B);
-    CK(cudaMemcpyAsync(hr.data(), rel, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CKI(read_small(p, rel, sizeof(double) * B, hr.data(), s));
     for (int b = 0; b < B; b++)
       if (fin[b]) h[b].relres = hr[b];
     p->launches += 3;
@@ -2007,6 +2086,7 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_w16);
   cudaFree(p->d_cscale);
   if (p->h_active) cudaFreeHost(p->h_active);
+  if (p->h_small) cudaFreeHost(p->h_small);
   if (p->ev) cudaEventDestroy(p->ev);
   for (auto& e : p->tev)
     if (e) cudaEventDestroy(e);

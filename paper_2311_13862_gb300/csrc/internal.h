@@ -252,6 +252,12 @@ void launch_ru_reset_ff(const CGArgs<float>& a, Tile t, const FFState& ff, int s
 
 // Reliable-update kernels of the FP32 path (see stencil.cu).
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s);
+// dst[k] = src[k] for k < words (dst may be pinned, mapped host memory).
+void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t words, cudaStream_t s);
+// The end of one block of a graph-resident solve loop: counts the block in *ctr and sets the
+// while node's condition to (counts[0] > 0, the active instances) && (counts[2] == 0, no
+// TMA wait ran out) && (*ctr < cap).
+void launch_loop_condition(cudaGraphConditionalHandle h, const int* counts, int* ctr, int cap, cudaStream_t s);
 void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s);
 void launch_ru_reset(const CGArgs<float>& a, Tile t, int start, cudaStream_t s);
 

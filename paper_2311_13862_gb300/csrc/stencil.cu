@@ -1212,6 +1212,29 @@ template void launch_apply_interleaved<float>(const Geo&, const float*, int, flo
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s) {
   k_ru_decide<<<(a.B + 3) / 4, 128, 0, s>>>(a);
 }
+namespace {
+__global__ void k_loop_condition(cudaGraphConditionalHandle h, const int* __restrict__ counts, int* ctr, int cap) {
+  const int blocks = ++*ctr;
+  cudaGraphSetConditional(h, (counts[0] > 0 && counts[2] == 0 && blocks < cap) ? 1u : 0u);
+}
+}  // namespace
+
+namespace {
+__global__ void k_copy_words(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, size_t words) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < words; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = src[k];
+}
+}  // namespace
+
+void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t words, cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 64);
+  k_copy_words<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(src, dst, words);
+}
+
+void launch_loop_condition(cudaGraphConditionalHandle h, const int* counts, int* ctr, int cap, cudaStream_t s) {
+  k_loop_condition<<<1, 1, 0, s>>>(h, counts, ctr, cap);
+}
+
 void launch_ru_fold(const CGArgs<float>& a, cudaStream_t s) {
   const int threads = 256;
   const int64_t work = (a.g.n & 3) == 0 ? a.g.n / 4 : a.g.n;  // the kernel falls back to one node per
