@@ -492,6 +492,9 @@ __global__ void __launch_bounds__(256) k_ru_reset_ff(CGArgs<float> a, FFState ff
   const int64_t off = (int64_t)b * g.n;
   const int64_t plane = (int64_t)g.nx * g.ny;
   const int64_t col = (int64_t)ps.j * g.nx + ps.i;
+  // With MG and no resync the residual is the one k_ru_ff just wrote, and its r.r partials
+  // are that kernel's (same tiling, in ff.part): r need not be read again.
+  const bool reuse_rr = mg && !resync;
   float rho = 0.f, rr = 0.f;
   if (ps.own) {
     int zcls_cur = -1;
@@ -501,6 +504,10 @@ __global__ void __launch_bounds__(256) k_ru_reset_ff(CGArgs<float> a, FFState ff
       const int64_t idx = off + z * plane + col;
       st4(a.u + idx, make_float4(0.f, 0.f, 0.f, 0.f));
       if (!active) continue;
+      if (reuse_rr) {
+        if (restart) st4(a.p0 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
+        continue;
+      }
       const int zcl = g.cz[z];
       if (zcl != zcls_cur) {
         zcls_cur = zcl;
@@ -535,7 +542,8 @@ __global__ void __launch_bounds__(256) k_ru_reset_ff(CGArgs<float> a, FFState ff
   if (!active) return;  // uniform over the CTA
   // with MG, s and rho follow from a V-cycle after the reset
   double drho = mg ? 0.0 : (double)rho, drr = (double)rr;
-  block_sum2(drho, drr, red);
+  if (!reuse_rr) block_sum2(drho, drr, red);
+  else drr = ff.part[(int64_t)b * a.P + ps.part];
   if (tid == 0) {
     a.rho_rr[(int64_t)b * a.P + ps.part] = make_double2(drho, drr);
     if (restart) a.rho_rr[((int64_t)a.B + b) * a.P + ps.part] = make_double2(ps.part == 0 ? 1.0 : 0.0, 0.0);
