@@ -191,7 +191,6 @@ struct rbws_problem_s {
   cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // profiling events
   cudaEvent_t mgev[10] = {};                                 // ... of the fused MG steps
   int64_t launches = 0;           // kernels launched by the current call
-  int* h_active = nullptr;   // pinned
   // pinned, mapped host memory for the mixed-precision solve's own small reads (read_small)
   void* h_small = nullptr;
   void* d_small = nullptr;
@@ -450,12 +449,8 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
   }
   rbws_status rc = RBWS_OK;
   for (;;) {
-    cudaMemcpyAsync(p->h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
-      rc = (rbws_status)cuda_fail(ce, "solve loop");
-      break;
-    }
-    const int active = *p->h_active;
+    int active = 0;  // read off the copy engines (read_small)
+    if ((rc = read_small(p, a.active, sizeof(int), &active, s)) != RBWS_OK) break;
     if (active > 0) {
       if (!prof) {
         if ((ce = cudaGraphLaunch(exec, s)) != cudaSuccess) {
@@ -500,12 +495,9 @@ rbws_status run_pcg(rbws_problem p, CGArgs<T>& a, Tile t, int max_restarts, int 
     launch_cg_finalize<T>(a, 0, 1, max_restarts, s);
     p->launches += 2;
     p->launches += launch_precond_start<T>(a, t, s);
-    cudaMemcpyAsync(p->h_active, a.active, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
-      rc = (rbws_status)cuda_fail(ce, "true residual");
-      break;
-    }
-    if (*p->h_active == 0) break;
+    int restarted = 0;
+    if ((rc = read_small(p, a.active, sizeof(int), &restarted, s)) != RBWS_OK) break;
+    if (restarted == 0) break;
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -1767,7 +1759,6 @@ static rbws_status problem_setup(rbws_problem p, const double* f_host, rbws_prob
     return fail(e, "cudaStreamCreate");
   if ((e = cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming)) != cudaSuccess)
     return fail(e, "cudaEventCreate");
-  if ((e = cudaMallocHost(&p->h_active, sizeof(int))) != cudaSuccess) return fail(e, "cudaMallocHost");
   std::vector<uint8_t> cls;
   cls.insert(cls.end(), p->ax.cls.begin(), p->ax.cls.end());
   cls.insert(cls.end(), p->ay.cls.begin(), p->ay.cls.end());
@@ -2085,7 +2076,6 @@ void rbws_problem_destroy(rbws_problem p) {
   cudaFree(p->d_w32);
   cudaFree(p->d_w16);
   cudaFree(p->d_cscale);
-  if (p->h_active) cudaFreeHost(p->h_active);
   if (p->h_small) cudaFreeHost(p->h_small);
   if (p->ev) cudaEventDestroy(p->ev);
   for (auto& e : p->tev)
