@@ -556,7 +556,8 @@ void fill_f(float* x, int64_t n, float v, cudaStream_t s) { k_fill_f<<<152 * 4, 
 
 // Per-instance FP64 true residual norms ||f - A u|| / ||f||  (B values, device).
 rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const double* u,
-                           double* r_out, double* rel_dev, const int* mask = nullptr) {
+                           double* r_out, double* rel_dev, const int* mask = nullptr, const float* uh = nullptr,
+                           const float* ul = nullptr) {
   Tile t = choose_tile(p->nx);
   const int tiles = ((p->nx + t.tx - 1) / t.tx) * ((p->ny + t.ty - 1) / t.ty);
   const int zc = choose_zc(p->nz, (int64_t)tiles * B);
@@ -565,8 +566,12 @@ rbws_status residual_norms(rbws_problem p, const double* coef64, int B, const do
   double* part = (double*)p->buf("res_part", sizeof(double) * (size_t)B * P, &err);
   if (err) return (rbws_status)err;
   const bool own_f = p->rhs.f != nullptr;
-  launch_residual64(p->geo, t, zc, coef64, B, own_f ? p->rhs.f : p->d_f, u, r_out, part, P, mask, p->cur,
-                    own_f ? p->rhs.stride : 0);
+  if (uh)  // u = hi + lo formed on the way, and written to u
+    launch_residual64_ff(p->geo, t, zc, coef64, B, own_f ? p->rhs.f : p->d_f, uh, ul, const_cast<double*>(u), r_out,
+                         part, P, mask, p->cur, own_f ? p->rhs.stride : 0);
+  else
+    launch_residual64(p->geo, t, zc, coef64, B, own_f ? p->rhs.f : p->d_f, u, r_out, part, P, mask, p->cur,
+                      own_f ? p->rhs.stride : 0);
   launch_norms_from_partials(part, B, P, p->fnorm, rel_dev, p->cur, own_f ? p->rhs.norms : nullptr);
   p->launches += 2;
   CK(cudaGetLastError());
@@ -1035,8 +1040,8 @@ rbws_status solve_fp32_ir(rbws_problem p, const double* d_mu, int B, double tol,
     launch_ru_ff(a, t, ff, start, ss);
     launch_norms_from_partials(ff.part, B, a.P, p->fnorm, ff.rel, ss, a.fnorm);
     launch_ru_mark(a, ff, ss);
-    launch_ff_to64(a, ff, ff.chk, ss);
-    const rbws_status rr = residual_norms(p, coef64, B, u, r64, rel, ff.chk);
+    // the FP64 check of the marked: u = hi + lo written as the residual kernel stages it
+    const rbws_status rr = residual_norms(p, coef64, B, u, r64, rel, ff.chk, ff.uh, ff.ul);
     launch_ru_reset_ff(a, t, ff, start ? 1 : 0, ss);
     return rr;
   };

@@ -94,6 +94,44 @@ __device__ __forceinline__ PRows prows(int j, int m) {
 #endif
 
 #ifdef __CUDACC__
+// hi + lo as a double, with integer operations only (the FP64 pipe runs at a small
+// fraction of the FP32 rate on this part).  For a float-float pair |lo| <= ulp(hi): the
+// 24-bit significand of hi goes to the top of a 53-bit one and lo, shifted to the same
+// scale (its bits below the double's last place dropped), is added or subtracted.  The
+// result is hi + lo to within one unit in the last place of the double.  A zero or
+// subnormal hi gives lo converted alone (subnormal floats count as zero).
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
+  unsigned H = __float_as_uint(hi), L = __float_as_uint(lo);
+  int eh = (int)((H >> 23) & 0xffu);
+  if (eh == 0) {  // hi is zero (or subnormal): the result is lo
+    H = L;
+    L = 0u;
+    eh = (int)((H >> 23) & 0xffu);
+    if (eh == 0) return 0.0;
+  }
+  const int el = (int)((L >> 23) & 0xffu);
+  long long M = (long long)((H & 0x7fffffu) | 0x800000u) << 29;  // hi's significand in 53 bits
+  if (el != 0) {
+    const long long ml = (long long)((L & 0x7fffffu) | 0x800000u);
+    const int sh = el - eh + 29;  // lo's significand scaled to M's last place
+    long long t = 0;
+    if (sh >= 0) t = ml << sh;
+    else if (sh > -25) t = ml >> (-sh);
+    M += ((H ^ L) & 0x80000000u) ? -t : t;
+  }
+  int e = eh + 896;  // double's biased exponent for M in [2^52, 2^53)
+  if (M >= (1ll << 53)) {
+    M >>= 1;
+    e += 1;
+  } else if (M < (1ll << 52)) {
+    M <<= 1;
+    e -= 1;
+  }
+  const unsigned long long bits = ((unsigned long long)(H & 0x80000000u) << 32) |
+                                  ((unsigned long long)e << 52) | ((unsigned long long)M & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -254,6 +292,11 @@ void launch_ru_reset_ff(const CGArgs<float>& a, Tile t, const FFState& ff, int s
 void launch_ru_decide(const CGArgs<float>& a, cudaStream_t s);
 // dst[k] = src[k] for k < words (dst may be pinned, mapped host memory).
 void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t words, cudaStream_t s);
+// launch_residual64 from the float-float solution: u = hi + lo (ff_to_f64) formed as the
+// planes are staged, written to u_out for the masked instances, and r = f - A u.
+void launch_residual64_ff(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
+                          const float* uh, const float* ul, double* u_out, double* r, double* rr_part, int P,
+                          const int* mask, cudaStream_t s, int64_t f_stride);
 // The end of one block of a graph-resident solve loop: counts the block in *ctr and sets the
 // while node's condition to (counts[0] > 0, the active instances) && (counts[2] == 0, no
 // TMA wait ran out) && (*ctr < cap).

@@ -78,44 +78,6 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   return __uint_as_float((hw & 0x80000000u) | ((unsigned)e << 23) | m);
 }
 
-// hi + lo as a double, with integer operations only (the FP64 pipe runs at a small
-// fraction of the FP32 rate on this part).  For a float-float pair |lo| <= ulp(hi): the
-// 24-bit significand of hi goes to the top of a 53-bit one and lo, shifted to the same
-// scale (its bits below the double's last place dropped), is added or subtracted.  The
-// result is hi + lo to within one unit in the last place of the double.  A zero or
-// subnormal hi gives lo converted alone (subnormal floats count as zero).
-__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-  unsigned H = __float_as_uint(hi), L = __float_as_uint(lo);
-  int eh = (int)((H >> 23) & 0xffu);
-  if (eh == 0) {  // hi is zero (or subnormal): the result is lo
-    H = L;
-    L = 0u;
-    eh = (int)((H >> 23) & 0xffu);
-    if (eh == 0) return 0.0;
-  }
-  const int el = (int)((L >> 23) & 0xffu);
-  long long M = (long long)((H & 0x7fffffu) | 0x800000u) << 29;  // hi's significand in 53 bits
-  if (el != 0) {
-    const long long ml = (long long)((L & 0x7fffffu) | 0x800000u);
-    const int sh = el - eh + 29;  // lo's significand scaled to M's last place
-    long long t = 0;
-    if (sh >= 0) t = ml << sh;
-    else if (sh > -25) t = ml >> (-sh);
-    M += ((H ^ L) & 0x80000000u) ? -t : t;
-  }
-  int e = eh + 896;  // double's biased exponent for M in [2^52, 2^53)
-  if (M >= (1ll << 53)) {
-    M >>= 1;
-    e += 1;
-  } else if (M < (1ll << 52)) {
-    M <<= 1;
-    e -= 1;
-  }
-  const unsigned long long bits = ((unsigned long long)(H & 0x80000000u) << 32) |
-                                  ((unsigned long long)e << 52) | ((unsigned long long)M & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
-}
-
 __device__ __forceinline__ void split_f64(double x, float& h, float& l) {
   h = __double2float_rn(x);
   l = __double2float_rn(x - (double)h);

@@ -305,6 +305,41 @@ __global__ void k_residual64(Geo g, int tiles_x, int zc, const double* __restric
   if (threadIdx.x == 0 && threadIdx.y == 0) rr_part[(int64_t)b * P + tp.part] = acc;
 }
 
+// The same residual from the float-float solution of the mixed-precision iteration: each
+// staged value is hi + lo converted to FP64 (ff_to_f64), and each node's value is written
+// to u (the FP64 solution that the check decides on), so no separate conversion pass reads
+// and writes the solution first.
+__global__ void k_residual64_ff(Geo g, int tiles_x, int zc, const double* __restrict__ coef,
+                                const double* __restrict__ f, int64_t f_stride, const float* __restrict__ uh,
+                                const float* __restrict__ ul, double* __restrict__ u, double* __restrict__ r,
+                                double* __restrict__ rr_part, int P, const int* __restrict__ mask) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[64];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  const int b = blockIdx.z;
+  if (mask && !mask[b]) return;
+  const TilePos tp = tile_pos(g, tiles_x, zc);
+  const int64_t off = (int64_t)b * g.n;
+  const float* hb = uh + off;
+  const float* lb = ul + off;
+  double* ub = u + off;
+  const double* fb = f ? f + (int64_t)b * f_stride : nullptr;
+  double* rb = r ? r + off : nullptr;
+  const double* cb = coef + (int64_t)b * g.ncls() * kCoefStride;
+  double acc = 0.0;
+  zmarch<double, true>(
+      g, cb, tp.x0, tp.y0, tp.z0, tp.z1, sm, [&](int64_t idx) { return ff_to_f64(hb[idx], lb[idx]); },
+      [&](int64_t idx, double uc, double rv, double) {  // uc = u at the node, rv = f - A u
+        ub[idx] = uc;
+        if (rb) rb[idx] = rv;
+        acc = fma(rv, rv, acc);
+      },
+      [&](int64_t idx) { return fb ? fb[idx] : 1.0; });
+  double dummy = 0.0;
+  block_sum2(acc, dummy, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) rr_part[(int64_t)b * P + tp.part] = acc;
+}
+
 // ---------------------------------------------------------------------------
 // PCG phase kernels.  Per iteration k (parity = k % 2):
 //   A: beta = rho_k / rho_{k-1};  p_new = s + beta p_old (staged, halo too);
@@ -1141,6 +1176,18 @@ void launch_residual64(const Geo& g, Tile t, int zc, const double* coef, int B, 
   dim3 grid(tiles_x * tiles_y, nzc, B), block(t.tx, t.ty);
   k_residual64<<<grid, block, plane_smem(t, sizeof(double)), s>>>(g, tiles_x, zc, coef, f, f_stride, u, r,
                                                                   rr_part, tiles_x * tiles_y * nzc, mask);
+}
+
+void launch_residual64_ff(const Geo& g, Tile t, int zc, const double* coef, int B, const double* f,
+                          const float* uh, const float* ul, double* u_out, double* r, double* rr_part, int P,
+                          const int* mask, cudaStream_t s, int64_t f_stride) {
+  const int tiles_x = (g.nx + t.tx - 1) / t.tx, tiles_y = (g.ny + t.ty - 1) / t.ty;
+  const int nzc = (g.nz + zc - 1) / zc;
+  (void)P;
+  dim3 grid(tiles_x * tiles_y, nzc, B), block(t.tx, t.ty);
+  k_residual64_ff<<<grid, block, plane_smem(t, sizeof(double)), s>>>(g, tiles_x, zc, coef, f, f_stride, uh, ul,
+                                                                     u_out, r, rr_part, tiles_x * tiles_y * nzc,
+                                                                     mask);
 }
 
 template <typename T>
