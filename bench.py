@@ -102,11 +102,16 @@ class ClockSampler:
 
 
 def traffic_per_dof(kernel_tag):
-    """DRAM bytes per active DoF of a kernel from a committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", kernel_tag + ".md")
+    """DRAM bytes per active DoF of a kernel from a committed ncu summary, or None.
+
+    A tag "file#kernel" reads the line "traffic_bytes_per_dof[kernel]:" of a summary that
+    covers several kernels; a plain tag reads "traffic_bytes_per_dof:"."""
+    name, _, sub = kernel_tag.partition("#")
+    key = "traffic_bytes_per_dof[%s]:" % sub if sub else "traffic_bytes_per_dof:"
+    path = os.path.join(ROOT, "profiles", name + ".md")
     try:
         for line in open(path):
-            if line.strip().startswith("traffic_bytes_per_dof:"):
+            if line.strip().startswith(key):
                 return float(line.split(":", 1)[1].split()[0])
     except OSError:
         pass
@@ -860,6 +865,8 @@ def main():
             # with the V-cycle as preconditioner the update phase stores no s
             up_name, alg_update, up_tag = ("k_cg_b_v4 (u += alpha p, r -= alpha q, r.r; s from the V-cycle)", 24,
                                            "cg_update_phase_f32_v4_mg_64cube")
+            if sched == 2:
+                st_tag = "cg_stencil_phase_f32_tma_mg_64cube"
     else:
         st_name, alg_stencil, st_tag = "k_cg_a<double> (FP64 stencil phase)", 32, None
         up_name, alg_update, up_tag = "k_cg_b<double> (FP64 update phase)", 56, None
@@ -906,8 +913,8 @@ def main():
                          "mg_fine_smooth_od_f32_64cube"),
                         ("k_mg_fine_rr_tma (restricted residual P^T (r - A Y))", 8.5,
                          "mg_fine_residual_restrict_f32_64cube"),
-                        ("k_mg_prolong_add4 (Y += P e)", 8.5, None),
-                        ("k_mg_smooth_tma<0,0> (damped Jacobi step)", 12.0, None),
+                        ("k_mg_prolong_add4 (Y += P e)", 8.5, "mg_fine_prolong_smooth_f32_64cube#prolong"),
+                        ("k_mg_smooth_tma<0,0> (damped Jacobi step)", 12.0, "mg_fine_prolong_smooth_f32_64cube#smooth"),
                         ("k_mg_smooth_tma<0,1> (damped Jacobi step + rho partials)", 12.0,
                          "mg_fine_smooth_rho_f32_64cube")]
         mf = acc["mg_fine_ms"]
