@@ -241,7 +241,8 @@ RBWS_API void rbws_problem_destroy(rbws_problem p);
  * its boundary value reaches the right-hand side through rbws_dirichlet_lift.  Every
  * value must be finite and >= 0, and every node needs a positive diagonal for the
  * coefficients mu the caller will pass (mu_q >= 0 with sum_q mu_q kappa_q > 0 keeps A(mu)
- * symmetric positive definite).  f_host: host [n] or NULL for f = 1.  Each axis needs
+ * symmetric positive definite); a node whose six faces are zero in every term is
+ * rejected (RBWS_ERR_INVALID_ARG).  f_host: host [n] or NULL for f = 1.  Each axis needs
  * 2 <= n <= 256 (each node is its own coefficient class, 8-bit per axis); 1 <= Q <= 64.
  * The solvers, warm starts, the greedy, L1ROC and the multigrid preconditioner (Galerkin
  * coarse operators of every term, one coefficient row per coarse node) all apply; the

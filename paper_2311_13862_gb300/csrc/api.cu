@@ -1972,6 +1972,23 @@ extern "C" rbws_status rbws_problem_create_field(const rbws_grid* grid, int32_t 
         set_error("rbws_problem_create_field: face coefficients must be finite and >= 0");
         return RBWS_ERR_INVALID_ARG;
       }
+  // a node whose six faces are zero in every term has a zero row for every mu
+  for (int k = 0; k < nz; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) {
+        bool pos = false;
+        for (int q = 0; q < Q && !pos; q++) {
+          const double* fx = kfx + q * sfx + ((int64_t)k * ny + j) * (nx + 1) + i;
+          const double* fy = kfy + q * sfy + ((int64_t)k * (ny + 1) + j) * nx + i;
+          const double* fz = kfz + q * sfz + ((int64_t)k * ny + j) * nx + i;
+          pos = fx[0] > 0.0 || fx[1] > 0.0 || fy[0] > 0.0 || fy[nx] > 0.0 || fz[0] > 0.0 || fz[(int64_t)ny * nx] > 0.0;
+        }
+        if (!pos) {
+          set_error("rbws_problem_create_field: node (" + std::to_string(i) + ", " + std::to_string(j) + ", " +
+                    std::to_string(k) + ") has no positive face coefficient in any term");
+          return RBWS_ERR_INVALID_ARG;
+        }
+      }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();

@@ -160,3 +160,36 @@ def test_explicit_maps_are_checked_before_the_device(lib_path):
     if not torch.cuda.is_available():
         with pytest.raises(rbws.RbwsError, match="CUDA"):  # accepted; no device here
             rbws.rbws_problem_create(grid, None, Q=3, subdomain_map=m)
+
+
+def test_face_fields_are_checked_before_the_device(lib_path):
+    """Face-field problems: sizes, face values and rows that are zero in every term are
+    rejected on the host; a valid field reaches device set-up."""
+    import numpy as np
+    import torch
+    from paper_2311_13862_gb300 import rbws
+    nx, ny, nz, Q = 5, 4, 3, 2
+    kfx = np.ones((Q, nz, ny, nx + 1))
+    kfy = np.ones((Q, nz, ny + 1, nx))
+    kfz = np.ones((Q, nz + 1, ny, nx))
+    with pytest.raises(rbws.RbwsError, match="INVALID_ARG"):
+        rbws.rbws_problem_create_field((1, ny, nz), kfx[:, :, :, :2], kfy[:, :, :, :1], kfz[:, :, :, :1])
+    for arr, val in ((kfx, -1.0), (kfy, np.nan), (kfz, np.inf)):
+        bad = arr.copy()
+        bad[1, 1, 1, 1] = val
+        args = [kfx, kfy, kfz]
+        args[[id(a) for a in (kfx, kfy, kfz)].index(id(arr))] = bad
+        with pytest.raises(rbws.RbwsError, match="finite and >= 0"):
+            rbws.rbws_problem_create_field((nx, ny, nz), *args)
+    # node (2, 1, 1): its six faces zero in both terms
+    zx, zy, zz = kfx.copy(), kfy.copy(), kfz.copy()
+    zx[:, 1, 1, 2:4] = 0.0
+    zy[:, 1, 1:3, 2] = 0.0
+    zz[:, 1:3, 1, 2] = 0.0
+    with pytest.raises(rbws.RbwsError, match=r"node \(2, 1, 1\) has no positive face"):
+        rbws.rbws_problem_create_field((nx, ny, nz), zx, zy, zz)
+    # zero in one term only: the other term keeps the row
+    zx[1], zy[1], zz[1] = kfx[1], kfy[1], kfz[1]
+    if not torch.cuda.is_available():
+        with pytest.raises(rbws.RbwsError, match="CUDA"):  # accepted; no device here
+            rbws.rbws_problem_create_field((nx, ny, nz), zx, zy, zz)
