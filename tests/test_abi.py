@@ -81,19 +81,26 @@ def test_options_default_sets_every_field(lib_path):
     assert o.wait_cycles == 0 and o.ru_mode == 0 and o.persistent == 0
 
 
-def _ckpt_bytes(nx=4, ny=3, nz=2, blocks=(2, 1, 1), N=2, checksum_ok=True, submap=None, Q=None):
+def _ckpt_bytes(nx=4, ny=3, nz=2, blocks=(2, 1, 1), N=2, checksum_ok=True, submap=None, Q=None, faces=None):
     """A checkpoint in the library's documented layout (no network, f = 1; the subdomain map
-    submap [n] uint8 with Q subdomains if given, else the block rule)."""
+    submap [n] uint8 with Q subdomains if given, else the block rule; with faces = (kfx, kfy,
+    kfz), a face-field problem of Q terms: version 4, the axes and the face arrays first)."""
     import struct
     import numpy as np
     n = nx * ny * nz
-    Q = blocks[0] * blocks[1] * blocks[2] if submap is None else Q
-    payload = ((b"" if submap is None else np.asarray(submap, dtype=np.uint8).tobytes())
+    Q = blocks[0] * blocks[1] * blocks[2] if submap is None and faces is None else Q
+    version, has_map, head = 2, int(submap is not None), b""
+    if faces is not None:
+        version, has_map = 4, 2
+        # rbws_axes: kappa_scale f64[3], neumann_hi i32[3], reserved i32
+        head = struct.pack("<3d4i", 1.0, 1.0, 1.0, 0, 0, 0, 0)
+        head += b"".join(np.ascontiguousarray(a, dtype=np.float64).tobytes() for a in faces)
+    payload = (head + (b"" if submap is None else np.asarray(submap, dtype=np.uint8).tobytes())
                + np.arange(N * n, dtype=np.float64).tobytes() + np.ones(Q * N * N).tobytes()
                + np.ones(N).tobytes())
     # i32 fields: nx ny nz bx by bz Q has_f N net_H net_N has_map, then 4 bytes of padding
-    hdr = struct.pack("<8sI12i4x2dQ", b"RBWSPRB1", 2, nx, ny, nz, blocks[0], blocks[1], blocks[2], Q, 0, N, 0, 0,
-                      int(submap is not None), 0.0, 0.0, len(payload))
+    hdr = struct.pack("<8sI12i4x2dQ", b"RBWSPRB1", version, nx, ny, nz, blocks[0], blocks[1], blocks[2], Q, 0, N,
+                      0, 0, has_map, 0.0, 0.0, len(payload))
     h = 1469598103934665603
     for c in payload:
         h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
@@ -134,6 +141,20 @@ def test_checkpoint_loader_accepts_a_valid_file_up_to_device_set_up(tmp_path, li
         rbws.rbws_load(ok)
     ok.write_bytes(_ckpt_bytes(submap=[0, 2, 1, 0] + [0] * 20, Q=2))
     with pytest.raises(rbws.RbwsError, match="INVALID_ARG"):  # map value 2 >= Q
+        rbws.rbws_load(ok)
+    # a face-field problem (version 4): the face arrays travel in the payload
+    import numpy as np
+    nx, ny, nz, Q = 4, 3, 2, 2
+    kfx, kfy, kfz = np.ones((Q, nz, ny, nx + 1)), np.ones((Q, nz, ny + 1, nx)), np.ones((Q, nz + 1, ny, nx))
+    ok.write_bytes(_ckpt_bytes(Q=Q, faces=(kfx, kfy, kfz)))
+    with pytest.raises(rbws.RbwsError, match="CUDA"):
+        rbws.rbws_load(ok)
+    kfx[:, 0, 0, 0:2], kfy[:, 0, 0:2, 0], kfz[:, 0:2, 0, 0] = 0.0, 0.0, 0.0  # node (0, 0, 0): no face left
+    ok.write_bytes(_ckpt_bytes(Q=Q, faces=(kfx, kfy, kfz)))
+    with pytest.raises(rbws.RbwsError, match="INVALID_ARG"):
+        rbws.rbws_load(ok)
+    ok.write_bytes(_ckpt_bytes(Q=Q, faces=(kfx, kfy, kfz))[:-9])
+    with pytest.raises(rbws.RbwsError, match="truncated"):
         rbws.rbws_load(ok)
 
 
