@@ -40,10 +40,32 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+constexpr int kGemmThreads = 128;
+constexpr int kStageElems = BM * BK / kGemmThreads;  // elements of a k-tile per thread and operand
+static_assert(BM == BN && BM * BK % kGemmThreads == 0, "k-tile staging");
+
+// One k-tile of both operands into registers, every load issued before any is used:
+// A(m0 + r, k0 + c) and B(k0 + c, n0 + r) for the elements e = tid + 128 u (r = e / BK,
+// c = e % BK), zero outside the operands.
+__device__ __forceinline__ void gemm_load_tile(const MlpGemm& g, int m0, int n0, int k0, float (&va)[kStageElems],
+                                               float (&vb)[kStageElems]) {
+#pragma unroll
+  for (int u = 0; u < kStageElems; u++) {
+    const int e = threadIdx.x + kGemmThreads * u, r = e / BK, c = e % BK, m = m0 + r, k = k0 + c;
+    va[u] = (m < g.M && k < g.K) ? ld_any(g.A, g.a_bf16, (int64_t)m * g.sam + (int64_t)k * g.sak) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kStageElems; u++) {
+    const int e = threadIdx.x + kGemmThreads * u, r = e / BK, c = e % BK, n = n0 + r, k = k0 + c;
+    vb[u] = (n < g.N && k < g.K) ? ld_any(g.B, g.b_bf16, (int64_t)k * g.sbk + (int64_t)n * g.sbn) : 0.f;
+  }
+}
+
 // C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]); Z = C, Aout = GELU(C).
 // A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn]; operands are rounded to
-// BF16 when staged in shared memory.  4 warps, 64x64 CTA tile, 32x32 per warp.
-__global__ void __launch_bounds__(128) k_gemm_bf16(MlpGemm g) {
+// BF16 when staged in shared memory.  4 warps, 64x64 CTA tile, 32x32 per warp.  The
+// next k-tile's loads are in flight while the MMAs of the current one run.
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(MlpGemm g) {
   __shared__ __align__(16) __nv_bfloat16 As[BM][BKP];
   __shared__ __align__(16) __nv_bfloat16 Bs[BN][BKP];
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -57,18 +79,17 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(MlpGemm g) {
     for (int j = 0; j < 4; j++)
 #pragma unroll
       for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
+  float va[kStageElems], vb[kStageElems];
+  if (g.K > 0) gemm_load_tile(g, m0, n0, 0, va, vb);
   for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
-      const int r = e / BK, c = e % BK, m = m0 + r, k = k0 + c;
-      const float v = (m < g.M && k < g.K) ? ld_any(g.A, g.a_bf16, (int64_t)m * g.sam + (int64_t)k * g.sak) : 0.f;
-      As[r][c] = __float2bfloat16(v);
-    }
-    for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
-      const int r = e / BK, c = e % BK, n = n0 + r, k = k0 + c;
-      const float v = (n < g.N && k < g.K) ? ld_any(g.B, g.b_bf16, (int64_t)k * g.sbk + (int64_t)n * g.sbn) : 0.f;
-      Bs[r][c] = __float2bfloat16(v);
+#pragma unroll
+    for (int u = 0; u < kStageElems; u++) {
+      const int e = threadIdx.x + kGemmThreads * u;
+      As[e / BK][e % BK] = __float2bfloat16(va[u]);
+      Bs[e / BK][e % BK] = __float2bfloat16(vb[u]);
     }
     __syncthreads();
+    if (k0 + BK < g.K) gemm_load_tile(g, m0, n0, k0 + BK, va, vb);
 #pragma unroll
     for (int mt = 0; mt < 2; mt++) {
       const int rb = wm + mt * 16;
@@ -267,7 +288,7 @@ inline int blocks_for(int64_t n, int t) { return (int)std::min<int64_t>((n + t -
 
 void launch_mlp_gemm(const MlpGemm& g, cudaStream_t s) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+  k_gemm_bf16<<<grid, kGemmThreads, 0, s>>>(g);
 }
 
 void launch_mlp_inputs(const double* mu, int B, int p, double lo, double hi, float* x, cudaStream_t s) {
