@@ -487,8 +487,18 @@ RBWS_API rbws_status rbws_reduced_solve(rbws_problem p, const double* mu, int32_
  * Galerkin coefficients of the n parameters, computed on the device), loss =
  * mean squared error of the scaled coefficients, Adam (beta 0.9/0.999, eps
  * 1e-8) with learning rate lr, minibatches of `batch` in the given order
- * (the remainder n % batch is unused), `epochs` passes.  Parameters start
- * from U(-1/sqrt(fan_in), 1/sqrt(fan_in)) drawn by splitmix64(seed + index).
+ * (the remainder n % batch is unused), `epochs` passes.
+ *  - Coefficient scales: scale_j = sqrt(mean_b c[b][j]^2) over the n targets
+ *    (1 where that is 0), rounded to FP32; the network fits c[b][j] / scale_j.
+ *  - Initial parameters, U(-1/sqrt(fan_in), 1/sqrt(fan_in)): parameter i
+ *    (0-based, in the layout above) takes the (i+1)-th output z of splitmix64
+ *    started from state `seed` (Steele, Lea & Flood 2014), u = (z >> 11) 2^-53,
+ *    and the value (2u - 1) b rounded to FP32, with b = 1/sqrt(fan_in) rounded
+ *    to FP32 and fan_in the layer's input width (p for W1 and b1, H for the
+ *    others).  epochs = 0 installs these parameters untrained.
+ *  - Adam (Kingma & Ba 2015, Algorithm 1), per minibatch step t = 1, 2, ...:
+ *    m = 0.9 m + 0.1 g, v = 0.999 v + 0.001 g^2,
+ *    w -= lr (m / (1 - 0.9^t)) / (sqrt(v / (1 - 0.999^t)) + 1e-8), in FP32.
  * final_loss_out: mean minibatch loss of the last epoch (NaN if epochs = 0).
  * Needs a basis; replaces any previous network. */
 RBWS_API rbws_status rbws_train_surrogate(rbws_problem p, const double* mu, int32_t n,

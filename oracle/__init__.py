@@ -17,8 +17,11 @@ Function map (paper passage -> function):
   Sec. 3.1 L1ROC (Algorithm 5, DEIM,   oracle.l1roc: offline(), colloc_solve(), l1_indicator()
     over-collocation)                    (numpy)
   learned warm start network           mlp_forward(), mlp_loss_grad()
-Parity status: all pinned by CPU tests except trained network weights
-("parity unpinned": only forward/backward are pinned).
+  its training set-up (starting draw,  oracle.mlp_train: init_params(), rms_scale(),
+    target scales, Adam step)            normalise(), adam() (numpy)
+Parity status: every function is pinned by CPU tests.  Training is compared with the GPU
+through its starting parameters and its first Adam step; longer runs of the GPU training
+are judged by what the network buys (its warm start against a zero start).
 """
 from __future__ import annotations
 

@@ -72,6 +72,41 @@ def test_gradients_match_oracle(small_problem):
         off += sz
 
 
+def test_initial_parameters_and_first_adam_step_match_oracle(small_problem):
+    """epochs = 0 installs the starting parameters: bitwise the oracle's draw (splitmix64 as
+    the header states it).  One epoch of one minibatch is one Adam step from them: the scales
+    and the loss at the start match the oracle's FP64 network, and every parameter moves as
+    the oracle's Adam step on the oracle's FP64 gradient (about lr against the gradient's
+    sign), except where the BF16 operands' rounding decides a sign."""
+    from oracle import mlp_train as T
+    w, op, basis = small_problem
+    p, N, H, seed, lr = op.Q, basis.N, 32, 11, 1e-3
+    mu = inputs.surrogate_mu(w, 64)
+    kw = dict(hidden=H, batch=64, lr=lr, mu_lo=w.mu_lo, mu_hi=w.mu_hi, seed=seed)
+    with rbws.Problem(w.grid, w.blocks) as P:
+        rbws.rbws_set_basis(P.h, basis.W, basis.ANq, basis.fN)
+        rbws.rbws_train_surrogate(P.h, mu, epochs=0, **kw)
+        H0, theta0, scale0 = rbws.rbws_surrogate_get_params(P.h)
+        loss1 = rbws.rbws_train_surrogate(P.h, mu, epochs=1, **kw)
+        _, theta1, scale1 = rbws.rbws_surrogate_get_params(P.h)
+    assert H0 == H
+    assert np.array_equal(theta0, T.init_params(p, H, N, seed))
+    C = np.stack([O.rb_solve(basis.ANq, basis.fN, m) for m in mu])
+    np.testing.assert_allclose(scale0, T.rms_scale(C), rtol=1e-6)
+    assert np.array_equal(scale1, scale0)
+    x = T.normalise(mu, w.mu_lo, w.mu_hi)
+    loss_ref, g = O.mlp_loss_grad(p, H, N, theta0.astype(np.float64), x, C / scale0.astype(np.float64))
+    assert loss1 == pytest.approx(loss_ref, rel=3e-2)
+    step = theta1.astype(np.float64) - theta0.astype(np.float64)
+    ref_step = T.adam(theta0, 0.0, 0.0, g, 1, lr)[0] - theta0.astype(np.float64)
+    assert np.all(np.abs(step) <= lr * (1 + 1e-4))
+    for name, a, e, _ in T.layer_segments(p, H, N):
+        ga = g[a:e]
+        clear = np.abs(ga) > 0.1 * np.sqrt(np.mean(ga * ga))
+        off = np.abs(step[a:e] - ref_step[a:e]) > 1e-2 * lr
+        assert np.count_nonzero(off & clear) <= max(1, int(0.01 * np.count_nonzero(clear))), name
+
+
 @pytest.fixture(scope="module")
 def halves_problem():
     """16^3, two half-cubes: the RB warm start pays off here (N = 10)."""
