@@ -1106,18 +1106,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// The driver entry point is the same for every device: looked up once per process (the
+// initialisation of a function-local static is thread-safe).
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -1156,7 +1156,8 @@ bool tma_supported(const Geo& g, Tile t) {
          tma_smem_bytes(t) <= 200 * 1024;
 }
 
-// Once per process and device, outside any stream capture.
+// Raises the TMA kernels' shared-memory limit on the current device; called before their
+// launches, outside any stream capture (cheap to repeat).
 void tma_prepare() {
   cudaFuncSetAttribute(k_cg_a_tma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_cg_a_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
