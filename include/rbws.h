@@ -342,8 +342,7 @@ RBWS_API rbws_status rbws_update_ff(rbws_problem p, const double* mu, int32_t B,
  * (3*bx+2)*(3*by+2)*(3*bz+2)); larger requests return RBWS_ERR_INVALID_ARG
  * with the sizes in the message.  The first call on a device (and the first
  * after the caller reset that device's context) sets up the array's device
- * address with cudaGetSymbolAddress; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
+ * address with cudaGetSymbolAddress.  All calls share the array and it keeps the last call's contents;
  * every call overwrites what it reads, so nothing needs to start at zero.
  * Calls whose GPU work overlaps (from two threads, two problems on one
  * device, or two streams) race on the array.  Synchronous: the call returns
