@@ -1,6 +1,10 @@
 // rb.cu -- reduced basis kernels: batched reduced Galerkin solve (Sec. 2.3),
 // lift u0 = W c (Algorithm 4, line 2), and the dense helpers of the offline
-// greedy (projections W^T y, Gram-Schmidt updates).  All FP64.
+// greedy (projections W^T y, Gram-Schmidt updates), in FP64; for the
+// mixed-precision starts the FP32 lift (k_lift32) and the projections W^T f_b of
+// per-instance sources (k_project_tc on the tensor cores with split TF32
+// operands, k_project32 on the CUDA cores above N = 48), FP64 sums across runs;
+// the Gaussian sources of the per-instance-source workload and the L1 indicator.
 #include <cuda_runtime.h>
 
 #include <algorithm>

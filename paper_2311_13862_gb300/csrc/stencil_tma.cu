@@ -10,6 +10,11 @@
 // starts stay 16-byte aligned because tiles start at multiples of 4 nodes).
 // p at the neighbours is formed from the staged s and p_old when it is read.
 //
+// The same ring feeds the other TMA kernels of this file: phase B of the
+// 32-byte schedule (k_cg_b_s_tma), and the finest-level multigrid steps --
+// the damped Jacobi steps (k_mg_smooth_tma, k_mg_smooth_od_tma with omega/D
+// staged beside r) and the residual + restriction pass (k_mg_fine_rr_tma).
+//
 // Every mbarrier wait is bounded (about 2 s of clock64 time).  A CTA whose
 // wait runs out sets *err, lets its outstanding copies land (again bounded)
 // and returns; the host reports RBWS_ERR_DEVICE_TIMEOUT.
