@@ -1,7 +1,10 @@
 // api.cu -- the C ABI of librbws and the host-side orchestration: problem
-// set-up, the batched PCG driver (CUDA-graph captured iterations with device
-// convergence masks), FP32-inner / FP64-outer refinement, the Galerkin warm
-// start and the offline greedy.
+// set-up (block rule, explicit maps, anisotropic / Neumann axes, face-field
+// problems), the batched PCG driver (CUDA-graph captured iterations with device
+// convergence masks), FP32-inner / FP64-outer refinement (its blocks looped on
+// the device by a conditional graph node), the warm starts (Galerkin, L1ROC,
+// learned), the offline greedy, uneven request batches, the autotuner and
+// checkpoints.
 #include <cuda_runtime.h>
 
 #include <algorithm>
